@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark of the Strang-split Vlasov step (arXiv:1206.3229, Sec. 3) on GB300.
+
+Default workload: HMF model, 4096 x 4096 grid, theta in [-pi, pi) periodic, p in [-2, 2) with f = 0
+outside, dt = 0.05, homogeneous waterbag (U = 0.55) with a 1e-6 cos(theta) mode, FP64.  A "step"
+is one full Strang step (x half-shift, force, p-shift, x half-shift, moments).
+
+Prints ONE JSON line (rank 0).  value = cell-updates/s of the whole job (N ranks x Nx*Np*K / max
+time).  Multi-GPU runs are independent replicas (no data-path collective); the NCCL process group
+only provides the barrier and the max-over-ranks of the time.
+
+--impl reference times the FP64 CPU oracle (the independent C implementation the tests use) on the
+host cores, on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1206_3229_gb300 import inputs as I  # noqa: E402
+
+METRIC = "Vlasov cell-updates/s"
+UNIT = "cell-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_by_name(name: str) -> I.Workload:
+    return I.WORKLOADS[name]
+
+
+def oracle_grid(w):
+    import oracle as O
+    return O.Grid(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.x_periodic, w.p_periodic, w.dt,
+                  w.eps, w.G)
+
+
+def cpu_oracle_timing(w: I.Workload, f0: np.ndarray, budget_s: float, max_steps: int) -> dict:
+    """The FP64 oracle as it stands, on all host cores: whole Strang steps of the same workload."""
+    import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    g = oracle_grid(w)
+    f = np.array(f0, copy=True)
+    t0 = time.perf_counter()
+    f, _ = O.run(g, f, 1, with_moments=True)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    more = int(max(0, min(max_steps - 1, budget_s / max(per, 1e-9) - 1)))
+    if more:
+        f, _ = O.run(g, f, more, with_moments=True)
+    t2 = time.perf_counter()
+    steps = 1 + more
+    elapsed = t2 - t0
+    return {"value": w.cells * steps / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full Strang step(s) of {w.name} ({w.nx}x{w.np}, FP64, moments each step) "
+                      f"in {elapsed:.2f} s"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    f0 = I.initial_state(w)
+    import oracle as O
+    cores = O.set_threads(os.cpu_count() or 1)
+    g = oracle_grid(w)
+    f = np.array(f0, copy=True)
+    # warm-up and sizing: each "step" is one full oracle Strang step of the workload
+    t0 = time.perf_counter()
+    f, _ = O.run(g, f, max(args.warmup, 1), with_moments=True)
+    per = (time.perf_counter() - t0) / max(args.warmup, 1)
+    steps = int(max(1, min(args.steps, 150.0 / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    f, _ = O.run(g, f, steps, with_moments=True)
+    el = time.perf_counter() - t0
+    v = w.cells * steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": f"{w.nx}x{w.np}", "dt": w.dt, "precision": "f64",
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} full Strang steps of {w.name} on {cores} host threads"
+                                       + ("" if steps == args.steps else f" (capped from {args.steps})")},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=I.HMF_4096_UNSTABLE.name, choices=sorted(I.WORKLOADS))
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-f32", action="store_true", help="skip the secondary FP32 measurement")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = workload_by_name(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1206_3229_gb300 import vlasov as V
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    f0 = I.initial_state(w)
+    cells = w.cells
+    esz = 8 if args.precision == "f64" else 4
+    stream = torch.cuda.Stream()
+    sim = V.Sim.from_workload(w, precision=args.precision, stream=stream.cuda_stream)
+    sim.set_f(f0)
+
+    # warm-up (the first step captures the CUDA graphs)
+    sim.step(args.warmup)
+    sim.sync()
+    sim.moments()
+
+    # ---- timed region: K graph-launched steps, device events on the solver's stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    hist = sim.moments()
+    value = world * cells * args.steps / (ms_max * 1e-3)
+
+    # ---- per-kernel durations (eager launches with events on the same stream)
+    slot_ms = sim.step_timed(4)
+    names = sim.slot_names()
+    peak_gbs, peak_src = _peaks()
+    shift_bytes = 2.0 * cells * esz   # one read + one write of f per sweep (the algorithmic traffic)
+    dom = int(np.argmax(slot_ms))
+    dom_name = names[dom]
+    achieved = shift_bytes / (slot_ms[dom] * 1e-3) / 1e9 if "shift" in dom_name else None
+    step_gbs = 3 * shift_bytes / (ms_max / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                "frac": (achieved / peak_gbs) if achieved else None, "traffic": None,
+                "peak_source": peak_src,
+                "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(names, slot_ms)},
+                "per_kernel_gbs": {n: round(shift_bytes / (v * 1e-3) / 1e9, 1) for n, v in zip(names, slot_ms)
+                                   if "shift" in n and not n.endswith("filters")}}
+
+    # ---- end to end through the public API with host buffers
+    pinned = torch.empty((w.np, w.nx), dtype=torch.float64, pin_memory=True).numpy()
+    pinned[...] = f0
+    out = torch.empty((w.np, w.nx), dtype=torch.float64, pin_memory=True).numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_f(pinned)
+    sim.step(args.steps)
+    m = sim.moments()
+    sim.get_f(out)
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    et = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_s = float(et.item())
+    e2e = {"value": world * cells * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": cells * 8 / args.steps,
+           "d2h_bytes_per_step": (cells * 8 + 64 * args.steps) / args.steps,
+           "note": "one job per timed region: vlasov_set_f from pinned host f0, K steps, moments and f back"}
+    launches = sim.kernels_per_step() * args.steps
+
+    # ---- secondary: the FP32-storage path on the same workload
+    f32 = None
+    if not args.no_f32 and args.precision == "f64":
+        s32 = V.Sim.from_workload(w, precision="f32", stream=stream.cuda_stream)
+        s32.set_f(f0)
+        s32.step(args.warmup)
+        s32.sync()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        s32.step(args.steps)
+        a1.record(stream)
+        a1.synchronize()
+        ms32 = a0.elapsed_time(a1)
+        sl32 = s32.step_timed(4)
+        v32 = cells * args.steps / (ms32 * 1e-3)
+        f32 = {"value": world * v32, "ms_per_step": ms32 / args.steps,
+               "hbm_roofline_frac_step": 3 * 2.0 * cells * 4 / (ms32 / args.steps * 1e-3) / 1e9 / peak_gbs,
+               "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(s32.slot_names(), sl32)}}
+        s32.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_timing(w, f0, args.cpu_budget, 50)
+
+    sim.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": w.name, "grid": f"{w.nx}x{w.np}", "dt": w.dt, "precision": args.precision,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": f"inputs larger than L2: each sweep streams {2 * cells * esz / 1e6:.0f} MB "
+                                 "(read + write) against a 129 MB L2"},
+                "hbm_roofline_frac_step": step_gbs / peak_gbs,
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "gpu_launches": launches,
+                "clocks": clk.summary(),
+                "moments_last": {"t": float(hist[-1, 0]), "mass": float(hist[-1, 1]),
+                                 "M": float(np.hypot(hist[-1, 2], hist[-1, 3])), "energy": float(hist[-1, 6])}
+                if len(hist) else None,
+                "f32": f32}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,130 @@
+/*
+ * vlasov.h -- C ABI of libvlasov.so, a GB300 (sm_103a) solver for the one-dimensional Vlasov
+ * equation with long-range mean-field forces, by the semi-Lagrangian Strang split of
+ * T. M. Rocha Filho, arXiv:1206.3229 (Sec. 3):
+ *
+ *   step 1  f^(I)(x,p)    = f(x - p dt/2, p)            Eq. (step1)
+ *   step 2  F^(I)(x)      = mean-field force of f^(I)   Eq. (step2), (meanforce)
+ *   step 3  f^(II)(x,p)   = f^(I)(x, p - F^(I)(x) dt)   Eq. (step3)
+ *   step 4  f(x,p,t+dt)   = f^(II)(x - p dt/2, p)       Eq. (step4)
+ *
+ * Every shift takes the cubic-spline value at the foot of the characteristic, Eqs. (splinegen,
+ * splinecoeffs), with f'' from the eighth-order 9-point central difference, Eq. (findif).
+ *
+ * Storage (Sec. 3): f[j*Nx + i] with x (theta) contiguous, j the momentum row.  Nodes are
+ * x_i = xmin + i*dx, dx = (xmax-xmin)/Nx and p_j = pmin + j*dp, dp = (pmax-pmin)/Np.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (VLASOV_OK) or a negative VLASOV_E* code; no call aborts the process.  The text of
+ *    the last error of the calling thread is returned by vlasov_last_error().
+ *  - Host arrays are borrowed for the duration of the call and copied; device arrays named
+ *    "dev_*" must be device memory of the current device, and stay owned by the caller.
+ *  - One simulation handle must not be used by two threads at once; different handles are
+ *    independent.  Work is enqueued on the handle's stream; calls documented as "syncs" wait for it.
+ */
+#ifndef VLASOV_H
+#define VLASOV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VLASOV_OK 0
+#define VLASOV_EINVAL (-1)   /* bad argument: sizes, domain, dt, model, precision */
+#define VLASOV_ENOMEM (-2)   /* device or host allocation failed */
+#define VLASOV_ECUDA (-3)    /* a CUDA runtime/driver call failed (message has the CUDA text) */
+#define VLASOV_ETIMEOUT (-4) /* a bounded device-side wait expired; results of that step are void */
+#define VLASOV_ESTATE (-5)   /* call not valid in the handle's state (e.g. step before set_f) */
+
+/* Force models of Sec. 2.  FREE has F = 0 (free streaming; for tests). */
+enum { VLASOV_HMF = 0, VLASOV_RING = 1, VLASOV_SHEET = 2, VLASOV_FREE = 3 };
+
+/* Storage/arithmetic of f.  F64: IEEE double storage and arithmetic.  F32: float storage and
+   interpolation; displacements, spline weights and all moment sums stay FP64. */
+enum { VLASOV_F64 = 0, VLASOV_F32 = 1 };
+
+typedef struct vlasov_sim vlasov_sim; /* opaque; owns every device buffer it uses */
+
+typedef struct {
+    double xmin, xmax;   /* x (theta) domain; x_periodic=1 wraps it */
+    double pmin, pmax;   /* momentum domain */
+    int x_periodic;      /* 1: periodic; 0: f = 0 (and f'' = 0) outside the grid */
+    int p_periodic;      /* same for p */
+    double eps;          /* ring softening of Eq. (ringpot), > 0 for VLASOV_RING */
+    double G;            /* sheet coupling: V(x) = 2 pi G |x| */
+    int precision;       /* VLASOV_F64 or VLASOV_F32 */
+    void* stream;        /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
+} vlasov_domain;
+
+/* Moments of f after a full step (Sec. 4 diagnostics): mass = int f, Mx/My = int cos/sin(x) f
+   (Eq. mxmydef), kinetic = int p^2/2 f, potential = 1/2 int int V(x-x') rho rho', energy = sum. */
+typedef struct {
+    double t, mass, Mx, My, kinetic, potential, energy;
+    long long step;
+} vlasov_moments_t;
+
+/* Create a simulation on the current CUDA device.
+   Nx, Np: multiples of 8, 16 <= N; Nx <= 4096 for F64 and <= 8192 for F32 (x rows are staged
+   whole in shared memory).
+   dt > 0.  domain: xmin < xmax, pmin < pmax; eps > 0 for the ring model.
+   On success *out owns ~2*Nx*Np*sizeof(f) + O(Nx*#SM) bytes of device memory.
+   Errors: VLASOV_EINVAL, VLASOV_ENOMEM, VLASOV_ECUDA. */
+int vlasov_create(int model, int Nx, int Np, const vlasov_domain* domain, double dt,
+                  vlasov_sim** out);
+
+/* Upload f (host, Np*Nx doubles, f[j*Nx+i]); converts to the handle's precision.  Resets the
+   step counter and the moment history.  Syncs. */
+int vlasov_set_f(vlasov_sim* sim, const double* host_f);
+
+/* Same from a device array of Np*Nx doubles (e.g. a torch tensor's data_ptr()). Enqueued. */
+int vlasov_set_f_device(vlasov_sim* sim, const double* dev_f);
+
+/* Download the current f as doubles (host, Np*Nx).  Syncs.  VLASOV_ETIMEOUT if a device wait
+   expired since the last check. */
+int vlasov_get_f(vlasov_sim* sim, double* host_f);
+
+/* Same into device memory (Np*Nx doubles).  Enqueued. */
+int vlasov_get_f_device(vlasov_sim* sim, double* dev_f);
+
+/* Enqueue n Strang steps (Sec. 3 steps 1-4).  Asynchronous: launches CUDA graphs on the handle's
+   stream.  The moments of f after each step are appended to a device ring of 4096 records. */
+int vlasov_step(vlasov_sim* sim, int n);
+
+/* Copy out up to max moment records produced since the previous call (oldest first) into out,
+   set *count.  Records older than the ring's 4096 are dropped (count tells what is returned).
+   Syncs; VLASOV_ETIMEOUT if a device wait expired. */
+int vlasov_moments(vlasov_sim* sim, vlasov_moments_t* out, int max, int* count);
+
+/* Test hooks (each syncs).
+   vlasov_substep: one shift of the current f along axis 0 (x, rows) or 1 (p, columns) by the
+     given displacements in cells (host; Np values for axis 0, Nx for axis 1): node i takes the
+     spline value at i - disp.  Eqs. (step1)/(step3) with an arbitrary displacement.
+   vlasov_density_force: density rho_i = dp sum_j f[j,i] and force F_i of Eq. (meanforce) for the
+     current f (host outputs of Nx doubles; either may be NULL). */
+int vlasov_substep(vlasov_sim* sim, int axis, const double* host_disp);
+int vlasov_density_force(vlasov_sim* sim, double* host_rho, double* host_F);
+
+/* Wait for the handle's stream and report any device-side error flag. */
+int vlasov_sync(vlasov_sim* sim);
+
+/* Free every device resource of the handle (NULL is ignored). */
+void vlasov_destroy(vlasov_sim* sim);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* vlasov_last_error(void);
+
+/* Number of kernel launches one vlasov_step(1) enqueues for this handle (for launch accounting). */
+int vlasov_kernels_per_step(const vlasov_sim* sim);
+
+/* Run n steps with eager launches (no graph) and a CUDA event around every kernel, on the handle's
+   stream; ms_per_launch[q] receives the mean duration of launch slot q of a step (q <
+   vlasov_kernels_per_step; max_launches must be at least that), *nlaunch the slot count.  Slots in
+   order: x-shift (step 1, density partials), density/moment reduction, [ring force], p-shift
+   filters (force), p-shift (step 3), x-shift (step 4, density+kinetic partials), moment
+   reduction, [ring potential].  Syncs. */
+int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

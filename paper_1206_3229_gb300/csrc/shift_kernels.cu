@@ -1,0 +1,555 @@
+// shift_kernels.cu -- the two sweeps of the Strang split (Sec. 3 of arXiv:1206.3229).
+//
+//  x-shift (Eqs. step1/step4): every p row j moves by s_j = p_j dt/(2 dx) cells.  Row-constant
+//  spline weights (one 10-tap filter per row), so a CTA stages whole rows in shared memory with
+//  1-D bulk (TMA) copies, a few rows in flight, and each thread produces V = 16/sizeof(T)
+//  consecutive outputs from a register window loaded with 16-byte shared-memory reads; the output
+//  is one coalesced 16-byte store per thread.  Optional epilogue: per-column sums (density) and
+//  the p^2/2-weighted row sums (kinetic energy) of the produced rows.
+//
+//  p-shift (Eq. step3): every x column i moves by sigma_i = F_i dt/dp cells.  Done in the natural
+//  layout (no global transpose): a tile of 32 columns x 128 output rows stages the union window
+//  of input rows it needs with 2-D TMA boxes (out-of-range rows come back as zeros, which is the
+//  f = 0 outside reading of the p axis), each thread walks 16 rows of one column with a sliding
+//  register window.
+#include "ptx.cuh"
+#include "vlasov_internal.cuh"
+
+namespace vl {
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<double> {
+    static constexpr int V = 2;
+    static constexpr int W = 12;   // window: V + 9 taps + alignment slack, rounded to V
+    using vec = double2;
+    using acc = double;
+};
+template <>
+struct VecOf<float> {
+    static constexpr int V = 4;
+    static constexpr int W = 16;
+    using vec = float4;
+    using acc = float;
+};
+
+constexpr int XS_MAXCH = 8;   // chunks of V*threads outputs per row handled by one thread
+
+// Dynamic shared memory rounded up to a 128-byte boundary (TMA destinations); every launch
+// reserves 128 extra bytes for this.
+__device__ __forceinline__ unsigned char* align128(unsigned char* p)
+{
+    const uint32_t a = smem_u32(p);
+    return p + ((128u - (a & 127u)) & 127u);
+}
+
+// D_k of Eq. (findif) (undivided) for a window starting at f_{k-4}.
+template <typename T>
+__device__ __forceinline__ T fd_undivided(const T* x)
+{
+    const T c0 = T(VL_FD_C0), c1 = T(VL_FD_C1), c2 = T(VL_FD_C2), c3 = T(VL_FD_C3), c4 = T(VL_FD_C4);
+    return c4 * (x[0] + x[8]) + c3 * (x[1] + x[7]) + c2 * (x[2] + x[6]) + c1 * (x[3] + x[5]) + c0 * x[4];
+}
+
+// Non-periodic axes take f'' = 0 at nodes outside the grid.  The 10-tap filter evaluates D at
+// k and k+1 from the zero-extended f, so remove those terms when k or k+1 lies outside [0, n).
+// `x` starts at f_{k-4}.
+template <typename T>
+__device__ __forceinline__ T edge_fix(T out, const T* x, int k, int n, T g, T d)
+{
+    if (k < 0 || k >= n) out -= g * fd_undivided(x);
+    if (k + 1 < 0 || k + 1 >= n) out -= d * fd_undivided(x + 1);
+    return out;
+}
+
+// ============================================================================ x-shift
+template <typename T, int A, bool PERIODIC>
+__device__ __forceinline__ void xshift_chunk(const T* __restrict__ rowbuf, int e, const T (&w)[NTAP],
+                                             int i, int k, int Nx, T g, T d, T (&out)[VecOf<T>::V])
+{
+    constexpr int V = VecOf<T>::V, W = VecOf<T>::W;
+    using vec = typename VecOf<T>::vec;
+    T x[W];
+    const vec* p = reinterpret_cast<const vec*>(rowbuf + e);
+#pragma unroll
+    for (int q = 0; q < W / V; ++q) {
+        vec v = p[q];
+        if constexpr (V == 2) {
+            x[2 * q] = v.x;
+            x[2 * q + 1] = v.y;
+        } else {
+            x[4 * q] = v.x;
+            x[4 * q + 1] = v.y;
+            x[4 * q + 2] = v.z;
+            x[4 * q + 3] = v.w;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        T acc = w[0] * x[A + v];
+#pragma unroll
+        for (int t = 1; t < NTAP; ++t) acc = fma(w[t], x[A + v + t], acc);
+        out[v] = acc;
+    }
+    if constexpr (!PERIODIC) {
+        if (k < 0 || k + V - 1 >= Nx - 1) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = edge_fix(out[v], &x[A + v], k + v, Nx, g, d);
+        }
+    }
+    (void)i;
+}
+
+template <typename T, int A, bool PERIODIC>
+__device__ __forceinline__ void xshift_row(const T* __restrict__ rowbuf, T* __restrict__ orow,
+                                           const T (&w)[NTAP], int n0, int Nx, T g, T d, int nthreads,
+                                           typename VecOf<T>::acc (&colacc)[XS_MAXCH][VecOf<T>::V],
+                                           typename VecOf<T>::acc& rowsum)
+{
+    constexpr int V = VecOf<T>::V;
+    using vec = typename VecOf<T>::vec;
+    const int tid = threadIdx.x;
+    int base;   // window start of output 0 (aligned down by A)
+    if constexpr (PERIODIC) {
+        base = (n0 - 4 - A) % Nx;
+        if (base < 0) base += Nx;
+    } else {
+        base = n0 - 4 - A;
+    }
+#pragma unroll
+    for (int c = 0; c < XS_MAXCH; ++c) {
+        const int i = V * (tid + c * nthreads);
+        if (i < Nx) {
+            int e = i + base;
+            if constexpr (PERIODIC) {
+                if (e >= Nx) e -= Nx;
+            }
+            T out[V];
+            xshift_chunk<T, A, PERIODIC>(rowbuf, e, w, i, i + n0, Nx, g, d, out);
+            vec o;
+            if constexpr (V == 2) {
+                o.x = out[0];
+                o.y = out[1];
+            } else {
+                o.x = out[0];
+                o.y = out[1];
+                o.z = out[2];
+                o.w = out[3];
+            }
+            *reinterpret_cast<vec*>(orow + i) = o;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                colacc[c][v] += out[v];
+                rowsum += out[v];
+            }
+        }
+    }
+}
+
+template <typename T, bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
+{
+    constexpr int V = VecOf<T>::V;
+    using acc_t = typename VecOf<T>::acc;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    T* bufs = reinterpret_cast<T*>(smem_raw + 128);
+    __shared__ double red[32];
+
+    const T* __restrict__ fin = static_cast<const T*>(a.fin);
+    T* __restrict__ fout = static_cast<T*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
+    const int stride = Nx + 2 * PAD;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int G = gridDim.x;
+    const T* __restrict__ wrow = static_cast<const T*>(a.w);
+    const T* __restrict__ gdrow = static_cast<const T*>(a.gd);
+    const uint32_t row_bytes = (uint32_t)(Nx * sizeof(T));
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 16u * (uint32_t)sizeof(T) : 0u);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    if constexpr (!PERIODIC) {
+        // zero halos of every stage (never touched by the copies)
+        for (int s = 0; s < S; ++s) {
+            T* b = bufs + (size_t)s * stride;
+            for (int e = tid; e < PAD; e += nthreads) {
+                b[e] = T(0);
+                b[PAD + Nx + e] = T(0);
+            }
+        }
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int r) {
+        T* dst = bufs + (size_t)s * stride + PAD;
+        const T* src = fin + (size_t)r * Nx;
+        mbar_arrive_expect_tx(&bars[s], tx_bytes);
+        bulk_g2s(dst, src, row_bytes, &bars[s]);
+        if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 16u * (uint32_t)sizeof(T), &bars[s]);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            const int r = blockIdx.x + s * G;
+            if (r < Np) issue(s, r);
+        }
+    }
+
+    acc_t colacc[XS_MAXCH][V];
+#pragma unroll
+    for (int c = 0; c < XS_MAXCH; ++c)
+#pragma unroll
+        for (int v = 0; v < V; ++v) colacc[c][v] = acc_t(0);
+    double kin = 0.0;
+
+    int it = 0;
+    int r = blockIdx.x;
+    bool failed = false;
+    for (; r < Np; r += G, ++it) {
+        const int s = it % S;
+        const uint32_t parity = (uint32_t)((it / S) & 1);
+        const bool ok = mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS);
+        acc_t rowsum = acc_t(0);
+        if (ok) {
+            const int n0 = a.n0[r];
+            T w[NTAP];
+#pragma unroll
+            for (int t = 0; t < NTAP; ++t) w[t] = wrow[(size_t)t * Np + r];
+            T g = T(0), d = T(0);
+            if constexpr (!PERIODIC) {
+                g = gdrow[r];
+                d = gdrow[Np + r];
+            }
+            const T* rowbuf = bufs + (size_t)s * stride + PAD;
+            T* orow = fout + (size_t)r * Nx;
+            const int A = (n0 - 4) & (V - 1);
+            if constexpr (V == 2) {
+                if (A == 0) xshift_row<T, 0, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum);
+                else        xshift_row<T, 1, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum);
+            } else {
+                switch (A) {
+                    case 0: xshift_row<T, 0, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
+                    case 1: xshift_row<T, 1, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
+                    case 2: xshift_row<T, 2, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
+                    default: xshift_row<T, 3, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
+                }
+            }
+            if constexpr (KIN) {
+                const double pj = a.pmin + (double)r * a.dp;
+                kin += 0.5 * pj * pj * (double)rowsum;
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            const int rn = r + S * G;
+            if (rn < Np) {
+                fence_proxy_async_smem();
+                issue(s, rn);
+            }
+        }
+    }
+
+    if (failed) {
+        // Record the failure and wait (bounded) for this CTA's copies still in flight.
+        if (tid == 0) {
+            atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
+            for (int k = 0; k < S; ++k) {
+                const int rr = r + k * G;
+                if (rr >= Np) break;
+                const int itk = it + k;
+                mbar_wait_bounded(&bars[itk % S], (uint32_t)((itk / S) & 1), WAIT_LIMIT_NS);
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    if (a.colpart) {
+        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < XS_MAXCH; ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) cp[i + v] = (double)colacc[c][v];
+            }
+        }
+    }
+    if constexpr (KIN) {
+        double v = kin;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int q = 0; q < (nthreads + 31) / 32; ++q) s += red[q];
+            a.kinpart[blockIdx.x] = s;
+        }
+    }
+}
+
+int xshift_max_cols(int elem_bytes, int threads)
+{
+    const int V = 16 / elem_bytes;
+    return V * threads * XS_MAXCH;
+}
+
+size_t xshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
+{
+    return 256 + (size_t)stages * (size_t)(Nx + 2 * pad) * (size_t)elem_bytes;
+}
+
+template <typename T, bool P, bool K>
+static cudaError_t launch_x(int grid, int threads, const XShiftArgs& a, cudaStream_t st)
+{
+    const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, (int)sizeof(T));
+    xshift_kernel<T, P, K><<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int threads, const XShiftArgs& a,
+                          cudaStream_t st)
+{
+    if (elem_bytes == 8) {
+        if (periodic) return kin ? launch_x<double, true, true>(grid, threads, a, st)
+                                 : launch_x<double, true, false>(grid, threads, a, st);
+        return kin ? launch_x<double, false, true>(grid, threads, a, st)
+                   : launch_x<double, false, false>(grid, threads, a, st);
+    }
+    if (periodic) return kin ? launch_x<float, true, true>(grid, threads, a, st)
+                             : launch_x<float, true, false>(grid, threads, a, st);
+    return kin ? launch_x<float, false, true>(grid, threads, a, st)
+               : launch_x<float, false, false>(grid, threads, a, st);
+}
+
+// ============================================================================ p-shift
+template <typename T, bool PPER>
+__device__ __forceinline__ T gload_p(const T* __restrict__ f, int row, int col, int Nx, int Np)
+{
+    if constexpr (PPER) {
+        int rr = row % Np;
+        if (rr < 0) rr += Np;
+        return f[(size_t)rr * Nx + col];
+    } else {
+        return (row >= 0 && row < Np) ? f[(size_t)row * Nx + col] : T(0);
+    }
+}
+
+struct TileWin {
+    int i0, j0, r0, nb;
+    bool smem_ok;
+};
+
+// Window of input rows a tile needs: [j0 + kmin - 4, j0 + TH - 1 + kmax + 5].  Called by whole
+// warps (all lanes hold one column); identical in every warp.
+template <bool PPER>
+__device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __restrict__ n0, int Nx, int lane,
+                                               int& n0_lane, bool& colvalid)
+{
+    TileWin t;
+    const int tx = tile % ntx, ty = tile / ntx;
+    t.i0 = tx * PS_TW;
+    t.j0 = ty * PS_TH;
+    const int i = t.i0 + lane;
+    colvalid = i < Nx;
+    n0_lane = colvalid ? n0[i] : 0;
+    int kmin = colvalid ? n0_lane : 0x7fffffff;
+    int kmax = colvalid ? n0_lane : (int)0x80000000;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if (!colvalid) n0_lane = kmin;   // columns past Nx read (and discard) the tile's own window
+    t.r0 = t.j0 + kmin - 4;
+    const long long R = (long long)PS_TH + 9 + ((long long)kmax - (long long)kmin);
+    t.smem_ok = !PPER && R <= PS_RB;
+    t.nb = t.smem_ok ? (int)((R + PS_BH - 1) / PS_BH) : 0;
+    return t;
+}
+
+template <typename T, bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    T* bufs = reinterpret_cast<T*>(smem_raw + 128);
+    constexpr int BUF = PS_RB * PS_TW;
+
+    const T* __restrict__ fin = static_cast<const T*>(a.fin);
+    T* __restrict__ fout = static_cast<T*>(a.fout);
+    const T* __restrict__ wcol = static_cast<const T*>(a.w);
+    const T* __restrict__ gdcol = static_cast<const T*>(a.gd);
+    const int Nx = a.Nx, Np = a.Np;
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+    const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PS_TH - 1) / PS_TH;
+    const int ntiles = ntx * nty;
+    const int G = gridDim.x;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+        prefetch_tensormap(&tmap);
+    }
+    __syncthreads();
+
+    // lane 0 of warp 0: start the copies of a tile's window into buffer b (or complete the phase
+    // with no bytes when the tile takes the direct-load path).
+    auto issue = [&](int b, const TileWin& t) {
+        if (t.smem_ok) {
+            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(T)));
+            for (int q = 0; q < t.nb; ++q)
+                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, &tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
+        } else {
+            mbar_arrive_expect_tx(&bars[b], 0u);
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (grp == 0 && tile < ntiles) {
+        int n0l;
+        bool cv;
+        TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0l, cv);
+        if (lane == 0) issue(0, t);
+    }
+
+    int q = 0;
+    bool failed = false;
+    for (; tile < ntiles; tile += G, ++q) {
+        const int b = q & 1;
+        const int nt = tile + G;
+        if (grp == 0 && nt < ntiles) {
+            int n0l;
+            bool cv;
+            TileWin tn = tile_window<PPER>(nt, ntx, a.n0, Nx, lane, n0l, cv);
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(b ^ 1, tn);
+            }
+        }
+        int n0_i;
+        bool colvalid;
+        const TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0_i, colvalid);
+        const int i = t.i0 + lane;
+        T w[NTAP];
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) w[k] = colvalid ? wcol[(size_t)k * Nx + i] : T(0);
+        T g = T(0), d = T(0);
+        if constexpr (!PPER) {
+            if (colvalid) {
+                g = gdcol[i];
+                d = gdcol[Nx + i];
+            }
+        }
+        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
+        if (ok) {
+            const int jb = t.j0 + grp * PS_RPT;     // first output row of this thread
+            T x[PS_RPT + 9];
+            if (t.smem_ok) {
+                const T* buf = bufs + (size_t)b * BUF;
+                const int base = jb + n0_i - 4 - t.r0;
+#pragma unroll
+                for (int u = 0; u < PS_RPT + 9; ++u) x[u] = buf[(base + u) * PS_TW + lane];
+            } else {
+#pragma unroll
+                for (int u = 0; u < PS_RPT + 9; ++u)
+                    x[u] = colvalid ? gload_p<T, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : T(0);
+            }
+#pragma unroll
+            for (int rr = 0; rr < PS_RPT; ++rr) {
+                const int j = jb + rr;
+                T acc = w[0] * x[rr];
+#pragma unroll
+                for (int k = 1; k < NTAP; ++k) acc = fma(w[k], x[rr + k], acc);
+                if constexpr (!PPER) {
+                    const int kk = j + n0_i;
+                    if (kk < 0 || kk >= Np - 1) acc = edge_fix(acc, &x[rr], kk, Np, g, d);
+                }
+                if (colvalid && j < Np) fout[(size_t)j * Nx + i] = acc;
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed && tid == 0) {
+        atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+        // the prefetch of the next tile may still be in flight
+        if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
+        mbar_wait_bounded(&bars[q & 1], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
+    }
+}
+
+size_t pshift_smem_bytes(int elem_bytes)
+{
+    return 256 + 2 * (size_t)PS_RB * PS_TW * (size_t)elem_bytes;
+}
+
+template <typename T, bool PPER>
+static cudaError_t launch_p(int grid, const CUtensorMap* tmap, const PShiftArgs& a, cudaStream_t st)
+{
+    const size_t smem = pshift_smem_bytes((int)sizeof(T));
+    pshift_kernel<T, PPER><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
+                          cudaStream_t st)
+{
+    if (elem_bytes == 8) return p_periodic ? launch_p<double, true>(grid, tmap, a, st) : launch_p<double, false>(grid, tmap, a, st);
+    return p_periodic ? launch_p<float, true>(grid, tmap, a, st) : launch_p<float, false>(grid, tmap, a, st);
+}
+
+// Opt every shift kernel into the shared memory it may use (called once per device, before any
+// launch or stream capture).  Also reports the resident CTAs per SM of the two sweeps.
+cudaError_t set_kernel_attributes(int max_smem)
+{
+    cudaError_t e = cudaSuccess;
+#define VL_ATTR(fn) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)
+    VL_ATTR((xshift_kernel<double, true, true>));
+    VL_ATTR((xshift_kernel<double, true, false>));
+    VL_ATTR((xshift_kernel<double, false, true>));
+    VL_ATTR((xshift_kernel<double, false, false>));
+    VL_ATTR((xshift_kernel<float, true, true>));
+    VL_ATTR((xshift_kernel<float, true, false>));
+    VL_ATTR((xshift_kernel<float, false, true>));
+    VL_ATTR((xshift_kernel<float, false, false>));
+    VL_ATTR((pshift_kernel<double, true>));
+    VL_ATTR((pshift_kernel<double, false>));
+    VL_ATTR((pshift_kernel<float, true>));
+    VL_ATTR((pshift_kernel<float, false>));
+#undef VL_ATTR
+    return e;
+}
+
+cudaError_t xshift_occupancy(int elem_bytes, bool periodic, int threads, size_t smem, int* blocks)
+{
+    if (elem_bytes == 8)
+        return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<double, true, true>, threads, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<double, false, true>, threads, smem);
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<float, true, true>, threads, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<float, false, true>, threads, smem);
+}
+
+cudaError_t pshift_occupancy(int elem_bytes, int* blocks)
+{
+    const size_t smem = pshift_smem_bytes(elem_bytes);
+    if (elem_bytes == 8)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<double, false>, PS_TW * PS_RG, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<float, false>, PS_TW * PS_RG, smem);
+}
+
+}  // namespace vl

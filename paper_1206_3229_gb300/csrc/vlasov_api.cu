@@ -1,0 +1,724 @@
+// vlasov_api.cu -- host runtime behind the C ABI of include/vlasov.h.
+//
+// A handle owns two ping-pong copies of f, the per-row x-shift filters (fixed for the run: they
+// depend only on p_j, dt and dx), the per-column p-shift filters (rewritten every step by the
+// force), reduction scratch, a ring of per-step moment records, and two CUDA graphs holding one
+// Strang step each (one per starting buffer).  vlasov_step(n) launches those graphs n times.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vlasov.h"
+#include "vlasov_internal.cuh"
+
+using namespace vl;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU_TRY(expr)                                                                                 \
+    do {                                                                                             \
+        cudaError_t e_ = (expr);                                                                     \
+        if (e_ != cudaSuccess) return fail(VLASOV_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));   \
+    } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+constexpr int ALIGN_N = 8;
+
+}  // namespace
+
+struct vlasov_sim {
+    int model = 0, Nx = 0, Np = 0, prec = 0, esz = 8;
+    bool xper = true, pper = false;
+    double xmin = 0, xmax = 0, pmin = 0, pmax = 0, dx = 0, dp = 0, dt = 0, eps = 0, G = 1;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int dev = 0, nsm = 0;
+
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool has_f = false;
+
+    LineParamsDev xp, pp, sp;   // x rows (fixed), p columns (per step), scratch for substeps
+    int xthreads = 256, xstages = 1, xpad = 16, xgrid = 1, pgrid = 1, crgrid = 1;
+
+    double* colpart = nullptr;  // [xgrid][Nx]
+    double* kinpart = nullptr;  // [xgrid]
+    double* rho = nullptr;
+    double* F = nullptr;
+    double* Fout = nullptr;
+    double* blockpart = nullptr;
+    double* ringpart = nullptr;
+    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring
+    Scalars* sc = nullptr;
+    double* costab = nullptr;
+    double* sintab = nullptr;
+    double* ringdV = nullptr;
+    double* ringV = nullptr;
+    MomentRec* hist = nullptr;
+    long long* dstep = nullptr;
+    long long read_step = 0;
+    int* err = nullptr;
+
+    CUtensorMap tmap[2];
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void free_params(LineParamsDev& p)
+{
+    cudaFree(p.n0);
+    cudaFree(p.w);
+    cudaFree(p.gd);
+    p = LineParamsDev{};
+}
+
+int alloc_params(LineParamsDev& p, int n, int esz)
+{
+    CU_TRY(cudaMalloc(&p.n0, sizeof(int) * (size_t)n));
+    CU_TRY(cudaMalloc(&p.w, (size_t)esz * NTAP * (size_t)n));
+    CU_TRY(cudaMalloc(&p.gd, (size_t)esz * 2 * (size_t)n));
+    return VLASOV_OK;
+}
+
+// Host-side filters for n lines with displacements disp[] (cells), uploaded to p.
+int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, int* max_abs_n0)
+{
+    std::vector<int> n0(n);
+    std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n);
+    int mx = 0;
+    for (int l = 0; l < n; ++l) {
+        LineSplit L;
+        line_split(disp[l], L);
+        n0[l] = L.n0;
+        mx = std::max(mx, std::abs(L.n0));
+        for (int t = 0; t < NTAP; ++t) w[(size_t)t * n + l] = L.w[t];
+        gd[l] = L.g;
+        gd[(size_t)n + l] = L.d;
+    }
+    if (max_abs_n0) *max_abs_n0 = mx;
+    CU_TRY(cudaMemcpyAsync(p.n0, n0.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s->st));
+    if (s->esz == 8) {
+        CU_TRY(cudaMemcpyAsync(p.w, w.data(), 8 * w.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaMemcpyAsync(p.gd, gd.data(), 8 * gd.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    } else {
+        std::vector<float> wf(w.begin(), w.end()), gf(gd.begin(), gd.end());
+        CU_TRY(cudaMemcpyAsync(p.w, wf.data(), 4 * wf.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaMemcpyAsync(p.gd, gf.data(), 4 * gf.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    }
+    return VLASOV_OK;
+}
+
+int make_tmap(vlasov_sim* s, int b)
+{
+    auto enc = get_encode_tiled();
+    if (!enc) return fail(VLASOV_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)s->Nx, (cuuint64_t)s->Np};
+    cuuint64_t strides[1] = {(cuuint64_t)s->Nx * (cuuint64_t)s->esz};
+    cuuint32_t box[2] = {(cuuint32_t)PS_TW, (cuuint32_t)PS_BH};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&s->tmap[b], s->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                     s->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return VLASOV_OK;
+}
+
+XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& p, bool reduce, bool kin)
+{
+    XShiftArgs a;
+    a.fin = in;
+    a.fout = out;
+    a.Nx = s->Nx;
+    a.Np = s->Np;
+    a.pad = s->xpad;
+    a.stages = s->xstages;
+    a.n0 = p.n0;
+    a.w = p.w;
+    a.gd = p.gd;
+    a.colpart = reduce ? s->colpart : nullptr;
+    a.kinpart = kin ? s->kinpart : nullptr;
+    a.pmin = s->pmin;
+    a.dp = s->dp;
+    a.err = s->err;
+    return a;
+}
+
+PShiftArgs pargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& p)
+{
+    PShiftArgs a;
+    a.fin = in;
+    a.fout = out;
+    a.Nx = s->Nx;
+    a.Np = s->Np;
+    a.n0 = p.n0;
+    a.w = p.w;
+    a.gd = p.gd;
+    a.err = s->err;
+    return a;
+}
+
+ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments)
+{
+    ColReduceArgs a;
+    a.colpart = s->colpart;
+    a.B = B;
+    a.kinpart = kin ? s->kinpart : nullptr;
+    a.Nx = s->Nx;
+    a.dx = s->dx;
+    a.dp = s->dp;
+    a.xmin = s->xmin;
+    a.costab = s->costab;
+    a.sintab = s->sintab;
+    a.rho = s->rho;
+    a.blockpart = s->blockpart;
+    a.ticket = &s->tickets[0];
+    a.sc = s->sc;
+    a.model = s->model;
+    a.G = s->G;
+    a.F = s->F;
+    a.final_moments = final_moments ? 1 : 0;
+    a.hist = s->hist;
+    a.step = s->dstep;
+    a.dt = s->dt;
+    return a;
+}
+
+RingArgs ringargs(vlasov_sim* s, bool final_moments)
+{
+    RingArgs a;
+    a.N = s->Nx;
+    a.dx = s->dx;
+    a.rho = s->rho;
+    a.dV = s->ringdV;
+    a.V = s->ringV;
+    a.F = s->F;
+    a.blockpart = s->ringpart;
+    a.ticket = &s->tickets[1];
+    a.sc = s->sc;
+    a.final_moments = final_moments ? 1 : 0;
+    a.hist = s->hist;
+    a.step = s->dstep;
+    a.dt = s->dt;
+    return a;
+}
+
+int launch_pparams_only(vlasov_sim* s, double* Fout)
+{
+    PParamsArgs a;
+    a.Nx = s->Nx;
+    a.model = s->model;
+    a.sc = s->sc;
+    a.costab = s->costab;
+    a.sintab = s->sintab;
+    a.Fin = s->F;
+    a.cp = s->dt / s->dp;
+    a.n0 = s->pp.n0;
+    a.w = s->pp.w;
+    a.gd = s->pp.gd;
+    a.Fout = Fout;
+    CU_TRY(launch_pparams(s->esz, a, s->st));
+    return VLASOV_OK;
+}
+
+int launch_force_params(vlasov_sim* s, double* Fout)
+{
+    if (s->model == VLASOV_RING) CU_TRY(launch_ring(ringargs(s, false), s->st));
+    return launch_pparams_only(s, Fout);
+}
+
+// Optional per-launch event marks (vlasov_step_timed): ev[k] is recorded before launch k and
+// ev[k+1] after it.
+struct Marks {
+    cudaEvent_t* ev = nullptr;
+    int k = 0;
+};
+
+int mark(vlasov_sim* s, Marks* m)
+{
+    if (m && m->ev) CU_TRY(cudaEventRecord(m->ev[m->k++], s->st));
+    return VLASOV_OK;
+}
+
+#define MARK()                    \
+    do {                          \
+        int rc_ = mark(s, marks); \
+        if (rc_) return rc_;      \
+    } while (0)
+
+// Enqueue one Strang step starting from buffer c (result in buffer c^1).
+int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
+{
+    const int o = c ^ 1;
+    MARK();
+    // step 1: f^(I) = f(x - p dt/2, p), with the density partials of f^(I)
+    CU_TRY(launch_xshift(s->esz, s->xper, false, s->xgrid, s->xthreads, xargs(s, s->f[c], s->f[o], s->xp, true, false),
+                         s->st));
+    MARK();
+    // step 2: rho, moments, F^(I), p-shift filters
+    CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
+    MARK();
+    if (s->model == VLASOV_RING) {
+        CU_TRY(launch_ring(ringargs(s, false), s->st));
+        MARK();
+    }
+    {
+        int rc = launch_pparams_only(s, nullptr);
+        if (rc) return rc;
+    }
+    MARK();
+    // step 3: f^(II) = f^(I)(x, p - F dt)
+    CU_TRY(launch_pshift(s->esz, s->pper, s->pgrid, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->st));
+    MARK();
+    // step 4: f(t+dt) = f^(II)(x - p dt/2, p), with density + kinetic partials for the moments
+    CU_TRY(launch_xshift(s->esz, s->xper, true, s->xgrid, s->xthreads, xargs(s, s->f[c], s->f[o], s->xp, true, true),
+                         s->st));
+    MARK();
+    CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
+    MARK();
+    if (s->model == VLASOV_RING) {
+        CU_TRY(launch_ring(ringargs(s, true), s->st));
+        MARK();
+    }
+    return VLASOV_OK;
+}
+#undef MARK
+
+int build_graph(vlasov_sim* s, int c)
+{
+    if (s->graph[c]) return VLASOV_OK;
+    cudaGraph_t g = nullptr;
+    CU_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_step(s, c);
+    const cudaError_t e = cudaStreamEndCapture(s->st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(VLASOV_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&s->graph[c], g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return fail(VLASOV_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    return VLASOV_OK;
+}
+
+int check_dev_err(vlasov_sim* s)
+{
+    int h = 0;
+    CU_TRY(cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    if (h != DEV_ERR_NONE) {
+        cudaMemsetAsync(s->err, 0, sizeof(int), s->st);
+        return fail(VLASOV_ETIMEOUT, "a bounded device wait expired (code %d); results since the last check are void", h);
+    }
+    return VLASOV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vlasov_last_error(void) { return g_err.c_str(); }
+
+void vlasov_destroy(vlasov_sim* s)
+{
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (int b = 0; b < 2; ++b) {
+        if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+        cudaFree(s->f[b]);
+    }
+    free_params(s->xp);
+    free_params(s->pp);
+    free_params(s->sp);
+    void* bufs[] = {s->colpart, s->kinpart, s->rho, s->F, s->Fout, s->blockpart, s->ringpart, s->tickets, s->sc,
+                    s->costab, s->sintab, s->ringdV, s->ringV, s->hist, s->dstep, s->err};
+    for (void* p : bufs) cudaFree(p);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    delete s;
+}
+
+int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, vlasov_sim** out)
+{
+    if (!out) return fail(VLASOV_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(VLASOV_EINVAL, "domain is NULL");
+    if (model < VLASOV_HMF || model > VLASOV_FREE) return fail(VLASOV_EINVAL, "unknown model %d", model);
+    if (d->precision != VLASOV_F64 && d->precision != VLASOV_F32)
+        return fail(VLASOV_EINVAL, "unknown precision %d", d->precision);
+    const int esz = d->precision == VLASOV_F64 ? 8 : 4;
+    if (Nx < 16 || Np < 16 || Nx % ALIGN_N || Np % ALIGN_N)
+        return fail(VLASOV_EINVAL, "Nx=%d, Np=%d: both must be multiples of %d and >= 16", Nx, Np, ALIGN_N);
+    if (Nx > xshift_max_cols(esz, XS_THREADS_MIN))
+        return fail(VLASOV_EINVAL, "Nx=%d exceeds %d for this precision", Nx, xshift_max_cols(esz, XS_THREADS_MIN));
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(VLASOV_EINVAL, "dt must be > 0");
+    if (!(d->xmax > d->xmin) || !(d->pmax > d->pmin)) return fail(VLASOV_EINVAL, "empty domain");
+    if (model == VLASOV_RING && !(d->eps > 0)) return fail(VLASOV_EINVAL, "ring model needs eps > 0");
+
+    vlasov_sim* s = new vlasov_sim();
+    s->model = model;
+    s->Nx = Nx;
+    s->Np = Np;
+    s->prec = d->precision;
+    s->esz = esz;
+    s->xper = d->x_periodic != 0;
+    s->pper = d->p_periodic != 0;
+    s->xmin = d->xmin;
+    s->xmax = d->xmax;
+    s->pmin = d->pmin;
+    s->pmax = d->pmax;
+    s->dx = (d->xmax - d->xmin) / (double)Nx;
+    s->dp = (d->pmax - d->pmin) / (double)Np;
+    s->dt = dt;
+    s->eps = d->eps;
+    s->G = d->G;
+
+    auto bail = [&](int rc) {
+        vlasov_destroy(s);
+        return rc;
+    };
+#define TRY(expr)                 \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_) return bail(rc_); \
+    } while (0)
+#define CTRY(expr)                                                                                       \
+    do {                                                                                                 \
+        cudaError_t e_ = (expr);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? VLASOV_ENOMEM : VLASOV_ECUDA, "%s: %s", #expr, \
+                             cudaGetErrorString(e_)));                                                   \
+    } while (0)
+
+    CTRY(cudaGetDevice(&s->dev));
+    CTRY(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
+    int max_optin = 0;
+    CTRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
+    if (d->stream) {
+        s->st = static_cast<cudaStream_t>(d->stream);
+    } else {
+        CTRY(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+        s->own_stream = true;
+    }
+    CTRY(set_kernel_attributes(max_optin - 1024));
+
+    const size_t cells = (size_t)Nx * (size_t)Np;
+    for (int b = 0; b < 2; ++b) {
+        CTRY(cudaMalloc(&s->f[b], cells * esz));
+        CTRY(cudaMemsetAsync(s->f[b], 0, cells * esz, s->st));
+    }
+
+    // x-shift filters: row j moves by s_j = p_j * ((dt/2)/dx) cells.
+    std::vector<double> srow(Np);
+    {
+        const double cx = (0.5 * dt) / s->dx;
+        for (int j = 0; j < Np; ++j) {
+            const double p = s->pmin + (double)j * s->dp;
+            srow[j] = p * cx;
+        }
+    }
+    TRY(alloc_params(s->xp, Np, esz));
+    TRY(alloc_params(s->pp, Nx, esz));
+    TRY(alloc_params(s->sp, std::max(Nx, Np), esz));
+    int max_n0 = 0;
+    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0));
+
+    // x-shift launch shape: whole rows staged per CTA.
+    s->xthreads = XS_THREADS_MIN;
+    s->xpad = s->xper ? 16 : ((max_n0 + 8 + 15) / 16) * 16;
+    const size_t row_bytes = (size_t)(Nx + 2 * s->xpad) * esz;
+    const size_t smem_budget = (size_t)max_optin - 2048;
+    s->xstages = (int)std::min<size_t>(4, (smem_budget - 256) / row_bytes);
+    if (s->xstages < 1) return bail(fail(VLASOV_EINVAL, "a row of Nx=%d (+%d halo) does not fit shared memory", Nx, s->xpad));
+    int occ = 0;
+    CTRY(xshift_occupancy(esz, s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    occ = std::max(occ, 1);
+    s->xgrid = std::min(Np, s->nsm * occ);
+
+    int pocc = 0;
+    CTRY(pshift_occupancy(esz, &pocc));
+    pocc = std::max(pocc, 1);
+    const int ptiles = ((Nx + PS_TW - 1) / PS_TW) * ((Np + PS_TH - 1) / PS_TH);
+    s->pgrid = std::min(ptiles, s->nsm * pocc);
+    s->crgrid = (Nx + 31) / 32;
+
+    CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->xgrid * Nx));
+    CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->xgrid));
+    CTRY(cudaMalloc(&s->rho, sizeof(double) * Nx));
+    CTRY(cudaMalloc(&s->F, sizeof(double) * Nx));
+    CTRY(cudaMemsetAsync(s->F, 0, sizeof(double) * Nx, s->st));
+    CTRY(cudaMalloc(&s->Fout, sizeof(double) * Nx));
+    CTRY(cudaMalloc(&s->blockpart, sizeof(double) * 4 * (size_t)s->crgrid));
+    CTRY(cudaMalloc(&s->ringpart, sizeof(double) * (size_t)((Nx + 7) / 8)));
+    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 2));
+    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 2, s->st));
+    CTRY(cudaMalloc(&s->sc, sizeof(Scalars)));
+    CTRY(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->st));
+    CTRY(cudaMalloc(&s->hist, sizeof(MomentRec) * HIST_CAP));
+    CTRY(cudaMalloc(&s->dstep, sizeof(long long)));
+    CTRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
+    CTRY(cudaMalloc(&s->err, sizeof(int)));
+    CTRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->st));
+
+    // Tables on the x nodes: cos/sin for HMF (Eq. hmfmeanforce, mxmydef); ring kernel V, V'.
+    {
+        std::vector<double> c(Nx), sn(Nx), dV(Nx), V(Nx);
+        for (int i = 0; i < Nx; ++i) {
+            const double th = s->xmin + (double)i * s->dx;
+            c[i] = std::cos(th);
+            sn[i] = std::sin(th);
+            const double u = (double)i * s->dx;
+            if (model == VLASOV_RING) {
+                const double q = 1.0 - std::cos(u) + s->eps;
+                dV[i] = std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q));   // V'(u), Eq. (ringpot)
+                V[i] = -1.0 / (std::sqrt(2.0) * std::sqrt(q));                      // V(u)
+            } else {
+                dV[i] = V[i] = 0.0;
+            }
+        }
+        CTRY(cudaMalloc(&s->costab, sizeof(double) * Nx));
+        CTRY(cudaMalloc(&s->sintab, sizeof(double) * Nx));
+        CTRY(cudaMalloc(&s->ringdV, sizeof(double) * Nx));
+        CTRY(cudaMalloc(&s->ringV, sizeof(double) * Nx));
+        CTRY(cudaMemcpyAsync(s->costab, c.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaMemcpyAsync(s->sintab, sn.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaMemcpyAsync(s->ringdV, dV.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaMemcpyAsync(s->ringV, V.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaStreamSynchronize(s->st));
+    }
+    TRY(make_tmap(s, 0));
+    TRY(make_tmap(s, 1));
+#undef TRY
+#undef CTRY
+    *out = s;
+    return VLASOV_OK;
+}
+
+int vlasov_set_f(vlasov_sim* s, const double* host_f)
+{
+    if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");
+    const size_t cells = (size_t)s->Nx * s->Np;
+    if (s->esz == 8) {
+        CU_TRY(cudaMemcpyAsync(s->f[s->cur], host_f, cells * 8, cudaMemcpyHostToDevice, s->st));
+    } else {
+        std::vector<float> tmp(cells);
+        for (size_t k = 0; k < cells; ++k) tmp[k] = (float)host_f[k];
+        CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 4, cudaMemcpyHostToDevice, s->st));
+    }
+    CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    s->read_step = 0;
+    s->has_f = true;
+    return VLASOV_OK;
+}
+
+int vlasov_set_f_device(vlasov_sim* s, const double* dev_f)
+{
+    if (!s || !dev_f) return fail(VLASOV_EINVAL, "NULL argument");
+    const size_t cells = (size_t)s->Nx * s->Np;
+    CU_TRY(launch_convert(dev_f, 8, s->f[s->cur], s->esz, cells, s->st));
+    CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
+    s->read_step = 0;
+    s->has_f = true;
+    return VLASOV_OK;
+}
+
+int vlasov_get_f(vlasov_sim* s, double* host_f)
+{
+    if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");
+    const size_t cells = (size_t)s->Nx * s->Np;
+    if (s->esz == 8) {
+        CU_TRY(cudaMemcpyAsync(host_f, s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    } else {
+        std::vector<float> tmp(cells);
+        CU_TRY(cudaMemcpyAsync(tmp.data(), s->f[s->cur], cells * 4, cudaMemcpyDeviceToHost, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+        for (size_t k = 0; k < cells; ++k) host_f[k] = (double)tmp[k];
+    }
+    return check_dev_err(s);
+}
+
+int vlasov_get_f_device(vlasov_sim* s, double* dev_f)
+{
+    if (!s || !dev_f) return fail(VLASOV_EINVAL, "NULL argument");
+    const size_t cells = (size_t)s->Nx * s->Np;
+    CU_TRY(launch_convert(s->f[s->cur], s->esz, dev_f, 8, cells, s->st));
+    return VLASOV_OK;
+}
+
+int vlasov_step(vlasov_sim* s, int n)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (n < 0) return fail(VLASOV_EINVAL, "n < 0");
+    if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_step before vlasov_set_f");
+    for (int k = 0; k < n; ++k) {
+        int rc = build_graph(s, s->cur);
+        if (rc) return rc;
+        CU_TRY(cudaGraphLaunch(s->graph[s->cur], s->st));
+        s->cur ^= 1;
+    }
+    return VLASOV_OK;
+}
+
+int vlasov_moments(vlasov_sim* s, vlasov_moments_t* out, int max, int* count)
+{
+    if (!s || (!out && max > 0)) return fail(VLASOV_EINVAL, "NULL argument");
+    long long h = 0;
+    CU_TRY(cudaMemcpyAsync(&h, s->dstep, sizeof h, cudaMemcpyDeviceToHost, s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    long long first = std::max(s->read_step, h - (long long)HIST_CAP);
+    long long n = std::min<long long>(h - first, (long long)std::max(max, 0));
+    std::vector<MomentRec> tmp((size_t)std::max<long long>(n, 0));
+    for (long long k = 0; k < n; ++k) {
+        const long long idx = (first + k) % HIST_CAP;
+        CU_TRY(cudaMemcpyAsync(&tmp[(size_t)k], s->hist + idx, sizeof(MomentRec), cudaMemcpyDeviceToHost, s->st));
+    }
+    CU_TRY(cudaStreamSynchronize(s->st));
+    for (long long k = 0; k < n; ++k) {
+        const MomentRec& r = tmp[(size_t)k];
+        out[k].t = r.t;
+        out[k].mass = r.mass;
+        out[k].Mx = r.Mx;
+        out[k].My = r.My;
+        out[k].kinetic = r.kinetic;
+        out[k].potential = r.potential;
+        out[k].energy = r.energy;
+        out[k].step = r.step;
+    }
+    s->read_step = first + n;
+    if (count) *count = (int)n;
+    return check_dev_err(s);
+}
+
+int vlasov_substep(vlasov_sim* s, int axis, const double* host_disp)
+{
+    if (!s || !host_disp) return fail(VLASOV_EINVAL, "NULL argument");
+    if (axis != 0 && axis != 1) return fail(VLASOV_EINVAL, "axis must be 0 (x) or 1 (p)");
+    if (!s->has_f) return fail(VLASOV_ESTATE, "substep before vlasov_set_f");
+    const int c = s->cur, o = c ^ 1;
+    if (axis == 0) {
+        int mx = 0;
+        int rc = upload_params(s, s->sp, host_disp, s->Np, &mx);
+        if (rc) return rc;
+        XShiftArgs a = xargs(s, s->f[c], s->f[o], s->sp, false, false);
+        if (!s->xper && mx + 8 > s->xpad) {
+            // wider zero halo for this call: the staged row grows, fewer rows in flight
+            a.pad = ((mx + 8 + 15) / 16) * 16;
+            int max_optin = 0;
+            CU_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
+            const size_t row_bytes = (size_t)(s->Nx + 2 * a.pad) * s->esz;
+            const size_t budget = (size_t)max_optin - 2048 - 256;
+            a.stages = (int)std::min<size_t>(4, budget / row_bytes);
+            if (a.stages < 1) return fail(VLASOV_EINVAL, "x displacement of %d cells does not fit shared memory", mx);
+        }
+        CU_TRY(launch_xshift(s->esz, s->xper, false, s->xgrid, s->xthreads, a, s->st));
+    } else {
+        int rc = upload_params(s, s->sp, host_disp, s->Nx, nullptr);
+        if (rc) return rc;
+        CU_TRY(launch_pshift(s->esz, s->pper, s->pgrid, &s->tmap[c], pargs(s, s->f[c], s->f[o], s->sp), s->st));
+    }
+    s->cur = o;
+    CU_TRY(cudaStreamSynchronize(s->st));
+    return check_dev_err(s);
+}
+
+int vlasov_density_force(vlasov_sim* s, double* host_rho, double* host_F)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (!s->has_f) return fail(VLASOV_ESTATE, "density before vlasov_set_f");
+    CU_TRY(launch_colsum(s->esz, s->f[s->cur], s->Nx, s->Np, s->colpart, 1, s->st));
+    CU_TRY(launch_colreduce(crargs(s, 1, false, false), s->crgrid, s->st));
+    int rc = launch_force_params(s, s->Fout);
+    if (rc) return rc;
+    if (host_rho) CU_TRY(cudaMemcpyAsync(host_rho, s->rho, sizeof(double) * s->Nx, cudaMemcpyDeviceToHost, s->st));
+    if (host_F) CU_TRY(cudaMemcpyAsync(host_F, s->Fout, sizeof(double) * s->Nx, cudaMemcpyDeviceToHost, s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    return check_dev_err(s);
+}
+
+int vlasov_sync(vlasov_sim* s)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    CU_TRY(cudaStreamSynchronize(s->st));
+    return check_dev_err(s);
+}
+
+int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launches, int* nlaunch)
+{
+    if (!s || n < 1 || !ms_per_launch) return fail(VLASOV_EINVAL, "bad argument");
+    if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_step_timed before vlasov_set_f");
+    const int L = vlasov_kernels_per_step(s);
+    if (max_launches < L) return fail(VLASOV_EINVAL, "max_launches < %d", L);
+    std::vector<cudaEvent_t> ev((size_t)(L + 1) * n, nullptr);
+    for (auto& e : ev) CU_TRY(cudaEventCreate(&e));
+    int rc = VLASOV_OK;
+    for (int k = 0; k < n && !rc; ++k) {
+        Marks m;
+        m.ev = ev.data() + (size_t)k * (L + 1);
+        rc = enqueue_step(s, s->cur, &m);
+        s->cur ^= 1;
+    }
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) rc = fail(VLASOV_ECUDA, "sync: %s", cudaGetErrorString(e));
+    }
+    if (!rc) {
+        for (int q = 0; q < L; ++q) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[(size_t)k * (L + 1) + q], ev[(size_t)k * (L + 1) + q + 1]);
+                acc += ms;
+            }
+            ms_per_launch[q] = acc / n;
+        }
+        if (nlaunch) *nlaunch = L;
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc) return rc;
+    return check_dev_err(s);
+}
+
+int vlasov_kernels_per_step(const vlasov_sim* s)
+{
+    if (!s) return 0;
+    return s->model == VLASOV_RING ? 8 : 6;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// vlasov_internal.cuh -- shared declarations of the CUDA library (kernels + host runtime).
+//
+// Layout (Sec. 3 of arXiv:1206.3229): f[j*Nx + i], x contiguous, p rows.  Two ping-pong buffers
+// hold f; a Strang step is x-shift (A->B), p-shift (B->A), x-shift (A->B).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vl {
+
+// ---------------------------------------------------------------------------------------------
+// Eq. (findif): f''(u_k) du^2 = sum_{m=-4..4} c_|m| f(u_{k+m}), c = -205/72, 8/5, -1/5, 8/315, -1/560.
+#define VL_FD_C0 (-205.0 / 72.0)
+#define VL_FD_C1 (8.0 / 5.0)
+#define VL_FD_C2 (-1.0 / 5.0)
+#define VL_FD_C3 (8.0 / 315.0)
+#define VL_FD_C4 (-1.0 / 560.0)
+
+constexpr int NTAP = 10;          // the spline + FD stencil spans f_{k-4} .. f_{k+5}
+constexpr int HIST_CAP = 4096;    // moment records kept on the device
+
+// Spline weights of one line for a displacement s (cells).  Eqs. (splinegen, splinecoeffs) with
+// f''_k = D_k/du^2 and D_k = sum_m c_|m| f_{k+m}: the du^2 of gamma/delta cancels, so
+//   f_new(i) = alpha f_k + beta f_{k+1} + g D_k + d D_{k+1},  k = i + n0,
+//   g = (alpha^3 - alpha)/6, d = (beta^3 - beta)/6,
+// which is the 10-tap filter  f_new(i) = sum_{t=0..9} w_t f_{k-4+t}.
+struct LineSplit {
+    int n0;
+    double alpha, beta, g, d;
+    double w[NTAP];
+};
+
+__host__ __device__ inline void line_split(double s, LineSplit& L)
+{
+    const double ms = -s;
+    const double fl = floor(ms);
+    L.n0 = (int)fl;
+    L.beta = ms - fl;
+    L.alpha = 1.0 - L.beta;
+    const double a = L.alpha, b = L.beta;
+    L.g = (a * a * a - a) / 6.0;
+    L.d = (b * b * b - b) / 6.0;
+    const double g = L.g, d = L.d;
+    L.w[0] = g * VL_FD_C4;
+    L.w[1] = g * VL_FD_C3 + d * VL_FD_C4;
+    L.w[2] = g * VL_FD_C2 + d * VL_FD_C3;
+    L.w[3] = g * VL_FD_C1 + d * VL_FD_C2;
+    L.w[4] = a + g * VL_FD_C0 + d * VL_FD_C1;
+    L.w[5] = b + g * VL_FD_C1 + d * VL_FD_C0;
+    L.w[6] = g * VL_FD_C2 + d * VL_FD_C1;
+    L.w[7] = g * VL_FD_C3 + d * VL_FD_C2;
+    L.w[8] = g * VL_FD_C4 + d * VL_FD_C3;
+    L.w[9] = d * VL_FD_C4;
+}
+
+// Per-line parameters in device memory, structure-of-arrays over `n` lines:
+//   n0[line], w[t*n + line] (t < 10), gd[line] = g, gd[n + line] = d  (in the storage type T).
+struct LineParamsDev {
+    int* n0 = nullptr;
+    void* w = nullptr;
+    void* gd = nullptr;
+};
+
+// Device-side error codes written to the handle's flag by a bounded wait that gave up.
+enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2 };
+
+// Scalars produced by the reductions of one sweep (device struct).
+struct Scalars {
+    double mass, Mx, My, kinetic, potential;
+};
+
+// One moment record (mirrors vlasov_moments_t).
+struct MomentRec {
+    double t, mass, Mx, My, kinetic, potential, energy;
+    long long step;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Launch arguments.
+struct XShiftArgs {
+    const void* fin;
+    void* fout;
+    int Nx, Np;
+    int pad;              // zero/halo elements each side of a staged row
+    int stages;           // rows in flight per CTA
+    const int* n0;        // per row
+    const void* w;        // [10][Np] in T
+    const void* gd;       // [2][Np] in T
+    double* colpart;      // [gridDim.x][Nx] column sums of the output, or null
+    double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
+    double pmin, dp;
+    int* err;
+};
+
+struct PShiftArgs {
+    const void* fin;
+    void* fout;
+    int Nx, Np;
+    const int* n0;        // per column
+    const void* w;        // [10][Nx] in T
+    const void* gd;       // [2][Nx] in T
+    int* err;
+};
+
+struct ColReduceArgs {
+    const double* colpart;   // [B][Nx]
+    int B;
+    const double* kinpart;   // [B] or null
+    int Nx;
+    double dx, dp, xmin;
+    const double* costab;    // cos(x_i), sin(x_i)
+    const double* sintab;
+    double* rho;             // [Nx] out
+    double* blockpart;       // [gridDim.x][4] scratch
+    unsigned int* ticket;    // zero on entry; reset by the last block
+    Scalars* sc;             // out
+    int model;
+    double G;                // sheet
+    double* F;               // sheet: force out [Nx]
+    int final_moments;       // 1: write the moment record (all models but ring)
+    MomentRec* hist;
+    long long* step;
+    double dt;
+};
+
+struct PParamsArgs {
+    int Nx, model;
+    const Scalars* sc;
+    const double* costab;
+    const double* sintab;
+    const double* Fin;       // ring / sheet force [Nx]
+    double cp;               // dt / dp
+    int* n0;
+    void* w;
+    void* gd;
+    double* Fout;            // optional copy of F [Nx]
+};
+
+struct RingArgs {
+    int N;
+    double dx;
+    const double* rho;
+    const double* dV;        // V'(m dx), m = 0..N-1
+    const double* V;         // V(m dx)
+    double* F;               // out
+    double* blockpart;       // [gridDim.x]
+    unsigned int* ticket;
+    Scalars* sc;
+    int final_moments;
+    MomentRec* hist;
+    long long* step;
+    double dt;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Launchers (return cudaError_t of the launch).
+constexpr int XS_THREADS_MIN = 256;
+int xshift_max_cols(int elem_bytes, int threads);
+size_t xshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes);
+cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int threads,
+                          const XShiftArgs& a, cudaStream_t st);
+
+constexpr int PS_TW = 32;        // columns per tile (one warp lane per column)
+constexpr int PS_RG = 8;         // row groups (warps) per CTA
+constexpr int PS_RPT = 16;       // output rows per thread
+constexpr int PS_TH = PS_RG * PS_RPT;  // output rows per tile
+constexpr int PS_BH = 32;        // rows per TMA box
+constexpr int PS_RB = 256;       // staged rows per buffer
+size_t pshift_smem_bytes(int elem_bytes);
+cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUtensorMap* tmap,
+                          const PShiftArgs& a, cudaStream_t st);
+
+cudaError_t set_kernel_attributes(int max_smem);
+cudaError_t xshift_occupancy(int elem_bytes, bool periodic, int threads, size_t smem, int* blocks);
+cudaError_t pshift_occupancy(int elem_bytes, int* blocks);
+
+cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
+cudaError_t launch_ring(const RingArgs& a, cudaStream_t st);
+cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double* colpart, int B,
+                          cudaStream_t st);
+cudaError_t launch_convert(const void* src, int src_bytes, void* dst, int dst_bytes, size_t n,
+                           cudaStream_t st);
+
+}  // namespace vl

@@ -1,0 +1,207 @@
+"""ctypes binding of libvlasov.so (include/vlasov.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels.  The binding fails loudly when the
+library is missing or no CUDA device is present; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+from .inputs import Workload
+
+HMF, RING, SHEET, FREE = 0, 1, 2, 3
+F64, F32 = 0, 1
+MODELS = {"hmf": HMF, "ring": RING, "sheet": SHEET, "free": FREE}
+PRECISIONS = {"f64": F64, "f32": F32}
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+
+EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_f", "vlasov_get_f_device",
+            "vlasov_step", "vlasov_moments", "vlasov_substep", "vlasov_density_force", "vlasov_sync",
+            "vlasov_destroy", "vlasov_last_error", "vlasov_kernels_per_step", "vlasov_step_timed")
+
+
+class VlasovError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vlasov error {code}: {msg}")
+        self.code = code
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("pmin", ctypes.c_double), ("pmax", ctypes.c_double),
+                ("x_periodic", ctypes.c_int), ("p_periodic", ctypes.c_int),
+                ("eps", ctypes.c_double), ("G", ctypes.c_double),
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Moments(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("mass", ctypes.c_double), ("Mx", ctypes.c_double),
+                ("My", ctypes.c_double), ("kinetic", ctypes.c_double), ("potential", ctypes.c_double),
+                ("energy", ctypes.c_double), ("step", ctypes.c_longlong)]
+
+
+MOMENT_FIELDS = ("t", "mass", "Mx", "My", "kinetic", "potential", "energy")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libvlasov.so (building it first if it is missing or stale and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libvlasov.so not found at {path}; run paper_1206_3229_gb300/build.py")
+        lib = ctypes.CDLL(path)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        lib.vlasov_create.argtypes = [ip, ip, ip, ctypes.POINTER(Domain), ctypes.c_double, ctypes.POINTER(vp)]
+        lib.vlasov_set_f.argtypes = [vp, dp]
+        lib.vlasov_set_f_device.argtypes = [vp, vp]
+        lib.vlasov_get_f.argtypes = [vp, dp]
+        lib.vlasov_get_f_device.argtypes = [vp, vp]
+        lib.vlasov_step.argtypes = [vp, ip]
+        lib.vlasov_moments.argtypes = [vp, ctypes.POINTER(Moments), ip, ctypes.POINTER(ctypes.c_int)]
+        lib.vlasov_substep.argtypes = [vp, ip, dp]
+        lib.vlasov_density_force.argtypes = [vp, dp, dp]
+        lib.vlasov_sync.argtypes = [vp]
+        lib.vlasov_destroy.argtypes = [vp]
+        lib.vlasov_destroy.restype = None
+        lib.vlasov_last_error.argtypes = []
+        lib.vlasov_last_error.restype = ctypes.c_char_p
+        lib.vlasov_kernels_per_step.argtypes = [vp]
+        lib.vlasov_step_timed.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ctypes.c_int)]
+        for name in EXPORTED:
+            if name not in ("vlasov_destroy", "vlasov_last_error"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise VlasovError(rc, _lib.vlasov_last_error().decode(errors="replace"))
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Sim:
+    """One simulation handle (vlasov_create ... vlasov_destroy)."""
+
+    def __init__(self, model: str | int, nx: int, np_: int, xmin: float, xmax: float, pmin: float,
+                 pmax: float, dt: float, x_periodic: bool = True, p_periodic: bool = False,
+                 eps: float = 0.0, G: float = 1.0, precision: str | int = "f64", stream: int | None = None):
+        lib = load()
+        self.model = MODELS[model] if isinstance(model, str) else int(model)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.nx, self.np = int(nx), int(np_)
+        dom = Domain(xmin, xmax, pmin, pmax, int(x_periodic), int(p_periodic), eps, G, self.precision,
+                     ctypes.c_void_p(stream) if stream else None)
+        h = ctypes.c_void_p()
+        _check(lib.vlasov_create(self.model, self.nx, self.np, ctypes.byref(dom), float(dt), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    @classmethod
+    def from_workload(cls, w: Workload, precision: str = "f64", stream: int | None = None) -> "Sim":
+        return cls(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.dt, w.x_periodic, w.p_periodic,
+                   w.eps, w.G, precision, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vlasov_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def set_f(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.nx * self.np
+        _check(self._lib.vlasov_set_f(self._h, _dptr(f)))
+
+    def set_f_device(self, dev_ptr: int):
+        _check(self._lib.vlasov_set_f_device(self._h, ctypes.c_void_p(dev_ptr)))
+
+    def get_f(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.np, self.nx), dtype=np.float64)
+        _check(self._lib.vlasov_get_f(self._h, _dptr(out)))
+        return out
+
+    def get_f_device(self, dev_ptr: int):
+        _check(self._lib.vlasov_get_f_device(self._h, ctypes.c_void_p(dev_ptr)))
+
+    def step(self, n: int = 1):
+        _check(self._lib.vlasov_step(self._h, int(n)))
+
+    def moments(self, max_records: int = 4096) -> np.ndarray:
+        """Records since the previous call, as an array [n, 8]: t, mass, Mx, My, kinetic, potential, energy, step."""
+        buf = (Moments * max(max_records, 1))()
+        cnt = ctypes.c_int(0)
+        _check(self._lib.vlasov_moments(self._h, buf, int(max_records), ctypes.byref(cnt)))
+        return np.array([[getattr(buf[k], f) for f in MOMENT_FIELDS] + [buf[k].step] for k in range(cnt.value)],
+                        dtype=np.float64).reshape(-1, 8)
+
+    def substep(self, axis: int, disp: np.ndarray):
+        disp = np.ascontiguousarray(disp, dtype=np.float64)
+        assert disp.size == (self.np if axis == 0 else self.nx)
+        _check(self._lib.vlasov_substep(self._h, int(axis), _dptr(disp)))
+
+    def density_force(self):
+        rho = np.empty(self.nx)
+        F = np.empty(self.nx)
+        _check(self._lib.vlasov_density_force(self._h, _dptr(rho), _dptr(F)))
+        return rho, F
+
+    def sync(self):
+        _check(self._lib.vlasov_sync(self._h))
+
+    def kernels_per_step(self) -> int:
+        return int(self._lib.vlasov_kernels_per_step(self._h))
+
+    def step_timed(self, n: int) -> np.ndarray:
+        """Mean milliseconds of each launch slot of a step over n eager steps (see vlasov.h)."""
+        out = np.zeros(16)
+        cnt = ctypes.c_int(0)
+        _check(self._lib.vlasov_step_timed(self._h, int(n), _dptr(out), 16, ctypes.byref(cnt)))
+        return out[:cnt.value].copy()
+
+    def slot_names(self) -> list[str]:
+        names = ["xshift_step1", "reduce_density"]
+        if self.model == RING:
+            names.append("ring_force")
+        names += ["pshift_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
+        if self.model == RING:
+            names.append("ring_potential")
+        return names
