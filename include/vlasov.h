@@ -124,6 +124,26 @@ int vlasov_kernels_per_step(const vlasov_sim* sim);
    reduction, [ring potential].  Syncs. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
+/* One x-shift sweep (Eq. step1 form: row j moves by dev_disp[j] cells) with its density, for
+   callers that cannot allocate device memory.  The paper has no counterpart: this exists because
+   some callers may not call cudaMalloc at all (a host callback or allocator hook, a framework that
+   owns every device allocation, a plug-in that must keep its device footprint fixed after load).
+   It allocates nothing: its scratch (row filters and column partial sums, about 5.1 MiB) is a
+   fixed array inside the library that every GPU loading the library holds until process exit.
+   dev_fin, dev_fout: Np*Nx doubles (f[j*Nx+i], device, caller-owned, must not overlap);
+   dev_rho: Nx doubles out, rho_i = dp * sum_j fout[j,i] with dp = (pmax-pmin)/Np;
+   dev_disp: Np doubles (device).  Limits: 16 <= Nx, Np <= 4096, multiples of 8; with
+   x_periodic = 0 every |disp| must stay below 55 cells.  A displacement out of range (or NaN), or a
+   bounded device wait that gives up, makes dev_rho all NaN.  FP64 only.
+   Enqueued on `stream` (NULL = legacy default stream); returns VLASOV_EINVAL/ECUDA on bad input.
+   The first call on a device looks up the scratch address and sets kernel attributes for that
+   device; make that first call outside any stream capture.  Every call shares the one scratch
+   array: calls that overlap on the GPU (other streams, other threads) race and must not be
+   issued; keep them ordered on one stream. */
+int vlasov_xshift_density_noalloc(const double* dev_fin, double* dev_fout, double* dev_rho, int Nx, int Np,
+                                  double pmin, double pmax, int x_periodic, const double* dev_disp,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -350,6 +350,10 @@ int check_dev_err(vlasov_sim* s)
 
 }  // namespace
 
+namespace vl {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace vl
+
 extern "C" {
 
 const char* vlasov_last_error(void) { return g_err.c_str(); }

@@ -181,6 +181,8 @@ cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st
 cudaError_t launch_ring(const RingArgs& a, cudaStream_t st);
 cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double* colpart, int B,
                           cudaStream_t st);
+void set_last_error(const char* msg);   // text returned by vlasov_last_error() on this thread
+
 cudaError_t launch_convert(const void* src, int src_bytes, void* dst, int dst_bytes, size_t n,
                            cudaStream_t st);
 

@@ -23,7 +23,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 
 EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_f", "vlasov_get_f_device",
             "vlasov_step", "vlasov_moments", "vlasov_substep", "vlasov_density_force", "vlasov_sync",
-            "vlasov_destroy", "vlasov_last_error", "vlasov_kernels_per_step", "vlasov_step_timed")
+            "vlasov_destroy", "vlasov_last_error", "vlasov_kernels_per_step", "vlasov_step_timed",
+            "vlasov_xshift_density_noalloc")
 
 
 class VlasovError(RuntimeError):
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_last_error.restype = ctypes.c_char_p
         lib.vlasov_kernels_per_step.argtypes = [vp]
         lib.vlasov_step_timed.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ctypes.c_int)]
+        lib.vlasov_xshift_density_noalloc.argtypes = [vp, vp, vp, ip, ip, ctypes.c_double, ctypes.c_double, ip,
+                                                      vp, vp]
         for name in EXPORTED:
             if name not in ("vlasov_destroy", "vlasov_last_error"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -100,6 +103,17 @@ def _check(rc: int):
 def _dptr(a: np.ndarray):
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def xshift_density_noalloc(dev_fin: int, dev_fout: int, dev_rho: int, nx: int, np_: int, pmin: float,
+                           pmax: float, x_periodic: bool, dev_disp: int, stream: int | None = None):
+    """vlasov_xshift_density_noalloc: one x-shift with density for callers that cannot allocate
+    device memory (all pointers are caller-owned device buffers; the library's fixed scratch is used)."""
+    lib = load()
+    _check(lib.vlasov_xshift_density_noalloc(ctypes.c_void_p(dev_fin), ctypes.c_void_p(dev_fout),
+                                             ctypes.c_void_p(dev_rho), int(nx), int(np_), float(pmin), float(pmax),
+                                             int(bool(x_periodic)), ctypes.c_void_p(dev_disp),
+                                             ctypes.c_void_p(stream) if stream else None))
 
 
 class Sim:
