@@ -76,7 +76,9 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* domain, double
    step counter and the moment history.  Syncs. */
 int vlasov_set_f(vlasov_sim* sim, const double* host_f);
 
-/* Same from a device array of Np*Nx doubles (e.g. a torch tensor's data_ptr()). Enqueued. */
+/* Same from a device array of Np*Nx doubles (e.g. a torch tensor's data_ptr()).  Syncs (it reads
+   back max|f| to set the scales of the fixed-point moment sums, as vlasov_set_f does).  The moment
+   sums assume |f| stays below 4x the largest |f| uploaded. */
 int vlasov_set_f_device(vlasov_sim* sim, const double* dev_f);
 
 /* Download the current f as doubles (host, Np*Nx).  Syncs.  VLASOV_ETIMEOUT if a device wait

@@ -2,97 +2,99 @@
 // line parameters, and small utility kernels.
 //
 // Density (Sec. 2): rho_i = dp sum_j f[j,i], assembled from the per-CTA column partials written
-// by the x-shift epilogue, in a fixed order (deterministic).  Moments: mass = dx sum rho,
-// Mx, My = dx sum cos/sin(x_i) rho_i (Eq. mxmydef), kinetic = dx dp sum_j p_j^2/2 sum_i f.
-// Forces, Eq. (meanforce) by the rectangle rule:
+// by the x-shift epilogue.  Moments: mass = dx sum rho, Mx, My = dx sum cos/sin(x_i) rho_i
+// (Eq. mxmydef), kinetic = dx dp sum_j p_j^2/2 sum_i f.  Forces, Eq. (meanforce) by the rectangle
+// rule:
 //   HMF   (Eq. hmfmeanforce): F_i = -Mx sin x_i + My cos x_i
 //   ring  (Eq. ringpot):      F_i = -dx sum_k V'((i-k) dx) rho_k   (circulant)
 //   sheet (V = 2 pi G |x|):   F_i = -2 pi G dx (sum_{k<i} rho_k - sum_{k>i} rho_k)  (prefix scan)
-// All reductions are FP64 with Neumaier compensation in the final stages.
+// Every sum across threads is an exact integer fixed-point sum (fixed_point.cuh): deterministic,
+// order-free, and without the long dependent FP64 chains that are slow on this GPU.
+#include "fixed_point.cuh"
 #include "vlasov_internal.cuh"
 
 namespace vl {
 
-struct NSum {
-    double s = 0.0, c = 0.0;
-    __device__ __forceinline__ void add(double x)
-    {
-        const double t = s + x;
-        if (fabs(s) >= fabs(x)) c += (s - t) + x;
-        else c += (x - t) + s;
-        s = t;
-    }
-    __device__ __forceinline__ double val() const { return s + c; }
-};
+constexpr int CR_COLS = 32;      // columns per colreduce block
+constexpr int CR_GROUPS = 8;     // partial-row groups per block (blockDim = 256)
 
-__device__ __forceinline__ double warp_sum(double v)
+__device__ __forceinline__ i128 shfl_up_i128(i128 v, int o)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    const uint64_t lo = (uint64_t)v, hi = (uint64_t)((u128)v >> 64);
+    const uint64_t l2 = (uint64_t)__shfl_up_sync(0xffffffffu, (long long)lo, o);
+    const uint64_t h2 = (uint64_t)__shfl_up_sync(0xffffffffu, (long long)hi, o);
+    return (i128)(((u128)h2 << 64) | (u128)l2);
 }
 
-// Block-wide sum in a fixed order (warp trees, then warp 0 over the warp results).
-__device__ double block_sum(double v, double* sh)
+// Exclusive scan of one int128 per thread across the block (blockDim <= 1024); returns the prefix
+// and writes the block total to *total.  `sh` holds >= 33 entries.
+__device__ i128 block_exclusive_scan_i128(i128 v, i128* sh, i128* total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (wid == 0) {
-        r = lane < nw ? sh[lane] : 0.0;
-        r = warp_sum(r);
+    i128 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const i128 t = shfl_up_i128(inc, o);
+        if (lane >= o) inc += t;
     }
     __syncthreads();
-    if (threadIdx.x == 0) sh[0] = r;
+    if (lane == 31) sh[wid] = inc;
     __syncthreads();
-    r = sh[0];
+    if (threadIdx.x == 0) {
+        i128 run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const i128 t = sh[w];
+            sh[w] = run;
+            run += t;
+        }
+        sh[32] = run;
+    }
+    __syncthreads();
+    const i128 r = sh[wid] + inc - v;
+    *total = sh[32];
     __syncthreads();
     return r;
 }
 
-constexpr int CR_COLS = 32;      // columns per colreduce block
-constexpr int CR_GROUPS = 8;     // partial groups per block (blockDim = 256)
-
 // ============================================================================ colreduce
-// Block: 32 columns x 8 groups over the B partials; then block partials of (mass, Mx, My); the
-// last block to finish (ticket) reduces those in block order, adds the kinetic partials, and runs
-// the model-specific tail (sheet scan, moment record).
+// Block: 32 columns x 8 groups over the B partial rows.  Each partial becomes an int64 on the
+// column scale, so the column sum is exact; then int128 block partials of mass, Mx, My.  The last
+// block to finish (ticket) adds those, the kinetic partials, runs the sheet prefix scan, and writes
+// the scalars and (after the second x-shift) the moment record.
 __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
 {
-    __shared__ double sh[CR_GROUPS][CR_COLS];
-    __shared__ double red[32];
+    __shared__ long long shc[CR_GROUPS][CR_COLS];
+    __shared__ i128 red[33];
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int i = blockIdx.x * CR_COLS + lane;
 
-    double s = 0.0;
+    long long s = 0;
     if (i < a.Nx)
-        for (int b = grp; b < a.B; b += CR_GROUPS) s += a.colpart[(size_t)b * a.Nx + i];
-    sh[grp][lane] = s;
+        for (int b = grp; b < a.B; b += CR_GROUPS)
+            s += (long long)fx128_from_f64(a.colpart[(size_t)b * a.Nx + i], a.k_col);
+    shc[grp][lane] = s;
     __syncthreads();
-    double rho = 0.0, cm = 0.0, cx = 0.0, cy = 0.0;
-    if (grp == 0) {
-        double t = 0.0;
+    i128 cm = 0, cx = 0, cy = 0;
+    if (grp == 0 && i < a.Nx) {
+        long long t = 0;
 #pragma unroll
-        for (int q = 0; q < CR_GROUPS; ++q) t += sh[q][lane];
-        if (i < a.Nx) {
-            rho = a.dp * t;
-            a.rho[i] = rho;
-            cm = rho;
-            cx = a.costab[i] * rho;
-            cy = a.sintab[i] * rho;
-        }
+        for (int q = 0; q < CR_GROUPS; ++q) t += shc[q][lane];
+        a.colfx[i] = t;
+        a.rho[i] = a.dp * fx128_to_f64((i128)t, a.k_col);
+        cm = (i128)t;
+        const i128 half = (i128)1 << 31;
+        cx = ((i128)a.cosfx[i] * (i128)t + half) >> 32;   // scale 2^-(k_col + 30)
+        cy = ((i128)a.sinfx[i] * (i128)t + half) >> 32;
     }
-    cm = block_sum(cm, red);
-    cx = block_sum(cx, red);
-    cy = block_sum(cy, red);
+    cm = block_sum_i128(cm, red);
+    cx = block_sum_i128(cx, red);
+    cy = block_sum_i128(cy, red);
+    i128* bp = static_cast<i128*>(a.blockpart);
     if (threadIdx.x == 0) {
-        a.blockpart[blockIdx.x * 4 + 0] = cm;
-        a.blockpart[blockIdx.x * 4 + 1] = cx;
-        a.blockpart[blockIdx.x * 4 + 2] = cy;
+        bp[blockIdx.x * 3 + 0] = cm;
+        bp[blockIdx.x * 3 + 1] = cx;
+        bp[blockIdx.x * 3 + 2] = cy;
         __threadfence();
         const unsigned int tk = atomicAdd(a.ticket, 1u);
         is_last = (tk == gridDim.x - 1);
@@ -101,88 +103,59 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
     if (!is_last) return;
     __threadfence();
 
-    // ---- last block: totals in block order (thread 0, compensated)
-    __shared__ double tot[4];
-    if (threadIdx.x == 0) {
-        NSum m, x, y, k;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            m.add(__ldcg(&a.blockpart[b * 4 + 0]));
-            x.add(__ldcg(&a.blockpart[b * 4 + 1]));
-            y.add(__ldcg(&a.blockpart[b * 4 + 2]));
-        }
-        if (a.kinpart)
-            for (int b = 0; b < a.B; ++b) k.add(a.kinpart[b]);
-        tot[0] = a.dx * m.val();
-        tot[1] = a.dx * x.val();
-        tot[2] = a.dx * y.val();
-        tot[3] = a.dx * a.dp * k.val();
-        *a.ticket = 0u;   // ready for the next launch
+    // ---- last block: totals (exact, any order)
+    i128 m = 0, x = 0, y = 0, k = 0;
+    const volatile i128* vb = bp;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        m += vb[b * 3 + 0];
+        x += vb[b * 3 + 1];
+        y += vb[b * 3 + 2];
     }
-    __syncthreads();
-    const double mass = tot[0], Mx = tot[1], My = tot[2], kin = tot[3];
-    double U = 0.0;
+    if (a.kinpart)
+        for (int b = threadIdx.x; b < a.B; b += blockDim.x) k += fx128_from_f64(__ldcg(&a.kinpart[b]), a.k_kin);
+    m = block_sum_i128(m, red);
+    x = block_sum_i128(x, red);
+    y = block_sum_i128(y, red);
+    k = block_sum_i128(k, red);
 
+    i128 U_acc = 0;
     if (a.model == 2) {
-        // Sheet: exclusive prefix C_i = sum_{k<i} rho_k (compensated, fixed order), then
-        // F_i = -2 pi G dx (2 C_i + rho_i - S), S = sum rho; U = 2 pi G dx^3 sum_i rho_i (i C_i - X_i),
-        // X_i = sum_{k<i} k rho_k.
-        __shared__ double offs[256][2];
-        __shared__ double offx[256][2];
+        // Sheet: C_i = sum_{k<i} s_k (exact); Q_i = 2 C_i + s_i - S gives F_i = -2 pi G dx dp Q_i.
         const int nt = blockDim.x;
         const int per = (a.Nx + nt - 1) / nt;
-        const int lo = threadIdx.x * per, hi = min(a.Nx, lo + per);
-        NSum ls, lx;
+        const int lo = min(a.Nx, (int)threadIdx.x * per), hi = min(a.Nx, lo + per);
+        i128 ls = 0, lx = 0;
         for (int q = lo; q < hi; ++q) {
-            const double r = __ldcg(&a.rho[q]);
-            ls.add(r);
-            lx.add((double)q * r);
+            const long long v = __ldcg(&a.colfx[q]);
+            ls += v;
+            lx += (i128)q * v;
         }
-        offs[threadIdx.x][0] = ls.s;
-        offs[threadIdx.x][1] = ls.c;
-        offx[threadIdx.x][0] = lx.s;
-        offx[threadIdx.x][1] = lx.c;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            NSum run, runx;
-            for (int t = 0; t < nt; ++t) {
-                const double s0 = offs[t][0], c0 = offs[t][1], s1 = offx[t][0], c1 = offx[t][1];
-                offs[t][0] = run.s;
-                offs[t][1] = run.c;
-                offx[t][0] = runx.s;
-                offx[t][1] = runx.c;
-                run.add(s0);
-                run.add(c0);
-                runx.add(s1);
-                runx.add(c1);
+        i128 S = 0, XS = 0;
+        i128 C = block_exclusive_scan_i128(ls, red, &S);
+        i128 X = block_exclusive_scan_i128(lx, red, &XS);
+        for (int q = lo; q < hi; ++q) {
+            const long long v = __ldcg(&a.colfx[q]);
+            a.Qd[q] = fx128_to_f64(2 * C + (i128)v - S, a.k_col);
+            if (a.final_moments) {
+                // U = 2 pi G dx^3 sum_i rho_i sum_{k<i} (i-k) rho_k
+                const double r = fx128_to_f64((i128)v, a.k_col);
+                const double wgt = fx128_to_f64((i128)q * C - X, a.k_col);
+                U_acc += fx128_from_f64(r * wgt, a.k_pot);
             }
-            tot[0] = run.val();
+            C += v;
+            X += (i128)q * v;
         }
-        __syncthreads();
-        const double S = tot[0];
-        const double k2 = 2.0 * 3.14159265358979323846 * a.G;
-        NSum c, xx;
-        c.s = offs[threadIdx.x][0];
-        c.c = offs[threadIdx.x][1];
-        xx.s = offx[threadIdx.x][0];
-        xx.c = offx[threadIdx.x][1];
-        double up = 0.0;
-        for (int q = lo; q < hi; ++q) {
-            const double r = __ldcg(&a.rho[q]);
-            const double C = c.val();
-            a.F[q] = -k2 * a.dx * (2.0 * C + r - S);
-            if (a.final_moments) up += r * ((double)q * C - xx.val());
-            c.add(r);
-            xx.add((double)q * r);
-        }
-        if (a.final_moments) {
-            up = block_sum(up, red);
-            U = k2 * a.dx * a.dx * a.dx * up;
-        }
-    } else if (a.model == 0) {
-        U = 0.5 * (mass * mass - Mx * Mx - My * My);
+        if (a.final_moments) U_acc = block_sum_i128(U_acc, red);
     }
 
     if (threadIdx.x == 0) {
+        const double mass = a.dxdp * fx128_to_f64(m, a.k_col);
+        const double Mx = a.dxdp * fx128_to_f64(x, a.k_col + 30);
+        const double My = a.dxdp * fx128_to_f64(y, a.k_col + 30);
+        const double kin = a.dxdp * fx128_to_f64(k, a.k_kin);
+        double U = 0.0;
+        if (a.model == 0) U = 0.5 * (mass * mass - Mx * Mx - My * My);
+        else if (a.model == 2 && a.final_moments) U = a.pot_scale * fx128_to_f64(U_acc, a.k_pot);
         a.sc->mass = mass;
         a.sc->Mx = Mx;
         a.sc->My = My;
@@ -202,6 +175,7 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
             a.hist[st % HIST_CAP] = rec;
             *a.step = st + 1;
         }
+        *a.ticket = 0u;   // ready for the next launch
     }
 }
 
@@ -212,46 +186,74 @@ cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st)
 }
 
 // ============================================================================ ring force
-// One warp per output node i: F_i = -dx sum_k V'(((i-k) mod N) dx) rho_k (and, for the moments,
-// Phi_i = dx sum_k V(...) rho_k).  The last block forms U = 1/2 dx sum_i rho_i Phi_i.
+// F_i = -dx sum_k V'(((i-k) mod N) dx) rho_k, or after the last x-shift Phi_i = dx sum_k V(...) rho_k
+// and U = 1/2 dx sum_i rho_i Phi_i (exact int128 sum).  A block stages rho in shared memory in the
+// arithmetic type T (double for FP64 storage, float for FP32 storage) and produces RING_OUT outputs,
+// eight per warp, lanes striding over k.
+constexpr int RING_OUT = 64;
+
+template <typename T>
 __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
 {
-    __shared__ double red[32];
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    T* rs = reinterpret_cast<T*>(ring_smem);
+    __shared__ i128 red[33];
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int i = blockIdx.x * 8 + wid;
     const int N = a.N;
-    double up = 0.0;
-    if (i < N) {
-        double f = 0.0;
-        // after the last x-shift only the potential is needed; otherwise only the force
-        const double* __restrict__ ker = a.final_moments ? a.V : a.dV;
-        for (int k = lane; k < N; k += 32) {
-            int m = i - k;
-            if (m < 0) m += N;
-            f = fma(ker[m], a.rho[k], f);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) rs[k] = (T)a.rho[k];
+    __syncthreads();
+    const T* __restrict__ ker = static_cast<const T*>(a.final_moments ? a.V : a.dV);
+    const int i0 = blockIdx.x * RING_OUT + wid * 8;
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = T(0);
+    int iq[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) iq[q] = (i0 + q < N) ? i0 + q : 0;   // outputs past N: dummy, unused
+    for (int k = lane; k < N; k += 32) {
+        const T r = rs[k];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int m = iq[q] - k;          // in (-N, N)
+            m += (m < 0) ? N : 0;
+            acc[q] = fma(ker[m], r, acc[q]);
         }
-        f = warp_sum(f);
-        if (lane == 0) {
-            if (a.final_moments) up = a.rho[i] * a.dx * f;
-            else a.F[i] = -a.dx * f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    i128 up = 0;
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = i0 + q;
+            if (i < N) {
+                if (a.final_moments) up += fx128_from_f64(a.rho[i] * (a.dx * (double)acc[q]), a.k_pot);
+                else a.F[i] = -a.dx * (double)acc[q];
+            }
         }
     }
     if (!a.final_moments) return;
-    up = block_sum(up, red);
+    up = block_sum_i128(up, red);
+    i128* bp = static_cast<i128*>(a.blockpart);
     if (threadIdx.x == 0) {
-        a.blockpart[blockIdx.x] = up;
+        bp[blockIdx.x] = up;
         __threadfence();
         const unsigned int tk = atomicAdd(a.ticket, 1u);
         is_last = (tk == gridDim.x - 1);
     }
     __syncthreads();
-    if (!is_last || threadIdx.x != 0) return;
+    if (!is_last) return;
     __threadfence();
-    NSum u;
-    for (int b = 0; b < (int)gridDim.x; ++b) u.add(__ldcg(&a.blockpart[b]));
+    i128 u = 0;
+    const volatile i128* vb = bp;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) u += vb[b];
+    u = block_sum_i128(u, red);
+    if (threadIdx.x != 0) return;
     *a.ticket = 0u;
-    const double U = 0.5 * a.dx * u.val();
+    const double U = a.pot_scale * fx128_to_f64(u, a.k_pot);
     const Scalars s = *a.sc;
     const long long st = *a.step;
     MomentRec rec;
@@ -268,13 +270,20 @@ __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
     a.sc->potential = U;
 }
 
-cudaError_t launch_ring(const RingArgs& a, cudaStream_t st)
+int ring_blocks(int N) { return (N + RING_OUT - 1) / RING_OUT; }
+
+cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st)
 {
-    ring_kernel<<<(a.N + 7) / 8, 256, 0, st>>>(a);
+    const int grid = ring_blocks(a.N);
+    if (elem_bytes == 8) ring_kernel<double><<<grid, 256, (size_t)a.N * 8, st>>>(a);
+    else ring_kernel<float><<<grid, 256, (size_t)a.N * 4, st>>>(a);
     return cudaGetLastError();
 }
 
 // ============================================================================ p-shift parameters
+// Column i moves by sigma_i = F_i dt/dp cells.  The split of the foot (n0 = floor(-sigma),
+// beta = -sigma - n0) is FP64 always; the ten filter weights are FP64 for FP64 storage and FP32
+// for FP32 storage.
 template <typename T>
 __global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
 {
@@ -283,18 +292,34 @@ __global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
     double F;
     if (a.model == 0) F = -a.sc->Mx * a.sintab[i] + a.sc->My * a.costab[i];
     else if (a.model == 3) F = 0.0;
+    else if (a.model == 2) F = a.Fscale * a.Fin[i];
     else F = a.Fin[i];
     if (a.Fout) a.Fout[i] = F;
     const double sigma = F * a.cp;
-    LineSplit L;
-    line_split(sigma, L);
+    const double ms = -sigma;
+    const double fl = floor(ms);
+    const double beta = ms - fl;
     T* w = static_cast<T*>(a.w);
     T* gd = static_cast<T*>(a.gd);
-    a.n0[i] = L.n0;
-#pragma unroll
-    for (int t = 0; t < NTAP; ++t) w[(size_t)t * a.Nx + i] = (T)L.w[t];
-    gd[i] = (T)L.g;
-    gd[a.Nx + i] = (T)L.d;
+    a.n0[i] = (int)fl;
+    const T b = (T)beta;
+    const T al = (T)(1.0 - beta);
+    const T g = (al * al * al - al) * (T)(1.0 / 6.0);
+    const T d = (b * b * b - b) * (T)(1.0 / 6.0);
+    const T c0 = T(VL_FD_C0), c1 = T(VL_FD_C1), c2 = T(VL_FD_C2), c3 = T(VL_FD_C3), c4 = T(VL_FD_C4);
+    const size_t n = (size_t)a.Nx;
+    w[0 * n + i] = g * c4;
+    w[1 * n + i] = g * c3 + d * c4;
+    w[2 * n + i] = g * c2 + d * c3;
+    w[3 * n + i] = g * c1 + d * c2;
+    w[4 * n + i] = al + g * c0 + d * c1;
+    w[5 * n + i] = b + g * c1 + d * c0;
+    w[6 * n + i] = g * c2 + d * c1;
+    w[7 * n + i] = g * c3 + d * c2;
+    w[8 * n + i] = g * c4 + d * c3;
+    w[9 * n + i] = d * c4;
+    gd[i] = g;
+    gd[n + i] = d;
 }
 
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st)
@@ -352,6 +377,27 @@ cudaError_t launch_convert(const void* src, int src_bytes, void* dst, int dst_by
         return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, st);
     else
         return cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+}
+
+// Largest |f| of a device array (for the fixed-point scales after a device-side upload).  The bit
+// pattern of a non-negative double orders like the value, so an integer atomicMax works.
+template <typename T>
+__global__ void maxabs_kernel(const T* __restrict__ f, size_t n, unsigned long long* out)
+{
+    double m = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)f[k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_maxabs(int elem_bytes, const void* f, size_t n, unsigned long long* out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (elem_bytes == 8) maxabs_kernel<double><<<608, 256, 0, st>>>(static_cast<const double*>(f), n, out);
+    else maxabs_kernel<float><<<608, 256, 0, st>>>(static_cast<const float*>(f), n, out);
     return cudaGetLastError();
 }
 

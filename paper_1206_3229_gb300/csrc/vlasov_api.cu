@@ -76,16 +76,24 @@ struct vlasov_sim {
     double* colpart = nullptr;  // [xgrid][Nx]
     double* kinpart = nullptr;  // [xgrid]
     double* rho = nullptr;
+    long long* colfx = nullptr; // [Nx] fixed-point column sums
+    double* Qd = nullptr;       // [Nx] sheet prefix combination
     double* F = nullptr;
     double* Fout = nullptr;
-    double* blockpart = nullptr;
-    double* ringpart = nullptr;
+    void* blockpart = nullptr;  // int128 [crgrid][3]
+    void* ringpart = nullptr;   // int128 [(Nx+7)/8]
     unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring
+    unsigned long long* maxbits = nullptr;
     Scalars* sc = nullptr;
     double* costab = nullptr;
     double* sintab = nullptr;
-    double* ringdV = nullptr;
-    double* ringV = nullptr;
+    long long* cosfx = nullptr;
+    long long* sinfx = nullptr;
+    void* ringdV = nullptr;     // in the storage type
+    void* ringV = nullptr;
+    // fixed-point scales of the reductions (from a bound 2^Ef >= 4 max|f|)
+    int Ef = 0, k_col = 0, k_kin = 0, k_pot = 0;
+    bool scales_set = false;
     MomentRec* hist = nullptr;
     long long* dstep = nullptr;
     long long read_step = 0;
@@ -192,6 +200,45 @@ PShiftArgs pargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     return a;
 }
 
+int ceil_log2(double v)
+{
+    int e = 0;
+    const double m = std::frexp(v, &e);   // v = m 2^e, m in [0.5, 1)
+    return m == 0.5 ? e - 1 : e;
+}
+
+// Fixed-point shifts of the reductions from the largest |f| (bound 2^Ef >= 4 max|f|).  Kernel
+// arguments are captured in the step graphs, so a change of scale drops the graphs.
+void update_scales(vlasov_sim* s, double maxabs)
+{
+    int e = 0;
+    if (maxabs > 0 && std::isfinite(maxabs)) std::frexp(maxabs, &e);   // maxabs < 2^e
+    const int Ef = e + 2;
+    const int Lp = ceil_log2((double)s->Np), Lx = ceil_log2((double)s->Nx);
+    const double pm = std::max(std::fabs(s->pmin), std::fabs(s->pmax));
+    const int k_col = 61 - Ef - Lp;
+    const int k_kin = 124 - ceil_log2(0.5 * pm * pm * (double)s->Np * (double)s->Nx) - Ef;
+    int k_pot = 0;
+    if (s->model == VLASOV_SHEET) k_pot = 124 - (3 * Lx + 2 * (Lp + Ef));
+    if (s->model == VLASOV_RING) {
+        const double vmax = 1.0 / std::sqrt(2.0 * s->eps);
+        const double rmax = s->dp * (double)s->Np * std::ldexp(1.0, Ef);
+        k_pot = 124 - ceil_log2((double)s->Nx * (double)s->Nx * s->dx * vmax * rmax * rmax);
+    }
+    if (!s->scales_set || Ef != s->Ef || k_col != s->k_col || k_kin != s->k_kin || k_pot != s->k_pot) {
+        for (int b = 0; b < 2; ++b)
+            if (s->graph[b]) {
+                cudaGraphExecDestroy(s->graph[b]);
+                s->graph[b] = nullptr;
+            }
+    }
+    s->Ef = Ef;
+    s->k_col = k_col;
+    s->k_kin = k_kin;
+    s->k_pot = k_pot;
+    s->scales_set = true;
+}
+
 ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments)
 {
     ColReduceArgs a;
@@ -199,18 +246,21 @@ ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments)
     a.B = B;
     a.kinpart = kin ? s->kinpart : nullptr;
     a.Nx = s->Nx;
-    a.dx = s->dx;
+    a.k_col = s->k_col;
+    a.k_kin = s->k_kin;
+    a.k_pot = s->k_pot;
     a.dp = s->dp;
-    a.xmin = s->xmin;
-    a.costab = s->costab;
-    a.sintab = s->sintab;
+    a.dxdp = s->dx * s->dp;
+    a.pot_scale = 2.0 * 3.14159265358979323846 * s->G * s->dx * s->dx * s->dx * s->dp * s->dp;
+    a.cosfx = s->cosfx;
+    a.sinfx = s->sinfx;
     a.rho = s->rho;
+    a.colfx = s->colfx;
+    a.Qd = s->Qd;
     a.blockpart = s->blockpart;
     a.ticket = &s->tickets[0];
     a.sc = s->sc;
     a.model = s->model;
-    a.G = s->G;
-    a.F = s->F;
     a.final_moments = final_moments ? 1 : 0;
     a.hist = s->hist;
     a.step = s->dstep;
@@ -228,6 +278,8 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     a.V = s->ringV;
     a.F = s->F;
     a.blockpart = s->ringpart;
+    a.k_pot = s->k_pot;
+    a.pot_scale = 0.5 * s->dx;
     a.ticket = &s->tickets[1];
     a.sc = s->sc;
     a.final_moments = final_moments ? 1 : 0;
@@ -245,7 +297,8 @@ int launch_pparams_only(vlasov_sim* s, double* Fout)
     a.sc = s->sc;
     a.costab = s->costab;
     a.sintab = s->sintab;
-    a.Fin = s->F;
+    a.Fin = s->model == VLASOV_SHEET ? s->Qd : s->F;
+    a.Fscale = -2.0 * 3.14159265358979323846 * s->G * s->dx * s->dp;
     a.cp = s->dt / s->dp;
     a.n0 = s->pp.n0;
     a.w = s->pp.w;
@@ -257,7 +310,7 @@ int launch_pparams_only(vlasov_sim* s, double* Fout)
 
 int launch_force_params(vlasov_sim* s, double* Fout)
 {
-    if (s->model == VLASOV_RING) CU_TRY(launch_ring(ringargs(s, false), s->st));
+    if (s->model == VLASOV_RING) CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
     return launch_pparams_only(s, Fout);
 }
 
@@ -293,7 +346,7 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
     MARK();
     if (s->model == VLASOV_RING) {
-        CU_TRY(launch_ring(ringargs(s, false), s->st));
+        CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
         MARK();
     }
     {
@@ -311,7 +364,7 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
     MARK();
     if (s->model == VLASOV_RING) {
-        CU_TRY(launch_ring(ringargs(s, true), s->st));
+        CU_TRY(launch_ring(s->esz, ringargs(s, true), s->st));
         MARK();
     }
     return VLASOV_OK;
@@ -369,8 +422,9 @@ void vlasov_destroy(vlasov_sim* s)
     free_params(s->xp);
     free_params(s->pp);
     free_params(s->sp);
-    void* bufs[] = {s->colpart, s->kinpart, s->rho, s->F, s->Fout, s->blockpart, s->ringpart, s->tickets, s->sc,
-                    s->costab, s->sintab, s->ringdV, s->ringV, s->hist, s->dstep, s->err};
+    void* bufs[] = {s->colpart, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
+                    s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
+                    s->hist, s->dstep, s->err};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -483,11 +537,15 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->xgrid * Nx));
     CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->xgrid));
     CTRY(cudaMalloc(&s->rho, sizeof(double) * Nx));
+    CTRY(cudaMalloc(&s->colfx, sizeof(long long) * Nx));
+    CTRY(cudaMalloc(&s->Qd, sizeof(double) * Nx));
+    CTRY(cudaMemsetAsync(s->Qd, 0, sizeof(double) * Nx, s->st));
     CTRY(cudaMalloc(&s->F, sizeof(double) * Nx));
     CTRY(cudaMemsetAsync(s->F, 0, sizeof(double) * Nx, s->st));
     CTRY(cudaMalloc(&s->Fout, sizeof(double) * Nx));
-    CTRY(cudaMalloc(&s->blockpart, sizeof(double) * 4 * (size_t)s->crgrid));
-    CTRY(cudaMalloc(&s->ringpart, sizeof(double) * (size_t)((Nx + 7) / 8)));
+    CTRY(cudaMalloc(&s->blockpart, 16 * 3 * (size_t)s->crgrid));
+    CTRY(cudaMalloc(&s->ringpart, 16 * (size_t)ring_blocks(Nx)));
+    CTRY(cudaMalloc(&s->maxbits, sizeof(unsigned long long)));
     CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 2));
     CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 2, s->st));
     CTRY(cudaMalloc(&s->sc, sizeof(Scalars)));
@@ -501,10 +559,13 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     // Tables on the x nodes: cos/sin for HMF (Eq. hmfmeanforce, mxmydef); ring kernel V, V'.
     {
         std::vector<double> c(Nx), sn(Nx), dV(Nx), V(Nx);
+        std::vector<long long> cfx(Nx), sfx(Nx);
         for (int i = 0; i < Nx; ++i) {
             const double th = s->xmin + (double)i * s->dx;
             c[i] = std::cos(th);
             sn[i] = std::sin(th);
+            cfx[i] = std::llround(std::ldexp(c[i], 62));
+            sfx[i] = std::llround(std::ldexp(sn[i], 62));
             const double u = (double)i * s->dx;
             if (model == VLASOV_RING) {
                 const double q = 1.0 - std::cos(u) + s->eps;
@@ -516,13 +577,24 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         }
         CTRY(cudaMalloc(&s->costab, sizeof(double) * Nx));
         CTRY(cudaMalloc(&s->sintab, sizeof(double) * Nx));
-        CTRY(cudaMalloc(&s->ringdV, sizeof(double) * Nx));
-        CTRY(cudaMalloc(&s->ringV, sizeof(double) * Nx));
+        CTRY(cudaMalloc(&s->cosfx, sizeof(long long) * Nx));
+        CTRY(cudaMalloc(&s->sinfx, sizeof(long long) * Nx));
+        CTRY(cudaMalloc(&s->ringdV, (size_t)esz * Nx));
+        CTRY(cudaMalloc(&s->ringV, (size_t)esz * Nx));
         CTRY(cudaMemcpyAsync(s->costab, c.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->sintab, sn.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
-        CTRY(cudaMemcpyAsync(s->ringdV, dV.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
-        CTRY(cudaMemcpyAsync(s->ringV, V.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
-        CTRY(cudaStreamSynchronize(s->st));
+        CTRY(cudaMemcpyAsync(s->cosfx, cfx.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaMemcpyAsync(s->sinfx, sfx.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
+        if (esz == 8) {
+            CTRY(cudaMemcpyAsync(s->ringdV, dV.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
+            CTRY(cudaMemcpyAsync(s->ringV, V.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
+            CTRY(cudaStreamSynchronize(s->st));
+        } else {
+            std::vector<float> dVf(dV.begin(), dV.end()), Vf(V.begin(), V.end());
+            CTRY(cudaMemcpyAsync(s->ringdV, dVf.data(), sizeof(float) * Nx, cudaMemcpyHostToDevice, s->st));
+            CTRY(cudaMemcpyAsync(s->ringV, Vf.data(), sizeof(float) * Nx, cudaMemcpyHostToDevice, s->st));
+            CTRY(cudaStreamSynchronize(s->st));
+        }
     }
     TRY(make_tmap(s, 0));
     TRY(make_tmap(s, 1));
@@ -536,6 +608,10 @@ int vlasov_set_f(vlasov_sim* s, const double* host_f)
 {
     if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");
     const size_t cells = (size_t)s->Nx * s->Np;
+    double mx = 0.0;
+    for (size_t k = 0; k < cells; ++k) mx = std::max(mx, std::fabs(host_f[k]));
+    if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
+    update_scales(s, mx);
     if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(s->f[s->cur], host_f, cells * 8, cudaMemcpyHostToDevice, s->st));
     } else {
@@ -556,6 +632,14 @@ int vlasov_set_f_device(vlasov_sim* s, const double* dev_f)
     const size_t cells = (size_t)s->Nx * s->Np;
     CU_TRY(launch_convert(dev_f, 8, s->f[s->cur], s->esz, cells, s->st));
     CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
+    unsigned long long bits = 0;
+    CU_TRY(launch_maxabs(8, dev_f, cells, s->maxbits, s->st));
+    CU_TRY(cudaMemcpyAsync(&bits, s->maxbits, sizeof bits, cudaMemcpyDeviceToHost, s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    double mx;
+    std::memcpy(&mx, &bits, sizeof mx);
+    if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
+    update_scales(s, mx);
     s->read_step = 0;
     s->has_f = true;
     return VLASOV_OK;

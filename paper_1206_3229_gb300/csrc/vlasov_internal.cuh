@@ -105,20 +105,25 @@ struct PShiftArgs {
 };
 
 struct ColReduceArgs {
-    const double* colpart;   // [B][Nx]
+    const double* colpart;   // [B][Nx] per-CTA column sums of f (x-shift epilogue)
     int B;
-    const double* kinpart;   // [B] or null
+    const double* kinpart;   // [B] per-CTA sum_j p_j^2/2 sum_i f, or null
     int Nx;
-    double dx, dp, xmin;
-    const double* costab;    // cos(x_i), sin(x_i)
-    const double* sintab;
-    double* rho;             // [Nx] out
-    double* blockpart;       // [gridDim.x][4] scratch
+    int k_col;               // fixed-point shift of column sums: X = round(x * 2^k_col) (int64)
+    int k_kin;               // shift of the kinetic partials (int128)
+    int k_pot;               // shift of the sheet potential terms (int128)
+    double dp;
+    double dxdp;             // dx * dp
+    double pot_scale;        // sheet: 2 pi G dx^3 dp^2
+    const long long* cosfx;  // round(cos(x_i) * 2^62), round(sin(x_i) * 2^62)
+    const long long* sinfx;
+    double* rho;             // [Nx] out: dp * column sum
+    long long* colfx;        // [Nx] out: fixed-point column sums
+    double* Qd;              // [Nx] out (sheet): (2 C_i + s_i - S) * 2^-k_col, C_i = sum_{k<i} s_k
+    void* blockpart;         // [gridDim.x][3] int128 scratch
     unsigned int* ticket;    // zero on entry; reset by the last block
     Scalars* sc;             // out
     int model;
-    double G;                // sheet
-    double* F;               // sheet: force out [Nx]
     int final_moments;       // 1: write the moment record (all models but ring)
     MomentRec* hist;
     long long* step;
@@ -130,7 +135,8 @@ struct PParamsArgs {
     const Scalars* sc;
     const double* costab;
     const double* sintab;
-    const double* Fin;       // ring / sheet force [Nx]
+    const double* Fin;       // ring: force [Nx]; sheet: Qd [Nx]
+    double Fscale;           // sheet: F_i = Fscale * Qd_i
     double cp;               // dt / dp
     int* n0;
     void* w;
@@ -142,10 +148,12 @@ struct RingArgs {
     int N;
     double dx;
     const double* rho;
-    const double* dV;        // V'(m dx), m = 0..N-1
-    const double* V;         // V(m dx)
+    const void* dV;          // V'(m dx), m = 0..N-1 (double, or float for FP32 storage)
+    const void* V;           // V(m dx)
     double* F;               // out
-    double* blockpart;       // [gridDim.x]
+    void* blockpart;         // [gridDim.x] int128
+    int k_pot;               // shift of the potential terms rho_i * Phi_i
+    double pot_scale;        // 0.5 * dx
     unsigned int* ticket;
     Scalars* sc;
     int final_moments;
@@ -178,12 +186,14 @@ cudaError_t pshift_occupancy(int elem_bytes, int* blocks);
 
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
-cudaError_t launch_ring(const RingArgs& a, cudaStream_t st);
+cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
+int ring_blocks(int N);
 cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double* colpart, int B,
                           cudaStream_t st);
 void set_last_error(const char* msg);   // text returned by vlasov_last_error() on this thread
 
 cudaError_t launch_convert(const void* src, int src_bytes, void* dst, int dst_bytes, size_t n,
                            cudaStream_t st);
+cudaError_t launch_maxabs(int elem_bytes, const void* f, size_t n, unsigned long long* out, cudaStream_t st);
 
 }  // namespace vl
