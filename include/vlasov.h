@@ -35,13 +35,19 @@ extern "C" {
 #define VLASOV_ECUDA (-3)    /* a CUDA runtime/driver call failed (message has the CUDA text) */
 #define VLASOV_ETIMEOUT (-4) /* a bounded device-side wait expired; results of that step are void */
 #define VLASOV_ESTATE (-5)   /* call not valid in the handle's state (e.g. step before set_f) */
+#define VLASOV_ERANGE (-6)   /* VLASOV_F64: |f| grew beyond the fixed-point range; results void */
 
 /* Force models of Sec. 2.  FREE has F = 0 (free streaming; for tests). */
 enum { VLASOV_HMF = 0, VLASOV_RING = 1, VLASOV_SHEET = 2, VLASOV_FREE = 3 };
 
-/* Storage/arithmetic of f.  F64: IEEE double storage and arithmetic.  F32: float storage and
-   interpolation; displacements, spline weights and all moment sums stay FP64. */
-enum { VLASOV_F64 = 0, VLASOV_F32 = 1 };
+/* Storage/arithmetic of f.
+   F64: double storage.  The spline filter runs on integer and FP32 units (FP64 arithmetic is slow
+        on this GPU): products of the high parts are exact int64 on a fixed-point grid of 2^-31 of a
+        bound 2^Ef >= 4 max|f| (Ef from the last upload), residuals in FP32; error per sweep about
+        2^-49 of 2^Ef, the size of FP64 rounding noise.  Needs |f| < 2^(Ef+1) (else VLASOV_ERANGE).
+   F32: float storage and interpolation; displacements and all moment sums stay FP64-accurate.
+   F64_NATIVE: double storage, IEEE FP64 filter arithmetic (reference; FP64-pipe bound). */
+enum { VLASOV_F64 = 0, VLASOV_F32 = 1, VLASOV_F64_NATIVE = 2 };
 
 typedef struct vlasov_sim vlasov_sim; /* opaque; owns every device buffer it uses */
 
@@ -52,7 +58,7 @@ typedef struct {
     int p_periodic;      /* same for p */
     double eps;          /* ring softening of Eq. (ringpot), > 0 for VLASOV_RING */
     double G;            /* sheet coupling: V(x) = 2 pi G |x| */
-    int precision;       /* VLASOV_F64 or VLASOV_F32 */
+    int precision;       /* VLASOV_F64, VLASOV_F32 or VLASOV_F64_NATIVE */
     void* stream;        /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
 } vlasov_domain;
 

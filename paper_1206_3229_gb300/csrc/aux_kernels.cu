@@ -10,6 +10,7 @@
 //   sheet (V = 2 pi G |x|):   F_i = -2 pi G dx (sum_{k<i} rho_k - sum_{k>i} rho_k)  (prefix scan)
 // Every sum across threads is an exact integer fixed-point sum (fixed_point.cuh): deterministic,
 // order-free, and without the long dependent FP64 chains that are slow on this GPU.
+#include "emul.cuh"
 #include "fixed_point.cuh"
 #include "vlasov_internal.cuh"
 
@@ -320,6 +321,19 @@ __global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
     w[9 * n + i] = d * c4;
     gd[i] = g;
     gd[n + i] = d;
+    if constexpr (sizeof(T) == 8) {
+        if (a.Wh) {
+#pragma unroll
+            for (int t = 0; t < NTAP; ++t) {
+                int h;
+                float l, f;
+                emul_weight((double)w[(size_t)t * n + i], h, l, f);
+                a.Wh[(size_t)t * n + i] = h;
+                a.wl[(size_t)t * n + i] = l;
+                a.wf[(size_t)t * n + i] = f;
+            }
+        }
+    }
 }
 
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st)

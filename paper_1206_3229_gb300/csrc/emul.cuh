@@ -1,0 +1,123 @@
+// emul.cuh -- FP64-accurate spline filter without FP64 instructions.
+//
+// GB300 executes FP64 arithmetic at ~1.6 operations per clock per SM (and float<->double
+// conversions at the same rate), far below what a 10-tap filter on FP64 data needs to keep up with
+// HBM.  For FP64 storage the sweeps therefore compute
+//
+//     out = sum_t w_t x_t
+//
+// with integer and FP32 units only, on a fixed-point grid set by a bound 2^Ef >= |f| (four times
+// the largest |f| uploaded):
+//   x_t * 2^(31-Ef) = kx_t + r_t,  kx_t = floor (int32), r_t in (-1, 1) (float, 24 bits)
+//   w_t * 2^30      = Wh_t + wl_t, Wh_t = round (int32), |wl_t| <= 1/2 (float)
+//   out * 2^(61-Ef) = sum_t Wh_t kx_t                      exact, int64 (IMAD.WIDE)
+//                   + sum_t (wl_t kx_t + w_t 2^30 r_t)      FP32 FMAs
+// and the int64 total is turned back into an FP64 value with integer instructions.  The error is
+// about 2^-49 of 2^Ef per sweep, the size of the rounding noise of an FP64 evaluation.  All
+// conversions read and build IEEE bit patterns directly.
+#pragma once
+#include <stdint.h>
+
+namespace vl {
+
+struct EmulElem {
+    int kx;     // floor part on the 2^(Ef-31) grid
+    float r;    // remainder in grid units
+};
+
+// Split x on the grid 2^(Ef-31).  s_base = 1044 + Ef.  |x| must be below 2^(Ef+1) (otherwise
+// `out_of_range` is set and the value is clamped to that); values below 2^(Ef-77) become zero.
+__device__ __forceinline__ EmulElem emul_split(double x, int s_base, bool& out_of_range)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    int s = s_base - e;                             // value = m * 2^-s in grid units
+    if (s < 22) {
+        out_of_range = true;
+        s = 22;
+    }
+    EmulElem o;
+    if (e == 0 || s > 77) {
+        o.kx = 0;
+        o.r = 0.f;
+        return o;
+    }
+    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const uint64_t k = s < 64 ? (m >> s) : 0ull;
+    const uint64_t rem = s < 64 ? (m - (k << s)) : m;     // < 2^s
+    const uint32_t top = s >= 24 ? (uint32_t)(rem >> (s - 24)) : (uint32_t)(rem << (24 - s));
+    float r = __uint2float_rn(top) * 5.9604644775390625e-08f;   // * 2^-24
+    int kx = (int)k;
+    if (hi >> 31) {
+        kx = -kx;
+        r = -r;
+    }
+    o.kx = kx;
+    o.r = r;
+    return o;
+}
+
+// Value of an element in FP64 (for the rare boundary corrections).
+__device__ __forceinline__ double emul_value(EmulElem v, double grid)
+{
+    return ((double)v.kx + (double)v.r) * grid;
+}
+
+// T * 2^(Ef-61) as an FP64 value, round to nearest even, integer instructions only.
+__device__ __forceinline__ double emul_to_f64(long long T, int Ef)
+{
+    if (T == 0) return 0.0;
+    const uint64_t sgn = (uint64_t)T >> 63;
+    const uint64_t a = sgn ? (uint64_t)(-T) : (uint64_t)T;
+    const int lz = __clzll((long long)a);
+    const uint64_t n = a << lz;                     // leading one at bit 63
+    uint64_t mant = n >> 11;                        // 53 bits including the hidden one
+    const uint64_t rem = n & 0x7FFull;
+    mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+    // biased exponent of a value in [2^(63-lz), 2^(64-lz)) times 2^(Ef-61); the hidden bit of
+    // mant adds one to the exponent field (and a rounding carry into bit 53 adds one more).
+    const int64_t E = (int64_t)(63 - lz + Ef - 61 + 1023 - 1);
+    const uint64_t bits = (sgn << 63) + ((uint64_t)E << 52) + mant;
+    return __longlong_as_double((long long)bits);
+}
+
+// Filter weights in the emulated form.  Wh = round(w 2^30), wl = (w 2^30 - Wh) as float,
+// wf = w 2^30 as float.  Integer instructions only.
+__host__ __device__ __forceinline__ void emul_weight(double w, int& Wh, float& wl, float& wf)
+{
+#ifdef __CUDA_ARCH__
+    const uint64_t b = (uint64_t)__double_as_longlong(w);
+#else
+    uint64_t b;
+    __builtin_memcpy(&b, &w, 8);
+#endif
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) {
+        Wh = 0;
+        wl = 0.f;
+        wf = 0.f;
+        return;
+    }
+    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    // w * 2^60 = m * 2^(e - 1075 + 60); |w| < 4 so the shift is <= 3 to the left
+    const int sh = e - 1015;
+    long long fx;   // round(w * 2^60)
+    if (sh >= 0) fx = (long long)(m << sh);
+    else if (sh > -64) fx = (long long)((m >> (-sh)) + ((m >> (-sh - 1)) & 1ull));
+    else fx = 0;
+    if (b >> 63) fx = -fx;
+    // Wh = round(fx / 2^30), remainder in [-2^29, 2^29]
+    const long long h = (fx + (1ll << 29)) >> 30;
+    const long long l = fx - (h << 30);
+    Wh = (int)h;
+#ifdef __CUDA_ARCH__
+    wl = __ll2float_rn(l) * 9.313225746154785e-10f;   // * 2^-30
+    wf = __ll2float_rn(fx) * 9.313225746154785e-10f;  // round(w 2^60) rounded to float, * 2^-30
+#else
+    wl = (float)l * 9.313225746154785e-10f;
+    wf = (float)fx * 9.313225746154785e-10f;
+#endif
+}
+
+}  // namespace vl

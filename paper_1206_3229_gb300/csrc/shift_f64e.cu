@@ -1,0 +1,447 @@
+// shift_f64e.cu -- the two sweeps for FP64 storage, computed without FP64 instructions.
+//
+// Same data movement as shift_kernels.cu (rows staged by 1-D bulk copies for the x-shift, 2-D TMA
+// column tiles for the p-shift), plus one pass over the staged values that rewrites every FP64
+// element in place as (kx, r) on the 2^(Ef-31) grid (emul.cuh).  The filter then runs on integer
+// and FP32 pipes: 10 IMAD.WIDE + 20 FFMA per output, the result is rebuilt as an FP64 bit pattern
+// with integer instructions.  Boundary corrections of non-periodic axes (f'' = 0 outside the grid)
+// are rare and done in FP64.
+#include "emul.cuh"
+#include "fixed_point.cuh"
+#include "ptx.cuh"
+#include "shift_common.cuh"
+#include "vlasov_internal.cuh"
+
+namespace vl {
+
+// Rewrite n doubles at p (shared memory) as EmulElem, block-strided.
+__device__ __forceinline__ void convert_range(double* p, int n, int s_base, bool& bad)
+{
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const EmulElem v = emul_split(p[e], s_base, bad);
+        reinterpret_cast<int2*>(p)[e] = make_int2(v.kx, __float_as_int(v.r));
+    }
+}
+
+struct EmulW {
+    int Wh[NTAP];
+    float wl[NTAP];
+    float wf[NTAP];
+};
+
+// One output from a window of ten elements (kx[t], kf[t] = (float)kx[t], r[t]).
+__device__ __forceinline__ long long emul_fir(const EmulW& w, const int* kx, const float* kf, const float* r)
+{
+    long long M = 0;
+    float S = 0.f;
+#pragma unroll
+    for (int t = 0; t < NTAP; ++t) {
+        M += (long long)w.Wh[t] * (long long)kx[t];
+        S = fmaf(w.wl[t], kf[t], S);
+        S = fmaf(w.wf[t], r[t], S);
+    }
+    return M + __float2ll_rn(S);
+}
+
+// FP64 boundary correction (non-periodic axes): value of the zero-extended filter minus the
+// f'' terms at nodes outside [0, n).  x points at the ten window values (as doubles).
+__device__ __forceinline__ double emul_edge(double out, const double* x, int k, int n, double g, double d)
+{
+    return edge_fix(out, x, k, n, g, d);
+}
+
+constexpr int XE_V = 4;      // consecutive outputs per thread and chunk
+constexpr int XE_W = 14;     // window elements: V + 9 + alignment slack (even)
+constexpr int XE_MAXCH = 4;  // chunks per row per thread (Nx <= 4 * 4 * 256 = 4096)
+
+// ============================================================================ x-shift (emulated FP64)
+template <bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_e_kernel(XShiftArgs a, EmulArgs em)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    double* bufs = reinterpret_cast<double*>(smem_raw + 128);
+    __shared__ double red[32];
+
+    const double* __restrict__ fin = static_cast<const double*>(a.fin);
+    double* __restrict__ fout = static_cast<double*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
+    const int stride = Nx + 2 * PAD;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int G = gridDim.x;
+    const uint32_t row_bytes = (uint32_t)(Nx * 8);
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u);
+    const int s_base = 1044 + em.Ef;
+    const double grid = ldexp(1.0, em.Ef - 31);
+    bool bad = false;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    if constexpr (!PERIODIC) {
+        for (int s = 0; s < S; ++s) {
+            double* b = bufs + (size_t)s * stride;
+            for (int e = tid; e < PAD; e += nthreads) {
+                b[e] = 0.0;
+                b[PAD + Nx + e] = 0.0;
+            }
+        }
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int r) {
+        double* dst = bufs + (size_t)s * stride + PAD;
+        const double* src = fin + (size_t)r * Nx;
+        mbar_arrive_expect_tx(&bars[s], tx_bytes);
+        bulk_g2s(dst, src, row_bytes, &bars[s]);
+        if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            const int r = blockIdx.x + s * G;
+            if (r < Np) issue(s, r);
+        }
+    }
+
+    long long colacc[XE_MAXCH][XE_V];
+#pragma unroll
+    for (int c = 0; c < XE_MAXCH; ++c)
+#pragma unroll
+        for (int v = 0; v < XE_V; ++v) colacc[c][v] = 0;
+    double kin = 0.0;
+
+    int it = 0;
+    int r = blockIdx.x;
+    bool failed = false;
+    for (; r < Np; r += G, ++it) {
+        const int s = it % S;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / S) & 1), WAIT_LIMIT_NS);
+        double* rowbuf = bufs + (size_t)s * stride + PAD;
+        if (ok) convert_range(rowbuf, Nx + (PERIODIC ? 16 : 0), s_base, bad);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const int n0 = em.n0[r];
+        EmulW w;
+#pragma unroll
+        for (int t = 0; t < NTAP; ++t) {
+            w.Wh[t] = em.Wh[(size_t)t * Np + r];
+            w.wl[t] = em.wl[(size_t)t * Np + r];
+            w.wf[t] = em.wf[(size_t)t * Np + r];
+        }
+        double g = 0.0, d = 0.0;
+        if constexpr (!PERIODIC) {
+            g = em.gd[r];
+            d = em.gd[Np + r];
+        }
+        const int A = (n0 - 4) & 1;
+        int base;
+        if constexpr (PERIODIC) {
+            base = (n0 - 4 - A) % Nx;
+            if (base < 0) base += Nx;
+        } else {
+            base = n0 - 4 - A;
+        }
+        const int2* src = reinterpret_cast<const int2*>(rowbuf);
+        double* orow = fout + (size_t)r * Nx;
+        long long rowsum = 0;
+#pragma unroll
+        for (int c = 0; c < XE_MAXCH; ++c) {
+            const int i = XE_V * (tid + c * nthreads);
+            if (i < Nx) {
+                int e = i + base;
+                if constexpr (PERIODIC) {
+                    if (e >= Nx) e -= Nx;
+                }
+                int kx[XE_W];
+                float kf[XE_W], rr[XE_W];
+                const int4* q = reinterpret_cast<const int4*>(src + e);
+#pragma unroll
+                for (int u = 0; u < XE_W / 2; ++u) {
+                    const int4 v = q[u];
+                    kx[2 * u] = v.x;
+                    rr[2 * u] = __int_as_float(v.y);
+                    kx[2 * u + 1] = v.z;
+                    rr[2 * u + 1] = __int_as_float(v.w);
+                }
+#pragma unroll
+                for (int u = 0; u < XE_W; ++u) kf[u] = __int2float_rn(kx[u]);
+                double out[XE_V];
+#pragma unroll
+                for (int v = 0; v < XE_V; ++v) {
+                    long long T;
+                    if (A == 0) T = emul_fir(w, kx + v, kf + v, rr + v);
+                    else T = emul_fir(w, kx + v + 1, kf + v + 1, rr + v + 1);
+                    out[v] = emul_to_f64(T, em.Ef);
+                    const long long Tc = (T + 512) >> 10;
+                    colacc[c][v] += Tc;
+                    rowsum += Tc;
+                }
+                if constexpr (!PERIODIC) {
+                    const int k = i + n0;
+                    if (k < 0 || k + XE_V - 1 >= Nx - 1) {
+                        double xv[XE_W];
+#pragma unroll
+                        for (int u = 0; u < XE_W; ++u) xv[u] = ((double)kx[u] + (double)rr[u]) * grid;
+#pragma unroll
+                        for (int v = 0; v < XE_V; ++v) out[v] = emul_edge(out[v], xv + v + A, k + v, Nx, g, d);
+                    }
+                }
+                double2* o = reinterpret_cast<double2*>(orow + i);
+                o[0] = make_double2(out[0], out[1]);
+                o[1] = make_double2(out[2], out[3]);
+            }
+        }
+        if constexpr (KIN) {
+            const double pj = a.pmin + (double)r * a.dp;
+            kin = fma(0.5 * pj * pj, fx128_to_f64((i128)rowsum, 51 - em.Ef), kin);
+        }
+        __syncthreads();   // every thread done with stage s
+        if (tid == 0) {
+            const int rn = r + S * G;
+            if (rn < Np) {
+                fence_proxy_async_smem();
+                issue(s, rn);
+            }
+        }
+    }
+    if (bad) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+
+    if (failed) {
+        if (tid == 0) {
+            atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
+            for (int k = 0; k < S; ++k) {
+                const int rr = r + k * G;
+                if (rr >= Np) break;
+                const int itk = it + k;
+                mbar_wait_bounded(&bars[itk % S], (uint32_t)((itk / S) & 1), WAIT_LIMIT_NS);
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    if (a.colpart) {
+        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < XE_MAXCH; ++c) {
+            const int i = XE_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XE_V; ++v) cp[i + v] = fx128_to_f64((i128)colacc[c][v], 51 - em.Ef);
+            }
+        }
+    }
+    if constexpr (KIN) {
+        double v = kin;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int q = 0; q < (nthreads + 31) / 32; ++q) s += red[q];
+            a.kinpart[blockIdx.x] = s;
+        }
+    }
+}
+
+// ============================================================================ p-shift (emulated FP64)
+template <bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                    PShiftArgs a, EmulArgs em)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    double* bufs = reinterpret_cast<double*>(smem_raw + 128);
+    constexpr int BUF = PS_RB * PS_TW;
+
+    const double* __restrict__ fin = static_cast<const double*>(a.fin);
+    double* __restrict__ fout = static_cast<double*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np;
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+    const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PS_TH - 1) / PS_TH;
+    const int ntiles = ntx * nty;
+    const int G = gridDim.x;
+    const int s_base = 1044 + em.Ef;
+    const double grid = ldexp(1.0, em.Ef - 31);
+    bool bad = false;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+        prefetch_tensormap(&tmap);
+    }
+    __syncthreads();
+
+    auto issue = [&](int b, const TileWin& t) {
+        if (t.smem_ok) {
+            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * 8));
+            for (int q = 0; q < t.nb; ++q)
+                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, &tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
+        } else {
+            mbar_arrive_expect_tx(&bars[b], 0u);
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (grp == 0 && tile < ntiles) {
+        int n0l;
+        bool cv;
+        TileWin t = tile_window<PPER>(tile, ntx, em.n0, Nx, lane, n0l, cv);
+        if (lane == 0) issue(0, t);
+    }
+
+    int q = 0;
+    bool failed = false;
+    for (; tile < ntiles; tile += G, ++q) {
+        const int b = q & 1;
+        const int nt = tile + G;
+        if (grp == 0 && nt < ntiles) {
+            int n0l;
+            bool cv;
+            TileWin tn = tile_window<PPER>(nt, ntx, em.n0, Nx, lane, n0l, cv);
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(b ^ 1, tn);
+            }
+        }
+        int n0_i;
+        bool colvalid;
+        const TileWin t = tile_window<PPER>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
+        const int i = t.i0 + lane;
+        EmulW w;
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) {
+            w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + i] : 0;
+            w.wl[k] = colvalid ? em.wl[(size_t)k * Nx + i] : 0.f;
+            w.wf[k] = colvalid ? em.wf[(size_t)k * Nx + i] : 0.f;
+        }
+        double g = 0.0, d = 0.0;
+        if constexpr (!PPER) {
+            if (colvalid) {
+                g = em.gd[i];
+                d = em.gd[Nx + i];
+            }
+        }
+        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
+        double* buf = bufs + (size_t)b * BUF;
+        if (ok && t.smem_ok) convert_range(buf, t.nb * PS_BH * PS_TW, s_base, bad);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const int jb = t.j0 + grp * PS_RPT;
+        int kx[PS_RPT + 9];
+        float kf[PS_RPT + 9], rr[PS_RPT + 9];
+        if (t.smem_ok) {
+            const int2* sb = reinterpret_cast<const int2*>(buf);
+            const int base = jb + n0_i - 4 - t.r0;
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u) {
+                const int2 v = sb[(base + u) * PS_TW + lane];
+                kx[u] = v.x;
+                rr[u] = __int_as_float(v.y);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u) {
+                const double x = colvalid ? gload_p<double, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0.0;
+                const EmulElem v = emul_split(x, s_base, bad);
+                kx[u] = v.kx;
+                rr[u] = v.r;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PS_RPT + 9; ++u) kf[u] = __int2float_rn(kx[u]);
+#pragma unroll
+        for (int rw = 0; rw < PS_RPT; ++rw) {
+            const int j = jb + rw;
+            double out = emul_to_f64(emul_fir(w, kx + rw, kf + rw, rr + rw), em.Ef);
+            if constexpr (!PPER) {
+                const int kk = j + n0_i;
+                if (kk < 0 || kk >= Np - 1) {
+                    double xv[NTAP];
+#pragma unroll
+                    for (int u = 0; u < NTAP; ++u) xv[u] = ((double)kx[rw + u] + (double)rr[rw + u]) * grid;
+                    out = emul_edge(out, xv, kk, Np, g, d);
+                }
+            }
+            if (colvalid && j < Np) fout[(size_t)j * Nx + i] = out;
+        }
+        __syncthreads();   // every thread done with buffer b before it is refilled
+    }
+    if (bad) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    if (failed && tid == 0) {
+        atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+        if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
+        mbar_wait_bounded(&bars[q & 1], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
+    }
+}
+
+int xshift_e_max_cols(int threads) { return XE_V * threads * XE_MAXCH; }
+
+cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
+                            cudaStream_t st)
+{
+    const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, 8);
+    if (periodic) {
+        if (kin) xshift_e_kernel<true, true><<<grid, threads, smem, st>>>(a, em);
+        else xshift_e_kernel<true, false><<<grid, threads, smem, st>>>(a, em);
+    } else {
+        if (kin) xshift_e_kernel<false, true><<<grid, threads, smem, st>>>(a, em);
+        else xshift_e_kernel<false, false><<<grid, threads, smem, st>>>(a, em);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pshift_e(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em,
+                            cudaStream_t st)
+{
+    const size_t smem = pshift_smem_bytes(8);
+    if (p_periodic) pshift_e_kernel<true><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
+    else pshift_e_kernel<false><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
+    return cudaGetLastError();
+}
+
+cudaError_t set_kernel_attributes_e(int max_smem)
+{
+    cudaError_t e = cudaSuccess;
+#define VL_ATTR(fn) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)
+    VL_ATTR((xshift_e_kernel<true, true>));
+    VL_ATTR((xshift_e_kernel<true, false>));
+    VL_ATTR((xshift_e_kernel<false, true>));
+    VL_ATTR((xshift_e_kernel<false, false>));
+    VL_ATTR((pshift_e_kernel<true>));
+    VL_ATTR((pshift_e_kernel<false>));
+#undef VL_ATTR
+    return e;
+}
+
+// ============================================================================ filter split (emulated)
+__global__ void emul_params_kernel(int n, const double* __restrict__ w, int* Wh, float* wl, float* wf)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * NTAP) return;
+    int h;
+    float l, f;
+    emul_weight(w[idx], h, l, f);
+    Wh[idx] = h;
+    wl[idx] = l;
+    wf[idx] = f;
+}
+
+cudaError_t launch_emul_params(int n, const double* w, int* Wh, float* wl, float* wf, cudaStream_t st)
+{
+    const int tot = n * NTAP;
+    emul_params_kernel<<<(tot + 255) / 256, 256, 0, st>>>(n, w, Wh, wl, wf);
+    return cudaGetLastError();
+}
+
+}  // namespace vl

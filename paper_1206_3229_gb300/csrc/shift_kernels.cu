@@ -13,6 +13,7 @@
 //  f = 0 outside reading of the p axis), each thread walks 16 rows of one column with a sliding
 //  register window.
 #include "ptx.cuh"
+#include "shift_common.cuh"
 #include "vlasov_internal.cuh"
 
 namespace vl {
@@ -35,33 +36,6 @@ struct VecOf<float> {
 };
 
 constexpr int XS_MAXCH = 8;   // chunks of V*threads outputs per row handled by one thread
-
-// Dynamic shared memory rounded up to a 128-byte boundary (TMA destinations); every launch
-// reserves 128 extra bytes for this.
-__device__ __forceinline__ unsigned char* align128(unsigned char* p)
-{
-    const uint32_t a = smem_u32(p);
-    return p + ((128u - (a & 127u)) & 127u);
-}
-
-// D_k of Eq. (findif) (undivided) for a window starting at f_{k-4}.
-template <typename T>
-__device__ __forceinline__ T fd_undivided(const T* x)
-{
-    const T c0 = T(VL_FD_C0), c1 = T(VL_FD_C1), c2 = T(VL_FD_C2), c3 = T(VL_FD_C3), c4 = T(VL_FD_C4);
-    return c4 * (x[0] + x[8]) + c3 * (x[1] + x[7]) + c2 * (x[2] + x[6]) + c1 * (x[3] + x[5]) + c0 * x[4];
-}
-
-// Non-periodic axes take f'' = 0 at nodes outside the grid.  The 10-tap filter evaluates D at
-// k and k+1 from the zero-extended f, so remove those terms when k or k+1 lies outside [0, n).
-// `x` starts at f_{k-4}.
-template <typename T>
-__device__ __forceinline__ T edge_fix(T out, const T* x, int k, int n, T g, T d)
-{
-    if (k < 0 || k >= n) out -= g * fd_undivided(x);
-    if (k + 1 < 0 || k + 1 >= n) out -= d * fd_undivided(x + 1);
-    return out;
-}
 
 // ============================================================================ x-shift
 template <typename T, int A, bool PERIODIC>
@@ -332,51 +306,6 @@ cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int
 }
 
 // ============================================================================ p-shift
-template <typename T, bool PPER>
-__device__ __forceinline__ T gload_p(const T* __restrict__ f, int row, int col, int Nx, int Np)
-{
-    if constexpr (PPER) {
-        int rr = row % Np;
-        if (rr < 0) rr += Np;
-        return f[(size_t)rr * Nx + col];
-    } else {
-        return (row >= 0 && row < Np) ? f[(size_t)row * Nx + col] : T(0);
-    }
-}
-
-struct TileWin {
-    int i0, j0, r0, nb;
-    bool smem_ok;
-};
-
-// Window of input rows a tile needs: [j0 + kmin - 4, j0 + TH - 1 + kmax + 5].  Called by whole
-// warps (all lanes hold one column); identical in every warp.
-template <bool PPER>
-__device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __restrict__ n0, int Nx, int lane,
-                                               int& n0_lane, bool& colvalid)
-{
-    TileWin t;
-    const int tx = tile % ntx, ty = tile / ntx;
-    t.i0 = tx * PS_TW;
-    t.j0 = ty * PS_TH;
-    const int i = t.i0 + lane;
-    colvalid = i < Nx;
-    n0_lane = colvalid ? n0[i] : 0;
-    int kmin = colvalid ? n0_lane : 0x7fffffff;
-    int kmax = colvalid ? n0_lane : (int)0x80000000;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    }
-    if (!colvalid) n0_lane = kmin;   // columns past Nx read (and discard) the tile's own window
-    t.r0 = t.j0 + kmin - 4;
-    const long long R = (long long)PS_TH + 9 + ((long long)kmax - (long long)kmin);
-    t.smem_ok = !PPER && R <= PS_RB;
-    t.nb = t.smem_ok ? (int)((R + PS_BH - 1) / PS_BH) : 0;
-    return t;
-}
-
 template <typename T, bool PPER>
 __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
 {

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/vlasov.h"
+#include "emul.cuh"
 #include "vlasov_internal.cuh"
 
 using namespace vl;
@@ -70,7 +71,9 @@ struct vlasov_sim {
     int cur = 0;
     bool has_f = false;
 
+    bool emul = false;          // FP64 storage, integer/FP32 filter arithmetic (emul.cuh)
     LineParamsDev xp, pp, sp;   // x rows (fixed), p columns (per step), scratch for substeps
+    EmulParamsDev xe, pe, se;   // their emulated-FP64 splits
     int xthreads = 256, xstages = 1, xpad = 16, xgrid = 1, pgrid = 1, crgrid = 1;
 
     double* colpart = nullptr;  // [xgrid][Nx]
@@ -121,8 +124,26 @@ int alloc_params(LineParamsDev& p, int n, int esz)
     return VLASOV_OK;
 }
 
-// Host-side filters for n lines with displacements disp[] (cells), uploaded to p.
-int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, int* max_abs_n0)
+void free_emul(EmulParamsDev& e)
+{
+    cudaFree(e.Wh);
+    cudaFree(e.wl);
+    cudaFree(e.wf);
+    e = EmulParamsDev{};
+}
+
+int alloc_emul(EmulParamsDev& e, int n)
+{
+    CU_TRY(cudaMalloc(&e.Wh, sizeof(int) * NTAP * (size_t)n));
+    CU_TRY(cudaMalloc(&e.wl, sizeof(float) * NTAP * (size_t)n));
+    CU_TRY(cudaMalloc(&e.wf, sizeof(float) * NTAP * (size_t)n));
+    return VLASOV_OK;
+}
+
+// Host-side filters for n lines with displacements disp[] (cells), uploaded to p (and, for the
+// emulated FP64 sweeps, their integer/FP32 split to e).
+int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, int* max_abs_n0,
+                  EmulParamsDev* e = nullptr)
 {
     std::vector<int> n0(n);
     std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n);
@@ -138,6 +159,15 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
     }
     if (max_abs_n0) *max_abs_n0 = mx;
     CU_TRY(cudaMemcpyAsync(p.n0, n0.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s->st));
+    if (s->emul && e) {
+        std::vector<int> Wh(w.size());
+        std::vector<float> wl(w.size()), wf(w.size());
+        for (size_t q = 0; q < w.size(); ++q) emul_weight(w[q], Wh[q], wl[q], wf[q]);
+        CU_TRY(cudaMemcpyAsync(e->Wh, Wh.data(), sizeof(int) * Wh.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaMemcpyAsync(e->wl, wl.data(), sizeof(float) * wl.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaMemcpyAsync(e->wf, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    }
     if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(p.w, w.data(), 8 * w.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaMemcpyAsync(p.gd, gd.data(), 8 * gd.size(), cudaMemcpyHostToDevice, s->st));
@@ -239,6 +269,31 @@ void update_scales(vlasov_sim* s, double maxabs)
     s->scales_set = true;
 }
 
+EmulArgs emargs(vlasov_sim* s, const LineParamsDev& p, const EmulParamsDev& e)
+{
+    EmulArgs a;
+    a.Ef = s->Ef;
+    a.n0 = p.n0;
+    a.Wh = e.Wh;
+    a.wl = e.wl;
+    a.wf = e.wf;
+    a.gd = static_cast<const double*>(p.gd);
+    return a;
+}
+
+cudaError_t run_xshift(vlasov_sim* s, const XShiftArgs& a, const LineParamsDev& p, const EmulParamsDev& e, bool kin)
+{
+    if (s->emul) return launch_xshift_e(s->xper, kin, s->xgrid, s->xthreads, a, emargs(s, p, e), s->st);
+    return launch_xshift(s->esz, s->xper, kin, s->xgrid, s->xthreads, a, s->st);
+}
+
+cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs& a, const LineParamsDev& p,
+                       const EmulParamsDev& e)
+{
+    if (s->emul) return launch_pshift_e(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
+    return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, s->st);
+}
+
 ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments)
 {
     ColReduceArgs a;
@@ -304,6 +359,9 @@ int launch_pparams_only(vlasov_sim* s, double* Fout)
     a.w = s->pp.w;
     a.gd = s->pp.gd;
     a.Fout = Fout;
+    a.Wh = s->emul ? s->pe.Wh : nullptr;
+    a.wl = s->emul ? s->pe.wl : nullptr;
+    a.wf = s->emul ? s->pe.wf : nullptr;
     CU_TRY(launch_pparams(s->esz, a, s->st));
     return VLASOV_OK;
 }
@@ -339,8 +397,7 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     const int o = c ^ 1;
     MARK();
     // step 1: f^(I) = f(x - p dt/2, p), with the density partials of f^(I)
-    CU_TRY(launch_xshift(s->esz, s->xper, false, s->xgrid, s->xthreads, xargs(s, s->f[c], s->f[o], s->xp, true, false),
-                         s->st));
+    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false), s->xp, s->xe, false));
     MARK();
     // step 2: rho, moments, F^(I), p-shift filters
     CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
@@ -355,11 +412,10 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     }
     MARK();
     // step 3: f^(II) = f^(I)(x, p - F dt)
-    CU_TRY(launch_pshift(s->esz, s->pper, s->pgrid, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->st));
+    CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
     MARK();
     // step 4: f(t+dt) = f^(II)(x - p dt/2, p), with density + kinetic partials for the moments
-    CU_TRY(launch_xshift(s->esz, s->xper, true, s->xgrid, s->xthreads, xargs(s, s->f[c], s->f[o], s->xp, true, true),
-                         s->st));
+    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, true), s->xp, s->xe, true));
     MARK();
     CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
     MARK();
@@ -396,6 +452,9 @@ int check_dev_err(vlasov_sim* s)
     CU_TRY(cudaStreamSynchronize(s->st));
     if (h != DEV_ERR_NONE) {
         cudaMemsetAsync(s->err, 0, sizeof(int), s->st);
+        if (h == DEV_ERR_RANGE)
+            return fail(VLASOV_ERANGE, "|f| outgrew the fixed-point range (4x the largest uploaded |f|); "
+                                       "results since the last check are void");
         return fail(VLASOV_ETIMEOUT, "a bounded device wait expired (code %d); results since the last check are void", h);
     }
     return VLASOV_OK;
@@ -422,6 +481,9 @@ void vlasov_destroy(vlasov_sim* s)
     free_params(s->xp);
     free_params(s->pp);
     free_params(s->sp);
+    free_emul(s->xe);
+    free_emul(s->pe);
+    free_emul(s->se);
     void* bufs[] = {s->colpart, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
                     s->hist, s->dstep, s->err};
@@ -436,9 +498,9 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     *out = nullptr;
     if (!d) return fail(VLASOV_EINVAL, "domain is NULL");
     if (model < VLASOV_HMF || model > VLASOV_FREE) return fail(VLASOV_EINVAL, "unknown model %d", model);
-    if (d->precision != VLASOV_F64 && d->precision != VLASOV_F32)
+    if (d->precision != VLASOV_F64 && d->precision != VLASOV_F32 && d->precision != VLASOV_F64_NATIVE)
         return fail(VLASOV_EINVAL, "unknown precision %d", d->precision);
-    const int esz = d->precision == VLASOV_F64 ? 8 : 4;
+    const int esz = d->precision == VLASOV_F32 ? 4 : 8;
     if (Nx < 16 || Np < 16 || Nx % ALIGN_N || Np % ALIGN_N)
         return fail(VLASOV_EINVAL, "Nx=%d, Np=%d: both must be multiples of %d and >= 16", Nx, Np, ALIGN_N);
     if (Nx > xshift_max_cols(esz, XS_THREADS_MIN))
@@ -453,6 +515,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     s->Np = Np;
     s->prec = d->precision;
     s->esz = esz;
+    s->emul = d->precision == VLASOV_F64;
     s->xper = d->x_periodic != 0;
     s->pper = d->p_periodic != 0;
     s->xmin = d->xmin;
@@ -493,6 +556,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         s->own_stream = true;
     }
     CTRY(set_kernel_attributes(max_optin - 1024));
+    CTRY(set_kernel_attributes_e(max_optin - 1024));
 
     const size_t cells = (size_t)Nx * (size_t)Np;
     for (int b = 0; b < 2; ++b) {
@@ -512,8 +576,13 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     TRY(alloc_params(s->xp, Np, esz));
     TRY(alloc_params(s->pp, Nx, esz));
     TRY(alloc_params(s->sp, std::max(Nx, Np), esz));
+    if (s->emul) {
+        TRY(alloc_emul(s->xe, Np));
+        TRY(alloc_emul(s->pe, Nx));
+        TRY(alloc_emul(s->se, std::max(Nx, Np)));
+    }
     int max_n0 = 0;
-    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0));
+    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0, &s->xe));
 
     // x-shift launch shape: whole rows staged per CTA.
     s->xthreads = XS_THREADS_MIN;
@@ -721,7 +790,7 @@ int vlasov_substep(vlasov_sim* s, int axis, const double* host_disp)
     const int c = s->cur, o = c ^ 1;
     if (axis == 0) {
         int mx = 0;
-        int rc = upload_params(s, s->sp, host_disp, s->Np, &mx);
+        int rc = upload_params(s, s->sp, host_disp, s->Np, &mx, &s->se);
         if (rc) return rc;
         XShiftArgs a = xargs(s, s->f[c], s->f[o], s->sp, false, false);
         if (!s->xper && mx + 8 > s->xpad) {
@@ -734,11 +803,11 @@ int vlasov_substep(vlasov_sim* s, int axis, const double* host_disp)
             a.stages = (int)std::min<size_t>(4, budget / row_bytes);
             if (a.stages < 1) return fail(VLASOV_EINVAL, "x displacement of %d cells does not fit shared memory", mx);
         }
-        CU_TRY(launch_xshift(s->esz, s->xper, false, s->xgrid, s->xthreads, a, s->st));
+        CU_TRY(run_xshift(s, a, s->sp, s->se, false));
     } else {
-        int rc = upload_params(s, s->sp, host_disp, s->Nx, nullptr);
+        int rc = upload_params(s, s->sp, host_disp, s->Nx, nullptr, &s->se);
         if (rc) return rc;
-        CU_TRY(launch_pshift(s->esz, s->pper, s->pgrid, &s->tmap[c], pargs(s, s->f[c], s->f[o], s->sp), s->st));
+        CU_TRY(run_pshift(s, &s->tmap[c], pargs(s, s->f[c], s->f[o], s->sp), s->sp, s->se));
     }
     s->cur = o;
     CU_TRY(cudaStreamSynchronize(s->st));

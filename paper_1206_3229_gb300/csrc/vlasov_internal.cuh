@@ -64,7 +64,7 @@ struct LineParamsDev {
 };
 
 // Device-side error codes written to the handle's flag by a bounded wait that gave up.
-enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2 };
+enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2, DEV_ERR_RANGE = 3 };
 
 // Scalars produced by the reductions of one sweep (device struct).
 struct Scalars {
@@ -92,6 +92,23 @@ struct XShiftArgs {
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
     double pmin, dp;
     int* err;
+};
+
+// Filters of the emulated-FP64 sweeps (emul.cuh), structure-of-arrays over n lines:
+//   Wh[t*n + line] (int32), wl[t*n + line], wf[t*n + line] (float), plus n0 and gd (FP64) as above.
+struct EmulArgs {
+    int Ef;               // fixed-point bound: |f| < 2^Ef
+    const int* n0;
+    const int* Wh;
+    const float* wl;
+    const float* wf;
+    const double* gd;
+};
+
+struct EmulParamsDev {
+    int* Wh = nullptr;
+    float* wl = nullptr;
+    float* wf = nullptr;
 };
 
 struct PShiftArgs {
@@ -142,6 +159,9 @@ struct PParamsArgs {
     void* w;
     void* gd;
     double* Fout;            // optional copy of F [Nx]
+    int* Wh;                 // emulated-FP64 split of the weights, or null
+    float* wl;
+    float* wf;
 };
 
 struct RingArgs {
@@ -181,6 +201,12 @@ cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUten
                           const PShiftArgs& a, cudaStream_t st);
 
 cudaError_t set_kernel_attributes(int max_smem);
+cudaError_t set_kernel_attributes_e(int max_smem);
+int xshift_e_max_cols(int threads);
+cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
+                            cudaStream_t st);
+cudaError_t launch_pshift_e(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em,
+                            cudaStream_t st);
 cudaError_t xshift_occupancy(int elem_bytes, bool periodic, int threads, size_t smem, int* blocks);
 cudaError_t pshift_occupancy(int elem_bytes, int* blocks);
 

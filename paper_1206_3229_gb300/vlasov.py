@@ -15,11 +15,11 @@ from . import build as _build
 from .inputs import Workload
 
 HMF, RING, SHEET, FREE = 0, 1, 2, 3
-F64, F32 = 0, 1
+F64, F32, F64_NATIVE = 0, 1, 2
 MODELS = {"hmf": HMF, "ring": RING, "sheet": SHEET, "free": FREE}
-PRECISIONS = {"f64": F64, "f32": F32}
+PRECISIONS = {"f64": F64, "f32": F32, "f64_native": F64_NATIVE}
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
 EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_f", "vlasov_get_f_device",
             "vlasov_step", "vlasov_moments", "vlasov_substep", "vlasov_density_force", "vlasov_sync",
