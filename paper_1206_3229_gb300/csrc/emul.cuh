@@ -58,6 +58,21 @@ __device__ __forceinline__ EmulElem emul_split(double x, int s_base, bool& out_o
     return o;
 }
 
+// round(S) (ties away from zero) as int64 with integer instructions; |S| < 2^62.  (The hardware
+// float->int64 conversion issues on the FP64 pipe on this GPU.)
+__device__ __forceinline__ long long f32_to_ll_round(float S)
+{
+    const uint32_t b = (uint32_t)__float_as_int(S);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = e - 150;                      // |S| = m * 2^sh
+    long long v;
+    if (e < 126) v = 0;                          // |S| < 0.5
+    else if (sh >= 0) v = (long long)m << sh;
+    else v = (long long)((m + (1u << (-sh - 1))) >> (-sh));
+    return (b >> 31) ? -v : v;
+}
+
 // Value of an element in FP64 (for the rare boundary corrections).
 __device__ __forceinline__ double emul_value(EmulElem v, double grid)
 {

@@ -40,7 +40,7 @@ struct TileWin {
 
 // Window of input rows a tile needs: [j0 + kmin - 4, j0 + TH - 1 + kmax + 5].  Called by whole
 // warps (all lanes hold one column); identical in every warp.
-template <bool PPER>
+template <bool PPER, int RB = PS_RB>
 __device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __restrict__ n0, int Nx, int lane,
                                                int& n0_lane, bool& colvalid)
 {
@@ -61,7 +61,7 @@ __device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __r
     if (!colvalid) n0_lane = kmin;   // columns past Nx read (and discard) the tile's own window
     t.r0 = t.j0 + kmin - 4;
     const long long R = (long long)PS_TH + 9 + ((long long)kmax - (long long)kmin);
-    t.smem_ok = !PPER && R <= PS_RB;
+    t.smem_ok = !PPER && R <= RB;
     t.nb = t.smem_ok ? (int)((R + PS_BH - 1) / PS_BH) : 0;
     return t;
 }

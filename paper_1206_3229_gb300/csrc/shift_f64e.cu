@@ -40,7 +40,7 @@ __device__ __forceinline__ long long emul_fir(const EmulW& w, const int* kx, con
         S = fmaf(w.wl[t], kf[t], S);
         S = fmaf(w.wf[t], r[t], S);
     }
-    return M + __float2ll_rn(S);
+    return M + f32_to_ll_round(S);
 }
 
 // FP64 boundary correction (non-periodic axes): value of the zero-extended filter minus the
@@ -51,12 +51,13 @@ __device__ __forceinline__ double emul_edge(double out, const double* x, int k, 
 }
 
 constexpr int XE_V = 4;      // consecutive outputs per thread and chunk
+constexpr int PSE_RB = 192;  // staged rows per buffer of the emulated p-shift (two CTAs per SM)
 constexpr int XE_W = 14;     // window elements: V + 9 + alignment slack (even)
 constexpr int XE_MAXCH = 4;  // chunks per row per thread (Nx <= 4 * 4 * 256 = 4096)
 
 // ============================================================================ x-shift (emulated FP64)
 template <bool PERIODIC, bool KIN>
-__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_e_kernel(XShiftArgs a, EmulArgs em)
+__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs a, EmulArgs em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
@@ -251,14 +252,14 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_e_kernel(XShiftArgs 
 
 // ============================================================================ p-shift (emulated FP64)
 template <bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                     PShiftArgs a, EmulArgs em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     double* bufs = reinterpret_cast<double*>(smem_raw + 128);
-    constexpr int BUF = PS_RB * PS_TW;
+    constexpr int BUF = PSE_RB * PS_TW;
 
     const double* __restrict__ fin = static_cast<const double*>(a.fin);
     double* __restrict__ fout = static_cast<double*>(a.fout);
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid
     if (grp == 0 && tile < ntiles) {
         int n0l;
         bool cv;
-        TileWin t = tile_window<PPER>(tile, ntx, em.n0, Nx, lane, n0l, cv);
+        TileWin t = tile_window<PPER, PSE_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
         if (lane == 0) issue(0, t);
     }
 
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid
         if (grp == 0 && nt < ntiles) {
             int n0l;
             bool cv;
-            TileWin tn = tile_window<PPER>(nt, ntx, em.n0, Nx, lane, n0l, cv);
+            TileWin tn = tile_window<PPER, PSE_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
             if (lane == 0) {
                 fence_proxy_async_smem();
                 issue(b ^ 1, tn);
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid
         }
         int n0_i;
         bool colvalid;
-        const TileWin t = tile_window<PPER>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
+        const TileWin t = tile_window<PPER, PSE_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
         const int i = t.i0 + lane;
         EmulW w;
 #pragma unroll
@@ -337,38 +338,63 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid
             break;
         }
         const int jb = t.j0 + grp * PS_RPT;
-        int kx[PS_RPT + 9];
-        float kf[PS_RPT + 9], rr[PS_RPT + 9];
-        if (t.smem_ok) {
-            const int2* sb = reinterpret_cast<const int2*>(buf);
-            const int base = jb + n0_i - 4 - t.r0;
+        // Input-stationary filter: walk the 25 window elements once; element u feeds outputs
+        // rw = u-9 .. u (tap u - rw).  Keeps 16 int64 + 16 float accumulators live instead of the
+        // whole converted window.
+        long long M[PS_RPT];
+        float Sacc[PS_RPT];
 #pragma unroll
-            for (int u = 0; u < PS_RPT + 9; ++u) {
+        for (int rw = 0; rw < PS_RPT; ++rw) {
+            M[rw] = 0;
+            Sacc[rw] = 0.f;
+        }
+        const int2* sb = reinterpret_cast<const int2*>(buf);
+        const int base = jb + n0_i - 4 - t.r0;
+#pragma unroll
+        for (int u = 0; u < PS_RPT + 9; ++u) {
+            int kx;
+            float rr;
+            if (t.smem_ok) {
                 const int2 v = sb[(base + u) * PS_TW + lane];
-                kx[u] = v.x;
-                rr[u] = __int_as_float(v.y);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < PS_RPT + 9; ++u) {
+                kx = v.x;
+                rr = __int_as_float(v.y);
+            } else {
                 const double x = colvalid ? gload_p<double, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0.0;
                 const EmulElem v = emul_split(x, s_base, bad);
-                kx[u] = v.kx;
-                rr[u] = v.r;
+                kx = v.kx;
+                rr = v.r;
+            }
+            const float kf = __int2float_rn(kx);
+#pragma unroll
+            for (int tap = 0; tap < NTAP; ++tap) {
+                const int rw = u - tap;
+                if (rw >= 0 && rw < PS_RPT) {
+                    M[rw] += (long long)w.Wh[tap] * (long long)kx;
+                    Sacc[rw] = fmaf(w.wl[tap], kf, Sacc[rw]);
+                    Sacc[rw] = fmaf(w.wf[tap], rr, Sacc[rw]);
+                }
             }
         }
 #pragma unroll
-        for (int u = 0; u < PS_RPT + 9; ++u) kf[u] = __int2float_rn(kx[u]);
-#pragma unroll
         for (int rw = 0; rw < PS_RPT; ++rw) {
             const int j = jb + rw;
-            double out = emul_to_f64(emul_fir(w, kx + rw, kf + rw, rr + rw), em.Ef);
+            double out = emul_to_f64(M[rw] + f32_to_ll_round(Sacc[rw]), em.Ef);
             if constexpr (!PPER) {
                 const int kk = j + n0_i;
                 if (kk < 0 || kk >= Np - 1) {
+                    // rare: rebuild the ten inputs in FP64 for the boundary correction
                     double xv[NTAP];
 #pragma unroll
-                    for (int u = 0; u < NTAP; ++u) xv[u] = ((double)kx[rw + u] + (double)rr[rw + u]) * grid;
+                    for (int u = 0; u < NTAP; ++u) {
+                        double x;
+                        if (t.smem_ok) {
+                            const int2 v = sb[(base + rw + u) * PS_TW + lane];
+                            x = ((double)v.x + (double)__int_as_float(v.y)) * grid;
+                        } else {
+                            x = colvalid ? gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np) : 0.0;
+                        }
+                        xv[u] = x;
+                    }
                     out = emul_edge(out, xv, kk, Np, g, d);
                 }
             }
@@ -385,6 +411,19 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_e_kernel(const __grid
 }
 
 int xshift_e_max_cols(int threads) { return XE_V * threads * XE_MAXCH; }
+
+size_t pshift_e_smem_bytes() { return 256 + 2 * (size_t)PSE_RB * PS_TW * 8; }
+
+cudaError_t xshift_e_occupancy(bool periodic, size_t smem, int* blocks)
+{
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_e_kernel<true, true>, XS_THREADS_MIN, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_e_kernel<false, true>, XS_THREADS_MIN, smem);
+}
+
+cudaError_t pshift_e_occupancy(int* blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_e_kernel<false>, PS_TW * PS_RG, pshift_e_smem_bytes());
+}
 
 cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                             cudaStream_t st)
@@ -403,7 +442,7 @@ cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, cons
 cudaError_t launch_pshift_e(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em,
                             cudaStream_t st)
 {
-    const size_t smem = pshift_smem_bytes(8);
+    const size_t smem = pshift_e_smem_bytes();
     if (p_periodic) pshift_e_kernel<true><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
     else pshift_e_kernel<false><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
     return cudaGetLastError();

@@ -590,14 +590,22 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     const size_t row_bytes = (size_t)(Nx + 2 * s->xpad) * esz;
     const size_t smem_budget = (size_t)max_optin - 2048;
     s->xstages = (int)std::min<size_t>(4, (smem_budget - 256) / row_bytes);
+    if (s->emul) {
+        // two CTAs per SM: up to three rows in flight each
+        const size_t half = (size_t)max_optin / 2 - 2048;
+        const int st2 = (int)std::min<size_t>(3, (half - 256) / row_bytes);
+        if (st2 >= 2) s->xstages = st2;
+    }
     if (s->xstages < 1) return bail(fail(VLASOV_EINVAL, "a row of Nx=%d (+%d halo) does not fit shared memory", Nx, s->xpad));
     int occ = 0;
-    CTRY(xshift_occupancy(esz, s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    if (s->emul) CTRY(xshift_e_occupancy(s->xper, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    else CTRY(xshift_occupancy(esz, s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
     occ = std::max(occ, 1);
     s->xgrid = std::min(Np, s->nsm * occ);
 
     int pocc = 0;
-    CTRY(pshift_occupancy(esz, &pocc));
+    if (s->emul) CTRY(pshift_e_occupancy(&pocc));
+    else CTRY(pshift_occupancy(esz, &pocc));
     pocc = std::max(pocc, 1);
     const int ptiles = ((Nx + PS_TW - 1) / PS_TW) * ((Np + PS_TH - 1) / PS_TH);
     s->pgrid = std::min(ptiles, s->nsm * pocc);

@@ -203,6 +203,9 @@ cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUten
 cudaError_t set_kernel_attributes(int max_smem);
 cudaError_t set_kernel_attributes_e(int max_smem);
 int xshift_e_max_cols(int threads);
+size_t pshift_e_smem_bytes();
+cudaError_t xshift_e_occupancy(bool periodic, size_t smem, int* blocks);
+cudaError_t pshift_e_occupancy(int* blocks);
 cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                             cudaStream_t st);
 cudaError_t launch_pshift_e(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em,
