@@ -27,35 +27,51 @@ struct EmulElem {
 
 // Split x on the grid 2^(Ef-31).  s_base = 1044 + Ef.  |x| must be below 2^(Ef+1) (otherwise
 // `out_of_range` is set and the value is clamped to that); values below 2^(Ef-77) become zero.
+// 32-bit funnel shifts on the two halves of the mantissa; no 64-bit variable shifts.
 __device__ __forceinline__ EmulElem emul_split(double x, int s_base, bool& out_of_range)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(b >> 32);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
     const int e = (int)((hi >> 20) & 0x7FFu);
     int s = s_base - e;                             // value = m * 2^-s in grid units
     if (s < 22) {
         out_of_range = true;
         s = 22;
     }
-    EmulElem o;
-    if (e == 0 || s > 77) {
-        o.kx = 0;
-        o.r = 0.f;
-        return o;
-    }
-    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    const uint64_t k = s < 64 ? (m >> s) : 0ull;
-    const uint64_t rem = s < 64 ? (m - (k << s)) : m;     // < 2^s
-    const uint32_t top = s >= 24 ? (uint32_t)(rem >> (s - 24)) : (uint32_t)(rem << (24 - s));
-    float r = __uint2float_rn(top) * 5.9604644775390625e-08f;   // * 2^-24
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;   // mantissa m = mh:lo (53 bits)
+    // integer part k = m >> s (s >= 22, so k < 2^31)
+    uint32_t k;
+    if (s < 32) k = __funnelshift_r(lo, mh, s);
+    else k = s < 53 ? (mh >> (s - 32)) : 0u;
+    // 24 bits right below the binary point: (m >> (s - 24)) mod 2^24
+    const int a = s - 24;
+    uint32_t t;
+    if (a <= 0) t = lo << (-a);
+    else if (a < 32) t = __funnelshift_r(lo, mh, a);
+    else t = a < 53 ? (mh >> (a - 32)) : 0u;
+    t &= 0xFFFFFFu;
+    float r = __uint2float_rn(t) * 5.9604644775390625e-08f;   // * 2^-24
     int kx = (int)k;
+    if (e == 0 || s > 77) {
+        kx = 0;
+        r = 0.f;
+    }
     if (hi >> 31) {
         kx = -kx;
         r = -r;
     }
+    EmulElem o;
     o.kx = kx;
     o.r = r;
     return o;
+}
+
+// acc + a * b with one IMAD.WIDE (32 x 32 -> 64 multiply-add).
+__device__ __forceinline__ long long mad_wide(int a, int b, long long acc)
+{
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(acc));
+    return d;
 }
 
 // round(S) (ties away from zero) as int64 with integer instructions; |S| < 2^62.  (The hardware

@@ -36,7 +36,7 @@ __device__ __forceinline__ long long emul_fir(const EmulW& w, const int* kx, con
     float S = 0.f;
 #pragma unroll
     for (int t = 0; t < NTAP; ++t) {
-        M += (long long)w.Wh[t] * (long long)kx[t];
+        M = mad_wide(w.Wh[t], kx[t], M);
         S = fmaf(w.wl[t], kf[t], S);
         S = fmaf(w.wf[t], r[t], S);
     }
@@ -184,11 +184,19 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                 if constexpr (!PERIODIC) {
                     const int k = i + n0;
                     if (k < 0 || k + XE_V - 1 >= Nx - 1) {
-                        double xv[XE_W];
+                        // rare boundary chunk: recompute in FP64 from the staged (kx, r) values
 #pragma unroll
-                        for (int u = 0; u < XE_W; ++u) xv[u] = ((double)kx[u] + (double)rr[u]) * grid;
+                        for (int v = 0; v < XE_V; ++v) {
+                            double xv[NTAP];
+                            double acc = 0.0;
 #pragma unroll
-                        for (int v = 0; v < XE_V; ++v) out[v] = emul_edge(out[v], xv + v + A, k + v, Nx, g, d);
+                            for (int t = 0; t < NTAP; ++t) {
+                                const int2 p = src[e + A + v + t];
+                                xv[t] = ((double)p.x + (double)__int_as_float(p.y)) * grid;
+                                acc = fma(em.w64[(size_t)t * Np + r], xv[t], acc);
+                            }
+                            out[v] = emul_edge(acc, xv, k + v, Nx, g, d);
+                        }
                     }
                 }
                 double2* o = reinterpret_cast<double2*>(orow + i);
@@ -369,36 +377,47 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
             for (int tap = 0; tap < NTAP; ++tap) {
                 const int rw = u - tap;
                 if (rw >= 0 && rw < PS_RPT) {
-                    M[rw] += (long long)w.Wh[tap] * (long long)kx;
+                    M[rw] = mad_wide(w.Wh[tap], kx, M[rw]);
                     Sacc[rw] = fmaf(w.wl[tap], kf, Sacc[rw]);
                     Sacc[rw] = fmaf(w.wf[tap], rr, Sacc[rw]);
                 }
             }
         }
+        bool any_edge = false;
 #pragma unroll
         for (int rw = 0; rw < PS_RPT; ++rw) {
             const int j = jb + rw;
-            double out = emul_to_f64(M[rw] + f32_to_ll_round(Sacc[rw]), em.Ef);
+            const double out = emul_to_f64(M[rw] + f32_to_ll_round(Sacc[rw]), em.Ef);
+            bool edge = false;
             if constexpr (!PPER) {
                 const int kk = j + n0_i;
-                if (kk < 0 || kk >= Np - 1) {
-                    // rare: rebuild the ten inputs in FP64 for the boundary correction
+                edge = kk < 0 || kk >= Np - 1;
+            }
+            any_edge |= edge;
+            if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
+        }
+        if constexpr (!PPER) {
+            if (any_edge && colvalid) {
+                // rare boundary rows (f'' = 0 outside the grid): recompute in FP64
+                for (int rw = 0; rw < PS_RPT; ++rw) {
+                    const int j = jb + rw, kk = j + n0_i;
+                    if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
                     double xv[NTAP];
-#pragma unroll
+                    double acc = 0.0;
                     for (int u = 0; u < NTAP; ++u) {
                         double x;
                         if (t.smem_ok) {
                             const int2 v = sb[(base + rw + u) * PS_TW + lane];
                             x = ((double)v.x + (double)__int_as_float(v.y)) * grid;
                         } else {
-                            x = colvalid ? gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np) : 0.0;
+                            x = gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
                         }
                         xv[u] = x;
+                        acc = fma(em.w64[(size_t)u * Nx + i], x, acc);
                     }
-                    out = emul_edge(out, xv, kk, Np, g, d);
+                    fout[(size_t)j * Nx + i] = emul_edge(acc, xv, kk, Np, g, d);
                 }
             }
-            if (colvalid && j < Np) fout[(size_t)j * Nx + i] = out;
         }
         __syncthreads();   // every thread done with buffer b before it is refilled
     }

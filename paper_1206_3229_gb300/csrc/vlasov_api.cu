@@ -278,6 +278,7 @@ EmulArgs emargs(vlasov_sim* s, const LineParamsDev& p, const EmulParamsDev& e)
     a.wl = e.wl;
     a.wf = e.wf;
     a.gd = static_cast<const double*>(p.gd);
+    a.w64 = static_cast<const double*>(p.w);
     return a;
 }
 

@@ -103,6 +103,7 @@ struct EmulArgs {
     const float* wl;
     const float* wf;
     const double* gd;
+    const double* w64;    // the FP64 weights [10][n] (boundary rows are recomputed in FP64)
 };
 
 struct EmulParamsDev {
