@@ -167,9 +167,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=I.HMF_4096_UNSTABLE.name, choices=sorted(I.WORKLOADS))
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "fx64", "f32", "f64_native"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-f32", action="store_true", help="skip the secondary FP32 measurement")
+    ap.add_argument("--no-f32", action="store_true", help="skip the secondary measurements of the other storage modes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -263,26 +263,27 @@ def main():
            "note": "one job per timed region: vlasov_set_f from pinned host f0, K steps, moments and f back"}
     launches = sim.kernels_per_step() * args.steps
 
-    # ---- secondary: the FP32-storage path on the same workload
-    f32 = None
-    if not args.no_f32 and args.precision == "f64":
-        s32 = V.Sim.from_workload(w, precision="f32", stream=stream.cuda_stream)
-        s32.set_f(f0)
-        s32.step(args.warmup)
-        s32.sync()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        s32.step(args.steps)
-        a1.record(stream)
-        a1.synchronize()
-        ms32 = a0.elapsed_time(a1)
-        sl32 = s32.step_timed(4)
-        v32 = cells * args.steps / (ms32 * 1e-3)
-        f32 = {"value": world * v32, "ms_per_step": ms32 / args.steps,
-               "hbm_roofline_frac_step": 3 * 2.0 * cells * 4 / (ms32 / args.steps * 1e-3) / 1e9 / peak_gbs,
-               "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(s32.slot_names(), sl32)}}
-        s32.close()
+    # ---- secondary: the other storage modes on the same workload (same timing rules)
+    others = {}
+    if not args.no_f32:
+        for prec in [p for p in ("fx64", "f32", "f64") if p != args.precision]:
+            s2 = V.Sim.from_workload(w, precision=prec, stream=stream.cuda_stream)
+            s2.set_f(f0)
+            s2.step(args.warmup)
+            s2.sync()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            s2.step(args.steps)
+            a1.record(stream)
+            a1.synchronize()
+            ms2 = a0.elapsed_time(a1)
+            sl2 = s2.step_timed(4)
+            eb = 4 if prec == "f32" else 8
+            others[prec] = {"value": world * cells * args.steps / (ms2 * 1e-3), "ms_per_step": ms2 / args.steps,
+                            "hbm_roofline_frac_step": 3 * 2.0 * cells * eb / (ms2 / args.steps * 1e-3) / 1e9 / peak_gbs,
+                            "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(s2.slot_names(), sl2)}}
+            s2.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -306,7 +307,7 @@ def main():
                 "moments_last": {"t": float(hist[-1, 0]), "mass": float(hist[-1, 1]),
                                  "M": float(np.hypot(hist[-1, 2], hist[-1, 3])), "energy": float(hist[-1, 6])}
                 if len(hist) else None,
-                "f32": f32}
+                "other_precisions": others}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -46,8 +46,12 @@ enum { VLASOV_HMF = 0, VLASOV_RING = 1, VLASOV_SHEET = 2, VLASOV_FREE = 3 };
         bound 2^Ef >= 4 max|f| (Ef from the last upload), residuals in FP32; error per sweep about
         2^-49 of 2^Ef, the size of FP64 rounding noise.  Needs |f| < 2^(Ef+1) (else VLASOV_ERANGE).
    F32: float storage and interpolation; displacements and all moment sums stay FP64-accurate.
-   F64_NATIVE: double storage, IEEE FP64 filter arithmetic (reference; FP64-pipe bound). */
-enum { VLASOV_F64 = 0, VLASOV_F32 = 1, VLASOV_F64_NATIVE = 2 };
+   F64_NATIVE: double storage, IEEE FP64 filter arithmetic (reference; FP64-pipe bound).
+   FX64: 64-bit fixed-point storage, f = X * 2^(Ef-62) with X int64 (same 8 bytes per cell; absolute
+        resolution 2^-60 of max|f|, finer than FP64 for every |f| above 2^-7 of max|f|), and the
+        F64 filter arithmetic without the IEEE decode/encode.  The API still takes and returns
+        doubles.  Needs |f| < 2^Ef (else VLASOV_ERANGE). */
+enum { VLASOV_F64 = 0, VLASOV_F32 = 1, VLASOV_F64_NATIVE = 2, VLASOV_FX64 = 3 };
 
 typedef struct vlasov_sim vlasov_sim; /* opaque; owns every device buffer it uses */
 
@@ -58,7 +62,7 @@ typedef struct {
     int p_periodic;      /* same for p */
     double eps;          /* ring softening of Eq. (ringpot), > 0 for VLASOV_RING */
     double G;            /* sheet coupling: V(x) = 2 pi G |x| */
-    int precision;       /* VLASOV_F64, VLASOV_F32 or VLASOV_F64_NATIVE */
+    int precision;       /* VLASOV_F64, VLASOV_F32, VLASOV_F64_NATIVE or VLASOV_FX64 */
     void* stream;        /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
 } vlasov_domain;
 

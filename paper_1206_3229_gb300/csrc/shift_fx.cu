@@ -1,0 +1,508 @@
+// shift_fx.cu -- the two sweeps for 64-bit fixed-point storage (VLASOV_FX64).
+//
+// f is stored as X = round(f * 2^(62-Ef)) in int64 (|f| < 2^Ef, Ef = a bound four times the largest
+// uploaded |f|): the same 8 bytes per cell as FP64, an absolute resolution of 2^-60 of max|f|, and no
+// IEEE decoding.  Each staged element splits with two integer instructions into
+//   X = kx * 2^31 + rem,  kx = X >> 31 (int32), rem in [0, 2^31)
+// and the filter runs exactly as in the emulated-FP64 sweeps (emul.cuh): 10 IMAD.WIDE on kx, 20
+// FFMA on (float)kx and (float)rem; the int64 result T (units 2^(Ef-61)) is stored as 2T.  Data
+// movement is that of shift_kernels.cu: whole rows by 1-D bulk copies (x-shift), 2-D TMA column
+// tiles with zero fill (p-shift).
+#include "emul.cuh"
+#include "fixed_point.cuh"
+#include "ptx.cuh"
+#include "shift_common.cuh"
+#include "vlasov_internal.cuh"
+
+namespace vl {
+
+namespace {
+
+constexpr int XF_V = 4;       // consecutive outputs per thread and chunk
+constexpr int XF_W = 14;      // window elements: V + 9 + alignment slack (even)
+constexpr int XF_MAXCH = 4;   // chunks per row per thread (Nx <= 4096)
+constexpr int PSF_RB = 192;   // staged rows per p-shift buffer (two CTAs per SM)
+
+struct FxW {
+    int Wh[NTAP];
+    float wl[NTAP];
+    float wr[NTAP];   // w * 2^30 * 2^-31: multiplies (float)rem directly
+};
+
+__device__ __forceinline__ void fx_split(long long X, int& kx, float& kf, float& rf)
+{
+    const uint32_t lo = (uint32_t)X, hi = (uint32_t)((unsigned long long)X >> 32);
+    kx = (int)__funnelshift_r(lo, hi, 31);
+    kf = __int2float_rn(kx);
+    rf = __uint2float_rn(lo & 0x7FFFFFFFu);
+}
+
+__device__ __forceinline__ long long fx_fir(const FxW& w, const int* kx, const float* kf, const float* rf)
+{
+    long long M = 0;
+    float S = 0.f;
+#pragma unroll
+    for (int t = 0; t < NTAP; ++t) {
+        M = mad_wide(w.Wh[t], kx[t], M);
+        S = fmaf(w.wl[t], kf[t], S);
+        S = fmaf(w.wr[t], rf[t], S);
+    }
+    return M + f32_to_ll_round(S);
+}
+
+// Stored value of a filter result T (units 2^(Ef-61)); flags results outside |f| < 2^Ef.
+__device__ __forceinline__ long long fx_store(long long T, bool& bad)
+{
+    const unsigned long long u = (unsigned long long)(T + (1ll << 61));
+    if (u >> 62) bad = true;
+    return T * 2;
+}
+
+// The rare boundary outputs of non-periodic axes, recomputed in FP64 from the fixed values.
+__device__ __forceinline__ long long fx_edge(const long long* X, const double* w64, size_t wstride, int k, int n,
+                                             double g, double d, double unit, int Ef)
+{
+    double xv[NTAP];
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < NTAP; ++t) {
+        xv[t] = (double)X[t] * unit;
+        acc = fma(w64[(size_t)t * wstride], xv[t], acc);
+    }
+    const double out = edge_fix(acc, xv, k, n, g, d);
+    return (long long)fx128_from_f64(out, 62 - Ef);
+}
+
+}  // namespace
+
+// ============================================================================ x-shift (FX64)
+template <bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs a, EmulArgs em)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
+    __shared__ double red[32];
+
+    const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
+    long long* __restrict__ fout = static_cast<long long*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
+    const int stride = Nx + 2 * PAD;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int G = gridDim.x;
+    const uint32_t row_bytes = (uint32_t)(Nx * 8);
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u);
+    const double unit = ldexp(1.0, em.Ef - 62);
+    bool bad = false;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    if constexpr (!PERIODIC) {
+        for (int s = 0; s < S; ++s) {
+            long long* b = bufs + (size_t)s * stride;
+            for (int e = tid; e < PAD; e += nthreads) {
+                b[e] = 0;
+                b[PAD + Nx + e] = 0;
+            }
+        }
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int r) {
+        long long* dst = bufs + (size_t)s * stride + PAD;
+        const long long* src = fin + (size_t)r * Nx;
+        mbar_arrive_expect_tx(&bars[s], tx_bytes);
+        bulk_g2s(dst, src, row_bytes, &bars[s]);
+        if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            const int r = blockIdx.x + s * G;
+            if (r < Np) issue(s, r);
+        }
+    }
+
+    long long colacc[XF_MAXCH][XF_V];
+#pragma unroll
+    for (int c = 0; c < XF_MAXCH; ++c)
+#pragma unroll
+        for (int v = 0; v < XF_V; ++v) colacc[c][v] = 0;
+    double kin = 0.0;
+
+    int it = 0;
+    int r = blockIdx.x;
+    bool failed = false;
+    for (; r < Np; r += G, ++it) {
+        const int s = it % S;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / S) & 1), WAIT_LIMIT_NS);
+        long long rowsum = 0;
+        if (ok) {
+            const long long* rowbuf = bufs + (size_t)s * stride + PAD;
+            const int n0 = em.n0[r];
+            FxW w;
+#pragma unroll
+            for (int t = 0; t < NTAP; ++t) {
+                w.Wh[t] = em.Wh[(size_t)t * Np + r];
+                w.wl[t] = em.wl[(size_t)t * Np + r];
+                w.wr[t] = em.wf[(size_t)t * Np + r] * 4.656612873077393e-10f;   // * 2^-31
+            }
+            const int A = (n0 - 4) & 1;
+            int base;
+            if constexpr (PERIODIC) {
+                base = (n0 - 4 - A) % Nx;
+                if (base < 0) base += Nx;
+            } else {
+                base = n0 - 4 - A;
+            }
+            long long* orow = fout + (size_t)r * Nx;
+#pragma unroll
+            for (int c = 0; c < XF_MAXCH; ++c) {
+                const int i = XF_V * (tid + c * nthreads);
+                if (i < Nx) {
+                    int e = i + base;
+                    if constexpr (PERIODIC) {
+                        if (e >= Nx) e -= Nx;
+                    }
+                    int kx[XF_W];
+                    float kf[XF_W], rf[XF_W];
+                    const longlong2* q = reinterpret_cast<const longlong2*>(rowbuf + e);
+#pragma unroll
+                    for (int u = 0; u < XF_W / 2; ++u) {
+                        const longlong2 v = q[u];
+                        fx_split(v.x, kx[2 * u], kf[2 * u], rf[2 * u]);
+                        fx_split(v.y, kx[2 * u + 1], kf[2 * u + 1], rf[2 * u + 1]);
+                    }
+                    long long out[XF_V];
+#pragma unroll
+                    for (int v = 0; v < XF_V; ++v) {
+                        const long long T = A == 0 ? fx_fir(w, kx + v, kf + v, rf + v) : fx_fir(w, kx + v + 1, kf + v + 1, rf + v + 1);
+                        out[v] = fx_store(T, bad);
+                    }
+                    if constexpr (!PERIODIC) {
+                        const int k = i + n0;
+                        if (k < 0 || k + XF_V - 1 >= Nx - 1) {
+                            const double g = em.gd[r], d = em.gd[Np + r];
+#pragma unroll
+                            for (int v = 0; v < XF_V; ++v)
+                                out[v] = fx_edge(rowbuf + e + A + v, em.w64 + r, Np, k + v, Nx, g, d, unit, em.Ef);
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < XF_V; ++v) {
+                        const long long Tc = (out[v] + 1024) >> 11;   // units 2^(Ef-51)
+                        colacc[c][v] += Tc;
+                        rowsum += Tc;
+                    }
+                    longlong2* o = reinterpret_cast<longlong2*>(orow + i);
+                    o[0] = make_longlong2(out[0], out[1]);
+                    o[1] = make_longlong2(out[2], out[3]);
+                }
+            }
+            if constexpr (KIN) {
+                const double pj = a.pmin + (double)r * a.dp;
+                kin = fma(0.5 * pj * pj, fx128_to_f64((i128)rowsum, 51 - em.Ef), kin);
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            const int rn = r + S * G;
+            if (rn < Np) {
+                fence_proxy_async_smem();
+                issue(s, rn);
+            }
+        }
+    }
+    if (bad) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+
+    if (failed) {
+        if (tid == 0) {
+            atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
+            for (int k = 0; k < S; ++k) {
+                const int rr = r + k * G;
+                if (rr >= Np) break;
+                const int itk = it + k;
+                mbar_wait_bounded(&bars[itk % S], (uint32_t)((itk / S) & 1), WAIT_LIMIT_NS);
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    if (a.colpart) {
+        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < XF_MAXCH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) cp[i + v] = fx128_to_f64((i128)colacc[c][v], 51 - em.Ef);
+            }
+        }
+    }
+    if constexpr (KIN) {
+        double v = kin;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < (nthreads + 31) / 32; ++q) sum += red[q];
+            a.kinpart[blockIdx.x] = sum;
+        }
+    }
+}
+
+// ============================================================================ p-shift (FX64)
+template <bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                     PShiftArgs a, EmulArgs em)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
+    constexpr int BUF = PSF_RB * PS_TW;
+
+    const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
+    long long* __restrict__ fout = static_cast<long long*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np;
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+    const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PS_TH - 1) / PS_TH;
+    const int ntiles = ntx * nty;
+    const int G = gridDim.x;
+    const double unit = ldexp(1.0, em.Ef - 62);
+    bool bad = false;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+        prefetch_tensormap(&tmap);
+    }
+    __syncthreads();
+
+    auto issue = [&](int b, const TileWin& t) {
+        if (t.smem_ok) {
+            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * 8));
+            for (int q = 0; q < t.nb; ++q)
+                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, &tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
+        } else {
+            mbar_arrive_expect_tx(&bars[b], 0u);
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (grp == 0 && tile < ntiles) {
+        int n0l;
+        bool cv;
+        TileWin t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
+        if (lane == 0) issue(0, t);
+    }
+
+    int q = 0;
+    bool failed = false;
+    for (; tile < ntiles; tile += G, ++q) {
+        const int b = q & 1;
+        const int nt = tile + G;
+        if (grp == 0 && nt < ntiles) {
+            int n0l;
+            bool cv;
+            TileWin tn = tile_window<PPER, PSF_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(b ^ 1, tn);
+            }
+        }
+        int n0_i;
+        bool colvalid;
+        const TileWin t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
+        const int i = t.i0 + lane;
+        FxW w;
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) {
+            w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + i] : 0;
+            w.wl[k] = colvalid ? em.wl[(size_t)k * Nx + i] : 0.f;
+            w.wr[k] = colvalid ? em.wf[(size_t)k * Nx + i] * 4.656612873077393e-10f : 0.f;
+        }
+        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
+        if (ok) {
+            const long long* buf = bufs + (size_t)b * BUF;
+            const int jb = t.j0 + grp * PS_RPT;
+            const int base = jb + n0_i - 4 - t.r0;
+            long long M[PS_RPT];
+            float Sacc[PS_RPT];
+#pragma unroll
+            for (int rw = 0; rw < PS_RPT; ++rw) {
+                M[rw] = 0;
+                Sacc[rw] = 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u) {
+                long long X;
+                if (t.smem_ok) X = buf[(base + u) * PS_TW + lane];
+                else X = colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll;
+                int kx;
+                float kf, rf;
+                fx_split(X, kx, kf, rf);
+#pragma unroll
+                for (int tap = 0; tap < NTAP; ++tap) {
+                    const int rw = u - tap;
+                    if (rw >= 0 && rw < PS_RPT) {
+                        M[rw] = mad_wide(w.Wh[tap], kx, M[rw]);
+                        Sacc[rw] = fmaf(w.wl[tap], kf, Sacc[rw]);
+                        Sacc[rw] = fmaf(w.wr[tap], rf, Sacc[rw]);
+                    }
+                }
+            }
+            bool any_edge = false;
+#pragma unroll
+            for (int rw = 0; rw < PS_RPT; ++rw) {
+                const int j = jb + rw;
+                const long long out = fx_store(M[rw] + f32_to_ll_round(Sacc[rw]), bad);
+                bool edge = false;
+                if constexpr (!PPER) {
+                    const int kk = j + n0_i;
+                    edge = kk < 0 || kk >= Np - 1;
+                }
+                any_edge |= edge;
+                if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
+            }
+            if constexpr (!PPER) {
+                if (any_edge && colvalid) {
+                    const double g = em.gd[i], d = em.gd[Nx + i];
+                    for (int rw = 0; rw < PS_RPT; ++rw) {
+                        const int j = jb + rw, kk = j + n0_i;
+                        if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
+                        long long X[NTAP];
+                        for (int u = 0; u < NTAP; ++u)
+                            X[u] = t.smem_ok ? buf[(base + rw + u) * PS_TW + lane]
+                                             : gload_p<long long, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                        fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
+                    }
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) {   // also: every thread done with buffer b before it is refilled
+            failed = true;
+            break;
+        }
+    }
+    if (bad) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    if (failed && tid == 0) {
+        atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+        if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
+        mbar_wait_bounded(&bars[q & 1], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
+    }
+}
+
+size_t pshift_fx_smem_bytes() { return 256 + 2 * (size_t)PSF_RB * PS_TW * 8; }
+
+cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
+                             cudaStream_t st)
+{
+    const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, 8);
+    if (periodic) {
+        if (kin) xshift_fx_kernel<true, true><<<grid, threads, smem, st>>>(a, em);
+        else xshift_fx_kernel<true, false><<<grid, threads, smem, st>>>(a, em);
+    } else {
+        if (kin) xshift_fx_kernel<false, true><<<grid, threads, smem, st>>>(a, em);
+        else xshift_fx_kernel<false, false><<<grid, threads, smem, st>>>(a, em);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
+                             const EmulArgs& em, cudaStream_t st)
+{
+    const size_t smem = pshift_fx_smem_bytes();
+    if (p_periodic) pshift_fx_kernel<true><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
+    else pshift_fx_kernel<false><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
+    return cudaGetLastError();
+}
+
+cudaError_t set_kernel_attributes_fx(int max_smem)
+{
+    cudaError_t e = cudaSuccess;
+#define VL_ATTR(fn) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)
+    VL_ATTR((xshift_fx_kernel<true, true>));
+    VL_ATTR((xshift_fx_kernel<true, false>));
+    VL_ATTR((xshift_fx_kernel<false, true>));
+    VL_ATTR((xshift_fx_kernel<false, false>));
+    VL_ATTR((pshift_fx_kernel<true>));
+    VL_ATTR((pshift_fx_kernel<false>));
+#undef VL_ATTR
+    return e;
+}
+
+cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks)
+{
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_fx_kernel<true, true>, XS_THREADS_MIN, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_fx_kernel<false, true>, XS_THREADS_MIN, smem);
+}
+
+cudaError_t pshift_fx_occupancy(int* blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_fx_kernel<false>, PS_TW * PS_RG,
+                                                         pshift_fx_smem_bytes());
+}
+
+// ============================================================================ conversions, column sums
+__global__ void f64_to_fx_kernel(const double* __restrict__ s, long long* __restrict__ d, size_t n, int k)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        d[q] = (long long)fx128_from_f64(s[q], k);
+}
+
+__global__ void fx_to_f64_kernel(const long long* __restrict__ s, double* __restrict__ d, size_t n, int k)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        d[q] = fx128_to_f64((i128)s[q], k);
+}
+
+cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st)
+{
+    f64_to_fx_kernel<<<1024, 256, 0, st>>>(s, d, n, 62 - Ef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cudaStream_t st)
+{
+    fx_to_f64_kernel<<<1024, 256, 0, st>>>(s, d, n, 62 - Ef);
+    return cudaGetLastError();
+}
+
+// Column sums of a fixed-point f into one partial row (density test hook): exact in int64 at
+// 2^-11 of the storage resolution.
+__global__ void __launch_bounds__(256) colsum_fx_kernel(const long long* __restrict__ f, int Nx, int Np, int Ef,
+                                                        double* colpart)
+{
+    __shared__ long long sh[8][32];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    long long s = 0;
+    if (i < Nx)
+        for (int j = grp; j < Np; j += 8) s += (f[(size_t)j * Nx + i] + 1024) >> 11;
+    sh[grp][lane] = s;
+    __syncthreads();
+    if (grp == 0 && i < Nx) {
+        long long t = 0;
+        for (int q = 0; q < 8; ++q) t += sh[q][lane];
+        colpart[i] = fx128_to_f64((i128)t, 51 - Ef);
+    }
+}
+
+cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double* colpart, cudaStream_t st)
+{
+    colsum_fx_kernel<<<(Nx + 31) / 32, 256, 0, st>>>(f, Nx, Np, Ef, colpart);
+    return cudaGetLastError();
+}
+
+}  // namespace vl

@@ -16,6 +16,7 @@
 
 #include "../../include/vlasov.h"
 #include "emul.cuh"
+#include "fixed_point.cuh"
 #include "vlasov_internal.cuh"
 
 using namespace vl;
@@ -72,6 +73,7 @@ struct vlasov_sim {
     bool has_f = false;
 
     bool emul = false;          // FP64 storage, integer/FP32 filter arithmetic (emul.cuh)
+    bool fx = false;            // 64-bit fixed-point storage, same filter arithmetic (shift_fx.cu)
     LineParamsDev xp, pp, sp;   // x rows (fixed), p columns (per step), scratch for substeps
     EmulParamsDev xe, pe, se;   // their emulated-FP64 splits
     int xthreads = 256, xstages = 1, xpad = 16, xgrid = 1, pgrid = 1, crgrid = 1;
@@ -159,7 +161,7 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
     }
     if (max_abs_n0) *max_abs_n0 = mx;
     CU_TRY(cudaMemcpyAsync(p.n0, n0.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s->st));
-    if (s->emul && e) {
+    if ((s->emul || s->fx) && e) {
         std::vector<int> Wh(w.size());
         std::vector<float> wl(w.size()), wf(w.size());
         for (size_t q = 0; q < w.size(); ++q) emul_weight(w[q], Wh[q], wl[q], wf[q]);
@@ -189,7 +191,9 @@ int make_tmap(vlasov_sim* s, int b)
     cuuint64_t strides[1] = {(cuuint64_t)s->Nx * (cuuint64_t)s->esz};
     cuuint32_t box[2] = {(cuuint32_t)PS_TW, (cuuint32_t)PS_BH};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&s->tmap[b], s->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+    const CUtensorMapDataType dt = s->fx ? CU_TENSOR_MAP_DATA_TYPE_INT64
+                                         : (s->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+    CUresult r = enc(&s->tmap[b], dt, 2,
                      s->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -284,6 +288,7 @@ EmulArgs emargs(vlasov_sim* s, const LineParamsDev& p, const EmulParamsDev& e)
 
 cudaError_t run_xshift(vlasov_sim* s, const XShiftArgs& a, const LineParamsDev& p, const EmulParamsDev& e, bool kin)
 {
+    if (s->fx) return launch_xshift_fx(s->xper, kin, s->xgrid, s->xthreads, a, emargs(s, p, e), s->st);
     if (s->emul) return launch_xshift_e(s->xper, kin, s->xgrid, s->xthreads, a, emargs(s, p, e), s->st);
     return launch_xshift(s->esz, s->xper, kin, s->xgrid, s->xthreads, a, s->st);
 }
@@ -291,6 +296,7 @@ cudaError_t run_xshift(vlasov_sim* s, const XShiftArgs& a, const LineParamsDev& 
 cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs& a, const LineParamsDev& p,
                        const EmulParamsDev& e)
 {
+    if (s->fx) return launch_pshift_fx(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
     if (s->emul) return launch_pshift_e(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
     return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, s->st);
 }
@@ -360,9 +366,9 @@ int launch_pparams_only(vlasov_sim* s, double* Fout)
     a.w = s->pp.w;
     a.gd = s->pp.gd;
     a.Fout = Fout;
-    a.Wh = s->emul ? s->pe.Wh : nullptr;
-    a.wl = s->emul ? s->pe.wl : nullptr;
-    a.wf = s->emul ? s->pe.wf : nullptr;
+    a.Wh = (s->emul || s->fx) ? s->pe.Wh : nullptr;
+    a.wl = (s->emul || s->fx) ? s->pe.wl : nullptr;
+    a.wf = (s->emul || s->fx) ? s->pe.wf : nullptr;
     CU_TRY(launch_pparams(s->esz, a, s->st));
     return VLASOV_OK;
 }
@@ -499,7 +505,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     *out = nullptr;
     if (!d) return fail(VLASOV_EINVAL, "domain is NULL");
     if (model < VLASOV_HMF || model > VLASOV_FREE) return fail(VLASOV_EINVAL, "unknown model %d", model);
-    if (d->precision != VLASOV_F64 && d->precision != VLASOV_F32 && d->precision != VLASOV_F64_NATIVE)
+    if (d->precision != VLASOV_F64 && d->precision != VLASOV_F32 && d->precision != VLASOV_F64_NATIVE &&
+        d->precision != VLASOV_FX64)
         return fail(VLASOV_EINVAL, "unknown precision %d", d->precision);
     const int esz = d->precision == VLASOV_F32 ? 4 : 8;
     if (Nx < 16 || Np < 16 || Nx % ALIGN_N || Np % ALIGN_N)
@@ -517,6 +524,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     s->prec = d->precision;
     s->esz = esz;
     s->emul = d->precision == VLASOV_F64;
+    s->fx = d->precision == VLASOV_FX64;
     s->xper = d->x_periodic != 0;
     s->pper = d->p_periodic != 0;
     s->xmin = d->xmin;
@@ -558,6 +566,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     }
     CTRY(set_kernel_attributes(max_optin - 1024));
     CTRY(set_kernel_attributes_e(max_optin - 1024));
+    CTRY(set_kernel_attributes_fx(max_optin - 1024));
 
     const size_t cells = (size_t)Nx * (size_t)Np;
     for (int b = 0; b < 2; ++b) {
@@ -577,7 +586,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     TRY(alloc_params(s->xp, Np, esz));
     TRY(alloc_params(s->pp, Nx, esz));
     TRY(alloc_params(s->sp, std::max(Nx, Np), esz));
-    if (s->emul) {
+    if (s->emul || s->fx) {
         TRY(alloc_emul(s->xe, Np));
         TRY(alloc_emul(s->pe, Nx));
         TRY(alloc_emul(s->se, std::max(Nx, Np)));
@@ -591,7 +600,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     const size_t row_bytes = (size_t)(Nx + 2 * s->xpad) * esz;
     const size_t smem_budget = (size_t)max_optin - 2048;
     s->xstages = (int)std::min<size_t>(4, (smem_budget - 256) / row_bytes);
-    if (s->emul) {
+    if (s->emul || s->fx) {
         // two CTAs per SM: up to three rows in flight each
         const size_t half = (size_t)max_optin / 2 - 2048;
         const int st2 = (int)std::min<size_t>(3, (half - 256) / row_bytes);
@@ -599,13 +608,15 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     }
     if (s->xstages < 1) return bail(fail(VLASOV_EINVAL, "a row of Nx=%d (+%d halo) does not fit shared memory", Nx, s->xpad));
     int occ = 0;
-    if (s->emul) CTRY(xshift_e_occupancy(s->xper, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    if (s->fx) CTRY(xshift_fx_occupancy(s->xper, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    else if (s->emul) CTRY(xshift_e_occupancy(s->xper, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
     else CTRY(xshift_occupancy(esz, s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
     occ = std::max(occ, 1);
     s->xgrid = std::min(Np, s->nsm * occ);
 
     int pocc = 0;
-    if (s->emul) CTRY(pshift_e_occupancy(&pocc));
+    if (s->fx) CTRY(pshift_fx_occupancy(&pocc));
+    else if (s->emul) CTRY(pshift_e_occupancy(&pocc));
     else CTRY(pshift_occupancy(esz, &pocc));
     pocc = std::max(pocc, 1);
     const int ptiles = ((Nx + PS_TW - 1) / PS_TW) * ((Np + PS_TH - 1) / PS_TH);
@@ -690,7 +701,12 @@ int vlasov_set_f(vlasov_sim* s, const double* host_f)
     for (size_t k = 0; k < cells; ++k) mx = std::max(mx, std::fabs(host_f[k]));
     if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
     update_scales(s, mx);
-    if (s->esz == 8) {
+    if (s->fx) {
+        std::vector<long long> tmp(cells);
+        for (size_t k = 0; k < cells; ++k) tmp[k] = (long long)fx128_from_f64(host_f[k], 62 - s->Ef);
+        CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 8, cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    } else if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(s->f[s->cur], host_f, cells * 8, cudaMemcpyHostToDevice, s->st));
     } else {
         std::vector<float> tmp(cells);
@@ -708,7 +724,6 @@ int vlasov_set_f_device(vlasov_sim* s, const double* dev_f)
 {
     if (!s || !dev_f) return fail(VLASOV_EINVAL, "NULL argument");
     const size_t cells = (size_t)s->Nx * s->Np;
-    CU_TRY(launch_convert(dev_f, 8, s->f[s->cur], s->esz, cells, s->st));
     CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
     unsigned long long bits = 0;
     CU_TRY(launch_maxabs(8, dev_f, cells, s->maxbits, s->st));
@@ -718,6 +733,8 @@ int vlasov_set_f_device(vlasov_sim* s, const double* dev_f)
     std::memcpy(&mx, &bits, sizeof mx);
     if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
     update_scales(s, mx);
+    if (s->fx) CU_TRY(launch_f64_to_fx(dev_f, static_cast<long long*>(s->f[s->cur]), cells, s->Ef, s->st));
+    else CU_TRY(launch_convert(dev_f, 8, s->f[s->cur], s->esz, cells, s->st));
     s->read_step = 0;
     s->has_f = true;
     return VLASOV_OK;
@@ -727,7 +744,12 @@ int vlasov_get_f(vlasov_sim* s, double* host_f)
 {
     if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");
     const size_t cells = (size_t)s->Nx * s->Np;
-    if (s->esz == 8) {
+    if (s->fx) {
+        std::vector<long long> tmp(cells);
+        CU_TRY(cudaMemcpyAsync(tmp.data(), s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+        for (size_t k = 0; k < cells; ++k) host_f[k] = fx128_to_f64((i128)tmp[k], 62 - s->Ef);
+    } else if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(host_f, s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
     } else {
@@ -743,7 +765,8 @@ int vlasov_get_f_device(vlasov_sim* s, double* dev_f)
 {
     if (!s || !dev_f) return fail(VLASOV_EINVAL, "NULL argument");
     const size_t cells = (size_t)s->Nx * s->Np;
-    CU_TRY(launch_convert(s->f[s->cur], s->esz, dev_f, 8, cells, s->st));
+    if (s->fx) CU_TRY(launch_fx_to_f64(static_cast<const long long*>(s->f[s->cur]), dev_f, cells, s->Ef, s->st));
+    else CU_TRY(launch_convert(s->f[s->cur], s->esz, dev_f, 8, cells, s->st));
     return VLASOV_OK;
 }
 
@@ -827,7 +850,8 @@ int vlasov_density_force(vlasov_sim* s, double* host_rho, double* host_F)
 {
     if (!s) return fail(VLASOV_EINVAL, "NULL handle");
     if (!s->has_f) return fail(VLASOV_ESTATE, "density before vlasov_set_f");
-    CU_TRY(launch_colsum(s->esz, s->f[s->cur], s->Nx, s->Np, s->colpart, 1, s->st));
+    if (s->fx) CU_TRY(launch_colsum_fx(static_cast<const long long*>(s->f[s->cur]), s->Nx, s->Np, s->Ef, s->colpart, s->st));
+    else CU_TRY(launch_colsum(s->esz, s->f[s->cur], s->Nx, s->Np, s->colpart, 1, s->st));
     CU_TRY(launch_colreduce(crargs(s, 1, false, false), s->crgrid, s->st));
     int rc = launch_force_params(s, s->Fout);
     if (rc) return rc;

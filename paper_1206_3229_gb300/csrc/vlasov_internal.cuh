@@ -214,6 +214,18 @@ cudaError_t launch_pshift_e(bool p_periodic, int grid, const CUtensorMap* tmap, 
 cudaError_t xshift_occupancy(int elem_bytes, bool periodic, int threads, size_t smem, int* blocks);
 cudaError_t pshift_occupancy(int elem_bytes, int* blocks);
 
+cudaError_t set_kernel_attributes_fx(int max_smem);
+size_t pshift_fx_smem_bytes();
+cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks);
+cudaError_t pshift_fx_occupancy(int* blocks);
+cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
+                             cudaStream_t st);
+cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
+                             const EmulArgs& em, cudaStream_t st);
+cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st);
+cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cudaStream_t st);
+cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double* colpart, cudaStream_t st);
+
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);

@@ -17,8 +17,9 @@ from paper_1206_3229_gb300 import vlasov as V
 
 pytestmark = pytest.mark.gpu
 
-TOL_SWEEP = {"f64": 2e-14, "f64_native": 1e-13, "f32": 2e-6}
-PRECS = ["f64", "f64_native", "f32"]
+TOL_SWEEP = {"f64": 2e-14, "fx64": 2e-14, "f64_native": 1e-13, "f32": 2e-6}
+PRECS = ["f64", "fx64", "f64_native", "f32"]
+FP64_MODES = ["f64", "fx64", "f64_native"]
 
 
 def grid_of(w: I.Workload) -> O.Grid:
@@ -87,7 +88,7 @@ def test_p_sweep_matches_oracle(prec, name, nx, np_, xper, pper):
         assert np.max(np.abs(got - want)) <= TOL_SWEEP[prec] * scale, name
 
 
-@pytest.mark.parametrize("prec", ["f64", "f64_native"])
+@pytest.mark.parametrize("prec", FP64_MODES)
 def test_integer_free_streaming_is_exact_on_gpu(prec):
     """F = 0 and dp (dt/2)/dx = 1: three steps move row j by 6 (j - np/2) cells exactly."""
     nx, npp = 64, 32
@@ -112,7 +113,7 @@ FORCE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f64_native"])
+@pytest.mark.parametrize("prec", FP64_MODES)
 @pytest.mark.parametrize("w", FORCE_CASES, ids=lambda w: w.model)
 def test_density_and_force_match_oracle(w, prec):
     f = I.initial_state(w)
@@ -127,7 +128,7 @@ def test_density_and_force_match_oracle(w, prec):
 
 
 # ------------------------------------------------------------------------------------- full steps
-@pytest.mark.parametrize("prec", ["f64", "f64_native"])
+@pytest.mark.parametrize("prec", FP64_MODES)
 def test_hmf_256_fp64_200_steps_matches_oracle(prec):
     """The 256^2 HMF waterbag in FP64: max|df| <= 1e-12 max f after 200 steps; moments per step."""
     w = I.HMF_256
@@ -150,7 +151,7 @@ def test_hmf_256_fp64_200_steps_matches_oracle(prec):
     (I.SHEET_4096.resized(128, 256), 40),
     (I.HMF_4096_UNSTABLE.resized(128, 256), 40),
 ], ids=["ring", "sheet", "hmf_mode"])
-@pytest.mark.parametrize("prec", ["f64", "f64_native"])
+@pytest.mark.parametrize("prec", FP64_MODES)
 def test_models_fp64_steps_match_oracle(w, steps, prec):
     f0 = I.initial_state(w)
     fo, mo = O.run(grid_of(w), f0, steps)
