@@ -70,10 +70,21 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int i = blockIdx.x * CR_COLS + lane;
 
+    // all loads of a thread are independent: issue them in batches of eight
     long long s = 0;
-    if (i < a.Nx)
-        for (int b = grp; b < a.B; b += CR_GROUPS)
-            s += (long long)fx128_from_f64(a.colpart[(size_t)b * a.Nx + i], a.k_col);
+    if (i < a.Nx) {
+        const double* __restrict__ cp = a.colpart + i;
+        const size_t st = (size_t)a.Nx * CR_GROUPS;
+        int b = grp;
+        for (; b + 7 * CR_GROUPS < a.B; b += 8 * CR_GROUPS) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(cp + (size_t)b * a.Nx + u * st);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += (long long)fx128_from_f64(v[u], a.k_col);
+        }
+        for (; b < a.B; b += CR_GROUPS) s += (long long)fx128_from_f64(__ldcs(cp + (size_t)b * a.Nx), a.k_col);
+    }
     shc[grp][lane] = s;
     __syncthreads();
     i128 cm = 0, cx = 0, cy = 0;
@@ -112,8 +123,17 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
         x += vb[b * 3 + 1];
         y += vb[b * 3 + 2];
     }
-    if (a.kinpart)
-        for (int b = threadIdx.x; b < a.B; b += blockDim.x) k += fx128_from_f64(__ldcg(&a.kinpart[b]), a.k_kin);
+    if (a.kinpart) {
+        double kv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = threadIdx.x + u * blockDim.x;
+            kv[u] = b < a.B ? __ldcg(&a.kinpart[b]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k += fx128_from_f64(kv[u], a.k_kin);
+        for (int b = threadIdx.x + 4 * blockDim.x; b < a.B; b += blockDim.x) k += fx128_from_f64(__ldcg(&a.kinpart[b]), a.k_kin);
+    }
     m = block_sum_i128(m, red);
     x = block_sum_i128(x, red);
     y = block_sum_i128(y, red);

@@ -147,7 +147,7 @@ extern "C" int vlasov_xshift_density_noalloc(const double* dev_fin, double* dev_
     a.Nx = Nx;
     a.Np = Np;
     a.pad = pad;
-    const size_t row_bytes = (size_t)(Nx + 2 * a.pad) * sizeof(double);
+    const size_t row_bytes = (size_t)(Nx + 2 * a.pad) * sizeof(double) + XREC_BYTES;
     a.stages = (int)std::min<size_t>(4, ((size_t)optin - 2048 - 256) / row_bytes);
     a.n0 = n0;
     a.w = w;

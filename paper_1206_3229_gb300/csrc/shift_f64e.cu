@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     double* bufs = reinterpret_cast<double*>(smem_raw + 128);
     __shared__ double red[32];
+    unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)a.stages * (a.Nx + 2 * a.pad));
 
     const double* __restrict__ fin = static_cast<const double*>(a.fin);
     double* __restrict__ fout = static_cast<double*>(a.fout);
@@ -72,7 +73,8 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int G = gridDim.x;
     const uint32_t row_bytes = (uint32_t)(Nx * 8);
-    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u);
+    const bool use_rec = a.rec != nullptr;
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + (use_rec ? XREC_BYTES : 0u);
     const int s_base = 1044 + em.Ef;
     const double grid = ldexp(1.0, em.Ef - 31);
     bool bad = false;
@@ -98,6 +100,9 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
         if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
+        if (use_rec)
+            bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+                     XREC_BYTES, &bars[s]);
     };
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -125,18 +130,19 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
             failed = true;
             break;
         }
-        const int n0 = em.n0[r];
+        const XRec* rc = use_rec ? reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES) : nullptr;
+        const int n0 = rc ? rc->n0 : em.n0[r];
         EmulW w;
 #pragma unroll
         for (int t = 0; t < NTAP; ++t) {
-            w.Wh[t] = em.Wh[(size_t)t * Np + r];
-            w.wl[t] = em.wl[(size_t)t * Np + r];
-            w.wf[t] = em.wf[(size_t)t * Np + r];
+            w.Wh[t] = rc ? rc->Wh[t] : em.Wh[(size_t)t * Np + r];
+            w.wl[t] = rc ? rc->wl[t] : em.wl[(size_t)t * Np + r];
+            w.wf[t] = rc ? rc->wf[t] : em.wf[(size_t)t * Np + r];
         }
         double g = 0.0, d = 0.0;
         if constexpr (!PERIODIC) {
-            g = em.gd[r];
-            d = em.gd[Np + r];
+            g = rc ? rc->g64 : em.gd[r];
+            d = rc ? rc->d64 : em.gd[Np + r];
         }
         const int A = (n0 - 4) & 1;
         int base;
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                             for (int t = 0; t < NTAP; ++t) {
                                 const int2 p = src[e + A + v + t];
                                 xv[t] = ((double)p.x + (double)__int_as_float(p.y)) * grid;
-                                acc = fma(em.w64[(size_t)t * Np + r], xv[t], acc);
+                                acc = fma(rc ? rc->w64[t] : em.w64[(size_t)t * Np + r], xv[t], acc);
                             }
                             out[v] = emul_edge(acc, xv, k + v, Nx, g, d);
                         }

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
     __shared__ double red[32];
+    unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)a.stages * (a.Nx + 2 * a.pad));
 
     const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
     long long* __restrict__ fout = static_cast<long long*>(a.fout);
@@ -92,7 +93,8 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int G = gridDim.x;
     const uint32_t row_bytes = (uint32_t)(Nx * 8);
-    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u);
+    const bool use_rec = a.rec != nullptr;
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + (use_rec ? XREC_BYTES : 0u);
     const double unit = ldexp(1.0, em.Ef - 62);
     bool bad = false;
 
@@ -117,6 +119,9 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
         if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
+        if (use_rec)
+            bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+                     XREC_BYTES, &bars[s]);
     };
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -141,13 +146,14 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
         long long rowsum = 0;
         if (ok) {
             const long long* rowbuf = bufs + (size_t)s * stride + PAD;
-            const int n0 = em.n0[r];
+            const XRec* rc = use_rec ? reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES) : nullptr;
+            const int n0 = rc ? rc->n0 : em.n0[r];
             FxW w;
 #pragma unroll
             for (int t = 0; t < NTAP; ++t) {
-                w.Wh[t] = em.Wh[(size_t)t * Np + r];
-                w.wl[t] = em.wl[(size_t)t * Np + r];
-                w.wr[t] = em.wf[(size_t)t * Np + r] * 4.656612873077393e-10f;   // * 2^-31
+                w.Wh[t] = rc ? rc->Wh[t] : em.Wh[(size_t)t * Np + r];
+                w.wl[t] = rc ? rc->wl[t] : em.wl[(size_t)t * Np + r];
+                w.wr[t] = (rc ? rc->wf[t] : em.wf[(size_t)t * Np + r]) * 4.656612873077393e-10f;   // * 2^-31
             }
             const int A = (n0 - 4) & 1;
             int base;
@@ -184,10 +190,12 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
                     if constexpr (!PERIODIC) {
                         const int k = i + n0;
                         if (k < 0 || k + XF_V - 1 >= Nx - 1) {
-                            const double g = em.gd[r], d = em.gd[Np + r];
+                            const double g = rc ? rc->g64 : em.gd[r], d = rc ? rc->d64 : em.gd[Np + r];
+                            const double* w64 = rc ? rc->w64 : em.w64 + r;
+                            const size_t wst = rc ? 1 : (size_t)Np;
 #pragma unroll
                             for (int v = 0; v < XF_V; ++v)
-                                out[v] = fx_edge(rowbuf + e + A + v, em.w64 + r, Np, k + v, Nx, g, d, unit, em.Ef);
+                                out[v] = fx_edge(rowbuf + e + A + v, w64, wst, k + v, Nx, g, d, unit, em.Ef);
                         }
                     }
 #pragma unroll

@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
     const T* __restrict__ wrow = static_cast<const T*>(a.w);
     const T* __restrict__ gdrow = static_cast<const T*>(a.gd);
     const uint32_t row_bytes = (uint32_t)(Nx * sizeof(T));
-    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 16u * (uint32_t)sizeof(T) : 0u);
+    const bool use_rec = a.rec != nullptr;
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 16u * (uint32_t)sizeof(T) : 0u) + (use_rec ? XREC_BYTES : 0u);
+    unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)S * stride);
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
@@ -165,6 +167,9 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
         if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 16u * (uint32_t)sizeof(T), &bars[s]);
+        if (use_rec)
+            bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+                     XREC_BYTES, &bars[s]);
     };
 
     if (tid == 0) {
@@ -190,14 +195,26 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
         const bool ok = mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS);
         acc_t rowsum = acc_t(0);
         if (ok) {
-            const int n0 = a.n0[r];
+            int n0;
             T w[NTAP];
-#pragma unroll
-            for (int t = 0; t < NTAP; ++t) w[t] = wrow[(size_t)t * Np + r];
             T g = T(0), d = T(0);
-            if constexpr (!PERIODIC) {
-                g = gdrow[r];
-                d = gdrow[Np + r];
+            if (use_rec) {
+                const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
+                n0 = rc->n0;
+#pragma unroll
+                for (int t = 0; t < NTAP; ++t) w[t] = sizeof(T) == 8 ? (T)rc->w64[t] : (T)rc->w32[t];
+                if constexpr (!PERIODIC) {
+                    g = sizeof(T) == 8 ? (T)rc->g64 : (T)rc->g32;
+                    d = sizeof(T) == 8 ? (T)rc->d64 : (T)rc->d32;
+                }
+            } else {
+                n0 = a.n0[r];
+#pragma unroll
+                for (int t = 0; t < NTAP; ++t) w[t] = wrow[(size_t)t * Np + r];
+                if constexpr (!PERIODIC) {
+                    g = gdrow[r];
+                    d = gdrow[Np + r];
+                }
             }
             const T* rowbuf = bufs + (size_t)s * stride + PAD;
             T* orow = fout + (size_t)r * Nx;
@@ -279,7 +296,7 @@ int xshift_max_cols(int elem_bytes, int threads)
 
 size_t xshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
 {
-    return 256 + (size_t)stages * (size_t)(Nx + 2 * pad) * (size_t)elem_bytes;
+    return 256 + (size_t)stages * ((size_t)(Nx + 2 * pad) * (size_t)elem_bytes + XREC_BYTES);
 }
 
 template <typename T, bool P, bool K>

@@ -76,6 +76,8 @@ struct vlasov_sim {
     bool fx = false;            // 64-bit fixed-point storage, same filter arithmetic (shift_fx.cu)
     LineParamsDev xp, pp, sp;   // x rows (fixed), p columns (per step), scratch for substeps
     EmulParamsDev xe, pe, se;   // their emulated-FP64 splits
+    void* xrec = nullptr;       // [Np] XRec of the fixed x rows
+    void* srec = nullptr;       // [max(Nx, Np)] XRec scratch for x substeps
     int xthreads = 256, xstages = 1, xpad = 16, xgrid = 1, pgrid = 1, crgrid = 1;
 
     double* colpart = nullptr;  // [xgrid][Nx]
@@ -143,10 +145,32 @@ int alloc_emul(EmulParamsDev& e, int n)
 }
 
 // Host-side filters for n lines with displacements disp[] (cells), uploaded to p (and, for the
-// emulated FP64 sweeps, their integer/FP32 split to e).
+// emulated FP64 sweeps, their integer/FP32 split to e; and as staged x-shift records to rec).
 int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, int* max_abs_n0,
-                  EmulParamsDev* e = nullptr)
+                  EmulParamsDev* e = nullptr, void* rec = nullptr)
 {
+    if (rec) {
+        std::vector<unsigned char> buf((size_t)n * XREC_BYTES, 0);
+        for (int l = 0; l < n; ++l) {
+            LineSplit L;
+            line_split(disp[l], L);
+            XRec r;
+            std::memset(&r, 0, sizeof r);
+            r.n0 = L.n0;
+            r.g64 = L.g;
+            r.d64 = L.d;
+            r.g32 = (float)L.g;
+            r.d32 = (float)L.d;
+            for (int t = 0; t < NTAP; ++t) {
+                r.w64[t] = L.w[t];
+                r.w32[t] = (float)L.w[t];
+                emul_weight(L.w[t], r.Wh[t], r.wl[t], r.wf[t]);
+            }
+            std::memcpy(&buf[(size_t)l * XREC_BYTES], &r, sizeof r);
+        }
+        CU_TRY(cudaMemcpyAsync(rec, buf.data(), buf.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    }
     std::vector<int> n0(n);
     std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n);
     int mx = 0;
@@ -200,9 +224,11 @@ int make_tmap(vlasov_sim* s, int b)
     return VLASOV_OK;
 }
 
-XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& p, bool reduce, bool kin)
+XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& p, bool reduce, bool kin,
+                 const void* rec = nullptr)
 {
     XShiftArgs a;
+    a.rec = rec;
     a.fin = in;
     a.fout = out;
     a.Nx = s->Nx;
@@ -404,7 +430,7 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     const int o = c ^ 1;
     MARK();
     // step 1: f^(I) = f(x - p dt/2, p), with the density partials of f^(I)
-    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false), s->xp, s->xe, false));
+    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false, s->xrec), s->xp, s->xe, false));
     MARK();
     // step 2: rho, moments, F^(I), p-shift filters
     CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
@@ -422,7 +448,7 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
     MARK();
     // step 4: f(t+dt) = f^(II)(x - p dt/2, p), with density + kinetic partials for the moments
-    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, true), s->xp, s->xe, true));
+    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, true, s->xrec), s->xp, s->xe, true));
     MARK();
     CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
     MARK();
@@ -493,7 +519,7 @@ void vlasov_destroy(vlasov_sim* s)
     free_emul(s->se);
     void* bufs[] = {s->colpart, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
-                    s->hist, s->dstep, s->err};
+                    s->hist, s->dstep, s->err, s->xrec, s->srec};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -592,12 +618,14 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         TRY(alloc_emul(s->se, std::max(Nx, Np)));
     }
     int max_n0 = 0;
-    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0, &s->xe));
+    CTRY(cudaMalloc(&s->xrec, (size_t)XREC_BYTES * Np));
+    CTRY(cudaMalloc(&s->srec, (size_t)XREC_BYTES * std::max(Nx, Np)));
+    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0, &s->xe, s->xrec));
 
     // x-shift launch shape: whole rows staged per CTA.
     s->xthreads = XS_THREADS_MIN;
     s->xpad = s->xper ? 16 : ((max_n0 + 8 + 15) / 16) * 16;
-    const size_t row_bytes = (size_t)(Nx + 2 * s->xpad) * esz;
+    const size_t row_bytes = (size_t)(Nx + 2 * s->xpad) * esz + XREC_BYTES;
     const size_t smem_budget = (size_t)max_optin - 2048;
     s->xstages = (int)std::min<size_t>(4, (smem_budget - 256) / row_bytes);
     if (s->emul || s->fx) {
@@ -822,15 +850,15 @@ int vlasov_substep(vlasov_sim* s, int axis, const double* host_disp)
     const int c = s->cur, o = c ^ 1;
     if (axis == 0) {
         int mx = 0;
-        int rc = upload_params(s, s->sp, host_disp, s->Np, &mx, &s->se);
+        int rc = upload_params(s, s->sp, host_disp, s->Np, &mx, &s->se, s->srec);
         if (rc) return rc;
-        XShiftArgs a = xargs(s, s->f[c], s->f[o], s->sp, false, false);
+        XShiftArgs a = xargs(s, s->f[c], s->f[o], s->sp, false, false, s->srec);
         if (!s->xper && mx + 8 > s->xpad) {
             // wider zero halo for this call: the staged row grows, fewer rows in flight
             a.pad = ((mx + 8 + 15) / 16) * 16;
             int max_optin = 0;
             CU_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
-            const size_t row_bytes = (size_t)(s->Nx + 2 * a.pad) * s->esz;
+            const size_t row_bytes = (size_t)(s->Nx + 2 * a.pad) * s->esz + XREC_BYTES;
             const size_t budget = (size_t)max_optin - 2048 - 256;
             a.stages = (int)std::min<size_t>(4, budget / row_bytes);
             if (a.stages < 1) return fail(VLASOV_EINVAL, "x displacement of %d cells does not fit shared memory", mx);

@@ -79,7 +79,23 @@ struct MomentRec {
 
 // ---------------------------------------------------------------------------------------------
 // Launch arguments.
+// Per-row filter record of the x-shift, staged into shared memory next to its row by the same bulk
+// copy transaction (all precisions' forms of the ten weights; filled on the host).
+struct XRec {
+    int n0, pad;
+    double w64[NTAP];
+    double g64, d64;
+    int Wh[NTAP];
+    float wl[NTAP];
+    float wf[NTAP];
+    float w32[NTAP];
+    float g32, d32;
+};
+constexpr int XREC_BYTES = 288;
+static_assert(sizeof(XRec) <= XREC_BYTES, "XRec must fit its staged slot");
+
 struct XShiftArgs {
+    const void* rec = nullptr;   // [Np] records of XREC_BYTES, or null: read the arrays below
     const void* fin;
     void* fout;
     int Nx, Np;
