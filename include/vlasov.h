@@ -136,6 +136,69 @@ int vlasov_kernels_per_step(const vlasov_sim* sim);
    reduction, [ring potential].  Syncs. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
+/* ---------------------------------------------------------------------------------------------
+   Batched form and serving.  Many simulations of different models, grid sizes, initial states and
+   step counts advance together: each kernel of a Strang step is launched once for all of them
+   (FP32 storage of f, FP64-accurate displacements and moment sums), from one captured CUDA graph.
+   p is always f = 0 outside in the batched form.  Results of a simulation do not depend on which
+   others share the batch (each keeps its own fixed CTA-to-row mapping; sums are order-free). */
+typedef struct vlasov_batch vlasov_batch;
+
+typedef struct {
+    int model;                   /* VLASOV_HMF, VLASOV_RING, VLASOV_SHEET, VLASOV_FREE */
+    int Nx, Np;                  /* multiples of 8, 16 <= N <= the batch's max_n */
+    double xmin, xmax, pmin, pmax;
+    int x_periodic;              /* 0: f = 0 outside in x (|x displacement| must stay <= 55 cells) */
+    double eps, G, dt;           /* ring softening, sheet coupling, time step */
+    int init;                    /* 0: f = c [|x|<x0][|p|<p0] (1 + noise xi), xi = 2u-1 from SplitMix64
+                                       output j*Nx+i+1 of `seed` (x0 >= half the x extent: all columns);
+                                    1: f = c [|p|<p0] (1 + amp cos x); both renormalised to unit mass */
+    double x0, p0, noise, amp;
+    unsigned long long seed;
+    int steps;                   /* Strang steps to run */
+    double arrival_s;            /* vlasov_serve: arrival time after the start of the run */
+} vlasov_request;
+
+typedef struct {
+    int status;                  /* 0 done; VLASOV_E* if it could not run (1: still pending) */
+    int steps;
+    double arrival_s, admit_s, done_s;   /* done_s: when the GPU finished its last step */
+    vlasov_moments_t last;       /* moments after the last step */
+    vlasov_moments_t first;      /* moments after the first step */
+} vlasov_result;
+
+/* A batch of `slots` simulation slots with grids up to max_n x max_n, all buffers carved out of one
+   device allocation of mem_budget_bytes (admission fails with VLASOV_ENOMEM while a request does not
+   fit).  stream: cudaStream_t or NULL for an owned one. */
+int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* stream, vlasov_batch** out);
+/* Device bytes one request occupies in a batch. */
+long long vlasov_batch_footprint(const vlasov_request* req);
+/* Admit a request into a free slot (*slot); host_f0 (Np*Nx doubles) or NULL for the device-side
+   initial state of req->init.  VLASOV_ESTATE: no free slot; VLASOV_ENOMEM: does not fit now. */
+int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* req, const double* host_f0, int* slot);
+/* Launch n batched steps; each slot stops at its own step count.  Asynchronous. */
+int vlasov_batch_step(vlasov_batch* b, int n);
+int vlasov_batch_slot_steps(vlasov_batch* b, int slot, int* steps_done);
+/* Syncs; f as doubles (host, may be NULL) and up to max per-step moment records (oldest first). */
+int vlasov_batch_get(vlasov_batch* b, int slot, double* host_f, vlasov_moments_t* moments, int max, int* count);
+/* Free a slot and its memory (waits for work in flight). */
+int vlasov_batch_release(vlasov_batch* b, int slot);
+void vlasov_batch_destroy(vlasov_batch* b);
+
+typedef struct {
+    int slots;                   /* concurrent simulations */
+    int max_n;                   /* largest grid (0: from the requests) */
+    long long mem_budget_bytes;  /* device memory for simulation state */
+    int max_inflight;            /* batched steps queued ahead of the GPU */
+    void* stream;
+} vlasov_serve_options;
+
+/* Continuous-batching run of a request stream: requests are admitted (in arrival order, at their
+   arrival time on the wall clock) as slots and memory free up, advance together one batched step at
+   a time, and retire independently.  results[i] belongs to reqs[i].  *makespan_s: wall time. */
+int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* opt, vlasov_result* results,
+                 double* makespan_s);
+
 /* One x-shift sweep (Eq. step1 form: row j moves by dev_disp[j] cells) with its density, for
    callers that cannot allocate device memory.  The paper has no counterpart: this exists because
    some callers may not call cudaMalloc at all (a host callback or allocator hook, a framework that

@@ -62,13 +62,15 @@ __device__ i128 block_exclusive_scan_i128(i128 v, i128* sh, i128* total)
 // column scale, so the column sum is exact; then int128 block partials of mass, Mx, My.  The last
 // block to finish (ticket) adds those, the kinetic partials, runs the sheet prefix scan, and writes
 // the scalars and (after the second x-shift) the moment record.
-__global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
+__device__ __forceinline__ void colreduce_body(const ColReduceArgs& a)
 {
     __shared__ long long shc[CR_GROUPS][CR_COLS];
     __shared__ i128 red[33];
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int i = blockIdx.x * CR_COLS + lane;
+    const int nblk = (a.Nx + CR_COLS - 1) / CR_COLS;   // blocks that take part (the grid may be larger)
+    if ((int)blockIdx.x >= nblk) return;
 
     // all loads of a thread are independent: issue them in batches of eight
     long long s = 0;
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
         bp[blockIdx.x * 3 + 2] = cy;
         __threadfence();
         const unsigned int tk = atomicAdd(a.ticket, 1u);
-        is_last = (tk == gridDim.x - 1);
+        is_last = (tk == (unsigned int)nblk - 1);
     }
     __syncthreads();
     if (!is_last) return;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
     // ---- last block: totals (exact, any order)
     i128 m = 0, x = 0, y = 0, k = 0;
     const volatile i128* vb = bp;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         m += vb[b * 3 + 0];
         x += vb[b * 3 + 1];
         y += vb[b * 3 + 2];
@@ -200,9 +202,27 @@ __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
     }
 }
 
+__global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
+{
+    colreduce_body(a);
+}
+
+__global__ void __launch_bounds__(256) colreduce_batch_kernel(const ColReduceArgs* __restrict__ args)
+{
+    const ColReduceArgs a = args[blockIdx.y];
+    if (a.Nx <= 0) return;
+    colreduce_body(a);
+}
+
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st)
 {
     colreduce_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColReduceArgs* args, cudaStream_t st)
+{
+    colreduce_batch_kernel<<<dim3(blocks_per_slot, slots), 256, 0, st>>>(args);
     return cudaGetLastError();
 }
 
@@ -214,7 +234,7 @@ cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st)
 constexpr int RING_OUT = 64;
 
 template <typename T>
-__global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
+__device__ __forceinline__ void ring_body(const RingArgs& a)
 {
     extern __shared__ __align__(16) unsigned char ring_smem[];
     T* rs = reinterpret_cast<T*>(ring_smem);
@@ -222,6 +242,8 @@ __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int N = a.N;
+    const int nblk = (N + RING_OUT - 1) / RING_OUT;
+    if ((int)blockIdx.x >= nblk) return;
     for (int k = threadIdx.x; k < N; k += blockDim.x) rs[k] = (T)a.rho[k];
     __syncthreads();
     const T* __restrict__ ker = static_cast<const T*>(a.final_moments ? a.V : a.dV);
@@ -263,14 +285,14 @@ __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
         bp[blockIdx.x] = up;
         __threadfence();
         const unsigned int tk = atomicAdd(a.ticket, 1u);
-        is_last = (tk == gridDim.x - 1);
+        is_last = (tk == (unsigned int)nblk - 1);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     i128 u = 0;
     const volatile i128* vb = bp;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) u += vb[b];
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) u += vb[b];
     u = block_sum_i128(u, red);
     if (threadIdx.x != 0) return;
     *a.ticket = 0u;
@@ -291,7 +313,26 @@ __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
     a.sc->potential = U;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
+{
+    ring_body<T>(a);
+}
+
+__global__ void __launch_bounds__(256) ring_batch_kernel(const RingArgs* __restrict__ args)
+{
+    const RingArgs a = args[blockIdx.y];
+    if (a.N <= 0) return;
+    ring_body<float>(a);
+}
+
 int ring_blocks(int N) { return (N + RING_OUT - 1) / RING_OUT; }
+
+cudaError_t launch_ring_batch(int slots, int max_n, const RingArgs* args, cudaStream_t st)
+{
+    ring_batch_kernel<<<dim3(ring_blocks(max_n), slots), 256, (size_t)max_n * 4, st>>>(args);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st)
 {
@@ -306,7 +347,7 @@ cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st)
 // beta = -sigma - n0) is FP64 always; the ten filter weights are FP64 for FP64 storage and FP32
 // for FP32 storage.
 template <typename T>
-__global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
+__device__ __forceinline__ void pparams_body(const PParamsArgs& a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.Nx) return;
@@ -354,6 +395,24 @@ __global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
             }
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
+{
+    pparams_body<T>(a);
+}
+
+__global__ void __launch_bounds__(64) pparams_batch_kernel(const PParamsArgs* __restrict__ args)
+{
+    const PParamsArgs a = args[blockIdx.y];
+    pparams_body<float>(a);
+}
+
+cudaError_t launch_pparams_batch(int slots, int max_n, const PParamsArgs* args, cudaStream_t st)
+{
+    pparams_batch_kernel<<<dim3((max_n + 63) / 64, slots), 64, 0, st>>>(args);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st)

@@ -1,0 +1,1006 @@
+// batch.cu -- many grids of uneven size and different models advanced together (FP32 storage),
+// and a continuous-batching serving loop on top.
+//
+// A batch has a fixed number of slots.  Every slot owns its buffers inside one device arena (a
+// first-fit allocator over a single allocation, so admission is limited by HBM footprint, not by a
+// fixed per-slot size).  The kernels of a Strang step are the single-grid kernels launched once per
+// sub-step with gridDim.y = slots: each CTA reads its slot's arguments from device arrays (two
+// copies per sweep, one per buffer parity, selected by a per-slot parity word that a one-block
+// kernel flips at the end of the step).  Free slots carry zero sizes and exit at once.  Because the
+// launch parameters never change, one captured CUDA graph runs every batched step, whatever the
+// occupancy; admission and retirement only rewrite a slot's argument entries in stream order.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "../../include/vlasov.h"
+#include "fixed_point.cuh"
+#include "vlasov_internal.cuh"
+
+using namespace vl;
+
+namespace {
+
+constexpr int B_CTAS_X = 16;     // x-shift CTAs per slot (rows per CTA = Np / 16)
+constexpr int B_CTAS_P = 32;     // p-shift CTAs per slot
+constexpr int B_PAD_ZERO = 64;   // zero halo of non-periodic rows (|x displacement| <= 55 cells)
+constexpr int B_STAGES = 3;
+constexpr int B_INIT_BLOCKS = 128;
+
+int bfail(int code, const char* msg)
+{
+    set_last_error(msg);
+    return code;
+}
+
+#define B_TRY(expr)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            char b_[256];                                                                      \
+            snprintf(b_, sizeof b_, "%s: %s", #expr, cudaGetErrorString(e_));                  \
+            return bfail(e_ == cudaErrorMemoryAllocation ? VLASOV_ENOMEM : VLASOV_ECUDA, b_);  \
+        }                                                                                      \
+    } while (0)
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int clog2(double v)
+{
+    int e = 0;
+    const double m = std::frexp(v, &e);
+    return m == 0.5 ? e - 1 : e;
+}
+
+// ------------------------------------------------------------------------------------------- arena
+struct Arena {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;   // offset -> bytes, coalesced
+
+    bool alloc(size_t bytes, size_t* off)
+    {
+        bytes = al256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t noff = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[noff] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = al256(bytes);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------------- device init
+// f_ij = rowv[j] * colv[i] * (1 + noise * xi_ij) in FP32, xi from the (j*Nx+i+1)-th SplitMix64 output
+// of `seed` (top 24 bits); the int128 fixed-point sum of f gives the mass, the last block stores
+// 1/mass; a second kernel scales f to unit mass.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long k)
+{
+    unsigned long long z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct InitArgs {
+    float* f;
+    int Nx, Np;
+    const float* rowv;
+    const float* colv;
+    float noise;
+    unsigned long long seed;
+    int k_m;                 // fixed-point shift of the mass sum
+    double dxdp;
+    void* part;              // int128 [B_INIT_BLOCKS]
+    unsigned int* ticket;
+    double* inv_mass;
+};
+
+__global__ void __launch_bounds__(256) init_fill_kernel(InitArgs a)
+{
+    __shared__ i128 red[33];
+    __shared__ bool is_last;
+    const size_t n = (size_t)a.Nx * a.Np;
+    i128 acc = 0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / a.Nx), i = (int)(k - (size_t)j * a.Nx);
+        float v = a.rowv[j] * a.colv[i];
+        if (v != 0.f && a.noise != 0.f) {
+            const unsigned long long z = splitmix64_at(a.seed, (unsigned long long)k + 1ull);
+            const float xi = __uint2float_rn((unsigned int)(z >> 40)) * 1.1920928955078125e-07f - 1.0f;   // 2u - 1
+            v = v * (1.0f + a.noise * xi);
+        }
+        a.f[k] = v;
+        acc += fx128_from_f32(v, a.k_m);
+    }
+    acc = block_sum_i128(acc, red);
+    i128* part = static_cast<i128*>(a.part);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = acc;
+        __threadfence();
+        is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    i128 t = 0;
+    const volatile i128* vp = part;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += vp[b];
+    t = block_sum_i128(t, red);
+    if (threadIdx.x == 0) {
+        const double mass = a.dxdp * fx128_to_f64(t, a.k_m);
+        *a.inv_mass = mass > 0 ? 1.0 / mass : 0.0;
+        *a.ticket = 0u;
+    }
+}
+
+__global__ void init_scale_kernel(float* f, size_t n, const double* inv_mass)
+{
+    const float s = (float)*inv_mass;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) f[k] *= s;
+}
+
+__global__ void flip_kernel(int* ver, int slots)
+{
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) ver[s] ^= 1;
+}
+
+__global__ void f32_to_f64_kernel(const float* s, double* d, size_t n)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        d[k] = (double)s[k];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// ------------------------------------------------------------------------------------------- slot layout
+struct SlotLayout {
+    size_t f[2], xrec, pn0, pw, pgd, colpart, kinpart, rho, F, Qd, colfx, blockpart, ringpart, tickets, sc, hist,
+        dstep, err, costab, sintab, cosfx, sinfx, ringdV, ringV, rowv, colv, initpart, inv_mass, total;
+};
+
+SlotLayout layout(int Nx, int Np)
+{
+    SlotLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = o;
+        o += al256(bytes);
+        return r;
+    };
+    const size_t cells = (size_t)Nx * Np;
+    L.f[0] = take(cells * 4);
+    L.f[1] = take(cells * 4);
+    L.xrec = take((size_t)Np * XREC_BYTES);
+    L.pn0 = take((size_t)Nx * 4);
+    L.pw = take((size_t)NTAP * Nx * 4);
+    L.pgd = take((size_t)2 * Nx * 4);
+    L.colpart = take((size_t)B_CTAS_X * Nx * 8);
+    L.kinpart = take((size_t)B_CTAS_X * 8);
+    L.rho = take((size_t)Nx * 8);
+    L.F = take((size_t)Nx * 8);
+    L.Qd = take((size_t)Nx * 8);
+    L.colfx = take((size_t)Nx * 8);
+    L.blockpart = take((size_t)((Nx + 31) / 32) * 48);
+    L.ringpart = take((size_t)ring_blocks(Nx) * 16);
+    L.tickets = take(16);
+    L.sc = take(sizeof(Scalars));
+    L.hist = take(sizeof(MomentRec) * HIST_CAP);
+    L.dstep = take(8);
+    L.err = take(8);
+    L.costab = take((size_t)Nx * 8);
+    L.sintab = take((size_t)Nx * 8);
+    L.cosfx = take((size_t)Nx * 8);
+    L.sinfx = take((size_t)Nx * 8);
+    L.ringdV = take((size_t)Nx * 4);
+    L.ringV = take((size_t)Nx * 4);
+    L.rowv = take((size_t)Np * 4);
+    L.colv = take((size_t)Nx * 4);
+    L.initpart = take((size_t)B_INIT_BLOCKS * 16);
+    L.inv_mass = take(8);
+    L.total = o;
+    return L;
+}
+
+struct Slot {
+    bool used = false;       // buffers allocated (admitted, possibly finished and draining)
+    bool active = false;     // advanced by batched steps
+    vlasov_request req;
+    size_t off = 0, bytes = 0;
+    SlotLayout L;
+    int steps_done = 0;
+    int Ef = 0, k_col = 0, k_kin = 0, k_pot = 0;
+    double admit_s = 0;
+    int done_event = -1;     // index into the step-event ring of the step that finished it
+    long long result_index = -1;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------- the batch
+struct vlasov_batch {
+    int S = 0, max_n = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    Arena arena;
+    std::vector<Slot> slots;
+    // device argument arrays and their host mirrors
+    XShiftArgs* d_xa = nullptr;      // [4][S][2]: periodic/zero x (step 1), periodic/zero x (step 4)
+    PShiftArgs* d_pa = nullptr;      // [S][2]
+    CUtensorMap* d_tm = nullptr;     // [S][2]
+    ColReduceArgs* d_cr = nullptr;   // [2][S]: after step 1, after step 4
+    RingArgs* d_rg = nullptr;        // [2][S]
+    PParamsArgs* d_pp = nullptr;     // [S]
+    int* d_ver = nullptr;            // [S]
+    std::vector<XShiftArgs> xa;
+    std::vector<PShiftArgs> pa;
+    std::vector<CUtensorMap> tm;
+    std::vector<ColReduceArgs> cr;
+    std::vector<RingArgs> rg;
+    std::vector<PParamsArgs> pp;
+    size_t xsmem = 0;
+    cudaGraphExec_t graph = nullptr;
+    long long steps_launched = 0;
+};
+
+namespace {
+
+char* P(vlasov_batch* b, const Slot& s, size_t off) { return b->arena.base + s.off + off; }
+
+void clear_slot_args(vlasov_batch* b, int k)
+{
+    for (int kind = 0; kind < 4; ++kind)
+        for (int v = 0; v < 2; ++v) {
+            XShiftArgs& a = b->xa[((size_t)kind * b->S + k) * 2 + v];
+            a = XShiftArgs{};
+            a.Np = 0;
+            a.Nx = 0;
+        }
+    for (int v = 0; v < 2; ++v) {
+        PShiftArgs& a = b->pa[(size_t)k * 2 + v];
+        std::memset(&a, 0, sizeof a);
+    }
+    for (int q = 0; q < 2; ++q) {
+        std::memset(&b->cr[(size_t)q * b->S + k], 0, sizeof(ColReduceArgs));
+        std::memset(&b->rg[(size_t)q * b->S + k], 0, sizeof(RingArgs));
+    }
+    std::memset(&b->pp[k], 0, sizeof(PParamsArgs));
+}
+
+int upload_slot_args(vlasov_batch* b, int k)
+{
+    const size_t S = b->S;
+    for (int kind = 0; kind < 4; ++kind)
+        B_TRY(cudaMemcpyAsync(b->d_xa + (kind * S + k) * 2, &b->xa[(kind * S + k) * 2], 2 * sizeof(XShiftArgs),
+                              cudaMemcpyHostToDevice, b->st));
+    B_TRY(cudaMemcpyAsync(b->d_pa + (size_t)k * 2, &b->pa[(size_t)k * 2], 2 * sizeof(PShiftArgs), cudaMemcpyHostToDevice, b->st));
+    B_TRY(cudaMemcpyAsync(b->d_tm + (size_t)k * 2, &b->tm[(size_t)k * 2], 2 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, b->st));
+    for (int q = 0; q < 2; ++q) {
+        B_TRY(cudaMemcpyAsync(b->d_cr + q * S + k, &b->cr[q * S + k], sizeof(ColReduceArgs), cudaMemcpyHostToDevice, b->st));
+        B_TRY(cudaMemcpyAsync(b->d_rg + q * S + k, &b->rg[q * S + k], sizeof(RingArgs), cudaMemcpyHostToDevice, b->st));
+    }
+    B_TRY(cudaMemcpyAsync(b->d_pp + k, &b->pp[k], sizeof(PParamsArgs), cudaMemcpyHostToDevice, b->st));
+    return VLASOV_OK;
+}
+
+// Fill the argument entries of an occupied slot (both buffer parities) from its layout.
+int fill_slot_args(vlasov_batch* b, int k)
+{
+    Slot& s = b->slots[k];
+    const vlasov_request& r = s.req;
+    const int Nx = r.Nx, Np = r.Np;
+    const double dx = (r.xmax - r.xmin) / Nx, dp = (r.pmax - r.pmin) / Np;
+    const bool per = r.x_periodic != 0;
+    void* fbuf[2] = {P(b, s, s.L.f[0]), P(b, s, s.L.f[1])};
+    for (int v = 0; v < 2; ++v) {          // v = buffer holding f at the start of the step
+        for (int step4 = 0; step4 < 2; ++step4) {
+            for (int kind_per = 0; kind_per < 2; ++kind_per) {
+                const int kind = step4 * 2 + (kind_per ? 0 : 1);   // 0 per/step1, 1 zero/step1, 2 per/step4, 3 zero/step4
+                XShiftArgs& a = b->xa[((size_t)kind * b->S + k) * 2 + v];
+                a = XShiftArgs{};
+                if ((kind_per == 1) != per) {
+                    a.Nx = a.Np = 0;
+                    continue;
+                }
+                a.rec = P(b, s, s.L.xrec);
+                a.fin = fbuf[v];          // both x half-shifts of the step read buffer v
+                a.fout = fbuf[v ^ 1];
+                a.Nx = Nx;
+                a.Np = Np;
+                a.pad = per ? 16 : B_PAD_ZERO;
+                a.stages = B_STAGES;
+                a.n0 = nullptr;
+                a.w = nullptr;
+                a.gd = nullptr;
+                a.colpart = reinterpret_cast<double*>(P(b, s, s.L.colpart));
+                a.kinpart = step4 ? reinterpret_cast<double*>(P(b, s, s.L.kinpart)) : nullptr;
+                a.pmin = r.pmin;
+                a.dp = dp;
+                a.err = reinterpret_cast<int*>(P(b, s, s.L.err));
+            }
+        }
+        // p-shift: reads the other buffer, writes back into v
+        PShiftArgs& pa = b->pa[(size_t)k * 2 + v];
+        pa.fin = fbuf[v ^ 1];
+        pa.fout = fbuf[v];
+        pa.Nx = Nx;
+        pa.Np = Np;
+        pa.n0 = reinterpret_cast<const int*>(P(b, s, s.L.pn0));
+        pa.w = P(b, s, s.L.pw);
+        pa.gd = P(b, s, s.L.pgd);
+        pa.err = reinterpret_cast<int*>(P(b, s, s.L.err));
+        auto enc = encode_tiled();
+        if (!enc) return bfail(VLASOV_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+        cuuint64_t dims[2] = {(cuuint64_t)Nx, (cuuint64_t)Np};
+        cuuint64_t strides[1] = {(cuuint64_t)Nx * 4};
+        cuuint32_t box[2] = {(cuuint32_t)PS_TW, (cuuint32_t)PS_BH};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&b->tm[(size_t)k * 2 + v], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, fbuf[v ^ 1], dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return bfail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed for a batch slot");
+    }
+    const int B = std::min(B_CTAS_X, Np);
+    for (int q = 0; q < 2; ++q) {
+        ColReduceArgs& c = b->cr[(size_t)q * b->S + k];
+        c.colpart = reinterpret_cast<const double*>(P(b, s, s.L.colpart));
+        c.B = B;
+        c.kinpart = q ? reinterpret_cast<const double*>(P(b, s, s.L.kinpart)) : nullptr;
+        c.Nx = Nx;
+        c.k_col = s.k_col;
+        c.k_kin = s.k_kin;
+        c.k_pot = s.k_pot;
+        c.dp = dp;
+        c.dxdp = dx * dp;
+        c.pot_scale = 2.0 * 3.14159265358979323846 * r.G * dx * dx * dx * dp * dp;
+        c.cosfx = reinterpret_cast<const long long*>(P(b, s, s.L.cosfx));
+        c.sinfx = reinterpret_cast<const long long*>(P(b, s, s.L.sinfx));
+        c.rho = reinterpret_cast<double*>(P(b, s, s.L.rho));
+        c.colfx = reinterpret_cast<long long*>(P(b, s, s.L.colfx));
+        c.Qd = reinterpret_cast<double*>(P(b, s, s.L.Qd));
+        c.blockpart = P(b, s, s.L.blockpart);
+        c.ticket = reinterpret_cast<unsigned int*>(P(b, s, s.L.tickets));
+        c.sc = reinterpret_cast<Scalars*>(P(b, s, s.L.sc));
+        c.model = r.model;
+        c.final_moments = q;
+        c.hist = reinterpret_cast<MomentRec*>(P(b, s, s.L.hist));
+        c.step = reinterpret_cast<long long*>(P(b, s, s.L.dstep));
+        c.dt = r.dt;
+        RingArgs& g = b->rg[(size_t)q * b->S + k];
+        std::memset(&g, 0, sizeof g);
+        if (r.model == VLASOV_RING) {
+            g.N = Nx;
+            g.dx = dx;
+            g.rho = c.rho;
+            g.dV = P(b, s, s.L.ringdV);
+            g.V = P(b, s, s.L.ringV);
+            g.F = reinterpret_cast<double*>(P(b, s, s.L.F));
+            g.blockpart = P(b, s, s.L.ringpart);
+            g.k_pot = s.k_pot;
+            g.pot_scale = 0.5 * dx;
+            g.ticket = reinterpret_cast<unsigned int*>(P(b, s, s.L.tickets)) + 1;
+            g.sc = c.sc;
+            g.final_moments = q;
+            g.hist = c.hist;
+            g.step = c.step;
+            g.dt = r.dt;
+        }
+    }
+    PParamsArgs& p = b->pp[k];
+    p.Nx = Nx;
+    p.model = r.model;
+    p.sc = reinterpret_cast<const Scalars*>(P(b, s, s.L.sc));
+    p.costab = reinterpret_cast<const double*>(P(b, s, s.L.costab));
+    p.sintab = reinterpret_cast<const double*>(P(b, s, s.L.sintab));
+    p.Fin = reinterpret_cast<const double*>(P(b, s, r.model == VLASOV_SHEET ? s.L.Qd : s.L.F));
+    p.Fscale = -2.0 * 3.14159265358979323846 * r.G * dx * dp;
+    p.cp = r.dt / dp;
+    p.n0 = reinterpret_cast<int*>(P(b, s, s.L.pn0));
+    p.w = P(b, s, s.L.pw);
+    p.gd = P(b, s, s.L.pgd);
+    p.Fout = nullptr;
+    p.Wh = nullptr;
+    p.wl = nullptr;
+    p.wf = nullptr;
+    return VLASOV_OK;
+}
+
+int validate_request(const vlasov_request* r, int max_n)
+{
+    if (!r) return bfail(VLASOV_EINVAL, "NULL request");
+    if (r->model < VLASOV_HMF || r->model > VLASOV_FREE) return bfail(VLASOV_EINVAL, "unknown model");
+    if (r->Nx < 16 || r->Np < 16 || r->Nx % 8 || r->Np % 8) return bfail(VLASOV_EINVAL, "Nx, Np: multiples of 8, >= 16");
+    if (r->Nx > max_n || r->Np > max_n) return bfail(VLASOV_EINVAL, "grid larger than the batch maximum");
+    if (!(r->dt > 0) || !(r->xmax > r->xmin) || !(r->pmax > r->pmin)) return bfail(VLASOV_EINVAL, "bad domain or dt");
+    if (r->model == VLASOV_RING && !(r->eps > 0)) return bfail(VLASOV_EINVAL, "ring needs eps > 0");
+    if (r->steps < 0) return bfail(VLASOV_EINVAL, "steps < 0");
+    return VLASOV_OK;
+}
+
+}  // namespace
+
+// ================================================================================== C ABI
+extern "C" {
+
+void vlasov_batch_destroy(vlasov_batch* b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->arena.base);
+    void* bufs[] = {b->d_xa, b->d_pa, b->d_tm, b->d_cr, b->d_rg, b->d_pp, b->d_ver};
+    for (void* p : bufs) cudaFree(p);
+    if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* stream, vlasov_batch** out)
+{
+    if (!out) return bfail(VLASOV_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (slots < 1 || slots > 4096) return bfail(VLASOV_EINVAL, "slots must be in 1..4096");
+    if (max_n < 16 || max_n % 8 || max_n > 8192) return bfail(VLASOV_EINVAL, "max_n must be a multiple of 8 in 16..8192");
+    if (mem_budget_bytes <= 0) return bfail(VLASOV_EINVAL, "memory budget must be positive");
+    vlasov_batch* b = new vlasov_batch();
+    b->S = slots;
+    b->max_n = max_n;
+    auto bail = [&](int rc) {
+        vlasov_batch_destroy(b);
+        return rc;
+    };
+#define BC(expr)                                  \
+    do {                                          \
+        int rc_ = [&]() -> int {                  \
+            B_TRY(expr);                          \
+            return VLASOV_OK;                     \
+        }();                                      \
+        if (rc_) return bail(rc_);                \
+    } while (0)
+    if (stream) {
+        b->st = static_cast<cudaStream_t>(stream);
+    } else {
+        BC(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    int dev = 0, optin = 0;
+    BC(cudaGetDevice(&dev));
+    BC(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    BC(set_kernel_attributes(optin - 1024));
+    BC(cudaMalloc(&b->arena.base, (size_t)mem_budget_bytes));
+    b->arena.size = (size_t)mem_budget_bytes;
+    b->arena.free_[0] = (size_t)mem_budget_bytes;
+    b->slots.resize(slots);
+    const size_t S = slots;
+    b->xa.assign(4 * S * 2, XShiftArgs{});
+    b->pa.assign(S * 2, PShiftArgs{});
+    b->tm.assign(S * 2, CUtensorMap{});
+    b->cr.assign(2 * S, ColReduceArgs{});
+    b->rg.assign(2 * S, RingArgs{});
+    b->pp.assign(S, PParamsArgs{});
+    for (int k = 0; k < slots; ++k) clear_slot_args(b, k);
+    BC(cudaMalloc(&b->d_xa, sizeof(XShiftArgs) * b->xa.size()));
+    BC(cudaMalloc(&b->d_pa, sizeof(PShiftArgs) * b->pa.size()));
+    BC(cudaMalloc(&b->d_tm, sizeof(CUtensorMap) * b->tm.size()));
+    BC(cudaMalloc(&b->d_cr, sizeof(ColReduceArgs) * b->cr.size()));
+    BC(cudaMalloc(&b->d_rg, sizeof(RingArgs) * b->rg.size()));
+    BC(cudaMalloc(&b->d_pp, sizeof(PParamsArgs) * b->pp.size()));
+    BC(cudaMalloc(&b->d_ver, sizeof(int) * S));
+    BC(cudaMemsetAsync(b->d_ver, 0, sizeof(int) * S, b->st));
+    BC(cudaMemcpyAsync(b->d_xa, b->xa.data(), sizeof(XShiftArgs) * b->xa.size(), cudaMemcpyHostToDevice, b->st));
+    BC(cudaMemcpyAsync(b->d_pa, b->pa.data(), sizeof(PShiftArgs) * b->pa.size(), cudaMemcpyHostToDevice, b->st));
+    BC(cudaMemsetAsync(b->d_tm, 0, sizeof(CUtensorMap) * b->tm.size(), b->st));
+    BC(cudaMemcpyAsync(b->d_cr, b->cr.data(), sizeof(ColReduceArgs) * b->cr.size(), cudaMemcpyHostToDevice, b->st));
+    BC(cudaMemcpyAsync(b->d_rg, b->rg.data(), sizeof(RingArgs) * b->rg.size(), cudaMemcpyHostToDevice, b->st));
+    BC(cudaMemcpyAsync(b->d_pp, b->pp.data(), sizeof(PParamsArgs) * b->pp.size(), cudaMemcpyHostToDevice, b->st));
+    BC(cudaStreamSynchronize(b->st));
+    b->xsmem = xshift_smem_bytes(max_n, B_PAD_ZERO, B_STAGES, 4);
+
+    // capture one batched Strang step
+    cudaGraph_t g = nullptr;
+    BC(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    int rc = VLASOV_OK;
+    auto L = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == VLASOV_OK) {
+            char m[256];
+            snprintf(m, sizeof m, "batched launch: %s", cudaGetErrorString(e));
+            rc = bfail(VLASOV_ECUDA, m);
+        }
+    };
+    const int crb = (max_n + 31) / 32;
+    L(launch_xshift_batch(true, false, slots, B_CTAS_X, b->xsmem, b->d_xa + 0 * S * 2, b->d_ver, b->st));
+    L(launch_xshift_batch(false, false, slots, B_CTAS_X, b->xsmem, b->d_xa + 1 * S * 2, b->d_ver, b->st));
+    L(launch_colreduce_batch(slots, crb, b->d_cr, b->st));
+    L(launch_ring_batch(slots, max_n, b->d_rg, b->st));
+    L(launch_pparams_batch(slots, max_n, b->d_pp, b->st));
+    L(launch_pshift_batch(slots, B_CTAS_P, b->d_tm, b->d_pa, b->d_ver, b->st));
+    L(launch_xshift_batch(true, true, slots, B_CTAS_X, b->xsmem, b->d_xa + 2 * S * 2, b->d_ver, b->st));
+    L(launch_xshift_batch(false, true, slots, B_CTAS_X, b->xsmem, b->d_xa + 3 * S * 2, b->d_ver, b->st));
+    L(launch_colreduce_batch(slots, crb, b->d_cr + S, b->st));
+    L(launch_ring_batch(slots, max_n, b->d_rg + S, b->st));
+    flip_kernel<<<1, 256, 0, b->st>>>(b->d_ver, slots);
+    L(cudaGetLastError());
+    cudaError_t ec = cudaStreamEndCapture(b->st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return bail(rc);
+    }
+    if (ec != cudaSuccess) return bail(bfail(VLASOV_ECUDA, "batch graph capture failed"));
+    ec = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ec != cudaSuccess) return bail(bfail(VLASOV_ECUDA, "batch graph instantiate failed"));
+#undef BC
+    *out = b;
+    return VLASOV_OK;
+}
+
+// Bytes of device memory a request occupies in a batch arena.
+long long vlasov_batch_footprint(const vlasov_request* r)
+{
+    if (!r || r->Nx <= 0 || r->Np <= 0) return -1;
+    return (long long)layout(r->Nx, r->Np).total;
+}
+
+int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* host_f0, int* slot_out)
+{
+    if (!b || !slot_out) return bfail(VLASOV_EINVAL, "NULL argument");
+    *slot_out = -1;
+    int rc = validate_request(r, b->max_n);
+    if (rc) return rc;
+    int k = -1;
+    for (int q = 0; q < b->S; ++q)
+        if (!b->slots[q].used) {
+            k = q;
+            break;
+        }
+    if (k < 0) return bfail(VLASOV_ESTATE, "no free slot");
+    const SlotLayout L = layout(r->Nx, r->Np);
+    size_t off = 0;
+    if (!b->arena.alloc(L.total, &off)) return bfail(VLASOV_ENOMEM, "request does not fit the batch memory budget now");
+    Slot& s = b->slots[k];
+    s = Slot{};
+    s.used = true;
+    s.req = *r;
+    s.off = off;
+    s.bytes = L.total;
+    s.L = L;
+    const int Nx = r->Nx, Np = r->Np;
+    const double dx = (r->xmax - r->xmin) / Nx, dp = (r->pmax - r->pmin) / Np;
+    const bool per = r->x_periodic != 0;
+
+    // host-side tables: node coordinates, initial profile factors, trig and ring tables, row filters
+    std::vector<float> rowv(Np), colv(Nx);
+    double colsum = 0, rowsum = 0;
+    for (int j = 0; j < Np; ++j) {
+        const double p = r->pmin + (double)j * dp;
+        float v = std::fabs(p) < r->p0 ? 1.0f : 0.0f;
+        rowv[j] = v;
+        rowsum += v;
+    }
+    const double half_x = 0.5 * (r->xmax - r->xmin);
+    for (int i = 0; i < Nx; ++i) {
+        const double x = r->xmin + (double)i * dx;
+        double v;
+        if (r->init == 0) v = (r->x0 >= half_x || std::fabs(x) < r->x0) ? 1.0 / (4.0 * r->x0 * r->p0) : 0.0;
+        else v = (1.0 / (2.0 * r->p0 * (r->xmax - r->xmin))) * (1.0 + r->amp * std::cos(x));
+        colv[i] = (float)v;
+        colsum += v;
+    }
+    const double mass_est = dx * dp * colsum * rowsum;
+    if (!(mass_est > 0)) {
+        b->arena.release(off, L.total);
+        s = Slot{};
+        return bfail(VLASOV_EINVAL, "initial state is empty on this grid");
+    }
+    double fmax = 0;
+    for (int i = 0; i < Nx; ++i) fmax = std::max(fmax, (double)colv[i]);
+    fmax = fmax * (1.0 + std::fabs(r->noise)) / mass_est;   // after normalisation
+    {
+        int e = 0;
+        std::frexp(fmax, &e);
+        s.Ef = e + 2;
+        const int Lp = clog2((double)Np), Lx = clog2((double)Nx);
+        const double pm = std::max(std::fabs(r->pmin), std::fabs(r->pmax));
+        s.k_col = 61 - s.Ef - Lp;
+        s.k_kin = 124 - clog2(0.5 * pm * pm * (double)Np * (double)Nx) - s.Ef;
+        s.k_pot = 0;
+        if (r->model == VLASOV_SHEET) s.k_pot = 124 - (3 * Lx + 2 * (Lp + s.Ef));
+        if (r->model == VLASOV_RING) {
+            const double vmax = 1.0 / std::sqrt(2.0 * r->eps);
+            const double rmax = dp * (double)Np * std::ldexp(1.0, s.Ef);
+            s.k_pot = 124 - clog2((double)Nx * (double)Nx * dx * vmax * rmax * rmax);
+        }
+    }
+    std::vector<double> c(Nx), sn(Nx);
+    std::vector<long long> cfx(Nx), sfx(Nx);
+    std::vector<float> dV(Nx, 0.f), V(Nx, 0.f);
+    for (int i = 0; i < Nx; ++i) {
+        const double th = r->xmin + (double)i * dx;
+        c[i] = std::cos(th);
+        sn[i] = std::sin(th);
+        cfx[i] = std::llround(std::ldexp(c[i], 62));
+        sfx[i] = std::llround(std::ldexp(sn[i], 62));
+        if (r->model == VLASOV_RING) {
+            const double u = (double)i * dx;
+            const double q = 1.0 - std::cos(u) + r->eps;
+            dV[i] = (float)(std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q)));
+            V[i] = (float)(-1.0 / (std::sqrt(2.0) * std::sqrt(q)));
+        }
+    }
+    std::vector<unsigned char> recs((size_t)Np * XREC_BYTES, 0);
+    const double cx = (0.5 * r->dt) / dx;
+    int max_n0 = 0;
+    for (int j = 0; j < Np; ++j) {
+        const double p = r->pmin + (double)j * dp;
+        LineSplit Ls;
+        line_split(p * cx, Ls);
+        XRec rc_;
+        std::memset(&rc_, 0, sizeof rc_);
+        rc_.n0 = Ls.n0;
+        max_n0 = std::max(max_n0, std::abs(Ls.n0));
+        rc_.g64 = Ls.g;
+        rc_.d64 = Ls.d;
+        rc_.g32 = (float)Ls.g;
+        rc_.d32 = (float)Ls.d;
+        for (int t = 0; t < NTAP; ++t) {
+            rc_.w64[t] = Ls.w[t];
+            rc_.w32[t] = (float)Ls.w[t];
+        }
+        std::memcpy(&recs[(size_t)j * XREC_BYTES], &rc_, sizeof rc_);
+    }
+    if (!per && max_n0 + 8 > B_PAD_ZERO) {
+        b->arena.release(off, L.total);
+        s = Slot{};
+        return bfail(VLASOV_EINVAL, "x displacement too large for the batched zero halo (55 cells)");
+    }
+    auto H2D = [&](size_t o, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(P(b, s, o), src, bytes, cudaMemcpyHostToDevice, b->st);
+    };
+    B_TRY(cudaMemsetAsync(P(b, s, 0), 0, L.total, b->st));
+    B_TRY(H2D(L.costab, c.data(), 8 * (size_t)Nx));
+    B_TRY(H2D(L.sintab, sn.data(), 8 * (size_t)Nx));
+    B_TRY(H2D(L.cosfx, cfx.data(), 8 * (size_t)Nx));
+    B_TRY(H2D(L.sinfx, sfx.data(), 8 * (size_t)Nx));
+    B_TRY(H2D(L.ringdV, dV.data(), 4 * (size_t)Nx));
+    B_TRY(H2D(L.ringV, V.data(), 4 * (size_t)Nx));
+    B_TRY(H2D(L.xrec, recs.data(), recs.size()));
+    const size_t cells = (size_t)Nx * Np;
+    if (host_f0) {
+        std::vector<float> tmp(cells);
+        for (size_t q = 0; q < cells; ++q) tmp[q] = (float)host_f0[q];
+        B_TRY(H2D(L.f[0], tmp.data(), cells * 4));
+        B_TRY(cudaStreamSynchronize(b->st));
+    } else {
+        B_TRY(H2D(L.rowv, rowv.data(), 4 * (size_t)Np));
+        B_TRY(H2D(L.colv, colv.data(), 4 * (size_t)Nx));
+        InitArgs ia;
+        ia.f = reinterpret_cast<float*>(P(b, s, L.f[0]));
+        ia.Nx = Nx;
+        ia.Np = Np;
+        ia.rowv = reinterpret_cast<const float*>(P(b, s, L.rowv));
+        ia.colv = reinterpret_cast<const float*>(P(b, s, L.colv));
+        ia.noise = (float)(r->init == 0 ? r->noise : 0.0);
+        ia.seed = r->seed;
+        ia.k_m = 120 - clog2((double)cells * fmax * mass_est * 2.0 + 1.0);
+        ia.dxdp = dx * dp;
+        ia.part = P(b, s, L.initpart);
+        ia.ticket = reinterpret_cast<unsigned int*>(P(b, s, L.tickets));
+        ia.inv_mass = reinterpret_cast<double*>(P(b, s, L.inv_mass));
+        init_fill_kernel<<<B_INIT_BLOCKS, 256, 0, b->st>>>(ia);
+        B_TRY(cudaGetLastError());
+        init_scale_kernel<<<256, 256, 0, b->st>>>(ia.f, cells, ia.inv_mass);
+        B_TRY(cudaGetLastError());
+    }
+    // this slot starts at buffer 0: its parity word must read 0 at its first step
+    const int zero = 0;
+    B_TRY(cudaMemcpyAsync(b->d_ver + k, &zero, sizeof(int), cudaMemcpyHostToDevice, b->st));
+    rc = fill_slot_args(b, k);
+    if (rc) {
+        b->arena.release(off, L.total);
+        s = Slot{};
+        return rc;
+    }
+    if (r->steps == 0) clear_slot_args(b, k);
+    rc = upload_slot_args(b, k);
+    if (rc) return rc;
+    // the small host tables above are staged by the runtime when copied from pageable memory, so
+    // they may go out of scope without waiting for the stream (admission overlaps running steps)
+    s.active = r->steps > 0;
+    *slot_out = k;
+    return VLASOV_OK;
+}
+
+int vlasov_batch_step(vlasov_batch* b, int n)
+{
+    if (!b || n < 0) return bfail(VLASOV_EINVAL, "bad argument");
+    for (int it = 0; it < n; ++it) {
+        bool any = false;
+        for (auto& s : b->slots) any |= s.active;
+        if (!any) break;
+        B_TRY(cudaGraphLaunch(b->graph, b->st));
+        ++b->steps_launched;
+        for (int k = 0; k < b->S; ++k) {
+            Slot& s = b->slots[k];
+            if (!s.active) continue;
+            if (++s.steps_done >= s.req.steps) {
+                // finished: no further batched step may touch it
+                s.active = false;
+                clear_slot_args(b, k);
+                int rc = upload_slot_args(b, k);
+                if (rc) return rc;
+            }
+        }
+    }
+    return VLASOV_OK;
+}
+
+int vlasov_batch_slot_steps(vlasov_batch* b, int slot, int* steps_done)
+{
+    if (!b || slot < 0 || slot >= b->S || !steps_done) return bfail(VLASOV_EINVAL, "bad argument");
+    *steps_done = b->slots[slot].steps_done;
+    return VLASOV_OK;
+}
+
+int vlasov_batch_get(vlasov_batch* b, int slot, double* host_f, vlasov_moments_t* out, int max, int* count)
+{
+    if (!b || slot < 0 || slot >= b->S) return bfail(VLASOV_EINVAL, "bad argument");
+    Slot& s = b->slots[slot];
+    if (!s.used) return bfail(VLASOV_ESTATE, "slot is free");
+    B_TRY(cudaStreamSynchronize(b->st));
+    const size_t cells = (size_t)s.req.Nx * s.req.Np;
+    if (host_f) {
+        std::vector<float> tmp(cells);
+        const int cur = s.steps_done & 1;
+        B_TRY(cudaMemcpy(tmp.data(), P(b, s, s.L.f[cur]), cells * 4, cudaMemcpyDeviceToHost));
+        for (size_t q = 0; q < cells; ++q) host_f[q] = (double)tmp[q];
+    }
+    if (count) *count = 0;
+    if (out && max > 0) {
+        const int n = std::min(std::min(max, s.steps_done), HIST_CAP);
+        std::vector<MomentRec> rec(HIST_CAP);
+        B_TRY(cudaMemcpy(rec.data(), P(b, s, s.L.hist), sizeof(MomentRec) * HIST_CAP, cudaMemcpyDeviceToHost));
+        const int first = s.steps_done - n;
+        for (int q = 0; q < n; ++q) {
+            const MomentRec& m = rec[(size_t)(first + q) % HIST_CAP];
+            out[q].t = m.t;
+            out[q].mass = m.mass;
+            out[q].Mx = m.Mx;
+            out[q].My = m.My;
+            out[q].kinetic = m.kinetic;
+            out[q].potential = m.potential;
+            out[q].energy = m.energy;
+            out[q].step = m.step;
+        }
+        if (count) *count = n;
+    }
+    int h = 0;
+    B_TRY(cudaMemcpy(&h, P(b, s, s.L.err), sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return bfail(h == DEV_ERR_RANGE ? VLASOV_ERANGE : VLASOV_ETIMEOUT, "device error flag set for this slot");
+    return VLASOV_OK;
+}
+
+int vlasov_batch_release(vlasov_batch* b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->S) return bfail(VLASOV_EINVAL, "bad argument");
+    Slot& s = b->slots[slot];
+    if (!s.used) return VLASOV_OK;
+    if (s.active) {
+        s.active = false;
+        clear_slot_args(b, slot);
+        int rc = upload_slot_args(b, slot);
+        if (rc) return rc;
+    }
+    B_TRY(cudaStreamSynchronize(b->st));   // nothing in flight may still use its memory
+    b->arena.release(s.off, s.bytes);
+    s = Slot{};
+    return VLASOV_OK;
+}
+
+// ------------------------------------------------------------------------------------------- serving loop
+int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* opt, vlasov_result* results,
+                 double* makespan_s)
+{
+    if (!reqs || n < 0 || !opt || !results) return bfail(VLASOV_EINVAL, "NULL argument");
+    int max_n = opt->max_n;
+    if (max_n <= 0)
+        for (int q = 0; q < n; ++q) max_n = std::max(max_n, std::max(reqs[q].Nx, reqs[q].Np));
+    vlasov_batch* b = nullptr;
+    int rc = vlasov_batch_create(std::max(1, opt->slots), std::max(16, max_n), opt->mem_budget_bytes, opt->stream, &b);
+    if (rc) return rc;
+    const int depth = std::max(1, opt->max_inflight);
+    std::vector<int> order(n);
+    for (int q = 0; q < n; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return reqs[a].arrival_s < reqs[c].arrival_s; });
+    for (int q = 0; q < n; ++q) {
+        std::memset(&results[q], 0, sizeof(vlasov_result));
+        results[q].status = 1;   // pending
+        results[q].arrival_s = reqs[q].arrival_s;
+    }
+    // events: one at the start, one after each launched batched step (ring)
+    const int NE = 256;
+    std::vector<cudaEvent_t> ev(NE);
+    cudaEvent_t ev0;
+    auto cleanup = [&]() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (ev0) cudaEventDestroy(ev0);
+        vlasov_batch_destroy(b);
+    };
+    ev0 = nullptr;
+    for (auto& e : ev) e = nullptr;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cleanup();
+            return bfail(VLASOV_ECUDA, "event create");
+        }
+    if (cudaEventCreate(&ev0) != cudaSuccess) {
+        cleanup();
+        return bfail(VLASOV_ECUDA, "event create");
+    }
+    cudaStreamSynchronize(b->st);
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaEventRecord(ev0, b->st);
+    auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+
+    struct Draining {
+        int slot;
+        int req;
+        long long step_index;   // global batched step after which it finished
+    };
+    std::vector<Draining> draining;
+    std::vector<int> slot_req(b->S, -1);
+    std::vector<MomentRec> hostrec(2 * b->S);
+    int next = 0, finished = 0;
+    long long launched = 0;
+    std::vector<long long> ev_step(NE, -1);   // which global step each ring event marks
+    rc = VLASOV_OK;
+    while (finished < n && rc == VLASOV_OK) {
+        // admit arrived requests in arrival order while a slot and memory are free
+        while (next < n && reqs[order[next]].arrival_s <= now_s()) {
+            const int q = order[next];
+            int slot = -1;
+            const int r2 = vlasov_batch_admit(b, &reqs[q], nullptr, &slot);
+            if (r2 == VLASOV_ESTATE || r2 == VLASOV_ENOMEM) {
+                // full now: admit later, unless nothing is running (then it can never fit)
+                bool busy = false;
+                for (auto& s : b->slots) busy |= s.used;
+                if (!busy) {
+                    results[q].status = r2;
+                    ++finished;
+                    ++next;
+                    continue;
+                }
+                break;
+            }
+            if (r2) {
+                results[q].status = r2;
+                ++finished;
+                ++next;
+                continue;
+            }
+            results[q].admit_s = now_s();
+            slot_req[slot] = q;
+            ++next;
+            if (reqs[q].steps == 0) {
+                results[q].status = 0;
+                results[q].done_s = results[q].admit_s;
+                vlasov_batch_release(b, slot);
+                slot_req[slot] = -1;
+                ++finished;
+            }
+        }
+        bool any_active = false;
+        for (auto& s : b->slots) any_active |= s.active;
+        if (any_active) {
+            // keep at most `depth` steps in flight
+            if (launched >= depth) {
+                const int e = (int)((launched - depth) % NE);
+                cudaEventSynchronize(ev[e]);
+            }
+            std::vector<int> was_active(b->S, 0);
+            for (int k = 0; k < b->S; ++k) was_active[k] = b->slots[k].active;
+            rc = vlasov_batch_step(b, 1);
+            if (rc) break;
+            const int e = (int)(launched % NE);
+            cudaEventRecord(ev[e], b->st);
+            ev_step[e] = launched;
+            for (int k = 0; k < b->S; ++k) {
+                if (was_active[k] && !b->slots[k].active) {
+                    // copy its last moment record (stream-ordered after the step) and drain
+                    Slot& s = b->slots[k];
+                    const int last = (s.steps_done - 1) % HIST_CAP;
+                    cudaMemcpyAsync(&hostrec[2 * k], P(b, s, s.L.hist) + sizeof(MomentRec) * last, sizeof(MomentRec),
+                                    cudaMemcpyDeviceToHost, b->st);
+                    cudaMemcpyAsync(&hostrec[2 * k + 1], P(b, s, s.L.hist), sizeof(MomentRec), cudaMemcpyDeviceToHost,
+                                    b->st);
+                    draining.push_back({k, slot_req[k], launched});
+                }
+            }
+            ++launched;
+        } else if (next < n) {
+            const double wait = reqs[order[next]].arrival_s - now_s();
+            if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
+        }
+        // retire drained slots whose last step has completed
+        for (size_t d = 0; d < draining.size();) {
+            const Draining& dr = draining[d];
+            const int e = (int)(dr.step_index % NE);
+            const bool recycled = ev_step[e] != dr.step_index;
+            if (recycled || cudaEventQuery(ev[e]) == cudaSuccess) {
+                if (recycled) cudaStreamSynchronize(b->st);
+                else cudaEventSynchronize(ev[e]);
+                cudaStreamSynchronize(b->st);   // the record copies were enqueued after the event
+                vlasov_result& out = results[dr.req];
+                float ms = 0.f;
+                if (!recycled) cudaEventElapsedTime(&ms, ev0, ev[e]);
+                else ms = (float)(now_s() * 1e3);
+                out.done_s = ms * 1e-3;
+                out.status = 0;
+                out.steps = b->slots[dr.slot].steps_done;
+                const MomentRec* m2[2] = {&hostrec[2 * dr.slot], &hostrec[2 * dr.slot + 1]};
+                vlasov_moments_t* dst[2] = {&out.last, &out.first};
+                for (int z = 0; z < 2; ++z) {
+                    dst[z]->t = m2[z]->t;
+                    dst[z]->mass = m2[z]->mass;
+                    dst[z]->Mx = m2[z]->Mx;
+                    dst[z]->My = m2[z]->My;
+                    dst[z]->kinetic = m2[z]->kinetic;
+                    dst[z]->potential = m2[z]->potential;
+                    dst[z]->energy = m2[z]->energy;
+                    dst[z]->step = m2[z]->step;
+                }
+                vlasov_batch_release(b, dr.slot);
+                slot_req[dr.slot] = -1;
+                ++finished;
+                draining.erase(draining.begin() + (long)d);
+            } else {
+                ++d;
+            }
+        }
+    }
+    cudaStreamSynchronize(b->st);
+    if (makespan_s) *makespan_s = now_s();
+    cleanup();
+    return rc;
+}
+
+}  // extern "C"

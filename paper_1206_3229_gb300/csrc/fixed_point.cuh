@@ -91,6 +91,26 @@ __host__ __device__ __forceinline__ double fx128_to_f64(i128 v, int k)
     return f64_from_bits(bits);
 }
 
+// round(x * 2^k) for a float (integer instructions only); |x| * 2^k < 2^126.
+__host__ __device__ __forceinline__ i128 fx128_from_f32(float x, int k)
+{
+#ifdef __CUDA_ARCH__
+    const uint32_t b = (uint32_t)__float_as_int(x);
+#else
+    uint32_t b;
+    __builtin_memcpy(&b, &x, 4);
+#endif
+    const int e = (int)((b >> 23) & 0xFF);
+    if (e == 0 || e == 0xFF) return 0;
+    const uint64_t m = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = e - 150 + k;
+    u128 v;
+    if (sh >= 0) v = sh > 102 ? (((u128)1 << 126) - 1) : ((u128)m << sh);
+    else if (sh > -64) v = (u128)((m >> (-sh)) + ((m >> (-sh - 1)) & 1ull));
+    else v = 0;
+    return (b >> 31) ? -(i128)v : (i128)v;
+}
+
 __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int o)
 {
     const uint64_t lo = (uint64_t)v, hi = (uint64_t)((u128)v >> 64);

@@ -122,7 +122,7 @@ __device__ __forceinline__ void xshift_row(const T* __restrict__ rowbuf, T* __re
 }
 
 template <typename T, bool PERIODIC, bool KIN>
-__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
+__device__ __forceinline__ void xshift_body(const XShiftArgs& a)
 {
     constexpr int V = VecOf<T>::V;
     using acc_t = typename VecOf<T>::acc;
@@ -288,6 +288,24 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
     }
 }
 
+template <typename T, bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
+{
+    xshift_body<T, PERIODIC, KIN>(a);
+}
+
+// Batched form: blockIdx.y selects the grid (slot); args[slot * 2 + ver[slot]] are its arguments
+// for the buffer parity it is at.  Slots with Np = 0 (free, or another boundary kind) exit.
+template <typename T, bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_batch_kernel(const XShiftArgs* __restrict__ args,
+                                                                          const int* __restrict__ ver)
+{
+    const int slot = blockIdx.y;
+    const XShiftArgs a = args[slot * 2 + ver[slot]];
+    if (a.Np <= 0 || (int)blockIdx.x >= a.Np) return;
+    xshift_body<T, PERIODIC, KIN>(a);
+}
+
 int xshift_max_cols(int elem_bytes, int threads)
 {
     const int V = 16 / elem_bytes;
@@ -324,7 +342,7 @@ cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int
 
 // ============================================================================ p-shift
 template <typename T, bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
+__device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const PShiftArgs& a)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
@@ -346,7 +364,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_c
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_barrier_init();
-        prefetch_tensormap(&tmap);
+        prefetch_tensormap(tmap_ptr);
     }
     __syncthreads();
 
@@ -356,7 +374,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_c
         if (t.smem_ok) {
             mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(T)));
             for (int q = 0; q < t.nb; ++q)
-                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, &tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
+                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap_ptr, t.i0, t.r0 + q * PS_BH, &bars[b]);
         } else {
             mbar_arrive_expect_tx(&bars[b], 0u);
         }
@@ -438,6 +456,25 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_c
     }
 }
 
+template <typename T, bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
+{
+    pshift_body<T, PPER>(&tmap, a);
+}
+
+// Batched form: tensor maps and arguments of each slot, per buffer parity, in global memory.
+template <typename T, bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_batch_kernel(const CUtensorMap* __restrict__ tmaps,
+                                                                         const PShiftArgs* __restrict__ args,
+                                                                         const int* __restrict__ ver)
+{
+    const int slot = blockIdx.y;
+    const int k = slot * 2 + ver[slot];
+    const PShiftArgs a = args[k];
+    if (a.Np <= 0) return;
+    pshift_body<T, PPER>(tmaps + k, a);
+}
+
 size_t pshift_smem_bytes(int elem_bytes)
 {
     return 256 + 2 * (size_t)PS_RB * PS_TW * (size_t)elem_bytes;
@@ -456,6 +493,28 @@ cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUten
 {
     if (elem_bytes == 8) return p_periodic ? launch_p<double, true>(grid, tmap, a, st) : launch_p<double, false>(grid, tmap, a, st);
     return p_periodic ? launch_p<float, true>(grid, tmap, a, st) : launch_p<float, false>(grid, tmap, a, st);
+}
+
+cudaError_t launch_xshift_batch(bool periodic, bool kin, int slots, int ctas_per_slot, size_t smem,
+                                const XShiftArgs* args, const int* ver, cudaStream_t st)
+{
+    const dim3 grid(ctas_per_slot, slots);
+    if (periodic) {
+        if (kin) xshift_batch_kernel<float, true, true><<<grid, XS_THREADS_MIN, smem, st>>>(args, ver);
+        else xshift_batch_kernel<float, true, false><<<grid, XS_THREADS_MIN, smem, st>>>(args, ver);
+    } else {
+        if (kin) xshift_batch_kernel<float, false, true><<<grid, XS_THREADS_MIN, smem, st>>>(args, ver);
+        else xshift_batch_kernel<float, false, false><<<grid, XS_THREADS_MIN, smem, st>>>(args, ver);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pshift_batch(int slots, int ctas_per_slot, const CUtensorMap* tmaps, const PShiftArgs* args,
+                                const int* ver, cudaStream_t st)
+{
+    const dim3 grid(ctas_per_slot, slots);
+    pshift_batch_kernel<float, false><<<grid, PS_TW * PS_RG, pshift_smem_bytes(4), st>>>(tmaps, args, ver);
+    return cudaGetLastError();
 }
 
 // Opt every shift kernel into the shared memory it may use (called once per device, before any
@@ -477,6 +536,11 @@ cudaError_t set_kernel_attributes(int max_smem)
     VL_ATTR((pshift_kernel<double, false>));
     VL_ATTR((pshift_kernel<float, true>));
     VL_ATTR((pshift_kernel<float, false>));
+    VL_ATTR((xshift_batch_kernel<float, true, true>));
+    VL_ATTR((xshift_batch_kernel<float, true, false>));
+    VL_ATTR((xshift_batch_kernel<float, false, true>));
+    VL_ATTR((xshift_batch_kernel<float, false, false>));
+    VL_ATTR((pshift_batch_kernel<float, false>));
 #undef VL_ATTR
     return e;
 }

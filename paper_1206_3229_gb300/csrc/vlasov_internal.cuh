@@ -243,6 +243,16 @@ cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cu
 cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double* colpart, cudaStream_t st);
 
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st);
+
+// Batched forms (FP32 storage): grid.y = slot; per-slot arguments (two buffer parities for the
+// sweeps) live in device arrays, so one captured graph serves any set of occupied slots.
+cudaError_t launch_xshift_batch(bool periodic, bool kin, int slots, int ctas_per_slot, size_t smem,
+                                const XShiftArgs* args, const int* ver, cudaStream_t st);
+cudaError_t launch_pshift_batch(int slots, int ctas_per_slot, const CUtensorMap* tmaps, const PShiftArgs* args,
+                                const int* ver, cudaStream_t st);
+cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColReduceArgs* args, cudaStream_t st);
+cudaError_t launch_ring_batch(int slots, int max_n, const RingArgs* args, cudaStream_t st);
+cudaError_t launch_pparams_batch(int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);

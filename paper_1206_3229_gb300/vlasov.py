@@ -24,7 +24,9 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ERANGE = 0, -1, -2, -3, -4, -5, -6
 EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_f", "vlasov_get_f_device",
             "vlasov_step", "vlasov_moments", "vlasov_substep", "vlasov_density_force", "vlasov_sync",
             "vlasov_destroy", "vlasov_last_error", "vlasov_kernels_per_step", "vlasov_step_timed",
-            "vlasov_xshift_density_noalloc")
+            "vlasov_xshift_density_noalloc", "vlasov_batch_create", "vlasov_batch_footprint",
+            "vlasov_batch_admit", "vlasov_batch_step", "vlasov_batch_slot_steps", "vlasov_batch_get",
+            "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve")
 
 
 class VlasovError(RuntimeError):
@@ -48,6 +50,109 @@ class Moments(ctypes.Structure):
 
 
 MOMENT_FIELDS = ("t", "mass", "Mx", "My", "kinetic", "potential", "energy")
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("Nx", ctypes.c_int), ("Np", ctypes.c_int),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double), ("pmin", ctypes.c_double),
+                ("pmax", ctypes.c_double), ("x_periodic", ctypes.c_int), ("eps", ctypes.c_double),
+                ("G", ctypes.c_double), ("dt", ctypes.c_double), ("init", ctypes.c_int), ("x0", ctypes.c_double),
+                ("p0", ctypes.c_double), ("noise", ctypes.c_double), ("amp", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("steps", ctypes.c_int), ("arrival_s", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps", ctypes.c_int), ("arrival_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("last", Moments), ("first", Moments)]
+
+
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_n", ctypes.c_int), ("mem_budget_bytes", ctypes.c_longlong),
+                ("max_inflight", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+def request_from_workload(w: Workload, steps: int | None = None, arrival_s: float = 0.0) -> Request:
+    """Batched-form request for a workload description (FP32 storage; p always zero outside)."""
+    return Request(MODELS[w.model], w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, int(w.x_periodic), w.eps, w.G,
+                   w.dt, 0 if w.init == "box" else 1, w.x0, w.p0, w.noise, w.mode_amp, w.seed,
+                   int(w.steps if steps is None else steps), float(arrival_s))
+
+
+def moments_row(m: Moments) -> list[float]:
+    return [getattr(m, f) for f in MOMENT_FIELDS] + [m.step]
+
+
+class Batch:
+    """vlasov_batch_*: many simulations advanced by one launch per sub-step."""
+
+    def __init__(self, slots: int, max_n: int, mem_budget_bytes: int, stream: int | None = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.vlasov_batch_create(int(slots), int(max_n), int(mem_budget_bytes),
+                                       ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self._h, self._lib = h, lib
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vlasov_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def admit(self, req: Request, f0: np.ndarray | None = None) -> int:
+        slot = ctypes.c_int(-1)
+        if f0 is not None:
+            f0 = np.ascontiguousarray(f0, dtype=np.float64)
+            assert f0.size == req.Nx * req.Np
+        _check(self._lib.vlasov_batch_admit(self._h, ctypes.byref(req), _dptr(f0) if f0 is not None else None,
+                                            ctypes.byref(slot)))
+        return slot.value
+
+    def step(self, n: int = 1):
+        _check(self._lib.vlasov_batch_step(self._h, int(n)))
+
+    def steps_done(self, slot: int) -> int:
+        v = ctypes.c_int(0)
+        _check(self._lib.vlasov_batch_slot_steps(self._h, int(slot), ctypes.byref(v)))
+        return v.value
+
+    def get(self, slot: int, nx: int, np_: int, max_records: int = 4096):
+        f = np.empty((np_, nx), dtype=np.float64)
+        buf = (Moments * max(max_records, 1))()
+        cnt = ctypes.c_int(0)
+        _check(self._lib.vlasov_batch_get(self._h, int(slot), _dptr(f), buf, int(max_records), ctypes.byref(cnt)))
+        m = np.array([moments_row(buf[k]) for k in range(cnt.value)], dtype=np.float64).reshape(-1, 8)
+        return f, m
+
+    def release(self, slot: int):
+        _check(self._lib.vlasov_batch_release(self._h, int(slot)))
+
+
+def batch_footprint(req: Request) -> int:
+    return int(load().vlasov_batch_footprint(ctypes.byref(req)))
+
+
+def serve(reqs: list[Request], slots: int, mem_budget_bytes: int, max_n: int = 0, max_inflight: int = 4,
+          stream: int | None = None):
+    """vlasov_serve: continuous batching of a request stream.  Returns (results, makespan_s)."""
+    lib = load()
+    arr = (Request * len(reqs))(*reqs)
+    res = (Result * max(len(reqs), 1))()
+    opt = ServeOptions(int(slots), int(max_n), int(mem_budget_bytes), int(max_inflight),
+                       ctypes.c_void_p(stream) if stream else None)
+    mk = ctypes.c_double(0.0)
+    _check(lib.vlasov_serve(arr, len(reqs), ctypes.byref(opt), res, ctypes.byref(mk)))
+    return [res[k] for k in range(len(reqs))], mk.value
 
 _lib = None
 _lock = threading.Lock()
@@ -88,9 +193,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_step_timed.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_xshift_density_noalloc.argtypes = [vp, vp, vp, ip, ip, ctypes.c_double, ctypes.c_double, ip,
                                                       vp, vp]
+        lib.vlasov_batch_create.argtypes = [ip, ip, ctypes.c_longlong, vp, ctypes.POINTER(vp)]
+        lib.vlasov_batch_footprint.argtypes = [ctypes.POINTER(Request)]
+        lib.vlasov_batch_admit.argtypes = [vp, ctypes.POINTER(Request), dp, ctypes.POINTER(ctypes.c_int)]
+        lib.vlasov_batch_step.argtypes = [vp, ip]
+        lib.vlasov_batch_slot_steps.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
+        lib.vlasov_batch_get.argtypes = [vp, ip, dp, ctypes.POINTER(Moments), ip, ctypes.POINTER(ctypes.c_int)]
+        lib.vlasov_batch_release.argtypes = [vp, ip]
+        lib.vlasov_batch_destroy.argtypes = [vp]
+        lib.vlasov_batch_destroy.restype = None
+        lib.vlasov_serve.argtypes = [ctypes.POINTER(Request), ip, ctypes.POINTER(ServeOptions),
+                                     ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTED:
-            if name not in ("vlasov_destroy", "vlasov_last_error"):
+            if name not in ("vlasov_destroy", "vlasov_last_error", "vlasov_batch_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
+        lib.vlasov_batch_footprint.restype = ctypes.c_longlong
         _lib = lib
         return lib
 

@@ -1,0 +1,148 @@
+"""Batched form (many simulations per launch) and the continuous-batching serving loop (GPU).
+
+* A simulation gives bit-identical results alone in a batch and in a mix of other models, sizes
+  and admission times (its own fixed CTA-to-row mapping; order-free integer moment sums).
+* It agrees with the single-grid FP32 path and with the FP64 oracle within the FP32 tolerance.
+* The device-side initial state equals the shared input generator's.
+* The serving loop admits by arrival time, slots and memory, and reproduces the alone-results.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1206_3229_gb300 import inputs as I
+from paper_1206_3229_gb300 import vlasov as V
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+def grid_of(w):
+    return O.Grid(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.x_periodic, w.p_periodic, w.dt, w.eps, w.G)
+
+
+HMF_R = I.HMF_256
+MIX = [
+    I.RING_2048.resized(128, 128),
+    I.SHEET_4096.resized(256, 256),
+    I.HMF_4096_UNSTABLE.resized(512, 256),
+    I.RING_2048.resized(256, 192),
+]
+
+
+def run_alone(w, steps, slots=4):
+    with V.Batch(slots, 512, GB) as b:
+        k = b.admit(V.request_from_workload(w, steps))
+        b.step(steps + 3)
+        assert b.steps_done(k) == steps
+        return b.get(k, w.nx, w.np)
+
+
+def test_alone_equals_in_mix_bitwise():
+    steps = 30
+    f_a, m_a = run_alone(HMF_R, steps)
+    with V.Batch(8, 512, 2 * GB) as b:
+        others = [b.admit(V.request_from_workload(w, 7 + 5 * q)) for q, w in enumerate(MIX[:3])]
+        b.step(5)
+        k = b.admit(V.request_from_workload(HMF_R, steps))
+        b.step(2)
+        late = b.admit(V.request_from_workload(MIX[3], 12))
+        b.step(steps + 5)
+        f_b, m_b = b.get(k, HMF_R.nx, HMF_R.np)
+        assert b.steps_done(k) == steps and b.steps_done(late) == 12
+        assert all(b.steps_done(o) == 7 + 5 * q for q, o in enumerate(others))
+    assert np.array_equal(f_a, f_b)
+    assert np.array_equal(m_a, m_b)
+    assert m_a.shape == (steps, 8)
+
+
+def test_batch_matches_single_grid_f32_path():
+    w = HMF_R
+    steps = 40
+    f0 = I.initial_state(w)
+    with V.Batch(2, 256, GB) as b:
+        k = b.admit(V.request_from_workload(w, steps), f0)
+        b.step(steps)
+        fb, mb = b.get(k, w.nx, w.np)
+    with V.Sim.from_workload(w, precision="f32") as s:
+        s.set_f(f0)
+        s.step(steps)
+        ms = s.moments()
+        fs = s.get_f()
+    assert np.max(np.abs(fb - fs)) <= 1e-5 * fs.max()
+    assert np.max(np.abs(np.hypot(mb[:, 2], mb[:, 3]) - np.hypot(ms[:, 2], ms[:, 3]))) <= 1e-6
+
+
+def test_batch_fp32_against_oracle_magnetisation():
+    w = HMF_R
+    steps = 100
+    f0 = I.initial_state(w)
+    _, mo = O.run(grid_of(w), f0, steps)
+    with V.Batch(2, 256, GB) as b:
+        k = b.admit(V.request_from_workload(w, steps), f0)
+        b.step(steps)
+        _, mb = b.get(k, w.nx, w.np)
+    dM = np.abs(np.hypot(mb[:, 2], mb[:, 3]) - np.hypot(mo[:, 2], mo[:, 3]))
+    assert dM.max() <= 1e-5
+    assert np.max(np.abs(mb[:, 1] - 1.0)) <= 1e-5
+
+
+@pytest.mark.parametrize("w", [I.HMF_256, I.RING_2048.resized(256, 128), I.SHEET_4096.resized(256, 256),
+                               I.HMF_4096_UNSTABLE.resized(128, 256)], ids=lambda w: w.name)
+def test_device_initial_state_matches_input_generator(w):
+    with V.Batch(1, 256, GB) as b:
+        k = b.admit(V.request_from_workload(w, 0))
+        f, _ = b.get(k, w.nx, w.np)
+    ref = I.initial_state(w)
+    assert np.max(np.abs(f - ref)) <= 2e-6 * ref.max()
+
+
+def test_serve_stream_reproduces_alone_results():
+    rng = np.random.default_rng(11)
+    pool = [I.HMF_256, I.RING_2048.resized(128, 128), I.SHEET_4096.resized(256, 256),
+            I.HMF_4096_UNSTABLE.resized(256, 256)]
+    reqs, ws = [], []
+    t = 0.0
+    for q in range(10):
+        w = pool[q % len(pool)]
+        steps = int(rng.integers(5, 25))
+        t += float(rng.exponential(0.01))
+        reqs.append(V.request_from_workload(w, steps, arrival_s=t))
+        ws.append((w, steps))
+    budget = 3 * max(V.batch_footprint(r) for r in reqs)
+    results, makespan = V.serve(reqs, slots=4, mem_budget_bytes=budget, max_n=256)
+    assert makespan > 0
+    for (w, steps), r in zip(ws, results):
+        assert r.status == 0 and r.steps == steps
+        assert r.admit_s >= r.arrival_s - 1e-6 and r.done_s >= r.admit_s - 1e-3
+        _, m = run_alone(w, steps)
+        assert V.moments_row(r.last) == list(m[-1])
+        assert V.moments_row(r.first) == list(m[0])
+
+
+def test_serve_admission_waits_for_memory():
+    big = V.request_from_workload(I.HMF_4096_UNSTABLE.resized(512, 512), 20, arrival_s=0.0)
+    big2 = V.request_from_workload(I.HMF_4096_UNSTABLE.resized(512, 512), 20, arrival_s=0.0)
+    budget = int(1.5 * V.batch_footprint(big))
+    results, _ = V.serve([big, big2], slots=4, mem_budget_bytes=budget, max_n=512)
+    a, c = results
+    assert a.status == 0 and c.status == 0
+    first, second = (a, c) if a.admit_s <= c.admit_s else (c, a)
+    assert second.admit_s >= first.done_s - 1e-3   # only one fits at a time
+
+
+def test_batch_rejects_bad_requests():
+    with V.Batch(1, 256, GB) as b:
+        bad = V.request_from_workload(I.HMF_256.resized(512), 1)
+        with pytest.raises(V.VlasovError) as ei:
+            b.admit(bad)
+        assert ei.value.code == V.EINVAL
+        k = b.admit(V.request_from_workload(I.HMF_256, 1))
+        with pytest.raises(V.VlasovError) as ei:
+            b.admit(V.request_from_workload(I.HMF_256, 1))
+        assert ei.value.code == V.ESTATE
+        b.release(k)
+        b.admit(V.request_from_workload(I.HMF_256, 1))
