@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -129,6 +130,70 @@ def cpu_oracle_timing(w: I.Workload, f0: np.ndarray, budget_s: float, max_steps:
                       f"in {elapsed:.2f} s"}
 
 
+def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int) -> dict:
+    """The seeded 512-request serving stream (FP32 batched form, continuous batching).
+
+    Offered load is set to 80% of a capacity measured in the same run on a short calibration burst.
+    Reports aggregate cell-updates/s over the makespan, p50/p99 time-to-result (completion of the
+    last step on the GPU minus arrival), and the same requests' estimated time one at a time on the
+    single-grid FP64 path (per-step times measured here per model and grid size).
+    """
+    import torch
+    sizes = (256, 512, 1024, 2048)
+    cal = I.serving_stream(48, seed=55, sizes=sizes, step_scale=0.1, rate_per_s=1e9)
+    reqs = [V.request_from_workload(w, st, 0.0) for (w, st, _t) in cal]
+    _, mk = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle)
+    capacity = sum(w.cells * st for (w, st, _t) in cal) / mk
+    mean_work = float(np.mean([n * n for n in sizes])) * 1050.0
+    rate = 0.8 * capacity / mean_work
+    stream = I.serving_stream(512, seed=5, sizes=sizes, rate_per_s=rate)
+    reqs = [V.request_from_workload(w, st, t) for (w, st, t) in stream]
+    res, makespan = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle)
+    ok = [r.status == 0 for r in res]
+    work = sum(w.cells * st for (w, st, _t), good in zip(stream, ok) if good)
+    lat = np.array([r.done_s - r.arrival_s for r, good in zip(res, ok) if good])
+
+    # one-at-a-time FP64 single-grid estimate: measured step time per (model, N)
+    t_step = {}
+    for (w, st, _t) in stream:
+        key = (w.model, w.nx)
+        if key in t_step:
+            continue
+        sim = V.Sim.from_workload(w, precision="f64", stream=stream_handle)
+        sim.set_f(I.initial_state(w))
+        sim.step(3)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st_ = torch.cuda.ExternalStream(stream_handle) if stream_handle else torch.cuda.current_stream()
+        e0.record(st_)
+        sim.step(10)
+        e1.record(st_)
+        e1.synchronize()
+        t_step[key] = e0.elapsed_time(e1) * 1e-3 / 10
+        sim.close()
+    seq_time = sum(st * t_step[(w.model, w.nx)] for (w, st, _t), good in zip(stream, ok) if good)
+
+    # accuracy: a few finished requests re-run on the FP64 single-grid path from the same f0
+    dM = []
+    for q in [i for i, (w, st, _t) in enumerate(stream) if w.nx <= 1024][:4]:
+        w, st, _t = stream[q]
+        sim = V.Sim.from_workload(w, precision="f64", stream=stream_handle)
+        sim.set_f(I.initial_state(w))
+        sim.step(st)
+        m = sim.moments()
+        sim.close()
+        dM.append(abs(math.hypot(res[q].last.Mx, res[q].last.My) - math.hypot(m[-1, 2], m[-1, 3])))
+    return {"requests": len(reqs), "completed": int(sum(ok)), "slots": slots, "mem_budget_gb": budget_bytes / 2 ** 30,
+            "dtype": "f32 storage, FP64-accurate displacements and moment sums",
+            "aggregate_value": work / makespan, "unit": UNIT, "makespan_s": makespan,
+            "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "offered_load_of_capacity": 0.8, "capacity_calibration": capacity, "arrival_rate_per_s": rate,
+            "fp64_single_grid_sequential_value": work / seq_time if seq_time > 0 else None,
+            "speedup_vs_fp64_single_grid_sequential": seq_time / makespan if seq_time > 0 else None,
+            "max_abs_dM_vs_fp64_sampled": max(dM) if dM else None, "dM_samples": len(dM)}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -171,6 +236,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f32", action="store_true", help="skip the secondary measurements of the other storage modes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the batched serving-stream measurement")
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = workload_by_name(args.workload)
@@ -285,6 +353,10 @@ def main():
                             "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(s2.slot_names(), sl2)}}
             s2.close()
 
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = serving_benchmark(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_timing(w, f0, args.cpu_budget, 50)
@@ -307,7 +379,8 @@ def main():
                 "moments_last": {"t": float(hist[-1, 0]), "mass": float(hist[-1, 1]),
                                  "M": float(np.hypot(hist[-1, 2], hist[-1, 3])), "energy": float(hist[-1, 6])}
                 if len(hist) else None,
-                "other_precisions": others}
+                "other_precisions": others,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -121,3 +121,36 @@ def initial_state(w: Workload) -> np.ndarray:
         raise ValueError(f"unknown init {w.init!r}")
     mass = w.dx * w.dp * f.sum()
     return np.ascontiguousarray(f / mass)
+
+
+# Domains and time steps per model for the serving stream (those of the single-grid workloads).
+SERVING_DOMAINS = {
+    "hmf": dict(xmin=-PI, xmax=PI, pmin=-2.0, pmax=2.0, x_periodic=True, dt=0.05, eps=0.0, G=1.0),
+    "ring": dict(xmin=-PI, xmax=PI, pmin=-3.0, pmax=3.0, x_periodic=True, dt=0.05, eps=0.01, G=1.0),
+    "sheet": dict(xmin=-8.0, xmax=8.0, pmin=-4.0, pmax=4.0, x_periodic=False, dt=0.02, eps=0.0, G=1.0),
+}
+
+
+def serving_stream(n: int = 512, seed: int = 5, sizes=(256, 512, 1024, 2048), steps=(100, 2000),
+                   rate_per_s: float = 50.0, step_scale: float = 1.0):
+    """A seeded Poisson stream of simulation requests: model uniform over HMF/ring/sheet, square grid
+    uniform over `sizes`, waterbag half-widths x0 ~ U[0.5, pi], p0 ~ U[0.3, 1.5], noise 1e-4, steps
+    ~ U[steps] (times step_scale), exponential inter-arrival times of mean 1/rate_per_s.
+    Returns a list of (Workload, steps, arrival_s)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    models = ("hmf", "ring", "sheet")
+    for q in range(n):
+        m = models[int(rng.integers(0, 3))]
+        N = int(sizes[int(rng.integers(0, len(sizes)))])
+        x0 = float(rng.uniform(0.5, PI))
+        p0 = float(rng.uniform(0.3, 1.5))
+        st = max(1, int(round(int(rng.integers(steps[0], steps[1] + 1)) * step_scale)))
+        t += float(rng.exponential(1.0 / rate_per_s))
+        d = SERVING_DOMAINS[m]
+        w = Workload(f"req{q}_{m}_{N}", m, N, N, d["xmin"], d["xmax"], d["pmin"], d["pmax"], d["x_periodic"], False,
+                     d["dt"], st, eps=d["eps"], G=d["G"], init="box", x0=x0, p0=p0, noise=1e-4,
+                     seed=seed * 100000 + q)
+        out.append((w, st, t))
+    return out
