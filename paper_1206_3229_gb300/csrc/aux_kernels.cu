@@ -74,7 +74,13 @@ __device__ __forceinline__ void colreduce_body(const ColReduceArgs& a)
 
     // all loads of a thread are independent: issue them in batches of eight
     long long s = 0;
-    if (i < a.Nx) {
+    if (a.colacc) {
+        // exact column sums were added by the x-shift CTAs; take them and clear for the next sweep
+        if (grp == 0 && i < a.Nx) {
+            s = (long long)a.colacc[i];
+            a.colacc[i] = 0ull;
+        }
+    } else if (i < a.Nx) {
         const double* __restrict__ cp = a.colpart + i;
         const size_t st = (size_t)a.Nx * CR_GROUPS;
         int b = grp;

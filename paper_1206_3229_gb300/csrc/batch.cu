@@ -195,7 +195,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
 
 // ------------------------------------------------------------------------------------------- slot layout
 struct SlotLayout {
-    size_t f[2], xrec, pn0, pw, pgd, colpart, kinpart, rho, F, Qd, colfx, blockpart, ringpart, tickets, sc, hist,
+    size_t f[2], xrec, pn0, pw, pgd, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart, ringpart, tickets, sc, hist,
         dstep, err, costab, sintab, cosfx, sinfx, ringdV, ringV, rowv, colv, initpart, inv_mass, total;
 };
 
@@ -216,6 +216,7 @@ SlotLayout layout(int Nx, int Np)
     L.pw = take((size_t)NTAP * Nx * 4);
     L.pgd = take((size_t)2 * Nx * 4);
     L.colpart = take((size_t)B_CTAS_X * Nx * 8);
+    L.colacc = take((size_t)Nx * 8);
     L.kinpart = take((size_t)B_CTAS_X * 8);
     L.rho = take((size_t)Nx * 8);
     L.F = take((size_t)Nx * 8);
@@ -352,7 +353,9 @@ int fill_slot_args(vlasov_batch* b, int k)
                 a.n0 = nullptr;
                 a.w = nullptr;
                 a.gd = nullptr;
-                a.colpart = reinterpret_cast<double*>(P(b, s, s.L.colpart));
+                a.colpart = nullptr;
+                a.colacc = reinterpret_cast<unsigned long long*>(P(b, s, s.L.colacc));
+                a.k_col = s.k_col;
                 a.kinpart = step4 ? reinterpret_cast<double*>(P(b, s, s.L.kinpart)) : nullptr;
                 a.pmin = r.pmin;
                 a.dp = dp;
@@ -383,6 +386,7 @@ int fill_slot_args(vlasov_batch* b, int k)
     const int B = std::min(B_CTAS_X, Np);
     for (int q = 0; q < 2; ++q) {
         ColReduceArgs& c = b->cr[(size_t)q * b->S + k];
+        c.colacc = reinterpret_cast<unsigned long long*>(P(b, s, s.L.colacc));
         c.colpart = reinterpret_cast<const double*>(P(b, s, s.L.colpart));
         c.B = B;
         c.kinpart = q ? reinterpret_cast<const double*>(P(b, s, s.L.kinpart)) : nullptr;

@@ -43,17 +43,55 @@ __device__ __forceinline__ long long emul_fir(const EmulW& w, const int* kx, con
     return M + f32_to_ll_round(S);
 }
 
+constexpr int XE_V = 4;      // consecutive outputs per thread and chunk
+constexpr int PSE_RB = 192;  // staged rows per buffer of the emulated p-shift (two CTAs per SM)
+constexpr int XE_W = 14;     // window elements: V + 9 + alignment slack (even)
+constexpr int XE_MAXCH = 4;  // chunks per row per thread (Nx <= 4 * 4 * 256 = 4096)
+
+// XE_V consecutive outputs from the converted (kx, r) pairs starting at `src` (f_{k-4-A} ..):
+// input-stationary with separate chains for the integer part and the two FP32 residual sums.
+template <int A>
+__device__ __forceinline__ void emul_chunk(const int2* src, const EmulW& w, long long (&T)[XE_V])
+{
+    long long M[XE_V];
+    float Sa[XE_V], Sb[XE_V];
+#pragma unroll
+    for (int v = 0; v < XE_V; ++v) {
+        M[v] = 0;
+        Sa[v] = 0.f;
+        Sb[v] = 0.f;
+    }
+    const int4* q = reinterpret_cast<const int4*>(src);
+#pragma unroll
+    for (int h = 0; h < XE_W / 2; ++h) {
+        const int4 pr = q[h];
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            const int u = 2 * h + z;
+            const int kx = z ? pr.z : pr.x;
+            const float rr = __int_as_float(z ? pr.w : pr.y);
+            const float kf = __int2float_rn(kx);
+#pragma unroll
+            for (int v = 0; v < XE_V; ++v) {
+                const int t = u - A - v;
+                if (t >= 0 && t < NTAP) {
+                    M[v] = mad_wide(w.Wh[t], kx, M[v]);
+                    Sa[v] = fmaf(w.wl[t], kf, Sa[v]);
+                    Sb[v] = fmaf(w.wf[t], rr, Sb[v]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < XE_V; ++v) T[v] = M[v] + f32_to_ll_round(Sa[v] + Sb[v]);
+}
+
 // FP64 boundary correction (non-periodic axes): value of the zero-extended filter minus the
 // f'' terms at nodes outside [0, n).  x points at the ten window values (as doubles).
 __device__ __forceinline__ double emul_edge(double out, const double* x, int k, int n, double g, double d)
 {
     return edge_fix(out, x, k, n, g, d);
 }
-
-constexpr int XE_V = 4;      // consecutive outputs per thread and chunk
-constexpr int PSE_RB = 192;  // staged rows per buffer of the emulated p-shift (two CTAs per SM)
-constexpr int XE_W = 14;     // window elements: V + 9 + alignment slack (even)
-constexpr int XE_MAXCH = 4;  // chunks per row per thread (Nx <= 4 * 4 * 256 = 4096)
 
 // ============================================================================ x-shift (emulated FP64)
 template <bool PERIODIC, bool KIN>
@@ -163,27 +201,14 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                 if constexpr (PERIODIC) {
                     if (e >= Nx) e -= Nx;
                 }
-                int kx[XE_W];
-                float kf[XE_W], rr[XE_W];
-                const int4* q = reinterpret_cast<const int4*>(src + e);
-#pragma unroll
-                for (int u = 0; u < XE_W / 2; ++u) {
-                    const int4 v = q[u];
-                    kx[2 * u] = v.x;
-                    rr[2 * u] = __int_as_float(v.y);
-                    kx[2 * u + 1] = v.z;
-                    rr[2 * u + 1] = __int_as_float(v.w);
-                }
-#pragma unroll
-                for (int u = 0; u < XE_W; ++u) kf[u] = __int2float_rn(kx[u]);
+                long long Tv[XE_V];
+                if (A == 0) emul_chunk<0>(src + e, w, Tv);
+                else emul_chunk<1>(src + e, w, Tv);
                 double out[XE_V];
 #pragma unroll
                 for (int v = 0; v < XE_V; ++v) {
-                    long long T;
-                    if (A == 0) T = emul_fir(w, kx + v, kf + v, rr + v);
-                    else T = emul_fir(w, kx + v + 1, kf + v + 1, rr + v + 1);
-                    out[v] = emul_to_f64(T, em.Ef);
-                    const long long Tc = (T + 512) >> 10;
+                    out[v] = emul_to_f64(Tv[v], em.Ef);
+                    const long long Tc = (Tv[v] + 512) >> 10;
                     colacc[c][v] += Tc;
                     rowsum += Tc;
                 }
@@ -239,7 +264,22 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
         return;
     }
 
-    if (a.colpart) {
+    if (a.colacc) {
+        // exact fixed-point column sums, added across CTAs: units 2^(Ef-51) -> 2^-k_col
+        const int sh = a.k_col + em.Ef - 51;
+#pragma unroll
+        for (int c = 0; c < XE_MAXCH; ++c) {
+            const int i = XE_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XE_V; ++v) {
+                    const long long x = colacc[c][v];
+                    const long long q = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
+                }
+            }
+        }
+    } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll
         for (int c = 0; c < XE_MAXCH; ++c) {
@@ -364,20 +404,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
         }
         const int2* sb = reinterpret_cast<const int2*>(buf);
         const int base = jb + n0_i - 4 - t.r0;
-#pragma unroll
-        for (int u = 0; u < PS_RPT + 9; ++u) {
-            int kx;
-            float rr;
-            if (t.smem_ok) {
-                const int2 v = sb[(base + u) * PS_TW + lane];
-                kx = v.x;
-                rr = __int_as_float(v.y);
-            } else {
-                const double x = colvalid ? gload_p<double, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0.0;
-                const EmulElem v = emul_split(x, s_base, bad);
-                kx = v.kx;
-                rr = v.r;
-            }
+        auto feed = [&](int u, int kx, float rr) {
             const float kf = __int2float_rn(kx);
 #pragma unroll
             for (int tap = 0; tap < NTAP; ++tap) {
@@ -387,6 +414,20 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
                     Sacc[rw] = fmaf(w.wl[tap], kf, Sacc[rw]);
                     Sacc[rw] = fmaf(w.wf[tap], rr, Sacc[rw]);
                 }
+            }
+        };
+        if (t.smem_ok) {
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u) {
+                const int2 v = sb[(base + u) * PS_TW + lane];
+                feed(u, v.x, __int_as_float(v.y));
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u) {
+                const double x = colvalid ? gload_p<double, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0.0;
+                const EmulElem v = emul_split(x, s_base, bad);
+                feed(u, v.kx, v.r);
             }
         }
         bool any_edge = false;

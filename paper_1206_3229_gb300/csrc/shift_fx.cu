@@ -73,6 +73,45 @@ __device__ __forceinline__ long long fx_edge(const long long* X, const double* w
     return (long long)fx128_from_f64(out, 62 - Ef);
 }
 
+// Four consecutive outputs of one x row from the staged fixed-point values starting at `src`
+// (f_{k-4-A} .. ): input-stationary, each element split once and fed to the outputs it touches;
+// separate chains for the integer part and the two FP32 residual sums keep dependencies short.
+template <int A>
+__device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, long long (&out)[XF_V], bool& bad)
+{
+    long long M[XF_V];
+    float Sa[XF_V], Sb[XF_V];
+#pragma unroll
+    for (int v = 0; v < XF_V; ++v) {
+        M[v] = 0;
+        Sa[v] = 0.f;
+        Sb[v] = 0.f;
+    }
+    const longlong2* q = reinterpret_cast<const longlong2*>(src);
+#pragma unroll
+    for (int h = 0; h < XF_W / 2; ++h) {
+        const longlong2 pr = q[h];
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            const int u = 2 * h + z;
+            int kx;
+            float kf, rf;
+            fx_split(z ? pr.y : pr.x, kx, kf, rf);
+#pragma unroll
+            for (int v = 0; v < XF_V; ++v) {
+                const int t = u - A - v;   // tap of element u for output v
+                if (t >= 0 && t < NTAP) {
+                    M[v] = mad_wide(w.Wh[t], kx, M[v]);
+                    Sa[v] = fmaf(w.wl[t], kf, Sa[v]);
+                    Sb[v] = fmaf(w.wr[t], rf, Sb[v]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < XF_V; ++v) out[v] = fx_store(M[v] + f32_to_ll_round(Sa[v] + Sb[v]), bad);
+}
+
 }  // namespace
 
 // ============================================================================ x-shift (FX64)
@@ -172,21 +211,9 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
                     if constexpr (PERIODIC) {
                         if (e >= Nx) e -= Nx;
                     }
-                    int kx[XF_W];
-                    float kf[XF_W], rf[XF_W];
-                    const longlong2* q = reinterpret_cast<const longlong2*>(rowbuf + e);
-#pragma unroll
-                    for (int u = 0; u < XF_W / 2; ++u) {
-                        const longlong2 v = q[u];
-                        fx_split(v.x, kx[2 * u], kf[2 * u], rf[2 * u]);
-                        fx_split(v.y, kx[2 * u + 1], kf[2 * u + 1], rf[2 * u + 1]);
-                    }
                     long long out[XF_V];
-#pragma unroll
-                    for (int v = 0; v < XF_V; ++v) {
-                        const long long T = A == 0 ? fx_fir(w, kx + v, kf + v, rf + v) : fx_fir(w, kx + v + 1, kf + v + 1, rf + v + 1);
-                        out[v] = fx_store(T, bad);
-                    }
+                    if (A == 0) fx_chunk<0>(rowbuf + e, w, out, bad);
+                    else fx_chunk<1>(rowbuf + e, w, out, bad);
                     if constexpr (!PERIODIC) {
                         const int k = i + n0;
                         if (k < 0 || k + XF_V - 1 >= Nx - 1) {
@@ -242,7 +269,22 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
         return;
     }
 
-    if (a.colpart) {
+    if (a.colacc) {
+        // exact fixed-point column sums, added across CTAs: units 2^(Ef-51) -> 2^-k_col
+        const int sh = a.k_col + em.Ef - 51;
+#pragma unroll
+        for (int c = 0; c < XF_MAXCH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long x = colacc[c][v];
+                    const long long q = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
+                }
+            }
+        }
+    } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll
         for (int c = 0; c < XF_MAXCH; ++c) {
@@ -351,11 +393,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
                 M[rw] = 0;
                 Sacc[rw] = 0.f;
             }
-#pragma unroll
-            for (int u = 0; u < PS_RPT + 9; ++u) {
-                long long X;
-                if (t.smem_ok) X = buf[(base + u) * PS_TW + lane];
-                else X = colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll;
+            auto feed = [&](int u, long long X) {
                 int kx;
                 float kf, rf;
                 fx_split(X, kx, kf, rf);
@@ -368,6 +406,14 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
                         Sacc[rw] = fmaf(w.wr[tap], rf, Sacc[rw]);
                     }
                 }
+            };
+            if (t.smem_ok) {
+#pragma unroll
+                for (int u = 0; u < PS_RPT + 9; ++u) feed(u, buf[(base + u) * PS_TW + lane]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < PS_RPT + 9; ++u)
+                    feed(u, colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll);
             }
             bool any_edge = false;
 #pragma unroll

@@ -12,6 +12,7 @@
 //  of input rows it needs with 2-D TMA boxes (out-of-range rows come back as zeros, which is the
 //  f = 0 outside reading of the p axis), each thread walks 16 rows of one column with a sliding
 //  register window.
+#include "fixed_point.cuh"
 #include "ptx.cuh"
 #include "shift_common.cuh"
 #include "vlasov_internal.cuh"
@@ -263,7 +264,22 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
         return;
     }
 
-    if (a.colpart) {
+    if (a.colacc) {
+        // exact fixed-point column sums, added across CTAs (order-free)
+#pragma unroll
+        for (int c = 0; c < XS_MAXCH; ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    long long q;
+                    if constexpr (sizeof(acc_t) == 8) q = (long long)fx128_from_f64((double)colacc[c][v], a.k_col);
+                    else q = (long long)fx128_from_f32((float)colacc[c][v], a.k_col);
+                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
+                }
+            }
+        }
+    } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll
         for (int c = 0; c < XS_MAXCH; ++c) {

@@ -81,6 +81,7 @@ struct vlasov_sim {
     int xthreads = 256, xstages = 1, xpad = 16, xgrid = 1, pgrid = 1, crgrid = 1;
 
     double* colpart = nullptr;  // [xgrid][Nx]
+    unsigned long long* colacc = nullptr;  // [Nx] exact column sums added by the x-shift
     double* kinpart = nullptr;  // [xgrid]
     double* rho = nullptr;
     long long* colfx = nullptr; // [Nx] fixed-point column sums
@@ -238,7 +239,12 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.n0 = p.n0;
     a.w = p.w;
     a.gd = p.gd;
-    a.colpart = reduce ? s->colpart : nullptr;
+    // FP32 sweeps are memory-bound and many CTAs run them: per-CTA partial rows are cheaper there
+    // than atomics; the compute-bound 8-byte sweeps add exact column sums atomically at their end
+    const bool atomics = s->esz == 8;
+    a.colpart = (reduce && !atomics) ? s->colpart : nullptr;
+    a.colacc = (reduce && atomics) ? s->colacc : nullptr;
+    a.k_col = s->k_col;
     a.kinpart = kin ? s->kinpart : nullptr;
     a.pmin = s->pmin;
     a.dp = s->dp;
@@ -327,9 +333,10 @@ cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs&
     return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, s->st);
 }
 
-ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments)
+ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments, bool from_acc = true)
 {
     ColReduceArgs a;
+    a.colacc = (from_acc && s->esz == 8) ? s->colacc : nullptr;
     a.colpart = s->colpart;
     a.B = B;
     a.kinpart = kin ? s->kinpart : nullptr;
@@ -517,7 +524,7 @@ void vlasov_destroy(vlasov_sim* s)
     free_emul(s->xe);
     free_emul(s->pe);
     free_emul(s->se);
-    void* bufs[] = {s->colpart, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
+    void* bufs[] = {s->colpart, s->colacc, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
                     s->hist, s->dstep, s->err, s->xrec, s->srec};
     for (void* p : bufs) cudaFree(p);
@@ -652,6 +659,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     s->crgrid = (Nx + 31) / 32;
 
     CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->xgrid * Nx));
+    CTRY(cudaMalloc(&s->colacc, sizeof(unsigned long long) * (size_t)Nx));
+    CTRY(cudaMemsetAsync(s->colacc, 0, sizeof(unsigned long long) * (size_t)Nx, s->st));
     CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->xgrid));
     CTRY(cudaMalloc(&s->rho, sizeof(double) * Nx));
     CTRY(cudaMalloc(&s->colfx, sizeof(long long) * Nx));
@@ -880,7 +889,7 @@ int vlasov_density_force(vlasov_sim* s, double* host_rho, double* host_F)
     if (!s->has_f) return fail(VLASOV_ESTATE, "density before vlasov_set_f");
     if (s->fx) CU_TRY(launch_colsum_fx(static_cast<const long long*>(s->f[s->cur]), s->Nx, s->Np, s->Ef, s->colpart, s->st));
     else CU_TRY(launch_colsum(s->esz, s->f[s->cur], s->Nx, s->Np, s->colpart, 1, s->st));
-    CU_TRY(launch_colreduce(crargs(s, 1, false, false), s->crgrid, s->st));
+    CU_TRY(launch_colreduce(crargs(s, 1, false, false, false), s->crgrid, s->st));
     int rc = launch_force_params(s, s->Fout);
     if (rc) return rc;
     if (host_rho) CU_TRY(cudaMemcpyAsync(host_rho, s->rho, sizeof(double) * s->Nx, cudaMemcpyDeviceToHost, s->st));

@@ -105,6 +105,8 @@ struct XShiftArgs {
     const void* w;        // [10][Np] in T
     const void* gd;       // [2][Np] in T
     double* colpart;      // [gridDim.x][Nx] column sums of the output, or null
+    unsigned long long* colacc = nullptr;   // or: [Nx] exact int64 column sums (round(x 2^k_col)), atomically added
+    int k_col = 0;
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
     double pmin, dp;
     int* err;
@@ -139,7 +141,8 @@ struct PShiftArgs {
 };
 
 struct ColReduceArgs {
-    const double* colpart;   // [B][Nx] per-CTA column sums of f (x-shift epilogue)
+    unsigned long long* colacc;   // [Nx] int64 column sums added by the x-shift (read and cleared), or null
+    const double* colpart;   // else [B][Nx] per-CTA column sums of f
     int B;
     const double* kinpart;   // [B] per-CTA sum_j p_j^2/2 sum_i f, or null
     int Nx;
