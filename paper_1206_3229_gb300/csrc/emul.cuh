@@ -11,7 +11,7 @@
 //   x_t * 2^(31-Ef) = kx_t + r_t,  kx_t = floor (int32), r_t in (-1, 1) (float, 24 bits)
 //   w_t * 2^30      = Wh_t + wl_t, Wh_t = round (int32), |wl_t| <= 1/2 (float)
 //   out * 2^(61-Ef) = sum_t Wh_t kx_t                      exact, int64 (IMAD.WIDE)
-//                   + sum_t (wl_t kx_t + w_t 2^30 r_t)      FP32 FMAs
+//                   + sum_t (wl_t kx_t + w_t 2^30 r_t)      FP32 FMAs, rounded onto the int64 sum
 // and the int64 total is turned back into an FP64 value with integer instructions.  The error is
 // about 2^-49 of 2^Ef per sweep, the size of the rounding noise of an FP64 evaluation.  All
 // conversions read and build IEEE bit patterns directly.
@@ -74,19 +74,22 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long acc)
     return d;
 }
 
-// round(S) (ties away from zero) as int64 with integer instructions; |S| < 2^62.  (The hardware
-// float->int64 conversion issues on the FP64 pipe on this GPU.)
-__device__ __forceinline__ long long f32_to_ll_round(float S)
+// The FP32 part of the sum enters the int64 total without a conversion instruction (the hardware
+// float->int64 conversion issues on the FP64 pipe on this GPU).  The weights that feed the FP32
+// sums carry an extra factor 2^-EMUL_RS, so the FP32 sum S' = S 2^-EMUL_RS satisfies |S'| < 2^22
+// (|S| < 2^33.5 for any |x| < 2^Ef: ten |wl kx| <= 2^30 terms plus |w| 2^30 |r| summed over the
+// taps, sum |w| < 2).  Adding 1.5 * 2^23 then leaves round(S') in the low mantissa bits:
+//     bits(S' + 1.5 * 2^23) = 0x4B400000 + round(S')            (round to nearest even)
+// and one IMAD.WIDE adds 2^EMUL_RS * bits to an integer sum that started at EMUL_M0, which cancels
+// the constant.  The rounding step 2^EMUL_RS on the 2^(Ef-61) grid is below the FP32 rounding of S.
+constexpr int EMUL_RS = 12;
+constexpr float EMUL_MAGIC = 12582912.0f;                        // 1.5 * 2^23
+constexpr long long EMUL_M0 = -(1ll << EMUL_RS) * 0x4B400000ll;
+constexpr float EMUL_WSCALE = 2.2737367544323206e-13f;           // 2^-(30 + EMUL_RS)
+
+__device__ __forceinline__ long long emul_finish(long long M, float Sp)
 {
-    const uint32_t b = (uint32_t)__float_as_int(S);
-    const int e = (int)((b >> 23) & 0xFFu);
-    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
-    const int sh = e - 150;                      // |S| = m * 2^sh
-    long long v;
-    if (e < 126) v = 0;                          // |S| < 0.5
-    else if (sh >= 0) v = (long long)m << sh;
-    else v = (long long)((m + (1u << (-sh - 1))) >> (-sh));
-    return (b >> 31) ? -v : v;
+    return mad_wide(__float_as_int(Sp + EMUL_MAGIC), 1 << EMUL_RS, M);
 }
 
 // Value of an element in FP64 (for the rare boundary corrections).
@@ -113,8 +116,8 @@ __device__ __forceinline__ double emul_to_f64(long long T, int Ef)
     return __longlong_as_double((long long)bits);
 }
 
-// Filter weights in the emulated form.  Wh = round(w 2^30), wl = (w 2^30 - Wh) as float,
-// wf = w 2^30 as float.  Integer instructions only.
+// Filter weights in the emulated form.  Wh = round(w 2^30), wl = (w 2^30 - Wh) 2^-EMUL_RS as
+// float, wf = w 2^30 2^-EMUL_RS as float.  Integer instructions only.
 __host__ __device__ __forceinline__ void emul_weight(double w, int& Wh, float& wl, float& wf)
 {
 #ifdef __CUDA_ARCH__
@@ -143,11 +146,11 @@ __host__ __device__ __forceinline__ void emul_weight(double w, int& Wh, float& w
     const long long l = fx - (h << 30);
     Wh = (int)h;
 #ifdef __CUDA_ARCH__
-    wl = __ll2float_rn(l) * 9.313225746154785e-10f;   // * 2^-30
-    wf = __ll2float_rn(fx) * 9.313225746154785e-10f;  // round(w 2^60) rounded to float, * 2^-30
+    wl = __ll2float_rn(l) * EMUL_WSCALE;               // * 2^-30 * 2^-EMUL_RS
+    wf = __ll2float_rn(fx) * EMUL_WSCALE;              // round(w 2^60) rounded to float, same scale
 #else
-    wl = (float)l * 9.313225746154785e-10f;
-    wf = (float)fx * 9.313225746154785e-10f;
+    wl = (float)l * EMUL_WSCALE;
+    wf = (float)fx * EMUL_WSCALE;
 #endif
 }
 

@@ -29,19 +29,6 @@ struct EmulW {
     float wf[NTAP];
 };
 
-// One output from a window of ten elements (kx[t], kf[t] = (float)kx[t], r[t]).
-__device__ __forceinline__ long long emul_fir(const EmulW& w, const int* kx, const float* kf, const float* r)
-{
-    long long M = 0;
-    float S = 0.f;
-#pragma unroll
-    for (int t = 0; t < NTAP; ++t) {
-        M = mad_wide(w.Wh[t], kx[t], M);
-        S = fmaf(w.wl[t], kf[t], S);
-        S = fmaf(w.wf[t], r[t], S);
-    }
-    return M + f32_to_ll_round(S);
-}
 
 constexpr int XE_V = 4;      // consecutive outputs per thread and chunk
 constexpr int PSE_RB = 192;  // staged rows per buffer of the emulated p-shift (two CTAs per SM)
@@ -57,7 +44,7 @@ __device__ __forceinline__ void emul_chunk(const int2* src, const EmulW& w, long
     float Sa[XE_V], Sb[XE_V];
 #pragma unroll
     for (int v = 0; v < XE_V; ++v) {
-        M[v] = 0;
+        M[v] = EMUL_M0;
         Sa[v] = 0.f;
         Sb[v] = 0.f;
     }
@@ -83,7 +70,7 @@ __device__ __forceinline__ void emul_chunk(const int2* src, const EmulW& w, long
         }
     }
 #pragma unroll
-    for (int v = 0; v < XE_V; ++v) T[v] = M[v] + f32_to_ll_round(Sa[v] + Sb[v]);
+    for (int v = 0; v < XE_V; ++v) T[v] = emul_finish(M[v], Sa[v] + Sb[v]);
 }
 
 // FP64 boundary correction (non-periodic axes): value of the zero-extended filter minus the
@@ -399,7 +386,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
         float Sacc[PS_RPT];
 #pragma unroll
         for (int rw = 0; rw < PS_RPT; ++rw) {
-            M[rw] = 0;
+            M[rw] = EMUL_M0;
             Sacc[rw] = 0.f;
         }
         const int2* sb = reinterpret_cast<const int2*>(buf);
@@ -434,7 +421,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
 #pragma unroll
         for (int rw = 0; rw < PS_RPT; ++rw) {
             const int j = jb + rw;
-            const double out = emul_to_f64(M[rw] + f32_to_ll_round(Sacc[rw]), em.Ef);
+            const double out = emul_to_f64(emul_finish(M[rw], Sacc[rw]), em.Ef);
             bool edge = false;
             if constexpr (!PPER) {
                 const int kk = j + n0_i;

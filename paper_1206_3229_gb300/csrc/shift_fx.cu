@@ -37,19 +37,6 @@ __device__ __forceinline__ void fx_split(long long X, int& kx, float& kf, float&
     rf = __uint2float_rn(lo & 0x7FFFFFFFu);
 }
 
-__device__ __forceinline__ long long fx_fir(const FxW& w, const int* kx, const float* kf, const float* rf)
-{
-    long long M = 0;
-    float S = 0.f;
-#pragma unroll
-    for (int t = 0; t < NTAP; ++t) {
-        M = mad_wide(w.Wh[t], kx[t], M);
-        S = fmaf(w.wl[t], kf[t], S);
-        S = fmaf(w.wr[t], rf[t], S);
-    }
-    return M + f32_to_ll_round(S);
-}
-
 // Stored value of a filter result T (units 2^(Ef-61)); flags results outside |f| < 2^Ef.
 __device__ __forceinline__ long long fx_store(long long T, bool& bad)
 {
@@ -83,7 +70,7 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
     float Sa[XF_V], Sb[XF_V];
 #pragma unroll
     for (int v = 0; v < XF_V; ++v) {
-        M[v] = 0;
+        M[v] = EMUL_M0;
         Sa[v] = 0.f;
         Sb[v] = 0.f;
     }
@@ -109,7 +96,7 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
         }
     }
 #pragma unroll
-    for (int v = 0; v < XF_V; ++v) out[v] = fx_store(M[v] + f32_to_ll_round(Sa[v] + Sb[v]), bad);
+    for (int v = 0; v < XF_V; ++v) out[v] = fx_store(emul_finish(M[v], Sa[v] + Sb[v]), bad);
 }
 
 }  // namespace
@@ -390,7 +377,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
             float Sacc[PS_RPT];
 #pragma unroll
             for (int rw = 0; rw < PS_RPT; ++rw) {
-                M[rw] = 0;
+                M[rw] = EMUL_M0;
                 Sacc[rw] = 0.f;
             }
             auto feed = [&](int u, long long X) {
@@ -419,7 +406,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
 #pragma unroll
             for (int rw = 0; rw < PS_RPT; ++rw) {
                 const int j = jb + rw;
-                const long long out = fx_store(M[rw] + f32_to_ll_round(Sacc[rw]), bad);
+                const long long out = fx_store(emul_finish(M[rw], Sacc[rw]), bad);
                 bool edge = false;
                 if constexpr (!PPER) {
                     const int kk = j + n0_i;
