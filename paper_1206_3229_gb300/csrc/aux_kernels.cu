@@ -18,6 +18,7 @@ namespace vl {
 
 constexpr int CR_COLS = 32;      // columns per colreduce block
 constexpr int CR_GROUPS = 8;     // partial-row groups per block (blockDim = 256)
+constexpr int CR_ACC_THREADS = 1024;   // single-CTA reduction of exact column sums
 
 __device__ __forceinline__ i128 shfl_up_i128(i128 v, int o)
 {
@@ -56,6 +57,91 @@ __device__ i128 block_exclusive_scan_i128(i128 v, i128* sh, i128* total)
     __syncthreads();
     return r;
 }
+
+// Totals of one sweep in one CTA: per-thread partials m, x, y (mass, cos-, sin-weighted column
+// sums) are added exactly across the block, with the kinetic partials; then the sheet prefix scan,
+// the scalars and (after the second x-shift) the moment record.
+__device__ __forceinline__ void colreduce_final(const ColReduceArgs& a, i128 m, i128 x, i128 y, i128* red)
+{
+    const long long step0 = (threadIdx.x == 0 && a.final_moments) ? __ldcg(a.step) : 0;   // read early
+    i128 k = 0;
+    if (a.kinpart) {
+        double kv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = threadIdx.x + u * blockDim.x;
+            kv[u] = b < a.B ? __ldcg(&a.kinpart[b]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k += fx128_from_f64(kv[u], a.k_kin);
+        for (int b = threadIdx.x + 4 * blockDim.x; b < a.B; b += blockDim.x) k += fx128_from_f64(__ldcg(&a.kinpart[b]), a.k_kin);
+    }
+    {
+        __shared__ i128 red4[128];
+        block_sum4_i128(m, x, y, k, red4);
+    }
+
+    i128 U_acc = 0;
+    if (a.model == 2) {
+        // Sheet: C_i = sum_{k<i} s_k (exact); Q_i = 2 C_i + s_i - S gives F_i = -2 pi G dx dp Q_i.
+        const int nt = blockDim.x;
+        const int per = (a.Nx + nt - 1) / nt;
+        const int lo = min(a.Nx, (int)threadIdx.x * per), hi = min(a.Nx, lo + per);
+        i128 ls = 0, lx = 0;
+        for (int q = lo; q < hi; ++q) {
+            const long long v = __ldcg(&a.colfx[q]);
+            ls += v;
+            lx += (i128)q * v;
+        }
+        i128 S = 0, XS = 0;
+        i128 C = block_exclusive_scan_i128(ls, red, &S);
+        i128 X = block_exclusive_scan_i128(lx, red, &XS);
+        for (int q = lo; q < hi; ++q) {
+            const long long v = __ldcg(&a.colfx[q]);
+            a.Qd[q] = fx128_to_f64(2 * C + (i128)v - S, a.k_col);
+            if (a.final_moments) {
+                // U = 2 pi G dx^3 sum_i rho_i sum_{k<i} (i-k) rho_k
+                const double r = fx128_to_f64((i128)v, a.k_col);
+                const double wgt = fx128_to_f64((i128)q * C - X, a.k_col);
+                U_acc += fx128_from_f64(r * wgt, a.k_pot);
+            }
+            C += v;
+            X += (i128)q * v;
+        }
+        if (a.final_moments) U_acc = block_sum_i128(U_acc, red);
+    }
+
+    if (threadIdx.x == 0) {
+        const double mass = a.dxdp * fx128_to_f64(m, a.k_col);
+        const double Mx = a.dxdp * fx128_to_f64(x, a.k_col + 30);
+        const double My = a.dxdp * fx128_to_f64(y, a.k_col + 30);
+        const double kin = a.dxdp * fx128_to_f64(k, a.k_kin);
+        double U = 0.0;
+        if (a.model == 0) U = 0.5 * (mass * mass - Mx * Mx - My * My);
+        else if (a.model == 2 && a.final_moments) U = a.pot_scale * fx128_to_f64(U_acc, a.k_pot);
+        a.sc->mass = mass;
+        a.sc->Mx = Mx;
+        a.sc->My = My;
+        a.sc->kinetic = kin;
+        a.sc->potential = U;
+        if (a.final_moments && a.model != 1) {
+            const long long st = step0;
+            MomentRec rec;
+            rec.t = (double)(st + 1) * a.dt;
+            rec.mass = mass;
+            rec.Mx = Mx;
+            rec.My = My;
+            rec.kinetic = kin;
+            rec.potential = U;
+            rec.energy = kin + U;
+            rec.step = st + 1;
+            a.hist[st % HIST_CAP] = rec;
+            *a.step = st + 1;
+        }
+        *a.ticket = 0u;   // ready for the next launch
+    }
+}
+
 
 // ============================================================================ colreduce
 // Block: 32 columns x 8 groups over the B partial rows.  Each partial becomes an int64 on the
@@ -124,88 +210,49 @@ __device__ __forceinline__ void colreduce_body(const ColReduceArgs& a)
     __threadfence();
 
     // ---- last block: totals (exact, any order)
-    i128 m = 0, x = 0, y = 0, k = 0;
+    i128 m = 0, x = 0, y = 0;
     const volatile i128* vb = bp;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         m += vb[b * 3 + 0];
         x += vb[b * 3 + 1];
         y += vb[b * 3 + 2];
     }
-    if (a.kinpart) {
-        double kv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int b = threadIdx.x + u * blockDim.x;
-            kv[u] = b < a.B ? __ldcg(&a.kinpart[b]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) k += fx128_from_f64(kv[u], a.k_kin);
-        for (int b = threadIdx.x + 4 * blockDim.x; b < a.B; b += blockDim.x) k += fx128_from_f64(__ldcg(&a.kinpart[b]), a.k_kin);
-    }
-    m = block_sum_i128(m, red);
-    x = block_sum_i128(x, red);
-    y = block_sum_i128(y, red);
-    k = block_sum_i128(k, red);
+    colreduce_final(a, m, x, y, red);
+}
 
-    i128 U_acc = 0;
-    if (a.model == 2) {
-        // Sheet: C_i = sum_{k<i} s_k (exact); Q_i = 2 C_i + s_i - S gives F_i = -2 pi G dx dp Q_i.
-        const int nt = blockDim.x;
-        const int per = (a.Nx + nt - 1) / nt;
-        const int lo = min(a.Nx, (int)threadIdx.x * per), hi = min(a.Nx, lo + per);
-        i128 ls = 0, lx = 0;
-        for (int q = lo; q < hi; ++q) {
-            const long long v = __ldcg(&a.colfx[q]);
-            ls += v;
-            lx += (i128)q * v;
+// Single-CTA form for the exact int64 column sums the 8-byte x-shifts add with atomics: one pass
+// over the Nx columns (take, clear, density, cos/sin-weighted sums) and the totals, with no
+// second round of blocks.
+__device__ __forceinline__ void colreduce_acc_body(const ColReduceArgs& a)
+{
+    __shared__ i128 red[33];
+    i128 m = 0, x = 0, y = 0;
+    const i128 half = (i128)1 << 31;
+    constexpr int U = 4;   // all loads of a round are issued before any store (no aliasing stalls)
+    for (int i0 = threadIdx.x; i0 < a.Nx; i0 += U * blockDim.x) {
+        long long t[U], c[U], sn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            const bool in = i < a.Nx;
+            t[u] = in ? (long long)__ldcg(a.colacc + i) : 0ll;
+            c[u] = in ? __ldg(a.cosfx + i) : 0ll;
+            sn[u] = in ? __ldg(a.sinfx + i) : 0ll;
         }
-        i128 S = 0, XS = 0;
-        i128 C = block_exclusive_scan_i128(ls, red, &S);
-        i128 X = block_exclusive_scan_i128(lx, red, &XS);
-        for (int q = lo; q < hi; ++q) {
-            const long long v = __ldcg(&a.colfx[q]);
-            a.Qd[q] = fx128_to_f64(2 * C + (i128)v - S, a.k_col);
-            if (a.final_moments) {
-                // U = 2 pi G dx^3 sum_i rho_i sum_{k<i} (i-k) rho_k
-                const double r = fx128_to_f64((i128)v, a.k_col);
-                const double wgt = fx128_to_f64((i128)q * C - X, a.k_col);
-                U_acc += fx128_from_f64(r * wgt, a.k_pot);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < a.Nx) {
+                a.colacc[i] = 0ull;
+                if (a.model == 2) a.colfx[i] = t[u];                                   // sheet: prefix scan input
+                if (a.model == 1) a.rho[i] = a.dp * fx128_to_f64((i128)t[u], a.k_col);   // ring: convolution input
             }
-            C += v;
-            X += (i128)q * v;
+            m += (i128)t[u];
+            x += ((i128)c[u] * (i128)t[u] + half) >> 32;   // scale 2^-(k_col + 30)
+            y += ((i128)sn[u] * (i128)t[u] + half) >> 32;
         }
-        if (a.final_moments) U_acc = block_sum_i128(U_acc, red);
     }
-
-    if (threadIdx.x == 0) {
-        const double mass = a.dxdp * fx128_to_f64(m, a.k_col);
-        const double Mx = a.dxdp * fx128_to_f64(x, a.k_col + 30);
-        const double My = a.dxdp * fx128_to_f64(y, a.k_col + 30);
-        const double kin = a.dxdp * fx128_to_f64(k, a.k_kin);
-        double U = 0.0;
-        if (a.model == 0) U = 0.5 * (mass * mass - Mx * Mx - My * My);
-        else if (a.model == 2 && a.final_moments) U = a.pot_scale * fx128_to_f64(U_acc, a.k_pot);
-        a.sc->mass = mass;
-        a.sc->Mx = Mx;
-        a.sc->My = My;
-        a.sc->kinetic = kin;
-        a.sc->potential = U;
-        if (a.final_moments && a.model != 1) {
-            const long long st = *a.step;
-            MomentRec rec;
-            rec.t = (double)(st + 1) * a.dt;
-            rec.mass = mass;
-            rec.Mx = Mx;
-            rec.My = My;
-            rec.kinetic = kin;
-            rec.potential = U;
-            rec.energy = kin + U;
-            rec.step = st + 1;
-            a.hist[st % HIST_CAP] = rec;
-            *a.step = st + 1;
-        }
-        *a.ticket = 0u;   // ready for the next launch
-    }
+    colreduce_final(a, m, x, y, red);
 }
 
 __global__ void __launch_bounds__(256) colreduce_kernel(ColReduceArgs a)
@@ -220,9 +267,15 @@ __global__ void __launch_bounds__(256) colreduce_batch_kernel(const ColReduceArg
     colreduce_body(a);
 }
 
+__global__ void __launch_bounds__(CR_ACC_THREADS) colreduce_acc_kernel(ColReduceArgs a)
+{
+    colreduce_acc_body(a);
+}
+
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st)
 {
-    colreduce_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.colacc) colreduce_acc_kernel<<<1, CR_ACC_THREADS, 0, st>>>(a);
+    else colreduce_kernel<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -349,9 +402,76 @@ cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st)
 }
 
 // ============================================================================ p-shift parameters
-// Column i moves by sigma_i = F_i dt/dp cells.  The split of the foot (n0 = floor(-sigma),
-// beta = -sigma - n0) is FP64 always; the ten filter weights are FP64 for FP64 storage and FP32
-// for FP32 storage.
+// Column i moves by sigma_i = F_i dt/dp cells (FP64).  For FP64-class storage the split of the
+// foot (n0 = floor(-sigma), beta = -sigma - n0) and the ten filter weights are computed in 62-bit
+// fixed point; for FP32 storage the split is FP64 and the weights FP32.
+// FD coefficients of Eq. (findif) as round(c * 2^60): -205/72, 8/5, -1/5, 8/315, -1/560.
+constexpr long long FD60_C0 = -3282623728394494862ll;
+constexpr long long FD60_C1 = 1844674407370955162ll;
+constexpr long long FD60_C2 = -230584300921369395ll;
+constexpr long long FD60_C3 = 29280546148745320ll;
+constexpr long long FD60_C4 = -2058788401083655ll;
+
+// x * c for x on the 2^-62 grid and c on the 2^-60 grid, rounded onto the 2^-62 grid.
+__device__ __forceinline__ long long mul_fd60(long long x, long long c)
+{
+    return (long long)(((i128)x * (i128)c + ((i128)1 << 59)) >> 60);
+}
+
+// (x^3 - x) / 6 for x in [0, 1] on the 2^-62 grid (the spline's f'' coefficients).
+__device__ __forceinline__ long long spline_cubic62(uint64_t x)
+{
+    const uint64_t x2 = (uint64_t)(((u128)x * x) >> 62);
+    const uint64_t x3 = (uint64_t)(((u128)x2 * x) >> 62);
+    return ((long long)x3 - (long long)x) / 6;
+}
+
+// The split of the foot and the ten weights for FP64-class storage, in 62-bit fixed point.  Only
+// the force and sigma = F dt/dp are FP64 operations: dependent FP64 operations have a latency of
+// hundreds of cycles on this GPU, integer ones a few.  The weights are exact to 2^-61 (FP64
+// arithmetic: 2^-53 relative).
+__device__ __forceinline__ void pparams_fixed(const PParamsArgs& a, int i, double sigma)
+{
+    const i128 V = fx128_from_f64(-sigma, 62);                     // -sigma 2^62
+    const int n0 = (int)(long long)(V >> 62);                      // floor(-sigma)
+    const uint64_t be = (uint64_t)(V & (((i128)1 << 62) - 1));   // beta 2^62 in [0, 2^62)
+    const uint64_t al = (1ull << 62) - be;                         // alpha = 1 - beta
+    const long long g = spline_cubic62(al), d = spline_cubic62(be);
+    long long W[NTAP];
+    W[0] = mul_fd60(g, FD60_C4);
+    W[1] = mul_fd60(g, FD60_C3) + mul_fd60(d, FD60_C4);
+    W[2] = mul_fd60(g, FD60_C2) + mul_fd60(d, FD60_C3);
+    W[3] = mul_fd60(g, FD60_C1) + mul_fd60(d, FD60_C2);
+    W[4] = (long long)al + mul_fd60(g, FD60_C0) + mul_fd60(d, FD60_C1);
+    W[5] = (long long)be + mul_fd60(g, FD60_C1) + mul_fd60(d, FD60_C0);
+    W[6] = mul_fd60(g, FD60_C2) + mul_fd60(d, FD60_C1);
+    W[7] = mul_fd60(g, FD60_C3) + mul_fd60(d, FD60_C2);
+    W[8] = mul_fd60(g, FD60_C4) + mul_fd60(d, FD60_C3);
+    W[9] = mul_fd60(d, FD60_C4);
+    const size_t n = (size_t)a.Nx;
+    double* w = static_cast<double*>(a.w);
+    double* gd = static_cast<double*>(a.gd);
+    a.n0[i] = n0;
+#pragma unroll
+    for (int t = 0; t < NTAP; ++t) w[(size_t)t * n + i] = fx128_to_f64((i128)W[t], 62);
+    gd[i] = fx128_to_f64((i128)g, 62);
+    gd[n + i] = fx128_to_f64((i128)d, 62);
+    if (a.Wh) {
+        // Wh = round(w 2^30); wl = (w 2^30 - Wh) 2^-EMUL_RS; wf = w 2^30 2^-EMUL_RS (emul.cuh)
+        const float sc = EMUL_WSCALE * 0.25f;   // 2^-(32 + EMUL_RS): W is on the 2^-62 grid
+#pragma unroll
+        for (int t = 0; t < NTAP; ++t) {
+            const long long h = (W[t] + (1ll << 31)) >> 32;
+            const long long l = W[t] - (h << 32);                                   // |l| <= 2^31
+            const float lf = 2.f * __int2float_rn((int)(l >> 1)) + (float)(int)(l & 1);
+            const float wfull = fmaf(__int2float_rn((int)(W[t] >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)W[t]));
+            a.Wh[(size_t)t * n + i] = (int)h;
+            a.wl[(size_t)t * n + i] = lf * sc;
+            a.wf[(size_t)t * n + i] = wfull * sc;
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void pparams_body(const PParamsArgs& a)
 {
@@ -364,6 +484,10 @@ __device__ __forceinline__ void pparams_body(const PParamsArgs& a)
     else F = a.Fin[i];
     if (a.Fout) a.Fout[i] = F;
     const double sigma = F * a.cp;
+    if constexpr (sizeof(T) == 8) {
+        pparams_fixed(a, i, sigma);
+        return;
+    }
     const double ms = -sigma;
     const double fl = floor(ms);
     const double beta = ms - fl;
@@ -388,19 +512,6 @@ __device__ __forceinline__ void pparams_body(const PParamsArgs& a)
     w[9 * n + i] = d * c4;
     gd[i] = g;
     gd[n + i] = d;
-    if constexpr (sizeof(T) == 8) {
-        if (a.Wh) {
-#pragma unroll
-            for (int t = 0; t < NTAP; ++t) {
-                int h;
-                float l, f;
-                emul_weight((double)w[(size_t)t * n + i], h, l, f);
-                a.Wh[(size_t)t * n + i] = h;
-                a.wl[(size_t)t * n + i] = l;
-                a.wf[(size_t)t * n + i] = f;
-            }
-        }
-    }
 }
 
 template <typename T>

@@ -145,4 +145,48 @@ __device__ __forceinline__ i128 block_sum_i128(i128 v, i128* sh)
     return r;
 }
 
+// Exact block-wide sums of four values in one pass (one set of barriers); `sh` holds >= 128 entries.
+__device__ __forceinline__ void block_sum4_i128(i128& a, i128& b, i128& c, i128& d, i128* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += shfl_xor_i128(a, o);
+        b += shfl_xor_i128(b, o);
+        c += shfl_xor_i128(c, o);
+        d += shfl_xor_i128(d, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[wid] = a;
+        sh[32 + wid] = b;
+        sh[64 + wid] = c;
+        sh[96 + wid] = d;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        i128 ra = lane < nw ? sh[lane] : (i128)0, rb = lane < nw ? sh[32 + lane] : (i128)0;
+        i128 rc = lane < nw ? sh[64 + lane] : (i128)0, rd = lane < nw ? sh[96 + lane] : (i128)0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ra += shfl_xor_i128(ra, o);
+            rb += shfl_xor_i128(rb, o);
+            rc += shfl_xor_i128(rc, o);
+            rd += shfl_xor_i128(rd, o);
+        }
+        if (lane == 0) {
+            sh[0] = ra;
+            sh[32] = rb;
+            sh[64] = rc;
+            sh[96] = rd;
+        }
+    }
+    __syncthreads();
+    a = sh[0];
+    b = sh[32];
+    c = sh[64];
+    d = sh[96];
+    __syncthreads();
+}
+
 }  // namespace vl

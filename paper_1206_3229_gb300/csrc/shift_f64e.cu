@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int G = gridDim.x;
     const uint32_t row_bytes = (uint32_t)(Nx * 8);
-    const bool use_rec = a.rec != nullptr;
-    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + (use_rec ? XREC_BYTES : 0u);
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + XREC_BYTES;   // row + wrap + record
     const int s_base = 1044 + em.Ef;
     const double grid = ldexp(1.0, em.Ef - 31);
     bool bad = false;
@@ -125,8 +124,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
         if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
-        if (use_rec)
-            bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+        bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
                      XREC_BYTES, &bars[s]);
     };
     if (tid == 0) {
@@ -155,19 +153,19 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
             failed = true;
             break;
         }
-        const XRec* rc = use_rec ? reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES) : nullptr;
-        const int n0 = rc ? rc->n0 : em.n0[r];
+        const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
+        const int n0 = rc->n0;
         EmulW w;
 #pragma unroll
         for (int t = 0; t < NTAP; ++t) {
-            w.Wh[t] = rc ? rc->Wh[t] : em.Wh[(size_t)t * Np + r];
-            w.wl[t] = rc ? rc->wl[t] : em.wl[(size_t)t * Np + r];
-            w.wf[t] = rc ? rc->wf[t] : em.wf[(size_t)t * Np + r];
+            w.Wh[t] = rc->Wh[t];
+            w.wl[t] = rc->wl[t];
+            w.wf[t] = rc->wf[t];
         }
         double g = 0.0, d = 0.0;
         if constexpr (!PERIODIC) {
-            g = rc ? rc->g64 : em.gd[r];
-            d = rc ? rc->d64 : em.gd[Np + r];
+            g = rc->g64;
+            d = rc->d64;
         }
         const int A = (n0 - 4) & 1;
         int base;
@@ -193,12 +191,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                 else emul_chunk<1>(src + e, w, Tv);
                 double out[XE_V];
 #pragma unroll
-                for (int v = 0; v < XE_V; ++v) {
-                    out[v] = emul_to_f64(Tv[v], em.Ef);
-                    const long long Tc = (Tv[v] + 512) >> 10;
-                    colacc[c][v] += Tc;
-                    rowsum += Tc;
-                }
+                for (int v = 0; v < XE_V; ++v) out[v] = emul_to_f64(Tv[v], em.Ef);
                 if constexpr (!PERIODIC) {
                     const int k = i + n0;
                     if (k < 0 || k + XE_V - 1 >= Nx - 1) {
@@ -211,11 +204,18 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                             for (int t = 0; t < NTAP; ++t) {
                                 const int2 p = src[e + A + v + t];
                                 xv[t] = ((double)p.x + (double)__int_as_float(p.y)) * grid;
-                                acc = fma(rc ? rc->w64[t] : em.w64[(size_t)t * Np + r], xv[t], acc);
+                                acc = fma(rc->w64[t], xv[t], acc);
                             }
                             out[v] = emul_edge(acc, xv, k + v, Nx, g, d);
+                            Tv[v] = (long long)fx128_from_f64(out[v], 61 - em.Ef);   // sums see the corrected value
                         }
                     }
+                }
+#pragma unroll
+                for (int v = 0; v < XE_V; ++v) {
+                    const long long Tc = Tv[v] >> 10;   // units 2^(Ef-51), rounded down
+                    colacc[c][v] += Tc;
+                    rowsum += Tc;
                 }
                 double2* o = reinterpret_cast<double2*>(orow + i);
                 o[0] = make_double2(out[0], out[1]);
@@ -481,6 +481,7 @@ cudaError_t pshift_e_occupancy(int* blocks)
 cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                             cudaStream_t st)
 {
+    if (a.rec == nullptr) return cudaErrorInvalidValue;   // the per-row record is staged with each row
     const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, 8);
     if (periodic) {
         if (kin) xshift_e_kernel<true, true><<<grid, threads, smem, st>>>(a, em);

@@ -1,11 +1,11 @@
 // shift_fx.cu -- the two sweeps for 64-bit fixed-point storage (VLASOV_FX64).
 //
-// f is stored as X = round(f * 2^(62-Ef)) in int64 (|f| < 2^Ef, Ef = a bound four times the largest
-// uploaded |f|): the same 8 bytes per cell as FP64, an absolute resolution of 2^-60 of max|f|, and no
+// f is stored as X = round(f * 2^(61-Ef)) in int64 (|f| < 2^Ef, Ef = a bound four times the largest
+// uploaded |f|): the same 8 bytes per cell as FP64, an absolute resolution of 2^-59 of max|f|, and no
 // IEEE decoding.  Each staged element splits with two integer instructions into
-//   X = kx * 2^31 + rem,  kx = X >> 31 (int32), rem in [0, 2^31)
-// and the filter runs exactly as in the emulated-FP64 sweeps (emul.cuh): 10 IMAD.WIDE on kx, 20
-// FFMA on (float)kx and (float)rem; the int64 result T (units 2^(Ef-61)) is stored as 2T.  Data
+//   X = kx * 2^30 + rem,  kx = X >> 30 (int32), rem in [0, 2^30)
+// and the filter runs as in the emulated-FP64 sweeps (emul.cuh): 10 IMAD.WIDE on kx and 10 paired
+// FMAs (FFMA2) on ((float)kx, (float)rem); the int64 result T is already in storage units.  Data
 // movement is that of shift_kernels.cu: whole rows by 1-D bulk copies (x-shift), 2-D TMA column
 // tiles with zero fill (p-shift).
 #include "emul.cuh"
@@ -18,31 +18,31 @@ namespace vl {
 
 namespace {
 
-constexpr int XF_V = 4;       // consecutive outputs per thread and chunk
-constexpr int XF_W = 14;      // window elements: V + 9 + alignment slack (even)
-constexpr int XF_MAXCH = 4;   // chunks per row per thread (Nx <= 4096)
+constexpr int XF_V = 8;       // consecutive outputs per thread and chunk
+constexpr int XF_W = 18;      // window elements: V + 9 + alignment slack (even)
+constexpr int XF_MAXCH = 2;   // chunks per row per thread (Nx <= 8 * 256 * 2 = 4096)
 constexpr int PSF_RB = 192;   // staged rows per p-shift buffer (two CTAs per SM)
 
 struct FxW {
     int Wh[NTAP];
-    float wl[NTAP];
-    float wr[NTAP];   // w * 2^30 * 2^-31: multiplies (float)rem directly
+    float2 wlr[NTAP];   // (wl, w 2^30 2^-30): one paired FMA with (kf, (float)rem)
 };
 
 __device__ __forceinline__ void fx_split(long long X, int& kx, float& kf, float& rf)
 {
     const uint32_t lo = (uint32_t)X, hi = (uint32_t)((unsigned long long)X >> 32);
-    kx = (int)__funnelshift_r(lo, hi, 31);
+    kx = (int)__funnelshift_r(lo, hi, 30);
     kf = __int2float_rn(kx);
-    rf = __uint2float_rn(lo & 0x7FFFFFFFu);
+    rf = __uint2float_rn(lo & 0x3FFFFFFFu);
 }
 
-// Stored value of a filter result T (units 2^(Ef-61)); flags results outside |f| < 2^Ef.
-__device__ __forceinline__ long long fx_store(long long T, bool& bad)
+// Stored value of a filter result T (storage units).  Results outside |f| < 2^Ef (|T| >= 2^61) are
+// caught from the high word: hi + 2^29 < 2^30 for every valid T, so the OR of these over a CTA
+// stays below 2^30 unless one result was out of range.
+__device__ __forceinline__ long long fx_store(long long T, uint32_t& rng)
 {
-    const unsigned long long u = (unsigned long long)(T + (1ll << 61));
-    if (u >> 62) bad = true;
-    return T * 2;
+    rng |= (uint32_t)((unsigned long long)T >> 32) + (1u << 29);
+    return T;
 }
 
 // The rare boundary outputs of non-periodic axes, recomputed in FP64 from the fixed values.
@@ -57,22 +57,21 @@ __device__ __forceinline__ long long fx_edge(const long long* X, const double* w
         acc = fma(w64[(size_t)t * wstride], xv[t], acc);
     }
     const double out = edge_fix(acc, xv, k, n, g, d);
-    return (long long)fx128_from_f64(out, 62 - Ef);
+    return (long long)fx128_from_f64(out, FX_FRAC - Ef);
 }
 
-// Four consecutive outputs of one x row from the staged fixed-point values starting at `src`
-// (f_{k-4-A} .. ): input-stationary, each element split once and fed to the outputs it touches;
-// separate chains for the integer part and the two FP32 residual sums keep dependencies short.
+// XF_V consecutive outputs of one x row from the staged fixed-point values starting at `src`
+// (f_{k-4-A} .. ): input-stationary, each element split once and fed to the outputs it touches.
+// The two FP32 residual products of a tap go through one paired FMA (FFMA2).
 template <int A>
-__device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, long long (&out)[XF_V], bool& bad)
+__device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, long long (&out)[XF_V], uint32_t& rng)
 {
     long long M[XF_V];
-    float Sa[XF_V], Sb[XF_V];
+    float2 S[XF_V];
 #pragma unroll
     for (int v = 0; v < XF_V; ++v) {
         M[v] = EMUL_M0;
-        Sa[v] = 0.f;
-        Sb[v] = 0.f;
+        S[v] = make_float2(0.f, 0.f);
     }
     const longlong2* q = reinterpret_cast<const longlong2*>(src);
 #pragma unroll
@@ -84,19 +83,19 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
             int kx;
             float kf, rf;
             fx_split(z ? pr.y : pr.x, kx, kf, rf);
+            const float2 x2 = make_float2(kf, rf);
 #pragma unroll
             for (int v = 0; v < XF_V; ++v) {
                 const int t = u - A - v;   // tap of element u for output v
                 if (t >= 0 && t < NTAP) {
                     M[v] = mad_wide(w.Wh[t], kx, M[v]);
-                    Sa[v] = fmaf(w.wl[t], kf, Sa[v]);
-                    Sb[v] = fmaf(w.wr[t], rf, Sb[v]);
+                    S[v] = __ffma2_rn(w.wlr[t], x2, S[v]);
                 }
             }
         }
     }
 #pragma unroll
-    for (int v = 0; v < XF_V; ++v) out[v] = fx_store(emul_finish(M[v], Sa[v] + Sb[v]), bad);
+    for (int v = 0; v < XF_V; ++v) out[v] = fx_store(emul_finish(M[v], S[v].x + S[v].y), rng);
 }
 
 }  // namespace
@@ -119,10 +118,10 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int G = gridDim.x;
     const uint32_t row_bytes = (uint32_t)(Nx * 8);
-    const bool use_rec = a.rec != nullptr;
-    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + (use_rec ? XREC_BYTES : 0u);
-    const double unit = ldexp(1.0, em.Ef - 62);
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + XREC_BYTES;   // row + wrap + record
+    const double unit = ldexp(1.0, em.Ef - FX_FRAC);
     bool bad = false;
+    uint32_t rng = 0;   // OR of (high word + 2^29) of every stored result
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
@@ -145,8 +144,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
         if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
-        if (use_rec)
-            bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+        bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
                      XREC_BYTES, &bars[s]);
     };
     if (tid == 0) {
@@ -172,14 +170,13 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
         long long rowsum = 0;
         if (ok) {
             const long long* rowbuf = bufs + (size_t)s * stride + PAD;
-            const XRec* rc = use_rec ? reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES) : nullptr;
-            const int n0 = rc ? rc->n0 : em.n0[r];
+            const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
+            const int n0 = rc->n0;
             FxW w;
 #pragma unroll
             for (int t = 0; t < NTAP; ++t) {
-                w.Wh[t] = rc ? rc->Wh[t] : em.Wh[(size_t)t * Np + r];
-                w.wl[t] = rc ? rc->wl[t] : em.wl[(size_t)t * Np + r];
-                w.wr[t] = (rc ? rc->wf[t] : em.wf[(size_t)t * Np + r]) * 4.656612873077393e-10f;   // * 2^-31
+                w.Wh[t] = rc->Wh[t];
+                w.wlr[t] = make_float2(rc->wl[t], rc->wf[t] * 9.313225746154785e-10f);   // * 2^-30
             }
             const int A = (n0 - 4) & 1;
             int base;
@@ -199,14 +196,14 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
                         if (e >= Nx) e -= Nx;
                     }
                     long long out[XF_V];
-                    if (A == 0) fx_chunk<0>(rowbuf + e, w, out, bad);
-                    else fx_chunk<1>(rowbuf + e, w, out, bad);
+                    if (A == 0) fx_chunk<0>(rowbuf + e, w, out, rng);
+                    else fx_chunk<1>(rowbuf + e, w, out, rng);
                     if constexpr (!PERIODIC) {
                         const int k = i + n0;
                         if (k < 0 || k + XF_V - 1 >= Nx - 1) {
-                            const double g = rc ? rc->g64 : em.gd[r], d = rc ? rc->d64 : em.gd[Np + r];
-                            const double* w64 = rc ? rc->w64 : em.w64 + r;
-                            const size_t wst = rc ? 1 : (size_t)Np;
+                            const double g = rc->g64, d = rc->d64;
+                            const double* w64 = rc->w64;
+                            const size_t wst = 1;
 #pragma unroll
                             for (int v = 0; v < XF_V; ++v)
                                 out[v] = fx_edge(rowbuf + e + A + v, w64, wst, k + v, Nx, g, d, unit, em.Ef);
@@ -214,13 +211,13 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
                     }
 #pragma unroll
                     for (int v = 0; v < XF_V; ++v) {
-                        const long long Tc = (out[v] + 1024) >> 11;   // units 2^(Ef-51)
+                        const long long Tc = out[v] >> 10;   // units 2^(Ef-51), rounded down
                         colacc[c][v] += Tc;
                         rowsum += Tc;
                     }
                     longlong2* o = reinterpret_cast<longlong2*>(orow + i);
-                    o[0] = make_longlong2(out[0], out[1]);
-                    o[1] = make_longlong2(out[2], out[3]);
+#pragma unroll
+                    for (int v = 0; v < XF_V / 2; ++v) o[v] = make_longlong2(out[2 * v], out[2 * v + 1]);
                 }
             }
             if constexpr (KIN) {
@@ -240,7 +237,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
             }
         }
     }
-    if (bad) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    if (bad || rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
 
     if (failed) {
         if (tid == 0) {
@@ -314,8 +311,9 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
     const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PS_TH - 1) / PS_TH;
     const int ntiles = ntx * nty;
     const int G = gridDim.x;
-    const double unit = ldexp(1.0, em.Ef - 62);
+    const double unit = ldexp(1.0, em.Ef - FX_FRAC);
     bool bad = false;
+    uint32_t rng = 0;   // OR of (high word + 2^29) of every stored result
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -365,8 +363,8 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
 #pragma unroll
         for (int k = 0; k < NTAP; ++k) {
             w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + i] : 0;
-            w.wl[k] = colvalid ? em.wl[(size_t)k * Nx + i] : 0.f;
-            w.wr[k] = colvalid ? em.wf[(size_t)k * Nx + i] * 4.656612873077393e-10f : 0.f;
+            w.wlr[k] = colvalid ? make_float2(em.wl[(size_t)k * Nx + i], em.wf[(size_t)k * Nx + i] * 9.313225746154785e-10f)
+                                : make_float2(0.f, 0.f);
         }
         const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
         if (ok) {
@@ -374,23 +372,23 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
             const int jb = t.j0 + grp * PS_RPT;
             const int base = jb + n0_i - 4 - t.r0;
             long long M[PS_RPT];
-            float Sacc[PS_RPT];
+            float2 Sacc[PS_RPT];
 #pragma unroll
             for (int rw = 0; rw < PS_RPT; ++rw) {
                 M[rw] = EMUL_M0;
-                Sacc[rw] = 0.f;
+                Sacc[rw] = make_float2(0.f, 0.f);
             }
             auto feed = [&](int u, long long X) {
                 int kx;
                 float kf, rf;
                 fx_split(X, kx, kf, rf);
+                const float2 x2 = make_float2(kf, rf);
 #pragma unroll
                 for (int tap = 0; tap < NTAP; ++tap) {
                     const int rw = u - tap;
                     if (rw >= 0 && rw < PS_RPT) {
                         M[rw] = mad_wide(w.Wh[tap], kx, M[rw]);
-                        Sacc[rw] = fmaf(w.wl[tap], kf, Sacc[rw]);
-                        Sacc[rw] = fmaf(w.wr[tap], rf, Sacc[rw]);
+                        Sacc[rw] = __ffma2_rn(w.wlr[tap], x2, Sacc[rw]);
                     }
                 }
             };
@@ -406,7 +404,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
 #pragma unroll
             for (int rw = 0; rw < PS_RPT; ++rw) {
                 const int j = jb + rw;
-                const long long out = fx_store(emul_finish(M[rw], Sacc[rw]), bad);
+                const long long out = fx_store(emul_finish(M[rw], Sacc[rw].x + Sacc[rw].y), rng);
                 bool edge = false;
                 if constexpr (!PPER) {
                     const int kk = j + n0_i;
@@ -435,7 +433,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
             break;
         }
     }
-    if (bad) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    if (bad || rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
     if (failed && tid == 0) {
         atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
         if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
@@ -448,6 +446,7 @@ size_t pshift_fx_smem_bytes() { return 256 + 2 * (size_t)PSF_RB * PS_TW * 8; }
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                              cudaStream_t st)
 {
+    if (a.rec == nullptr) return cudaErrorInvalidValue;   // the per-row record is staged with each row
     const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, 8);
     if (periodic) {
         if (kin) xshift_fx_kernel<true, true><<<grid, threads, smem, st>>>(a, em);
@@ -510,18 +509,18 @@ __global__ void fx_to_f64_kernel(const long long* __restrict__ s, double* __rest
 
 cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st)
 {
-    f64_to_fx_kernel<<<1024, 256, 0, st>>>(s, d, n, 62 - Ef);
+    f64_to_fx_kernel<<<1024, 256, 0, st>>>(s, d, n, FX_FRAC - Ef);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cudaStream_t st)
 {
-    fx_to_f64_kernel<<<1024, 256, 0, st>>>(s, d, n, 62 - Ef);
+    fx_to_f64_kernel<<<1024, 256, 0, st>>>(s, d, n, FX_FRAC - Ef);
     return cudaGetLastError();
 }
 
 // Column sums of a fixed-point f into one partial row (density test hook): exact in int64 at
-// 2^-11 of the storage resolution.
+// 2^-10 of the storage resolution (units 2^(Ef-51)).
 __global__ void __launch_bounds__(256) colsum_fx_kernel(const long long* __restrict__ f, int Nx, int Np, int Ef,
                                                         double* colpart)
 {
@@ -530,7 +529,7 @@ __global__ void __launch_bounds__(256) colsum_fx_kernel(const long long* __restr
     const int i = blockIdx.x * 32 + lane;
     long long s = 0;
     if (i < Nx)
-        for (int j = grp; j < Np; j += 8) s += (f[(size_t)j * Nx + i] + 1024) >> 11;
+        for (int j = grp; j < Np; j += 8) s += (f[(size_t)j * Nx + i] + 512) >> 10;
     sh[grp][lane] = s;
     __syncthreads();
     if (grp == 0 && i < Nx) {

@@ -740,7 +740,7 @@ int vlasov_set_f(vlasov_sim* s, const double* host_f)
     update_scales(s, mx);
     if (s->fx) {
         std::vector<long long> tmp(cells);
-        for (size_t k = 0; k < cells; ++k) tmp[k] = (long long)fx128_from_f64(host_f[k], 62 - s->Ef);
+        for (size_t k = 0; k < cells; ++k) tmp[k] = (long long)fx128_from_f64(host_f[k], FX_FRAC - s->Ef);
         CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 8, cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
     } else if (s->esz == 8) {
@@ -785,7 +785,7 @@ int vlasov_get_f(vlasov_sim* s, double* host_f)
         std::vector<long long> tmp(cells);
         CU_TRY(cudaMemcpyAsync(tmp.data(), s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
-        for (size_t k = 0; k < cells; ++k) host_f[k] = fx128_to_f64((i128)tmp[k], 62 - s->Ef);
+        for (size_t k = 0; k < cells; ++k) host_f[k] = fx128_to_f64((i128)tmp[k], FX_FRAC - s->Ef);
     } else if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(host_f, s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));

@@ -19,6 +19,7 @@ namespace vl {
 #define VL_FD_C4 (-1.0 / 560.0)
 
 constexpr int NTAP = 10;          // the spline + FD stencil spans f_{k-4} .. f_{k+5}
+constexpr int FX_FRAC = 61;       // 64-bit fixed-point storage: X = round(f * 2^(FX_FRAC - Ef))
 constexpr int HIST_CAP = 4096;    // moment records kept on the device
 
 // Spline weights of one line for a displacement s (cells).  Eqs. (splinegen, splinecoeffs) with
