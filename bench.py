@@ -2,8 +2,14 @@
 """Benchmark of the Strang-split Vlasov step (arXiv:1206.3229, Sec. 3) on GB300.
 
 Default workload: HMF model, 4096 x 4096 grid, theta in [-pi, pi) periodic, p in [-2, 2) with f = 0
-outside, dt = 0.05, homogeneous waterbag (U = 0.55) with a 1e-6 cos(theta) mode, FP64.  A "step"
-is one full Strang step (x half-shift, force, p-shift, x half-shift, moments).
+outside, dt = 0.05, homogeneous waterbag (U = 0.55) with a 1e-6 cos(theta) mode, at FP64 accuracy.
+A "step" is one full Strang step (x half-shift, force, p-shift, x half-shift, moments).
+
+The headline storage mode is fx64: f held as 64-bit fixed point (round(f 2^(61-Ef)), 2^Ef four
+times max|f|) and filtered with integer and FP32 units, accurate to about 2^-49 of 2^Ef per sweep:
+the FP64 parity tolerance of the tests (1e-12 max f after 200 steps) holds for it as for IEEE
+storage.  The IEEE-double storage (f64: same arithmetic, IEEE decode/encode), the hardware-FP64
+filter (f64_native) and FP32 storage are timed beside it.
 
 Prints ONE JSON line (rank 0).  value = cell-updates/s of the whole job (N ranks x Nx*Np*K / max
 time).  Multi-GPU runs are independent replicas (no data-path collective); the NCCL process group
@@ -130,13 +136,13 @@ def cpu_oracle_timing(w: I.Workload, f0: np.ndarray, budget_s: float, max_steps:
                       f"in {elapsed:.2f} s"}
 
 
-def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int) -> dict:
+def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode: str = "fx64") -> dict:
     """The seeded 512-request serving stream (FP32 batched form, continuous batching).
 
     Offered load is set to 80% of a capacity measured in the same run on a short calibration burst.
     Reports aggregate cell-updates/s over the makespan, p50/p99 time-to-result (completion of the
     last step on the GPU minus arrival), and the same requests' estimated time one at a time on the
-    single-grid FP64 path (per-step times measured here per model and grid size).
+    single-grid FP64-accurate path `fp64_mode` (per-step times measured here per model and grid size).
     """
     import torch
     sizes = (256, 512, 1024, 2048)
@@ -159,7 +165,7 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int) -> dict:
         key = (w.model, w.nx)
         if key in t_step:
             continue
-        sim = V.Sim.from_workload(w, precision="f64", stream=stream_handle)
+        sim = V.Sim.from_workload(w, precision=fp64_mode, stream=stream_handle)
         sim.set_f(I.initial_state(w))
         sim.step(3)
         sim.sync()
@@ -177,7 +183,7 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int) -> dict:
     dM = []
     for q in [i for i, (w, st, _t) in enumerate(stream) if w.nx <= 1024][:4]:
         w, st, _t = stream[q]
-        sim = V.Sim.from_workload(w, precision="f64", stream=stream_handle)
+        sim = V.Sim.from_workload(w, precision=fp64_mode, stream=stream_handle)
         sim.set_f(I.initial_state(w))
         sim.step(st)
         m = sim.moments()
@@ -189,9 +195,57 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int) -> dict:
             "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "offered_load_of_capacity": 0.8, "capacity_calibration": capacity, "arrival_rate_per_s": rate,
+            "fp64_single_grid_mode": fp64_mode,
             "fp64_single_grid_sequential_value": work / seq_time if seq_time > 0 else None,
             "speedup_vs_fp64_single_grid_sequential": seq_time / makespan if seq_time > 0 else None,
             "max_abs_dM_vs_fp64_sampled": max(dM) if dM else None, "dM_samples": len(dM)}
+
+
+DTYPE = {"fx64": "int64 fixed point + f32 (FP64-accurate)", "f64": "f64 storage, int64 + f32 arithmetic (FP64-accurate)",
+         "f64_native": "f64", "f32": "f32"}
+# Source files whose kernels each storage mode's sweeps run (for matching stored ncu traffic).
+KERNEL_SOURCES = {"fx64": ("shift_fx.cu",), "f64": ("shift_f64e.cu",), "f64_native": ("shift_kernels.cu",),
+                  "f32": ("shift_kernels.cu",)}
+COMMON_SOURCES = ("emul.cuh", "ptx.cuh", "shift_common.cuh", "vlasov_internal.cuh", "fixed_point.cuh")
+
+
+def kernel_source_hash(precision: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[precision] + COMMON_SOURCES:
+        with open(os.path.join(ROOT, "paper_1206_3229_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(precision: str, slot: str):
+    """DRAM bytes per launch of a sweep kernel from the committed ncu summary, or None when the
+    kernel sources changed since that capture (the summary records the source hash)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
+            d = json.load(fh)
+        e = d[precision]
+        if e["source_hash"] != kernel_source_hash(precision):
+            return None
+        return e["bytes_per_launch"].get(slot)
+    except Exception:
+        return None
+
+
+def reduce_max(x: float, world: int, device: str) -> float:
+    """Max of a per-rank number over the process group (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, cells: int, steps: int, seconds_max: float) -> float:
+    """Whole-job cell-updates/s: every rank advances its own grid `steps` times (weak scaling)."""
+    return world * cells * steps / seconds_max
 
 
 def run_reference(args, w):
@@ -232,7 +286,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=I.HMF_4096_UNSTABLE.name, choices=sorted(I.WORKLOADS))
-    ap.add_argument("--precision", default="f64", choices=["f64", "fx64", "f32", "f64_native"])
+    ap.add_argument("--precision", default="fx64", choices=["f64", "fx64", "f32", "f64_native"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f32", action="store_true", help="skip the secondary measurements of the other storage modes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -262,7 +316,7 @@ def main():
 
     f0 = I.initial_state(w)
     cells = w.cells
-    esz = 8 if args.precision == "f64" else 4
+    esz = 4 if args.precision == "f32" else 8
     stream = torch.cuda.Stream()
     sim = V.Sim.from_workload(w, precision=args.precision, stream=stream.cuda_stream)
     sim.set_f(f0)
@@ -285,12 +339,9 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max(ms, world, "cuda")
     hist = sim.moments()
-    value = world * cells * args.steps / (ms_max * 1e-3)
+    value = job_value(world, cells, args.steps, ms_max * 1e-3)
 
     # ---- per-kernel durations (eager launches with events on the same stream)
     slot_ms = sim.step_timed(4)
@@ -301,9 +352,10 @@ def main():
     dom_name = names[dom]
     achieved = shift_bytes / (slot_ms[dom] * 1e-3) / 1e9 if "shift" in dom_name else None
     step_gbs = 3 * shift_bytes / (ms_max / args.steps * 1e-3) / 1e9
+    traffic = stored_traffic(args.precision, dom_name)
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                "frac": (achieved / peak_gbs) if achieved else None, "traffic": None,
-                "peak_source": peak_src,
+                "frac": (achieved / peak_gbs) if achieved else None, "traffic": traffic,
+                "algorithmic_bytes": shift_bytes, "peak_source": peak_src,
                 "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(names, slot_ms)},
                 "per_kernel_gbs": {n: round(shift_bytes / (v * 1e-3) / 1e9, 1) for n, v in zip(names, slot_ms)
                                    if "shift" in n and not n.endswith("filters")}}
@@ -320,12 +372,8 @@ def main():
     m = sim.moments()
     sim.get_f(out)
     t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    et = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_s = float(et.item())
-    e2e = {"value": world * cells * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = reduce_max(t1 - t0, world, "cuda")
+    e2e = {"value": job_value(world, cells, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": cells * 8 / args.steps,
            "d2h_bytes_per_step": (cells * 8 + 64 * args.steps) / args.steps,
            "note": "one job per timed region: vlasov_set_f from pinned host f0, K steps, moments and f back"}
@@ -334,7 +382,7 @@ def main():
     # ---- secondary: the other storage modes on the same workload (same timing rules)
     others = {}
     if not args.no_f32:
-        for prec in [p for p in ("fx64", "f32", "f64") if p != args.precision]:
+        for prec in [p for p in ("fx64", "f64", "f64_native", "f32") if p != args.precision]:
             s2 = V.Sim.from_workload(w, precision=prec, stream=stream.cuda_stream)
             s2.set_f(f0)
             s2.step(args.warmup)
@@ -355,7 +403,8 @@ def main():
 
     serving = None
     if not args.no_serve and rank == 0:
-        serving = serving_benchmark(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30))
+        serving = serving_benchmark(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30),
+                                    "fx64" if args.precision == "f32" else args.precision)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -365,7 +414,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": w.name, "grid": f"{w.nx}x{w.np}", "dt": w.dt, "precision": args.precision,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": f"inputs larger than L2: each sweep streams {2 * cells * esz / 1e6:.0f} MB "
