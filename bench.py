@@ -136,8 +136,9 @@ def cpu_oracle_timing(w: I.Workload, f0: np.ndarray, budget_s: float, max_steps:
                       f"in {elapsed:.2f} s"}
 
 
-def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode: str = "fx64") -> dict:
-    """The seeded 512-request serving stream (FP32 batched form, continuous batching).
+def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode: str = "fx64",
+                      precision: str = "f32") -> dict:
+    """The seeded 512-request serving stream (batched form with `precision` storage, continuous batching).
 
     Offered load is set to 80% of a capacity measured in the same run on a short calibration burst.
     Reports aggregate cell-updates/s over the makespan, p50/p99 time-to-result (completion of the
@@ -148,13 +149,13 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode
     sizes = (256, 512, 1024, 2048)
     cal = I.serving_stream(48, seed=55, sizes=sizes, step_scale=0.1, rate_per_s=1e9)
     reqs = [V.request_from_workload(w, st, 0.0) for (w, st, _t) in cal]
-    _, mk = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle)
+    _, mk = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision=precision)
     capacity = sum(w.cells * st for (w, st, _t) in cal) / mk
     mean_work = float(np.mean([n * n for n in sizes])) * 1050.0
     rate = 0.8 * capacity / mean_work
     stream = I.serving_stream(512, seed=5, sizes=sizes, rate_per_s=rate)
     reqs = [V.request_from_workload(w, st, t) for (w, st, t) in stream]
-    res, makespan = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle)
+    res, makespan = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision=precision)
     ok = [r.status == 0 for r in res]
     work = sum(w.cells * st for (w, st, _t), good in zip(stream, ok) if good)
     lat = np.array([r.done_s - r.arrival_s for r, good in zip(res, ok) if good])
@@ -188,9 +189,12 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode
         sim.step(st)
         m = sim.moments()
         sim.close()
-        dM.append(abs(math.hypot(res[q].last.Mx, res[q].last.My) - math.hypot(m[-1, 2], m[-1, 3])))
+        dM.append({"model": w.model, "n": w.nx, "steps": st,
+                   "dM": abs(math.hypot(res[q].last.Mx, res[q].last.My) - math.hypot(m[-1, 2], m[-1, 3]))})
     return {"requests": len(reqs), "completed": int(sum(ok)), "slots": slots, "mem_budget_gb": budget_bytes / 2 ** 30,
-            "dtype": "f32 storage, FP64-accurate displacements and moment sums",
+            "precision": precision,
+            "dtype": ("f32 storage, FP64-accurate displacements and moment sums" if precision == "f32"
+                      else "int64 fixed point + f32 (FP64-accurate), as the single-grid fx64 path"),
             "aggregate_value": work / makespan, "unit": UNIT, "makespan_s": makespan,
             "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
@@ -198,7 +202,7 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode
             "fp64_single_grid_mode": fp64_mode,
             "fp64_single_grid_sequential_value": work / seq_time if seq_time > 0 else None,
             "speedup_vs_fp64_single_grid_sequential": seq_time / makespan if seq_time > 0 else None,
-            "max_abs_dM_vs_fp64_sampled": max(dM) if dM else None, "dM_samples": len(dM)}
+            "max_abs_dM_vs_fp64_sampled": max(d["dM"] for d in dM) if dM else None, "dM_samples": dM}
 
 
 DTYPE = {"fx64": "int64 fixed point + f32 (FP64-accurate)", "f64": "f64 storage, int64 + f32 arithmetic (FP64-accurate)",
@@ -403,8 +407,9 @@ def main():
 
     serving = None
     if not args.no_serve and rank == 0:
-        serving = serving_benchmark(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30),
-                                    "fx64" if args.precision == "f32" else args.precision)
+        ref_mode = "fx64" if args.precision == "f32" else args.precision
+        serving = {prec: serving_benchmark(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30),
+                                           ref_mode, prec) for prec in ("f32", "fx64")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -169,10 +169,14 @@ typedef struct {
 
 /* A batch of `slots` simulation slots with grids up to max_n x max_n, all buffers carved out of one
    device allocation of mem_budget_bytes (admission fails with VLASOV_ENOMEM while a request does not
-   fit).  stream: cudaStream_t or NULL for an owned one. */
-int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* stream, vlasov_batch** out);
-/* Device bytes one request occupies in a batch. */
-long long vlasov_batch_footprint(const vlasov_request* req);
+   fit).  precision: VLASOV_F32 (FP32 storage) or VLASOV_FX64 (the FP64-accurate 64-bit fixed-point
+   storage of the single-grid VLASOV_FX64 mode, same kernels: a slot's f is bit-identical to a
+   single-grid VLASOV_FX64 run of the same request and f0), for every slot; max_n <= 4096 for FX64.
+   stream: cudaStream_t or NULL for an owned one.  VLASOV_EINVAL for other precisions. */
+int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int precision, void* stream,
+                        vlasov_batch** out);
+/* Device bytes one request occupies in a batch of the given precision. */
+long long vlasov_batch_footprint(const vlasov_request* req, int precision);
 /* Admit a request into a free slot (*slot); host_f0 (Np*Nx doubles) or NULL for the device-side
    initial state of req->init.  VLASOV_ESTATE: no free slot; VLASOV_ENOMEM: does not fit now. */
 int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* req, const double* host_f0, int* slot);
@@ -190,6 +194,7 @@ typedef struct {
     int max_n;                   /* largest grid (0: from the requests) */
     long long mem_budget_bytes;  /* device memory for simulation state */
     int max_inflight;            /* batched steps queued ahead of the GPU */
+    int precision;               /* VLASOV_F32 or VLASOV_FX64 */
     void* stream;
 } vlasov_serve_options;
 

@@ -378,18 +378,21 @@ __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
     ring_body<T>(a);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) ring_batch_kernel(const RingArgs* __restrict__ args)
 {
     const RingArgs a = args[blockIdx.y];
     if (a.N <= 0) return;
-    ring_body<float>(a);
+    ring_body<T>(a);
 }
 
 int ring_blocks(int N) { return (N + RING_OUT - 1) / RING_OUT; }
 
-cudaError_t launch_ring_batch(int slots, int max_n, const RingArgs* args, cudaStream_t st)
+cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st)
 {
-    ring_batch_kernel<<<dim3(ring_blocks(max_n), slots), 256, (size_t)max_n * 4, st>>>(args);
+    const dim3 grid(ring_blocks(max_n), slots);
+    if (elem_bytes == 8) ring_batch_kernel<double><<<grid, 256, (size_t)max_n * 8, st>>>(args);
+    else ring_batch_kernel<float><<<grid, 256, (size_t)max_n * 4, st>>>(args);
     return cudaGetLastError();
 }
 
@@ -520,15 +523,18 @@ __global__ void __launch_bounds__(64) pparams_kernel(PParamsArgs a)
     pparams_body<T>(a);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(64) pparams_batch_kernel(const PParamsArgs* __restrict__ args)
 {
     const PParamsArgs a = args[blockIdx.y];
-    pparams_body<float>(a);
+    pparams_body<T>(a);
 }
 
-cudaError_t launch_pparams_batch(int slots, int max_n, const PParamsArgs* args, cudaStream_t st)
+cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PParamsArgs* args, cudaStream_t st)
 {
-    pparams_batch_kernel<<<dim3((max_n + 63) / 64, slots), 64, 0, st>>>(args);
+    const dim3 grid((max_n + 63) / 64, slots);
+    if (elem_bytes == 8) pparams_batch_kernel<double><<<grid, 64, 0, st>>>(args);
+    else pparams_batch_kernel<float><<<grid, 64, 0, st>>>(args);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
-// batch.cu -- many grids of uneven size and different models advanced together (FP32 storage),
-// and a continuous-batching serving loop on top.
+// batch.cu -- many grids of uneven size and different models advanced together (FP32 storage, or
+// FX64: the FP64-accurate 64-bit fixed point of shift_fx.cu), and a continuous-batching serving
+// loop on top.
 //
 // A batch has a fixed number of slots.  Every slot owns its buffers inside one device arena (a
 // first-fit allocator over a single allocation, so admission is limited by HBM footprint, not by a
@@ -21,6 +22,7 @@
 #include <vector>
 
 #include "../../include/vlasov.h"
+#include "emul.cuh"
 #include "fixed_point.cuh"
 #include "vlasov_internal.cuh"
 
@@ -28,11 +30,14 @@ using namespace vl;
 
 namespace {
 
-constexpr int B_CTAS_X = 16;     // x-shift CTAs per slot (rows per CTA = Np / 16)
-constexpr int B_CTAS_P = 32;     // p-shift CTAs per slot
+constexpr int B_CTAS_X_MAX = 512;   // most x-shift CTAs per slot (sizes the kinetic partials)
+constexpr int B_ROWS_PER_CTA = 16;  // x-shift rows per CTA (the CTA count of a slot depends on its Np only)
+constexpr int B_TILES_PER_CTA = 8;  // p-shift tiles per CTA of the largest grid of a batch
 constexpr int B_PAD_ZERO = 64;   // zero halo of non-periodic rows (|x displacement| <= 55 cells)
 constexpr int B_STAGES = 3;
 constexpr int B_INIT_BLOCKS = 128;
+
+int slot_ctas_x(int Np) { return std::min(B_CTAS_X_MAX, std::max(16, (Np + B_ROWS_PER_CTA - 1) / B_ROWS_PER_CTA)); }
 
 int bfail(int code, const char* msg)
 {
@@ -174,10 +179,66 @@ __global__ void flip_kernel(int* ver, int slots)
     for (int s = threadIdx.x; s < slots; s += blockDim.x) ver[s] ^= 1;
 }
 
-__global__ void f32_to_f64_kernel(const float* s, double* d, size_t n)
+// FX64 slots: the same initial state in FP64 (xi from the top 53 bits of the SplitMix64 output, as
+// the shared input generator draws it), its exact fixed-point mass, then scaling to unit mass and
+// conversion to the fixed-point storage.
+struct InitArgs64 {
+    double* f;               // FP64 staging (the slot's second f buffer)
+    int Nx, Np;
+    const double* rowv;
+    const double* colv;
+    double noise;
+    unsigned long long seed;
+    int k_m;
+    double dxdp;
+    void* part;
+    unsigned int* ticket;
+    double* inv_mass;
+};
+
+__global__ void __launch_bounds__(256) init_fill64_kernel(InitArgs64 a)
 {
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-        d[k] = (double)s[k];
+    __shared__ i128 red[33];
+    __shared__ bool is_last;
+    const size_t n = (size_t)a.Nx * a.Np;
+    i128 acc = 0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / a.Nx), i = (int)(k - (size_t)j * a.Nx);
+        double v = a.rowv[j] * a.colv[i];
+        if (v != 0.0 && a.noise != 0.0) {
+            const unsigned long long z = splitmix64_at(a.seed, (unsigned long long)k + 1ull);
+            const double xi = 2.0 * ((double)(z >> 11) * 1.1102230246251565e-16) - 1.0;   // 2u - 1, u = top 53 bits
+            v = v * (1.0 + a.noise * xi);
+        }
+        a.f[k] = v;
+        acc += fx128_from_f64(v, a.k_m);
+    }
+    acc = block_sum_i128(acc, red);
+    i128* part = static_cast<i128*>(a.part);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = acc;
+        __threadfence();
+        is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    i128 t = 0;
+    const volatile i128* vp = part;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += vp[b];
+    t = block_sum_i128(t, red);
+    if (threadIdx.x == 0) {
+        const double mass = a.dxdp * fx128_to_f64(t, a.k_m);
+        *a.inv_mass = mass > 0 ? 1.0 / mass : 0.0;
+        *a.ticket = 0u;
+    }
+}
+
+__global__ void init_scale_fx_kernel(const double* src, long long* dst, size_t n, const double* inv_mass, int k)
+{
+    const double s = *inv_mass;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        dst[q] = (long long)fx128_from_f64(src[q] * s, k);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
@@ -195,11 +256,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
 
 // ------------------------------------------------------------------------------------------- slot layout
 struct SlotLayout {
-    size_t f[2], xrec, pn0, pw, pgd, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart, ringpart, tickets, sc, hist,
-        dstep, err, costab, sintab, cosfx, sinfx, ringdV, ringV, rowv, colv, initpart, inv_mass, total;
+    size_t f[2], xrec, pn0, pw, pgd, pWh, pwl, pwf, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart, ringpart,
+        tickets, sc, hist, dstep, err, costab, sintab, cosfx, sinfx, ringdV, ringV, rowv, colv, initpart, inv_mass, total;
 };
 
-SlotLayout layout(int Nx, int Np)
+// esz: bytes per cell (4: FP32 storage, 8: FX64 storage)
+SlotLayout layout(int Nx, int Np, int esz)
 {
     SlotLayout L;
     size_t o = 0;
@@ -209,15 +271,17 @@ SlotLayout layout(int Nx, int Np)
         return r;
     };
     const size_t cells = (size_t)Nx * Np;
-    L.f[0] = take(cells * 4);
-    L.f[1] = take(cells * 4);
+    L.f[0] = take(cells * esz);
+    L.f[1] = take(cells * esz);
     L.xrec = take((size_t)Np * XREC_BYTES);
     L.pn0 = take((size_t)Nx * 4);
-    L.pw = take((size_t)NTAP * Nx * 4);
-    L.pgd = take((size_t)2 * Nx * 4);
-    L.colpart = take((size_t)B_CTAS_X * Nx * 8);
+    L.pw = take((size_t)NTAP * Nx * esz);
+    L.pgd = take((size_t)2 * Nx * esz);
+    L.pWh = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
+    L.pwl = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
+    L.pwf = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
     L.colacc = take((size_t)Nx * 8);
-    L.kinpart = take((size_t)B_CTAS_X * 8);
+    L.kinpart = take((size_t)B_CTAS_X_MAX * 8);
     L.rho = take((size_t)Nx * 8);
     L.F = take((size_t)Nx * 8);
     L.Qd = take((size_t)Nx * 8);
@@ -233,10 +297,10 @@ SlotLayout layout(int Nx, int Np)
     L.sintab = take((size_t)Nx * 8);
     L.cosfx = take((size_t)Nx * 8);
     L.sinfx = take((size_t)Nx * 8);
-    L.ringdV = take((size_t)Nx * 4);
-    L.ringV = take((size_t)Nx * 4);
-    L.rowv = take((size_t)Np * 4);
-    L.colv = take((size_t)Nx * 4);
+    L.ringdV = take((size_t)Nx * esz);
+    L.ringV = take((size_t)Nx * esz);
+    L.rowv = take((size_t)Np * esz);
+    L.colv = take((size_t)Nx * esz);
     L.initpart = take((size_t)B_INIT_BLOCKS * 16);
     L.inv_mass = take(8);
     L.total = o;
@@ -261,6 +325,9 @@ struct Slot {
 // ------------------------------------------------------------------------------------------- the batch
 struct vlasov_batch {
     int S = 0, max_n = 0;
+    int prec = VLASOV_F32;           // VLASOV_F32 or VLASOV_FX64, for every slot
+    int esz = 4;
+    int ctas_x = 16, ctas_p = 32;    // CTAs per slot of the batched sweeps (fixed at capture)
     cudaStream_t st = nullptr;
     bool own_stream = false;
     Arena arena;
@@ -272,6 +339,7 @@ struct vlasov_batch {
     ColReduceArgs* d_cr = nullptr;   // [2][S]: after step 1, after step 4
     RingArgs* d_rg = nullptr;        // [2][S]
     PParamsArgs* d_pp = nullptr;     // [S]
+    EmulArgs* d_em = nullptr;        // [S] (FX64)
     int* d_ver = nullptr;            // [S]
     std::vector<XShiftArgs> xa;
     std::vector<PShiftArgs> pa;
@@ -279,6 +347,7 @@ struct vlasov_batch {
     std::vector<ColReduceArgs> cr;
     std::vector<RingArgs> rg;
     std::vector<PParamsArgs> pp;
+    std::vector<EmulArgs> em;
     size_t xsmem = 0;
     cudaGraphExec_t graph = nullptr;
     long long steps_launched = 0;
@@ -306,6 +375,7 @@ void clear_slot_args(vlasov_batch* b, int k)
         std::memset(&b->rg[(size_t)q * b->S + k], 0, sizeof(RingArgs));
     }
     std::memset(&b->pp[k], 0, sizeof(PParamsArgs));
+    std::memset(&b->em[k], 0, sizeof(EmulArgs));
 }
 
 int upload_slot_args(vlasov_batch* b, int k)
@@ -321,6 +391,7 @@ int upload_slot_args(vlasov_batch* b, int k)
         B_TRY(cudaMemcpyAsync(b->d_rg + q * S + k, &b->rg[q * S + k], sizeof(RingArgs), cudaMemcpyHostToDevice, b->st));
     }
     B_TRY(cudaMemcpyAsync(b->d_pp + k, &b->pp[k], sizeof(PParamsArgs), cudaMemcpyHostToDevice, b->st));
+    B_TRY(cudaMemcpyAsync(b->d_em + k, &b->em[k], sizeof(EmulArgs), cudaMemcpyHostToDevice, b->st));
     return VLASOV_OK;
 }
 
@@ -360,6 +431,7 @@ int fill_slot_args(vlasov_batch* b, int k)
                 a.pmin = r.pmin;
                 a.dp = dp;
                 a.err = reinterpret_cast<int*>(P(b, s, s.L.err));
+                a.ctas = slot_ctas_x(Np);
             }
         }
         // p-shift: reads the other buffer, writes back into v
@@ -375,19 +447,20 @@ int fill_slot_args(vlasov_batch* b, int k)
         auto enc = encode_tiled();
         if (!enc) return bfail(VLASOV_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
         cuuint64_t dims[2] = {(cuuint64_t)Nx, (cuuint64_t)Np};
-        cuuint64_t strides[1] = {(cuuint64_t)Nx * 4};
+        cuuint64_t strides[1] = {(cuuint64_t)Nx * b->esz};
         cuuint32_t box[2] = {(cuuint32_t)PS_TW, (cuuint32_t)PS_BH};
         cuuint32_t estr[2] = {1, 1};
-        if (enc(&b->tm[(size_t)k * 2 + v], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, fbuf[v ^ 1], dims, strides, box, estr,
+        const CUtensorMapDataType dt = b->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        if (enc(&b->tm[(size_t)k * 2 + v], dt, 2, fbuf[v ^ 1], dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return bfail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed for a batch slot");
     }
-    const int B = std::min(B_CTAS_X, Np);
+    const int B = std::min(slot_ctas_x(Np), Np);
     for (int q = 0; q < 2; ++q) {
         ColReduceArgs& c = b->cr[(size_t)q * b->S + k];
         c.colacc = reinterpret_cast<unsigned long long*>(P(b, s, s.L.colacc));
-        c.colpart = reinterpret_cast<const double*>(P(b, s, s.L.colpart));
+        c.colpart = nullptr;   // the x-shifts add exact column sums into colacc
         c.B = B;
         c.kinpart = q ? reinterpret_cast<const double*>(P(b, s, s.L.kinpart)) : nullptr;
         c.Nx = Nx;
@@ -443,9 +516,21 @@ int fill_slot_args(vlasov_batch* b, int k)
     p.w = P(b, s, s.L.pw);
     p.gd = P(b, s, s.L.pgd);
     p.Fout = nullptr;
-    p.Wh = nullptr;
-    p.wl = nullptr;
-    p.wf = nullptr;
+    const bool fx = b->esz == 8;
+    p.Wh = fx ? reinterpret_cast<int*>(P(b, s, s.L.pWh)) : nullptr;
+    p.wl = fx ? reinterpret_cast<float*>(P(b, s, s.L.pwl)) : nullptr;
+    p.wf = fx ? reinterpret_cast<float*>(P(b, s, s.L.pwf)) : nullptr;
+    EmulArgs& e = b->em[k];
+    std::memset(&e, 0, sizeof e);
+    if (fx) {
+        e.Ef = s.Ef;
+        e.n0 = p.n0;
+        e.Wh = p.Wh;
+        e.wl = p.wl;
+        e.wf = p.wf;
+        e.gd = reinterpret_cast<const double*>(p.gd);
+        e.w64 = reinterpret_cast<const double*>(p.w);
+    }
     return VLASOV_OK;
 }
 
@@ -472,22 +557,39 @@ void vlasov_batch_destroy(vlasov_batch* b)
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->arena.base);
-    void* bufs[] = {b->d_xa, b->d_pa, b->d_tm, b->d_cr, b->d_rg, b->d_pp, b->d_ver};
+    void* bufs[] = {b->d_xa, b->d_pa, b->d_tm, b->d_cr, b->d_rg, b->d_pp, b->d_em, b->d_ver};
     for (void* p : bufs) cudaFree(p);
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     delete b;
 }
 
-int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* stream, vlasov_batch** out)
+int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int precision, void* stream,
+                        vlasov_batch** out)
 {
     if (!out) return bfail(VLASOV_EINVAL, "out is NULL");
     *out = nullptr;
     if (slots < 1 || slots > 4096) return bfail(VLASOV_EINVAL, "slots must be in 1..4096");
     if (max_n < 16 || max_n % 8 || max_n > 8192) return bfail(VLASOV_EINVAL, "max_n must be a multiple of 8 in 16..8192");
     if (mem_budget_bytes <= 0) return bfail(VLASOV_EINVAL, "memory budget must be positive");
+    if (precision != VLASOV_F32 && precision != VLASOV_FX64)
+        return bfail(VLASOV_EINVAL, "batch precision must be VLASOV_F32 or VLASOV_FX64");
+    if (precision == VLASOV_FX64 && max_n > xshift_fx_max_cols(XS_THREADS_MIN))
+        return bfail(VLASOV_EINVAL, "FX64 batch: max_n above the x-shift row limit");
     vlasov_batch* b = new vlasov_batch();
     b->S = slots;
     b->max_n = max_n;
+    b->prec = precision;
+    b->esz = precision == VLASOV_FX64 ? 8 : 4;
+    // Work per slot grows with its grid while the launch shape is fixed for every slot: the launch
+    // has the CTAs the largest grid needs (B_ROWS_PER_CTA rows, B_TILES_PER_CTA tiles each); a slot
+    // uses as many x-shift CTAs as its own Np calls for, independent of the batch (so its column and
+    // kinetic partial sums, and its results, do not depend on what else is in the batch), and the
+    // surplus CTAs exit at once.
+    b->ctas_x = slot_ctas_x(max_n);
+    {
+        const int tiles = ((max_n + PS_TW - 1) / PS_TW) * ((max_n + PS_TH - 1) / PS_TH);
+        b->ctas_p = std::min(1024, std::max(32, tiles / B_TILES_PER_CTA));
+    }
     auto bail = [&](int rc) {
         vlasov_batch_destroy(b);
         return rc;
@@ -510,6 +612,7 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* 
     BC(cudaGetDevice(&dev));
     BC(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     BC(set_kernel_attributes(optin - 1024));
+    BC(set_kernel_attributes_fx(optin - 1024));
     BC(cudaMalloc(&b->arena.base, (size_t)mem_budget_bytes));
     b->arena.size = (size_t)mem_budget_bytes;
     b->arena.free_[0] = (size_t)mem_budget_bytes;
@@ -521,6 +624,7 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* 
     b->cr.assign(2 * S, ColReduceArgs{});
     b->rg.assign(2 * S, RingArgs{});
     b->pp.assign(S, PParamsArgs{});
+    b->em.assign(S, EmulArgs{});
     for (int k = 0; k < slots; ++k) clear_slot_args(b, k);
     BC(cudaMalloc(&b->d_xa, sizeof(XShiftArgs) * b->xa.size()));
     BC(cudaMalloc(&b->d_pa, sizeof(PShiftArgs) * b->pa.size()));
@@ -528,6 +632,7 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* 
     BC(cudaMalloc(&b->d_cr, sizeof(ColReduceArgs) * b->cr.size()));
     BC(cudaMalloc(&b->d_rg, sizeof(RingArgs) * b->rg.size()));
     BC(cudaMalloc(&b->d_pp, sizeof(PParamsArgs) * b->pp.size()));
+    BC(cudaMalloc(&b->d_em, sizeof(EmulArgs) * b->em.size()));
     BC(cudaMalloc(&b->d_ver, sizeof(int) * S));
     BC(cudaMemsetAsync(b->d_ver, 0, sizeof(int) * S, b->st));
     BC(cudaMemcpyAsync(b->d_xa, b->xa.data(), sizeof(XShiftArgs) * b->xa.size(), cudaMemcpyHostToDevice, b->st));
@@ -536,8 +641,9 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* 
     BC(cudaMemcpyAsync(b->d_cr, b->cr.data(), sizeof(ColReduceArgs) * b->cr.size(), cudaMemcpyHostToDevice, b->st));
     BC(cudaMemcpyAsync(b->d_rg, b->rg.data(), sizeof(RingArgs) * b->rg.size(), cudaMemcpyHostToDevice, b->st));
     BC(cudaMemcpyAsync(b->d_pp, b->pp.data(), sizeof(PParamsArgs) * b->pp.size(), cudaMemcpyHostToDevice, b->st));
+    BC(cudaMemcpyAsync(b->d_em, b->em.data(), sizeof(EmulArgs) * b->em.size(), cudaMemcpyHostToDevice, b->st));
     BC(cudaStreamSynchronize(b->st));
-    b->xsmem = xshift_smem_bytes(max_n, B_PAD_ZERO, B_STAGES, 4);
+    b->xsmem = xshift_smem_bytes(max_n, B_PAD_ZERO, B_STAGES, b->esz);
 
     // capture one batched Strang step
     cudaGraph_t g = nullptr;
@@ -551,16 +657,22 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* 
         }
     };
     const int crb = (max_n + 31) / 32;
-    L(launch_xshift_batch(true, false, slots, B_CTAS_X, b->xsmem, b->d_xa + 0 * S * 2, b->d_ver, b->st));
-    L(launch_xshift_batch(false, false, slots, B_CTAS_X, b->xsmem, b->d_xa + 1 * S * 2, b->d_ver, b->st));
+    const bool fx = b->esz == 8;
+    auto xs = [&](bool per, bool kin, const XShiftArgs* a) {
+        return fx ? launch_xshift_fx_batch(per, kin, slots, b->ctas_x, b->xsmem, a, b->d_em, b->d_ver, b->st)
+                  : launch_xshift_batch(per, kin, slots, b->ctas_x, b->xsmem, a, b->d_ver, b->st);
+    };
+    L(xs(true, false, b->d_xa + 0 * S * 2));
+    L(xs(false, false, b->d_xa + 1 * S * 2));
     L(launch_colreduce_batch(slots, crb, b->d_cr, b->st));
-    L(launch_ring_batch(slots, max_n, b->d_rg, b->st));
-    L(launch_pparams_batch(slots, max_n, b->d_pp, b->st));
-    L(launch_pshift_batch(slots, B_CTAS_P, b->d_tm, b->d_pa, b->d_ver, b->st));
-    L(launch_xshift_batch(true, true, slots, B_CTAS_X, b->xsmem, b->d_xa + 2 * S * 2, b->d_ver, b->st));
-    L(launch_xshift_batch(false, true, slots, B_CTAS_X, b->xsmem, b->d_xa + 3 * S * 2, b->d_ver, b->st));
+    L(launch_ring_batch(b->esz, slots, max_n, b->d_rg, b->st));
+    L(launch_pparams_batch(b->esz, slots, max_n, b->d_pp, b->st));
+    L(fx ? launch_pshift_fx_batch(slots, b->ctas_p, b->d_tm, b->d_pa, b->d_em, b->d_ver, b->st)
+         : launch_pshift_batch(slots, b->ctas_p, b->d_tm, b->d_pa, b->d_ver, b->st));
+    L(xs(true, true, b->d_xa + 2 * S * 2));
+    L(xs(false, true, b->d_xa + 3 * S * 2));
     L(launch_colreduce_batch(slots, crb, b->d_cr + S, b->st));
-    L(launch_ring_batch(slots, max_n, b->d_rg + S, b->st));
+    L(launch_ring_batch(b->esz, slots, max_n, b->d_rg + S, b->st));
     flip_kernel<<<1, 256, 0, b->st>>>(b->d_ver, slots);
     L(cudaGetLastError());
     cudaError_t ec = cudaStreamEndCapture(b->st, &g);
@@ -578,10 +690,11 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, void* 
 }
 
 // Bytes of device memory a request occupies in a batch arena.
-long long vlasov_batch_footprint(const vlasov_request* r)
+long long vlasov_batch_footprint(const vlasov_request* r, int precision)
 {
     if (!r || r->Nx <= 0 || r->Np <= 0) return -1;
-    return (long long)layout(r->Nx, r->Np).total;
+    if (precision != VLASOV_F32 && precision != VLASOV_FX64) return -1;
+    return (long long)layout(r->Nx, r->Np, precision == VLASOV_FX64 ? 8 : 4).total;
 }
 
 int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* host_f0, int* slot_out)
@@ -597,7 +710,8 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
             break;
         }
     if (k < 0) return bfail(VLASOV_ESTATE, "no free slot");
-    const SlotLayout L = layout(r->Nx, r->Np);
+    const SlotLayout L = layout(r->Nx, r->Np, b->esz);
+    const bool fx = b->esz == 8;
     size_t off = 0;
     if (!b->arena.alloc(L.total, &off)) return bfail(VLASOV_ENOMEM, "request does not fit the batch memory budget now");
     Slot& s = b->slots[k];
@@ -612,11 +726,11 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
     const bool per = r->x_periodic != 0;
 
     // host-side tables: node coordinates, initial profile factors, trig and ring tables, row filters
-    std::vector<float> rowv(Np), colv(Nx);
+    std::vector<double> rowv(Np), colv(Nx);
     double colsum = 0, rowsum = 0;
     for (int j = 0; j < Np; ++j) {
         const double p = r->pmin + (double)j * dp;
-        float v = std::fabs(p) < r->p0 ? 1.0f : 0.0f;
+        const double v = std::fabs(p) < r->p0 ? 1.0 : 0.0;
         rowv[j] = v;
         rowsum += v;
     }
@@ -626,7 +740,7 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
         double v;
         if (r->init == 0) v = (r->x0 >= half_x || std::fabs(x) < r->x0) ? 1.0 / (4.0 * r->x0 * r->p0) : 0.0;
         else v = (1.0 / (2.0 * r->p0 * (r->xmax - r->xmin))) * (1.0 + r->amp * std::cos(x));
-        colv[i] = (float)v;
+        colv[i] = fx ? v : (double)(float)v;   // FP32 slots build f from the FP32 profile
         colsum += v;
     }
     const double mass_est = dx * dp * colsum * rowsum;
@@ -638,9 +752,15 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
     double fmax = 0;
     for (int i = 0; i < Nx; ++i) fmax = std::max(fmax, (double)colv[i]);
     fmax = fmax * (1.0 + std::fabs(r->noise)) / mass_est;   // after normalisation
+    const size_t cells = (size_t)Nx * Np;
+    double fscale = fmax;   // bound 2^Ef >= 4 max|f|: from the given f0 (as the single-grid path), else the estimate
+    if (host_f0 && fx) {
+        fscale = 0;
+        for (size_t q = 0; q < cells; ++q) fscale = std::max(fscale, std::fabs(host_f0[q]));
+    }
     {
         int e = 0;
-        std::frexp(fmax, &e);
+        std::frexp(fscale, &e);
         s.Ef = e + 2;
         const int Lp = clog2((double)Np), Lx = clog2((double)Nx);
         const double pm = std::max(std::fabs(r->pmin), std::fabs(r->pmax));
@@ -656,7 +776,7 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
     }
     std::vector<double> c(Nx), sn(Nx);
     std::vector<long long> cfx(Nx), sfx(Nx);
-    std::vector<float> dV(Nx, 0.f), V(Nx, 0.f);
+    std::vector<double> dV(Nx, 0.0), V(Nx, 0.0);
     for (int i = 0; i < Nx; ++i) {
         const double th = r->xmin + (double)i * dx;
         c[i] = std::cos(th);
@@ -666,8 +786,8 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
         if (r->model == VLASOV_RING) {
             const double u = (double)i * dx;
             const double q = 1.0 - std::cos(u) + r->eps;
-            dV[i] = (float)(std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q)));
-            V[i] = (float)(-1.0 / (std::sqrt(2.0) * std::sqrt(q)));
+            dV[i] = std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q));
+            V[i] = -1.0 / (std::sqrt(2.0) * std::sqrt(q));
         }
     }
     std::vector<unsigned char> recs((size_t)Np * XREC_BYTES, 0);
@@ -688,6 +808,7 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
         for (int t = 0; t < NTAP; ++t) {
             rc_.w64[t] = Ls.w[t];
             rc_.w32[t] = (float)Ls.w[t];
+            emul_weight(Ls.w[t], rc_.Wh[t], rc_.wl[t], rc_.wf[t]);
         }
         std::memcpy(&recs[(size_t)j * XREC_BYTES], &rc_, sizeof rc_);
     }
@@ -704,18 +825,45 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
     B_TRY(H2D(L.sintab, sn.data(), 8 * (size_t)Nx));
     B_TRY(H2D(L.cosfx, cfx.data(), 8 * (size_t)Nx));
     B_TRY(H2D(L.sinfx, sfx.data(), 8 * (size_t)Nx));
-    B_TRY(H2D(L.ringdV, dV.data(), 4 * (size_t)Nx));
-    B_TRY(H2D(L.ringV, V.data(), 4 * (size_t)Nx));
+    std::vector<float> dVf(dV.begin(), dV.end()), Vf(V.begin(), V.end());
+    B_TRY(H2D(L.ringdV, fx ? (const void*)dV.data() : (const void*)dVf.data(), (size_t)b->esz * Nx));
+    B_TRY(H2D(L.ringV, fx ? (const void*)V.data() : (const void*)Vf.data(), (size_t)b->esz * Nx));
     B_TRY(H2D(L.xrec, recs.data(), recs.size()));
-    const size_t cells = (size_t)Nx * Np;
-    if (host_f0) {
+    if (host_f0 && fx) {
+        std::vector<long long> tmp(cells);
+        for (size_t q = 0; q < cells; ++q) tmp[q] = (long long)fx128_from_f64(host_f0[q], FX_FRAC - s.Ef);
+        B_TRY(H2D(L.f[0], tmp.data(), cells * 8));
+        B_TRY(cudaStreamSynchronize(b->st));
+    } else if (host_f0) {
         std::vector<float> tmp(cells);
         for (size_t q = 0; q < cells; ++q) tmp[q] = (float)host_f0[q];
         B_TRY(H2D(L.f[0], tmp.data(), cells * 4));
         B_TRY(cudaStreamSynchronize(b->st));
+    } else if (fx) {
+        B_TRY(H2D(L.rowv, rowv.data(), 8 * (size_t)Np));
+        B_TRY(H2D(L.colv, colv.data(), 8 * (size_t)Nx));
+        InitArgs64 ia;
+        ia.f = reinterpret_cast<double*>(P(b, s, L.f[1]));
+        ia.Nx = Nx;
+        ia.Np = Np;
+        ia.rowv = reinterpret_cast<const double*>(P(b, s, L.rowv));
+        ia.colv = reinterpret_cast<const double*>(P(b, s, L.colv));
+        ia.noise = r->init == 0 ? r->noise : 0.0;
+        ia.seed = r->seed;
+        ia.k_m = 120 - clog2((double)cells * fmax * mass_est * 2.0 + 1.0);
+        ia.dxdp = dx * dp;
+        ia.part = P(b, s, L.initpart);
+        ia.ticket = reinterpret_cast<unsigned int*>(P(b, s, L.tickets));
+        ia.inv_mass = reinterpret_cast<double*>(P(b, s, L.inv_mass));
+        init_fill64_kernel<<<B_INIT_BLOCKS, 256, 0, b->st>>>(ia);
+        B_TRY(cudaGetLastError());
+        init_scale_fx_kernel<<<256, 256, 0, b->st>>>(ia.f, reinterpret_cast<long long*>(P(b, s, L.f[0])), cells,
+                                                     ia.inv_mass, FX_FRAC - s.Ef);
+        B_TRY(cudaGetLastError());
     } else {
-        B_TRY(H2D(L.rowv, rowv.data(), 4 * (size_t)Np));
-        B_TRY(H2D(L.colv, colv.data(), 4 * (size_t)Nx));
+        std::vector<float> rowf(rowv.begin(), rowv.end()), colf(colv.begin(), colv.end());
+        B_TRY(H2D(L.rowv, rowf.data(), 4 * (size_t)Np));
+        B_TRY(H2D(L.colv, colf.data(), 4 * (size_t)Nx));
         InitArgs ia;
         ia.f = reinterpret_cast<float*>(P(b, s, L.f[0]));
         ia.Nx = Nx;
@@ -792,10 +940,16 @@ int vlasov_batch_get(vlasov_batch* b, int slot, double* host_f, vlasov_moments_t
     B_TRY(cudaStreamSynchronize(b->st));
     const size_t cells = (size_t)s.req.Nx * s.req.Np;
     if (host_f) {
-        std::vector<float> tmp(cells);
         const int cur = s.steps_done & 1;
-        B_TRY(cudaMemcpy(tmp.data(), P(b, s, s.L.f[cur]), cells * 4, cudaMemcpyDeviceToHost));
-        for (size_t q = 0; q < cells; ++q) host_f[q] = (double)tmp[q];
+        if (b->esz == 8) {
+            std::vector<long long> tmp(cells);
+            B_TRY(cudaMemcpy(tmp.data(), P(b, s, s.L.f[cur]), cells * 8, cudaMemcpyDeviceToHost));
+            for (size_t q = 0; q < cells; ++q) host_f[q] = fx128_to_f64((i128)tmp[q], FX_FRAC - s.Ef);
+        } else {
+            std::vector<float> tmp(cells);
+            B_TRY(cudaMemcpy(tmp.data(), P(b, s, s.L.f[cur]), cells * 4, cudaMemcpyDeviceToHost));
+            for (size_t q = 0; q < cells; ++q) host_f[q] = (double)tmp[q];
+        }
     }
     if (count) *count = 0;
     if (out && max > 0) {
@@ -848,7 +1002,8 @@ int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* 
     if (max_n <= 0)
         for (int q = 0; q < n; ++q) max_n = std::max(max_n, std::max(reqs[q].Nx, reqs[q].Np));
     vlasov_batch* b = nullptr;
-    int rc = vlasov_batch_create(std::max(1, opt->slots), std::max(16, max_n), opt->mem_budget_bytes, opt->stream, &b);
+    int rc = vlasov_batch_create(std::max(1, opt->slots), std::max(16, max_n), opt->mem_budget_bytes,
+                                 opt->precision ? opt->precision : VLASOV_F32, opt->stream, &b);
     if (rc) return rc;
     const int depth = std::max(1, opt->max_inflight);
     std::vector<int> order(n);

@@ -102,7 +102,7 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
 
 // ============================================================================ x-shift (FX64)
 template <bool PERIODIC, bool KIN>
-__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs a, EmulArgs em)
+__device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulArgs& em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
     const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
     const int stride = Nx + 2 * PAD;
     const int tid = threadIdx.x, nthreads = blockDim.x;
-    const int G = gridDim.x;
+    const int G = a.ctas > 0 ? a.ctas : (int)gridDim.x;
     const uint32_t row_bytes = (uint32_t)(Nx * 8);
     const uint32_t tx_bytes = row_bytes + (PERIODIC ? 128u : 0u) + XREC_BYTES;   // row + wrap + record
     const double unit = ldexp(1.0, em.Ef - FX_FRAC);
@@ -293,10 +293,29 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs
     }
 }
 
+template <bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs a, EmulArgs em)
+{
+    xshift_fx_body<PERIODIC, KIN>(a, em);
+}
+
+// Batched form: blockIdx.y selects the slot; args[slot * 2 + ver[slot]] and ems[slot] are its
+// arguments (free slots carry Np = 0).
+template <bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_batch_kernel(const XShiftArgs* __restrict__ args,
+                                                                            const EmulArgs* __restrict__ ems,
+                                                                            const int* __restrict__ ver)
+{
+    const int slot = blockIdx.y;
+    const XShiftArgs a = args[slot * 2 + ver[slot]];
+    if (a.Np <= 0 || (int)blockIdx.x >= a.Np || (a.ctas > 0 && (int)blockIdx.x >= a.ctas)) return;
+    const EmulArgs em = ems[slot];
+    xshift_fx_body<PERIODIC, KIN>(a, em);
+}
+
 // ============================================================================ p-shift (FX64)
 template <bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                     PShiftArgs a, EmulArgs em)
+__device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
@@ -319,7 +338,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_barrier_init();
-        prefetch_tensormap(&tmap);
+        prefetch_tensormap(tmap);
     }
     __syncthreads();
 
@@ -327,7 +346,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
         if (t.smem_ok) {
             mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * 8));
             for (int q = 0; q < t.nb; ++q)
-                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, &tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
+                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
         } else {
             mbar_arrive_expect_tx(&bars[b], 0u);
         }
@@ -441,6 +460,30 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __gri
     }
 }
 
+template <bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                     PShiftArgs a, EmulArgs em)
+{
+    pshift_fx_body<PPER>(&tmap, a, em);
+}
+
+// Batched form: the slot's tensor map sits in global memory next to its arguments.
+template <bool PPER>
+__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_batch_kernel(const CUtensorMap* __restrict__ tmaps,
+                                                                           const PShiftArgs* __restrict__ args,
+                                                                           const EmulArgs* __restrict__ ems,
+                                                                           const int* __restrict__ ver)
+{
+    const int slot = blockIdx.y;
+    const int k = slot * 2 + ver[slot];
+    const PShiftArgs a = args[k];
+    if (a.Nx <= 0) return;
+    const EmulArgs em = ems[slot];
+    pshift_fx_body<PPER>(tmaps + k, a, em);
+}
+
+int xshift_fx_max_cols(int threads) { return XF_V * threads * XF_MAXCH; }
+
 size_t pshift_fx_smem_bytes() { return 256 + 2 * (size_t)PSF_RB * PS_TW * 8; }
 
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
@@ -467,6 +510,28 @@ cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap,
     return cudaGetLastError();
 }
 
+cudaError_t launch_xshift_fx_batch(bool periodic, bool kin, int slots, int ctas_per_slot, size_t smem,
+                                   const XShiftArgs* args, const EmulArgs* ems, const int* ver, cudaStream_t st)
+{
+    const dim3 grid(ctas_per_slot, slots);
+    if (periodic) {
+        if (kin) xshift_fx_batch_kernel<true, true><<<grid, XS_THREADS_MIN, smem, st>>>(args, ems, ver);
+        else xshift_fx_batch_kernel<true, false><<<grid, XS_THREADS_MIN, smem, st>>>(args, ems, ver);
+    } else {
+        if (kin) xshift_fx_batch_kernel<false, true><<<grid, XS_THREADS_MIN, smem, st>>>(args, ems, ver);
+        else xshift_fx_batch_kernel<false, false><<<grid, XS_THREADS_MIN, smem, st>>>(args, ems, ver);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pshift_fx_batch(int slots, int ctas_per_slot, const CUtensorMap* tmaps, const PShiftArgs* args,
+                                   const EmulArgs* ems, const int* ver, cudaStream_t st)
+{
+    const dim3 grid(ctas_per_slot, slots);
+    pshift_fx_batch_kernel<false><<<grid, PS_TW * PS_RG, pshift_fx_smem_bytes(), st>>>(tmaps, args, ems, ver);
+    return cudaGetLastError();
+}
+
 cudaError_t set_kernel_attributes_fx(int max_smem)
 {
     cudaError_t e = cudaSuccess;
@@ -478,6 +543,11 @@ cudaError_t set_kernel_attributes_fx(int max_smem)
     VL_ATTR((xshift_fx_kernel<false, false>));
     VL_ATTR((pshift_fx_kernel<true>));
     VL_ATTR((pshift_fx_kernel<false>));
+    VL_ATTR((xshift_fx_batch_kernel<true, true>));
+    VL_ATTR((xshift_fx_batch_kernel<true, false>));
+    VL_ATTR((xshift_fx_batch_kernel<false, true>));
+    VL_ATTR((xshift_fx_batch_kernel<false, false>));
+    VL_ATTR((pshift_fx_batch_kernel<false>));
 #undef VL_ATTR
     return e;
 }

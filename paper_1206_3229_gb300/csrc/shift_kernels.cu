@@ -138,7 +138,7 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
     const int stride = Nx + 2 * PAD;
     const int tid = threadIdx.x, nthreads = blockDim.x;
-    const int G = gridDim.x;
+    const int G = a.ctas > 0 ? a.ctas : (int)gridDim.x;
     const T* __restrict__ wrow = static_cast<const T*>(a.w);
     const T* __restrict__ gdrow = static_cast<const T*>(a.gd);
     const uint32_t row_bytes = (uint32_t)(Nx * sizeof(T));
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_batch_kernel(const X
 {
     const int slot = blockIdx.y;
     const XShiftArgs a = args[slot * 2 + ver[slot]];
-    if (a.Np <= 0 || (int)blockIdx.x >= a.Np) return;
+    if (a.Np <= 0 || (int)blockIdx.x >= a.Np || (a.ctas > 0 && (int)blockIdx.x >= a.ctas)) return;
     xshift_body<T, PERIODIC, KIN>(a);
 }
 

@@ -111,6 +111,8 @@ struct XShiftArgs {
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
     double pmin, dp;
     int* err;
+    int ctas = 0;         // CTAs that share the rows (row stride; the partials above have this many
+                          // entries); 0: gridDim.x.  CTAs at or past it do nothing.
 };
 
 // Filters of the emulated-FP64 sweeps (emul.cuh), structure-of-arrays over n lines:
@@ -224,6 +226,7 @@ cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUten
 cudaError_t set_kernel_attributes(int max_smem);
 cudaError_t set_kernel_attributes_e(int max_smem);
 int xshift_e_max_cols(int threads);
+int xshift_fx_max_cols(int threads);
 size_t pshift_e_smem_bytes();
 cudaError_t xshift_e_occupancy(bool periodic, size_t smem, int* blocks);
 cudaError_t pshift_e_occupancy(int* blocks);
@@ -248,15 +251,19 @@ cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double*
 
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st);
 
-// Batched forms (FP32 storage): grid.y = slot; per-slot arguments (two buffer parities for the
-// sweeps) live in device arrays, so one captured graph serves any set of occupied slots.
+// Batched forms (FP32 or FX64 storage): grid.y = slot; per-slot arguments (two buffer parities
+// for the sweeps) live in device arrays, so one captured graph serves any set of occupied slots.
 cudaError_t launch_xshift_batch(bool periodic, bool kin, int slots, int ctas_per_slot, size_t smem,
                                 const XShiftArgs* args, const int* ver, cudaStream_t st);
 cudaError_t launch_pshift_batch(int slots, int ctas_per_slot, const CUtensorMap* tmaps, const PShiftArgs* args,
                                 const int* ver, cudaStream_t st);
+cudaError_t launch_xshift_fx_batch(bool periodic, bool kin, int slots, int ctas_per_slot, size_t smem,
+                                   const XShiftArgs* args, const EmulArgs* ems, const int* ver, cudaStream_t st);
+cudaError_t launch_pshift_fx_batch(int slots, int ctas_per_slot, const CUtensorMap* tmaps, const PShiftArgs* args,
+                                   const EmulArgs* ems, const int* ver, cudaStream_t st);
 cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColReduceArgs* args, cudaStream_t st);
-cudaError_t launch_ring_batch(int slots, int max_n, const RingArgs* args, cudaStream_t st);
-cudaError_t launch_pparams_batch(int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
+cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st);
+cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);

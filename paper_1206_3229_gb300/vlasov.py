@@ -68,11 +68,11 @@ class Result(ctypes.Structure):
 
 class ServeOptions(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_n", ctypes.c_int), ("mem_budget_bytes", ctypes.c_longlong),
-                ("max_inflight", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_inflight", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 def request_from_workload(w: Workload, steps: int | None = None, arrival_s: float = 0.0) -> Request:
-    """Batched-form request for a workload description (FP32 storage; p always zero outside)."""
+    """Batched-form request for a workload description (p always zero outside)."""
     return Request(MODELS[w.model], w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, int(w.x_periodic), w.eps, w.G,
                    w.dt, 0 if w.init == "box" else 1, w.x0, w.p0, w.noise, w.mode_amp, w.seed,
                    int(w.steps if steps is None else steps), float(arrival_s))
@@ -82,13 +82,21 @@ def moments_row(m: Moments) -> list[float]:
     return [getattr(m, f) for f in MOMENT_FIELDS] + [m.step]
 
 
-class Batch:
-    """vlasov_batch_*: many simulations advanced by one launch per sub-step."""
+def _batch_precision(precision) -> int:
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if p not in (F32, FX64):
+        raise ValueError("batched form: precision 'f32' or 'fx64'")
+    return p
 
-    def __init__(self, slots: int, max_n: int, mem_budget_bytes: int, stream: int | None = None):
+
+class Batch:
+    """vlasov_batch_*: many simulations advanced by one launch per sub-step (FP32 or FX64 storage)."""
+
+    def __init__(self, slots: int, max_n: int, mem_budget_bytes: int, stream: int | None = None,
+                 precision: str | int = "f32"):
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.vlasov_batch_create(int(slots), int(max_n), int(mem_budget_bytes),
+        _check(lib.vlasov_batch_create(int(slots), int(max_n), int(mem_budget_bytes), _batch_precision(precision),
                                        ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
         self._h, self._lib = h, lib
 
@@ -138,17 +146,17 @@ class Batch:
         _check(self._lib.vlasov_batch_release(self._h, int(slot)))
 
 
-def batch_footprint(req: Request) -> int:
-    return int(load().vlasov_batch_footprint(ctypes.byref(req)))
+def batch_footprint(req: Request, precision: str | int = "f32") -> int:
+    return int(load().vlasov_batch_footprint(ctypes.byref(req), _batch_precision(precision)))
 
 
 def serve(reqs: list[Request], slots: int, mem_budget_bytes: int, max_n: int = 0, max_inflight: int = 4,
-          stream: int | None = None):
+          stream: int | None = None, precision: str | int = "f32"):
     """vlasov_serve: continuous batching of a request stream.  Returns (results, makespan_s)."""
     lib = load()
     arr = (Request * len(reqs))(*reqs)
     res = (Result * max(len(reqs), 1))()
-    opt = ServeOptions(int(slots), int(max_n), int(mem_budget_bytes), int(max_inflight),
+    opt = ServeOptions(int(slots), int(max_n), int(mem_budget_bytes), int(max_inflight), _batch_precision(precision),
                        ctypes.c_void_p(stream) if stream else None)
     mk = ctypes.c_double(0.0)
     _check(lib.vlasov_serve(arr, len(reqs), ctypes.byref(opt), res, ctypes.byref(mk)))
@@ -193,8 +201,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_step_timed.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_xshift_density_noalloc.argtypes = [vp, vp, vp, ip, ip, ctypes.c_double, ctypes.c_double, ip,
                                                       vp, vp]
-        lib.vlasov_batch_create.argtypes = [ip, ip, ctypes.c_longlong, vp, ctypes.POINTER(vp)]
-        lib.vlasov_batch_footprint.argtypes = [ctypes.POINTER(Request)]
+        lib.vlasov_batch_create.argtypes = [ip, ip, ctypes.c_longlong, ip, vp, ctypes.POINTER(vp)]
+        lib.vlasov_batch_footprint.argtypes = [ctypes.POINTER(Request), ip]
         lib.vlasov_batch_admit.argtypes = [vp, ctypes.POINTER(Request), dp, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_batch_step.argtypes = [vp, ip]
         lib.vlasov_batch_slot_steps.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]

@@ -146,3 +146,98 @@ def test_batch_rejects_bad_requests():
         assert ei.value.code == V.ESTATE
         b.release(k)
         b.admit(V.request_from_workload(I.HMF_256, 1))
+
+
+# ------------------------------------------------------------------------------ FX64 (FP64-accurate) slots
+FX_CASES = [I.HMF_256, I.RING_2048.resized(128, 128), I.SHEET_4096.resized(256, 256),
+            I.HMF_4096_UNSTABLE.resized(256, 256)]
+
+
+@pytest.mark.parametrize("w", FX_CASES, ids=lambda w: w.name)
+def test_fx64_batch_is_bitwise_the_single_grid_fx64_path(w):
+    """Same kernels, same fixed-point bound from the same f0: identical f; the moment sums are exact
+    integers except the kinetic term's per-CTA FP64 partials (grouped differently)."""
+    steps = 25
+    f0 = I.initial_state(w)
+    with V.Batch(2, 512, GB, precision="fx64") as b:
+        k = b.admit(V.request_from_workload(w, steps), f0)
+        b.step(steps)
+        fb, mb = b.get(k, w.nx, w.np)
+    with V.Sim.from_workload(w, precision="fx64") as s:
+        s.set_f(f0)
+        s.step(steps)
+        ms = s.moments()
+        fs = s.get_f()
+    assert np.array_equal(fb, fs)
+    for col in (1, 2, 3, 5):   # mass, Mx, My, potential
+        assert np.array_equal(mb[:, col], ms[:, col]), col
+    assert np.max(np.abs(mb[:, 4] - ms[:, 4])) <= 1e-14 * max(1.0, np.abs(ms[:, 4]).max())
+
+
+def test_fx64_batch_alone_equals_in_mix_bitwise():
+    steps = 20
+    f_a = None
+    with V.Batch(2, 512, GB, precision="fx64") as b:
+        k = b.admit(V.request_from_workload(HMF_R, steps))
+        b.step(steps + 2)
+        f_a, m_a = b.get(k, HMF_R.nx, HMF_R.np)
+    with V.Batch(6, 512, 2 * GB, precision="fx64") as b:
+        others = [b.admit(V.request_from_workload(w, 5 + 4 * q)) for q, w in enumerate(MIX[:3])]
+        b.step(3)
+        k = b.admit(V.request_from_workload(HMF_R, steps))
+        b.step(1)
+        b.admit(V.request_from_workload(MIX[3], 9))
+        b.step(steps + 4)
+        f_b, m_b = b.get(k, HMF_R.nx, HMF_R.np)
+        assert b.steps_done(k) == steps
+        assert all(b.steps_done(o) == 5 + 4 * q for q, o in enumerate(others))
+    assert np.array_equal(f_a, f_b)
+    assert np.array_equal(m_a, m_b)
+
+
+def test_fx64_batch_against_oracle_fp64_tolerance():
+    """The FX64 batched form meets the FP64 parity bar: 100 HMF steps at 256^2."""
+    w = HMF_R
+    steps = 100
+    f0 = I.initial_state(w)
+    fo, mo = O.run(grid_of(w), f0, steps)
+    with V.Batch(1, 256, GB, precision="fx64") as b:
+        k = b.admit(V.request_from_workload(w, steps), f0)
+        b.step(steps)
+        fb, mb = b.get(k, w.nx, w.np)
+    assert np.max(np.abs(fb - fo)) <= 1e-12 * fo.max()
+    assert np.max(np.abs(np.hypot(mb[:, 2], mb[:, 3]) - np.hypot(mo[:, 2], mo[:, 3]))) <= 1e-12
+
+
+@pytest.mark.parametrize("w", [I.HMF_256, I.SHEET_4096.resized(256, 256), I.HMF_4096_UNSTABLE.resized(128, 256)],
+                         ids=lambda w: w.name)
+def test_fx64_device_initial_state_matches_input_generator(w):
+    with V.Batch(1, 256, GB, precision="fx64") as b:
+        k = b.admit(V.request_from_workload(w, 0))
+        f, _ = b.get(k, w.nx, w.np)
+    ref = I.initial_state(w)
+    assert np.max(np.abs(f - ref)) <= 1e-14 * ref.max()
+
+
+def test_fx64_serve_results_equal_single_grid_moments():
+    pool = [I.HMF_256, I.RING_2048.resized(128, 128), I.SHEET_4096.resized(256, 256)]
+    reqs, ws = [], []
+    for q in range(6):
+        w = pool[q % len(pool)]
+        steps = 6 + 3 * q
+        reqs.append(V.request_from_workload(w, steps, arrival_s=0.002 * q))
+        ws.append((w, steps))
+    budget = 3 * max(V.batch_footprint(r, "fx64") for r in reqs)
+    results, _ = V.serve(reqs, slots=3, mem_budget_bytes=budget, max_n=256, precision="fx64")
+    for (w, steps), r in zip(ws, results):
+        assert r.status == 0 and r.steps == steps
+        with V.Batch(1, 256, GB, precision="fx64") as b:
+            k = b.admit(V.request_from_workload(w, steps))
+            b.step(steps)
+            _, m = b.get(k, w.nx, w.np)
+        assert V.moments_row(r.last) == list(m[-1])
+
+
+def test_batch_rejects_other_precisions():
+    with pytest.raises(ValueError):
+        V.Batch(1, 256, GB, precision="f64")
