@@ -217,9 +217,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                     colacc[c][v] += Tc;
                     rowsum += Tc;
                 }
-                double2* o = reinterpret_cast<double2*>(orow + i);
-                o[0] = make_double2(out[0], out[1]);
-                o[1] = make_double2(out[2], out[3]);
+                st_global_v4_f64(orow + i, out[0], out[1], out[2], out[3]);   // one full 32-byte sector
             }
         }
         if constexpr (KIN) {

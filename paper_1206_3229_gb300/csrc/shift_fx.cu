@@ -215,9 +215,9 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                         colacc[c][v] += Tc;
                         rowsum += Tc;
                     }
-                    longlong2* o = reinterpret_cast<longlong2*>(orow + i);
 #pragma unroll
-                    for (int v = 0; v < XF_V / 2; ++v) o[v] = make_longlong2(out[2 * v], out[2 * v + 1]);
+                    for (int v = 0; v < XF_V; v += 4)   // full 32-byte sectors per instruction
+                        st_global_v4_b64(orow + i + v, out[v], out[v + 1], out[v + 2], out[v + 3]);
                 }
             }
             if constexpr (KIN) {
