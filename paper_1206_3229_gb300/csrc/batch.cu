@@ -542,6 +542,8 @@ int validate_request(const vlasov_request* r, int max_n)
     if (r->Nx > max_n || r->Np > max_n) return bfail(VLASOV_EINVAL, "grid larger than the batch maximum");
     if (!(r->dt > 0) || !(r->xmax > r->xmin) || !(r->pmax > r->pmin)) return bfail(VLASOV_EINVAL, "bad domain or dt");
     if (r->model == VLASOV_RING && !(r->eps > 0)) return bfail(VLASOV_EINVAL, "ring needs eps > 0");
+    if (std::max(std::fabs(r->pmin), std::fabs(r->pmax)) >= 2896.0)
+        return bfail(VLASOV_EINVAL, "|p| must stay below 2896 (fixed-point kinetic weights)");
     if (r->steps < 0) return bfail(VLASOV_EINVAL, "steps < 0");
     return VLASOV_OK;
 }
@@ -800,6 +802,7 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
         XRec rc_;
         std::memset(&rc_, 0, sizeof rc_);
         rc_.n0 = Ls.n0;
+        rc_.p2q = std::llround(std::ldexp(0.5 * p * p, KIN_Q));
         max_n0 = std::max(max_n0, std::abs(Ls.n0));
         rc_.g64 = Ls.g;
         rc_.d64 = Ls.d;

@@ -77,21 +77,21 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
 #pragma unroll
     for (int h = 0; h < XF_W / 2; ++h) {
         const longlong2 pr = q[h];
+        int kx0, kx1;
+        float kf0, rf0, kf1, rf1;
+        fx_split(pr.x, kx0, kf0, rf0);
+        fx_split(pr.y, kx1, kf1, rf1);
+        const float2 xa = make_float2(kf0, rf0), xb = make_float2(kf1, rf1);
 #pragma unroll
-        for (int z = 0; z < 2; ++z) {
-            const int u = 2 * h + z;
-            int kx;
-            float kf, rf;
-            fx_split(z ? pr.y : pr.x, kx, kf, rf);
-            const float2 x2 = make_float2(kf, rf);
-#pragma unroll
-            for (int v = 0; v < XF_V; ++v) {
-                const int t = u - A - v;   // tap of element u for output v
-                if (t >= 0 && t < NTAP) {
-                    M[v] = mad_wide(w.Wh[t], kx, M[v]);
-                    S[v] = __ffma2_rn(w.wlr[t], x2, S[v]);
-                }
-            }
+        for (int v = 0; v < XF_V; ++v) {
+            const int t0 = 2 * h - A - v, t1 = t0 + 1;   // taps of the two elements for output v
+            const bool v0 = t0 >= 0 && t0 < NTAP, v1 = t1 >= 0 && t1 < NTAP;
+            // products first, then one three-input 64-bit sum (IADD3 + IADD3.X) per pair
+            if (v0 && v1) M[v] = M[v] + (long long)w.Wh[t0] * (long long)kx0 + (long long)w.Wh[t1] * (long long)kx1;
+            else if (v0) M[v] += (long long)w.Wh[t0] * (long long)kx0;
+            else if (v1) M[v] += (long long)w.Wh[t1] * (long long)kx1;
+            if (v0) S[v] = __ffma2_rn(w.wlr[t0], xa, S[v]);
+            if (v1) S[v] = __ffma2_rn(w.wlr[t1], xb, S[v]);
         }
     }
 #pragma unroll
@@ -108,7 +108,9 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
     unsigned char* smem_raw = align128(smem_dyn);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
-    __shared__ double red[32];
+    __shared__ i128 redk[32];
+    __shared__ unsigned int done_cnt[8];   // warps finished with each stage's current row
+    __shared__ unsigned int issued[8];     // copies issued into each stage
     unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)a.stages * (a.Nx + 2 * a.pad));
 
     const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
@@ -123,8 +125,13 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
     bool bad = false;
     uint32_t rng = 0;   // OR of (high word + 2^29) of every stored result
 
+    const int lane = tid & 31, nwarps = nthreads >> 5;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bars[s], 1);
+            done_cnt[s] = 0;
+            issued[s] = 0;
+        }
         fence_barrier_init();
     }
     if constexpr (!PERIODIC) {
@@ -141,6 +148,7 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
     auto issue = [&](int s, int r) {
         long long* dst = bufs + (size_t)s * stride + PAD;
         const long long* src = fin + (size_t)r * Nx;
+        issued[s] += 1;
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
         if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 128u, &bars[s]);
@@ -159,14 +167,14 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
     for (int c = 0; c < XF_MAXCH; ++c)
 #pragma unroll
         for (int v = 0; v < XF_V; ++v) colacc[c][v] = 0;
-    double kin = 0.0;
+    i128 kin = 0;   // units 2^(Ef-51-KIN_Q)
 
     int it = 0;
     int r = blockIdx.x;
     bool failed = false;
     for (; r < Np; r += G, ++it) {
         const int s = it % S;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / S) & 1), WAIT_LIMIT_NS);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], (uint32_t)((it / S) & 1), WAIT_LIMIT_NS));
         long long rowsum = 0;
         if (ok) {
             const long long* rowbuf = bufs + (size_t)s * stride + PAD;
@@ -220,34 +228,35 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                         st_global_v4_b64(orow + i + v, out[v], out[v + 1], out[v + 2], out[v + 3]);
                 }
             }
-            if constexpr (KIN) {
-                const double pj = a.pmin + (double)r * a.dp;
-                kin = fma(0.5 * pj * pj, fx128_to_f64((i128)rowsum, 51 - em.Ef), kin);
-            }
+            if constexpr (KIN) kin += (i128)rowsum * (i128)rc->p2q;   // exact: sum_i f * p_j^2/2
         }
-        if (__syncthreads_or(!ok)) {
+        if (!ok) {
             failed = true;
             break;
         }
-        if (tid == 0) {
-            const int rn = r + S * G;
-            if (rn < Np) {
-                fence_proxy_async_smem();
-                issue(s, rn);
+        // No CTA-wide barrier per row: the last warp done with stage s refills it.
+        __syncwarp();
+        if (lane == 0) {
+            unsigned int prev;
+            asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(prev) : "r"(smem_u32(&done_cnt[s])) : "memory");
+            if (prev == (unsigned int)nwarps - 1) {
+                done_cnt[s] = 0;
+                const int rn = r + S * G;
+                if (rn < Np) {
+                    fence_proxy_async_smem();
+                    issue(s, rn);
+                }
             }
         }
     }
+    failed = __syncthreads_or(failed);
     if (bad || rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
 
     if (failed) {
         if (tid == 0) {
             atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
-            for (int k = 0; k < S; ++k) {
-                const int rr = r + k * G;
-                if (rr >= Np) break;
-                const int itk = it + k;
-                mbar_wait_bounded(&bars[itk % S], (uint32_t)((itk / S) & 1), WAIT_LIMIT_NS);
-            }
+            for (int k = 0; k < S; ++k)   // the last copy issued into each stage must land before exit
+                if (issued[k] > 0) mbar_wait_bounded(&bars[k], (uint32_t)((issued[k] - 1) & 1), WAIT_LIMIT_NS);
         }
         __syncthreads();
         return;
@@ -280,16 +289,8 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
         }
     }
     if constexpr (KIN) {
-        double v = kin;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red[tid >> 5] = v;
-        __syncthreads();
-        if (tid == 0) {
-            double sum = 0.0;
-            for (int q = 0; q < (nthreads + 31) / 32; ++q) sum += red[q];
-            a.kinpart[blockIdx.x] = sum;
-        }
+        const i128 t = block_sum_i128(kin, redk);
+        if (tid == 0) a.kinpart[blockIdx.x] = fx128_to_f64(t, 51 + KIN_Q - em.Ef);
     }
 }
 

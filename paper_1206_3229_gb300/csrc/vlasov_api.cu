@@ -148,7 +148,7 @@ int alloc_emul(EmulParamsDev& e, int n)
 // Host-side filters for n lines with displacements disp[] (cells), uploaded to p (and, for the
 // emulated FP64 sweeps, their integer/FP32 split to e; and as staged x-shift records to rec).
 int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, int* max_abs_n0,
-                  EmulParamsDev* e = nullptr, void* rec = nullptr)
+                  EmulParamsDev* e = nullptr, void* rec = nullptr, bool rows_are_p = false)
 {
     if (rec) {
         std::vector<unsigned char> buf((size_t)n * XREC_BYTES, 0);
@@ -166,6 +166,10 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
                 r.w64[t] = L.w[t];
                 r.w32[t] = (float)L.w[t];
                 emul_weight(L.w[t], r.Wh[t], r.wl[t], r.wf[t]);
+            }
+            if (rows_are_p) {
+                const double pj = s->pmin + (double)l * s->dp;   // as the kernels' p_j
+                r.p2q = std::llround(std::ldexp(0.5 * pj * pj, KIN_Q));
             }
             std::memcpy(&buf[(size_t)l * XREC_BYTES], &r, sizeof r);
         }
@@ -549,6 +553,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     if (!(dt > 0) || !std::isfinite(dt)) return fail(VLASOV_EINVAL, "dt must be > 0");
     if (!(d->xmax > d->xmin) || !(d->pmax > d->pmin)) return fail(VLASOV_EINVAL, "empty domain");
     if (model == VLASOV_RING && !(d->eps > 0)) return fail(VLASOV_EINVAL, "ring model needs eps > 0");
+    if (std::max(std::fabs(d->pmin), std::fabs(d->pmax)) >= 2896.0)
+        return fail(VLASOV_EINVAL, "|p| must stay below 2896 (fixed-point kinetic weights)");
 
     vlasov_sim* s = new vlasov_sim();
     s->model = model;
@@ -627,7 +633,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     int max_n0 = 0;
     CTRY(cudaMalloc(&s->xrec, (size_t)XREC_BYTES * Np));
     CTRY(cudaMalloc(&s->srec, (size_t)XREC_BYTES * std::max(Nx, Np)));
-    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0, &s->xe, s->xrec));
+    TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0, &s->xe, s->xrec, true));
 
     // x-shift launch shape: whole rows staged per CTA.
     s->xthreads = XS_THREADS_MIN;

@@ -91,8 +91,10 @@ struct XRec {
     float wf[NTAP];
     float w32[NTAP];
     float g32, d32;
+    long long p2q;        // round(p_j^2 / 2 * 2^KIN_Q) of the row: exact kinetic-energy weight
 };
 constexpr int XREC_BYTES = 288;
+constexpr int KIN_Q = 40;   // |p| < 2896 keeps p^2/2 * 2^KIN_Q below 2^62
 static_assert(sizeof(XRec) <= XREC_BYTES, "XRec must fit its staged slot");
 
 struct XShiftArgs {
