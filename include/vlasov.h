@@ -133,13 +133,16 @@ int vlasov_kernels_per_step(const vlasov_sim* sim);
    vlasov_kernels_per_step; max_launches must be at least that), *nlaunch the slot count.  Slots in
    order: x-shift (step 1, density partials), density/moment reduction, [ring force], p-shift
    filters (force), p-shift (step 3), x-shift (step 4, density+kinetic partials), moment
-   reduction, [ring potential].  Syncs. */
+   reduction, [ring potential].  For the HMF model with 8-byte storage the reduction and the
+   filters after step 1 are one launch (Mx, My, force and filters), so there are five slots.
+   Syncs. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
 /* ---------------------------------------------------------------------------------------------
    Batched form and serving.  Many simulations of different models, grid sizes, initial states and
    step counts advance together: each kernel of a Strang step is launched once for all of them
-   (FP32 storage of f, FP64-accurate displacements and moment sums), from one captured CUDA graph.
+   (FP32 or FX64 storage of f, FP64-accurate displacements and moment sums), from one captured
+   CUDA graph.
    p is always f = 0 outside in the batched form.  Results of a simulation do not depend on which
    others share the batch (each keeps its own fixed CTA-to-row mapping; sums are order-free). */
 typedef struct vlasov_batch vlasov_batch;

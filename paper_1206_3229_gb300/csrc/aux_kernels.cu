@@ -538,6 +538,63 @@ cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PPa
     return cudaGetLastError();
 }
 
+// HMF after the first x-shift, 8-byte storage.  Every block forms the cos/sin-weighted column-sum
+// totals from the exact int64 column sums itself (the same integers in every block, so the same
+// Mx, My as the separate reduction), then F_i = -Mx sin x_i + My cos x_i and the parameters of its
+// columns.  The last block to finish reading clears the column sums for the second x-shift.
+constexpr int PPF_THREADS = 256;
+__global__ void __launch_bounds__(PPF_THREADS) pparams_hmf_fused_kernel(PParamsArgs a)
+{
+    __shared__ i128 red4[128];
+    __shared__ bool is_last;
+    const int i = blockIdx.x * PPF_THREADS + threadIdx.x;
+    i128 m = 0, x = 0, y = 0, z = 0;
+    const i128 half = (i128)1 << 31;
+    constexpr int U = 4;
+    for (int k0 = threadIdx.x; k0 < a.Nx; k0 += U * PPF_THREADS) {
+        long long t[U], c[U], sn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * PPF_THREADS;
+            const bool in = k < a.Nx;
+            t[u] = in ? (long long)__ldcg(a.colacc + k) : 0ll;
+            c[u] = in ? __ldg(a.cosfx + k) : 0ll;
+            sn[u] = in ? __ldg(a.sinfx + k) : 0ll;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            x += ((i128)c[u] * (i128)t[u] + half) >> 32;   // scale 2^-(k_col + 30)
+            y += ((i128)sn[u] * (i128)t[u] + half) >> 32;
+        }
+    }
+    block_sum4_i128(m, x, y, z, red4);
+    // done with the column sums: the last block clears them
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        unsigned long long* acc = const_cast<unsigned long long*>(a.colacc);
+        for (int k = threadIdx.x; k < a.Nx; k += PPF_THREADS) acc[k] = 0ull;
+        if (threadIdx.x == 0) *a.ticket = 0u;
+    }
+    if (i >= a.Nx) return;
+    const double Mx = a.dxdp * fx128_to_f64(x, a.k_col + 30);
+    const double My = a.dxdp * fx128_to_f64(y, a.k_col + 30);
+    const double F = -Mx * a.sintab[i] + My * a.costab[i];
+    if (a.Fout) a.Fout[i] = F;
+    pparams_fixed(a, i, F * a.cp);
+}
+
+cudaError_t launch_pparams_hmf_fused(const PParamsArgs& a, cudaStream_t st)
+{
+    pparams_hmf_fused_kernel<<<(a.Nx + PPF_THREADS - 1) / PPF_THREADS, PPF_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st)
 {
     const int grid = (a.Nx + 63) / 64;

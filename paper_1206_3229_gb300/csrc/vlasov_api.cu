@@ -90,7 +90,7 @@ struct vlasov_sim {
     double* Fout = nullptr;
     void* blockpart = nullptr;  // int128 [crgrid][3]
     void* ringpart = nullptr;   // int128 [(Nx+7)/8]
-    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring
+    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring, [2] fused HMF filters
     unsigned long long* maxbits = nullptr;
     Scalars* sc = nullptr;
     double* costab = nullptr;
@@ -388,7 +388,7 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     return a;
 }
 
-int launch_pparams_only(vlasov_sim* s, double* Fout)
+int launch_pparams_only(vlasov_sim* s, double* Fout, bool hmf_fused = false)
 {
     PParamsArgs a;
     a.Nx = s->Nx;
@@ -406,6 +406,16 @@ int launch_pparams_only(vlasov_sim* s, double* Fout)
     a.Wh = (s->emul || s->fx) ? s->pe.Wh : nullptr;
     a.wl = (s->emul || s->fx) ? s->pe.wl : nullptr;
     a.wf = (s->emul || s->fx) ? s->pe.wf : nullptr;
+    if (hmf_fused) {
+        a.colacc = s->colacc;
+        a.cosfx = s->cosfx;
+        a.sinfx = s->sinfx;
+        a.k_col = s->k_col;
+        a.dxdp = s->dx * s->dp;
+        a.ticket = &s->tickets[2];
+        CU_TRY(launch_pparams_hmf_fused(a, s->st));
+        return VLASOV_OK;
+    }
     CU_TRY(launch_pparams(s->esz, a, s->st));
     return VLASOV_OK;
 }
@@ -444,13 +454,17 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false, s->xrec), s->xp, s->xe, false));
     MARK();
     // step 2: rho, moments, F^(I), p-shift filters
-    CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
-    MARK();
-    if (s->model == VLASOV_RING) {
-        CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
+    if (s->model == VLASOV_HMF && s->esz == 8) {
+        // one launch: Mx, My from the exact column sums, then F and the filters
+        int rc = launch_pparams_only(s, nullptr, true);
+        if (rc) return rc;
+    } else {
+        CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
         MARK();
-    }
-    {
+        if (s->model == VLASOV_RING) {
+            CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
+            MARK();
+        }
         int rc = launch_pparams_only(s, nullptr);
         if (rc) return rc;
     }
@@ -678,8 +692,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(cudaMalloc(&s->blockpart, 16 * 3 * (size_t)s->crgrid));
     CTRY(cudaMalloc(&s->ringpart, 16 * (size_t)ring_blocks(Nx)));
     CTRY(cudaMalloc(&s->maxbits, sizeof(unsigned long long)));
-    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 2));
-    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 2, s->st));
+    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 3));
+    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 3, s->st));
     CTRY(cudaMalloc(&s->sc, sizeof(Scalars)));
     CTRY(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->st));
     CTRY(cudaMalloc(&s->hist, sizeof(MomentRec) * HIST_CAP));
@@ -951,7 +965,8 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 int vlasov_kernels_per_step(const vlasov_sim* s)
 {
     if (!s) return 0;
-    return s->model == VLASOV_RING ? 8 : 6;
+    if (s->model == VLASOV_RING) return 8;
+    return (s->model == VLASOV_HMF && s->esz == 8) ? 5 : 6;
 }
 
 }  // extern "C"

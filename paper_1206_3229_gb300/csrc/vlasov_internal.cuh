@@ -173,6 +173,14 @@ struct ColReduceArgs {
 };
 
 struct PParamsArgs {
+    // HMF with exact column sums: the kernel itself forms Mx, My from these (every block the same
+    // exact integer totals), and the last block to finish clears colacc for the next sweep.
+    const unsigned long long* colacc = nullptr;
+    const long long* cosfx = nullptr;
+    const long long* sinfx = nullptr;
+    int k_col = 0;
+    double dxdp = 0;
+    unsigned int* ticket = nullptr;
     int Nx, model;
     const Scalars* sc;
     const double* costab;
@@ -267,6 +275,9 @@ cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColRedu
 cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st);
 cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
+// HMF, 8-byte storage: density totals from the exact column sums + force + p-shift parameters in
+// one launch (replaces the reduction launch after the first x-shift).
+cudaError_t launch_pparams_hmf_fused(const PParamsArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);
 cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double* colpart, int B,
