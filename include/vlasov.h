@@ -133,9 +133,7 @@ int vlasov_kernels_per_step(const vlasov_sim* sim);
    vlasov_kernels_per_step; max_launches must be at least that), *nlaunch the slot count.  Slots in
    order: x-shift (step 1, density partials), density/moment reduction, [ring force], p-shift
    filters (force), p-shift (step 3), x-shift (step 4, density+kinetic partials), moment
-   reduction, [ring potential].  For the HMF model with 8-byte storage the reduction and the
-   filters after step 1 are one launch (Mx, My, force and filters), so there are five slots.
-   Syncs. */
+   reduction, [ring potential].  Syncs. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
 /* ---------------------------------------------------------------------------------------------

@@ -166,6 +166,20 @@ __device__ __forceinline__ void colreduce_body(const ColReduceArgs& a)
             s = (long long)a.colacc[i];
             a.colacc[i] = 0ull;
         }
+    } else if (a.colpart64) {
+        // exact per-CTA partial rows (already on the column scale): plain int64 sums
+        if (i < a.Nx) {
+            const long long* __restrict__ cp = a.colpart64 + i;
+            int b = grp;
+            for (; b + 7 * CR_GROUPS < a.B; b += 8 * CR_GROUPS) {
+                long long v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcs(cp + (size_t)(b + u * CR_GROUPS) * a.Nx);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s += v[u];
+            }
+            for (; b < a.B; b += CR_GROUPS) s += __ldcs(cp + (size_t)b * a.Nx);
+        }
     } else if (i < a.Nx) {
         const double* __restrict__ cp = a.colpart + i;
         const size_t st = (size_t)a.Nx * CR_GROUPS;
@@ -272,9 +286,76 @@ __global__ void __launch_bounds__(CR_ACC_THREADS) colreduce_acc_kernel(ColReduce
     colreduce_acc_body(a);
 }
 
+// Exact per-CTA partial rows (int64, column scale): 32 columns x 32 row groups per block, so each
+// thread adds only about B/32 partials; warp 0 forms the block's mass and cos/sin-weighted sums with
+// shuffles, and the last block to finish computes the totals (colreduce_final).
+constexpr int CRP_THREADS = 1024;
+__global__ void __launch_bounds__(CRP_THREADS) colreduce_p64_kernel(ColReduceArgs a)
+{
+    __shared__ long long shc[32][33];
+    __shared__ i128 red[33];
+    __shared__ bool is_last;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int nblk = (a.Nx + 31) / 32;
+    if ((int)blockIdx.x >= nblk) return;
+    long long s = 0;
+    if (i < a.Nx) {
+        const long long* __restrict__ cp = a.colpart64 + i;
+        int b = grp;
+        for (; b + 3 * 32 < a.B; b += 4 * 32) {
+            long long v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldcs(cp + (size_t)(b + u * 32) * a.Nx);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += v[u];
+        }
+        for (; b < a.B; b += 32) s += __ldcs(cp + (size_t)b * a.Nx);
+    }
+    shc[grp][lane] = s;
+    __syncthreads();
+    i128* bp = static_cast<i128*>(a.blockpart);
+    if (grp == 0) {
+        i128 cm = 0, cx = 0, cy = 0;
+        if (i < a.Nx) {
+            long long t = 0;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) t += shc[q][lane];
+            a.colfx[i] = t;
+            a.rho[i] = a.dp * fx128_to_f64((i128)t, a.k_col);
+            const i128 half = (i128)1 << 31;
+            cm = (i128)t;
+            cx = ((i128)a.cosfx[i] * (i128)t + half) >> 32;   // scale 2^-(k_col + 30)
+            cy = ((i128)a.sinfx[i] * (i128)t + half) >> 32;
+        }
+        cm = warp_sum_i128(cm);
+        cx = warp_sum_i128(cx);
+        cy = warp_sum_i128(cy);
+        if (lane == 0) {
+            bp[blockIdx.x * 3 + 0] = cm;
+            bp[blockIdx.x * 3 + 1] = cx;
+            bp[blockIdx.x * 3 + 2] = cy;
+            __threadfence();
+            is_last = atomicAdd(a.ticket, 1u) == (unsigned int)nblk - 1;
+        }
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    i128 m = 0, x = 0, y = 0;
+    const volatile i128* vb = bp;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        m += vb[b * 3 + 0];
+        x += vb[b * 3 + 1];
+        y += vb[b * 3 + 2];
+    }
+    colreduce_final(a, m, x, y, red);
+}
+
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st)
 {
     if (a.colacc) colreduce_acc_kernel<<<1, CR_ACC_THREADS, 0, st>>>(a);
+    else if (a.colpart64) colreduce_p64_kernel<<<(a.Nx + 31) / 32, CRP_THREADS, 0, st>>>(a);
     else colreduce_kernel<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -535,63 +616,6 @@ cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PPa
     const dim3 grid((max_n + 63) / 64, slots);
     if (elem_bytes == 8) pparams_batch_kernel<double><<<grid, 64, 0, st>>>(args);
     else pparams_batch_kernel<float><<<grid, 64, 0, st>>>(args);
-    return cudaGetLastError();
-}
-
-// HMF after the first x-shift, 8-byte storage.  Every block forms the cos/sin-weighted column-sum
-// totals from the exact int64 column sums itself (the same integers in every block, so the same
-// Mx, My as the separate reduction), then F_i = -Mx sin x_i + My cos x_i and the parameters of its
-// columns.  The last block to finish reading clears the column sums for the second x-shift.
-constexpr int PPF_THREADS = 256;
-__global__ void __launch_bounds__(PPF_THREADS) pparams_hmf_fused_kernel(PParamsArgs a)
-{
-    __shared__ i128 red4[128];
-    __shared__ bool is_last;
-    const int i = blockIdx.x * PPF_THREADS + threadIdx.x;
-    i128 m = 0, x = 0, y = 0, z = 0;
-    const i128 half = (i128)1 << 31;
-    constexpr int U = 4;
-    for (int k0 = threadIdx.x; k0 < a.Nx; k0 += U * PPF_THREADS) {
-        long long t[U], c[U], sn[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * PPF_THREADS;
-            const bool in = k < a.Nx;
-            t[u] = in ? (long long)__ldcg(a.colacc + k) : 0ll;
-            c[u] = in ? __ldg(a.cosfx + k) : 0ll;
-            sn[u] = in ? __ldg(a.sinfx + k) : 0ll;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            x += ((i128)c[u] * (i128)t[u] + half) >> 32;   // scale 2^-(k_col + 30)
-            y += ((i128)sn[u] * (i128)t[u] + half) >> 32;
-        }
-    }
-    block_sum4_i128(m, x, y, z, red4);
-    // done with the column sums: the last block clears them
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (is_last) {
-        __threadfence();
-        unsigned long long* acc = const_cast<unsigned long long*>(a.colacc);
-        for (int k = threadIdx.x; k < a.Nx; k += PPF_THREADS) acc[k] = 0ull;
-        if (threadIdx.x == 0) *a.ticket = 0u;
-    }
-    if (i >= a.Nx) return;
-    const double Mx = a.dxdp * fx128_to_f64(x, a.k_col + 30);
-    const double My = a.dxdp * fx128_to_f64(y, a.k_col + 30);
-    const double F = -Mx * a.sintab[i] + My * a.costab[i];
-    if (a.Fout) a.Fout[i] = F;
-    pparams_fixed(a, i, F * a.cp);
-}
-
-cudaError_t launch_pparams_hmf_fused(const PParamsArgs& a, cudaStream_t st)
-{
-    pparams_hmf_fused_kernel<<<(a.Nx + PPF_THREADS - 1) / PPF_THREADS, PPF_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -264,6 +264,24 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                 }
             }
         }
+    } else if (a.colpart64) {
+        // exact per-CTA column sums, one partial row per CTA (plain 32-byte stores, no atomics)
+        const int sh = a.k_col + em.Ef - 51;
+        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < XE_MAXCH; ++c) {
+            const int i = XE_V * (tid + c * nthreads);
+            if (i < Nx) {
+                long long q[XE_V];
+#pragma unroll
+                for (int v = 0; v < XE_V; ++v) {
+                    const long long x = colacc[c][v];
+                    q[v] = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+                }
+#pragma unroll
+                for (int v = 0; v < XE_V; v += 4) st_global_v4_b64(cp + i + v, q[v], q[v + 1], q[v + 2], q[v + 3]);
+            }
+        }
     } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll

@@ -277,6 +277,24 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                 }
             }
         }
+    } else if (a.colpart64) {
+        // exact per-CTA column sums, one partial row per CTA (plain 32-byte stores, no atomics)
+        const int sh = a.k_col + em.Ef - 51;
+        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < XF_MAXCH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+                long long q[XF_V];
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long x = colacc[c][v];
+                    q[v] = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+                }
+#pragma unroll
+                for (int v = 0; v < XF_V; v += 4) st_global_v4_b64(cp + i + v, q[v], q[v + 1], q[v + 2], q[v + 3]);
+            }
+        }
     } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll

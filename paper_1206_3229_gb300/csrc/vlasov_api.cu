@@ -90,7 +90,7 @@ struct vlasov_sim {
     double* Fout = nullptr;
     void* blockpart = nullptr;  // int128 [crgrid][3]
     void* ringpart = nullptr;   // int128 [(Nx+7)/8]
-    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring, [2] fused HMF filters
+    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring
     unsigned long long* maxbits = nullptr;
     Scalars* sc = nullptr;
     double* costab = nullptr;
@@ -243,11 +243,14 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.n0 = p.n0;
     a.w = p.w;
     a.gd = p.gd;
-    // FP32 sweeps are memory-bound and many CTAs run them: per-CTA partial rows are cheaper there
-    // than atomics; the compute-bound 8-byte sweeps add exact column sums atomically at their end
-    const bool atomics = s->esz == 8;
-    a.colpart = (reduce && !atomics) ? s->colpart : nullptr;
+    // Column sums of the output: the FX64 / emulated-FP64 sweeps write exact int64 partial rows
+    // (one per CTA; 4096 atomics per CTA at the end of a sweep cost more than these 10 MB of
+    // stores), hardware FP64 adds exact sums atomically, FP32 writes FP64 partial rows.
+    const bool part64 = s->fx || s->emul;
+    const bool atomics = s->esz == 8 && !part64;
+    a.colpart = (reduce && s->esz == 4) ? s->colpart : nullptr;
     a.colacc = (reduce && atomics) ? s->colacc : nullptr;
+    a.colpart64 = (reduce && part64) ? reinterpret_cast<long long*>(s->colpart) : nullptr;
     a.k_col = s->k_col;
     a.kinpart = kin ? s->kinpart : nullptr;
     a.pmin = s->pmin;
@@ -340,7 +343,9 @@ cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs&
 ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments, bool from_acc = true)
 {
     ColReduceArgs a;
-    a.colacc = (from_acc && s->esz == 8) ? s->colacc : nullptr;
+    const bool part64 = from_acc && (s->fx || s->emul);
+    a.colacc = (from_acc && s->esz == 8 && !part64) ? s->colacc : nullptr;
+    a.colpart64 = part64 ? reinterpret_cast<const long long*>(s->colpart) : nullptr;
     a.colpart = s->colpart;
     a.B = B;
     a.kinpart = kin ? s->kinpart : nullptr;
@@ -388,7 +393,7 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     return a;
 }
 
-int launch_pparams_only(vlasov_sim* s, double* Fout, bool hmf_fused = false)
+int launch_pparams_only(vlasov_sim* s, double* Fout)
 {
     PParamsArgs a;
     a.Nx = s->Nx;
@@ -406,16 +411,6 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool hmf_fused = false)
     a.Wh = (s->emul || s->fx) ? s->pe.Wh : nullptr;
     a.wl = (s->emul || s->fx) ? s->pe.wl : nullptr;
     a.wf = (s->emul || s->fx) ? s->pe.wf : nullptr;
-    if (hmf_fused) {
-        a.colacc = s->colacc;
-        a.cosfx = s->cosfx;
-        a.sinfx = s->sinfx;
-        a.k_col = s->k_col;
-        a.dxdp = s->dx * s->dp;
-        a.ticket = &s->tickets[2];
-        CU_TRY(launch_pparams_hmf_fused(a, s->st));
-        return VLASOV_OK;
-    }
     CU_TRY(launch_pparams(s->esz, a, s->st));
     return VLASOV_OK;
 }
@@ -454,17 +449,13 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false, s->xrec), s->xp, s->xe, false));
     MARK();
     // step 2: rho, moments, F^(I), p-shift filters
-    if (s->model == VLASOV_HMF && s->esz == 8) {
-        // one launch: Mx, My from the exact column sums, then F and the filters
-        int rc = launch_pparams_only(s, nullptr, true);
-        if (rc) return rc;
-    } else {
-        CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
+    CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
+    MARK();
+    if (s->model == VLASOV_RING) {
+        CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
         MARK();
-        if (s->model == VLASOV_RING) {
-            CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
-            MARK();
-        }
+    }
+    {
         int rc = launch_pparams_only(s, nullptr);
         if (rc) return rc;
     }
@@ -692,8 +683,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(cudaMalloc(&s->blockpart, 16 * 3 * (size_t)s->crgrid));
     CTRY(cudaMalloc(&s->ringpart, 16 * (size_t)ring_blocks(Nx)));
     CTRY(cudaMalloc(&s->maxbits, sizeof(unsigned long long)));
-    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 3));
-    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 3, s->st));
+    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 2));
+    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 2, s->st));
     CTRY(cudaMalloc(&s->sc, sizeof(Scalars)));
     CTRY(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->st));
     CTRY(cudaMalloc(&s->hist, sizeof(MomentRec) * HIST_CAP));
@@ -965,8 +956,7 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 int vlasov_kernels_per_step(const vlasov_sim* s)
 {
     if (!s) return 0;
-    if (s->model == VLASOV_RING) return 8;
-    return (s->model == VLASOV_HMF && s->esz == 8) ? 5 : 6;
+    return s->model == VLASOV_RING ? 8 : 6;
 }
 
 }  // extern "C"

@@ -109,6 +109,7 @@ struct XShiftArgs {
     const void* gd;       // [2][Np] in T
     double* colpart;      // [gridDim.x][Nx] column sums of the output, or null
     unsigned long long* colacc = nullptr;   // or: [Nx] exact int64 column sums (round(x 2^k_col)), atomically added
+    long long* colpart64 = nullptr;          // or: [ctas][Nx] exact int64 per-CTA column sums (units 2^-k_col)
     int k_col = 0;
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
     double pmin, dp;
@@ -148,6 +149,7 @@ struct PShiftArgs {
 struct ColReduceArgs {
     unsigned long long* colacc;   // [Nx] int64 column sums added by the x-shift (read and cleared), or null
     const double* colpart;   // else [B][Nx] per-CTA column sums of f
+    const long long* colpart64 = nullptr;   // or [B][Nx] exact per-CTA column sums (units 2^-k_col)
     int B;
     const double* kinpart;   // [B] per-CTA sum_j p_j^2/2 sum_i f, or null
     int Nx;
@@ -173,14 +175,6 @@ struct ColReduceArgs {
 };
 
 struct PParamsArgs {
-    // HMF with exact column sums: the kernel itself forms Mx, My from these (every block the same
-    // exact integer totals), and the last block to finish clears colacc for the next sweep.
-    const unsigned long long* colacc = nullptr;
-    const long long* cosfx = nullptr;
-    const long long* sinfx = nullptr;
-    int k_col = 0;
-    double dxdp = 0;
-    unsigned int* ticket = nullptr;
     int Nx, model;
     const Scalars* sc;
     const double* costab;
@@ -275,9 +269,6 @@ cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColRedu
 cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st);
 cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
-// HMF, 8-byte storage: density totals from the exact column sums + force + p-shift parameters in
-// one launch (replaces the reduction launch after the first x-shift).
-cudaError_t launch_pparams_hmf_fused(const PParamsArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);
 cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double* colpart, int B,

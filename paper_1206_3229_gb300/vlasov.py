@@ -337,8 +337,6 @@ class Sim:
         return out[:cnt.value].copy()
 
     def slot_names(self) -> list[str]:
-        if self.model == HMF and self.precision != F32:
-            return ["xshift_step1", "density_force_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
         names = ["xshift_step1", "reduce_density"]
         if self.model == RING:
             names.append("ring_force")
