@@ -66,11 +66,21 @@ __device__ __forceinline__ EmulElem emul_split(double x, int s_base, bool& out_o
     return o;
 }
 
-// acc + a * b with one IMAD.WIDE (32 x 32 -> 64 multiply-add).
+// acc + a * b (32 x 32 -> 64 multiply-add).  On this GPU the 64-bit accumulate costs two integer
+// additions besides the IMAD.WIDE; where two products go into the same sum, mul_wide + one
+// three-input add is cheaper.
 __device__ __forceinline__ long long mad_wide(int a, int b, long long acc)
 {
     long long d;
     asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(acc));
+    return d;
+}
+
+// a * b as int64 (one IMAD.WIDE).
+__device__ __forceinline__ long long mul_wide(int a, int b)
+{
+    long long d;
+    asm("mul.wide.s32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
     return d;
 }
 

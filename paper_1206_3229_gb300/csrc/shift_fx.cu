@@ -416,27 +416,38 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
                 M[rw] = EMUL_M0;
                 Sacc[rw] = make_float2(0.f, 0.f);
             }
-            auto feed = [&](int u, long long X) {
-                int kx;
-                float kf, rf;
-                fx_split(X, kx, kf, rf);
-                const float2 x2 = make_float2(kf, rf);
+            // Elements u and u+1 together: their two products for an output enter its int64 sum in
+            // one three-input add (two IMAD.WIDE + IADD3 + IADD3.X) instead of two 64-bit
+            // multiply-adds (three instructions each on this GPU).
+            auto feed2 = [&](int u, long long X0, long long X1, bool second) {
+                int kx0, kx1;
+                float kf0, rf0, kf1, rf1;
+                fx_split(X0, kx0, kf0, rf0);
+                fx_split(X1, kx1, kf1, rf1);
+                const float2 xa = make_float2(kf0, rf0), xb = make_float2(kf1, rf1);
 #pragma unroll
-                for (int tap = 0; tap < NTAP; ++tap) {
-                    const int rw = u - tap;
-                    if (rw >= 0 && rw < PS_RPT) {
-                        M[rw] = mad_wide(w.Wh[tap], kx, M[rw]);
-                        Sacc[rw] = __ffma2_rn(w.wlr[tap], x2, Sacc[rw]);
-                    }
+                for (int rw = 0; rw < PS_RPT; ++rw) {
+                    const int t0 = u - rw, t1 = t0 + 1;
+                    const bool v0 = t0 >= 0 && t0 < NTAP, v1 = second && t1 >= 0 && t1 < NTAP;
+                    if (v0 && v1) M[rw] = M[rw] + mul_wide(w.Wh[t0], kx0) + mul_wide(w.Wh[t1], kx1);
+                    else if (v0) M[rw] += mul_wide(w.Wh[t0], kx0);
+                    else if (v1) M[rw] += mul_wide(w.Wh[t1], kx1);
+                    if (v0) Sacc[rw] = __ffma2_rn(w.wlr[t0], xa, Sacc[rw]);
+                    if (v1) Sacc[rw] = __ffma2_rn(w.wlr[t1], xb, Sacc[rw]);
                 }
             };
+            constexpr int NU = PS_RPT + 9;
             if (t.smem_ok) {
 #pragma unroll
-                for (int u = 0; u < PS_RPT + 9; ++u) feed(u, buf[(base + u) * PS_TW + lane]);
+                for (int u = 0; u < NU; u += 2)
+                    feed2(u, buf[(base + u) * PS_TW + lane], u + 1 < NU ? buf[(base + u + 1) * PS_TW + lane] : 0ll, u + 1 < NU);
             } else {
 #pragma unroll
-                for (int u = 0; u < PS_RPT + 9; ++u)
-                    feed(u, colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll);
+                for (int u = 0; u < NU; u += 2) {
+                    const long long X0 = colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll;
+                    const long long X1 = (colvalid && u + 1 < NU) ? gload_p<long long, PPER>(fin, jb + n0_i - 3 + u, i, Nx, Np) : 0ll;
+                    feed2(u, X0, X1, u + 1 < NU);
+                }
             }
             bool any_edge = false;
 #pragma unroll
