@@ -133,7 +133,9 @@ int vlasov_kernels_per_step(const vlasov_sim* sim);
    vlasov_kernels_per_step; max_launches must be at least that), *nlaunch the slot count.  Slots in
    order: x-shift (step 1, density partials), density/moment reduction, [ring force], p-shift
    filters (force), p-shift (step 3), x-shift (step 4, density+kinetic partials), moment
-   reduction, [ring potential].  Syncs. */
+   reduction, [ring potential].  HMF with VLASOV_FX64 (Nx * Np <= 2^24) has five: the x-shifts hand
+   the reductions three exact per-CTA numbers, so the filters launch forms Mx, My itself and there
+   is no density reduction launch.  Syncs. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
 /* ---------------------------------------------------------------------------------------------

@@ -619,6 +619,77 @@ cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PPa
     return cudaGetLastError();
 }
 
+// Exact totals of the x-shift's per-CTA HMF partials, in every thread of the block.
+__device__ __forceinline__ void sum_ctaparts(const void* parts, int ctas, i128& m, i128& x, i128& y, i128* red4)
+{
+    const i128* p = static_cast<const i128*>(parts);
+    m = 0;
+    x = 0;
+    y = 0;
+    i128 z = 0;
+    for (int b = threadIdx.x; b < ctas; b += blockDim.x) {
+        m += p[(size_t)b * 3 + 0];
+        x += p[(size_t)b * 3 + 1];
+        y += p[(size_t)b * 3 + 2];
+    }
+    block_sum4_i128(m, x, y, z, red4);
+}
+
+// HMF after the first x-shift: Mx, My from the per-CTA partials (the same exact integers in every
+// block), then F_i = -Mx sin x_i + My cos x_i and the p-shift parameters of the block's columns.
+constexpr int PPC_THREADS = 256;
+__global__ void __launch_bounds__(PPC_THREADS) pparams_hmf_cta_kernel(PParamsArgs a)
+{
+    __shared__ i128 red4[128];
+    i128 m, x, y;
+    sum_ctaparts(a.ctapart, a.ctas, m, x, y, red4);
+    const int i = blockIdx.x * PPC_THREADS + threadIdx.x;
+    if (i >= a.Nx) return;
+    const double Mx = a.dxdp * fx128_to_f64(x, 101 - a.Ef);
+    const double My = a.dxdp * fx128_to_f64(y, 101 - a.Ef);
+    const double F = -Mx * a.sintab[i] + My * a.costab[i];
+    if (a.Fout) a.Fout[i] = F;
+    pparams_fixed(a, i, F * a.cp);
+}
+
+cudaError_t launch_pparams_hmf_cta(const PParamsArgs& a, cudaStream_t st)
+{
+    pparams_hmf_cta_kernel<<<(a.Nx + PPC_THREADS - 1) / PPC_THREADS, PPC_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// x * 2^s rounded (s < 0: round half up), exact in int128.
+__device__ __forceinline__ i128 shift_round(i128 x, int s)
+{
+    if (s >= 0) return x << s;
+    return (x + ((i128)1 << (-s - 1))) >> (-s);
+}
+
+// HMF moments after the second x-shift: totals of the per-CTA partials on the scales of
+// colreduce_final (2^-k_col and 2^-(k_col+30)), then the kinetic partials, U and the record.
+__global__ void __launch_bounds__(256) colreduce_cta_kernel(ColReduceArgs a)
+{
+    __shared__ i128 red4[128];
+    __shared__ i128 red[33];
+    i128 m, x, y;
+    sum_ctaparts(a.ctapart, a.B, m, x, y, red4);
+    m = shift_round(m, a.k_col + a.Ef - 51);
+    x = shift_round(x, a.k_col + a.Ef - 71);
+    y = shift_round(y, a.k_col + a.Ef - 71);
+    if (threadIdx.x != 0) {   // colreduce_final adds the block's values: hand them to one thread
+        m = 0;
+        x = 0;
+        y = 0;
+    }
+    colreduce_final(a, m, x, y, red);
+}
+
+cudaError_t launch_colreduce_cta(const ColReduceArgs& a, cudaStream_t st)
+{
+    colreduce_cta_kernel<<<1, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st)
 {
     const int grid = (a.Nx + 63) / 64;

@@ -108,7 +108,6 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
     unsigned char* smem_raw = align128(smem_dyn);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
-    __shared__ i128 redk[32];
     __shared__ unsigned int done_cnt[8];   // warps finished with each stage's current row
     __shared__ unsigned int issued[8];     // copies issued into each stage
     unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)a.stages * (a.Nx + 2 * a.pad));
@@ -249,8 +248,9 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
             }
         }
     }
-    failed = __syncthreads_or(failed);
+    failed = __syncthreads_or(failed);   // also: every warp is done with the stage buffers
     if (bad || rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    i128* scratch = reinterpret_cast<i128*>(bufs);   // block-sum scratch (128 entries) in the free stages
 
     if (failed) {
         if (tid == 0) {
@@ -276,6 +276,30 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                     atomicAdd(a.colacc + i + v, (unsigned long long)q);
                 }
             }
+        }
+    } else if (a.ctapart) {
+        // HMF: only sum_i rho_i and the cos/sin-weighted sums are needed; form them for this CTA's
+        // column sums here (exact int128) and write three numbers instead of a partial row
+        i128 pm = 0, px = 0, py = 0, pz = 0;
+#pragma unroll
+        for (int c = 0; c < XF_MAXCH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long t = colacc[c][v];
+                    pm += (i128)t;
+                    px += (i128)__ldg(a.cos50 + i + v) * (i128)t;
+                    py += (i128)__ldg(a.sin50 + i + v) * (i128)t;
+                }
+            }
+        }
+        block_sum4_i128(pm, px, py, pz, scratch);
+        if (tid == 0) {
+            i128* cp = static_cast<i128*>(a.ctapart) + (size_t)blockIdx.x * 3;
+            cp[0] = pm;
+            cp[1] = px;
+            cp[2] = py;
         }
     } else if (a.colpart64) {
         // exact per-CTA column sums, one partial row per CTA (plain 32-byte stores, no atomics)
@@ -307,7 +331,7 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
         }
     }
     if constexpr (KIN) {
-        const i128 t = block_sum_i128(kin, redk);
+        const i128 t = block_sum_i128(kin, scratch);
         if (tid == 0) a.kinpart[blockIdx.x] = fx128_to_f64(t, 51 + KIN_Q - em.Ef);
     }
 }

@@ -97,6 +97,10 @@ struct vlasov_sim {
     double* sintab = nullptr;
     long long* cosfx = nullptr;
     long long* sinfx = nullptr;
+    long long* cos50 = nullptr;   // round(cos x_i 2^50), round(sin x_i 2^50)
+    long long* sin50 = nullptr;
+    void* ctapart = nullptr;      // [xgrid][3] int128 per-CTA HMF partials
+    bool hmf_cta = false;         // HMF, FX64: reductions from per-CTA partials (no per-column pass)
     void* ringdV = nullptr;     // in the storage type
     void* ringV = nullptr;
     // fixed-point scales of the reductions (from a bound 2^Ef >= 4 max|f|)
@@ -250,7 +254,10 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     const bool atomics = s->esz == 8 && !part64;
     a.colpart = (reduce && s->esz == 4) ? s->colpart : nullptr;
     a.colacc = (reduce && atomics) ? s->colacc : nullptr;
-    a.colpart64 = (reduce && part64) ? reinterpret_cast<long long*>(s->colpart) : nullptr;
+    a.colpart64 = (reduce && part64 && !s->hmf_cta) ? reinterpret_cast<long long*>(s->colpart) : nullptr;
+    a.ctapart = (reduce && s->hmf_cta) ? s->ctapart : nullptr;
+    a.cos50 = s->cos50;
+    a.sin50 = s->sin50;
     a.k_col = s->k_col;
     a.kinpart = kin ? s->kinpart : nullptr;
     a.pmin = s->pmin;
@@ -393,7 +400,7 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     return a;
 }
 
-int launch_pparams_only(vlasov_sim* s, double* Fout)
+int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false)
 {
     PParamsArgs a;
     a.Nx = s->Nx;
@@ -411,6 +418,14 @@ int launch_pparams_only(vlasov_sim* s, double* Fout)
     a.Wh = (s->emul || s->fx) ? s->pe.Wh : nullptr;
     a.wl = (s->emul || s->fx) ? s->pe.wl : nullptr;
     a.wf = (s->emul || s->fx) ? s->pe.wf : nullptr;
+    if (from_cta) {
+        a.ctapart = s->ctapart;
+        a.ctas = s->xgrid;
+        a.Ef = s->Ef;
+        a.dxdp = s->dx * s->dp;
+        CU_TRY(launch_pparams_hmf_cta(a, s->st));
+        return VLASOV_OK;
+    }
     CU_TRY(launch_pparams(s->esz, a, s->st));
     return VLASOV_OK;
 }
@@ -449,13 +464,16 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false, s->xrec), s->xp, s->xe, false));
     MARK();
     // step 2: rho, moments, F^(I), p-shift filters
-    CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
-    MARK();
-    if (s->model == VLASOV_RING) {
-        CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
+    if (s->hmf_cta) {
+        int rc = launch_pparams_only(s, nullptr, true);   // Mx, My from the per-CTA partials
+        if (rc) return rc;
+    } else {
+        CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
         MARK();
-    }
-    {
+        if (s->model == VLASOV_RING) {
+            CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
+            MARK();
+        }
         int rc = launch_pparams_only(s, nullptr);
         if (rc) return rc;
     }
@@ -466,7 +484,14 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     // step 4: f(t+dt) = f^(II)(x - p dt/2, p), with density + kinetic partials for the moments
     CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, true, s->xrec), s->xp, s->xe, true));
     MARK();
-    CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
+    if (s->hmf_cta) {
+        ColReduceArgs c = crargs(s, s->xgrid, true, true);
+        c.ctapart = s->ctapart;
+        c.Ef = s->Ef;
+        CU_TRY(launch_colreduce_cta(c, s->st));
+    } else {
+        CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
+    }
     MARK();
     if (s->model == VLASOV_RING) {
         CU_TRY(launch_ring(s->esz, ringargs(s, true), s->st));
@@ -535,7 +560,7 @@ void vlasov_destroy(vlasov_sim* s)
     free_emul(s->se);
     void* bufs[] = {s->colpart, s->colacc, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
-                    s->hist, s->dstep, s->err, s->xrec, s->srec};
+                    s->hist, s->dstep, s->err, s->xrec, s->srec, s->cos50, s->sin50, s->ctapart};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -670,6 +695,10 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     s->crgrid = (Nx + 31) / 32;
 
     CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->xgrid * Nx));
+    CTRY(cudaMalloc(&s->ctapart, 48 * (size_t)s->xgrid));
+    // HMF with FX64 storage needs no per-column density: the x-shifts hand over three exact
+    // numbers per CTA (bounded in int128 while Nx * Np <= 2^24)
+    s->hmf_cta = s->fx && model == VLASOV_HMF && (double)Nx * (double)Np <= 16777216.0;
     CTRY(cudaMalloc(&s->colacc, sizeof(unsigned long long) * (size_t)Nx));
     CTRY(cudaMemsetAsync(s->colacc, 0, sizeof(unsigned long long) * (size_t)Nx, s->st));
     CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->xgrid));
@@ -696,13 +725,15 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     // Tables on the x nodes: cos/sin for HMF (Eq. hmfmeanforce, mxmydef); ring kernel V, V'.
     {
         std::vector<double> c(Nx), sn(Nx), dV(Nx), V(Nx);
-        std::vector<long long> cfx(Nx), sfx(Nx);
+        std::vector<long long> cfx(Nx), sfx(Nx), c50(Nx), s50(Nx);
         for (int i = 0; i < Nx; ++i) {
             const double th = s->xmin + (double)i * s->dx;
             c[i] = std::cos(th);
             sn[i] = std::sin(th);
             cfx[i] = std::llround(std::ldexp(c[i], 62));
             sfx[i] = std::llround(std::ldexp(sn[i], 62));
+            c50[i] = std::llround(std::ldexp(c[i], 50));
+            s50[i] = std::llround(std::ldexp(sn[i], 50));
             const double u = (double)i * s->dx;
             if (model == VLASOV_RING) {
                 const double q = 1.0 - std::cos(u) + s->eps;
@@ -716,12 +747,16 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         CTRY(cudaMalloc(&s->sintab, sizeof(double) * Nx));
         CTRY(cudaMalloc(&s->cosfx, sizeof(long long) * Nx));
         CTRY(cudaMalloc(&s->sinfx, sizeof(long long) * Nx));
+        CTRY(cudaMalloc(&s->cos50, sizeof(long long) * Nx));
+        CTRY(cudaMalloc(&s->sin50, sizeof(long long) * Nx));
         CTRY(cudaMalloc(&s->ringdV, (size_t)esz * Nx));
         CTRY(cudaMalloc(&s->ringV, (size_t)esz * Nx));
         CTRY(cudaMemcpyAsync(s->costab, c.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->sintab, sn.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->cosfx, cfx.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->sinfx, sfx.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaMemcpyAsync(s->cos50, c50.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
+        CTRY(cudaMemcpyAsync(s->sin50, s50.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
         if (esz == 8) {
             CTRY(cudaMemcpyAsync(s->ringdV, dV.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
             CTRY(cudaMemcpyAsync(s->ringV, V.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
@@ -956,7 +991,8 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 int vlasov_kernels_per_step(const vlasov_sim* s)
 {
     if (!s) return 0;
-    return s->model == VLASOV_RING ? 8 : 6;
+    if (s->model == VLASOV_RING) return 8;
+    return s->hmf_cta ? 5 : 6;
 }
 
 }  // extern "C"

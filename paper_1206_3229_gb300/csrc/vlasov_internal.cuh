@@ -110,6 +110,10 @@ struct XShiftArgs {
     double* colpart;      // [gridDim.x][Nx] column sums of the output, or null
     unsigned long long* colacc = nullptr;   // or: [Nx] exact int64 column sums (round(x 2^k_col)), atomically added
     long long* colpart64 = nullptr;          // or: [ctas][Nx] exact int64 per-CTA column sums (units 2^-k_col)
+    void* ctapart = nullptr;                 // or (HMF): [ctas][3] int128 per-CTA sum_i t_i, sum_i cos50_i t_i,
+                                             // sum_i sin50_i t_i of the CTA's column sums t_i (units 2^(Ef-51))
+    const long long* cos50 = nullptr;        //   round(cos x_i 2^50), round(sin x_i 2^50)
+    const long long* sin50 = nullptr;
     int k_col = 0;
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
     double pmin, dp;
@@ -150,6 +154,8 @@ struct ColReduceArgs {
     unsigned long long* colacc;   // [Nx] int64 column sums added by the x-shift (read and cleared), or null
     const double* colpart;   // else [B][Nx] per-CTA column sums of f
     const long long* colpart64 = nullptr;   // or [B][Nx] exact per-CTA column sums (units 2^-k_col)
+    const void* ctapart = nullptr;          // or (HMF) [B][3] int128 per-CTA partials of the x-shift
+    int Ef = 0;                             //   (their units: 2^(Ef-51), 2^(Ef-101))
     int B;
     const double* kinpart;   // [B] per-CTA sum_j p_j^2/2 sum_i f, or null
     int Nx;
@@ -175,6 +181,11 @@ struct ColReduceArgs {
 };
 
 struct PParamsArgs {
+    // HMF from the x-shift's per-CTA partials: every block adds the same [ctas][3] int128 partials
+    // (exactly) to get Mx, My.
+    const void* ctapart = nullptr;
+    int ctas = 0, Ef = 0;
+    double dxdp = 0;
     int Nx, model;
     const Scalars* sc;
     const double* costab;
@@ -269,6 +280,10 @@ cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColRedu
 cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st);
 cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
+// HMF, 8-byte storage, from the x-shift's per-CTA partials: force and p-shift parameters
+// (pparams_hmf_cta), and the moments after the second x-shift (colreduce_cta, one block).
+cudaError_t launch_pparams_hmf_cta(const PParamsArgs& a, cudaStream_t st);
+cudaError_t launch_colreduce_cta(const ColReduceArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);
 cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double* colpart, int B,

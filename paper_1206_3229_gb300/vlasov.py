@@ -337,6 +337,8 @@ class Sim:
         return out[:cnt.value].copy()
 
     def slot_names(self) -> list[str]:
+        if self.model == HMF and self.precision == FX64 and self.nx * self.np <= 1 << 24:
+            return ["xshift_step1", "force_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
         names = ["xshift_step1", "reduce_density"]
         if self.model == RING:
             names.append("ring_force")

@@ -155,8 +155,11 @@ FX_CASES = [I.HMF_256, I.RING_2048.resized(128, 128), I.SHEET_4096.resized(256, 
 
 @pytest.mark.parametrize("w", FX_CASES, ids=lambda w: w.name)
 def test_fx64_batch_is_bitwise_the_single_grid_fx64_path(w):
-    """Same kernels, same fixed-point bound from the same f0: identical f; the moment sums are exact
-    integers except the kinetic term's per-CTA FP64 partials (grouped differently)."""
+    """Same sweep kernels, same fixed-point bound from the same f0: identical f for ring and sheet;
+    the moment sums are exact integers except the kinetic term's per-CTA FP64 partials (grouped
+    differently).  HMF: the single-grid path forms Mx, My from per-CTA partials with 50-bit cos/sin
+    weights, the batch from per-column totals with 62-bit weights, so the force differs in its last
+    bits and f agrees to rounding."""
     steps = 25
     f0 = I.initial_state(w)
     with V.Batch(2, 512, GB, precision="fx64") as b:
@@ -168,6 +171,11 @@ def test_fx64_batch_is_bitwise_the_single_grid_fx64_path(w):
         s.step(steps)
         ms = s.moments()
         fs = s.get_f()
+    if w.model == "hmf":
+        assert np.max(np.abs(fb - fs)) <= 1e-13 * fs.max()
+        for col in (1, 2, 3, 4, 5):
+            assert np.max(np.abs(mb[:, col] - ms[:, col])) <= 1e-13, col
+        return
     assert np.array_equal(fb, fs)
     for col in (1, 2, 3, 5):   # mass, Mx, My, potential
         assert np.array_equal(mb[:, col], ms[:, col]), col
