@@ -99,8 +99,18 @@ int vlasov_get_f(vlasov_sim* sim, double* host_f);
 int vlasov_get_f_device(vlasov_sim* sim, double* dev_f);
 
 /* Enqueue n Strang steps (Sec. 3 steps 1-4).  Asynchronous: launches CUDA graphs on the handle's
-   stream.  The moments of f after each step are appended to a device ring of 4096 records. */
+   stream.  The moments of f after each step are appended to a device ring of 4096 records.
+   With fused x-shifts (vlasov_fused_x) a call of n >= 2 steps runs the second x half-shift of step
+   k and the first of step k+1 as one launch that keeps the row between them on chip: the same
+   arithmetic and the same bits as separate launches, with one HBM round trip of f fewer per step.
+   The state between calls is always a whole step. */
 int vlasov_step(vlasov_sim* sim, int n);
+
+/* Turn the fused x-shifts on (1) or off (0).  On by default where available: VLASOV_FX64 storage
+   with Nx <= 4096; asking for them elsewhere returns VLASOV_EINVAL.  vlasov_fused_x reports the
+   current setting (0 or 1). */
+int vlasov_set_fused_x(vlasov_sim* sim, int on);
+int vlasov_fused_x(const vlasov_sim* sim);
 
 /* Copy out up to max moment records produced since the previous call (oldest first) into out,
    set *count.  Records older than the ring's 4096 are dropped (count tells what is returned).
@@ -125,17 +135,22 @@ void vlasov_destroy(vlasov_sim* sim);
 /* Message of the last failing call on this thread ("" if none). */
 const char* vlasov_last_error(void);
 
-/* Number of kernel launches one vlasov_step(1) enqueues for this handle (for launch accounting). */
+/* Kernel launches per step in a long run (the slots of vlasov_step_timed), and the exact number
+   that vlasov_step(n) enqueues (for launch accounting). */
 int vlasov_kernels_per_step(const vlasov_sim* sim);
+long long vlasov_launches(const vlasov_sim* sim, int n);
 
 /* Run n steps with eager launches (no graph) and a CUDA event around every kernel, on the handle's
    stream; ms_per_launch[q] receives the mean duration of launch slot q of a step (q <
-   vlasov_kernels_per_step; max_launches must be at least that), *nlaunch the slot count.  Slots in
-   order: x-shift (step 1, density partials), density/moment reduction, [ring force], p-shift
-   filters (force), p-shift (step 3), x-shift (step 4, density+kinetic partials), moment
-   reduction, [ring potential].  HMF with VLASOV_FX64 (Nx * Np <= 2^24) has five: the x-shifts hand
-   the reductions three exact per-CTA numbers, so the filters launch forms Mx, My itself and there
-   is no density reduction launch.  Syncs. */
+   vlasov_kernels_per_step; max_launches must be at least that), *nlaunch the slot count.  Syncs.
+   Without fused x-shifts (or n = 1) the slots of each of the n steps, in order: x-shift (step 1,
+   density partials), density reduction, [ring force], p-shift filters (force), p-shift (step 3),
+   x-shift (step 4, density+kinetic partials), moment reduction, [ring potential].  HMF with
+   VLASOV_FX64 (Nx * Np <= 2^24) has no density reduction launch: the x-shifts hand the reductions
+   three exact per-CTA numbers and the filters launch forms Mx, My itself.
+   With fused x-shifts and n >= 2 the slots are those between two steps, averaged over the n-1 such
+   places: fused x-shifts (step 4 and the next step 1), moment reduction, [ring potential],
+   [density reduction, ring force], p-shift filters, p-shift. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
 /* ---------------------------------------------------------------------------------------------

@@ -75,6 +75,9 @@ __device__ __forceinline__ void colreduce_final(const ColReduceArgs& a, i128 m, 
 #pragma unroll
         for (int u = 0; u < 4; ++u) k += fx128_from_f64(kv[u], a.k_kin);
         for (int b = threadIdx.x + 4 * blockDim.x; b < a.B; b += blockDim.x) k += fx128_from_f64(__ldcg(&a.kinpart[b]), a.k_kin);
+    } else if (a.kin128) {
+        const i128* kp = static_cast<const i128*>(a.kin128);
+        for (int b = threadIdx.x; b < a.B; b += blockDim.x) k += kp[b];
     }
     {
         __shared__ i128 red4[128];
@@ -115,7 +118,7 @@ __device__ __forceinline__ void colreduce_final(const ColReduceArgs& a, i128 m, 
         const double mass = a.dxdp * fx128_to_f64(m, a.k_col);
         const double Mx = a.dxdp * fx128_to_f64(x, a.k_col + 30);
         const double My = a.dxdp * fx128_to_f64(y, a.k_col + 30);
-        const double kin = a.dxdp * fx128_to_f64(k, a.k_kin);
+        const double kin = a.dxdp * fx128_to_f64(k, a.kinpart ? a.k_kin : a.kin_frac);
         double U = 0.0;
         if (a.model == 0) U = 0.5 * (mass * mass - Mx * Mx - My * My);
         else if (a.model == 2 && a.final_moments) U = a.pot_scale * fx128_to_f64(U_acc, a.k_pot);

@@ -4,8 +4,8 @@
 // uploaded |f|): the same 8 bytes per cell as FP64, an absolute resolution of 2^-59 of max|f|, and no
 // IEEE decoding.  Each staged element splits with two integer instructions into
 //   X = kx * 2^30 + rem,  kx = X >> 30 (int32), rem in [0, 2^30)
-// and the filter runs as in the emulated-FP64 sweeps (emul.cuh): 10 IMAD.WIDE on kx and 10 paired
-// FMAs (FFMA2) on ((float)kx, (float)rem); the int64 result T is already in storage units.  Data
+// and the filter runs as in the emulated-FP64 sweeps (emul.cuh): 10 IMAD.WIDE on kx and 20 FP32
+// FMAs on (float)kx and (float)rem; the int64 result T is already in storage units.  Data
 // movement is that of shift_kernels.cu: whole rows by 1-D bulk copies (x-shift), 2-D TMA column
 // tiles with zero fill (p-shift).
 #include "emul.cuh"
@@ -60,11 +60,14 @@ __device__ __forceinline__ long long fx_edge(const long long* X, const double* w
     return (long long)fx128_from_f64(out, FX_FRAC - Ef);
 }
 
-// XF_V consecutive outputs of one x row from the staged fixed-point values starting at `src`
-// (f_{k-4-A} .. ): input-stationary, each element split once and fed to the outputs it touches.
-// The two FP32 residual products of a tap go through one paired FMA (FFMA2).
-template <int A>
-__device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, long long (&out)[XF_V], uint32_t& rng)
+// XF_V consecutive outputs of one x row from the staged fixed-point values f_{k-4-A} .. , read as
+// pairs: pair h at q[h] in a plain row, or (PADDED) at q[h + (Q + h) / 4] in a padded row whose
+// window starts at pair 4 m + Q (pair p at 16-byte slot p + p / 4, q = slot of the first pair).
+// Input-stationary: each element is split once and fed to the outputs it touches.  The two FP32
+// residual products of a tap are two scalar FMAs.
+template <int A, bool PADDED = false>
+__device__ __forceinline__ void fx_chunk(const longlong2* q, const FxW& w, long long (&out)[XF_V], uint32_t& rng,
+                                         int Q = 0)
 {
     long long M[XF_V];
     float2 S[XF_V];
@@ -73,10 +76,9 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
         M[v] = EMUL_M0;
         S[v] = make_float2(0.f, 0.f);
     }
-    const longlong2* q = reinterpret_cast<const longlong2*>(src);
 #pragma unroll
     for (int h = 0; h < XF_W / 2; ++h) {
-        const longlong2 pr = q[h];
+        const longlong2 pr = q[PADDED ? h + ((Q + h) >> 2) : h];
         int kx0, kx1;
         float kf0, rf0, kf1, rf1;
         fx_split(pr.x, kx0, kf0, rf0);
@@ -90,12 +92,132 @@ __device__ __forceinline__ void fx_chunk(const long long* src, const FxW& w, lon
             if (v0 && v1) M[v] = M[v] + (long long)w.Wh[t0] * (long long)kx0 + (long long)w.Wh[t1] * (long long)kx1;
             else if (v0) M[v] += (long long)w.Wh[t0] * (long long)kx0;
             else if (v1) M[v] += (long long)w.Wh[t1] * (long long)kx1;
-            if (v0) S[v] = __ffma2_rn(w.wlr[t0], xa, S[v]);
-            if (v1) S[v] = __ffma2_rn(w.wlr[t1], xb, S[v]);
+            // two scalar FMAs rather than one paired FFMA2: measured 11 % faster in the fused
+            // x-shift, whose heavy FMA pipe (shared with the IMAD.WIDE products) was the busiest unit
+            if (v0) {
+                S[v].x = fmaf(w.wlr[t0].x, xa.x, S[v].x);
+                S[v].y = fmaf(w.wlr[t0].y, xa.y, S[v].y);
+            }
+            if (v1) {
+                S[v].x = fmaf(w.wlr[t1].x, xb.x, S[v].x);
+                S[v].y = fmaf(w.wlr[t1].y, xb.y, S[v].y);
+            }
         }
     }
 #pragma unroll
     for (int v = 0; v < XF_V; ++v) out[v] = fx_store(emul_finish(M[v], S[v].x + S[v].y), rng);
+}
+
+// End of an x-shift sweep: hand over this CTA's exact column sums acc[c][v] (column
+// XF_V (tid + c blockDim) + v, units 2^(Ef-51)) in the form the arguments ask for.  Every thread
+// of the block calls it (block reductions inside).
+template <int CH>
+__device__ __forceinline__ void fx_colsum_epilogue(const XShiftArgs& a, const long long (&acc)[CH][XF_V], int Ef,
+                                                   i128* scratch)
+{
+    const int Nx = a.Nx, tid = threadIdx.x, nthreads = blockDim.x;
+    if (a.colacc) {
+        // exact fixed-point column sums, added across CTAs: units 2^(Ef-51) -> 2^-k_col
+        const int sh = a.k_col + Ef - 51;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long x = acc[c][v];
+                    const long long q = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
+                }
+            }
+        }
+    } else if (a.ctapart) {
+        // HMF: only sum_i rho_i and the cos/sin-weighted sums are needed; form them for this CTA's
+        // column sums here (exact int128) and write three numbers instead of a partial row
+        i128 pm = 0, px = 0, py = 0, pz = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long t = acc[c][v];
+                    pm += (i128)t;
+                    px += (i128)__ldg(a.cos50 + i + v) * (i128)t;
+                    py += (i128)__ldg(a.sin50 + i + v) * (i128)t;
+                }
+            }
+        }
+        block_sum4_i128(pm, px, py, pz, scratch);
+        if (tid == 0) {
+            i128* cp = static_cast<i128*>(a.ctapart) + (size_t)blockIdx.x * 3;
+            cp[0] = pm;
+            cp[1] = px;
+            cp[2] = py;
+        }
+    } else if (a.colpart64) {
+        // exact per-CTA column sums, one partial row per CTA (plain 32-byte stores, no atomics)
+        const int sh = a.k_col + Ef - 51;
+        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+                long long q[XF_V];
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long x = acc[c][v];
+                    q[v] = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
+                }
+#pragma unroll
+                for (int v = 0; v < XF_V; v += 4) st_global_v4_b64(cp + i + v, q[v], q[v + 1], q[v + 2], q[v + 3]);
+            }
+        }
+    } else if (a.colpart) {
+        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = XF_V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) cp[i + v] = fx128_to_f64((i128)acc[c][v], 51 - Ef);
+            }
+        }
+    }
+}
+
+// The CTA's kinetic sum (per-thread kin, units 2^(Ef-51-KIN_Q)): exact int128 when the
+// arguments ask for it (the total is then independent of how rows were split over CTAs),
+// else rounded to FP64.
+__device__ __forceinline__ void fx_kin_epilogue(const XShiftArgs& a, i128 kin, int Ef, i128* scratch)
+{
+    const i128 t = block_sum_i128(kin, scratch);
+    if (threadIdx.x == 0) {
+        if (a.kin128) static_cast<i128*>(a.kin128)[blockIdx.x] = t;
+        else a.kinpart[blockIdx.x] = fx128_to_f64(t, 51 + KIN_Q - Ef);
+    }
+}
+
+// Padded rows (fused x-shifts): 8-element lines 80 bytes apart, so that pair p (elements 2p, 2p+1)
+// sits at 16-byte slot p + p / 4.  A warp's 16-byte window reads, 64 bytes apart per thread in a
+// plain row (four-way bank conflicts), then hit distinct banks.  A TMA box of 10 x H elements over
+// a tensor of 8-element lines writes this layout directly (the two columns past the line are out
+// of bounds and arrive as zeros).
+__host__ __device__ __forceinline__ int xxf_front(int pad, bool periodic) { return periodic ? 0 : (pad + 63) / 64 * 64; }
+__host__ __device__ __forceinline__ int xxf_row_bytes(int Nx, int pad, bool periodic)
+{
+    const int lines = (2 * xxf_front(pad, periodic) + Nx + (periodic ? 16 : 0)) / 8;
+    return (lines * 80 + 127) / 128 * 128;   // rows stay 128-byte aligned (TMA destinations)
+}
+
+// The chunk whose window starts at pair p0 of a padded row.
+template <int A>
+__device__ __forceinline__ void fx_chunk_padded(const longlong2* slots, int p0, const FxW& w, long long (&out)[XF_V],
+                                                uint32_t& rng)
+{
+    // Q at run time: one instantiation (a compile-time Q, four copies of the unrolled chunk in
+    // each pass, measured slower: instruction-cache misses)
+    fx_chunk<A, true>(slots + 5 * (p0 >> 2) + (p0 & 3), w, out, rng, p0 & 3);
 }
 
 }  // namespace
@@ -203,8 +325,9 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                         if (e >= Nx) e -= Nx;
                     }
                     long long out[XF_V];
-                    if (A == 0) fx_chunk<0>(rowbuf + e, w, out, rng);
-                    else fx_chunk<1>(rowbuf + e, w, out, rng);
+                    const longlong2* q2 = reinterpret_cast<const longlong2*>(rowbuf + e);
+                    if (A == 0) fx_chunk<0>(q2, w, out, rng);
+                    else fx_chunk<1>(q2, w, out, rng);
                     if constexpr (!PERIODIC) {
                         const int k = i + n0;
                         if (k < 0 || k + XF_V - 1 >= Nx - 1) {
@@ -262,78 +385,8 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
         return;
     }
 
-    if (a.colacc) {
-        // exact fixed-point column sums, added across CTAs: units 2^(Ef-51) -> 2^-k_col
-        const int sh = a.k_col + em.Ef - 51;
-#pragma unroll
-        for (int c = 0; c < XF_MAXCH; ++c) {
-            const int i = XF_V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < XF_V; ++v) {
-                    const long long x = colacc[c][v];
-                    const long long q = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
-                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
-                }
-            }
-        }
-    } else if (a.ctapart) {
-        // HMF: only sum_i rho_i and the cos/sin-weighted sums are needed; form them for this CTA's
-        // column sums here (exact int128) and write three numbers instead of a partial row
-        i128 pm = 0, px = 0, py = 0, pz = 0;
-#pragma unroll
-        for (int c = 0; c < XF_MAXCH; ++c) {
-            const int i = XF_V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < XF_V; ++v) {
-                    const long long t = colacc[c][v];
-                    pm += (i128)t;
-                    px += (i128)__ldg(a.cos50 + i + v) * (i128)t;
-                    py += (i128)__ldg(a.sin50 + i + v) * (i128)t;
-                }
-            }
-        }
-        block_sum4_i128(pm, px, py, pz, scratch);
-        if (tid == 0) {
-            i128* cp = static_cast<i128*>(a.ctapart) + (size_t)blockIdx.x * 3;
-            cp[0] = pm;
-            cp[1] = px;
-            cp[2] = py;
-        }
-    } else if (a.colpart64) {
-        // exact per-CTA column sums, one partial row per CTA (plain 32-byte stores, no atomics)
-        const int sh = a.k_col + em.Ef - 51;
-        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
-#pragma unroll
-        for (int c = 0; c < XF_MAXCH; ++c) {
-            const int i = XF_V * (tid + c * nthreads);
-            if (i < Nx) {
-                long long q[XF_V];
-#pragma unroll
-                for (int v = 0; v < XF_V; ++v) {
-                    const long long x = colacc[c][v];
-                    q[v] = sh >= 0 ? (long long)((unsigned long long)x << sh) : ((x + (1ll << (-sh - 1))) >> (-sh));
-                }
-#pragma unroll
-                for (int v = 0; v < XF_V; v += 4) st_global_v4_b64(cp + i + v, q[v], q[v + 1], q[v + 2], q[v + 3]);
-            }
-        }
-    } else if (a.colpart) {
-        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
-#pragma unroll
-        for (int c = 0; c < XF_MAXCH; ++c) {
-            const int i = XF_V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < XF_V; ++v) cp[i + v] = fx128_to_f64((i128)colacc[c][v], 51 - em.Ef);
-            }
-        }
-    }
-    if constexpr (KIN) {
-        const i128 t = block_sum_i128(kin, scratch);
-        if (tid == 0) a.kinpart[blockIdx.x] = fx128_to_f64(t, 51 + KIN_Q - em.Ef);
-    }
+    fx_colsum_epilogue<XF_MAXCH>(a, colacc, em.Ef, scratch);
+    if constexpr (KIN) fx_kin_epilogue(a, kin, em.Ef, scratch);
 }
 
 template <bool PERIODIC, bool KIN>
@@ -354,6 +407,231 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_batch_kernel(cons
     if (a.Np <= 0 || (int)blockIdx.x >= a.Np || (a.ctas > 0 && (int)blockIdx.x >= a.ctas)) return;
     const EmulArgs em = ems[slot];
     xshift_fx_body<PERIODIC, KIN>(a, em);
+}
+
+// ============================================================================ fused x-shifts (FX64)
+// The second x half-shift of step n and the first of step n+1 (Sec. 3, steps four and one of the
+// Strang cycle) move row j by the same p_j dt/2 with the same filter, and neither needs anything
+// from other rows.  So one launch stages each row once, filters it into a shared-memory row (the
+// state f(t_n + dt) at the end of step n: its column sums and kinetic sum are step n's moments),
+// filters that row again and writes only the result (f^(I) of step n+1, whose column sums give the
+// next force).  The arithmetic of each pass is that of xshift_fx_body, so the result is the same
+// bits as two launches; the HBM traffic is that of one.  One output chunk of XF_V columns per
+// thread (Nx <= XF_V * blockDim.x); rows stride by the CTA count; S stages of whole rows in flight
+// (TMA boxes of H lines into padded rows), two padded intermediate rows alternate so that one
+// barrier per row suffices.
+//   a: input, records, shape, and the outputs of the first pass (step n's moment sums, kinetic);
+//   b: output row buffer (b.fout) and the column sums of the second pass.
+template <bool PERIODIC>
+__device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const XShiftArgs& a, const XShiftArgs& b,
+                                                const EmulArgs& em)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    __shared__ unsigned int issued[8];     // copies issued into each stage
+
+    const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
+    long long* __restrict__ fout = static_cast<long long*>(b.fout);
+    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
+    const int PADR = xxf_front(PAD, PERIODIC);   // zero elements before the row (whole 640-byte line groups)
+    const int sbytes = xxf_row_bytes(Nx, PAD, PERIODIC);
+    const int H = a.box_h;                 // TMA box height in lines (a multiple of 8 dividing Nx / 8)
+    unsigned char* stg = smem_raw + 128;
+    long long* ibufs = reinterpret_cast<long long*>(stg + (size_t)S * sbytes);   // two padded rows
+    const int istride = sbytes / 8;
+    unsigned char* recs = reinterpret_cast<unsigned char*>(ibufs + 2 * (size_t)istride);
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int G = a.ctas > 0 ? a.ctas : (int)gridDim.x;
+    const uint32_t tx_bytes = (uint32_t)(Nx / 8 * 80) + (PERIODIC ? 128u : 0u) + XREC_BYTES;   // boxes count whole
+    const double unit = ldexp(1.0, em.Ef - FX_FRAC);
+    const int i = XF_V * tid;              // this thread's output columns i .. i + XF_V - 1
+    const bool act = i < Nx;
+    uint32_t rng = 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bars[s], 1);
+            issued[s] = 0;
+        }
+        fence_barrier_init();
+    }
+    for (int e = tid; e < 2 * istride; e += nthreads) ibufs[e] = 0;
+    if constexpr (!PERIODIC) {
+        for (int s = 0; s < S; ++s) {   // zero halo lines of the stages
+            long long* q = reinterpret_cast<long long*>(stg + (size_t)s * sbytes);
+            for (int e = tid; e < PADR / 8 * 10; e += nthreads) q[e] = 0;
+            for (int e = (PADR + Nx) / 8 * 10 + tid; e < istride; e += nthreads) q[e] = 0;
+        }
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int r) {
+        unsigned char* dst = stg + (size_t)s * sbytes + PADR / 8 * 80;
+        const long long* src = fin + (size_t)r * Nx;
+        issued[s] += 1;
+        mbar_arrive_expect_tx(&bars[s], tx_bytes);
+        for (int l = 0; l < Nx / 8; l += H)   // boxes of 10 x H: 8 elements + 2 zero-filled per line
+            tma_load_2d(dst + l * 80, tmap, 0, r * (Nx / 8) + l, &bars[s]);
+        if constexpr (PERIODIC) {   // wrap lines
+            bulk_g2s(dst + (Nx / 8) * 80, src, 64u, &bars[s]);
+            bulk_g2s(dst + (Nx / 8 + 1) * 80, src + 8, 64u, &bars[s]);
+        }
+        bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+                 XREC_BYTES, &bars[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            const int r = blockIdx.x + s * G;
+            if (r < Np) issue(s, r);
+        }
+    }
+
+    long long acc1[1][XF_V], acc2[1][XF_V];   // column sums of the two passes, units 2^(Ef-51)
+#pragma unroll
+    for (int v = 0; v < XF_V; ++v) {
+        acc1[0][v] = 0;
+        acc2[0][v] = 0;
+    }
+    i128 kin = 0;   // units 2^(Ef-51-KIN_Q), rows after the first pass
+
+    int it = 0;
+    bool failed = false;
+    for (int r = blockIdx.x; r < Np; r += G, ++it) {
+        const int s = it % S;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], (uint32_t)((it / S) & 1), WAIT_LIMIT_NS));
+        long long* ib = ibufs + (size_t)(it & 1) * istride;
+        longlong2* ib2 = reinterpret_cast<longlong2*>(ib);
+        FxW w;
+        int n0 = 0;
+        long long p2q = 0, rowsum = 0;
+        if (ok) {
+            const unsigned char* sb = stg + (size_t)s * sbytes;
+            const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
+            n0 = rc->n0;
+            p2q = rc->p2q;
+#pragma unroll
+            for (int t = 0; t < NTAP; ++t) {
+                w.Wh[t] = rc->Wh[t];
+                w.wlr[t] = make_float2(rc->wl[t], rc->wf[t] * 9.313225746154785e-10f);   // * 2^-30
+            }
+            if (act) {
+                const int A = (n0 - 4) & 1;
+                int e = i + n0 - 4 - A;
+                if constexpr (PERIODIC) {
+                    e %= Nx;
+                    if (e < 0) e += Nx;
+                }
+                long long out[XF_V];
+                const int p1 = (PADR + e) >> 1;
+                const longlong2* sb2 = reinterpret_cast<const longlong2*>(sb);
+                if (A == 0) fx_chunk_padded<0>(sb2, p1, w, out, rng);
+                else fx_chunk_padded<1>(sb2, p1, w, out, rng);
+                if constexpr (!PERIODIC) {
+                    const int k = i + n0;
+                    if (k < 0 || k + XF_V - 1 >= Nx - 1) {
+                        const long long* sbl = reinterpret_cast<const long long*>(sb);
+                        for (int v = 0; v < XF_V; ++v) {
+                            long long xw[NTAP];
+                            for (int t = 0; t < NTAP; ++t) {
+                                const int ee = PADR + e + A + v + t;
+                                xw[t] = sbl[(ee >> 3) * 10 + (ee & 7)];
+                            }
+                            out[v] = fx_edge(xw, rc->w64, 1, k + v, Nx, rc->g64, rc->d64, unit, em.Ef);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < XF_V; ++v) {
+                    const long long Tc = out[v] >> 10;
+                    acc1[0][v] += Tc;
+                    rowsum += Tc;
+                }
+                {
+                    const int pb = (PADR + i) >> 1;
+#pragma unroll
+                    for (int k = 0; k < XF_V / 2; ++k) ib2[pb + k + ((pb + k) >> 2)] = make_longlong2(out[2 * k], out[2 * k + 1]);
+                }
+                if constexpr (PERIODIC) {
+                    if (i < 16) {   // the wrap copy read by the second pass's last windows
+                        const int pb = (PADR + Nx + i) >> 1;
+#pragma unroll
+                        for (int k = 0; k < XF_V / 2; ++k) ib2[pb + k + ((pb + k) >> 2)] = make_longlong2(out[2 * k], out[2 * k + 1]);
+                    }
+                }
+            }
+        }
+        // every warp's first pass is done: the intermediate row is complete and stage s is free
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            const int rn = r + S * G;
+            if (rn < Np) {
+                fence_proxy_async_smem();
+                issue(s, rn);
+            }
+        }
+        kin += (i128)rowsum * (i128)p2q;
+        if (act) {
+            const int A = (n0 - 4) & 1;
+            int e = i + n0 - 4 - A;
+            if constexpr (PERIODIC) {
+                e %= Nx;
+                if (e < 0) e += Nx;
+            }
+            long long out[XF_V];
+            const int p0 = (e + PADR) >> 1;
+            if (A == 0) fx_chunk_padded<0>(ib2, p0, w, out, rng);
+            else fx_chunk_padded<1>(ib2, p0, w, out, rng);
+            if constexpr (!PERIODIC) {
+                const int k = i + n0;
+                if (k < 0 || k + XF_V - 1 >= Nx - 1) {
+                    // the staged record may already be overwritten: read this row's from global memory
+                    const XRec* rg = reinterpret_cast<const XRec*>(static_cast<const unsigned char*>(a.rec) +
+                                                                   (size_t)r * XREC_BYTES);
+#pragma unroll
+                    for (int v = 0; v < XF_V; ++v) {
+                        long long xw[NTAP];
+                        for (int t = 0; t < NTAP; ++t) {
+                            const int ee = e + PADR + A + v + t, p = ee >> 1;
+                            xw[t] = ib[2 * (p + (p >> 2)) + (ee & 1)];
+                        }
+                        out[v] = fx_edge(xw, rg->w64, 1, k + v, Nx, rg->g64, rg->d64, unit, em.Ef);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < XF_V; ++v) acc2[0][v] += out[v] >> 10;
+            long long* orow = fout + (size_t)r * Nx;
+#pragma unroll
+            for (int v = 0; v < XF_V; v += 4) st_global_v4_b64(orow + i + v, out[v], out[v + 1], out[v + 2], out[v + 3]);
+        }
+    }
+    __syncthreads();   // every warp is done with the stage buffers
+    if (rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    i128* scratch = reinterpret_cast<i128*>(stg);
+
+    if (failed) {
+        if (tid == 0) {
+            atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
+            for (int k = 0; k < S; ++k)   // the last copy issued into each stage must land before exit
+                if (issued[k] > 0) mbar_wait_bounded(&bars[k], (uint32_t)((issued[k] - 1) & 1), WAIT_LIMIT_NS);
+        }
+        __syncthreads();
+        return;
+    }
+    fx_colsum_epilogue<1>(a, acc1, em.Ef, scratch);
+    fx_kin_epilogue(a, kin, em.Ef, scratch);
+    fx_colsum_epilogue<1>(b, acc2, em.Ef, scratch);
+}
+
+template <bool PERIODIC>
+__global__ void __launch_bounds__(XXF_THREADS_MAX, 1) xxshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                          XShiftArgs a, XShiftArgs b, EmulArgs em)
+{
+    xxshift_fx_body<PERIODIC>(&tmap, a, b, em);
 }
 
 // ============================================================================ p-shift (FX64)
@@ -456,8 +734,14 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
                     if (v0 && v1) M[rw] = M[rw] + mul_wide(w.Wh[t0], kx0) + mul_wide(w.Wh[t1], kx1);
                     else if (v0) M[rw] += mul_wide(w.Wh[t0], kx0);
                     else if (v1) M[rw] += mul_wide(w.Wh[t1], kx1);
-                    if (v0) Sacc[rw] = __ffma2_rn(w.wlr[t0], xa, Sacc[rw]);
-                    if (v1) Sacc[rw] = __ffma2_rn(w.wlr[t1], xb, Sacc[rw]);
+                    if (v0) {
+                        Sacc[rw].x = fmaf(w.wlr[t0].x, xa.x, Sacc[rw].x);
+                        Sacc[rw].y = fmaf(w.wlr[t0].y, xa.y, Sacc[rw].y);
+                    }
+                    if (v1) {
+                        Sacc[rw].x = fmaf(w.wlr[t1].x, xb.x, Sacc[rw].x);
+                        Sacc[rw].y = fmaf(w.wlr[t1].y, xb.y, Sacc[rw].y);
+                    }
                 }
             };
             constexpr int NU = PS_RPT + 9;
@@ -555,6 +839,34 @@ cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, con
     return cudaGetLastError();
 }
 
+int xxshift_fx_row_bytes(int Nx, int pad, bool periodic) { return xxf_row_bytes(Nx, pad, periodic); }
+
+size_t xxshift_fx_smem_bytes(int Nx, int pad, int stages)
+{
+    const size_t sb = (size_t)std::max(xxf_row_bytes(Nx, pad, true), xxf_row_bytes(Nx, pad, false));
+    return 256 + (size_t)stages * (sb + XREC_BYTES) + 2 * sb;
+}
+
+int xxshift_fx_threads(int Nx) { return std::max(32, (Nx / XF_V + 31) / 32 * 32); }
+
+cudaError_t launch_xxshift_fx(bool periodic, int grid, const CUtensorMap* tmap, const XShiftArgs& a, const XShiftArgs& b,
+                              const EmulArgs& em, cudaStream_t st)
+{
+    if (a.rec == nullptr || a.Nx > XF_V * XXF_THREADS_MAX || a.stages < 1 || a.stages > 8) return cudaErrorInvalidValue;
+    const size_t smem = xxshift_fx_smem_bytes(a.Nx, a.pad, a.stages);
+    const int threads = xxshift_fx_threads(a.Nx);
+    if (periodic) xxshift_fx_kernel<true><<<grid, threads, smem, st>>>(*tmap, a, b, em);
+    else xxshift_fx_kernel<false><<<grid, threads, smem, st>>>(*tmap, a, b, em);
+    return cudaGetLastError();
+}
+
+cudaError_t xxshift_fx_occupancy(bool periodic, int Nx, size_t smem, int* blocks)
+{
+    const int threads = xxshift_fx_threads(Nx);
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xxshift_fx_kernel<true>, threads, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xxshift_fx_kernel<false>, threads, smem);
+}
+
 cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
                              const EmulArgs& em, cudaStream_t st)
 {
@@ -602,6 +914,8 @@ cudaError_t set_kernel_attributes_fx(int max_smem)
     VL_ATTR((xshift_fx_batch_kernel<false, true>));
     VL_ATTR((xshift_fx_batch_kernel<false, false>));
     VL_ATTR((pshift_fx_batch_kernel<false>));
+    VL_ATTR((xxshift_fx_kernel<true>));
+    VL_ATTR((xxshift_fx_kernel<false>));
 #undef VL_ATTR
     return e;
 }

@@ -111,8 +111,21 @@ struct vlasov_sim {
     long long read_step = 0;
     int* err = nullptr;
 
+    // Fused x-shifts (FX64, Nx <= 4096): the second x half-shift of a step and the first of the
+    // next run as one launch (xxshift_fx), so vlasov_step(n) runs head (x-shift, force, p-shift),
+    // n-1 times mid (fused x-shifts, moments, force, p-shift) and tail (x-shift, moments).
+    bool fuse_ok = false, fuse = false;
+    int xxgrid = 0, xxstages = 0;
+    int nctas = 0;                    // max(xgrid, xxgrid): entries of the per-CTA partial buffers
+    void* ctapart_m = nullptr;        // [nctas][3] int128 HMF partials of the fused launch's first pass
+    long long* colpart_m = nullptr;   // [nctas][Nx] its per-CTA column sums (other models)
+    void* kin128 = nullptr;           // [nctas] int128 per-CTA kinetic sums (FX64)
+
     CUtensorMap tmap[2];
+    CUtensorMap xtmap[2];             // fused x-shifts: f[b] as 8-element lines, boxes of 10 x xbox_h
+    int xbox_h = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t ghead[2] = {nullptr, nullptr}, gmid[2] = {nullptr, nullptr}, gtail[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -230,6 +243,16 @@ int make_tmap(vlasov_sim* s, int b)
                      s->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (s->fuse_ok) {
+        // rows of f as 8-element lines; a box of 10 x xbox_h lands as padded lines (2 zero columns)
+        cuuint64_t ldims[2] = {8, (cuuint64_t)s->Nx * (cuuint64_t)s->Np / 8};
+        cuuint64_t lstrides[1] = {64};
+        cuuint32_t lbox[2] = {10, (cuuint32_t)s->xbox_h};
+        r = enc(&s->xtmap[b], CU_TENSOR_MAP_DATA_TYPE_INT64, 2, s->f[b], ldims, lstrides, lbox, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(VLASOV_ECUDA, "cuTensorMapEncodeTiled (row lines) failed (%d)", (int)r);
+    }
     return VLASOV_OK;
 }
 
@@ -260,6 +283,7 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.sin50 = s->sin50;
     a.k_col = s->k_col;
     a.kinpart = kin ? s->kinpart : nullptr;
+    a.kin128 = (kin && s->fx) ? s->kin128 : nullptr;
     a.pmin = s->pmin;
     a.dp = s->dp;
     a.err = s->err;
@@ -287,6 +311,16 @@ int ceil_log2(double v)
     return m == 0.5 ? e - 1 : e;
 }
 
+void drop_graphs(vlasov_sim* s)
+{
+    for (int b = 0; b < 2; ++b)
+        for (cudaGraphExec_t* g : {&s->graph[b], &s->ghead[b], &s->gmid[b], &s->gtail[b]})
+            if (*g) {
+                cudaGraphExecDestroy(*g);
+                *g = nullptr;
+            }
+}
+
 // Fixed-point shifts of the reductions from the largest |f| (bound 2^Ef >= 4 max|f|).  Kernel
 // arguments are captured in the step graphs, so a change of scale drops the graphs.
 void update_scales(vlasov_sim* s, double maxabs)
@@ -305,13 +339,7 @@ void update_scales(vlasov_sim* s, double maxabs)
         const double rmax = s->dp * (double)s->Np * std::ldexp(1.0, Ef);
         k_pot = 124 - ceil_log2((double)s->Nx * (double)s->Nx * s->dx * vmax * rmax * rmax);
     }
-    if (!s->scales_set || Ef != s->Ef || k_col != s->k_col || k_kin != s->k_kin || k_pot != s->k_pot) {
-        for (int b = 0; b < 2; ++b)
-            if (s->graph[b]) {
-                cudaGraphExecDestroy(s->graph[b]);
-                s->graph[b] = nullptr;
-            }
-    }
+    if (!s->scales_set || Ef != s->Ef || k_col != s->k_col || k_kin != s->k_kin || k_pot != s->k_pot) drop_graphs(s);
     s->Ef = Ef;
     s->k_col = k_col;
     s->k_kin = k_kin;
@@ -347,15 +375,17 @@ cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs&
     return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, s->st);
 }
 
-ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments, bool from_acc = true)
+ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments, bool from_acc = true, bool fused_m = false)
 {
     ColReduceArgs a;
     const bool part64 = from_acc && (s->fx || s->emul);
     a.colacc = (from_acc && s->esz == 8 && !part64) ? s->colacc : nullptr;
-    a.colpart64 = part64 ? reinterpret_cast<const long long*>(s->colpart) : nullptr;
+    a.colpart64 = part64 ? (fused_m ? s->colpart_m : reinterpret_cast<const long long*>(s->colpart)) : nullptr;
     a.colpart = s->colpart;
     a.B = B;
-    a.kinpart = kin ? s->kinpart : nullptr;
+    a.kinpart = (kin && !s->fx) ? s->kinpart : nullptr;
+    a.kin128 = (kin && s->fx) ? s->kin128 : nullptr;
+    a.kin_frac = 51 + KIN_Q - s->Ef;
     a.Nx = s->Nx;
     a.k_col = s->k_col;
     a.k_kin = s->k_kin;
@@ -400,7 +430,7 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     return a;
 }
 
-int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false)
+int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int ctas = 0)
 {
     PParamsArgs a;
     a.Nx = s->Nx;
@@ -420,7 +450,7 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false)
     a.wf = (s->emul || s->fx) ? s->pe.wf : nullptr;
     if (from_cta) {
         a.ctapart = s->ctapart;
-        a.ctas = s->xgrid;
+        a.ctas = ctas > 0 ? ctas : s->xgrid;
         a.Ef = s->Ef;
         a.dxdp = s->dx * s->dp;
         CU_TRY(launch_pparams_hmf_cta(a, s->st));
@@ -455,20 +485,24 @@ int mark(vlasov_sim* s, Marks* m)
         if (rc_) return rc_;      \
     } while (0)
 
-// Enqueue one Strang step starting from buffer c (result in buffer c^1).
-int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
+// Step 1 from buffer c into c^1: f^(I) = f(x - p dt/2, p), with the density partials of f^(I).
+int enq_x1(vlasov_sim* s, int c, Marks* marks)
+{
+    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[c ^ 1], s->xp, true, false, s->xrec), s->xp, s->xe, false));
+    MARK();
+    return VLASOV_OK;
+}
+
+// Steps 2-3: rho, F^(I) and the p-shift filters from the density partials of `ctas` CTAs, then the
+// p-shift f^(II) = f^(I)(x, p - F dt) from buffer c^1 into c.
+int enq_force_p(vlasov_sim* s, int c, int ctas, Marks* marks)
 {
     const int o = c ^ 1;
-    MARK();
-    // step 1: f^(I) = f(x - p dt/2, p), with the density partials of f^(I)
-    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, false, s->xrec), s->xp, s->xe, false));
-    MARK();
-    // step 2: rho, moments, F^(I), p-shift filters
     if (s->hmf_cta) {
-        int rc = launch_pparams_only(s, nullptr, true);   // Mx, My from the per-CTA partials
+        int rc = launch_pparams_only(s, nullptr, true, ctas);   // Mx, My from the per-CTA partials
         if (rc) return rc;
     } else {
-        CU_TRY(launch_colreduce(crargs(s, s->xgrid, false, false), s->crgrid, s->st));
+        CU_TRY(launch_colreduce(crargs(s, ctas, false, false), s->crgrid, s->st));
         MARK();
         if (s->model == VLASOV_RING) {
             CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
@@ -478,19 +512,22 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
         if (rc) return rc;
     }
     MARK();
-    // step 3: f^(II) = f^(I)(x, p - F dt)
     CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
     MARK();
-    // step 4: f(t+dt) = f^(II)(x - p dt/2, p), with density + kinetic partials for the moments
-    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[o], s->xp, true, true, s->xrec), s->xp, s->xe, true));
-    MARK();
+    return VLASOV_OK;
+}
+
+// The moment record of the state just written, from the partials of `ctas` CTAs (those of the
+// fused launch's first pass when fused_m).
+int enq_moments(vlasov_sim* s, int ctas, bool fused_m, Marks* marks)
+{
     if (s->hmf_cta) {
-        ColReduceArgs c = crargs(s, s->xgrid, true, true);
-        c.ctapart = s->ctapart;
+        ColReduceArgs c = crargs(s, ctas, true, true);
+        c.ctapart = fused_m ? s->ctapart_m : s->ctapart;
         c.Ef = s->Ef;
         CU_TRY(launch_colreduce_cta(c, s->st));
     } else {
-        CU_TRY(launch_colreduce(crargs(s, s->xgrid, true, true), s->crgrid, s->st));
+        CU_TRY(launch_colreduce(crargs(s, ctas, true, true, true, fused_m), s->crgrid, s->st));
     }
     MARK();
     if (s->model == VLASOV_RING) {
@@ -499,25 +536,93 @@ int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
     }
     return VLASOV_OK;
 }
+
+// Step 4 from buffer c into c^1: f(t+dt) = f^(II)(x - p dt/2, p), then the moments.
+int enq_x2(vlasov_sim* s, int c, Marks* marks)
+{
+    CU_TRY(run_xshift(s, xargs(s, s->f[c], s->f[c ^ 1], s->xp, true, true, s->xrec), s->xp, s->xe, true));
+    MARK();
+    return enq_moments(s, s->xgrid, false, marks);
+}
+
+// Step 4 of this step and step 1 of the next in one launch, buffer c into c^1; then the moments of
+// the state between them (the end of this step).
+int enq_xx(vlasov_sim* s, int c, Marks* marks)
+{
+    XShiftArgs a = xargs(s, s->f[c], nullptr, s->xp, true, true, s->xrec);
+    a.stages = s->xxstages;
+    a.box_h = s->xbox_h;
+    a.ctapart = s->hmf_cta ? s->ctapart_m : nullptr;
+    a.colpart64 = s->hmf_cta ? nullptr : s->colpart_m;
+    XShiftArgs b = xargs(s, nullptr, s->f[c ^ 1], s->xp, true, false, s->xrec);
+    CU_TRY(launch_xxshift_fx(s->xper, s->xxgrid, &s->xtmap[c], a, b, emargs(s, s->xp, s->xe), s->st));
+    MARK();
+    return enq_moments(s, s->xxgrid, true, marks);
+}
+
+// One whole Strang step from buffer c (result in c^1).
+int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
+{
+    MARK();
+    int rc = enq_x1(s, c, marks);
+    if (!rc) rc = enq_force_p(s, c, s->xgrid, marks);
+    if (!rc) rc = enq_x2(s, c, marks);
+    return rc;
+}
+
+// Pieces of a run of fused steps from buffer c (result in c^1): head, mid between steps, tail.
+enum Piece { P_HEAD, P_MID, P_TAIL };
+int enqueue_piece(vlasov_sim* s, int c, Piece k, Marks* marks = nullptr)
+{
+    MARK();
+    if (k == P_HEAD) {
+        int rc = enq_x1(s, c, marks);
+        return rc ? rc : enq_force_p(s, c, s->xgrid, marks);
+    }
+    if (k == P_MID) {
+        int rc = enq_xx(s, c, marks);
+        return rc ? rc : enq_force_p(s, c, s->xxgrid, marks);
+    }
+    return enq_x2(s, c, marks);
+}
 #undef MARK
 
-int build_graph(vlasov_sim* s, int c)
+template <typename F>
+int capture(vlasov_sim* s, cudaGraphExec_t* out, F&& enqueue)
 {
-    if (s->graph[c]) return VLASOV_OK;
+    if (*out) return VLASOV_OK;
     cudaGraph_t g = nullptr;
     CU_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_step(s, c);
+    const int rc = enqueue();
     const cudaError_t e = cudaStreamEndCapture(s->st, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     if (e != cudaSuccess) return fail(VLASOV_ECUDA, "stream capture: %s", cudaGetErrorString(e));
-    const cudaError_t e2 = cudaGraphInstantiate(&s->graph[c], g, 0);
+    const cudaError_t e2 = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e2 != cudaSuccess) return fail(VLASOV_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
     return VLASOV_OK;
 }
+
+int build_graph(vlasov_sim* s, int c)
+{
+    return capture(s, &s->graph[c], [&] { return enqueue_step(s, c); });
+}
+
+int build_fused_graphs(vlasov_sim* s, int c)
+{
+    int rc = capture(s, &s->ghead[c], [&] { return enqueue_piece(s, c, P_HEAD); });
+    if (!rc) rc = capture(s, &s->gmid[c], [&] { return enqueue_piece(s, c, P_MID); });
+    if (!rc) rc = capture(s, &s->gtail[c], [&] { return enqueue_piece(s, c, P_TAIL); });
+    return rc;
+}
+
+// Launches per piece: x-shift 1; force (reductions, filters); p-shift; x-shift 4 or the fused
+// x-shifts; moments.
+int force_launches(const vlasov_sim* s) { return s->hmf_cta ? 1 : (s->model == VLASOV_RING ? 3 : 2); }
+int moment_launches(const vlasov_sim* s) { return s->model == VLASOV_RING ? 2 : 1; }
 
 int check_dev_err(vlasov_sim* s)
 {
@@ -548,10 +653,8 @@ void vlasov_destroy(vlasov_sim* s)
 {
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
-    for (int b = 0; b < 2; ++b) {
-        if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
-        cudaFree(s->f[b]);
-    }
+    drop_graphs(s);
+    for (int b = 0; b < 2; ++b) cudaFree(s->f[b]);
     free_params(s->xp);
     free_params(s->pp);
     free_params(s->sp);
@@ -560,7 +663,8 @@ void vlasov_destroy(vlasov_sim* s)
     free_emul(s->se);
     void* bufs[] = {s->colpart, s->colacc, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
-                    s->hist, s->dstep, s->err, s->xrec, s->srec, s->cos50, s->sin50, s->ctapart};
+                    s->hist, s->dstep, s->err, s->xrec, s->srec, s->cos50, s->sin50, s->ctapart,
+                    s->ctapart_m, s->colpart_m, s->kin128};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -694,14 +798,43 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     s->pgrid = std::min(ptiles, s->nsm * pocc);
     s->crgrid = (Nx + 31) / 32;
 
-    CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->xgrid * Nx));
-    CTRY(cudaMalloc(&s->ctapart, 48 * (size_t)s->xgrid));
+    // Fused x-shifts: S stages of whole rows and two intermediate rows in one CTA's shared memory;
+    // rows arrive in TMA boxes of xbox_h 8-element lines (a multiple of 8 lines dividing Nx / 8,
+    // so that every box lands 128-byte aligned)
+    for (int d = 32; d >= 1 && Nx % 64 == 0; --d)
+        if ((Nx / 64) % d == 0) {
+            s->xbox_h = 8 * d;
+            break;
+        }
+    if (s->fx && Nx <= XF_FUSED_MAX_NX && s->xbox_h > 0) {
+        const size_t row = (size_t)std::max(xxshift_fx_row_bytes(Nx, s->xpad, true), xxshift_fx_row_bytes(Nx, s->xpad, false));
+        const size_t budget = (size_t)max_optin - 2048;
+        const int st = budget > 256 + 2 * row ? (int)std::min<size_t>(3, (budget - 256 - 2 * row) / (row + XREC_BYTES)) : 0;
+        if (st >= 2) {
+            int xocc = 0;
+            CTRY(xxshift_fx_occupancy(s->xper, Nx, xxshift_fx_smem_bytes(Nx, s->xpad, st), &xocc));
+            if (xocc >= 1) {
+                s->xxstages = st;
+                s->xxgrid = std::min(Np, s->nsm * xocc);
+                s->fuse_ok = s->fuse = true;
+            }
+        }
+    }
+    s->nctas = std::max(s->xgrid, s->xxgrid);
+
+    CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->nctas * Nx));
+    CTRY(cudaMalloc(&s->ctapart, 48 * (size_t)s->nctas));
+    CTRY(cudaMalloc(&s->kin128, 16 * (size_t)s->nctas));
+    if (s->fuse_ok) {
+        CTRY(cudaMalloc(&s->ctapart_m, 48 * (size_t)s->nctas));
+        CTRY(cudaMalloc(&s->colpart_m, sizeof(long long) * (size_t)s->nctas * Nx));
+    }
     // HMF with FX64 storage needs no per-column density: the x-shifts hand over three exact
     // numbers per CTA (bounded in int128 while Nx * Np <= 2^24)
     s->hmf_cta = s->fx && model == VLASOV_HMF && (double)Nx * (double)Np <= 16777216.0;
     CTRY(cudaMalloc(&s->colacc, sizeof(unsigned long long) * (size_t)Nx));
     CTRY(cudaMemsetAsync(s->colacc, 0, sizeof(unsigned long long) * (size_t)Nx, s->st));
-    CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->xgrid));
+    CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->nctas));
     CTRY(cudaMalloc(&s->rho, sizeof(double) * Nx));
     CTRY(cudaMalloc(&s->colfx, sizeof(long long) * Nx));
     CTRY(cudaMalloc(&s->Qd, sizeof(double) * Nx));
@@ -858,6 +991,16 @@ int vlasov_step(vlasov_sim* s, int n)
     if (!s) return fail(VLASOV_EINVAL, "NULL handle");
     if (n < 0) return fail(VLASOV_EINVAL, "n < 0");
     if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_step before vlasov_set_f");
+    if (s->fuse && n >= 2) {
+        const int c = s->cur;
+        int rc = build_fused_graphs(s, c);
+        if (rc) return rc;
+        CU_TRY(cudaGraphLaunch(s->ghead[c], s->st));
+        for (int k = 1; k < n; ++k) CU_TRY(cudaGraphLaunch(s->gmid[c], s->st));
+        CU_TRY(cudaGraphLaunch(s->gtail[c], s->st));
+        s->cur ^= 1;
+        return VLASOV_OK;
+    }
     for (int k = 0; k < n; ++k) {
         int rc = build_graph(s, s->cur);
         if (rc) return rc;
@@ -955,16 +1098,31 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 {
     if (!s || n < 1 || !ms_per_launch) return fail(VLASOV_EINVAL, "bad argument");
     if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_step_timed before vlasov_set_f");
+    const bool fused = s->fuse && n >= 2;
     const int L = vlasov_kernels_per_step(s);
     if (max_launches < L) return fail(VLASOV_EINVAL, "max_launches < %d", L);
-    std::vector<cudaEvent_t> ev((size_t)(L + 1) * n, nullptr);
+    // fused: head, n-1 timed mids, tail (the slots are those of a mid piece); else n whole steps
+    const int reps = fused ? n - 1 : n;
+    std::vector<cudaEvent_t> ev((size_t)(L + 1) * reps, nullptr);
     for (auto& e : ev) CU_TRY(cudaEventCreate(&e));
     int rc = VLASOV_OK;
-    for (int k = 0; k < n && !rc; ++k) {
-        Marks m;
-        m.ev = ev.data() + (size_t)k * (L + 1);
-        rc = enqueue_step(s, s->cur, &m);
+    const int c = s->cur;
+    if (fused) {
+        rc = enqueue_piece(s, c, P_HEAD);
+        for (int k = 0; k < reps && !rc; ++k) {
+            Marks m;
+            m.ev = ev.data() + (size_t)k * (L + 1);
+            rc = enqueue_piece(s, c, P_MID, &m);
+        }
+        if (!rc) rc = enqueue_piece(s, c, P_TAIL);
         s->cur ^= 1;
+    } else {
+        for (int k = 0; k < reps && !rc; ++k) {
+            Marks m;
+            m.ev = ev.data() + (size_t)k * (L + 1);
+            rc = enqueue_step(s, s->cur, &m);
+            s->cur ^= 1;
+        }
     }
     if (!rc) {
         cudaError_t e = cudaStreamSynchronize(s->st);
@@ -973,12 +1131,12 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
     if (!rc) {
         for (int q = 0; q < L; ++q) {
             double acc = 0.0;
-            for (int k = 0; k < n; ++k) {
+            for (int k = 0; k < reps; ++k) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ev[(size_t)k * (L + 1) + q], ev[(size_t)k * (L + 1) + q + 1]);
                 acc += ms;
             }
-            ms_per_launch[q] = acc / n;
+            ms_per_launch[q] = acc / reps;
         }
         if (nlaunch) *nlaunch = L;
     }
@@ -991,8 +1149,26 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 int vlasov_kernels_per_step(const vlasov_sim* s)
 {
     if (!s) return 0;
-    if (s->model == VLASOV_RING) return 8;
-    return s->hmf_cta ? 5 : 6;
+    return (s->fuse ? 2 : 3) + force_launches(s) + moment_launches(s);
 }
+
+long long vlasov_launches(const vlasov_sim* s, int n)
+{
+    if (!s || n < 1) return 0;
+    if (!(s->fuse && n >= 2)) return (long long)n * (3 + force_launches(s) + moment_launches(s));
+    // head (x-shift, force, p-shift), n-1 mids, tail (x-shift, moments)
+    return (2 + force_launches(s)) + (long long)(n - 1) * vlasov_kernels_per_step(s) + (1 + moment_launches(s));
+}
+
+int vlasov_set_fused_x(vlasov_sim* s, int on)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (on && !s->fuse_ok)
+        return fail(VLASOV_EINVAL, "fused x-shifts need VLASOV_FX64 storage and Nx <= %d", XF_FUSED_MAX_NX);
+    s->fuse = on != 0;
+    return VLASOV_OK;
+}
+
+int vlasov_fused_x(const vlasov_sim* s) { return (s && s->fuse) ? 1 : 0; }
 
 }  // extern "C"

@@ -116,8 +116,10 @@ struct XShiftArgs {
     const long long* sin50 = nullptr;
     int k_col = 0;
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
+    void* kin128 = nullptr;   // FX64: [ctas] int128 per-CTA kinetic sums instead (units 2^(Ef-51-KIN_Q))
     double pmin, dp;
     int* err;
+    int box_h = 0;        // fused x-shifts: lines of 8 elements per TMA box (divides Nx / 8, <= 256)
     int ctas = 0;         // CTAs that share the rows (row stride; the partials above have this many
                           // entries); 0: gridDim.x.  CTAs at or past it do nothing.
 };
@@ -158,6 +160,8 @@ struct ColReduceArgs {
     int Ef = 0;                             //   (their units: 2^(Ef-51), 2^(Ef-101))
     int B;
     const double* kinpart;   // [B] per-CTA sum_j p_j^2/2 sum_i f, or null
+    const void* kin128 = nullptr;   // or [B] int128 per-CTA kinetic sums in units 2^-kin_frac (exact total)
+    int kin_frac = 0;
     int Nx;
     int k_col;               // fixed-point shift of column sums: X = round(x * 2^k_col) (int64)
     int k_kin;               // shift of the kinetic partials (int128)
@@ -258,6 +262,17 @@ cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks);
 cudaError_t pshift_fx_occupancy(int* blocks);
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                              cudaStream_t st);
+// Fused x-shifts (second half of step n, first half of step n+1) with FX64 storage.
+constexpr int XXF_THREADS_MAX = 512;   // one chunk of 8 columns per thread: Nx <= 4096
+constexpr int XF_FUSED_MAX_NX = 8 * XXF_THREADS_MAX;
+int xxshift_fx_row_bytes(int Nx, int pad, bool periodic);   // one padded row in shared memory
+size_t xxshift_fx_smem_bytes(int Nx, int pad, int stages);
+int xxshift_fx_threads(int Nx);
+cudaError_t xxshift_fx_occupancy(bool periodic, int Nx, size_t smem, int* blocks);
+// tmap: f as a 2-D tensor of 8-element lines ({8, Nx * Np / 8}, 64-byte stride) with a box of
+// {10, a.box_h} (the two extra columns read as zeros: padded rows in shared memory).
+cudaError_t launch_xxshift_fx(bool periodic, int grid, const CUtensorMap* tmap, const XShiftArgs& a, const XShiftArgs& b,
+                              const EmulArgs& em, cudaStream_t st);
 cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
                              const EmulArgs& em, cudaStream_t st);
 cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st);

@@ -26,7 +26,8 @@ EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_
             "vlasov_destroy", "vlasov_last_error", "vlasov_kernels_per_step", "vlasov_step_timed",
             "vlasov_xshift_density_noalloc", "vlasov_batch_create", "vlasov_batch_footprint",
             "vlasov_batch_admit", "vlasov_batch_step", "vlasov_batch_slot_steps", "vlasov_batch_get",
-            "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve")
+            "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve", "vlasov_launches",
+            "vlasov_set_fused_x", "vlasov_fused_x")
 
 
 class VlasovError(RuntimeError):
@@ -198,6 +199,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_last_error.argtypes = []
         lib.vlasov_last_error.restype = ctypes.c_char_p
         lib.vlasov_kernels_per_step.argtypes = [vp]
+        lib.vlasov_launches.argtypes = [vp, ip]
+        lib.vlasov_set_fused_x.argtypes = [vp, ip]
+        lib.vlasov_fused_x.argtypes = [vp]
         lib.vlasov_step_timed.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_xshift_density_noalloc.argtypes = [vp, vp, vp, ip, ip, ctypes.c_double, ctypes.c_double, ip,
                                                       vp, vp]
@@ -216,6 +220,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             if name not in ("vlasov_destroy", "vlasov_last_error", "vlasov_batch_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
         lib.vlasov_batch_footprint.restype = ctypes.c_longlong
+        lib.vlasov_launches.restype = ctypes.c_longlong
         _lib = lib
         return lib
 
@@ -329,6 +334,19 @@ class Sim:
     def kernels_per_step(self) -> int:
         return int(self._lib.vlasov_kernels_per_step(self._h))
 
+    def launches(self, n: int) -> int:
+        """Kernel launches that step(n) enqueues."""
+        return int(self._lib.vlasov_launches(self._h, int(n)))
+
+    @property
+    def fused_x(self) -> bool:
+        """Whether step(n >= 2) fuses the second x half-shift of a step with the first of the next."""
+        return bool(self._lib.vlasov_fused_x(self._h))
+
+    @fused_x.setter
+    def fused_x(self, on: bool):
+        _check(self._lib.vlasov_set_fused_x(self._h, 1 if on else 0))
+
     def step_timed(self, n: int) -> np.ndarray:
         """Mean milliseconds of each launch slot of a step over n eager steps (see vlasov.h)."""
         out = np.zeros(16)
@@ -337,7 +355,19 @@ class Sim:
         return out[:cnt.value].copy()
 
     def slot_names(self) -> list[str]:
-        if self.model == HMF and self.precision == FX64 and self.nx * self.np <= 1 << 24:
+        """Names of the step_timed slots (for n >= 2 when fused_x)."""
+        hmf_cta = self.model == HMF and self.precision == FX64 and self.nx * self.np <= 1 << 24
+        if self.fused_x:
+            names = ["xshift_fused", "reduce_moments"]
+            if self.model == RING:
+                names.append("ring_potential")
+            if hmf_cta:
+                return names + ["force_filters", "pshift_step3"]
+            names.append("reduce_density")
+            if self.model == RING:
+                names.append("ring_force")
+            return names + ["pshift_filters", "pshift_step3"]
+        if hmf_cta:
             return ["xshift_step1", "force_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
         names = ["xshift_step1", "reduce_density"]
         if self.model == RING:

@@ -1,0 +1,90 @@
+"""Fused x-shifts: the second x half-shift of step n and the first of step n+1 (Sec. 3, steps four and
+one) run as one launch that keeps the row between them in shared memory.  The arithmetic of each pass
+is that of the separate x-shift launches and every cross-CTA sum is exact, so a fused run must give
+the same bits as an unfused one: f, and every moment record.  Also checked here: the full-size
+4096^2 HMF workload in the launch configuration the benchmark times (FX64, fused, several steps)
+against the oracle, and the launch accounting."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1206_3229_gb300 import inputs as I
+from paper_1206_3229_gb300 import vlasov as V
+
+pytestmark = pytest.mark.gpu
+
+
+def grid_of(w: I.Workload) -> O.Grid:
+    return O.Grid(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.x_periodic, w.p_periodic,
+                  w.dt, w.eps, w.G)
+
+
+def run(w, f0, steps, fused, calls=None):
+    with V.Sim.from_workload(w, precision="fx64") as s:
+        s.fused_x = fused
+        s.set_f(f0)
+        for n in (calls or [steps]):
+            s.step(n)
+        return s.get_f(), s.moments()
+
+
+@pytest.mark.parametrize("w", [
+    I.HMF_256.resized(256, 256),
+    I.HMF_4096_UNSTABLE.resized(512, 384),
+    I.RING_2048.resized(128, 128),
+    I.SHEET_4096.resized(128, 256),
+    I.HMF_256.resized(320, 328),          # ragged: 40 active threads of 64, boxes of 40 lines
+], ids=["hmf", "hmf_mode", "ring", "sheet", "ragged"])
+def test_fused_run_is_bitwise_the_unfused_run(w):
+    f0 = I.initial_state(w)
+    fa, ma = run(w, f0, 30, fused=False)
+    fb, mb = run(w, f0, 30, fused=True)
+    assert np.array_equal(fa, fb)
+    assert ma.shape == mb.shape == (30, 8)
+    assert np.array_equal(ma, mb)
+
+
+def test_split_calls_give_the_same_bits():
+    """Steps enqueued as 1 + 2 + 7 calls (head/tail pieces at every boundary) = one call of 10."""
+    w = I.HMF_256.resized(128, 128)
+    f0 = I.initial_state(w)
+    fa, ma = run(w, f0, 10, fused=True)
+    fb, mb = run(w, f0, 10, fused=True, calls=[1, 2, 7])
+    assert np.array_equal(fa, fb) and np.array_equal(ma, mb)
+
+
+def test_full_size_hmf_4096_fx64_fused_steps_match_oracle():
+    """The 4096^2 HMF workload as the benchmark runs it (FX64, fused x-shifts, one call of 3 steps)."""
+    w = I.HMF_4096_UNSTABLE
+    f0 = I.initial_state(w)
+    O.set_threads(0)
+    steps = 3
+    fo, mo = O.run(grid_of(w), f0, steps)
+    with V.Sim.from_workload(w, precision="fx64") as s:
+        assert s.fused_x
+        s.set_f(f0)
+        s.step(steps)
+        fg = s.get_f()
+        mg = s.moments()
+    assert np.max(np.abs(fg - fo)) <= 1e-13 * steps * fo.max()
+    for col in (1, 2, 3, 4, 5, 6):
+        assert np.max(np.abs(mg[:, col] - mo[:, col])) <= 1e-12 * max(1.0, np.abs(mo[:, col]).max()), col
+
+
+def test_launch_accounting_and_timed_slots():
+    w = I.HMF_256.resized(128, 128)
+    with V.Sim.from_workload(w, precision="fx64") as s:
+        s.set_f(I.initial_state(w))
+        assert s.fused_x
+        L = s.kernels_per_step()
+        assert L == 4 and len(s.slot_names()) == L
+        # head: x-shift, filters, p-shift; n-1 mids; tail: x-shift, moments
+        assert s.launches(1) == 5 and s.launches(10) == 3 + 9 * L + 2
+        ms = s.step_timed(3)
+        assert ms.shape == (L,) and np.all(ms > 0)
+        s.fused_x = False
+        assert s.kernels_per_step() == 5 and s.launches(10) == 50
+    with V.Sim.from_workload(w, precision="f64") as s:
+        assert not s.fused_x
+        with pytest.raises(V.VlasovError):
+            s.fused_x = True

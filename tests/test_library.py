@@ -58,3 +58,6 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.vlasov_sync(None) == V.EINVAL
     lib.vlasov_destroy(None)
     assert lib.vlasov_kernels_per_step(None) == 0
+    assert lib.vlasov_launches(None, 3) == 0
+    assert lib.vlasov_set_fused_x(None, 1) == V.EINVAL
+    assert lib.vlasov_fused_x(None) == 0
