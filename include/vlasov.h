@@ -82,7 +82,8 @@ typedef struct {
 int vlasov_create(int model, int Nx, int Np, const vlasov_domain* domain, double dt,
                   vlasov_sim** out);
 
-/* Upload f (host, Np*Nx doubles, f[j*Nx+i]); converts to the handle's precision.  Resets the
+/* Upload f (host, Np*Nx doubles, f[j*Nx+i]); converts to the handle's precision (on the device
+   for the 8-byte storage modes; page-locked host memory gives the full copy bandwidth).  Resets the
    step counter and the moment history.  Syncs. */
 int vlasov_set_f(vlasov_sim* sim, const double* host_f);
 

@@ -694,6 +694,15 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
                 fence_proxy_async_smem();
                 issue(b ^ 1, tn);
             }
+            if (cv) {   // the next tile's filters into L1 now, so that no warp waits for L2 on them then
+                const size_t in = (size_t)tn.i0 + lane;
+#pragma unroll
+                for (int k = 0; k < NTAP; ++k) {
+                    prefetch_l1(em.Wh + (size_t)k * Nx + in);
+                    prefetch_l1(em.wl + (size_t)k * Nx + in);
+                    prefetch_l1(em.wf + (size_t)k * Nx + in);
+                }
+            }
         }
         int n0_i;
         bool colvalid;

@@ -913,22 +913,20 @@ int vlasov_set_f(vlasov_sim* s, const double* host_f)
 {
     if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");
     const size_t cells = (size_t)s->Nx * s->Np;
+    if (s->esz == 8) {
+        // 8-byte storage: the FP64 upload lands in the state buffer (FP64 modes) or in the other one
+        // (FX64, converted from there); the bound on |f| and the conversion run on the device
+        void* dst = s->f[s->fx ? s->cur ^ 1 : s->cur];
+        CU_TRY(cudaMemcpyAsync(dst, host_f, cells * 8, cudaMemcpyHostToDevice, s->st));
+        return vlasov_set_f_device(s, static_cast<const double*>(dst));
+    }
     double mx = 0.0;
     for (size_t k = 0; k < cells; ++k) mx = std::max(mx, std::fabs(host_f[k]));
     if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
     update_scales(s, mx);
-    if (s->fx) {
-        std::vector<long long> tmp(cells);
-        for (size_t k = 0; k < cells; ++k) tmp[k] = (long long)fx128_from_f64(host_f[k], FX_FRAC - s->Ef);
-        CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 8, cudaMemcpyHostToDevice, s->st));
-        CU_TRY(cudaStreamSynchronize(s->st));
-    } else if (s->esz == 8) {
-        CU_TRY(cudaMemcpyAsync(s->f[s->cur], host_f, cells * 8, cudaMemcpyHostToDevice, s->st));
-    } else {
-        std::vector<float> tmp(cells);
-        for (size_t k = 0; k < cells; ++k) tmp[k] = (float)host_f[k];
-        CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 4, cudaMemcpyHostToDevice, s->st));
-    }
+    std::vector<float> tmp(cells);
+    for (size_t k = 0; k < cells; ++k) tmp[k] = (float)host_f[k];
+    CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 4, cudaMemcpyHostToDevice, s->st));
     CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
     CU_TRY(cudaStreamSynchronize(s->st));
     s->read_step = 0;
@@ -950,7 +948,7 @@ int vlasov_set_f_device(vlasov_sim* s, const double* dev_f)
     if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
     update_scales(s, mx);
     if (s->fx) CU_TRY(launch_f64_to_fx(dev_f, static_cast<long long*>(s->f[s->cur]), cells, s->Ef, s->st));
-    else CU_TRY(launch_convert(dev_f, 8, s->f[s->cur], s->esz, cells, s->st));
+    else if (dev_f != s->f[s->cur]) CU_TRY(launch_convert(dev_f, 8, s->f[s->cur], s->esz, cells, s->st));
     s->read_step = 0;
     s->has_f = true;
     return VLASOV_OK;
@@ -961,10 +959,11 @@ int vlasov_get_f(vlasov_sim* s, double* host_f)
     if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");
     const size_t cells = (size_t)s->Nx * s->Np;
     if (s->fx) {
-        std::vector<long long> tmp(cells);
-        CU_TRY(cudaMemcpyAsync(tmp.data(), s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
+        // decoded on the device into the other state buffer (free between steps), then one copy
+        double* tmp = static_cast<double*>(s->f[s->cur ^ 1]);
+        CU_TRY(launch_fx_to_f64(static_cast<const long long*>(s->f[s->cur]), tmp, cells, s->Ef, s->st));
+        CU_TRY(cudaMemcpyAsync(host_f, tmp, cells * 8, cudaMemcpyDeviceToHost, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
-        for (size_t k = 0; k < cells; ++k) host_f[k] = fx128_to_f64((i128)tmp[k], FX_FRAC - s->Ef);
     } else if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(host_f, s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
