@@ -363,6 +363,9 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                 "frac": (achieved / peak_gbs) if achieved else None, "traffic": traffic,
                 "algorithmic_bytes": shift_bytes, "peak_source": peak_src,
+                "note": ("the fused launch does the filter arithmetic of two sweeps on one read and one write of "
+                         "f; like the separate sweeps it is bound by instruction issue, not by HBM (ncu summary "
+                         "in profiles/)") if dom_name == "xshift_fused" else None,
                 "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(names, slot_ms)},
                 "per_kernel_gbs": {n: round(shift_bytes / (v * 1e-3) / 1e9, 1) for n, v in zip(names, slot_ms)
                                    if "shift" in n and not n.endswith("filters")}}

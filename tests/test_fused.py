@@ -44,6 +44,22 @@ def test_fused_run_is_bitwise_the_unfused_run(w):
     assert np.array_equal(ma, mb)
 
 
+@pytest.mark.parametrize("w", [
+    # free streaming on a zero-outside x axis with |displacement| up to 64 cells: 80-element halos,
+    # two 640-byte groups of zero lines before each staged row
+    I.Workload("free_far", "free", 256, 128, -8.0, 8.0, -4.0, 4.0, False, False, 2.0, 4),
+    I.HMF_256.resized(64, 16),            # smallest fused grid: one 8-line box per row, 16 rows
+], ids=["zero_x_far_shift", "tiny"])
+def test_fused_edge_cases_are_bitwise_the_unfused_run(w):
+    x = w.xmin + w.dx * np.arange(w.nx)
+    p = w.pmin + w.dp * np.arange(w.np)
+    f0 = np.exp(-0.5 * (x[None, :] / 1.5) ** 2 - (p[:, None] / 1.2) ** 2)   # smooth, ~0 at the edges
+    fa, ma = run(w, f0, 4, fused=False)
+    fb, mb = run(w, f0, 4, fused=True)
+    assert np.array_equal(fa, fb) and np.array_equal(ma, mb)
+    assert np.abs(fa).max() > 0.1
+
+
 def test_split_calls_give_the_same_bits():
     """Steps enqueued as 1 + 2 + 7 calls (head/tail pieces at every boundary) = one call of 10."""
     w = I.HMF_256.resized(128, 128)
