@@ -802,6 +802,7 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
         XRec rc_;
         std::memset(&rc_, 0, sizeof rc_);
         rc_.n0 = Ls.n0;
+        rc_.m4 = (int)((((long long)Ls.n0 - 4) % Nx + Nx) % Nx);
         rc_.p2q = std::llround(std::ldexp(0.5 * p * p, KIN_Q));
         max_n0 = std::max(max_n0, std::abs(Ls.n0));
         rc_.g64 = Ls.g;

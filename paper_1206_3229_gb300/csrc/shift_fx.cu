@@ -308,13 +308,7 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                 w.wlr[t] = make_float2(rc->wl[t], rc->wf[t] * 9.313225746154785e-10f);   // * 2^-30
             }
             const int A = (n0 - 4) & 1;
-            int base;
-            if constexpr (PERIODIC) {
-                base = (n0 - 4 - A) % Nx;
-                if (base < 0) base += Nx;
-            } else {
-                base = n0 - 4 - A;
-            }
+            const int base = PERIODIC ? rc->m4 - A : n0 - 4 - A;   // m4 has the parity of n0 - 4
             long long* orow = fout + (size_t)r * Nx;
 #pragma unroll
             for (int c = 0; c < XF_MAXCH; ++c) {
@@ -503,25 +497,22 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
         long long* ib = ibufs + (size_t)(it & 1) * istride;
         longlong2* ib2 = reinterpret_cast<longlong2*>(ib);
         FxW w;
-        int n0 = 0;
+        int n0 = 0, A = 0, e = 0;   // the row's shift; this thread's window start (both passes)
         long long p2q = 0, rowsum = 0;
         if (ok) {
             const unsigned char* sb = stg + (size_t)s * sbytes;
             const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
             n0 = rc->n0;
             p2q = rc->p2q;
+            A = (n0 - 4) & 1;
+            e = i + (PERIODIC ? rc->m4 - A : n0 - 4 - A);   // m4 has the parity of n0 - 4
+            if (PERIODIC && e >= Nx) e -= Nx;
 #pragma unroll
             for (int t = 0; t < NTAP; ++t) {
                 w.Wh[t] = rc->Wh[t];
                 w.wlr[t] = make_float2(rc->wl[t], rc->wf[t] * 9.313225746154785e-10f);   // * 2^-30
             }
             if (act) {
-                const int A = (n0 - 4) & 1;
-                int e = i + n0 - 4 - A;
-                if constexpr (PERIODIC) {
-                    e %= Nx;
-                    if (e < 0) e += Nx;
-                }
                 long long out[XF_V];
                 const int p1 = (PADR + e) >> 1;
                 const longlong2* sb2 = reinterpret_cast<const longlong2*>(sb);
@@ -575,12 +566,6 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
         }
         kin += (i128)rowsum * (i128)p2q;
         if (act) {
-            const int A = (n0 - 4) & 1;
-            int e = i + n0 - 4 - A;
-            if constexpr (PERIODIC) {
-                e %= Nx;
-                if (e < 0) e += Nx;
-            }
             long long out[XF_V];
             const int p0 = (e + PADR) >> 1;
             if (A == 0) fx_chunk_padded<0>(ib2, p0, w, out, rng);

@@ -175,6 +175,7 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
             XRec r;
             std::memset(&r, 0, sizeof r);
             r.n0 = L.n0;
+            r.m4 = (int)((((long long)L.n0 - 4) % s->Nx + s->Nx) % s->Nx);
             r.g64 = L.g;
             r.d64 = L.d;
             r.g32 = (float)L.g;

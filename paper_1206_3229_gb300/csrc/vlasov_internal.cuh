@@ -83,7 +83,8 @@ struct MomentRec {
 // Per-row filter record of the x-shift, staged into shared memory next to its row by the same bulk
 // copy transaction (all precisions' forms of the ten weights; filled on the host).
 struct XRec {
-    int n0, pad;
+    int n0;
+    int m4;               // (n0 - 4) mod Nx in [0, Nx): where a periodic row's window for output 0 starts
     double w64[NTAP];
     double g64, d64;
     int Wh[NTAP];
