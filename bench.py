@@ -147,6 +147,9 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode
     """
     import torch
     sizes = (256, 512, 1024, 2048)
+    # launch shape of the batched sweeps: the project's autotuner, run once before anything is timed
+    # (later batches of this max_n and precision use the shape it picked)
+    shape, shape_ms = V.batch_autotune(max(sizes), precision, stream_handle)
     cal = I.serving_stream(48, seed=55, sizes=sizes, step_scale=0.1, rate_per_s=1e9)
     reqs = [V.request_from_workload(w, st, 0.0) for (w, st, _t) in cal]
     _, mk = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision=precision)
@@ -193,6 +196,8 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode
                    "dM": abs(math.hypot(res[q].last.Mx, res[q].last.My) - math.hypot(m[-1, 2], m[-1, 3]))})
     return {"requests": len(reqs), "completed": int(sum(ok)), "slots": slots, "mem_budget_gb": budget_bytes / 2 ** 30,
             "precision": precision,
+            "launch_shape": {"rows_per_cta": shape[0], "tiles_per_cta": shape[1],
+                             "autotune_ms_per_batched_step": {f"{r}x{t}": round(v, 4) for (r, t), v in shape_ms.items()}},
             "dtype": ("f32 storage, FP64-accurate displacements and moment sums" if precision == "f32"
                       else "int64 fixed point + f32 (FP64-accurate), as the single-grid fx64 path"),
             "aggregate_value": work / makespan, "unit": UNIT, "makespan_s": makespan,

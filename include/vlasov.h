@@ -194,6 +194,34 @@ typedef struct {
    stream: cudaStream_t or NULL for an owned one.  VLASOV_EINVAL for other precisions. */
 int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int precision, void* stream,
                         vlasov_batch** out);
+
+/* Launch shape of the batched sweeps.  rows_per_cta: x-shift rows per CTA (a slot with Np rows runs
+   on clamp(ceil(Np / rows_per_cta), 16, 512) CTAs, whatever else is in the batch); tiles_per_cta:
+   p-shift tiles (32 columns x 128 rows) per CTA of the batch's largest grid (each slot's p-shift
+   launch has clamp(tiles / tiles_per_cta, 32, 1024) CTAs). */
+typedef struct {
+    int rows_per_cta;
+    int tiles_per_cta;
+} vlasov_batch_shape;
+
+/* As vlasov_batch_create with an explicit shape (NULL: the tuned shape for (max_n, precision) if
+   vlasov_batch_autotune ran for it in this process, else {16, 8}).  rows_per_cta in 1..4096,
+   tiles_per_cta in 1..1024, else VLASOV_EINVAL.  With VLASOV_FX64 a slot's results do not depend
+   on the shape (exact fixed-point sums); with VLASOV_F32 they move at rounding level (each CTA's
+   FP64 column and kinetic sums are rounded before the exact sum over CTAs).  Within one batch the
+   shape is fixed, so a slot's results never depend on the rest of the batch. */
+int vlasov_batch_create_shaped(int slots, int max_n, long long mem_budget_bytes, int precision, void* stream,
+                               const vlasov_batch_shape* shape, vlasov_batch** out);
+int vlasov_batch_shape_of(const vlasov_batch* b, vlasov_batch_shape* out);
+
+/* Autotuner of the batched launch shape: times every candidate (rows_per_cta in {8, 16, 32, 64} x
+   tiles_per_cta in {2, 4, 8, 16}, in that order, tiles fastest) on this GPU with a batch of eight
+   synthetic HMF requests (two each of max_n, max_n/2, max_n/4, max_n/8, at least 16) for 8 batched
+   steps after 2 warm-up steps, returns the fastest in *best and, if ms_per_step is not NULL, the
+   16 candidates' milliseconds per batched step (0 for a candidate that could not run).  The
+   result is kept for the process: later batches of this (max_n, precision) use it.  Needs about
+   2.5 x the device memory of those eight requests; syncs; a few seconds. */
+int vlasov_batch_autotune(int max_n, int precision, void* stream, vlasov_batch_shape* best, double* ms_per_step);
 /* Device bytes one request occupies in a batch of the given precision. */
 long long vlasov_batch_footprint(const vlasov_request* req, int precision);
 /* Admit a request into a free slot (*slot); host_f0 (Np*Nx doubles) or NULL for the device-side
@@ -215,6 +243,7 @@ typedef struct {
     int max_inflight;            /* batched steps queued ahead of the GPU */
     int precision;               /* VLASOV_F32 or VLASOV_FX64 */
     void* stream;
+    int autotune;                /* 1: vlasov_batch_autotune for (max_n, precision) before the run */
 } vlasov_serve_options;
 
 /* Continuous-batching run of a request stream: requests are admitted (in arrival order, at their

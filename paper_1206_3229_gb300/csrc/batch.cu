@@ -18,6 +18,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -31,13 +33,16 @@ using namespace vl;
 namespace {
 
 constexpr int B_CTAS_X_MAX = 512;   // most x-shift CTAs per slot (sizes the kinetic partials)
-constexpr int B_ROWS_PER_CTA = 16;  // x-shift rows per CTA (the CTA count of a slot depends on its Np only)
-constexpr int B_TILES_PER_CTA = 8;  // p-shift tiles per CTA of the largest grid of a batch
+constexpr int B_ROWS_PER_CTA = 16;  // default x-shift rows per CTA (the CTA count of a slot depends on its Np only)
+constexpr int B_TILES_PER_CTA = 8;  // default p-shift tiles per CTA of the largest grid of a batch
 constexpr int B_PAD_ZERO = 64;   // zero halo of non-periodic rows (|x displacement| <= 55 cells)
 constexpr int B_STAGES = 3;
 constexpr int B_INIT_BLOCKS = 128;
 
-int slot_ctas_x(int Np) { return std::min(B_CTAS_X_MAX, std::max(16, (Np + B_ROWS_PER_CTA - 1) / B_ROWS_PER_CTA)); }
+int slot_ctas_x(int Np, int rows_per_cta)
+{
+    return std::min(B_CTAS_X_MAX, std::max(16, (Np + rows_per_cta - 1) / rows_per_cta));
+}
 
 int bfail(int code, const char* msg)
 {
@@ -281,7 +286,7 @@ SlotLayout layout(int Nx, int Np, int esz)
     L.pwl = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
     L.pwf = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
     L.colacc = take((size_t)Nx * 8);
-    L.kinpart = take((size_t)B_CTAS_X_MAX * 8);
+    L.kinpart = take((size_t)B_CTAS_X_MAX * 16);   // FP64 (F32 storage) or int128 (FX64) per CTA
     L.rho = take((size_t)Nx * 8);
     L.F = take((size_t)Nx * 8);
     L.Qd = take((size_t)Nx * 8);
@@ -328,6 +333,7 @@ struct vlasov_batch {
     int prec = VLASOV_F32;           // VLASOV_F32 or VLASOV_FX64, for every slot
     int esz = 4;
     int ctas_x = 16, ctas_p = 32;    // CTAs per slot of the batched sweeps (fixed at capture)
+    vlasov_batch_shape shape = {B_ROWS_PER_CTA, B_TILES_PER_CTA};
     cudaStream_t st = nullptr;
     bool own_stream = false;
     Arena arena;
@@ -428,10 +434,11 @@ int fill_slot_args(vlasov_batch* b, int k)
                 a.colacc = reinterpret_cast<unsigned long long*>(P(b, s, s.L.colacc));
                 a.k_col = s.k_col;
                 a.kinpart = step4 ? reinterpret_cast<double*>(P(b, s, s.L.kinpart)) : nullptr;
+                a.kin128 = (step4 && b->esz == 8) ? P(b, s, s.L.kinpart) : nullptr;   // FX64: exact
                 a.pmin = r.pmin;
                 a.dp = dp;
                 a.err = reinterpret_cast<int*>(P(b, s, s.L.err));
-                a.ctas = slot_ctas_x(Np);
+                a.ctas = slot_ctas_x(Np, b->shape.rows_per_cta);
             }
         }
         // p-shift: reads the other buffer, writes back into v
@@ -456,13 +463,15 @@ int fill_slot_args(vlasov_batch* b, int k)
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return bfail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed for a batch slot");
     }
-    const int B = std::min(slot_ctas_x(Np), Np);
+    const int B = std::min(slot_ctas_x(Np, b->shape.rows_per_cta), Np);
     for (int q = 0; q < 2; ++q) {
         ColReduceArgs& c = b->cr[(size_t)q * b->S + k];
         c.colacc = reinterpret_cast<unsigned long long*>(P(b, s, s.L.colacc));
         c.colpart = nullptr;   // the x-shifts add exact column sums into colacc
         c.B = B;
-        c.kinpart = q ? reinterpret_cast<const double*>(P(b, s, s.L.kinpart)) : nullptr;
+        c.kinpart = (q && b->esz == 4) ? reinterpret_cast<const double*>(P(b, s, s.L.kinpart)) : nullptr;
+        c.kin128 = (q && b->esz == 8) ? P(b, s, s.L.kinpart) : nullptr;   // exact sum of int128 partials
+        c.kin_frac = 51 + KIN_Q - s.Ef;
         c.Nx = Nx;
         c.k_col = s.k_col;
         c.k_kin = s.k_kin;
@@ -548,6 +557,19 @@ int validate_request(const vlasov_request* r, int max_n)
     return VLASOV_OK;
 }
 
+// Launch shapes picked by vlasov_batch_autotune, per (device, max_n, precision), for this process.
+std::mutex g_shape_mu;
+std::map<std::tuple<int, int, int>, vlasov_batch_shape> g_shapes;
+
+void tuned_shape(int max_n, int precision, vlasov_batch_shape* out)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    auto it = g_shapes.find(std::make_tuple(dev, max_n, precision));
+    *out = it != g_shapes.end() ? it->second : vlasov_batch_shape{B_ROWS_PER_CTA, B_TILES_PER_CTA};
+}
+
 }  // namespace
 
 // ================================================================================== C ABI
@@ -568,6 +590,100 @@ void vlasov_batch_destroy(vlasov_batch* b)
 int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int precision, void* stream,
                         vlasov_batch** out)
 {
+    return vlasov_batch_create_shaped(slots, max_n, mem_budget_bytes, precision, stream, nullptr, out);
+}
+
+int vlasov_batch_shape_of(const vlasov_batch* b, vlasov_batch_shape* out)
+{
+    if (!b || !out) return bfail(VLASOV_EINVAL, "NULL argument");
+    *out = b->shape;
+    return VLASOV_OK;
+}
+
+int vlasov_batch_autotune(int max_n, int precision, void* stream, vlasov_batch_shape* best, double* ms_per_step)
+{
+    if (!best) return bfail(VLASOV_EINVAL, "best is NULL");
+    static const int R[4] = {8, 16, 32, 64}, T[4] = {2, 4, 8, 16};
+    // eight synthetic HMF waterbags: two each of max_n, max_n/2, max_n/4, max_n/8 (>= 16)
+    std::vector<vlasov_request> reqs;
+    long long budget = 1 << 20;
+    for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 2; ++c) {
+            vlasov_request r;
+            std::memset(&r, 0, sizeof r);
+            const int n = std::max(16, (max_n >> k) / 8 * 8);
+            r.model = VLASOV_HMF;
+            r.Nx = r.Np = n;
+            r.xmin = -3.14159265358979323846;
+            r.xmax = 3.14159265358979323846;
+            r.pmin = -2.0;
+            r.pmax = 2.0;
+            r.x_periodic = 1;
+            r.dt = 0.05;
+            r.init = 0;
+            r.x0 = 1.5;
+            r.p0 = 0.8;
+            r.noise = 1e-4;
+            r.seed = (unsigned long long)(2 * k + c + 1);
+            r.steps = 1000;
+            const long long fp = vlasov_batch_footprint(&r, precision);
+            if (fp < 0) return bfail(VLASOV_EINVAL, "autotune: precision must be VLASOV_F32 or VLASOV_FX64");
+            budget += fp + 4096;
+            reqs.push_back(r);
+        }
+    double best_ms = 0.0;
+    int last_rc = VLASOV_OK;
+    for (int q = 0; q < 16; ++q) {
+        const vlasov_batch_shape sh = {R[q / 4], T[q % 4]};
+        if (ms_per_step) ms_per_step[q] = 0.0;
+        vlasov_batch* b = nullptr;
+        int rc = vlasov_batch_create_shaped(8, max_n, budget, precision, stream, &sh, &b);
+        for (size_t k = 0; k < reqs.size() && !rc; ++k) {
+            int slot = -1;
+            rc = vlasov_batch_admit(b, &reqs[k], nullptr, &slot);
+        }
+        float ms = 0.f;
+        if (!rc) rc = vlasov_batch_step(b, 2);
+        if (!rc) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            cudaError_t e = cudaEventCreate(&e0);
+            if (e == cudaSuccess) e = cudaEventCreate(&e1);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->st);
+            if (e == cudaSuccess) rc = vlasov_batch_step(b, 8);
+            if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, b->st);
+            if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (e != cudaSuccess && !rc) {
+                char m[256];
+                snprintf(m, sizeof m, "autotune timing: %s", cudaGetErrorString(e));
+                rc = bfail(VLASOV_ECUDA, m);
+            }
+        }
+        vlasov_batch_destroy(b);
+        if (rc) {
+            last_rc = rc;
+            continue;
+        }
+        const double per = ms / 8.0;
+        if (ms_per_step) ms_per_step[q] = per;
+        if (best_ms == 0.0 || per < best_ms) {
+            best_ms = per;
+            *best = sh;
+        }
+    }
+    if (best_ms == 0.0) return last_rc ? last_rc : bfail(VLASOV_ECUDA, "autotune: no candidate ran");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes[std::make_tuple(dev, max_n, precision)] = *best;
+    return VLASOV_OK;
+}
+
+int vlasov_batch_create_shaped(int slots, int max_n, long long mem_budget_bytes, int precision, void* stream,
+                               const vlasov_batch_shape* shape, vlasov_batch** out)
+{
     if (!out) return bfail(VLASOV_EINVAL, "out is NULL");
     *out = nullptr;
     if (slots < 1 || slots > 4096) return bfail(VLASOV_EINVAL, "slots must be in 1..4096");
@@ -577,7 +693,12 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int pr
         return bfail(VLASOV_EINVAL, "batch precision must be VLASOV_F32 or VLASOV_FX64");
     if (precision == VLASOV_FX64 && max_n > xshift_fx_max_cols(XS_THREADS_MIN))
         return bfail(VLASOV_EINVAL, "FX64 batch: max_n above the x-shift row limit");
+    if (shape && (shape->rows_per_cta < 1 || shape->rows_per_cta > 4096 || shape->tiles_per_cta < 1 ||
+                  shape->tiles_per_cta > 1024))
+        return bfail(VLASOV_EINVAL, "batch shape: rows_per_cta in 1..4096, tiles_per_cta in 1..1024");
     vlasov_batch* b = new vlasov_batch();
+    if (shape) b->shape = *shape;
+    else tuned_shape(max_n, precision, &b->shape);
     b->S = slots;
     b->max_n = max_n;
     b->prec = precision;
@@ -587,10 +708,10 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int pr
     // uses as many x-shift CTAs as its own Np calls for, independent of the batch (so its column and
     // kinetic partial sums, and its results, do not depend on what else is in the batch), and the
     // surplus CTAs exit at once.
-    b->ctas_x = slot_ctas_x(max_n);
+    b->ctas_x = slot_ctas_x(max_n, b->shape.rows_per_cta);
     {
         const int tiles = ((max_n + PS_TW - 1) / PS_TW) * ((max_n + PS_TH - 1) / PS_TH);
-        b->ctas_p = std::min(1024, std::max(32, tiles / B_TILES_PER_CTA));
+        b->ctas_p = std::min(1024, std::max(32, tiles / b->shape.tiles_per_cta));
     }
     auto bail = [&](int rc) {
         vlasov_batch_destroy(b);
@@ -1006,8 +1127,14 @@ int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* 
     if (max_n <= 0)
         for (int q = 0; q < n; ++q) max_n = std::max(max_n, std::max(reqs[q].Nx, reqs[q].Np));
     vlasov_batch* b = nullptr;
-    int rc = vlasov_batch_create(std::max(1, opt->slots), std::max(16, max_n), opt->mem_budget_bytes,
-                                 opt->precision ? opt->precision : VLASOV_F32, opt->stream, &b);
+    const int prec = opt->precision ? opt->precision : VLASOV_F32;
+    max_n = std::max(16, max_n);
+    if (opt->autotune) {
+        vlasov_batch_shape sh;
+        int rc0 = vlasov_batch_autotune(max_n, prec, opt->stream, &sh, nullptr);
+        if (rc0) return rc0;
+    }
+    int rc = vlasov_batch_create(std::max(1, opt->slots), max_n, opt->mem_budget_bytes, prec, opt->stream, &b);
     if (rc) return rc;
     const int depth = std::max(1, opt->max_inflight);
     std::vector<int> order(n);

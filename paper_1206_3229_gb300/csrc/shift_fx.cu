@@ -557,7 +557,7 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
             failed = true;
             break;
         }
-        if (tid == 0) {
+        if (tid == 32 * (it % (nthreads >> 5))) {   // the refill's issuer rotates over the warps
             const int rn = r + S * G;
             if (rn < Np) {
                 fence_proxy_async_smem();

@@ -27,7 +27,8 @@ EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_
             "vlasov_xshift_density_noalloc", "vlasov_batch_create", "vlasov_batch_footprint",
             "vlasov_batch_admit", "vlasov_batch_step", "vlasov_batch_slot_steps", "vlasov_batch_get",
             "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve", "vlasov_launches",
-            "vlasov_set_fused_x", "vlasov_fused_x")
+            "vlasov_set_fused_x", "vlasov_fused_x", "vlasov_batch_create_shaped", "vlasov_batch_shape_of",
+            "vlasov_batch_autotune")
 
 
 class VlasovError(RuntimeError):
@@ -69,7 +70,20 @@ class Result(ctypes.Structure):
 
 class ServeOptions(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_n", ctypes.c_int), ("mem_budget_bytes", ctypes.c_longlong),
-                ("max_inflight", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_inflight", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("autotune", ctypes.c_int)]
+
+
+class BatchShape(ctypes.Structure):
+    """vlasov_batch_shape: x-shift rows per CTA, p-shift tiles per CTA of the largest grid."""
+    _fields_ = [("rows_per_cta", ctypes.c_int), ("tiles_per_cta", ctypes.c_int)]
+
+    def as_tuple(self) -> tuple[int, int]:
+        return (self.rows_per_cta, self.tiles_per_cta)
+
+
+# candidate order of vlasov_batch_autotune
+AUTOTUNE_CANDIDATES = [(r, t) for r in (8, 16, 32, 64) for t in (2, 4, 8, 16)]
 
 
 def request_from_workload(w: Workload, steps: int | None = None, arrival_s: float = 0.0) -> Request:
@@ -94,12 +108,20 @@ class Batch:
     """vlasov_batch_*: many simulations advanced by one launch per sub-step (FP32 or FX64 storage)."""
 
     def __init__(self, slots: int, max_n: int, mem_budget_bytes: int, stream: int | None = None,
-                 precision: str | int = "f32"):
+                 precision: str | int = "f32", shape: tuple[int, int] | None = None):
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.vlasov_batch_create(int(slots), int(max_n), int(mem_budget_bytes), _batch_precision(precision),
-                                       ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        sh = BatchShape(*shape) if shape is not None else None
+        _check(lib.vlasov_batch_create_shaped(int(slots), int(max_n), int(mem_budget_bytes),
+                                              _batch_precision(precision), ctypes.c_void_p(stream) if stream else None,
+                                              ctypes.byref(sh) if sh is not None else None, ctypes.byref(h)))
         self._h, self._lib = h, lib
+
+    @property
+    def shape(self) -> tuple[int, int]:
+        sh = BatchShape()
+        _check(self._lib.vlasov_batch_shape_of(self._h, ctypes.byref(sh)))
+        return sh.as_tuple()
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -151,14 +173,25 @@ def batch_footprint(req: Request, precision: str | int = "f32") -> int:
     return int(load().vlasov_batch_footprint(ctypes.byref(req), _batch_precision(precision)))
 
 
+def batch_autotune(max_n: int, precision: str | int = "f32", stream: int | None = None):
+    """vlasov_batch_autotune: the fastest launch shape for batches up to max_n on this GPU (kept for
+    the process) and every candidate's ms per batched step, keyed by AUTOTUNE_CANDIDATES."""
+    lib = load()
+    best = BatchShape()
+    ms = (ctypes.c_double * len(AUTOTUNE_CANDIDATES))()
+    _check(lib.vlasov_batch_autotune(int(max_n), _batch_precision(precision), ctypes.c_void_p(stream) if stream else None,
+                                     ctypes.byref(best), ms))
+    return best.as_tuple(), dict(zip(AUTOTUNE_CANDIDATES, [float(v) for v in ms]))
+
+
 def serve(reqs: list[Request], slots: int, mem_budget_bytes: int, max_n: int = 0, max_inflight: int = 4,
-          stream: int | None = None, precision: str | int = "f32"):
+          stream: int | None = None, precision: str | int = "f32", autotune: bool = False):
     """vlasov_serve: continuous batching of a request stream.  Returns (results, makespan_s)."""
     lib = load()
     arr = (Request * len(reqs))(*reqs)
     res = (Result * max(len(reqs), 1))()
     opt = ServeOptions(int(slots), int(max_n), int(mem_budget_bytes), int(max_inflight), _batch_precision(precision),
-                       ctypes.c_void_p(stream) if stream else None)
+                       ctypes.c_void_p(stream) if stream else None, 1 if autotune else 0)
     mk = ctypes.c_double(0.0)
     _check(lib.vlasov_serve(arr, len(reqs), ctypes.byref(opt), res, ctypes.byref(mk)))
     return [res[k] for k in range(len(reqs))], mk.value
@@ -207,6 +240,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                                       vp, vp]
         lib.vlasov_batch_create.argtypes = [ip, ip, ctypes.c_longlong, ip, vp, ctypes.POINTER(vp)]
         lib.vlasov_batch_footprint.argtypes = [ctypes.POINTER(Request), ip]
+        lib.vlasov_batch_create_shaped.argtypes = [ip, ip, ctypes.c_longlong, ip, vp, ctypes.POINTER(BatchShape),
+                                                   ctypes.POINTER(vp)]
+        lib.vlasov_batch_shape_of.argtypes = [vp, ctypes.POINTER(BatchShape)]
+        lib.vlasov_batch_autotune.argtypes = [ip, ip, vp, ctypes.POINTER(BatchShape), dp]
         lib.vlasov_batch_admit.argtypes = [vp, ctypes.POINTER(Request), dp, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_batch_step.argtypes = [vp, ip]
         lib.vlasov_batch_slot_steps.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]

@@ -61,3 +61,13 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.vlasov_launches(None, 3) == 0
     assert lib.vlasov_set_fused_x(None, 1) == V.EINVAL
     assert lib.vlasov_fused_x(None) == 0
+    assert lib.vlasov_batch_shape_of(None, None) == V.EINVAL
+    assert lib.vlasov_batch_autotune(256, V.F32, None, None, None) == V.EINVAL
+
+
+@pytest.mark.parametrize("rows,tiles", [(0, 8), (16, 0), (5000, 8), (16, 2000)])
+def test_batch_shape_is_checked_before_any_device_work(lib, rows, tiles):
+    h = ctypes.c_void_p()
+    sh = V.BatchShape(rows, tiles)
+    rc = lib.vlasov_batch_create_shaped(4, 256, 1 << 28, V.F32, None, ctypes.byref(sh), ctypes.byref(h))
+    assert rc == V.EINVAL and not h.value
