@@ -375,6 +375,17 @@ def main():
                 "per_kernel_gbs": {n: round(shift_bytes / (v * 1e-3) / 1e9, 1) for n, v in zip(names, slot_ms)
                                    if "shift" in n and not n.endswith("filters")}}
 
+    # ---- Casimirs of the state after the timed steps (entropy and integral of f^2): one synced call
+    cas_ms = []
+    for _ in range(3):
+        c0 = time.perf_counter()
+        S_ent, Q_l2 = sim.casimirs()
+        cas_ms.append((time.perf_counter() - c0) * 1e3)
+    casimirs = {"entropy": S_ent, "l2": Q_l2, "ms_per_call": min(cas_ms),
+                "read_gbs": cells * esz / (min(cas_ms) * 1e-3) / 1e9,
+                "note": "vlasov_casimirs: one FP64 log per cell (bound by the FP64 pipe, not HBM), host-timed "
+                        "call including its launch and synchronisation"}
+
     # ---- end to end through the public API with host buffers
     pinned = torch.empty((w.np, w.nx), dtype=torch.float64, pin_memory=True).numpy()
     pinned[...] = f0
@@ -449,6 +460,7 @@ def main():
                                  "M": float(np.hypot(hist[-1, 2], hist[-1, 3])), "energy": float(hist[-1, 6])}
                 if len(hist) else None,
                 "other_precisions": others,
+                "casimirs": casimirs,
                 "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -127,6 +127,13 @@ int vlasov_moments(vlasov_sim* sim, vlasov_moments_t* out, int max, int* count);
 int vlasov_substep(vlasov_sim* sim, int axis, const double* host_disp);
 int vlasov_density_force(vlasov_sim* sim, double* host_rho, double* host_F);
 
+/* Casimirs of the current f (Eq. casimirs, Sec. 4): *entropy = -dx dp sum over nodes with f > 0 of
+   f ln f (s(f) = -f log f, the entropy whose loss measures the information lost to the grid;
+   nodes where spline undershoot made f <= 0 add nothing) and *l2 = dx dp sum f^2 (s(f) = f^2);
+   either pointer may be NULL.  FP64 arithmetic on the stored values, fixed summation order
+   (deterministic).  Syncs. */
+int vlasov_casimirs(vlasov_sim* sim, double* entropy, double* l2);
+
 /* Wait for the handle's stream and report any device-side error flag. */
 int vlasov_sync(vlasov_sim* sim);
 

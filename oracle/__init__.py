@@ -77,6 +77,8 @@ def _load():
             lib.vo_force.argtypes = [pp, dp, dp]
             lib.vo_pshift_cells.argtypes = [pp, dp, dp]
             lib.vo_moments_of.argtypes = [pp, dp, ctypes.POINTER(_Moments)]
+            lib.vo_entropy.argtypes = [pp, dp]
+            lib.vo_entropy.restype = ctypes.c_double
             lib.vo_run.argtypes = [pp, dp, ctypes.c_long, ctypes.POINTER(_Moments)]
             lib.vo_run.restype = ctypes.c_int
             lib.vo_step_parts.argtypes = [pp, dp, dp, dp, dp, dp]
@@ -207,6 +209,13 @@ def moments(g: Grid, f: np.ndarray) -> dict:
     p = g._c()
     _load().vo_moments_of(ctypes.byref(p), _ptr(f), ctypes.byref(m))
     return {k: getattr(m, k) for k in MOMENT_FIELDS}
+
+
+def entropy(g: Grid, f: np.ndarray) -> float:
+    """Eq. (casimirs) with s(f) = -f log f (the entropy of Secs. 4.1-4.2): -dx dp sum_{f > 0} f ln f."""
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(g.np, g.nx)
+    p = g._c()
+    return float(_load().vo_entropy(ctypes.byref(p), _ptr(f)))
 
 
 def step_parts(g: Grid, f: np.ndarray) -> dict:

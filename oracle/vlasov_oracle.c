@@ -214,6 +214,19 @@ void vo_pshift_cells(const vo_params* P, const double* F, double* s_col)
 }
 
 /* ---------------------------------------------------------------- diagnostics (Sec. 4: energy, norm, Casimirs) */
+/* Eq. (casimirs) with s(f) = -f log f, the entropy of Secs. 4.1-4.2, by the rectangle rule on the
+   grid nodes; nodes where f <= 0 (spline undershoot) contribute nothing (f log f -> 0 as f -> 0+). */
+double vo_entropy(const vo_params* P, const double* f)
+{
+    const long nx = P->nx, np = P->np;
+    const double dx = (P->xmax - P->xmin) / (double)nx;
+    const double dp = (P->pmax - P->pmin) / (double)np;
+    nsum s = {0, 0};
+    for (size_t k = 0; k < (size_t)nx * (size_t)np; ++k)
+        if (f[k] > 0.0) ns_add(&s, -f[k] * log(f[k]));
+    return dx * dp * ns_val(&s);
+}
+
 void vo_moments_of(const vo_params* P, const double* f, vo_moments* out)
 {
     const long nx = P->nx, np = P->np;

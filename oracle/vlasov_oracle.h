@@ -55,6 +55,9 @@ void vo_force(const vo_params* P, const double* rho, double* F);
 /* p-displacement in cells of every column: s_i = F_i * (dt/dp). */
 void vo_pshift_cells(const vo_params* P, const double* F, double* s_col);
 
+/* Entropy Casimir of Eq. (casimirs), s(f) = -f log f: -dx dp sum over nodes with f > 0 of f ln f. */
+double vo_entropy(const vo_params* P, const double* f);
+
 /* mass, magnetisation, kinetic, potential, total energy and the L2 Casimir of f. */
 void vo_moments_of(const vo_params* P, const double* f, vo_moments* out);
 

@@ -701,6 +701,72 @@ cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st
     return cudaGetLastError();
 }
 
+// ============================================================================ Casimirs
+// Eq. (casimirs) for s(f) = -f log f (the entropy of Secs. 4.1-4.2) and s(f) = f^2, on the stored f:
+// per-thread FP64 sums over a fixed grid-stride set of cells, fixed-order block sums, one partial
+// pair per block; casimir_final_kernel adds the partials in block order.  Deterministic.
+// kind 0: FX64 cells (unit = 2^(Ef-61)), 1: double, 2: float.
+constexpr int CAS_THREADS = 256;
+
+template <int KIND>
+__global__ void __launch_bounds__(CAS_THREADS) casimir_kernel(const void* __restrict__ f, size_t n, double unit,
+                                                               double* __restrict__ part)
+{
+    double s = 0.0, q = 0.0;
+    for (size_t k = blockIdx.x * (size_t)CAS_THREADS + threadIdx.x; k < n; k += (size_t)gridDim.x * CAS_THREADS) {
+        double v;
+        if constexpr (KIND == 0) v = (double)__ldg(static_cast<const long long*>(f) + k) * unit;
+        else if constexpr (KIND == 1) v = __ldg(static_cast<const double*>(f) + k);
+        else v = (double)__ldg(static_cast<const float*>(f) + k);
+        if (v > 0.0) s -= v * log(v);
+        q = fma(v, v, q);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    __shared__ double sh[2][CAS_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = s;
+        sh[1][wid] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < CAS_THREADS / 32; ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void casimir_final_kernel(const double* __restrict__ part, int nb, double dxdp, double* __restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        a += part[2 * k];
+        b += part[2 * k + 1];
+    }
+    out[0] = dxdp * a;
+    out[1] = dxdp * b;
+}
+
+// part: 2 * CAS_BLOCKS doubles, out: 2 doubles (entropy, l2).
+cudaError_t launch_casimirs(int kind, const void* f, size_t n, double unit, double dxdp, double* part, double* out,
+                            cudaStream_t st)
+{
+    if (kind == 0) casimir_kernel<0><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
+    else if (kind == 1) casimir_kernel<1><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
+    else casimir_kernel<2><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
+    casimir_final_kernel<<<1, 32, 0, st>>>(part, CAS_BLOCKS, dxdp, out);
+    return cudaGetLastError();
+}
+
 // ============================================================================ utilities
 // Column sums of f into one partial row (used by the density/force test hook).
 template <typename T>

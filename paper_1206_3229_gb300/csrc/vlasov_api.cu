@@ -823,7 +823,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     }
     s->nctas = std::max(s->xgrid, s->xxgrid);
 
-    CTRY(cudaMalloc(&s->colpart, sizeof(double) * (size_t)s->nctas * Nx));
+    // per-CTA column partial rows; also the scratch of vlasov_casimirs (2 * CAS_BLOCKS + 2 doubles)
+    CTRY(cudaMalloc(&s->colpart, sizeof(double) * std::max((size_t)s->nctas * Nx, (size_t)2 * CAS_BLOCKS + 2)));
     CTRY(cudaMalloc(&s->ctapart, 48 * (size_t)s->nctas));
     CTRY(cudaMalloc(&s->kin128, 16 * (size_t)s->nctas));
     if (s->fuse_ok) {
@@ -1084,6 +1085,25 @@ int vlasov_density_force(vlasov_sim* s, double* host_rho, double* host_F)
     if (host_rho) CU_TRY(cudaMemcpyAsync(host_rho, s->rho, sizeof(double) * s->Nx, cudaMemcpyDeviceToHost, s->st));
     if (host_F) CU_TRY(cudaMemcpyAsync(host_F, s->Fout, sizeof(double) * s->Nx, cudaMemcpyDeviceToHost, s->st));
     CU_TRY(cudaStreamSynchronize(s->st));
+    return check_dev_err(s);
+}
+
+int vlasov_casimirs(vlasov_sim* s, double* entropy, double* l2)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_casimirs before vlasov_set_f");
+    const size_t cells = (size_t)s->Nx * s->Np;
+    const int kind = s->fx ? 0 : (s->esz == 8 ? 1 : 2);
+    const double unit = s->fx ? std::ldexp(1.0, s->Ef - FX_FRAC) : 1.0;
+    // scratch: the column partial rows (at least 2 * CAS_BLOCKS + 2 doubles)
+    double* part = s->colpart;
+    double* out = s->colpart + 2 * CAS_BLOCKS;
+    CU_TRY(launch_casimirs(kind, s->f[s->cur], cells, unit, s->dx * s->dp, part, out, s->st));
+    double h[2] = {0.0, 0.0};
+    CU_TRY(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    if (entropy) *entropy = h[0];
+    if (l2) *l2 = h[1];
     return check_dev_err(s);
 }
 

@@ -276,6 +276,10 @@ cudaError_t launch_xxshift_fx(bool periodic, int grid, const CUtensorMap* tmap, 
                               const EmulArgs& em, cudaStream_t st);
 cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
                              const EmulArgs& em, cudaStream_t st);
+// Casimirs (entropy, integral of f^2) of a stored f: kind 0 FX64 (unit = 2^(Ef-61)), 1 double, 2 float.
+constexpr int CAS_BLOCKS = 8 * 152;
+cudaError_t launch_casimirs(int kind, const void* f, size_t n, double unit, double dxdp, double* part, double* out,
+                            cudaStream_t st);
 cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st);
 cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cudaStream_t st);
 cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double* colpart, cudaStream_t st);

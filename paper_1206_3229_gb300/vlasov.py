@@ -28,7 +28,7 @@ EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_
             "vlasov_batch_admit", "vlasov_batch_step", "vlasov_batch_slot_steps", "vlasov_batch_get",
             "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve", "vlasov_launches",
             "vlasov_set_fused_x", "vlasov_fused_x", "vlasov_batch_create_shaped", "vlasov_batch_shape_of",
-            "vlasov_batch_autotune")
+            "vlasov_batch_autotune", "vlasov_casimirs")
 
 
 class VlasovError(RuntimeError):
@@ -244,6 +244,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                                    ctypes.POINTER(vp)]
         lib.vlasov_batch_shape_of.argtypes = [vp, ctypes.POINTER(BatchShape)]
         lib.vlasov_batch_autotune.argtypes = [ip, ip, vp, ctypes.POINTER(BatchShape), dp]
+        lib.vlasov_casimirs.argtypes = [vp, dp, dp]
         lib.vlasov_batch_admit.argtypes = [vp, ctypes.POINTER(Request), dp, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_batch_step.argtypes = [vp, ip]
         lib.vlasov_batch_slot_steps.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
@@ -367,6 +368,12 @@ class Sim:
 
     def sync(self):
         _check(self._lib.vlasov_sync(self._h))
+
+    def casimirs(self) -> tuple[float, float]:
+        """(entropy, integral of f^2) of the current f (vlasov_casimirs)."""
+        e, q = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(self._lib.vlasov_casimirs(self._h, ctypes.byref(e), ctypes.byref(q)))
+        return e.value, q.value
 
     def kernels_per_step(self) -> int:
         return int(self._lib.vlasov_kernels_per_step(self._h))

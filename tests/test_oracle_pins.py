@@ -312,3 +312,46 @@ def test_splitmix64_published_vectors():
         want = [int(v, 16) for v in gd[key].split()]
         got = I.splitmix64(seed, np.arange(1, len(want) + 1))
         assert [int(v) for v in got] == want
+
+
+# ------------------------------------------------------------------------------------- Casimirs
+def _gauss(nx, np_, sx, sp, L=12.0, P=12.0):
+    g = O.Grid("free", nx, np_, -L / 2, L / 2, -P / 2, P / 2, True, True, 0.1)
+    x = g.xmin + (g.xmax - g.xmin) / nx * np.arange(nx)
+    p = g.pmin + (g.pmax - g.pmin) / np_ * np.arange(np_)
+    f = np.exp(-0.5 * (x[None, :] / sx) ** 2 - 0.5 * (p[:, None] / sp) ** 2) / (2 * math.pi * sx * sp)
+    return g, f
+
+
+def test_entropy_and_l2_of_a_gaussian_match_their_closed_forms():
+    """Differential entropy of a 2-D normal density, 1 + ln(2 pi sx sp), and its integral of f^2,
+    1 / (4 pi sx sp): the rectangle rule converges spectrally for a resolved, decayed Gaussian."""
+    sx, sp = 0.9, 1.3
+    g, f = _gauss(192, 256, sx, sp, 24.0, 24.0)
+    assert O.entropy(g, f) == pytest.approx(1.0 + math.log(2 * math.pi * sx * sp), abs=1e-10)
+    assert O.moments(g, f)["l2"] == pytest.approx(1.0 / (4 * math.pi * sx * sp), abs=1e-10)
+
+
+def test_entropy_scaling_identity_and_negative_cells():
+    """S[lambda f] = lambda S[f] - lambda ln(lambda) M[f]; nodes with f <= 0 add nothing to S."""
+    g, f = _gauss(128, 96, 0.7, 1.1)
+    M = O.moments(g, f)["mass"]
+    for lam in (0.25, 3.0):
+        assert O.entropy(g, lam * f) == pytest.approx(lam * O.entropy(g, f) - lam * math.log(lam) * M, rel=1e-12)
+    h = f.copy()
+    h[::7, ::5] = -1e-3   # spline undershoot
+    mask = h > 0
+    assert O.entropy(g, h) == pytest.approx(O.entropy(g, np.where(mask, f, 0.0)), rel=1e-14)
+
+
+def test_entropy_is_conserved_by_integer_free_streaming_and_maximal_for_the_box():
+    """An integer-cell x-shift permutes nodes (the method is exact there): every Casimir is conserved.
+    Among densities of equal mass on the same support the uniform one has the largest entropy."""
+    w = I.HMF_256.resized(64, 64)
+    g = grid_of(w)
+    rng = np.random.default_rng(3)
+    f = rng.uniform(0.1, 1.0, (64, 64))
+    s = np.round(rng.uniform(-9, 9, 64))
+    assert O.entropy(g, O.advect_x(g, f, s)) == pytest.approx(O.entropy(g, f), rel=1e-13)
+    box = np.full_like(f, f.mean())
+    assert O.entropy(g, box) > O.entropy(g, f)
