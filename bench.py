@@ -211,10 +211,10 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode
 
 
 DTYPE = {"fx64": "int64 fixed point + f32 (FP64-accurate)", "f64": "f64 storage, int64 + f32 arithmetic (FP64-accurate)",
-         "f64_native": "f64", "f32": "f32"}
+         "f64_native": "f64", "f32": "f32", "bf16": "bf16 storage, f32 arithmetic (experiment)"}
 # Source files whose kernels each storage mode's sweeps run (for matching stored ncu traffic).
 KERNEL_SOURCES = {"fx64": ("shift_fx.cu",), "f64": ("shift_f64e.cu",), "f64_native": ("shift_kernels.cu",),
-                  "f32": ("shift_kernels.cu",)}
+                  "f32": ("shift_kernels.cu",), "bf16": ("shift_kernels.cu",)}
 COMMON_SOURCES = ("emul.cuh", "ptx.cuh", "shift_common.cuh", "vlasov_internal.cuh", "fixed_point.cuh")
 
 
@@ -295,7 +295,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=I.HMF_4096_UNSTABLE.name, choices=sorted(I.WORKLOADS))
-    ap.add_argument("--precision", default="fx64", choices=["f64", "fx64", "f32", "f64_native"])
+    ap.add_argument("--precision", default="fx64", choices=["f64", "fx64", "f32", "f64_native", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f32", action="store_true", help="skip the secondary measurements of the other storage modes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -325,7 +325,7 @@ def main():
 
     f0 = I.initial_state(w)
     cells = w.cells
-    esz = 4 if args.precision == "f32" else 8
+    esz = {"f32": 4, "bf16": 2}.get(args.precision, 8)
     stream = torch.cuda.Stream()
     sim = V.Sim.from_workload(w, precision=args.precision, stream=stream.cuda_stream)
     sim.set_f(f0)
@@ -408,7 +408,7 @@ def main():
     # ---- secondary: the other storage modes on the same workload (same timing rules)
     others = {}
     if not args.no_f32:
-        for prec in [p for p in ("fx64", "f64", "f64_native", "f32") if p != args.precision]:
+        for prec in [p for p in ("fx64", "f64", "f64_native", "f32", "bf16") if p != args.precision]:
             s2 = V.Sim.from_workload(w, precision=prec, stream=stream.cuda_stream)
             s2.set_f(f0)
             s2.step(args.warmup)
@@ -421,7 +421,7 @@ def main():
             a1.synchronize()
             ms2 = a0.elapsed_time(a1)
             sl2 = s2.step_timed(4)
-            eb = 4 if prec == "f32" else 8
+            eb = {"f32": 4, "bf16": 2}.get(prec, 8)
             sw2 = 2 if s2.fused_x and args.steps >= 2 else 3
             others[prec] = {"value": world * cells * args.steps / (ms2 * 1e-3), "ms_per_step": ms2 / args.steps,
                             "hbm_sweeps_per_step": sw2,

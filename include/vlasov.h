@@ -50,8 +50,11 @@ enum { VLASOV_HMF = 0, VLASOV_RING = 1, VLASOV_SHEET = 2, VLASOV_FREE = 3 };
    FX64: 64-bit fixed-point storage, f = X * 2^(Ef-62) with X int64 (same 8 bytes per cell; absolute
         resolution 2^-60 of max|f|, finer than FP64 for every |f| above 2^-7 of max|f|), and the
         F64 filter arithmetic without the IEEE decode/encode.  The API still takes and returns
-        doubles.  Needs |f| < 2^Ef (else VLASOV_ERANGE). */
-enum { VLASOV_F64 = 0, VLASOV_F32 = 1, VLASOV_F64_NATIVE = 2, VLASOV_FX64 = 3 };
+        doubles.  Needs |f| < 2^Ef (else VLASOV_ERANGE).
+   BF16: experiment: bfloat16 storage (8 significant bits, 2 bytes per cell), interpolation in FP32,
+        displacements and moment sums as for F32.  Uploads round to nearest even.  Single grids
+        only (not the batched form). */
+enum { VLASOV_F64 = 0, VLASOV_F32 = 1, VLASOV_F64_NATIVE = 2, VLASOV_FX64 = 3, VLASOV_BF16 = 4 };
 
 typedef struct vlasov_sim vlasov_sim; /* opaque; owns every device buffer it uses */
 
@@ -62,7 +65,7 @@ typedef struct {
     int p_periodic;      /* same for p */
     double eps;          /* ring softening of Eq. (ringpot), > 0 for VLASOV_RING */
     double G;            /* sheet coupling: V(x) = 2 pi G |x| */
-    int precision;       /* VLASOV_F64, VLASOV_F32, VLASOV_F64_NATIVE or VLASOV_FX64 */
+    int precision;       /* VLASOV_F64, VLASOV_F32, VLASOV_F64_NATIVE, VLASOV_FX64 or VLASOV_BF16 */
     void* stream;        /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
 } vlasov_domain;
 

@@ -12,6 +12,7 @@
 // order-free, and without the long dependent FP64 chains that are slow on this GPU.
 #include "emul.cuh"
 #include "fixed_point.cuh"
+#include <cuda_bf16.h>
 #include "vlasov_internal.cuh"
 
 namespace vl {
@@ -705,7 +706,7 @@ cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st
 // Eq. (casimirs) for s(f) = -f log f (the entropy of Secs. 4.1-4.2) and s(f) = f^2, on the stored f:
 // per-thread FP64 sums over a fixed grid-stride set of cells, fixed-order block sums, one partial
 // pair per block; casimir_final_kernel adds the partials in block order.  Deterministic.
-// kind 0: FX64 cells (unit = 2^(Ef-61)), 1: double, 2: float.
+// kind 0: FX64 cells (unit = 2^(Ef-61)), 1: double, 2: float, 3: bf16.
 constexpr int CAS_THREADS = 256;
 
 template <int KIND>
@@ -717,7 +718,8 @@ __global__ void __launch_bounds__(CAS_THREADS) casimir_kernel(const void* __rest
         double v;
         if constexpr (KIND == 0) v = (double)__ldg(static_cast<const long long*>(f) + k) * unit;
         else if constexpr (KIND == 1) v = __ldg(static_cast<const double*>(f) + k);
-        else v = (double)__ldg(static_cast<const float*>(f) + k);
+        else if constexpr (KIND == 2) v = (double)__ldg(static_cast<const float*>(f) + k);
+        else v = (double)__bfloat162float(static_cast<const __nv_bfloat16*>(f)[k]);
         if (v > 0.0) s -= v * log(v);
         q = fma(v, v, q);
     }
@@ -762,7 +764,8 @@ cudaError_t launch_casimirs(int kind, const void* f, size_t n, double unit, doub
 {
     if (kind == 0) casimir_kernel<0><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
     else if (kind == 1) casimir_kernel<1><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
-    else casimir_kernel<2><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
+    else if (kind == 2) casimir_kernel<2><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
+    else casimir_kernel<3><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
     casimir_final_kernel<<<1, 32, 0, st>>>(part, CAS_BLOCKS, dxdp, out);
     return cudaGetLastError();
 }
@@ -792,6 +795,8 @@ cudaError_t launch_colsum(int elem_bytes, const void* f, int Nx, int Np, double*
     (void)B;
     const int grid = (Nx + 31) / 32;
     if (elem_bytes == 8) colsum_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(f), Nx, Np, colpart);
+    else if (elem_bytes == 2)
+        colsum_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(f), Nx, Np, colpart);
     else colsum_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(f), Nx, Np, colpart);
     return cudaGetLastError();
 }
@@ -806,7 +811,13 @@ __global__ void convert_kernel(const S* __restrict__ s, D* __restrict__ d, size_
 cudaError_t launch_convert(const void* src, int src_bytes, void* dst, int dst_bytes, size_t n, cudaStream_t st)
 {
     const int grid = 1024;
-    if (src_bytes == 8 && dst_bytes == 4)
+    if (src_bytes == 8 && dst_bytes == 2)
+        convert_kernel<double, __nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const double*>(src),
+                                                                     static_cast<__nv_bfloat16*>(dst), n);
+    else if (src_bytes == 2 && dst_bytes == 8)
+        convert_kernel<__nv_bfloat16, double><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(src),
+                                                                     static_cast<double*>(dst), n);
+    else if (src_bytes == 8 && dst_bytes == 4)
         convert_kernel<double, float><<<grid, 256, 0, st>>>(static_cast<const double*>(src), static_cast<float*>(dst), n);
     else if (src_bytes == 4 && dst_bytes == 8)
         convert_kernel<float, double><<<grid, 256, 0, st>>>(static_cast<const float*>(src), static_cast<double*>(dst), n);

@@ -17,15 +17,23 @@
 #include "shift_common.cuh"
 #include "vlasov_internal.cuh"
 
+#include <cuda_bf16.h>
+#include <type_traits>
+
 namespace vl {
 
-template <typename T>
+using bf16 = __nv_bfloat16;
+
+// Storage type S of f (double, float, or bf16 for the BF16 storage experiment), the type T the
+// filter computes in, and the 16-byte vector of V cells the x-shift loads and stores.
+template <typename S>
 struct VecOf;
 template <>
 struct VecOf<double> {
     static constexpr int V = 2;
     static constexpr int W = 12;   // window: V + 9 taps + alignment slack, rounded to V
     using vec = double2;
+    using T = double;
     using acc = double;
 };
 template <>
@@ -33,33 +41,93 @@ struct VecOf<float> {
     static constexpr int V = 4;
     static constexpr int W = 16;
     using vec = float4;
+    using T = float;
+    using acc = float;
+};
+template <>
+struct VecOf<bf16> {
+    static constexpr int V = 8;
+    static constexpr int W = 24;
+    using vec = uint4;             // 8 bf16, element 2q in the low half of word q
+    using T = float;
     using acc = float;
 };
 
+__device__ __forceinline__ float to_math(bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_math(float v) { return v; }
+__device__ __forceinline__ double to_math(double v) { return v; }
+template <typename S>
+__device__ __forceinline__ S from_math(typename VecOf<S>::T v)
+{
+    if constexpr (std::is_same<S, bf16>::value) return __float2bfloat16_rn(v);   // round to nearest even
+    else return v;
+}
+
+// The V cells of a loaded vector as math values, and V results as a vector to store.
+template <typename S>
+__device__ __forceinline__ void unpack(const typename VecOf<S>::vec& v, typename VecOf<S>::T* x)
+{
+    if constexpr (std::is_same<S, double>::value) {
+        x[0] = v.x;
+        x[1] = v.y;
+    } else if constexpr (std::is_same<S, float>::value) {
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+    } else {
+        const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[q]));
+            x[2 * q] = f2.x;
+            x[2 * q + 1] = f2.y;
+        }
+    }
+}
+template <typename S>
+__device__ __forceinline__ typename VecOf<S>::vec pack(const typename VecOf<S>::T* x)
+{
+    typename VecOf<S>::vec v;
+    if constexpr (std::is_same<S, double>::value) {
+        v.x = x[0];
+        v.y = x[1];
+    } else if constexpr (std::is_same<S, float>::value) {
+        v.x = x[0];
+        v.y = x[1];
+        v.z = x[2];
+        v.w = x[3];
+    } else {
+        uint32_t wd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+            wd[q] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        v.x = wd[0];
+        v.y = wd[1];
+        v.z = wd[2];
+        v.w = wd[3];
+    }
+    return v;
+}
+
 constexpr int XS_MAXCH = 8;   // chunks of V*threads outputs per row handled by one thread
+// BF16 storage: 8-cell chunks, so 2 chunks per thread cover 4096 columns (fewer accumulator registers)
+template <typename S>
+__host__ __device__ constexpr int maxch_of() { return std::is_same<S, bf16>::value ? 2 : XS_MAXCH; }
 
 // ============================================================================ x-shift
-template <typename T, int A, bool PERIODIC>
-__device__ __forceinline__ void xshift_chunk(const T* __restrict__ rowbuf, int e, const T (&w)[NTAP],
-                                             int i, int k, int Nx, T g, T d, T (&out)[VecOf<T>::V])
+template <typename S, int A, bool PERIODIC, typename T = typename VecOf<S>::T>
+__device__ __forceinline__ void xshift_chunk(const S* __restrict__ rowbuf, int e, const T (&w)[NTAP],
+                                             int i, int k, int Nx, T g, T d, T (&out)[VecOf<S>::V])
 {
-    constexpr int V = VecOf<T>::V, W = VecOf<T>::W;
-    using vec = typename VecOf<T>::vec;
+    constexpr int V = VecOf<S>::V, W = VecOf<S>::W;
+    using vec = typename VecOf<S>::vec;
     T x[W];
     const vec* p = reinterpret_cast<const vec*>(rowbuf + e);
 #pragma unroll
-    for (int q = 0; q < W / V; ++q) {
-        vec v = p[q];
-        if constexpr (V == 2) {
-            x[2 * q] = v.x;
-            x[2 * q + 1] = v.y;
-        } else {
-            x[4 * q] = v.x;
-            x[4 * q + 1] = v.y;
-            x[4 * q + 2] = v.z;
-            x[4 * q + 3] = v.w;
-        }
-    }
+    for (int q = 0; q < W / V; ++q) unpack<S>(p[q], x + q * V);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         T acc = w[0] * x[A + v];
@@ -76,14 +144,14 @@ __device__ __forceinline__ void xshift_chunk(const T* __restrict__ rowbuf, int e
     (void)i;
 }
 
-template <typename T, int A, bool PERIODIC>
-__device__ __forceinline__ void xshift_row(const T* __restrict__ rowbuf, T* __restrict__ orow,
+template <typename S, int A, bool PERIODIC, typename T = typename VecOf<S>::T>
+__device__ __forceinline__ void xshift_row(const S* __restrict__ rowbuf, S* __restrict__ orow,
                                            const T (&w)[NTAP], int n0, int Nx, T g, T d, int nthreads,
-                                           typename VecOf<T>::acc (&colacc)[XS_MAXCH][VecOf<T>::V],
-                                           typename VecOf<T>::acc& rowsum)
+                                           typename VecOf<S>::acc (&colacc)[maxch_of<S>()][VecOf<S>::V],
+                                           typename VecOf<S>::acc& rowsum)
 {
-    constexpr int V = VecOf<T>::V;
-    using vec = typename VecOf<T>::vec;
+    constexpr int V = VecOf<S>::V;
+    using vec = typename VecOf<S>::vec;
     const int tid = threadIdx.x;
     int base;   // window start of output 0 (aligned down by A)
     if constexpr (PERIODIC) {
@@ -93,7 +161,7 @@ __device__ __forceinline__ void xshift_row(const T* __restrict__ rowbuf, T* __re
         base = n0 - 4 - A;
     }
 #pragma unroll
-    for (int c = 0; c < XS_MAXCH; ++c) {
+    for (int c = 0; c < maxch_of<S>(); ++c) {
         const int i = V * (tid + c * nthreads);
         if (i < Nx) {
             int e = i + base;
@@ -101,88 +169,82 @@ __device__ __forceinline__ void xshift_row(const T* __restrict__ rowbuf, T* __re
                 if (e >= Nx) e -= Nx;
             }
             T out[V];
-            xshift_chunk<T, A, PERIODIC>(rowbuf, e, w, i, i + n0, Nx, g, d, out);
-            vec o;
-            if constexpr (V == 2) {
-                o.x = out[0];
-                o.y = out[1];
-            } else {
-                o.x = out[0];
-                o.y = out[1];
-                o.z = out[2];
-                o.w = out[3];
-            }
+            xshift_chunk<S, A, PERIODIC>(rowbuf, e, w, i, i + n0, Nx, g, d, out);
+            const vec o = pack<S>(out);
             *reinterpret_cast<vec*>(orow + i) = o;
+            T stored[V];   // the column sums are those of the stored values
+            unpack<S>(o, stored);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                colacc[c][v] += out[v];
-                rowsum += out[v];
+                colacc[c][v] += stored[v];
+                rowsum += stored[v];
             }
         }
     }
 }
 
-template <typename T, bool PERIODIC, bool KIN>
+template <typename S, bool PERIODIC, bool KIN>
 __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
 {
-    constexpr int V = VecOf<T>::V;
-    using acc_t = typename VecOf<T>::acc;
+    using T = typename VecOf<S>::T;
+    constexpr int V = VecOf<S>::V;
+    using acc_t = typename VecOf<S>::acc;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    T* bufs = reinterpret_cast<T*>(smem_raw + 128);
+    S* bufs = reinterpret_cast<S*>(smem_raw + 128);
     __shared__ double red[32];
 
-    const T* __restrict__ fin = static_cast<const T*>(a.fin);
-    T* __restrict__ fout = static_cast<T*>(a.fout);
-    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, S = a.stages;
+    const S* __restrict__ fin = static_cast<const S*>(a.fin);
+    S* __restrict__ fout = static_cast<S*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, NS = a.stages;
     const int stride = Nx + 2 * PAD;
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int G = a.ctas > 0 ? a.ctas : (int)gridDim.x;
     const T* __restrict__ wrow = static_cast<const T*>(a.w);
     const T* __restrict__ gdrow = static_cast<const T*>(a.gd);
-    const uint32_t row_bytes = (uint32_t)(Nx * sizeof(T));
+    const uint32_t row_bytes = (uint32_t)(Nx * sizeof(S));
     const bool use_rec = a.rec != nullptr;
-    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 16u * (uint32_t)sizeof(T) : 0u) + (use_rec ? XREC_BYTES : 0u);
-    unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)S * stride);
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 16u * (uint32_t)sizeof(S) : 0u) + (use_rec ? XREC_BYTES : 0u);
+    unsigned char* recs = reinterpret_cast<unsigned char*>(bufs + (size_t)NS * stride);
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
     if constexpr (!PERIODIC) {
         // zero halos of every stage (never touched by the copies)
-        for (int s = 0; s < S; ++s) {
-            T* b = bufs + (size_t)s * stride;
+        for (int s = 0; s < NS; ++s) {
+            S* b = bufs + (size_t)s * stride;
             for (int e = tid; e < PAD; e += nthreads) {
-                b[e] = T(0);
-                b[PAD + Nx + e] = T(0);
+                b[e] = from_math<S>(T(0));
+                b[PAD + Nx + e] = from_math<S>(T(0));
             }
         }
     }
     __syncthreads();
 
     auto issue = [&](int s, int r) {
-        T* dst = bufs + (size_t)s * stride + PAD;
-        const T* src = fin + (size_t)r * Nx;
+        S* dst = bufs + (size_t)s * stride + PAD;
+        const S* src = fin + (size_t)r * Nx;
         mbar_arrive_expect_tx(&bars[s], tx_bytes);
         bulk_g2s(dst, src, row_bytes, &bars[s]);
-        if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 16u * (uint32_t)sizeof(T), &bars[s]);
+        if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 16u * (uint32_t)sizeof(S), &bars[s]);
         if (use_rec)
             bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
                      XREC_BYTES, &bars[s]);
     };
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < NS; ++s) {
             const int r = blockIdx.x + s * G;
             if (r < Np) issue(s, r);
         }
     }
 
-    acc_t colacc[XS_MAXCH][V];
+    acc_t colacc[maxch_of<S>()][V];
 #pragma unroll
-    for (int c = 0; c < XS_MAXCH; ++c)
+    for (int c = 0; c < maxch_of<S>(); ++c)
 #pragma unroll
         for (int v = 0; v < V; ++v) colacc[c][v] = acc_t(0);
     double kin = 0.0;
@@ -191,8 +253,8 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     int r = blockIdx.x;
     bool failed = false;
     for (; r < Np; r += G, ++it) {
-        const int s = it % S;
-        const uint32_t parity = (uint32_t)((it / S) & 1);
+        const int s = it % NS;
+        const uint32_t parity = (uint32_t)((it / NS) & 1);
         const bool ok = mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS);
         acc_t rowsum = acc_t(0);
         if (ok) {
@@ -217,20 +279,33 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
                     d = gdrow[Np + r];
                 }
             }
-            const T* rowbuf = bufs + (size_t)s * stride + PAD;
-            T* orow = fout + (size_t)r * Nx;
+            const S* rowbuf = bufs + (size_t)s * stride + PAD;
+            S* orow = fout + (size_t)r * Nx;
             const int A = (n0 - 4) & (V - 1);
+#define VL_ROW(AA) xshift_row<S, AA, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum)
             if constexpr (V == 2) {
-                if (A == 0) xshift_row<T, 0, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum);
-                else        xshift_row<T, 1, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum);
+                if (A == 0) VL_ROW(0);
+                else VL_ROW(1);
+            } else if constexpr (V == 4) {
+                switch (A) {
+                    case 0: VL_ROW(0); break;
+                    case 1: VL_ROW(1); break;
+                    case 2: VL_ROW(2); break;
+                    default: VL_ROW(3); break;
+                }
             } else {
                 switch (A) {
-                    case 0: xshift_row<T, 0, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
-                    case 1: xshift_row<T, 1, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
-                    case 2: xshift_row<T, 2, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
-                    default: xshift_row<T, 3, PERIODIC>(rowbuf, orow, w, n0, Nx, g, d, nthreads, colacc, rowsum); break;
+                    case 0: VL_ROW(0); break;
+                    case 1: VL_ROW(1); break;
+                    case 2: VL_ROW(2); break;
+                    case 3: VL_ROW(3); break;
+                    case 4: VL_ROW(4); break;
+                    case 5: VL_ROW(5); break;
+                    case 6: VL_ROW(6); break;
+                    default: VL_ROW(7); break;
                 }
             }
+#undef VL_ROW
             if constexpr (KIN) {
                 const double pj = a.pmin + (double)r * a.dp;
                 kin += 0.5 * pj * pj * (double)rowsum;
@@ -241,7 +316,7 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
             break;
         }
         if (tid == 0) {
-            const int rn = r + S * G;
+            const int rn = r + NS * G;
             if (rn < Np) {
                 fence_proxy_async_smem();
                 issue(s, rn);
@@ -253,11 +328,11 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
         // Record the failure and wait (bounded) for this CTA's copies still in flight.
         if (tid == 0) {
             atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
-            for (int k = 0; k < S; ++k) {
+            for (int k = 0; k < NS; ++k) {
                 const int rr = r + k * G;
                 if (rr >= Np) break;
                 const int itk = it + k;
-                mbar_wait_bounded(&bars[itk % S], (uint32_t)((itk / S) & 1), WAIT_LIMIT_NS);
+                mbar_wait_bounded(&bars[itk % NS], (uint32_t)((itk / NS) & 1), WAIT_LIMIT_NS);
             }
         }
         __syncthreads();
@@ -267,7 +342,7 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     if (a.colacc) {
         // exact fixed-point column sums, added across CTAs (order-free)
 #pragma unroll
-        for (int c = 0; c < XS_MAXCH; ++c) {
+        for (int c = 0; c < maxch_of<S>(); ++c) {
             const int i = V * (tid + c * nthreads);
             if (i < Nx) {
 #pragma unroll
@@ -282,7 +357,7 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll
-        for (int c = 0; c < XS_MAXCH; ++c) {
+        for (int c = 0; c < maxch_of<S>(); ++c) {
             const int i = V * (tid + c * nthreads);
             if (i < Nx) {
 #pragma unroll
@@ -304,10 +379,10 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     }
 }
 
-template <typename T, bool PERIODIC, bool KIN>
+template <typename S, bool PERIODIC, bool KIN>
 __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
 {
-    xshift_body<T, PERIODIC, KIN>(a);
+    xshift_body<S, PERIODIC, KIN>(a);
 }
 
 // Batched form: blockIdx.y selects the grid (slot); args[slot * 2 + ver[slot]] are its arguments
@@ -325,7 +400,7 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_batch_kernel(const X
 int xshift_max_cols(int elem_bytes, int threads)
 {
     const int V = 16 / elem_bytes;
-    return V * threads * XS_MAXCH;
+    return V * threads * (elem_bytes == 2 ? maxch_of<bf16>() : XS_MAXCH);
 }
 
 size_t xshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
@@ -333,11 +408,11 @@ size_t xshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
     return 256 + (size_t)stages * ((size_t)(Nx + 2 * pad) * (size_t)elem_bytes + XREC_BYTES);
 }
 
-template <typename T, bool P, bool K>
+template <typename S, bool P, bool K>
 static cudaError_t launch_x(int grid, int threads, const XShiftArgs& a, cudaStream_t st)
 {
-    const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, (int)sizeof(T));
-    xshift_kernel<T, P, K><<<grid, threads, smem, st>>>(a);
+    const size_t smem = xshift_smem_bytes(a.Nx, a.pad, a.stages, (int)sizeof(S));
+    xshift_kernel<S, P, K><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -350,6 +425,12 @@ cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int
         return kin ? launch_x<double, false, true>(grid, threads, a, st)
                    : launch_x<double, false, false>(grid, threads, a, st);
     }
+    if (elem_bytes == 2) {
+        if (periodic) return kin ? launch_x<bf16, true, true>(grid, threads, a, st)
+                                 : launch_x<bf16, true, false>(grid, threads, a, st);
+        return kin ? launch_x<bf16, false, true>(grid, threads, a, st)
+                   : launch_x<bf16, false, false>(grid, threads, a, st);
+    }
     if (periodic) return kin ? launch_x<float, true, true>(grid, threads, a, st)
                              : launch_x<float, true, false>(grid, threads, a, st);
     return kin ? launch_x<float, false, true>(grid, threads, a, st)
@@ -357,17 +438,18 @@ cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int
 }
 
 // ============================================================================ p-shift
-template <typename T, bool PPER>
+template <typename S, bool PPER>
 __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const PShiftArgs& a)
 {
+    using T = typename VecOf<S>::T;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    T* bufs = reinterpret_cast<T*>(smem_raw + 128);
+    S* bufs = reinterpret_cast<S*>(smem_raw + 128);
     constexpr int BUF = PS_RB * PS_TW;
 
-    const T* __restrict__ fin = static_cast<const T*>(a.fin);
-    T* __restrict__ fout = static_cast<T*>(a.fout);
+    const S* __restrict__ fin = static_cast<const S*>(a.fin);
+    S* __restrict__ fout = static_cast<S*>(a.fout);
     const T* __restrict__ wcol = static_cast<const T*>(a.w);
     const T* __restrict__ gdcol = static_cast<const T*>(a.gd);
     const int Nx = a.Nx, Np = a.Np;
@@ -388,7 +470,7 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
     // with no bytes when the tile takes the direct-load path).
     auto issue = [&](int b, const TileWin& t) {
         if (t.smem_ok) {
-            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(T)));
+            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(S)));
             for (int q = 0; q < t.nb; ++q)
                 tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap_ptr, t.i0, t.r0 + q * PS_BH, &bars[b]);
         } else {
@@ -437,14 +519,14 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
             const int jb = t.j0 + grp * PS_RPT;     // first output row of this thread
             T x[PS_RPT + 9];
             if (t.smem_ok) {
-                const T* buf = bufs + (size_t)b * BUF;
+                const S* buf = bufs + (size_t)b * BUF;
                 const int base = jb + n0_i - 4 - t.r0;
 #pragma unroll
-                for (int u = 0; u < PS_RPT + 9; ++u) x[u] = buf[(base + u) * PS_TW + lane];
+                for (int u = 0; u < PS_RPT + 9; ++u) x[u] = to_math(buf[(base + u) * PS_TW + lane]);
             } else {
 #pragma unroll
                 for (int u = 0; u < PS_RPT + 9; ++u)
-                    x[u] = colvalid ? gload_p<T, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : T(0);
+                    x[u] = colvalid ? to_math(gload_p<S, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np)) : T(0);
             }
 #pragma unroll
             for (int rr = 0; rr < PS_RPT; ++rr) {
@@ -456,7 +538,7 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
                     const int kk = j + n0_i;
                     if (kk < 0 || kk >= Np - 1) acc = edge_fix(acc, &x[rr], kk, Np, g, d);
                 }
-                if (colvalid && j < Np) fout[(size_t)j * Nx + i] = acc;
+                if (colvalid && j < Np) fout[(size_t)j * Nx + i] = from_math<S>(acc);
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -472,10 +554,10 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
     }
 }
 
-template <typename T, bool PPER>
+template <typename S, bool PPER>
 __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
 {
-    pshift_body<T, PPER>(&tmap, a);
+    pshift_body<S, PPER>(&tmap, a);
 }
 
 // Batched form: tensor maps and arguments of each slot, per buffer parity, in global memory.
@@ -496,11 +578,11 @@ size_t pshift_smem_bytes(int elem_bytes)
     return 256 + 2 * (size_t)PS_RB * PS_TW * (size_t)elem_bytes;
 }
 
-template <typename T, bool PPER>
+template <typename S, bool PPER>
 static cudaError_t launch_p(int grid, const CUtensorMap* tmap, const PShiftArgs& a, cudaStream_t st)
 {
-    const size_t smem = pshift_smem_bytes((int)sizeof(T));
-    pshift_kernel<T, PPER><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a);
+    const size_t smem = pshift_smem_bytes((int)sizeof(S));
+    pshift_kernel<S, PPER><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a);
     return cudaGetLastError();
 }
 
@@ -508,6 +590,7 @@ cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUten
                           cudaStream_t st)
 {
     if (elem_bytes == 8) return p_periodic ? launch_p<double, true>(grid, tmap, a, st) : launch_p<double, false>(grid, tmap, a, st);
+    if (elem_bytes == 2) return p_periodic ? launch_p<bf16, true>(grid, tmap, a, st) : launch_p<bf16, false>(grid, tmap, a, st);
     return p_periodic ? launch_p<float, true>(grid, tmap, a, st) : launch_p<float, false>(grid, tmap, a, st);
 }
 
@@ -557,6 +640,12 @@ cudaError_t set_kernel_attributes(int max_smem)
     VL_ATTR((xshift_batch_kernel<float, false, true>));
     VL_ATTR((xshift_batch_kernel<float, false, false>));
     VL_ATTR((pshift_batch_kernel<float, false>));
+    VL_ATTR((xshift_kernel<bf16, true, true>));
+    VL_ATTR((xshift_kernel<bf16, true, false>));
+    VL_ATTR((xshift_kernel<bf16, false, true>));
+    VL_ATTR((xshift_kernel<bf16, false, false>));
+    VL_ATTR((pshift_kernel<bf16, true>));
+    VL_ATTR((pshift_kernel<bf16, false>));
 #undef VL_ATTR
     return e;
 }
@@ -566,6 +655,9 @@ cudaError_t xshift_occupancy(int elem_bytes, bool periodic, int threads, size_t 
     if (elem_bytes == 8)
         return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<double, true, true>, threads, smem)
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<double, false, true>, threads, smem);
+    if (elem_bytes == 2)
+        return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<bf16, true, true>, threads, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<bf16, false, true>, threads, smem);
     return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<float, true, true>, threads, smem)
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_kernel<float, false, true>, threads, smem);
 }
@@ -575,6 +667,8 @@ cudaError_t pshift_occupancy(int elem_bytes, int* blocks)
     const size_t smem = pshift_smem_bytes(elem_bytes);
     if (elem_bytes == 8)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<double, false>, PS_TW * PS_RG, smem);
+    if (elem_bytes == 2)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<bf16, false>, PS_TW * PS_RG, smem);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<float, false>, PS_TW * PS_RG, smem);
 }
 

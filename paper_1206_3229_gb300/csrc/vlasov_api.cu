@@ -62,6 +62,7 @@ constexpr int ALIGN_N = 8;
 
 struct vlasov_sim {
     int model = 0, Nx = 0, Np = 0, prec = 0, esz = 8;
+    int msz = 8;                // bytes of the filter/parameter type: 8 (FP64 modes) or 4 (FP32, BF16 storage)
     bool xper = true, pper = false;
     double xmin = 0, xmax = 0, pmin = 0, pmax = 0, dx = 0, dp = 0, dt = 0, eps = 0, G = 1;
     cudaStream_t st = nullptr;
@@ -217,7 +218,7 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
         CU_TRY(cudaMemcpyAsync(e->wf, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
     }
-    if (s->esz == 8) {
+    if (s->msz == 8) {
         CU_TRY(cudaMemcpyAsync(p.w, w.data(), 8 * w.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaMemcpyAsync(p.gd, gd.data(), 8 * gd.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
@@ -239,7 +240,9 @@ int make_tmap(vlasov_sim* s, int b)
     cuuint32_t box[2] = {(cuuint32_t)PS_TW, (cuuint32_t)PS_BH};
     cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt = s->fx ? CU_TENSOR_MAP_DATA_TYPE_INT64
-                                         : (s->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+                                   : s->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : s->esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = enc(&s->tmap[b], dt, 2,
                      s->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -276,7 +279,7 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     // stores), hardware FP64 adds exact sums atomically, FP32 writes FP64 partial rows.
     const bool part64 = s->fx || s->emul;
     const bool atomics = s->esz == 8 && !part64;
-    a.colpart = (reduce && s->esz == 4) ? s->colpart : nullptr;
+    a.colpart = (reduce && s->esz <= 4) ? s->colpart : nullptr;
     a.colacc = (reduce && atomics) ? s->colacc : nullptr;
     a.colpart64 = (reduce && part64 && !s->hmf_cta) ? reinterpret_cast<long long*>(s->colpart) : nullptr;
     a.ctapart = (reduce && s->hmf_cta) ? s->ctapart : nullptr;
@@ -303,6 +306,28 @@ PShiftArgs pargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.gd = p.gd;
     a.err = s->err;
     return a;
+}
+
+// Cells a chunk's window reaches past |n0| on a zero-outside row: 4 taps + (V - 1) alignment slack,
+// V = 16 bytes / cell, at least the 8 the 8-byte and FP32 kernels always had.
+int xhalo_extra(int esz) { return esz == 2 ? 12 : 8; }
+
+// bf16 of a double, rounded to nearest even in one step (as the device's double-to-bf16
+// conversion): the value is rounded to 8 significant bits (or to the 2^-133 grid of the smallest
+// bf16), which an FP32 holds exactly, and the bf16 is that FP32's high half.
+uint16_t bf16_bits(double x)
+{
+    float r = (float)x;   // zero, non-finite, or overflow: the FP32 value decides
+    if (x != 0.0 && std::isfinite(x) && std::fabs(x) < 3.0e38) {
+        int e = 0;
+        std::frexp(x, &e);                                  // |x| in [2^(e-1), 2^e)
+        const int ue = std::max(e - 8, -133);               // exponent of the last kept bit
+        const double q = std::nearbyint(std::ldexp(x, -ue));   // default rounding: to nearest even
+        r = (float)std::ldexp(q, ue);
+    }
+    uint32_t u;
+    std::memcpy(&u, &r, 4);
+    return (uint16_t)(u >> 16);
 }
 
 int ceil_log2(double v)
@@ -457,13 +482,13 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int 
         CU_TRY(launch_pparams_hmf_cta(a, s->st));
         return VLASOV_OK;
     }
-    CU_TRY(launch_pparams(s->esz, a, s->st));
+    CU_TRY(launch_pparams(s->msz, a, s->st));
     return VLASOV_OK;
 }
 
 int launch_force_params(vlasov_sim* s, double* Fout)
 {
-    if (s->model == VLASOV_RING) CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
+    if (s->model == VLASOV_RING) CU_TRY(launch_ring(s->msz, ringargs(s, false), s->st));
     return launch_pparams_only(s, Fout);
 }
 
@@ -506,7 +531,7 @@ int enq_force_p(vlasov_sim* s, int c, int ctas, Marks* marks)
         CU_TRY(launch_colreduce(crargs(s, ctas, false, false), s->crgrid, s->st));
         MARK();
         if (s->model == VLASOV_RING) {
-            CU_TRY(launch_ring(s->esz, ringargs(s, false), s->st));
+            CU_TRY(launch_ring(s->msz, ringargs(s, false), s->st));
             MARK();
         }
         int rc = launch_pparams_only(s, nullptr);
@@ -532,7 +557,7 @@ int enq_moments(vlasov_sim* s, int ctas, bool fused_m, Marks* marks)
     }
     MARK();
     if (s->model == VLASOV_RING) {
-        CU_TRY(launch_ring(s->esz, ringargs(s, true), s->st));
+        CU_TRY(launch_ring(s->msz, ringargs(s, true), s->st));
         MARK();
     }
     return VLASOV_OK;
@@ -678,9 +703,9 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     if (!d) return fail(VLASOV_EINVAL, "domain is NULL");
     if (model < VLASOV_HMF || model > VLASOV_FREE) return fail(VLASOV_EINVAL, "unknown model %d", model);
     if (d->precision != VLASOV_F64 && d->precision != VLASOV_F32 && d->precision != VLASOV_F64_NATIVE &&
-        d->precision != VLASOV_FX64)
+        d->precision != VLASOV_FX64 && d->precision != VLASOV_BF16)
         return fail(VLASOV_EINVAL, "unknown precision %d", d->precision);
-    const int esz = d->precision == VLASOV_F32 ? 4 : 8;
+    const int esz = d->precision == VLASOV_F32 ? 4 : d->precision == VLASOV_BF16 ? 2 : 8;
     if (Nx < 16 || Np < 16 || Nx % ALIGN_N || Np % ALIGN_N)
         return fail(VLASOV_EINVAL, "Nx=%d, Np=%d: both must be multiples of %d and >= 16", Nx, Np, ALIGN_N);
     if (Nx > xshift_max_cols(esz, XS_THREADS_MIN))
@@ -697,6 +722,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     s->Np = Np;
     s->prec = d->precision;
     s->esz = esz;
+    s->msz = esz == 8 ? 8 : 4;
     s->emul = d->precision == VLASOV_F64;
     s->fx = d->precision == VLASOV_FX64;
     s->xper = d->x_periodic != 0;
@@ -757,9 +783,9 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
             srow[j] = p * cx;
         }
     }
-    TRY(alloc_params(s->xp, Np, esz));
-    TRY(alloc_params(s->pp, Nx, esz));
-    TRY(alloc_params(s->sp, std::max(Nx, Np), esz));
+    TRY(alloc_params(s->xp, Np, s->msz));
+    TRY(alloc_params(s->pp, Nx, s->msz));
+    TRY(alloc_params(s->sp, std::max(Nx, Np), s->msz));
     if (s->emul || s->fx) {
         TRY(alloc_emul(s->xe, Np));
         TRY(alloc_emul(s->pe, Nx));
@@ -772,7 +798,9 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
 
     // x-shift launch shape: whole rows staged per CTA.
     s->xthreads = XS_THREADS_MIN;
-    s->xpad = s->xper ? 16 : ((max_n0 + 8 + 15) / 16) * 16;
+    // zero halo of non-periodic rows: the window of a chunk reaches |n0| + 4 + (V - 1) cells past the
+    // row, V = 16 bytes / cell (8 for BF16 storage)
+    s->xpad = s->xper ? 16 : ((max_n0 + xhalo_extra(esz) + 15) / 16) * 16;
     const size_t row_bytes = (size_t)(Nx + 2 * s->xpad) * esz + XREC_BYTES;
     const size_t smem_budget = (size_t)max_optin - 2048;
     s->xstages = (int)std::min<size_t>(4, (smem_budget - 256) / row_bytes);
@@ -884,15 +912,15 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         CTRY(cudaMalloc(&s->sinfx, sizeof(long long) * Nx));
         CTRY(cudaMalloc(&s->cos50, sizeof(long long) * Nx));
         CTRY(cudaMalloc(&s->sin50, sizeof(long long) * Nx));
-        CTRY(cudaMalloc(&s->ringdV, (size_t)esz * Nx));
-        CTRY(cudaMalloc(&s->ringV, (size_t)esz * Nx));
+        CTRY(cudaMalloc(&s->ringdV, (size_t)s->msz * Nx));
+        CTRY(cudaMalloc(&s->ringV, (size_t)s->msz * Nx));
         CTRY(cudaMemcpyAsync(s->costab, c.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->sintab, sn.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->cosfx, cfx.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->sinfx, sfx.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->cos50, c50.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
         CTRY(cudaMemcpyAsync(s->sin50, s50.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
-        if (esz == 8) {
+        if (s->msz == 8) {
             CTRY(cudaMemcpyAsync(s->ringdV, dV.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
             CTRY(cudaMemcpyAsync(s->ringV, V.data(), sizeof(double) * Nx, cudaMemcpyHostToDevice, s->st));
             CTRY(cudaStreamSynchronize(s->st));
@@ -926,9 +954,17 @@ int vlasov_set_f(vlasov_sim* s, const double* host_f)
     for (size_t k = 0; k < cells; ++k) mx = std::max(mx, std::fabs(host_f[k]));
     if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "f holds a non-finite value");
     update_scales(s, mx);
-    std::vector<float> tmp(cells);
-    for (size_t k = 0; k < cells; ++k) tmp[k] = (float)host_f[k];
-    CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 4, cudaMemcpyHostToDevice, s->st));
+    if (s->esz == 2) {
+        std::vector<uint16_t> tmp(cells);
+        for (size_t k = 0; k < cells; ++k) tmp[k] = bf16_bits(host_f[k]);
+        CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 2, cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));   // tmp is released on return
+    } else {
+        std::vector<float> tmp(cells);
+        for (size_t k = 0; k < cells; ++k) tmp[k] = (float)host_f[k];
+        CU_TRY(cudaMemcpyAsync(s->f[s->cur], tmp.data(), cells * 4, cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+    }
     CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
     CU_TRY(cudaStreamSynchronize(s->st));
     s->read_step = 0;
@@ -969,6 +1005,16 @@ int vlasov_get_f(vlasov_sim* s, double* host_f)
     } else if (s->esz == 8) {
         CU_TRY(cudaMemcpyAsync(host_f, s->f[s->cur], cells * 8, cudaMemcpyDeviceToHost, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
+    } else if (s->esz == 2) {
+        std::vector<uint16_t> tmp(cells);
+        CU_TRY(cudaMemcpyAsync(tmp.data(), s->f[s->cur], cells * 2, cudaMemcpyDeviceToHost, s->st));
+        CU_TRY(cudaStreamSynchronize(s->st));
+        for (size_t k = 0; k < cells; ++k) {
+            const uint32_t u = (uint32_t)tmp[k] << 16;   // a bf16 is the high half of an FP32
+            float v;
+            std::memcpy(&v, &u, 4);
+            host_f[k] = (double)v;
+        }
     } else {
         std::vector<float> tmp(cells);
         CU_TRY(cudaMemcpyAsync(tmp.data(), s->f[s->cur], cells * 4, cudaMemcpyDeviceToHost, s->st));
@@ -1052,9 +1098,9 @@ int vlasov_substep(vlasov_sim* s, int axis, const double* host_disp)
         int rc = upload_params(s, s->sp, host_disp, s->Np, &mx, &s->se, s->srec);
         if (rc) return rc;
         XShiftArgs a = xargs(s, s->f[c], s->f[o], s->sp, false, false, s->srec);
-        if (!s->xper && mx + 8 > s->xpad) {
+        if (!s->xper && mx + xhalo_extra(s->esz) > s->xpad) {
             // wider zero halo for this call: the staged row grows, fewer rows in flight
-            a.pad = ((mx + 8 + 15) / 16) * 16;
+            a.pad = ((mx + xhalo_extra(s->esz) + 15) / 16) * 16;
             int max_optin = 0;
             CU_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
             const size_t row_bytes = (size_t)(s->Nx + 2 * a.pad) * s->esz + XREC_BYTES;
@@ -1093,7 +1139,7 @@ int vlasov_casimirs(vlasov_sim* s, double* entropy, double* l2)
     if (!s) return fail(VLASOV_EINVAL, "NULL handle");
     if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_casimirs before vlasov_set_f");
     const size_t cells = (size_t)s->Nx * s->Np;
-    const int kind = s->fx ? 0 : (s->esz == 8 ? 1 : 2);
+    const int kind = s->fx ? 0 : (s->esz == 8 ? 1 : s->esz == 4 ? 2 : 3);
     const double unit = s->fx ? std::ldexp(1.0, s->Ef - FX_FRAC) : 1.0;
     // scratch: the column partial rows (at least 2 * CAS_BLOCKS + 2 doubles)
     double* part = s->colpart;

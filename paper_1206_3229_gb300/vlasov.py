@@ -15,9 +15,9 @@ from . import build as _build
 from .inputs import Workload
 
 HMF, RING, SHEET, FREE = 0, 1, 2, 3
-F64, F32, F64_NATIVE, FX64 = 0, 1, 2, 3
+F64, F32, F64_NATIVE, FX64, BF16 = 0, 1, 2, 3, 4
 MODELS = {"hmf": HMF, "ring": RING, "sheet": SHEET, "free": FREE}
-PRECISIONS = {"f64": F64, "f32": F32, "f64_native": F64_NATIVE, "fx64": FX64}
+PRECISIONS = {"f64": F64, "f32": F32, "f64_native": F64_NATIVE, "fx64": FX64, "bf16": BF16}
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
