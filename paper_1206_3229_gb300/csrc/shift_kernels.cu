@@ -354,6 +354,21 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
                 }
             }
         }
+    } else if (a.colpart64) {
+        // exact fixed-point partial rows (units 2^-k_col): the reduction adds them with integer
+        // instructions, not a chain of FP64 additions per column
+        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < maxch_of<S>(); ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if constexpr (sizeof(acc_t) == 8) cp[i + v] = (long long)fx128_from_f64((double)colacc[c][v], a.k_col);
+                    else cp[i + v] = (long long)fx128_from_f32((float)colacc[c][v], a.k_col);
+                }
+            }
+        }
     } else if (a.colpart) {
         double* cp = a.colpart + (size_t)blockIdx.x * Nx;
 #pragma unroll

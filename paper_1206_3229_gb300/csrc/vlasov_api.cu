@@ -274,12 +274,13 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.n0 = p.n0;
     a.w = p.w;
     a.gd = p.gd;
-    // Column sums of the output: the FX64 / emulated-FP64 sweeps write exact int64 partial rows
-    // (one per CTA; 4096 atomics per CTA at the end of a sweep cost more than these 10 MB of
-    // stores), hardware FP64 adds exact sums atomically, FP32 writes FP64 partial rows.
-    const bool part64 = s->fx || s->emul;
+    // Column sums of the output: every sweep but the hardware-FP64 one writes exact int64 partial
+    // rows (one per CTA; 4096 atomics per CTA at the end of a sweep cost more than these 10 MB of
+    // stores, and FP64 partial rows would be added by slow dependent FP64 additions); hardware FP64
+    // adds exact sums atomically.
+    const bool part64 = s->fx || s->emul || s->esz <= 4;
     const bool atomics = s->esz == 8 && !part64;
-    a.colpart = (reduce && s->esz <= 4) ? s->colpart : nullptr;
+    a.colpart = nullptr;
     a.colacc = (reduce && atomics) ? s->colacc : nullptr;
     a.colpart64 = (reduce && part64 && !s->hmf_cta) ? reinterpret_cast<long long*>(s->colpart) : nullptr;
     a.ctapart = (reduce && s->hmf_cta) ? s->ctapart : nullptr;
@@ -404,7 +405,7 @@ cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs&
 ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments, bool from_acc = true, bool fused_m = false)
 {
     ColReduceArgs a;
-    const bool part64 = from_acc && (s->fx || s->emul);
+    const bool part64 = from_acc && (s->fx || s->emul || s->esz <= 4);
     a.colacc = (from_acc && s->esz == 8 && !part64) ? s->colacc : nullptr;
     a.colpart64 = part64 ? (fused_m ? s->colpart_m : reinterpret_cast<const long long*>(s->colpart)) : nullptr;
     a.colpart = s->colpart;
