@@ -560,6 +560,8 @@ __device__ __forceinline__ void pparams_fixed(const PParamsArgs& a, int i, doubl
     }
 }
 
+__device__ __forceinline__ void pparams_f32(const PParamsArgs& a, int i, double sigma);
+
 template <typename T>
 __device__ __forceinline__ void pparams_body(const PParamsArgs& a)
 {
@@ -572,10 +574,14 @@ __device__ __forceinline__ void pparams_body(const PParamsArgs& a)
     else F = a.Fin[i];
     if (a.Fout) a.Fout[i] = F;
     const double sigma = F * a.cp;
-    if constexpr (sizeof(T) == 8) {
-        pparams_fixed(a, i, sigma);
-        return;
-    }
+    if constexpr (sizeof(T) == 8) pparams_fixed(a, i, sigma);
+    else pparams_f32(a, i, sigma);
+}
+
+// FP32-class storage: the foot split in FP64, the ten weights in FP32.
+__device__ __forceinline__ void pparams_f32(const PParamsArgs& a, int i, double sigma)
+{
+    using T = float;
     const double ms = -sigma;
     const double fl = floor(ms);
     const double beta = ms - fl;
@@ -642,6 +648,7 @@ __device__ __forceinline__ void sum_ctaparts(const void* parts, int ctas, i128& 
 // HMF after the first x-shift: Mx, My from the per-CTA partials (the same exact integers in every
 // block), then F_i = -Mx sin x_i + My cos x_i and the p-shift parameters of the block's columns.
 constexpr int PPC_THREADS = 256;
+template <typename T>
 __global__ void __launch_bounds__(PPC_THREADS) pparams_hmf_cta_kernel(PParamsArgs a)
 {
     __shared__ i128 red4[128];
@@ -653,12 +660,15 @@ __global__ void __launch_bounds__(PPC_THREADS) pparams_hmf_cta_kernel(PParamsArg
     const double My = a.dxdp * fx128_to_f64(y, 101 - a.Ef);
     const double F = -Mx * a.sintab[i] + My * a.costab[i];
     if (a.Fout) a.Fout[i] = F;
-    pparams_fixed(a, i, F * a.cp);
+    if constexpr (sizeof(T) == 8) pparams_fixed(a, i, F * a.cp);
+    else pparams_f32(a, i, F * a.cp);
 }
 
-cudaError_t launch_pparams_hmf_cta(const PParamsArgs& a, cudaStream_t st)
+cudaError_t launch_pparams_hmf_cta(int elem_bytes, const PParamsArgs& a, cudaStream_t st)
 {
-    pparams_hmf_cta_kernel<<<(a.Nx + PPC_THREADS - 1) / PPC_THREADS, PPC_THREADS, 0, st>>>(a);
+    const int grid = (a.Nx + PPC_THREADS - 1) / PPC_THREADS;
+    if (elem_bytes == 8) pparams_hmf_cta_kernel<double><<<grid, PPC_THREADS, 0, st>>>(a);
+    else pparams_hmf_cta_kernel<float><<<grid, PPC_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -354,6 +354,33 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
                 }
             }
         }
+    } else if (a.ctapart) {
+        // HMF: this CTA's column sums t_i as integers in units 2^(Ef-51), then sum t_i and the
+        // 50-bit cos/sin-weighted sums (exact int128), three numbers per CTA instead of a row
+        i128 pm = 0, px = 0, py = 0, pz = 0;
+#pragma unroll
+        for (int c = 0; c < maxch_of<S>(); ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    long long t;
+                    if constexpr (sizeof(acc_t) == 8) t = (long long)fx128_from_f64((double)colacc[c][v], 51 - a.Ef);
+                    else t = (long long)fx128_from_f32((float)colacc[c][v], 51 - a.Ef);
+                    pm += (i128)t;
+                    px += (i128)__ldg(a.cos50 + i + v) * (i128)t;
+                    py += (i128)__ldg(a.sin50 + i + v) * (i128)t;
+                }
+            }
+        }
+        i128* scratch = reinterpret_cast<i128*>(bufs);   // the stages are free: every warp passed the last barrier
+        block_sum4_i128(pm, px, py, pz, scratch);
+        if (tid == 0) {
+            i128* cp = static_cast<i128*>(a.ctapart) + (size_t)blockIdx.x * 3;
+            cp[0] = pm;
+            cp[1] = px;
+            cp[2] = py;
+        }
     } else if (a.colpart64) {
         // exact fixed-point partial rows (units 2^-k_col): the reduction adds them with integer
         // instructions, not a chain of FP64 additions per column

@@ -286,6 +286,7 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.ctapart = (reduce && s->hmf_cta) ? s->ctapart : nullptr;
     a.cos50 = s->cos50;
     a.sin50 = s->sin50;
+    a.Ef = s->Ef;
     a.k_col = s->k_col;
     a.kinpart = kin ? s->kinpart : nullptr;
     a.kin128 = (kin && s->fx) ? s->kin128 : nullptr;
@@ -480,7 +481,7 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int 
         a.ctas = ctas > 0 ? ctas : s->xgrid;
         a.Ef = s->Ef;
         a.dxdp = s->dx * s->dp;
-        CU_TRY(launch_pparams_hmf_cta(a, s->st));
+        CU_TRY(launch_pparams_hmf_cta(s->msz, a, s->st));
         return VLASOV_OK;
     }
     CU_TRY(launch_pparams(s->msz, a, s->st));
@@ -860,9 +861,10 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         CTRY(cudaMalloc(&s->ctapart_m, 48 * (size_t)s->nctas));
         CTRY(cudaMalloc(&s->colpart_m, sizeof(long long) * (size_t)s->nctas * Nx));
     }
-    // HMF with FX64 storage needs no per-column density: the x-shifts hand over three exact
-    // numbers per CTA (bounded in int128 while Nx * Np <= 2^24)
-    s->hmf_cta = s->fx && model == VLASOV_HMF && (double)Nx * (double)Np <= 16777216.0;
+    // HMF with FX64 or BF16 storage needs no per-column density: the x-shifts hand over three exact
+    // numbers per CTA (bounded in int128 while Nx * Np <= 2^24).  (With FP32 storage the int128
+    // weighting of a CTA's 16 columns per thread measured slower than the integer partial rows.)
+    s->hmf_cta = (s->fx || esz == 2) && model == VLASOV_HMF && (double)Nx * (double)Np <= 16777216.0;
     CTRY(cudaMalloc(&s->colacc, sizeof(unsigned long long) * (size_t)Nx));
     CTRY(cudaMemsetAsync(s->colacc, 0, sizeof(unsigned long long) * (size_t)Nx, s->st));
     CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->nctas));

@@ -114,6 +114,7 @@ struct XShiftArgs {
     void* ctapart = nullptr;                 // or (HMF): [ctas][3] int128 per-CTA sum_i t_i, sum_i cos50_i t_i,
                                              // sum_i sin50_i t_i of the CTA's column sums t_i (units 2^(Ef-51))
     const long long* cos50 = nullptr;        //   round(cos x_i 2^50), round(sin x_i 2^50)
+    int Ef = 0;                              //   (FP32-class storage: the bound 2^Ef of those units)
     const long long* sin50 = nullptr;
     int k_col = 0;
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
@@ -302,7 +303,7 @@ cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PPa
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
 // HMF, 8-byte storage, from the x-shift's per-CTA partials: force and p-shift parameters
 // (pparams_hmf_cta), and the moments after the second x-shift (colreduce_cta, one block).
-cudaError_t launch_pparams_hmf_cta(const PParamsArgs& a, cudaStream_t st);
+cudaError_t launch_pparams_hmf_cta(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
 cudaError_t launch_colreduce_cta(const ColReduceArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);
