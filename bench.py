@@ -131,9 +131,17 @@ def cpu_oracle_timing(w: I.Workload, f0: np.ndarray, budget_s: float, max_steps:
     t2 = time.perf_counter()
     steps = 1 + more
     elapsed = t2 - t0
+    # the paper compares with a serial code: the same oracle on one core, one step
+    O.set_threads(1)
+    s0 = time.perf_counter()
+    O.run(g, f, 1, with_moments=True)
+    single = time.perf_counter() - s0
+    O.set_threads(cores)
     return {"value": w.cells * steps / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} full Strang step(s) of {w.name} ({w.nx}x{w.np}, FP64, moments each step) "
-                      f"in {elapsed:.2f} s"}
+                      f"in {elapsed:.2f} s",
+            "single_thread": {"value": w.cells / single, "unit": UNIT, "cores": 1,
+                              "sample": f"1 full Strang step of {w.name} on one core in {single:.2f} s"}}
 
 
 def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode: str = "fx64",
