@@ -373,9 +373,11 @@ cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColRedu
 // ============================================================================ ring force
 // F_i = -dx sum_k V'(((i-k) mod N) dx) rho_k, or after the last x-shift Phi_i = dx sum_k V(...) rho_k
 // and U = 1/2 dx sum_i rho_i Phi_i (exact int128 sum).  A block stages rho in shared memory in the
-// arithmetic type T (double for FP64 storage, float for FP32 storage) and produces RING_OUT outputs,
-// eight per warp, lanes striding over k.
-constexpr int RING_OUT = 64;
+// arithmetic type T (double for FP64 storage, float for FP32 storage), with the kernel table beside
+// it, and produces RING_OUT outputs, RING_OUT / 8 per warp, lanes striding over k.  Few outputs
+// per block spread the N^2 multiply-adds over every SM (FP64 ones run on the slow FP64 pipe).
+constexpr int RING_OUT = 16;
+constexpr int RING_OPW = RING_OUT / 8;
 
 template <typename T>
 __device__ __forceinline__ void ring_body(const RingArgs& a)
@@ -388,33 +390,37 @@ __device__ __forceinline__ void ring_body(const RingArgs& a)
     const int N = a.N;
     const int nblk = (N + RING_OUT - 1) / RING_OUT;
     if ((int)blockIdx.x >= nblk) return;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) rs[k] = (T)a.rho[k];
-    __syncthreads();
+    T* ks = rs + N;   // the kernel table V' (force) or V (potential) by index difference
     const T* __restrict__ ker = static_cast<const T*>(a.final_moments ? a.V : a.dV);
-    const int i0 = blockIdx.x * RING_OUT + wid * 8;
-    T acc[8];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        rs[k] = (T)a.rho[k];
+        ks[k] = ker[k];
+    }
+    __syncthreads();
+    const int i0 = blockIdx.x * RING_OUT + wid * RING_OPW;
+    T acc[RING_OPW];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = T(0);
-    int iq[8];
+    for (int q = 0; q < RING_OPW; ++q) acc[q] = T(0);
+    int iq[RING_OPW];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) iq[q] = (i0 + q < N) ? i0 + q : 0;   // outputs past N: dummy, unused
+    for (int q = 0; q < RING_OPW; ++q) iq[q] = (i0 + q < N) ? i0 + q : 0;   // outputs past N: dummy, unused
     for (int k = lane; k < N; k += 32) {
         const T r = rs[k];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < RING_OPW; ++q) {
             int m = iq[q] - k;          // in (-N, N)
             m += (m < 0) ? N : 0;
-            acc[q] = fma(ker[m], r, acc[q]);
+            acc[q] = fma(ks[m], r, acc[q]);
         }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < RING_OPW; ++q)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     i128 up = 0;
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < RING_OPW; ++q) {
             const int i = i0 + q;
             if (i < N) {
                 if (a.final_moments) up += fx128_from_f64(a.rho[i] * (a.dx * (double)acc[q]), a.k_pot);
@@ -473,19 +479,32 @@ __global__ void __launch_bounds__(256) ring_batch_kernel(const RingArgs* __restr
 
 int ring_blocks(int N) { return (N + RING_OUT - 1) / RING_OUT; }
 
+// The ring kernels stage rho and the kernel table: 2 N elements of shared memory (64 KB at N = 4096
+// in FP64).
+cudaError_t set_ring_attributes(int max_smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(ring_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ring_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ring_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ring_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return e;
+}
+
 cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st)
 {
     const dim3 grid(ring_blocks(max_n), slots);
-    if (elem_bytes == 8) ring_batch_kernel<double><<<grid, 256, (size_t)max_n * 8, st>>>(args);
-    else ring_batch_kernel<float><<<grid, 256, (size_t)max_n * 4, st>>>(args);
+    if (elem_bytes == 8) ring_batch_kernel<double><<<grid, 256, (size_t)max_n * 16, st>>>(args);
+    else ring_batch_kernel<float><<<grid, 256, (size_t)max_n * 8, st>>>(args);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st)
 {
     const int grid = ring_blocks(a.N);
-    if (elem_bytes == 8) ring_kernel<double><<<grid, 256, (size_t)a.N * 8, st>>>(a);
-    else ring_kernel<float><<<grid, 256, (size_t)a.N * 4, st>>>(a);
+    if (elem_bytes == 8) ring_kernel<double><<<grid, 256, (size_t)a.N * 16, st>>>(a);
+    else ring_kernel<float><<<grid, 256, (size_t)a.N * 8, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -736,6 +736,7 @@ int vlasov_batch_create_shaped(int slots, int max_n, long long mem_budget_bytes,
     BC(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     BC(set_kernel_attributes(optin - 1024));
     BC(set_kernel_attributes_fx(optin - 1024));
+    BC(set_ring_attributes(optin - 1024));
     BC(cudaMalloc(&b->arena.base, (size_t)mem_budget_bytes));
     b->arena.size = (size_t)mem_budget_bytes;
     b->arena.free_[0] = (size_t)mem_budget_bytes;

@@ -60,6 +60,28 @@ __device__ __forceinline__ long long fx_edge(const long long* X, const double* w
     return (long long)fx128_from_f64(out, FX_FRAC - Ef);
 }
 
+// The XF_V outputs of a chunk that touches a zero-outside row end, recomputed in FP64 (rare; kept
+// out of line so that its registers do not weigh on the filter loop).  Window element m (m = 0 at
+// f_{k-4} of the chunk's first output) is row[b0 + m] of a plain row, or of a padded row (PADDED:
+// 8-element lines 10 elements apart).  Returned by value, so that no caller array needs an address.
+struct FxOut {
+    long long v[XF_V];
+};
+__device__ __noinline__ FxOut fx_edge_chunk(const long long* row, int b0, bool padded, const XRec* rc, int k, int Nx,
+                                            double unit, int Ef)
+{
+    FxOut o;
+    for (int v = 0; v < XF_V; ++v) {
+        long long xw[NTAP];
+        for (int t = 0; t < NTAP; ++t) {
+            const int ee = b0 + v + t;
+            xw[t] = padded ? row[(ee >> 3) * 10 + (ee & 7)] : row[ee];
+        }
+        o.v[v] = fx_edge(xw, rc->w64, 1, k + v, Nx, rc->g64, rc->d64, unit, Ef);
+    }
+    return o;
+}
+
 // XF_V consecutive outputs of one x row from the staged fixed-point values f_{k-4-A} .. , read as
 // pairs: pair h at q[h] in a plain row, or (PADDED) at q[h + (Q + h) / 4] in a padded row whose
 // window starts at pair 4 m + Q (pair p at 16-byte slot p + p / 4, q = slot of the first pair).
@@ -325,12 +347,9 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                     if constexpr (!PERIODIC) {
                         const int k = i + n0;
                         if (k < 0 || k + XF_V - 1 >= Nx - 1) {
-                            const double g = rc->g64, d = rc->d64;
-                            const double* w64 = rc->w64;
-                            const size_t wst = 1;
+                            const FxOut o = fx_edge_chunk(rowbuf, e + A, false, rc, k, Nx, unit, em.Ef);
 #pragma unroll
-                            for (int v = 0; v < XF_V; ++v)
-                                out[v] = fx_edge(rowbuf + e + A + v, w64, wst, k + v, Nx, g, d, unit, em.Ef);
+                            for (int v = 0; v < XF_V; ++v) out[v] = o.v[v];
                         }
                     }
 #pragma unroll
@@ -521,15 +540,10 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
                 if constexpr (!PERIODIC) {
                     const int k = i + n0;
                     if (k < 0 || k + XF_V - 1 >= Nx - 1) {
-                        const long long* sbl = reinterpret_cast<const long long*>(sb);
-                        for (int v = 0; v < XF_V; ++v) {
-                            long long xw[NTAP];
-                            for (int t = 0; t < NTAP; ++t) {
-                                const int ee = PADR + e + A + v + t;
-                                xw[t] = sbl[(ee >> 3) * 10 + (ee & 7)];
-                            }
-                            out[v] = fx_edge(xw, rc->w64, 1, k + v, Nx, rc->g64, rc->d64, unit, em.Ef);
-                        }
+                        const FxOut o = fx_edge_chunk(reinterpret_cast<const long long*>(sb), PADR + e + A, true, rc,
+                                                      k, Nx, unit, em.Ef);
+#pragma unroll
+                        for (int v = 0; v < XF_V; ++v) out[v] = o.v[v];
                     }
                 }
 #pragma unroll
@@ -576,15 +590,9 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
                     // the staged record may already be overwritten: read this row's from global memory
                     const XRec* rg = reinterpret_cast<const XRec*>(static_cast<const unsigned char*>(a.rec) +
                                                                    (size_t)r * XREC_BYTES);
+                    const FxOut o = fx_edge_chunk(ib, PADR + e + A, true, rg, k, Nx, unit, em.Ef);
 #pragma unroll
-                    for (int v = 0; v < XF_V; ++v) {
-                        long long xw[NTAP];
-                        for (int t = 0; t < NTAP; ++t) {
-                            const int ee = e + PADR + A + v + t, p = ee >> 1;
-                            xw[t] = ib[2 * (p + (p >> 2)) + (ee & 1)];
-                        }
-                        out[v] = fx_edge(xw, rg->w64, 1, k + v, Nx, rg->g64, rg->d64, unit, em.Ef);
-                    }
+                    for (int v = 0; v < XF_V; ++v) out[v] = o.v[v];
                 }
             }
 #pragma unroll

@@ -769,6 +769,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(set_kernel_attributes(max_optin - 1024));
     CTRY(set_kernel_attributes_e(max_optin - 1024));
     CTRY(set_kernel_attributes_fx(max_optin - 1024));
+    CTRY(set_ring_attributes(max_optin - 1024));
 
     const size_t cells = (size_t)Nx * (size_t)Np;
     for (int b = 0; b < 2; ++b) {

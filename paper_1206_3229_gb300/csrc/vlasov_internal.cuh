@@ -304,6 +304,7 @@ cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st
 // HMF, 8-byte storage, from the x-shift's per-CTA partials: force and p-shift parameters
 // (pparams_hmf_cta), and the moments after the second x-shift (colreduce_cta, one block).
 cudaError_t launch_pparams_hmf_cta(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
+cudaError_t set_ring_attributes(int max_smem);
 cudaError_t launch_colreduce_cta(const ColReduceArgs& a, cudaStream_t st);
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st);
 int ring_blocks(int N);
