@@ -110,9 +110,9 @@ int vlasov_get_f_device(vlasov_sim* sim, double* dev_f);
    The state between calls is always a whole step. */
 int vlasov_step(vlasov_sim* sim, int n);
 
-/* Turn the fused x-shifts on (1) or off (0).  On by default where available: VLASOV_FX64 storage
-   with Nx <= 4096; asking for them elsewhere returns VLASOV_EINVAL.  vlasov_fused_x reports the
-   current setting (0 or 1). */
+/* Turn the fused x-shifts on (1) or off (0).  Available with VLASOV_FX64 storage, Nx <= 4096 and
+   Nx a multiple of 64 (elsewhere asking for them returns VLASOV_EINVAL); on by default there when x
+   is periodic.  vlasov_fused_x reports the current setting (0 or 1). */
 int vlasov_set_fused_x(vlasov_sim* sim, int on);
 int vlasov_fused_x(const vlasov_sim* sim);
 

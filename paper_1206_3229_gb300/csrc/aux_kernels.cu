@@ -544,17 +544,17 @@ __device__ __forceinline__ void pparams_fixed(const PParamsArgs& a, int i, doubl
     const uint64_t be = (uint64_t)(V & (((i128)1 << 62) - 1));   // beta 2^62 in [0, 2^62)
     const uint64_t al = (1ull << 62) - be;                         // alpha = 1 - beta
     const long long g = spline_cubic62(al), d = spline_cubic62(be);
-    long long W[NTAP];
-    W[0] = mul_fd60(g, FD60_C4);
-    W[1] = mul_fd60(g, FD60_C3) + mul_fd60(d, FD60_C4);
-    W[2] = mul_fd60(g, FD60_C2) + mul_fd60(d, FD60_C3);
-    W[3] = mul_fd60(g, FD60_C1) + mul_fd60(d, FD60_C2);
-    W[4] = (long long)al + mul_fd60(g, FD60_C0) + mul_fd60(d, FD60_C1);
-    W[5] = (long long)be + mul_fd60(g, FD60_C1) + mul_fd60(d, FD60_C0);
-    W[6] = mul_fd60(g, FD60_C2) + mul_fd60(d, FD60_C1);
-    W[7] = mul_fd60(g, FD60_C3) + mul_fd60(d, FD60_C2);
-    W[8] = mul_fd60(g, FD60_C4) + mul_fd60(d, FD60_C3);
-    W[9] = mul_fd60(d, FD60_C4);
+    // W = the alpha/beta taps + g D_k (taps 0..8) + d D_{k+1} (taps 1..9), each exact on the 2^-62 grid
+    const long long C[5] = {FD60_C0, FD60_C1, FD60_C2, FD60_C3, FD60_C4};
+    long long Wg[NTAP], Wd[NTAP], W[NTAP];
+#pragma unroll
+    for (int t = 0; t < NTAP; ++t) {
+        const int m0 = t - 4, m1 = t - 5;
+        Wg[t] = (m0 >= -4 && m0 <= 4) ? mul_fd60(g, C[m0 < 0 ? -m0 : m0]) : 0;
+        Wd[t] = (m1 >= -4 && m1 <= 4) ? mul_fd60(d, C[m1 < 0 ? -m1 : m1]) : 0;
+        const long long base = t == 4 ? (long long)al : t == 5 ? (long long)be : 0;
+        W[t] = base + Wg[t] + Wd[t];
+    }
     const size_t n = (size_t)a.Nx;
     double* w = static_cast<double*>(a.w);
     double* gd = static_cast<double*>(a.gd);
@@ -566,15 +566,27 @@ __device__ __forceinline__ void pparams_fixed(const PParamsArgs& a, int i, doubl
     if (a.Wh) {
         // Wh = round(w 2^30); wl = (w 2^30 - Wh) 2^-EMUL_RS; wf = w 2^30 2^-EMUL_RS (emul.cuh)
         const float sc = EMUL_WSCALE * 0.25f;   // 2^-(32 + EMUL_RS): W is on the 2^-62 grid
-#pragma unroll
-        for (int t = 0; t < NTAP; ++t) {
-            const long long h = (W[t] + (1ll << 31)) >> 32;
-            const long long l = W[t] - (h << 32);                                   // |l| <= 2^31
+        auto split = [&](long long Wt, int* Wh, float* wl, float* wf, size_t idx) {
+            const long long h = (Wt + (1ll << 31)) >> 32;
+            const long long l = Wt - (h << 32);                                     // |l| <= 2^31
             const float lf = 2.f * __int2float_rn((int)(l >> 1)) + (float)(int)(l & 1);
-            const float wfull = fmaf(__int2float_rn((int)(W[t] >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)W[t]));
-            a.Wh[(size_t)t * n + i] = (int)h;
-            a.wl[(size_t)t * n + i] = lf * sc;
-            a.wf[(size_t)t * n + i] = wfull * sc;
+            const float wfull = fmaf(__int2float_rn((int)(Wt >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)Wt));
+            Wh[idx] = (int)h;
+            wl[idx] = lf * sc;
+            wf[idx] = wfull * sc;
+        };
+#pragma unroll
+        for (int t = 0; t < NTAP; ++t) split(W[t], a.Wh, a.wl, a.wf, (size_t)t * n + i);
+        if (a.Whe) {
+            // zero-outside columns: the filters without g D_k (foot cell k = -1) and without
+            // d D_{k+1} (k = Np - 1), [2][NTAP][n]
+            const long long base4 = (long long)al, base5 = (long long)be;
+#pragma unroll
+            for (int t = 0; t < NTAP; ++t) {
+                const long long base = t == 4 ? base4 : t == 5 ? base5 : 0;
+                split(base + Wd[t], a.Whe, a.wle, a.wfe, (size_t)t * n + i);
+                split(base + Wg[t], a.Whe, a.wle, a.wfe, (size_t)(NTAP + t) * n + i);
+            }
         }
     }
 }

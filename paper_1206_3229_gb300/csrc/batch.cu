@@ -261,7 +261,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
 
 // ------------------------------------------------------------------------------------------- slot layout
 struct SlotLayout {
-    size_t f[2], xrec, pn0, pw, pgd, pWh, pwl, pwf, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart, ringpart,
+    size_t f[2], xrec, pn0, pw, pgd, pWh, pwl, pwf, pWhe, pwle, pwfe, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart, ringpart,
         tickets, sc, hist, dstep, err, costab, sintab, cosfx, sinfx, ringdV, ringV, rowv, colv, initpart, inv_mass, total;
 };
 
@@ -285,6 +285,9 @@ SlotLayout layout(int Nx, int Np, int esz)
     L.pWh = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
     L.pwl = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
     L.pwf = esz == 8 ? take((size_t)NTAP * Nx * 4) : 0;
+    L.pWhe = esz == 8 ? take((size_t)2 * NTAP * Nx * 4) : 0;   // edge filters of the zero-outside p columns
+    L.pwle = esz == 8 ? take((size_t)2 * NTAP * Nx * 4) : 0;
+    L.pwfe = esz == 8 ? take((size_t)2 * NTAP * Nx * 4) : 0;
     L.colacc = take((size_t)Nx * 8);
     L.kinpart = take((size_t)B_CTAS_X_MAX * 16);   // FP64 (F32 storage) or int128 (FX64) per CTA
     L.rho = take((size_t)Nx * 8);
@@ -529,6 +532,9 @@ int fill_slot_args(vlasov_batch* b, int k)
     p.Wh = fx ? reinterpret_cast<int*>(P(b, s, s.L.pWh)) : nullptr;
     p.wl = fx ? reinterpret_cast<float*>(P(b, s, s.L.pwl)) : nullptr;
     p.wf = fx ? reinterpret_cast<float*>(P(b, s, s.L.pwf)) : nullptr;
+    p.Whe = fx ? reinterpret_cast<int*>(P(b, s, s.L.pWhe)) : nullptr;
+    p.wle = fx ? reinterpret_cast<float*>(P(b, s, s.L.pwle)) : nullptr;
+    p.wfe = fx ? reinterpret_cast<float*>(P(b, s, s.L.pwfe)) : nullptr;
     EmulArgs& e = b->em[k];
     std::memset(&e, 0, sizeof e);
     if (fx) {
@@ -539,6 +545,9 @@ int fill_slot_args(vlasov_batch* b, int k)
         e.wf = p.wf;
         e.gd = reinterpret_cast<const double*>(p.gd);
         e.w64 = reinterpret_cast<const double*>(p.w);
+        e.Whe = p.Whe;
+        e.wle = p.wle;
+        e.wfe = p.wfe;
     }
     return VLASOV_OK;
 }
@@ -936,6 +945,10 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
             rc_.w32[t] = (float)Ls.w[t];
             emul_weight(Ls.w[t], rc_.Wh[t], rc_.wl[t], rc_.wf[t]);
         }
+        double we[2][NTAP];
+        line_edge_weights(Ls, we);
+        for (int q = 0; q < 2; ++q)
+            for (int t = 0; t < NTAP; ++t) emul_weight(we[q][t], rc_.Whe[q][t], rc_.wle[q][t], rc_.wfe[q][t]);
         std::memcpy(&recs[(size_t)j * XREC_BYTES], &rc_, sizeof rc_);
     }
     if (!per && max_n0 + 8 > B_PAD_ZERO) {

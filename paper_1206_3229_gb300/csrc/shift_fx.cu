@@ -60,25 +60,70 @@ __device__ __forceinline__ long long fx_edge(const long long* X, const double* w
     return (long long)fx128_from_f64(out, FX_FRAC - Ef);
 }
 
-// The XF_V outputs of a chunk that touches a zero-outside row end, recomputed in FP64 (rare; kept
-// out of line so that its registers do not weigh on the filter loop).  Window element m (m = 0 at
-// f_{k-4} of the chunk's first output) is row[b0 + m] of a plain row, or of a padded row (PADDED:
-// 8-element lines 10 elements apart).  Returned by value, so that no caller array needs an address.
+// A chunk with an output whose foot cell touches or leaves a zero-outside row end (rare; kept out
+// of line so that its registers do not weigh on the filter loop).  Outputs with the foot cell
+// wholly outside are 0; the two touching the end take the row's edge filters (line_edge_weights) in
+// the same fixed-point arithmetic as the interior; the others keep the interior results o.v.
+// Window element m (m = 0 at f_{k-4} of the chunk's first output) is row[b0 + m] of a plain row,
+// or of a padded row (PADDED: 8-element lines 10 elements apart).  Returned by value (no caller
+// array needs an address), with the range bits of the recomputed outputs.
 struct FxOut {
     long long v[XF_V];
+    uint32_t rng;
 };
-__device__ __noinline__ FxOut fx_edge_chunk(const long long* row, int b0, bool padded, const XRec* rc, int k, int Nx,
-                                            double unit, int Ef)
+__device__ __noinline__ FxOut fx_edge_chunk(FxOut o, const long long* row, int b0, bool padded, const XRec* rc,
+                                            int k, int Nx)
 {
-    FxOut o;
+    o.rng = 0;
     for (int v = 0; v < XF_V; ++v) {
-        long long xw[NTAP];
+        const int kv = k + v;
+        if (kv >= 0 && kv < Nx - 1) continue;
+        if (kv < -1 || kv >= Nx) {
+            o.v[v] = 0;
+            continue;
+        }
+        const int q = kv < 0 ? 0 : 1;
+        long long M = EMUL_M0;
+        float sl = 0.f, sr = 0.f;
         for (int t = 0; t < NTAP; ++t) {
             const int ee = b0 + v + t;
-            xw[t] = padded ? row[(ee >> 3) * 10 + (ee & 7)] : row[ee];
+            int kx;
+            float kf, rf;
+            fx_split(padded ? row[(ee >> 3) * 10 + (ee & 7)] : row[ee], kx, kf, rf);
+            M += (long long)rc->Whe[q][t] * (long long)kx;
+            sl = fmaf(rc->wle[q][t], kf, sl);
+            sr = fmaf(rc->wfe[q][t] * 9.313225746154785e-10f, rf, sr);   // * 2^-30
         }
-        o.v[v] = fx_edge(xw, rc->w64, 1, k + v, Nx, rc->g64, rc->d64, unit, Ef);
+        o.v[v] = fx_store(emul_finish(M, sl + sr), o.rng);
     }
+    return o;
+}
+
+// One boundary output of a zero-outside column (window X = f_{kk-4} .., foot cell kk): 0 when the
+// cell lies wholly outside, else the column's edge filter (em.Whe: [2][NTAP][Nx]) in the fixed-point
+// arithmetic of the interior.  (Inline: an out-of-line call here cost the p-shift a stack frame
+// and spills in its filter loop.)
+struct FxOne {
+    long long v;
+    uint32_t rng;
+};
+__device__ __forceinline__ FxOne fx_edge_one(const long long* X, const EmulArgs& em, int i, int Nx, int kk, int Np)
+{
+    FxOne o{0, 0};
+    if (kk < -1 || kk >= Np) return o;
+    const int q = kk < 0 ? 0 : 1;
+    long long M = EMUL_M0;
+    float sl = 0.f, sr = 0.f;
+    for (int t = 0; t < NTAP; ++t) {
+        const size_t idx = ((size_t)q * NTAP + t) * Nx + i;
+        int kx;
+        float kf, rf;
+        fx_split(X[t], kx, kf, rf);
+        M += (long long)em.Whe[idx] * (long long)kx;
+        sl = fmaf(em.wle[idx], kf, sl);
+        sr = fmaf(em.wfe[idx] * 9.313225746154785e-10f, rf, sr);   // * 2^-30
+    }
+    o.v = fx_store(emul_finish(M, sl + sr), o.rng);
     return o;
 }
 
@@ -347,9 +392,13 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
                     if constexpr (!PERIODIC) {
                         const int k = i + n0;
                         if (k < 0 || k + XF_V - 1 >= Nx - 1) {
-                            const FxOut o = fx_edge_chunk(rowbuf, e + A, false, rc, k, Nx, unit, em.Ef);
+                            FxOut o;
+#pragma unroll
+                            for (int v = 0; v < XF_V; ++v) o.v[v] = out[v];
+                            o = fx_edge_chunk(o, rowbuf, e + A, false, rc, k, Nx);
 #pragma unroll
                             for (int v = 0; v < XF_V; ++v) out[v] = o.v[v];
+                            rng |= o.rng;
                         }
                     }
 #pragma unroll
@@ -540,10 +589,13 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
                 if constexpr (!PERIODIC) {
                     const int k = i + n0;
                     if (k < 0 || k + XF_V - 1 >= Nx - 1) {
-                        const FxOut o = fx_edge_chunk(reinterpret_cast<const long long*>(sb), PADR + e + A, true, rc,
-                                                      k, Nx, unit, em.Ef);
+                        FxOut o;
+#pragma unroll
+                        for (int v = 0; v < XF_V; ++v) o.v[v] = out[v];
+                        o = fx_edge_chunk(o, reinterpret_cast<const long long*>(sb), PADR + e + A, true, rc, k, Nx);
 #pragma unroll
                         for (int v = 0; v < XF_V; ++v) out[v] = o.v[v];
+                        rng |= o.rng;
                     }
                 }
 #pragma unroll
@@ -590,9 +642,13 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
                     // the staged record may already be overwritten: read this row's from global memory
                     const XRec* rg = reinterpret_cast<const XRec*>(static_cast<const unsigned char*>(a.rec) +
                                                                    (size_t)r * XREC_BYTES);
-                    const FxOut o = fx_edge_chunk(ib, PADR + e + A, true, rg, k, Nx, unit, em.Ef);
+                    FxOut o;
+#pragma unroll
+                    for (int v = 0; v < XF_V; ++v) o.v[v] = out[v];
+                    o = fx_edge_chunk(o, ib, PADR + e + A, true, rg, k, Nx);
 #pragma unroll
                     for (int v = 0; v < XF_V; ++v) out[v] = o.v[v];
+                    rng |= o.rng;
                 }
             }
 #pragma unroll
@@ -782,7 +838,13 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
                         for (int u = 0; u < NTAP; ++u)
                             X[u] = t.smem_ok ? buf[(base + rw + u) * PS_TW + lane]
                                              : gload_p<long long, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
-                        fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
+                        if (em.Whe) {   // fixed point, with the column's edge filters
+                            const FxOne o = fx_edge_one(X, em, i, Nx, kk, Np);
+                            rng |= o.rng;
+                            fout[(size_t)j * Nx + i] = o.v;
+                        } else {
+                            fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
+                        }
                     }
                 }
             }

@@ -152,6 +152,9 @@ void free_emul(EmulParamsDev& e)
     cudaFree(e.Wh);
     cudaFree(e.wl);
     cudaFree(e.wf);
+    cudaFree(e.Whe);
+    cudaFree(e.wle);
+    cudaFree(e.wfe);
     e = EmulParamsDev{};
 }
 
@@ -160,6 +163,9 @@ int alloc_emul(EmulParamsDev& e, int n)
     CU_TRY(cudaMalloc(&e.Wh, sizeof(int) * NTAP * (size_t)n));
     CU_TRY(cudaMalloc(&e.wl, sizeof(float) * NTAP * (size_t)n));
     CU_TRY(cudaMalloc(&e.wf, sizeof(float) * NTAP * (size_t)n));
+    CU_TRY(cudaMalloc(&e.Whe, sizeof(int) * 2 * NTAP * (size_t)n));
+    CU_TRY(cudaMalloc(&e.wle, sizeof(float) * 2 * NTAP * (size_t)n));
+    CU_TRY(cudaMalloc(&e.wfe, sizeof(float) * 2 * NTAP * (size_t)n));
     return VLASOV_OK;
 }
 
@@ -186,6 +192,10 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
                 r.w32[t] = (float)L.w[t];
                 emul_weight(L.w[t], r.Wh[t], r.wl[t], r.wf[t]);
             }
+            double we[2][NTAP];
+            line_edge_weights(L, we);
+            for (int q = 0; q < 2; ++q)
+                for (int t = 0; t < NTAP; ++t) emul_weight(we[q][t], r.Whe[q][t], r.wle[q][t], r.wfe[q][t]);
             if (rows_are_p) {
                 const double pj = s->pmin + (double)l * s->dp;   // as the kernels' p_j
                 r.p2q = std::llround(std::ldexp(0.5 * pj * pj, KIN_Q));
@@ -196,7 +206,7 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
         CU_TRY(cudaStreamSynchronize(s->st));
     }
     std::vector<int> n0(n);
-    std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n);
+    std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n), we((size_t)2 * NTAP * n);
     int mx = 0;
     for (int l = 0; l < n; ++l) {
         LineSplit L;
@@ -206,6 +216,10 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
         for (int t = 0; t < NTAP; ++t) w[(size_t)t * n + l] = L.w[t];
         gd[l] = L.g;
         gd[(size_t)n + l] = L.d;
+        double e2[2][NTAP];
+        line_edge_weights(L, e2);
+        for (int q = 0; q < 2; ++q)
+            for (int t = 0; t < NTAP; ++t) we[((size_t)q * NTAP + t) * n + l] = e2[q][t];
     }
     if (max_abs_n0) *max_abs_n0 = mx;
     CU_TRY(cudaMemcpyAsync(p.n0, n0.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s->st));
@@ -216,6 +230,12 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
         CU_TRY(cudaMemcpyAsync(e->Wh, Wh.data(), sizeof(int) * Wh.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaMemcpyAsync(e->wl, wl.data(), sizeof(float) * wl.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaMemcpyAsync(e->wf, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice, s->st));
+        std::vector<int> Whe(we.size());
+        std::vector<float> wle(we.size()), wfe(we.size());
+        for (size_t q = 0; q < we.size(); ++q) emul_weight(we[q], Whe[q], wle[q], wfe[q]);
+        CU_TRY(cudaMemcpyAsync(e->Whe, Whe.data(), sizeof(int) * Whe.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaMemcpyAsync(e->wle, wle.data(), sizeof(float) * wle.size(), cudaMemcpyHostToDevice, s->st));
+        CU_TRY(cudaMemcpyAsync(e->wfe, wfe.data(), sizeof(float) * wfe.size(), cudaMemcpyHostToDevice, s->st));
         CU_TRY(cudaStreamSynchronize(s->st));
     }
     if (s->msz == 8) {
@@ -385,6 +405,9 @@ EmulArgs emargs(vlasov_sim* s, const LineParamsDev& p, const EmulParamsDev& e)
     a.wf = e.wf;
     a.gd = static_cast<const double*>(p.gd);
     a.w64 = static_cast<const double*>(p.w);
+    a.Whe = e.Whe;
+    a.wle = e.wle;
+    a.wfe = e.wfe;
     return a;
 }
 
@@ -476,6 +499,9 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int 
     a.Wh = (s->emul || s->fx) ? s->pe.Wh : nullptr;
     a.wl = (s->emul || s->fx) ? s->pe.wl : nullptr;
     a.wf = (s->emul || s->fx) ? s->pe.wf : nullptr;
+    a.Whe = (s->emul || s->fx) ? s->pe.Whe : nullptr;
+    a.wle = (s->emul || s->fx) ? s->pe.wle : nullptr;
+    a.wfe = (s->emul || s->fx) ? s->pe.wfe : nullptr;
     if (from_cta) {
         a.ctapart = s->ctapart;
         a.ctas = ctas > 0 ? ctas : s->xgrid;
@@ -848,7 +874,10 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
             if (xocc >= 1) {
                 s->xxstages = st;
                 s->xxgrid = std::min(Np, s->nsm * xocc);
-                s->fuse_ok = s->fuse = true;
+                s->fuse_ok = true;
+                // on by default for periodic rows; on zero-outside rows (sheet) the separate
+                // x-shifts measured faster (each fused row barrier waits for the rows' edge outputs)
+                s->fuse = s->xper;
             }
         }
     }

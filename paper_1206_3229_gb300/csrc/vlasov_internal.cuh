@@ -56,6 +56,20 @@ __host__ __device__ inline void line_split(double s, LineSplit& L)
     L.w[9] = d * VL_FD_C4;
 }
 
+// Zero-outside lines take f'' = 0 at nodes outside the grid.  Outputs whose foot cell lies wholly
+// outside are 0; the two whose cell touches the end need the filter without one f'' term:
+//   we[0]: k = -1, without g D_k   (D_k spans taps 0..8 with c_|t-4|),
+//   we[1]: k = n - 1, without d D_{k+1}  (taps 1..9 with c_|t-5|).
+__host__ __device__ inline void line_edge_weights(const LineSplit& L, double we[2][NTAP])
+{
+    const double c[5] = {VL_FD_C0, VL_FD_C1, VL_FD_C2, VL_FD_C3, VL_FD_C4};
+    for (int t = 0; t < NTAP; ++t) {
+        const int m0 = t - 4, m1 = t - 5;
+        we[0][t] = L.w[t] - (m0 >= -4 && m0 <= 4 ? L.g * c[m0 < 0 ? -m0 : m0] : 0.0);
+        we[1][t] = L.w[t] - (m1 >= -4 && m1 <= 4 ? L.d * c[m1 < 0 ? -m1 : m1] : 0.0);
+    }
+}
+
 // Per-line parameters in device memory, structure-of-arrays over `n` lines:
 //   n0[line], w[t*n + line] (t < 10), gd[line] = g, gd[n + line] = d  (in the storage type T).
 struct LineParamsDev {
@@ -93,8 +107,12 @@ struct XRec {
     float w32[NTAP];
     float g32, d32;
     long long p2q;        // round(p_j^2 / 2 * 2^KIN_Q) of the row: exact kinetic-energy weight
+    // zero-outside rows: line_edge_weights split as Wh/wl/wf (the fixed-point sweeps' edge outputs)
+    int Whe[2][NTAP];
+    float wle[2][NTAP];
+    float wfe[2][NTAP];
 };
-constexpr int XREC_BYTES = 288;
+constexpr int XREC_BYTES = 528;
 constexpr int KIN_Q = 40;   // |p| < 2896 keeps p^2/2 * 2^KIN_Q below 2^62
 static_assert(sizeof(XRec) <= XREC_BYTES, "XRec must fit its staged slot");
 
@@ -136,12 +154,18 @@ struct EmulArgs {
     const float* wf;
     const double* gd;
     const double* w64;    // the FP64 weights [10][n] (boundary rows are recomputed in FP64)
+    const int* Whe = nullptr;     // or: the edge filters [2][10][n] of zero-outside lines, split as
+    const float* wle = nullptr;   //   Wh/wl/wf (the boundary outputs in fixed-point arithmetic)
+    const float* wfe = nullptr;
 };
 
 struct EmulParamsDev {
     int* Wh = nullptr;
     float* wl = nullptr;
     float* wf = nullptr;
+    int* Whe = nullptr;     // [2][NTAP][n]: the edge filters of zero-outside lines (line_edge_weights)
+    float* wle = nullptr;
+    float* wfe = nullptr;
 };
 
 struct PShiftArgs {
@@ -206,6 +230,9 @@ struct PParamsArgs {
     int* Wh;                 // emulated-FP64 split of the weights, or null
     float* wl;
     float* wf;
+    int* Whe = nullptr;      // and of the edge filters [2][NTAP][Nx], or null
+    float* wle = nullptr;
+    float* wfe = nullptr;
 };
 
 struct RingArgs {
