@@ -195,19 +195,28 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs 
                 if constexpr (!PERIODIC) {
                     const int k = i + n0;
                     if (k < 0 || k + XE_V - 1 >= Nx - 1) {
-                        // rare boundary chunk: recompute in FP64 from the staged (kx, r) values
-#pragma unroll
+                        // rare boundary chunk (f'' = 0 outside the row): outputs whose foot cell is
+                        // outside are 0, the two touching the end take the row's edge filters, in
+                        // the same integer/FP32 arithmetic as the interior
                         for (int v = 0; v < XE_V; ++v) {
-                            double xv[NTAP];
-                            double acc = 0.0;
-#pragma unroll
+                            const int kv = k + v;
+                            if (kv >= 0 && kv < Nx - 1) continue;
+                            if (kv < -1 || kv >= Nx) {
+                                Tv[v] = 0;
+                                out[v] = 0.0;
+                                continue;
+                            }
+                            const int q = kv < 0 ? 0 : 1;
+                            long long M = EMUL_M0;
+                            float sa = 0.f, sb = 0.f;
                             for (int t = 0; t < NTAP; ++t) {
                                 const int2 p = src[e + A + v + t];
-                                xv[t] = ((double)p.x + (double)__int_as_float(p.y)) * grid;
-                                acc = fma(rc->w64[t], xv[t], acc);
+                                M = mad_wide(rc->Whe[q][t], p.x, M);
+                                sa = fmaf(rc->wle[q][t], __int2float_rn(p.x), sa);
+                                sb = fmaf(rc->wfe[q][t], __int_as_float(p.y), sb);
                             }
-                            out[v] = emul_edge(acc, xv, k + v, Nx, g, d);
-                            Tv[v] = (long long)fx128_from_f64(out[v], 61 - em.Ef);   // sums see the corrected value
+                            Tv[v] = emul_finish(M, sa + sb);
+                            out[v] = emul_to_f64(Tv[v], em.Ef);
                         }
                     }
                 }
@@ -447,8 +456,41 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
             if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
         }
         if constexpr (!PPER) {
-            if (any_edge && colvalid) {
-                // rare boundary rows (f'' = 0 outside the grid): recompute in FP64
+            if (any_edge && colvalid && em.Whe) {
+                // rare boundary rows (f'' = 0 outside the grid): 0 where the foot cell is outside,
+                // the column's edge filters where it touches the end, in the interior arithmetic
+                for (int rw = 0; rw < PS_RPT; ++rw) {
+                    const int j = jb + rw, kk = j + n0_i;
+                    if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
+                    if (kk < -1 || kk >= Np) {
+                        fout[(size_t)j * Nx + i] = 0.0;
+                        continue;
+                    }
+                    const int q = kk < 0 ? 0 : 1;
+                    long long M = EMUL_M0;
+                    float sa = 0.f, sbb = 0.f;
+                    for (int u = 0; u < NTAP; ++u) {
+                        int kx;
+                        float rr;
+                        if (t.smem_ok) {
+                            const int2 v = sb[(base + rw + u) * PS_TW + lane];
+                            kx = v.x;
+                            rr = __int_as_float(v.y);
+                        } else {
+                            const double x = gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                            const EmulElem ev = emul_split(x, s_base, bad);
+                            kx = ev.kx;
+                            rr = ev.r;
+                        }
+                        const size_t idx = ((size_t)q * NTAP + u) * Nx + i;
+                        M = mad_wide(em.Whe[idx], kx, M);
+                        sa = fmaf(em.wle[idx], __int2float_rn(kx), sa);
+                        sbb = fmaf(em.wfe[idx], rr, sbb);
+                    }
+                    fout[(size_t)j * Nx + i] = emul_to_f64(emul_finish(M, sa + sbb), em.Ef);
+                }
+            } else if (any_edge && colvalid) {
+                // no edge filters (not given): recompute in FP64
                 for (int rw = 0; rw < PS_RPT; ++rw) {
                     const int j = jb + rw, kk = j + n0_i;
                     if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
