@@ -787,16 +787,33 @@ __global__ void __launch_bounds__(CAS_THREADS) casimir_kernel(const void* __rest
     }
 }
 
-__global__ void casimir_final_kernel(const double* __restrict__ part, int nb, double dxdp, double* __restrict__ out)
+// One block of CAS_FINAL_THREADS: thread t adds the partials t, t + CAS_FINAL_THREADS, ..., then a
+// fixed shared-memory tree (a dependent chain of FP64 additions costs microseconds per hundred
+// on this GPU, so the partials are not added one after another by one thread).
+constexpr int CAS_FINAL_THREADS = 512;
+__global__ void __launch_bounds__(CAS_FINAL_THREADS) casimir_final_kernel(const double* __restrict__ part, int nb,
+                                                                         double dxdp, double* __restrict__ out)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double sa[CAS_FINAL_THREADS], sb[CAS_FINAL_THREADS];
     double a = 0.0, b = 0.0;
-    for (int k = 0; k < nb; ++k) {
+    for (int k = threadIdx.x; k < nb; k += CAS_FINAL_THREADS) {
         a += part[2 * k];
         b += part[2 * k + 1];
     }
-    out[0] = dxdp * a;
-    out[1] = dxdp * b;
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = CAS_FINAL_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sa[threadIdx.x] += sa[threadIdx.x + h];
+            sb[threadIdx.x] += sb[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = dxdp * sa[0];
+        out[1] = dxdp * sb[0];
+    }
 }
 
 // part: 2 * CAS_BLOCKS doubles, out: 2 doubles (entropy, l2).
@@ -807,7 +824,7 @@ cudaError_t launch_casimirs(int kind, const void* f, size_t n, double unit, doub
     else if (kind == 1) casimir_kernel<1><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
     else if (kind == 2) casimir_kernel<2><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
     else casimir_kernel<3><<<CAS_BLOCKS, CAS_THREADS, 0, st>>>(f, n, unit, part);
-    casimir_final_kernel<<<1, 32, 0, st>>>(part, CAS_BLOCKS, dxdp, out);
+    casimir_final_kernel<<<1, CAS_FINAL_THREADS, 0, st>>>(part, CAS_BLOCKS, dxdp, out);
     return cudaGetLastError();
 }
 
