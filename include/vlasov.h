@@ -106,13 +106,17 @@ int vlasov_get_f_device(vlasov_sim* sim, double* dev_f);
    stream.  The moments of f after each step are appended to a device ring of 4096 records.
    With fused x-shifts (vlasov_fused_x) a call of n >= 2 steps runs the second x half-shift of step
    k and the first of step k+1 as one launch that keeps the row between them on chip: the same
-   arithmetic and the same bits as separate launches, with one HBM round trip of f fewer per step.
+   arithmetic as separate launches, with one HBM round trip of f fewer per step.
    The state between calls is always a whole step. */
 int vlasov_step(vlasov_sim* sim, int n);
 
-/* Turn the fused x-shifts on (1) or off (0).  Available with VLASOV_FX64 storage, Nx <= 4096 and
-   Nx a multiple of 64 (elsewhere asking for them returns VLASOV_EINVAL); on by default there when x
-   is periodic.  vlasov_fused_x reports the current setting (0 or 1). */
+/* Turn the fused x-shifts on (1) or off (0).  Available with VLASOV_FX64 storage (Nx <= 4096 and
+   a multiple of 64; on by default when x is periodic) and with VLASOV_F32 or VLASOV_BF16 storage
+   (Nx <= 4096; on by default for VLASOV_F32).  Elsewhere asking for them returns VLASOV_EINVAL.
+   With FX64 the fused run gives the same bits as the separate launches; with FP32-class storage f
+   is bitwise the same for a given force, but the per-CTA FP32 column and kinetic sums run over
+   another row partition, so self-consistent runs agree to within the rounding of those sums.
+   vlasov_fused_x reports the current setting (0 or 1). */
 int vlasov_set_fused_x(vlasov_sim* sim, int on);
 int vlasov_fused_x(const vlasov_sim* sim);
 

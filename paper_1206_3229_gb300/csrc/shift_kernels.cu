@@ -144,10 +144,14 @@ __device__ __forceinline__ void xshift_chunk(const S* __restrict__ rowbuf, int e
     (void)i;
 }
 
-template <typename S, int A, bool PERIODIC, typename T = typename VecOf<S>::T>
+// One row: chunks of V outputs at columns V (tid + c nthreads), c < CH, written to orow (global or
+// shared memory; with WRAP the chunks below column 16 also at orow + Nx, the wrap copy a periodic
+// second pass reads).
+template <typename S, int A, bool PERIODIC, int CH = maxch_of<S>(), bool WRAP = false,
+          typename T = typename VecOf<S>::T>
 __device__ __forceinline__ void xshift_row(const S* __restrict__ rowbuf, S* __restrict__ orow,
                                            const T (&w)[NTAP], int n0, int Nx, T g, T d, int nthreads,
-                                           typename VecOf<S>::acc (&colacc)[maxch_of<S>()][VecOf<S>::V],
+                                           typename VecOf<S>::acc (&colacc)[CH][VecOf<S>::V],
                                            typename VecOf<S>::acc& rowsum)
 {
     constexpr int V = VecOf<S>::V;
@@ -161,7 +165,7 @@ __device__ __forceinline__ void xshift_row(const S* __restrict__ rowbuf, S* __re
         base = n0 - 4 - A;
     }
 #pragma unroll
-    for (int c = 0; c < maxch_of<S>(); ++c) {
+    for (int c = 0; c < CH; ++c) {
         const int i = V * (tid + c * nthreads);
         if (i < Nx) {
             int e = i + base;
@@ -172,6 +176,9 @@ __device__ __forceinline__ void xshift_row(const S* __restrict__ rowbuf, S* __re
             xshift_chunk<S, A, PERIODIC>(rowbuf, e, w, i, i + n0, Nx, g, d, out);
             const vec o = pack<S>(out);
             *reinterpret_cast<vec*>(orow + i) = o;
+            if constexpr (WRAP) {
+                if (i < 16) *reinterpret_cast<vec*>(orow + Nx + i) = o;
+            }
             T stored[V];   // the column sums are those of the stored values
             unpack<S>(o, stored);
 #pragma unroll
@@ -180,6 +187,101 @@ __device__ __forceinline__ void xshift_row(const S* __restrict__ rowbuf, S* __re
                 rowsum += stored[v];
             }
         }
+    }
+}
+
+// End of a sweep: hand over this CTA's column sums acc[c][v] (column V (tid + c blockDim) + v) in
+// the form the arguments ask for.  Every thread calls it; `scratch` (>= 2 KB of shared memory no
+// warp still reads) serves the block reduction.
+template <typename S, int CH>
+__device__ __forceinline__ void colsum_epilogue(const XShiftArgs& a, const typename VecOf<S>::acc (&colacc)[CH][VecOf<S>::V],
+                                                i128* scratch)
+{
+    using acc_t = typename VecOf<S>::acc;
+    constexpr int V = VecOf<S>::V;
+    const int Nx = a.Nx, tid = threadIdx.x, nthreads = blockDim.x;
+    if (a.colacc) {
+        // exact fixed-point column sums, added across CTAs (order-free)
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    long long q;
+                    if constexpr (sizeof(acc_t) == 8) q = (long long)fx128_from_f64((double)colacc[c][v], a.k_col);
+                    else q = (long long)fx128_from_f32((float)colacc[c][v], a.k_col);
+                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
+                }
+            }
+        }
+    } else if (a.ctapart) {
+        // HMF: this CTA's column sums t_i as integers in units 2^(Ef-51), then sum t_i and the
+        // 50-bit cos/sin-weighted sums (exact int128), three numbers per CTA instead of a row
+        i128 pm = 0, px = 0, py = 0, pz = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    long long t;
+                    if constexpr (sizeof(acc_t) == 8) t = (long long)fx128_from_f64((double)colacc[c][v], 51 - a.Ef);
+                    else t = (long long)fx128_from_f32((float)colacc[c][v], 51 - a.Ef);
+                    pm += (i128)t;
+                    px += (i128)__ldg(a.cos50 + i + v) * (i128)t;
+                    py += (i128)__ldg(a.sin50 + i + v) * (i128)t;
+                }
+            }
+        }
+        block_sum4_i128(pm, px, py, pz, scratch);
+        if (tid == 0) {
+            i128* cp = static_cast<i128*>(a.ctapart) + (size_t)blockIdx.x * 3;
+            cp[0] = pm;
+            cp[1] = px;
+            cp[2] = py;
+        }
+    } else if (a.colpart64) {
+        // exact fixed-point partial rows (units 2^-k_col): the reduction adds them with integer
+        // instructions, not a chain of FP64 additions per column
+        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if constexpr (sizeof(acc_t) == 8) cp[i + v] = (long long)fx128_from_f64((double)colacc[c][v], a.k_col);
+                    else cp[i + v] = (long long)fx128_from_f32((float)colacc[c][v], a.k_col);
+                }
+            }
+        }
+    } else if (a.colpart) {
+        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = V * (tid + c * nthreads);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) cp[i + v] = (double)colacc[c][v];
+            }
+        }
+    }
+}
+
+// The CTA's kinetic sum (per-thread FP64 partial kin) into a.kinpart[blockIdx.x]; red: 32 doubles.
+__device__ __forceinline__ void kin_epilogue(const XShiftArgs& a, double kin, double* red)
+{
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    double v = kin;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < (nthreads + 31) / 32; ++q) sum += red[q];
+        a.kinpart[blockIdx.x] = sum;
     }
 }
 
@@ -339,86 +441,8 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
         return;
     }
 
-    if (a.colacc) {
-        // exact fixed-point column sums, added across CTAs (order-free)
-#pragma unroll
-        for (int c = 0; c < maxch_of<S>(); ++c) {
-            const int i = V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    long long q;
-                    if constexpr (sizeof(acc_t) == 8) q = (long long)fx128_from_f64((double)colacc[c][v], a.k_col);
-                    else q = (long long)fx128_from_f32((float)colacc[c][v], a.k_col);
-                    atomicAdd(a.colacc + i + v, (unsigned long long)q);
-                }
-            }
-        }
-    } else if (a.ctapart) {
-        // HMF: this CTA's column sums t_i as integers in units 2^(Ef-51), then sum t_i and the
-        // 50-bit cos/sin-weighted sums (exact int128), three numbers per CTA instead of a row
-        i128 pm = 0, px = 0, py = 0, pz = 0;
-#pragma unroll
-        for (int c = 0; c < maxch_of<S>(); ++c) {
-            const int i = V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    long long t;
-                    if constexpr (sizeof(acc_t) == 8) t = (long long)fx128_from_f64((double)colacc[c][v], 51 - a.Ef);
-                    else t = (long long)fx128_from_f32((float)colacc[c][v], 51 - a.Ef);
-                    pm += (i128)t;
-                    px += (i128)__ldg(a.cos50 + i + v) * (i128)t;
-                    py += (i128)__ldg(a.sin50 + i + v) * (i128)t;
-                }
-            }
-        }
-        i128* scratch = reinterpret_cast<i128*>(bufs);   // the stages are free: every warp passed the last barrier
-        block_sum4_i128(pm, px, py, pz, scratch);
-        if (tid == 0) {
-            i128* cp = static_cast<i128*>(a.ctapart) + (size_t)blockIdx.x * 3;
-            cp[0] = pm;
-            cp[1] = px;
-            cp[2] = py;
-        }
-    } else if (a.colpart64) {
-        // exact fixed-point partial rows (units 2^-k_col): the reduction adds them with integer
-        // instructions, not a chain of FP64 additions per column
-        long long* cp = a.colpart64 + (size_t)blockIdx.x * Nx;
-#pragma unroll
-        for (int c = 0; c < maxch_of<S>(); ++c) {
-            const int i = V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if constexpr (sizeof(acc_t) == 8) cp[i + v] = (long long)fx128_from_f64((double)colacc[c][v], a.k_col);
-                    else cp[i + v] = (long long)fx128_from_f32((float)colacc[c][v], a.k_col);
-                }
-            }
-        }
-    } else if (a.colpart) {
-        double* cp = a.colpart + (size_t)blockIdx.x * Nx;
-#pragma unroll
-        for (int c = 0; c < maxch_of<S>(); ++c) {
-            const int i = V * (tid + c * nthreads);
-            if (i < Nx) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) cp[i + v] = (double)colacc[c][v];
-            }
-        }
-    }
-    if constexpr (KIN) {
-        double v = kin;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red[tid >> 5] = v;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int q = 0; q < (nthreads + 31) / 32; ++q) s += red[q];
-            a.kinpart[blockIdx.x] = s;
-        }
-    }
+    colsum_epilogue<S, maxch_of<S>()>(a, colacc, reinterpret_cast<i128*>(bufs));
+    if constexpr (KIN) kin_epilogue(a, kin, red);
 }
 
 template <typename S, bool PERIODIC, bool KIN>
@@ -437,6 +461,221 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_batch_kernel(const X
     const XShiftArgs a = args[slot * 2 + ver[slot]];
     if (a.Np <= 0 || (int)blockIdx.x >= a.Np || (a.ctas > 0 && (int)blockIdx.x >= a.ctas)) return;
     xshift_body<T, PERIODIC, KIN>(a);
+}
+
+// ============================================================================ fused x-shifts
+// FP32-class storage: the second x half-shift of step n and the first of step n+1 in one launch,
+// as xxshift_fx_body does for FX64 — each row staged once, the first pass written to a shared-memory
+// row (its column sums and kinetic sum: step n's moments), the second read from there and written
+// to HBM (its column sums: the next density).  Same arithmetic as two launches.  512 threads,
+// 8 / V chunks of V columns each (Nx <= 4096); two intermediate rows alternate (one barrier per row).
+//   a: input, records, shape, first-pass outputs; b: output buffer and second-pass column sums.
+template <typename S, bool PERIODIC>
+__device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftArgs& b)
+{
+    using T = typename VecOf<S>::T;
+    using acc_t = typename VecOf<S>::acc;
+    constexpr int V = VecOf<S>::V;
+    constexpr int CH = 8 / V;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    S* bufs = reinterpret_cast<S*>(smem_raw + 128);
+    __shared__ double red[32];
+    __shared__ unsigned int issued[8];
+
+    const S* __restrict__ fin = static_cast<const S*>(a.fin);
+    S* __restrict__ fout = static_cast<S*>(b.fout);
+    const int Nx = a.Nx, Np = a.Np, PAD = a.pad, NS = a.stages;
+    const int stride = Nx + 2 * PAD;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int G = a.ctas > 0 ? a.ctas : (int)gridDim.x;
+    S* ibufs = bufs + (size_t)NS * stride;   // two intermediate rows
+    unsigned char* recs = reinterpret_cast<unsigned char*>(ibufs + 2 * (size_t)stride);
+    const uint32_t row_bytes = (uint32_t)(Nx * sizeof(S));
+    const uint32_t tx_bytes = row_bytes + (PERIODIC ? 16u * (uint32_t)sizeof(S) : 0u) + XREC_BYTES;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&bars[s], 1);
+            issued[s] = 0;
+        }
+        fence_barrier_init();
+    }
+    for (int e = tid; e < 2 * stride; e += nthreads) ibufs[e] = from_math<S>(T(0));
+    if constexpr (!PERIODIC) {
+        for (int s = 0; s < NS; ++s) {
+            S* q = bufs + (size_t)s * stride;
+            for (int e = tid; e < PAD; e += nthreads) {
+                q[e] = from_math<S>(T(0));
+                q[PAD + Nx + e] = from_math<S>(T(0));
+            }
+        }
+    }
+    __syncthreads();
+
+    auto issue = [&](int s, int r) {
+        S* dst = bufs + (size_t)s * stride + PAD;
+        const S* src = fin + (size_t)r * Nx;
+        issued[s] += 1;
+        mbar_arrive_expect_tx(&bars[s], tx_bytes);
+        bulk_g2s(dst, src, row_bytes, &bars[s]);
+        if constexpr (PERIODIC) bulk_g2s(dst + Nx, src, 16u * (uint32_t)sizeof(S), &bars[s]);
+        bulk_g2s(recs + (size_t)s * XREC_BYTES, static_cast<const unsigned char*>(a.rec) + (size_t)r * XREC_BYTES,
+                 XREC_BYTES, &bars[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            const int r = blockIdx.x + s * G;
+            if (r < Np) issue(s, r);
+        }
+    }
+
+    acc_t acc1[CH][V], acc2[CH][V];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            acc1[c][v] = acc_t(0);
+            acc2[c][v] = acc_t(0);
+        }
+    double kin = 0.0;
+
+    int it = 0;
+    bool failed = false;
+    for (int r = blockIdx.x; r < Np; r += G, ++it) {
+        const int s = it % NS;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / NS) & 1), WAIT_LIMIT_NS);
+        S* ib = ibufs + (size_t)(it & 1) * stride + PAD;
+        int n0 = 0;
+        T w[NTAP];
+        T g = T(0), d = T(0);
+        acc_t rowsum = acc_t(0);
+        if (ok) {
+            const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
+            n0 = rc->n0;
+#pragma unroll
+            for (int t = 0; t < NTAP; ++t) w[t] = sizeof(T) == 8 ? (T)rc->w64[t] : (T)rc->w32[t];
+            if constexpr (!PERIODIC) {
+                g = sizeof(T) == 8 ? (T)rc->g64 : (T)rc->g32;
+                d = sizeof(T) == 8 ? (T)rc->d64 : (T)rc->d32;
+            }
+            const S* rowbuf = bufs + (size_t)s * stride + PAD;
+            const int A = (n0 - 4) & (V - 1);
+#define VL_PASS1(AA) xshift_row<S, AA, PERIODIC, CH, PERIODIC>(rowbuf, ib, w, n0, Nx, g, d, nthreads, acc1, rowsum)
+            if constexpr (V == 4) {
+                switch (A) {
+                    case 0: VL_PASS1(0); break;
+                    case 1: VL_PASS1(1); break;
+                    case 2: VL_PASS1(2); break;
+                    default: VL_PASS1(3); break;
+                }
+            } else {
+                switch (A) {
+                    case 0: VL_PASS1(0); break;
+                    case 1: VL_PASS1(1); break;
+                    case 2: VL_PASS1(2); break;
+                    case 3: VL_PASS1(3); break;
+                    case 4: VL_PASS1(4); break;
+                    case 5: VL_PASS1(5); break;
+                    case 6: VL_PASS1(6); break;
+                    default: VL_PASS1(7); break;
+                }
+            }
+#undef VL_PASS1
+        }
+        // every warp's first pass is done: the intermediate row is complete and stage s is free
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            const int rn = r + NS * G;
+            if (rn < Np) {
+                fence_proxy_async_smem();
+                issue(s, rn);
+            }
+        }
+        {
+            const double pj = a.pmin + (double)r * a.dp;
+            kin += 0.5 * pj * pj * (double)rowsum;
+        }
+        acc_t rowsum2 = acc_t(0);
+        S* orow = fout + (size_t)r * Nx;
+        const int A = (n0 - 4) & (V - 1);
+#define VL_PASS2(AA) xshift_row<S, AA, PERIODIC, CH, false>(ib, orow, w, n0, Nx, g, d, nthreads, acc2, rowsum2)
+        if constexpr (V == 4) {
+            switch (A) {
+                case 0: VL_PASS2(0); break;
+                case 1: VL_PASS2(1); break;
+                case 2: VL_PASS2(2); break;
+                default: VL_PASS2(3); break;
+            }
+        } else {
+            switch (A) {
+                case 0: VL_PASS2(0); break;
+                case 1: VL_PASS2(1); break;
+                case 2: VL_PASS2(2); break;
+                case 3: VL_PASS2(3); break;
+                case 4: VL_PASS2(4); break;
+                case 5: VL_PASS2(5); break;
+                case 6: VL_PASS2(6); break;
+                default: VL_PASS2(7); break;
+            }
+        }
+#undef VL_PASS2
+    }
+    __syncthreads();   // every warp is done with the stages and intermediate rows
+
+    if (failed) {
+        if (tid == 0) {
+            atomicCAS(a.err, 0, DEV_ERR_XSHIFT_WAIT);
+            for (int k = 0; k < NS; ++k)   // the last copy issued into each stage must land before exit
+                if (issued[k] > 0) mbar_wait_bounded(&bars[k], (uint32_t)((issued[k] - 1) & 1), WAIT_LIMIT_NS);
+        }
+        __syncthreads();
+        return;
+    }
+    i128* scratch = reinterpret_cast<i128*>(bufs);
+    colsum_epilogue<S, CH>(a, acc1, scratch);
+    kin_epilogue(a, kin, red);
+    colsum_epilogue<S, CH>(b, acc2, scratch);
+}
+
+template <typename S, bool PERIODIC>
+__global__ void __launch_bounds__(XXS_THREADS, 2) xxshift_kernel(XShiftArgs a, XShiftArgs b)
+{
+    xxshift_body<S, PERIODIC>(a, b);
+}
+
+size_t xxshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
+{
+    const size_t row = (size_t)(Nx + 2 * pad) * (size_t)elem_bytes;
+    return 256 + (size_t)stages * (row + XREC_BYTES) + 2 * row;
+}
+
+cudaError_t launch_xxshift(int elem_bytes, bool periodic, int grid, const XShiftArgs& a, const XShiftArgs& b,
+                           cudaStream_t st)
+{
+    if (a.rec == nullptr || a.Nx > 8 * XXS_THREADS || a.stages < 1 || a.stages > 8) return cudaErrorInvalidValue;
+    const size_t smem = xxshift_smem_bytes(a.Nx, a.pad, a.stages, elem_bytes);
+    if (elem_bytes == 2) {
+        if (periodic) xxshift_kernel<bf16, true><<<grid, XXS_THREADS, smem, st>>>(a, b);
+        else xxshift_kernel<bf16, false><<<grid, XXS_THREADS, smem, st>>>(a, b);
+    } else {
+        if (periodic) xxshift_kernel<float, true><<<grid, XXS_THREADS, smem, st>>>(a, b);
+        else xxshift_kernel<float, false><<<grid, XXS_THREADS, smem, st>>>(a, b);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t xxshift_occupancy(int elem_bytes, bool periodic, size_t smem, int* blocks)
+{
+    if (elem_bytes == 2)
+        return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xxshift_kernel<bf16, true>, XXS_THREADS, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xxshift_kernel<bf16, false>, XXS_THREADS, smem);
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xxshift_kernel<float, true>, XXS_THREADS, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xxshift_kernel<float, false>, XXS_THREADS, smem);
 }
 
 int xshift_max_cols(int elem_bytes, int threads)
@@ -688,6 +927,10 @@ cudaError_t set_kernel_attributes(int max_smem)
     VL_ATTR((xshift_kernel<bf16, false, false>));
     VL_ATTR((pshift_kernel<bf16, true>));
     VL_ATTR((pshift_kernel<bf16, false>));
+    VL_ATTR((xxshift_kernel<float, true>));
+    VL_ATTR((xxshift_kernel<float, false>));
+    VL_ATTR((xxshift_kernel<bf16, true>));
+    VL_ATTR((xxshift_kernel<bf16, false>));
 #undef VL_ATTR
     return e;
 }

@@ -267,7 +267,7 @@ int make_tmap(vlasov_sim* s, int b)
                      s->f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(VLASOV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    if (s->fuse_ok) {
+    if (s->fuse_ok && s->fx) {
         // rows of f as 8-element lines; a box of 10 x xbox_h lands as padded lines (2 zero columns)
         cuuint64_t ldims[2] = {8, (cuuint64_t)s->Nx * (cuuint64_t)s->Np / 8};
         cuuint64_t lstrides[1] = {64};
@@ -609,7 +609,8 @@ int enq_xx(vlasov_sim* s, int c, Marks* marks)
     a.ctapart = s->hmf_cta ? s->ctapart_m : nullptr;
     a.colpart64 = s->hmf_cta ? nullptr : s->colpart_m;
     XShiftArgs b = xargs(s, nullptr, s->f[c ^ 1], s->xp, true, false, s->xrec);
-    CU_TRY(launch_xxshift_fx(s->xper, s->xxgrid, &s->xtmap[c], a, b, emargs(s, s->xp, s->xe), s->st));
+    if (s->fx) CU_TRY(launch_xxshift_fx(s->xper, s->xxgrid, &s->xtmap[c], a, b, emargs(s, s->xp, s->xe), s->st));
+    else CU_TRY(launch_xxshift(s->esz, s->xper, s->xxgrid, a, b, s->st));
     MARK();
     return enq_moments(s, s->xxgrid, true, marks);
 }
@@ -878,6 +879,27 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
                 // on by default for periodic rows; on zero-outside rows (sheet) the separate
                 // x-shifts measured faster (each fused row barrier waits for the rows' edge outputs)
                 s->fuse = s->xper;
+            }
+        }
+    } else if (!s->fx && !s->emul && esz <= 4 && Nx <= XXS_MAX_NX) {
+        // FP32-class storage: whole padded rows by bulk copies, as the separate x-shift stages them;
+        // two CTAs per SM (a CTA waits at a barrier every row) with up to three rows in flight each
+        const size_t row = (size_t)(Nx + 2 * s->xpad) * esz;
+        auto stages_in = [&](size_t budget) {
+            return budget > 256 + 2 * row ? (int)std::min<size_t>(3, (budget - 256 - 2 * row) / (row + XREC_BYTES)) : 0;
+        };
+        int st = stages_in((size_t)max_optin / 2 - 2048);
+        if (st < 2) st = stages_in((size_t)max_optin - 2048);
+        if (st >= 2) {
+            int xocc = 0;
+            CTRY(xxshift_occupancy(esz, s->xper, xxshift_smem_bytes(Nx, s->xpad, st, esz), &xocc));
+            if (xocc >= 1) {
+                s->xxstages = st;
+                s->xxgrid = std::min(Np, s->nsm * xocc);
+                s->fuse_ok = true;
+                // on by default for FP32 storage (measured faster on periodic and zero-outside
+                // rows); with BF16 the separate x-shifts measured faster
+                s->fuse = esz == 4;
             }
         }
     }
@@ -1263,7 +1285,8 @@ int vlasov_set_fused_x(vlasov_sim* s, int on)
 {
     if (!s) return fail(VLASOV_EINVAL, "NULL handle");
     if (on && !s->fuse_ok)
-        return fail(VLASOV_EINVAL, "fused x-shifts need VLASOV_FX64 storage and Nx <= %d", XF_FUSED_MAX_NX);
+        return fail(VLASOV_EINVAL, "fused x-shifts need VLASOV_FX64 (Nx <= %d), VLASOV_F32 or VLASOV_BF16 (Nx <= %d) storage",
+                    XF_FUSED_MAX_NX, XXS_MAX_NX);
     s->fuse = on != 0;
     return VLASOV_OK;
 }

@@ -291,6 +291,14 @@ cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks);
 cudaError_t pshift_fx_occupancy(int* blocks);
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                              cudaStream_t st);
+// Fused x-shifts with FP32-class storage (elem_bytes 4: FP32, 2: BF16): 512 threads of 8 columns.
+constexpr int XXS_THREADS = 512;
+constexpr int XXS_MAX_NX = 8 * XXS_THREADS;
+size_t xxshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes);
+cudaError_t launch_xxshift(int elem_bytes, bool periodic, int grid, const XShiftArgs& a, const XShiftArgs& b,
+                           cudaStream_t st);
+cudaError_t xxshift_occupancy(int elem_bytes, bool periodic, size_t smem, int* blocks);
+
 // Fused x-shifts (second half of step n, first half of step n+1) with FX64 storage.
 constexpr int XXF_THREADS_MAX = 512;   // one chunk of 8 columns per thread: Nx <= 4096
 constexpr int XF_FUSED_MAX_NX = 8 * XXF_THREADS_MAX;

@@ -3,7 +3,11 @@ one) run as one launch that keeps the row between them in shared memory.  The ar
 is that of the separate x-shift launches and every cross-CTA sum is exact, so a fused run must give
 the same bits as an unfused one: f, and every moment record.  Also checked here: the full-size
 4096^2 HMF workload in the launch configuration the benchmark times (FX64, fused, several steps)
-against the oracle, and the launch accounting."""
+against the oracle, and the launch accounting.
+
+With FP32 or BF16 storage the fused launch runs the same per-pass arithmetic, but the per-CTA column
+and kinetic sums are FP32 sums over that launch's own row partition: free streaming (no force) must
+still give the same bits, a self-consistent run the same state to within the rounding of those sums."""
 import numpy as np
 import pytest
 
@@ -19,8 +23,8 @@ def grid_of(w: I.Workload) -> O.Grid:
                   w.dt, w.eps, w.G)
 
 
-def run(w, f0, steps, fused, calls=None):
-    with V.Sim.from_workload(w, precision="fx64") as s:
+def run(w, f0, steps, fused, calls=None, precision="fx64"):
+    with V.Sim.from_workload(w, precision=precision) as s:
         s.fused_x = fused
         s.set_f(f0)
         for n in (calls or [steps]):
@@ -102,5 +106,76 @@ def test_launch_accounting_and_timed_slots():
         assert s.kernels_per_step() == 5 and s.launches(10) == 50
     with V.Sim.from_workload(w, precision="f64") as s:
         assert not s.fused_x
+        with pytest.raises(V.VlasovError):
+            s.fused_x = True
+
+
+FREE_PERIODIC = I.Workload("free_periodic", "free", 512, 256, -np.pi, np.pi, -4.0, 4.0, True, False, 0.05, 4)
+FREE_ZERO = I.Workload("free_zero", "free", 256, 128, -8.0, 8.0, -4.0, 4.0, False, False, 2.0, 4)
+
+
+def smooth_f0(w):
+    x = w.xmin + w.dx * np.arange(w.nx)
+    p = w.pmin + w.dp * np.arange(w.np)
+    return np.exp(-0.5 * (x[None, :] / 1.5) ** 2 - (p[:, None] / 1.2) ** 2)
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("w", [FREE_PERIODIC, FREE_ZERO], ids=["periodic", "zero_outside"])
+def test_fp32_class_fused_free_streaming_is_bitwise(w, precision):
+    f0 = smooth_f0(w)
+    fa, ma = run(w, f0, 12, fused=False, precision=precision)
+    fb, mb = run(w, f0, 12, fused=True, precision=precision)
+    assert np.array_equal(fa, fb)
+    assert np.abs(fa).max() > 0.1
+    # mass: per-CTA FP32 column sums of another row partition, then exact fixed-point totals
+    np.testing.assert_allclose(mb[:, 1], ma[:, 1], rtol=1e-6, atol=0)
+
+
+# (tolerance on f relative to max f, tolerance on the mass, on the other moments relative to their scale)
+FP32_CLASS_TOL = {"f32": (1e-5, 1e-6, 1e-5), "bf16": (5e-2, 1e-3, 2e-2)}
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("w", [
+    I.HMF_256.resized(256, 256),
+    I.RING_2048.resized(128, 128),
+    I.SHEET_4096.resized(128, 256),
+    I.HMF_256.resized(320, 328),
+], ids=["hmf", "ring", "sheet", "ragged"])
+def test_fp32_class_fused_run_matches_unfused(w, precision):
+    f0 = I.initial_state(w)
+    steps = 30
+    fa, ma = run(w, f0, steps, fused=False, precision=precision)
+    fb, mb = run(w, f0, steps, fused=True, precision=precision)
+    tf, tm, to = FP32_CLASS_TOL[precision]
+    assert np.max(np.abs(fa - fb)) <= tf * np.abs(fa).max()
+    assert ma.shape == mb.shape == (steps, 8)
+    assert np.array_equal(ma[:, 0], mb[:, 0]) and np.array_equal(ma[:, 7], mb[:, 7])   # t, step
+    assert np.max(np.abs(ma[:, 1] - mb[:, 1])) <= tm * np.abs(ma[:, 1]).max()
+    for col in (2, 3, 4, 5, 6):
+        scale = max(np.abs(ma[:, col]).max(), 1e-3 * np.abs(ma[:, 4]).max())
+        assert np.max(np.abs(ma[:, col] - mb[:, col])) <= to * scale, col
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_fp32_class_fused_defaults_and_accounting(precision):
+    w = I.HMF_256.resized(128, 128)
+    with V.Sim.from_workload(w, precision=precision) as s:
+        s.set_f(I.initial_state(w))
+        assert s.fused_x == (precision == "f32")   # on by default for FP32 storage only
+        s.fused_x = True
+        L = s.kernels_per_step()
+        assert len(s.slot_names()) == L
+        assert s.launches(10) == 10 * (L + 1) - 9   # one x-shift launch saved per step boundary
+        ms = s.step_timed(3)
+        assert ms.shape == (L,) and np.all(ms > 0)
+    w = I.SHEET_4096.resized(128, 256)
+    with V.Sim.from_workload(w, precision=precision) as s:
+        assert s.fused_x == (precision == "f32")
+        s.fused_x = False
+        assert not s.fused_x
+    with V.Sim.from_workload(I.HMF_256.resized(4104, 16), precision=precision) as s:
+        assert not s.fused_x                       # rows longer than 4096 cells: separate x-shifts
         with pytest.raises(V.VlasovError):
             s.fused_x = True
