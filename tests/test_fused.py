@@ -167,7 +167,7 @@ def test_fp32_class_fused_defaults_and_accounting(precision):
         s.fused_x = True
         L = s.kernels_per_step()
         assert len(s.slot_names()) == L
-        assert s.launches(10) == 10 * (L + 1) - 9   # one x-shift launch saved per step boundary
+        assert s.launches(10) == s.launches(2) + 8 * L   # head + n-1 mids + tail
         ms = s.step_timed(3)
         assert ms.shape == (L,) and np.all(ms > 0)
     w = I.SHEET_4096.resized(128, 256)
@@ -175,7 +175,8 @@ def test_fp32_class_fused_defaults_and_accounting(precision):
         assert s.fused_x == (precision == "f32")
         s.fused_x = False
         assert not s.fused_x
-    with V.Sim.from_workload(I.HMF_256.resized(4104, 16), precision=precision) as s:
-        assert not s.fused_x                       # rows longer than 4096 cells: separate x-shifts
-        with pytest.raises(V.VlasovError):
-            s.fused_x = True
+    if precision == "f32":   # (BF16 grids are limited to Nx <= 4096 altogether)
+        with V.Sim.from_workload(I.HMF_256.resized(4104, 16), precision=precision) as s:
+            assert not s.fused_x                   # rows longer than 4096 cells: separate x-shifts
+            with pytest.raises(V.VlasovError):
+                s.fused_x = True
