@@ -60,6 +60,10 @@ constexpr int ALIGN_N = 8;
 
 }  // namespace
 
+// Graph runs: whole steps (or middle pieces of fused steps) are launched in graphs of 2^L of them,
+// L < RUN_LEVELS.
+constexpr int RUN_LEVELS = 6;
+
 struct vlasov_sim {
     int model = 0, Nx = 0, Np = 0, prec = 0, esz = 8;
     int msz = 8;                // bytes of the filter/parameter type: 8 (FP64 modes) or 4 (FP32, BF16 storage)
@@ -125,8 +129,10 @@ struct vlasov_sim {
     CUtensorMap tmap[2];
     CUtensorMap xtmap[2];             // fused x-shifts: f[b] as 8-element lines, boxes of 10 x xbox_h
     int xbox_h = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t ghead[2] = {nullptr, nullptr}, gmid[2] = {nullptr, nullptr}, gtail[2] = {nullptr, nullptr};
+    // per starting buffer: runs of 2^L whole steps, head and tail pieces, runs of 2^L middle pieces
+    cudaGraphExec_t grun[2][RUN_LEVELS] = {};
+    cudaGraphExec_t ghead[2] = {nullptr, nullptr}, gtail[2] = {nullptr, nullptr};
+    cudaGraphExec_t gmid[2][RUN_LEVELS] = {};
 };
 
 namespace {
@@ -361,12 +367,20 @@ int ceil_log2(double v)
 
 void drop_graphs(vlasov_sim* s)
 {
-    for (int b = 0; b < 2; ++b)
-        for (cudaGraphExec_t* g : {&s->graph[b], &s->ghead[b], &s->gmid[b], &s->gtail[b]})
-            if (*g) {
-                cudaGraphExecDestroy(*g);
-                *g = nullptr;
-            }
+    auto drop = [](cudaGraphExec_t* g) {
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    };
+    for (int b = 0; b < 2; ++b) {
+        drop(&s->ghead[b]);
+        drop(&s->gtail[b]);
+        for (int L = 0; L < RUN_LEVELS; ++L) {
+            drop(&s->grun[b][L]);
+            drop(&s->gmid[b][L]);
+        }
+    }
 }
 
 // Fixed-point shifts of the reductions from the largest |f| (bound 2^Ef >= 4 max|f|).  Kernel
@@ -661,16 +675,31 @@ int capture(vlasov_sim* s, cudaGraphExec_t* out, F&& enqueue)
     return VLASOV_OK;
 }
 
-int build_graph(vlasov_sim* s, int c)
+// Graphs of 2^L whole steps from buffer c (L = 0: one step, ending on c^1; L > 0 ends on c).  All
+// levels are captured at the first call from c, so that no capture falls between two launches.
+int build_graphs(vlasov_sim* s, int c)
 {
-    return capture(s, &s->graph[c], [&] { return enqueue_step(s, c); });
+    int rc = VLASOV_OK;
+    for (int L = 0; L < RUN_LEVELS && !rc; ++L)
+        rc = capture(s, &s->grun[c][L], [&] {
+            int r = VLASOV_OK;
+            for (int k = 0; k < (1 << L) && !r; ++k) r = enqueue_step(s, c ^ (k & 1));
+            return r;
+        });
+    return rc;
 }
 
+// Head, tail, and runs of 2^L middle pieces (each from buffer c back into c).
 int build_fused_graphs(vlasov_sim* s, int c)
 {
     int rc = capture(s, &s->ghead[c], [&] { return enqueue_piece(s, c, P_HEAD); });
-    if (!rc) rc = capture(s, &s->gmid[c], [&] { return enqueue_piece(s, c, P_MID); });
     if (!rc) rc = capture(s, &s->gtail[c], [&] { return enqueue_piece(s, c, P_TAIL); });
+    for (int L = 0; L < RUN_LEVELS && !rc; ++L)
+        rc = capture(s, &s->gmid[c][L], [&] {
+            int r = VLASOV_OK;
+            for (int k = 0; k < (1 << L) && !r; ++k) r = enqueue_piece(s, c, P_MID);
+            return r;
+        });
     return rc;
 }
 
@@ -1097,18 +1126,24 @@ int vlasov_step(vlasov_sim* s, int n)
         const int c = s->cur;
         int rc = build_fused_graphs(s, c);
         if (rc) return rc;
+        // one graph launch per run of 2^L middle pieces, largest runs first (a graph launch costs
+        // the stream a few microseconds more than a kernel boundary inside a graph)
         CU_TRY(cudaGraphLaunch(s->ghead[c], s->st));
-        for (int k = 1; k < n; ++k) CU_TRY(cudaGraphLaunch(s->gmid[c], s->st));
+        int m = n - 1;
+        for (int L = RUN_LEVELS - 1; L >= 0; --L)
+            for (; m >= (1 << L); m -= 1 << L) CU_TRY(cudaGraphLaunch(s->gmid[c][L], s->st));
         CU_TRY(cudaGraphLaunch(s->gtail[c], s->st));
         s->cur ^= 1;
         return VLASOV_OK;
     }
-    for (int k = 0; k < n; ++k) {
-        int rc = build_graph(s, s->cur);
-        if (rc) return rc;
-        CU_TRY(cudaGraphLaunch(s->graph[s->cur], s->st));
-        s->cur ^= 1;
-    }
+    int m = n;
+    for (int L = RUN_LEVELS - 1; L >= 0; --L)
+        for (; m >= (1 << L); m -= 1 << L) {
+            int rc = build_graphs(s, s->cur);
+            if (rc) return rc;
+            CU_TRY(cudaGraphLaunch(s->grun[s->cur][L], s->st));
+            if (L == 0) s->cur ^= 1;
+        }
     return VLASOV_OK;
 }
 
