@@ -46,7 +46,8 @@ class _Params(ctypes.Structure):
                 ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
                 ("pmin", ctypes.c_double), ("pmax", ctypes.c_double),
                 ("x_periodic", ctypes.c_int), ("p_periodic", ctypes.c_int),
-                ("eps", ctypes.c_double), ("G", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("G", ctypes.c_double), ("dt", ctypes.c_double),
+                ("spline", ctypes.c_int)]
 
 
 class _Moments(ctypes.Structure):
@@ -68,6 +69,7 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(_Params)
             lib.vo_fd2.argtypes = [dp, ctypes.c_long, ctypes.c_int, ctypes.c_double, dp]
+            lib.vo_gs2.argtypes = [dp, ctypes.c_long, ctypes.c_int, ctypes.c_double, dp]
             lib.vo_spline_shift.argtypes = [dp, dp, ctypes.c_long, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_double, dp]
             for fn in (lib.vo_advect_x, lib.vo_advect_p):
@@ -111,6 +113,7 @@ class Grid:
     dt: float
     eps: float = 0.0
     G: float = 1.0
+    spline: str = "fd"     # "fd": Eq. (findif); "gs": global spline, Eq. (tridiagsys)
 
     @property
     def dx(self) -> float:
@@ -123,7 +126,7 @@ class Grid:
     def _c(self) -> _Params:
         return _Params(_MODEL_IDS[self.model], self.nx, self.np, self.xmin, self.xmax,
                        self.pmin, self.pmax, int(self.x_periodic), int(self.p_periodic),
-                       self.eps, self.G, self.dt)
+                       self.eps, self.G, self.dt, {"fd": 0, "gs": 1}[self.spline])
 
 
 def set_threads(n: int) -> int:
@@ -139,10 +142,20 @@ def fd2(f: np.ndarray, periodic: bool, du: float) -> np.ndarray:
     return out
 
 
-def spline_shift(f: np.ndarray, periodic: bool, du: float, s: float) -> np.ndarray:
-    """Eqs. (findif, splinegen, splinecoeffs) on one line: value at the foot i - s of node i."""
+def gs2(f: np.ndarray, periodic: bool, du: float) -> np.ndarray:
+    """Eq. (tridiagsys) along a 1-D line: the global-spline f'' (cyclic system on periodic lines;
+    f = f'' = 0 at the neighbour nodes -1 and n of a non-periodic line)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
-    d2 = fd2(f, periodic, du)
+    out = np.empty_like(f)
+    _load().vo_gs2(_ptr(f), f.size, int(periodic), float(du), _ptr(out))
+    return out
+
+
+def spline_shift(f: np.ndarray, periodic: bool, du: float, s: float, spline: str = "fd") -> np.ndarray:
+    """Eqs. (splinegen, splinecoeffs) on one line: value at the foot i - s of node i, with f'' from
+    Eq. (findif) (spline="fd") or Eq. (tridiagsys) (spline="gs")."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    d2 = gs2(f, periodic, du) if spline == "gs" else fd2(f, periodic, du)
     out = np.empty_like(f)
     _load().vo_spline_shift(_ptr(f), _ptr(d2), f.size, int(periodic), float(du), float(s), _ptr(out))
     return out

@@ -15,6 +15,10 @@
  *  - The foot of node i is y = i - s (s = displacement in cells).  It is split once per line as
  *    n0 = floor(-s), beta = (-s) - n0, alpha = 1 - beta, so k = i + n0 and alpha equals
  *    (x_{k+1} - x)/(x_{k+1} - x_k) of Eq. splinecoeffs.
+ *  - Global-spline variant (Eq. tridiagsys, used only for the comparison of Tables 1-2): the diagonal
+ *    coefficient printed as 1/3 is read as 2/3, the value the first-derivative continuity the text
+ *    derives it from gives (and the cited Numerical Recipes system, (x_{i+1}-x_{i-1})/3 = 2 du/3).
+ *    Non-periodic lines solve it for the n grid nodes with f = f'' = 0 at the neighbours -1 and n.
  *  - The force is the rectangle rule of Eq. meanforce on the x nodes.  Ring: kernel
  *    V'(u) = sin u / (2 sqrt 2 (1 - cos u + eps)^{3/2}) at u = (i-k) dx.  Sheet: V = 2 pi G |x-x'|,
  *    so F_i = -2 pi G dx (sum_{k<i} rho_k - sum_{k>i} rho_k).
@@ -67,6 +71,69 @@ void vo_fd2(const double* f, long n, int periodic, double du, double* d2)
     }
 }
 
+/* ---------------------------------------------------------------- Sec. 3, Eq. (tridiagsys) */
+/* Tridiagonal solve (sub a, diagonal b, super c, all constant) of n unknowns by elimination and
+   back substitution; r is overwritten by the solution, w is n doubles of scratch. */
+static void tridiag_const(double a, double b, double c, double* r, long n, double* w)
+{
+    double den = b;
+    r[0] /= den;
+    for (long k = 1; k < n; ++k) {
+        w[k] = c / den;
+        den = b - a * w[k];
+        r[k] = (r[k] - a * r[k - 1]) / den;
+    }
+    for (long k = n - 2; k >= 0; --k) r[k] -= w[k + 1] * r[k + 1];
+}
+
+void vo_gs2(const double* f, long n, int periodic, double du, double* d2)
+{
+    const double a = 1.0 / 6.0, b = 2.0 / 3.0, c = 1.0 / 6.0;   /* times du^2 on the left */
+    const double inv = 1.0 / (du * du);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    for (long k = 0; k < n; ++k)
+        d2[k] = (at(f, n, periodic, k + 1) - 2.0 * f[k] + at(f, n, periodic, k - 1)) * inv;
+    if (!periodic) {
+        tridiag_const(a, b, c, d2, n, w);
+        free(w);
+        return;
+    }
+    /* Cyclic system: corners A[0][n-1] = a, A[n-1][0] = c.  Sherman-Morrison: A = A' + u v^T with
+       u = (g, 0, .., 0, c), v = (1, 0, .., 0, a/g), g = -b; A' is A without corners and with the
+       diagonal ends b - g and b - c a / g (a general tridiagonal solve, written out here). */
+    const double g = -b;
+    double* y = d2;
+    double* z = (double*)malloc(sizeof(double) * (size_t)n);
+    double* diag = (double*)malloc(sizeof(double) * (size_t)n);
+    for (long k = 0; k < n; ++k) {
+        diag[k] = b;
+        z[k] = 0.0;
+    }
+    diag[0] = b - g;
+    diag[n - 1] = b - c * a / g;
+    z[0] = g;
+    z[n - 1] = c;
+    /* forward elimination for both right-hand sides */
+    double den = diag[0];
+    y[0] /= den;
+    z[0] /= den;
+    for (long k = 1; k < n; ++k) {
+        w[k] = c / den;
+        den = diag[k] - a * w[k];
+        y[k] = (y[k] - a * y[k - 1]) / den;
+        z[k] = (z[k] - a * z[k - 1]) / den;
+    }
+    for (long k = n - 2; k >= 0; --k) {
+        y[k] -= w[k + 1] * y[k + 1];
+        z[k] -= w[k + 1] * z[k + 1];
+    }
+    const double fac = (y[0] + a / g * y[n - 1]) / (1.0 + z[0] + a / g * z[n - 1]);
+    for (long k = 0; k < n; ++k) y[k] -= fac * z[k];
+    free(z);
+    free(diag);
+    free(w);
+}
+
 /* ---------------------------------------------------------------- Sec. 3, Eqs. (splinegen, splinecoeffs) */
 void vo_spline_shift(const double* f, const double* d2, long n, int periodic, double du,
                      double s, double* out)
@@ -97,7 +164,8 @@ void vo_advect_x(const vo_params* P, const double* f, const double* s_row, doubl
 #pragma omp for schedule(static)
         for (long j = 0; j < np; ++j) {
             const double* row = f + (size_t)j * nx;
-            vo_fd2(row, nx, P->x_periodic, dx, d2);
+            if (P->spline) vo_gs2(row, nx, P->x_periodic, dx, d2);
+            else vo_fd2(row, nx, P->x_periodic, dx, d2);
             vo_spline_shift(row, d2, nx, P->x_periodic, dx, s_row[j], out + (size_t)j * nx);
         }
         free(d2);
@@ -117,7 +185,8 @@ void vo_advect_p(const vo_params* P, const double* f, const double* s_col, doubl
 #pragma omp for schedule(static)
         for (long i = 0; i < nx; ++i) {
             for (long j = 0; j < np; ++j) col[j] = f[(size_t)j * nx + i];
-            vo_fd2(col, np, P->p_periodic, dp, d2);
+            if (P->spline) vo_gs2(col, np, P->p_periodic, dp, d2);
+            else vo_fd2(col, np, P->p_periodic, dp, d2);
             vo_spline_shift(col, d2, np, P->p_periodic, dp, s_col[i], res);
             for (long j = 0; j < np; ++j) out[(size_t)j * nx + i] = res[j];
         }

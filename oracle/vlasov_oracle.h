@@ -27,6 +27,8 @@ typedef struct {
     double eps;                /* ring softening, Eq. (ringpot) */
     double G;                  /* sheet coupling: V = 2*pi*G*|x - x'| */
     double dt;                 /* time step */
+    int spline;                /* 0: f'' by Eq. (findif) (the paper's method); 1: global spline,
+                                  f'' from the tridiagonal system of Eq. (tridiagsys) */
 } vo_params;
 
 typedef struct {
@@ -35,6 +37,12 @@ typedef struct {
 
 /* Eq. (findif): f''_k = (1/du^2) sum_{m=-4..4} c_|m| f_{k+m} along one line of n points. */
 void vo_fd2(const double* f, long n, int periodic, double du, double* d2);
+
+/* Eq. (tridiagsys), the global cubic spline the paper compares against (Tables 1-2): f'' of the
+   n nodes from (f''_{k-1}/6 + 2 f''_k/3 + f''_{k+1}/6) du^2 = f_{k+1} - 2 f_k + f_{k-1}.
+   Periodic lines: the cyclic system.  Non-periodic lines: f = 0 and f'' = 0 at the nodes -1 and n
+   next to the grid (a natural spline through the zero-extended data), f'' = 0 further out. */
+void vo_gs2(const double* f, long n, int periodic, double du, double* d2);
 
 /* Eqs. (splinegen, splinecoeffs): value at the foot y_i = i - s (s in cells) of every node i. */
 void vo_spline_shift(const double* f, const double* d2, long n, int periodic, double du,

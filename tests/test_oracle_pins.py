@@ -355,3 +355,88 @@ def test_entropy_is_conserved_by_integer_free_streaming_and_maximal_for_the_box(
     assert O.entropy(g, O.advect_x(g, f, s)) == pytest.approx(O.entropy(g, f), rel=1e-13)
     box = np.full_like(f, f.mean())
     assert O.entropy(g, box) > O.entropy(g, f)
+
+
+# ----------------------------------------------------------------------------- global spline (Eq. tridiagsys)
+# The comparison method of Tables 1-2.  Pinned against an independent cubic-spline library (SciPy's
+# CubicSpline: periodic end conditions, and natural end conditions on the knots -1..n with zero
+# data there), against the closed-form symbol of the cyclic system, and by exact integer shifts.
+
+def _scipy_spline_shift(f, periodic, du, s):
+    interpolate = pytest.importorskip("scipy.interpolate")
+    n = f.size
+    x = np.arange(n) * du
+    if periodic:
+        cs = interpolate.CubicSpline(np.append(x, n * du), np.append(f, f[0]), bc_type="periodic")
+        return cs(np.mod(x - s * du, n * du))
+    xe = np.arange(-1, n + 1) * du
+    cs = interpolate.CubicSpline(xe, np.concatenate([[0.0], f, [0.0]]), bc_type="natural")
+    y = x - s * du
+    return np.where((y >= -du) & (y <= n * du), cs(np.clip(y, -du, n * du)), 0.0)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("s", [0.3, -2.7, 5.25, -0.999, 17.5])
+def test_gs_shift_matches_library_cubic_spline(periodic, s):
+    rng = np.random.default_rng(11)
+    n = 96
+    du = 0.07
+    f = rng.standard_normal(n)
+    got = O.spline_shift(f, periodic, du, s, spline="gs")
+    ref = _scipy_spline_shift(f, periodic, du, s)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("q", [1, 3, 10, 31])
+def test_gs_second_derivative_symbol_on_periodic_modes(q):
+    """cos(q x) on n periodic nodes: the cyclic system gives f'' = lambda f with
+    lambda = (6/du^2)(2 cos th - 2)/(4 + 2 cos th), th = q du (Fourier symbol of Eq. tridiagsys)."""
+    n = 128
+    du = 2 * math.pi / n
+    x = np.arange(n) * du
+    th = q * du
+    lam = 6.0 / du**2 * (2 * math.cos(th) - 2) / (4 + 2 * math.cos(th))
+    for f in (np.cos(q * x), np.sin(q * x)):
+        got = O.gs2(f, True, du)
+        assert np.max(np.abs(got - lam * f)) <= 1e-12 * abs(lam)
+
+
+def test_gs_tends_to_the_exact_second_derivative_and_differs_from_fd():
+    """Smooth periodic data: the spline's nodal f'' is second-order accurate (symbol -k^2 (1 + th^2/12)),
+    Eq. findif eighth-order: two different f'' whose errors shrink at their own rates."""
+    errs_gs, errs_fd = [], []
+    for n in (16, 32):
+        du = 2 * math.pi / n
+        x = np.arange(n) * du
+        f = np.sin(x)
+        errs_gs.append(np.max(np.abs(O.gs2(f, True, du) + f)))
+        errs_fd.append(np.max(np.abs(O.fd2(f, True, du) + f)))
+    assert 3.8 < errs_gs[0] / errs_gs[1] < 4.2    # O(du^2)
+    assert errs_fd[0] / errs_fd[1] > 200           # O(du^8)
+
+
+def test_gs_free_streaming_integer_cells_is_exact():
+    """Integer shifts reproduce the data exactly for the global spline too (beta = 0)."""
+    nx, npp = 64, 32
+    dx = 2 * math.pi / nx
+    dp = 1.0 / 32
+    dt = 2 * dx / dp
+    g = O.Grid("free", nx, npp, -math.pi, math.pi, -(npp // 2) * dp, (npp // 2) * dp, True, False, dt,
+               spline="gs")
+    rng = np.random.default_rng(4)
+    f0 = rng.uniform(0, 1, (npp, nx))
+    f, _ = O.run(g, f0, 3, with_moments=False)
+    expect = np.stack([np.roll(f0[j], 3 * 2 * (j - npp // 2)) for j in range(npp)])
+    assert np.max(np.abs(f - expect)) <= 1e-13 * f0.max()
+
+
+def test_gs_run_conserves_mass_on_the_paper_waterbag():
+    """HMF 256^2, 200 steps with the global spline: mass to rounding, energy drift of Table 1 size."""
+    w = I.HMF_256
+    g = O.Grid(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.x_periodic, w.p_periodic,
+               w.dt, w.eps, w.G, spline="gs")
+    f0 = I.initial_state(w)
+    m0 = O.moments(g, f0)
+    _, hist = O.run(g, f0, w.steps)
+    assert np.max(np.abs(hist[:, 1] - m0["mass"])) <= 1e-12
+    assert np.max(np.abs(hist[:, 6] - m0["energy"])) / abs(m0["energy"]) <= 1e-2
