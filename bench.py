@@ -437,6 +437,36 @@ def main():
                             "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(s2.slot_names(), sl2)}}
             s2.close()
 
+    # ---- secondary: the global-spline variant (Eq. tridiagsys, Tables 1-2) on the same workload.
+    # Its sweeps run a 64-tap filter per output in IEEE arithmetic: bound by the FP64 pipe (FP64) or
+    # by shared-memory reads (FP32); the roofline below is the x-shift's multiply-add rate against
+    # the nominal FP64 rate (2 DFMA/clock/SM) or FP32 rate (128 FFMA/clock/SM) at 152 SMs, 2070 MHz.
+    gspline = {}
+    if not args.no_f32:
+        for prec, peak_tfma in (("f64_native", 152 * 2 * 2.07e9 / 1e12), ("f32", 152 * 128 * 2.07e9 / 1e12)):
+            s2 = V.Sim.from_workload(w, precision=prec, stream=stream.cuda_stream)
+            s2.spline = "gs"
+            s2.set_f(f0)
+            s2.step(2)
+            s2.sync()
+            k2 = min(args.steps, 10)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            s2.step(k2)
+            a1.record(stream)
+            a1.synchronize()
+            ms2 = a0.elapsed_time(a1) / k2
+            sl2 = dict(zip(s2.slot_names(), s2.step_timed(2)))
+            tx = float(sl2["xshift_step1"])
+            ach = cells * 64 / (tx * 1e-3) / 1e12
+            gspline[prec] = {"value": world * cells / (ms2 * 1e-3), "ms_per_step": ms2,
+                             "per_kernel_ms": {n: round(float(v), 5) for n, v in sl2.items()},
+                             "roofline": {"bound": "alu", "kernel": "gs_xshift", "achieved": ach, "peak": peak_tfma,
+                                          "unit": "TFMA/s", "frac": ach / peak_tfma,
+                                          "peak_source": "nominal unit count x max SM clock"}}
+            s2.close()
+
     serving = None
     if not args.no_serve and rank == 0:
         ref_mode = "fx64" if args.precision == "f32" else args.precision
@@ -468,6 +498,7 @@ def main():
                                  "M": float(np.hypot(hist[-1, 2], hist[-1, 3])), "energy": float(hist[-1, 6])}
                 if len(hist) else None,
                 "other_precisions": others,
+                "global_spline": gspline,
                 "casimirs": casimirs,
                 "serving": serving}
         print(json.dumps(line), flush=True)

@@ -110,6 +110,19 @@ int vlasov_get_f_device(vlasov_sim* sim, double* dev_f);
    The state between calls is always a whole step. */
 int vlasov_step(vlasov_sim* sim, int n);
 
+/* Spline of every shift.  VLASOV_SPLINE_FD (default): the paper's method, f'' from the eighth-order
+   9-point difference of Eq. (findif).  VLASOV_SPLINE_GS: the global cubic spline the paper compares
+   it with (Sec. 3, Eq. tridiagsys; Tables 1-2): f'' solves the tridiagonal system of a line, cyclic
+   on a periodic axis; on a zero-outside axis the natural spline through the data extended by zeros
+   (f = f'' = 0 at the nodes next to the grid; the system's diagonal read as 2/3, the value the
+   first-derivative continuity of its derivation gives).  GS runs in IEEE arithmetic of the storage
+   type: VLASOV_F64_NATIVE or VLASOV_F32 storage, 64 <= Nx <= 8192, Np >= 64 (else VLASOV_EINVAL),
+   and turns the fused x-shifts off.  Waits for the handle's stream; later steps and substeps use it.
+   vlasov_spline reports the current choice. */
+enum { VLASOV_SPLINE_FD = 0, VLASOV_SPLINE_GS = 1 };
+int vlasov_set_spline(vlasov_sim* sim, int spline);
+int vlasov_spline(const vlasov_sim* sim);
+
 /* Turn the fused x-shifts on (1) or off (0).  Available with VLASOV_FX64 storage (Nx <= 4096 and
    a multiple of 64; on by default when x is periodic) and with VLASOV_F32 or VLASOV_BF16 storage
    (Nx <= 4096; on by default for VLASOV_F32).  Elsewhere asking for them returns VLASOV_EINVAL.

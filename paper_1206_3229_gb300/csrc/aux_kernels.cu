@@ -544,6 +544,7 @@ __device__ __forceinline__ void pparams_fixed(const PParamsArgs& a, int i, doubl
     const uint64_t be = (uint64_t)(V & (((i128)1 << 62) - 1));   // beta 2^62 in [0, 2^62)
     const uint64_t al = (1ull << 62) - be;                         // alpha = 1 - beta
     const long long g = spline_cubic62(al), d = spline_cubic62(be);
+    if (a.beta) a.beta[i] = fx128_to_f64((i128)be, 62);
     // W = the alpha/beta taps + g D_k (taps 0..8) + d D_{k+1} (taps 1..9), each exact on the 2^-62 grid
     const long long C[5] = {FD60_C0, FD60_C1, FD60_C2, FD60_C3, FD60_C4};
     long long Wg[NTAP], Wd[NTAP], W[NTAP];
@@ -616,6 +617,7 @@ __device__ __forceinline__ void pparams_f32(const PParamsArgs& a, int i, double 
     const double ms = -sigma;
     const double fl = floor(ms);
     const double beta = ms - fl;
+    if (a.beta) a.beta[i] = beta;
     T* w = static_cast<T*>(a.w);
     T* gd = static_cast<T*>(a.gd);
     a.n0[i] = (int)fl;

@@ -718,6 +718,235 @@ cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int
                : launch_x<float, false, false>(grid, threads, a, st);
 }
 
+// ============================================================================ global spline
+// The comparison method of the paper's Tables 1-2 (Eq. tridiagsys): the spline whose f'' solves
+// the tridiagonal system instead of Eq. findif, as a filter of GS_TAPS taps over the line extended
+// periodically or oddly about the nodes -1 and n (the constants' header gives the derivation).
+// IEEE arithmetic in the storage type S (double or float); the filter taps are formed in FP64.
+
+// Tap t < GS_TAPS of a line with foot fraction beta.
+__device__ __forceinline__ double gs_tap(double beta, const double* __restrict__ h, int t)
+{
+    const double alpha = 1.0 - beta;
+    const double gm = (alpha * alpha * alpha - alpha) / 6.0, dl = (beta * beta * beta - beta) / 6.0;
+    const int u = t - GS_R - 1;
+    double w = (u == 0 ? alpha : 0.0) + (u == 1 ? beta : 0.0);
+    if (u <= GS_R + 1) w += gm * h[u + GS_R + 1];
+    if (u - 1 >= -GS_R - 1) w += dl * h[u + GS_R];
+    return w;
+}
+
+// Value of the extended line at node q (|q| within one halo of the grid): periodic wrap, or the odd
+// extension about -1 and n of a zero-outside line (0 where the reflection leaves the grid: such
+// nodes feed only outputs whose foot lies outside, which are 0).
+template <typename S, bool PER>
+__device__ __forceinline__ S gs_ext(const S* __restrict__ line, long long stride, int q, int n)
+{
+    if (q >= 0 && q < n) return line[(long long)q * stride];
+    if constexpr (PER) {
+        int r = q % n;
+        if (r < 0) r += n;
+        return line[(long long)r * stride];
+    } else {
+        if (q == -1 || q == n) return S(0);
+        const int m = q < 0 ? -2 - q : 2 * n - q;
+        return (m >= 0 && m < n) ? S(-line[(long long)m * stride]) : S(0);
+    }
+}
+
+// x: rows strided over the CTAs; a row and its GS_HALO extended nodes each side in shared memory,
+// thread t owns columns t + c blockDim (c < GS_XCH: coalesced, conflict-free window reads), with the
+// density (and kinetic) partials of the same forms as the spline x-shift.
+template <typename S, bool PERIODIC, bool KIN>
+__global__ void __launch_bounds__(GS_XTHREADS) gs_xshift_kernel(XShiftArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    const int Nx = a.Nx, Np = a.Np, tid = threadIdx.x, nthreads = blockDim.x;
+    S* ext = reinterpret_cast<S*>(smem_dyn);
+    S* W = ext + Nx + 2 * GS_HALO;
+    __shared__ double red[32];
+    const S* __restrict__ fin = static_cast<const S*>(a.fin);
+    S* __restrict__ fout = static_cast<S*>(a.fout);
+    S colacc[GS_XCH];
+#pragma unroll
+    for (int c = 0; c < GS_XCH; ++c) colacc[c] = S(0);
+    double kin = 0.0;
+    for (int r = blockIdx.x; r < Np; r += gridDim.x) {
+        const S* row = fin + (size_t)r * Nx;
+        for (int q = tid; q < Nx + 2 * GS_HALO; q += nthreads) ext[q] = gs_ext<S, PERIODIC>(row, 1, q - GS_HALO, Nx);
+        if (tid < GS_TAPS) W[tid] = (S)gs_tap(a.beta[r], a.gs_h, tid);
+        const int n0 = a.n0[r];
+        __syncthreads();
+        // FP32: the row's taps in registers (one shared-memory read per multiply-add); FP64 taps
+        // would take 128 registers and stay in shared memory
+        constexpr int WR = sizeof(S) == 4 ? GS_TAPS : 1;
+        S wr[WR];
+        if constexpr (sizeof(S) == 4) {
+#pragma unroll
+            for (int t = 0; t < GS_TAPS; ++t) wr[t] = W[t];
+        }
+        S rowsum = S(0);
+        S* orow = fout + (size_t)r * Nx;
+#pragma unroll
+        for (int c = 0; c < GS_XCH; ++c) {
+            const int i = tid + c * nthreads;
+            if (i < Nx) {
+                int k = i + n0;
+                S out = S(0);
+                if constexpr (PERIODIC) {
+                    k %= Nx;
+                    if (k < 0) k += Nx;
+                }
+                if (PERIODIC || (k >= -1 && k < Nx)) {
+                    const S* e = ext + k + 1;   // extended node k - GS_R - 1
+                    S acc = S(0);
+                    if constexpr (sizeof(S) == 4) {
+#pragma unroll
+                        for (int t = 0; t < GS_TAPS; ++t) acc = fma(wr[t], e[t], acc);
+                    } else {
+#pragma unroll 16
+                        for (int t = 0; t < GS_TAPS; ++t) acc = fma(W[t], e[t], acc);
+                    }
+                    out = acc;
+                }
+                orow[i] = out;
+                colacc[c] += out;
+                rowsum += out;
+            }
+        }
+        if constexpr (KIN) {
+            const double pj = a.pmin + (double)r * a.dp;
+            kin += 0.5 * pj * pj * (double)rowsum;
+        }
+        __syncthreads();   // every thread done with this row's nodes and taps
+    }
+    // column sums in the forms of the spline x-shift: exact int64 atomics, int64 or FP64 CTA rows
+#pragma unroll
+    for (int c = 0; c < GS_XCH; ++c) {
+        const int i = tid + c * nthreads;
+        if (i >= Nx) continue;
+        long long q;
+        if constexpr (sizeof(S) == 8) q = (long long)fx128_from_f64((double)colacc[c], a.k_col);
+        else q = (long long)fx128_from_f32((float)colacc[c], a.k_col);
+        if (a.colacc) atomicAdd(a.colacc + i, (unsigned long long)q);
+        else if (a.colpart64) a.colpart64[(size_t)blockIdx.x * Nx + i] = q;
+        else if (a.colpart) a.colpart[(size_t)blockIdx.x * Nx + i] = (double)colacc[c];
+    }
+    if constexpr (KIN) kin_epilogue(a, kin, red);
+}
+
+// p: tiles of 32 columns x GS_PTH rows; the union of the columns' windows (GS_PROWS rows at most,
+// else straight from global memory) and each column's taps in shared memory; lane = column.
+template <typename S, bool PPER>
+__global__ void __launch_bounds__(256) gs_pshift_kernel(PShiftArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    S* stage = reinterpret_cast<S*>(smem_dyn);   // [GS_PROWS][32]
+    S* W = stage + GS_PROWS * 32;                 // [GS_TAPS][32]
+    const S* __restrict__ fin = static_cast<const S*>(a.fin);
+    S* __restrict__ fout = static_cast<S*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntx = (Nx + 31) / 32, nty = (Np + GS_PTH - 1) / GS_PTH;
+    for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+        const int i = (tile % ntx) * 32 + lane, j0 = (tile / ntx) * GS_PTH;
+        const bool colok = i < Nx;
+        const int n0 = colok ? a.n0[i] : 0;
+        int kmin = colok ? n0 : 0x7fffffff, kmax = colok ? n0 : (int)0x80000000;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        const int r0 = j0 + kmin - GS_R - 1;
+        const long long rows = (long long)GS_PTH + GS_TAPS + ((long long)kmax - kmin);
+        const bool staged = rows <= GS_PROWS;
+        if (staged) {
+            for (int q = warp; q < (int)rows; q += 8)
+                stage[q * 32 + lane] = colok ? gs_ext<S, PPER>(fin + i, Nx, r0 + q, Np) : S(0);
+        }
+        const double be = colok ? a.beta[i] : 0.0;
+        for (int t = warp; t < GS_TAPS; t += 8) W[t * 32 + lane] = (S)gs_tap(be, a.gs_h, t);
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < GS_PTH / 8; ++q) {
+            const int j = j0 + warp * (GS_PTH / 8) + q;
+            if (!colok || j >= Np) continue;
+            const int k = j + n0;
+            S out = S(0);
+            if (PPER || (k >= -1 && k < Np)) {
+                S acc = S(0);
+                if (staged) {
+                    const S* e = stage + (k - GS_R - 1 - r0) * 32 + lane;
+#pragma unroll 16
+                    for (int t = 0; t < GS_TAPS; ++t) acc = fma(W[t * 32 + lane], e[t * 32], acc);
+                } else {
+#pragma unroll 4
+                    for (int t = 0; t < GS_TAPS; ++t)
+                        acc = fma(W[t * 32 + lane], gs_ext<S, PPER>(fin + i, Nx, k - GS_R - 1 + t, Np), acc);
+                }
+                out = acc;
+            }
+            fout[(size_t)j * Nx + i] = out;
+        }
+        __syncthreads();   // before the next tile's rows and taps
+    }
+}
+
+size_t gs_xshift_smem_bytes(int Nx, int elem_bytes)
+{
+    return (size_t)(Nx + 2 * GS_HALO + GS_TAPS) * (size_t)elem_bytes;
+}
+
+size_t gs_pshift_smem_bytes(int elem_bytes) { return (size_t)(GS_PROWS + GS_TAPS) * 32 * (size_t)elem_bytes; }
+
+cudaError_t launch_gs_xshift(int elem_bytes, bool periodic, bool kin, int grid, const XShiftArgs& a, cudaStream_t st)
+{
+    if (a.beta == nullptr || a.gs_h == nullptr || a.Nx > GS_XTHREADS * GS_XCH || a.Nx < GS_MIN_N)
+        return cudaErrorInvalidValue;
+    const size_t smem = gs_xshift_smem_bytes(a.Nx, elem_bytes);
+    const int T = GS_XTHREADS;
+    if (elem_bytes == 8) {
+        if (periodic) kin ? gs_xshift_kernel<double, true, true><<<grid, T, smem, st>>>(a)
+                          : gs_xshift_kernel<double, true, false><<<grid, T, smem, st>>>(a);
+        else kin ? gs_xshift_kernel<double, false, true><<<grid, T, smem, st>>>(a)
+                 : gs_xshift_kernel<double, false, false><<<grid, T, smem, st>>>(a);
+    } else if (elem_bytes == 4) {
+        if (periodic) kin ? gs_xshift_kernel<float, true, true><<<grid, T, smem, st>>>(a)
+                          : gs_xshift_kernel<float, true, false><<<grid, T, smem, st>>>(a);
+        else kin ? gs_xshift_kernel<float, false, true><<<grid, T, smem, st>>>(a)
+                 : gs_xshift_kernel<float, false, false><<<grid, T, smem, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gs_pshift(int elem_bytes, bool p_periodic, int grid, const PShiftArgs& a, cudaStream_t st)
+{
+    if (a.beta == nullptr || a.gs_h == nullptr || a.Np < GS_MIN_N) return cudaErrorInvalidValue;
+    const size_t smem = gs_pshift_smem_bytes(elem_bytes);
+    if (elem_bytes == 8) {
+        if (p_periodic) gs_pshift_kernel<double, true><<<grid, 256, smem, st>>>(a);
+        else gs_pshift_kernel<double, false><<<grid, 256, smem, st>>>(a);
+    } else if (elem_bytes == 4) {
+        if (p_periodic) gs_pshift_kernel<float, true><<<grid, 256, smem, st>>>(a);
+        else gs_pshift_kernel<float, false><<<grid, 256, smem, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gs_occupancy(int elem_bytes, bool xdir, size_t smem, int* blocks)
+{
+    if (xdir)
+        return elem_bytes == 8
+                   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, gs_xshift_kernel<double, true, true>, GS_XTHREADS, smem)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, gs_xshift_kernel<float, true, true>, GS_XTHREADS, smem);
+    return elem_bytes == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, gs_pshift_kernel<double, false>, 256, smem)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, gs_pshift_kernel<float, false>, 256, smem);
+}
+
 // ============================================================================ p-shift
 template <typename S, bool PPER>
 __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const PShiftArgs& a)
@@ -927,6 +1156,18 @@ cudaError_t set_kernel_attributes(int max_smem)
     VL_ATTR((xshift_kernel<bf16, false, false>));
     VL_ATTR((pshift_kernel<bf16, true>));
     VL_ATTR((pshift_kernel<bf16, false>));
+    VL_ATTR((gs_xshift_kernel<double, true, true>));
+    VL_ATTR((gs_xshift_kernel<double, true, false>));
+    VL_ATTR((gs_xshift_kernel<double, false, true>));
+    VL_ATTR((gs_xshift_kernel<double, false, false>));
+    VL_ATTR((gs_xshift_kernel<float, true, true>));
+    VL_ATTR((gs_xshift_kernel<float, true, false>));
+    VL_ATTR((gs_xshift_kernel<float, false, true>));
+    VL_ATTR((gs_xshift_kernel<float, false, false>));
+    VL_ATTR((gs_pshift_kernel<double, true>));
+    VL_ATTR((gs_pshift_kernel<double, false>));
+    VL_ATTR((gs_pshift_kernel<float, true>));
+    VL_ATTR((gs_pshift_kernel<float, false>));
     VL_ATTR((xxshift_kernel<float, true>));
     VL_ATTR((xxshift_kernel<float, false>));
     VL_ATTR((xxshift_kernel<bf16, true>));

@@ -84,6 +84,9 @@ struct vlasov_sim {
     void* xrec = nullptr;       // [Np] XRec of the fixed x rows
     void* srec = nullptr;       // [max(Nx, Np)] XRec scratch for x substeps
     int xthreads = 256, xstages = 1, xpad = 16, xgrid = 1, pgrid = 1, crgrid = 1;
+    bool gs = false;            // global-spline sweeps (vlasov_set_spline)
+    double* gs_h = nullptr;     // [GS_HTAPS] their filter h
+    int gspgrid = 0;
 
     double* colpart = nullptr;  // [xgrid][Nx]
     unsigned long long* colacc = nullptr;  // [Nx] exact column sums added by the x-shift
@@ -142,6 +145,7 @@ void free_params(LineParamsDev& p)
     cudaFree(p.n0);
     cudaFree(p.w);
     cudaFree(p.gd);
+    cudaFree(p.beta);
     p = LineParamsDev{};
 }
 
@@ -150,6 +154,7 @@ int alloc_params(LineParamsDev& p, int n, int esz)
     CU_TRY(cudaMalloc(&p.n0, sizeof(int) * (size_t)n));
     CU_TRY(cudaMalloc(&p.w, (size_t)esz * NTAP * (size_t)n));
     CU_TRY(cudaMalloc(&p.gd, (size_t)esz * 2 * (size_t)n));
+    CU_TRY(cudaMalloc(&p.beta, sizeof(double) * (size_t)n));
     return VLASOV_OK;
 }
 
@@ -212,12 +217,13 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
         CU_TRY(cudaStreamSynchronize(s->st));
     }
     std::vector<int> n0(n);
-    std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n), we((size_t)2 * NTAP * n);
+    std::vector<double> w((size_t)NTAP * n), gd(2 * (size_t)n), we((size_t)2 * NTAP * n), beta(n);
     int mx = 0;
     for (int l = 0; l < n; ++l) {
         LineSplit L;
         line_split(disp[l], L);
         n0[l] = L.n0;
+        beta[l] = L.beta;
         mx = std::max(mx, std::abs(L.n0));
         for (int t = 0; t < NTAP; ++t) w[(size_t)t * n + l] = L.w[t];
         gd[l] = L.g;
@@ -229,6 +235,7 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
     }
     if (max_abs_n0) *max_abs_n0 = mx;
     CU_TRY(cudaMemcpyAsync(p.n0, n0.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s->st));
+    CU_TRY(cudaMemcpyAsync(p.beta, beta.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s->st));
     if ((s->emul || s->fx) && e) {
         std::vector<int> Wh(w.size());
         std::vector<float> wl(w.size()), wf(w.size());
@@ -319,6 +326,8 @@ XShiftArgs xargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.pmin = s->pmin;
     a.dp = s->dp;
     a.err = s->err;
+    a.beta = p.beta;
+    a.gs_h = s->gs_h;
     return a;
 }
 
@@ -333,6 +342,8 @@ PShiftArgs pargs(vlasov_sim* s, const void* in, void* out, const LineParamsDev& 
     a.w = p.w;
     a.gd = p.gd;
     a.err = s->err;
+    a.beta = p.beta;
+    a.gs_h = s->gs_h;
     return a;
 }
 
@@ -427,6 +438,7 @@ EmulArgs emargs(vlasov_sim* s, const LineParamsDev& p, const EmulParamsDev& e)
 
 cudaError_t run_xshift(vlasov_sim* s, const XShiftArgs& a, const LineParamsDev& p, const EmulParamsDev& e, bool kin)
 {
+    if (s->gs) return launch_gs_xshift(s->esz, s->xper, kin, s->xgrid, a, s->st);   // partials: xgrid rows
     if (s->fx) return launch_xshift_fx(s->xper, kin, s->xgrid, s->xthreads, a, emargs(s, p, e), s->st);
     if (s->emul) return launch_xshift_e(s->xper, kin, s->xgrid, s->xthreads, a, emargs(s, p, e), s->st);
     return launch_xshift(s->esz, s->xper, kin, s->xgrid, s->xthreads, a, s->st);
@@ -435,6 +447,7 @@ cudaError_t run_xshift(vlasov_sim* s, const XShiftArgs& a, const LineParamsDev& 
 cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs& a, const LineParamsDev& p,
                        const EmulParamsDev& e)
 {
+    if (s->gs) return launch_gs_pshift(s->esz, s->pper, s->gspgrid, a, s->st);
     if (s->fx) return launch_pshift_fx(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
     if (s->emul) return launch_pshift_e(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
     return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, s->st);
@@ -516,6 +529,7 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int 
     a.Whe = (s->emul || s->fx) ? s->pe.Whe : nullptr;
     a.wle = (s->emul || s->fx) ? s->pe.wle : nullptr;
     a.wfe = (s->emul || s->fx) ? s->pe.wfe : nullptr;
+    a.beta = s->gs ? s->pp.beta : nullptr;
     if (from_cta) {
         a.ctapart = s->ctapart;
         a.ctas = ctas > 0 ? ctas : s->xgrid;
@@ -748,7 +762,7 @@ void vlasov_destroy(vlasov_sim* s)
     void* bufs[] = {s->colpart, s->colacc, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
                     s->hist, s->dstep, s->err, s->xrec, s->srec, s->cos50, s->sin50, s->ctapart,
-                    s->ctapart_m, s->colpart_m, s->kin128};
+                    s->ctapart_m, s->colpart_m, s->kin128, s->gs_h};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -990,6 +1004,10 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
                 dV[i] = V[i] = 0.0;
             }
         }
+        double h[GS_HTAPS];
+        gs_filter_h(h);
+        CTRY(cudaMalloc(&s->gs_h, sizeof h));
+        CTRY(cudaMemcpy(s->gs_h, h, sizeof h, cudaMemcpyHostToDevice));
         CTRY(cudaMalloc(&s->costab, sizeof(double) * Nx));
         CTRY(cudaMalloc(&s->sintab, sizeof(double) * Nx));
         CTRY(cudaMalloc(&s->cosfx, sizeof(long long) * Nx));
@@ -1319,6 +1337,7 @@ long long vlasov_launches(const vlasov_sim* s, int n)
 int vlasov_set_fused_x(vlasov_sim* s, int on)
 {
     if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (on && s->gs) return fail(VLASOV_EINVAL, "fused x-shifts run the spline of Eq. findif only");
     if (on && !s->fuse_ok)
         return fail(VLASOV_EINVAL, "fused x-shifts need VLASOV_FX64 (Nx <= %d), VLASOV_F32 or VLASOV_BF16 (Nx <= %d) storage",
                     XF_FUSED_MAX_NX, XXS_MAX_NX);
@@ -1327,5 +1346,33 @@ int vlasov_set_fused_x(vlasov_sim* s, int on)
 }
 
 int vlasov_fused_x(const vlasov_sim* s) { return (s && s->fuse) ? 1 : 0; }
+
+int vlasov_set_spline(vlasov_sim* s, int spline)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (spline != VLASOV_SPLINE_FD && spline != VLASOV_SPLINE_GS) return fail(VLASOV_EINVAL, "unknown spline %d", spline);
+    const bool gs = spline == VLASOV_SPLINE_GS;
+    if (gs == s->gs) return VLASOV_OK;
+    if (gs) {
+        if (s->fx || s->emul || s->esz == 2)
+            return fail(VLASOV_EINVAL, "the global spline runs with VLASOV_F64_NATIVE or VLASOV_F32 storage");
+        if (s->Nx < GS_MIN_N || s->Np < GS_MIN_N || s->Nx > GS_XTHREADS * GS_XCH)
+            return fail(VLASOV_EINVAL, "the global spline needs %d <= Nx <= %d and Np >= %d", GS_MIN_N,
+                        GS_XTHREADS * GS_XCH, GS_MIN_N);
+        if (s->gspgrid == 0) {
+            int occ = 0;
+            CU_TRY(gs_occupancy(s->esz, false, gs_pshift_smem_bytes(s->esz), &occ));
+            const int tiles = ((s->Nx + 31) / 32) * ((s->Np + GS_PTH - 1) / GS_PTH);
+            s->gspgrid = std::max(1, std::min(tiles, s->nsm * std::max(occ, 1)));
+        }
+        s->fuse = false;
+    }
+    CU_TRY(cudaStreamSynchronize(s->st));
+    drop_graphs(s);
+    s->gs = gs;
+    return VLASOV_OK;
+}
+
+int vlasov_spline(const vlasov_sim* s) { return (s && s->gs) ? VLASOV_SPLINE_GS : VLASOV_SPLINE_FD; }
 
 }  // extern "C"

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace vl {
 
 // ---------------------------------------------------------------------------------------------
@@ -76,7 +78,39 @@ struct LineParamsDev {
     int* n0 = nullptr;
     void* w = nullptr;
     void* gd = nullptr;
+    double* beta = nullptr;   // foot fraction per line (global-spline sweeps)
 };
+
+// Global-spline variant (Eq. tridiagsys).  On a periodic line the cyclic system's inverse is the
+// circulant g_m = r^|m| / (2 sqrt 3), r = sqrt 3 - 2 (|r|^31 < 2e-18: truncated at |m| <= GS_R it is
+// exact to FP64 rounding for lines of >= 2 GS_R + 1 nodes).  On a zero-outside line (f = f'' = 0 at
+// the nodes -1 and n) the same holds for the data extended oddly about -1 and n.  So the spline
+// value at a foot k + beta is a filter of GS_TAPS taps over the extended line, starting at node
+// k - GS_R - 1: W_u = alpha [u = 0] + beta [u = 1] + gamma h_u + delta h_(u-1), u = -GS_R-1 .. GS_R+2,
+// with h = 6 g * (1, -2, 1) (GS_HTAPS taps, u = -GS_R-1 .. GS_R+1) and gamma, delta of Eq.
+// splinecoeffs in cell units.
+constexpr int GS_R = 30;
+constexpr int GS_HTAPS = 2 * GS_R + 3;
+constexpr int GS_TAPS = 2 * GS_R + 4;
+constexpr int GS_HALO = GS_R + 2;          // extended nodes each side of a staged line
+constexpr int GS_MIN_N = 2 * GS_R + 4;     // lines this short or longer
+constexpr int GS_XTHREADS = 512;
+constexpr int GS_XCH = 16;                 // columns per x-shift thread: Nx <= GS_XTHREADS * GS_XCH
+constexpr int GS_PROWS = 256;              // staged rows of a p-shift tile (32 columns)
+constexpr int GS_PTH = 64;                 // output rows of a p-shift tile (8 warps x 8)
+
+inline void gs_filter_h(double h[GS_HTAPS])
+{
+    const double r = std::sqrt(3.0) - 2.0;
+    double g[2 * GS_R + 1];
+    double rm = 1.0;
+    for (int m = 0; m <= GS_R; ++m) {
+        g[GS_R + m] = g[GS_R - m] = rm / (2.0 * std::sqrt(3.0));
+        rm *= r;
+    }
+    auto gm = [&](int m) { return (m >= -GS_R && m <= GS_R) ? g[GS_R + m] : 0.0; };
+    for (int u = -GS_R - 1; u <= GS_R + 1; ++u) h[u + GS_R + 1] = 6.0 * (gm(u - 1) - 2.0 * gm(u) + gm(u + 1));
+}
 
 // Device-side error codes written to the handle's flag by a bounded wait that gave up.
 enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2, DEV_ERR_RANGE = 3 };
@@ -138,6 +172,8 @@ struct XShiftArgs {
     double* kinpart;      // [gridDim.x] sum_j p_j^2/2 sum_i out, or null
     void* kin128 = nullptr;   // FX64: [ctas] int128 per-CTA kinetic sums instead (units 2^(Ef-51-KIN_Q))
     double pmin, dp;
+    const double* beta = nullptr;   // global spline: foot fraction per row, and the filter h
+    const double* gs_h = nullptr;
     int* err;
     int box_h = 0;        // fused x-shifts: lines of 8 elements per TMA box (divides Nx / 8, <= 256)
     int ctas = 0;         // CTAs that share the rows (row stride; the partials above have this many
@@ -176,6 +212,8 @@ struct PShiftArgs {
     const void* w;        // [10][Nx] in T
     const void* gd;       // [2][Nx] in T
     int* err;
+    const double* beta = nullptr;   // global spline: foot fraction per column, and the filter h
+    const double* gs_h = nullptr;
 };
 
 struct ColReduceArgs {
@@ -233,6 +271,7 @@ struct PParamsArgs {
     int* Whe = nullptr;      // and of the edge filters [2][NTAP][Nx], or null
     float* wle = nullptr;
     float* wfe = nullptr;
+    double* beta = nullptr;  // foot fraction per column (global-spline sweeps), or null
 };
 
 struct RingArgs {
@@ -291,6 +330,13 @@ cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks);
 cudaError_t pshift_fx_occupancy(int* blocks);
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                              cudaStream_t st);
+// Global-spline sweeps (IEEE FP64 or FP32 storage and arithmetic).
+size_t gs_xshift_smem_bytes(int Nx, int elem_bytes);
+size_t gs_pshift_smem_bytes(int elem_bytes);
+cudaError_t launch_gs_xshift(int elem_bytes, bool periodic, bool kin, int grid, const XShiftArgs& a, cudaStream_t st);
+cudaError_t launch_gs_pshift(int elem_bytes, bool p_periodic, int grid, const PShiftArgs& a, cudaStream_t st);
+cudaError_t gs_occupancy(int elem_bytes, bool xdir, size_t smem, int* blocks);
+
 // Fused x-shifts with FP32-class storage (elem_bytes 4: FP32, 2: BF16): 512 threads of 8 columns.
 constexpr int XXS_THREADS = 512;
 constexpr int XXS_MAX_NX = 8 * XXS_THREADS;

@@ -28,7 +28,9 @@ EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_
             "vlasov_batch_admit", "vlasov_batch_step", "vlasov_batch_slot_steps", "vlasov_batch_get",
             "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve", "vlasov_launches",
             "vlasov_set_fused_x", "vlasov_fused_x", "vlasov_batch_create_shaped", "vlasov_batch_shape_of",
-            "vlasov_batch_autotune", "vlasov_casimirs")
+            "vlasov_batch_autotune", "vlasov_casimirs", "vlasov_set_spline", "vlasov_spline")
+
+SPLINES = {"fd": 0, "gs": 1}   # Eq. (findif) (the paper's method) / global spline, Eq. (tridiagsys)
 
 
 class VlasovError(RuntimeError):
@@ -235,6 +237,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_launches.argtypes = [vp, ip]
         lib.vlasov_set_fused_x.argtypes = [vp, ip]
         lib.vlasov_fused_x.argtypes = [vp]
+        lib.vlasov_set_spline.argtypes = [vp, ip]
+        lib.vlasov_spline.argtypes = [vp]
         lib.vlasov_step_timed.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ctypes.c_int)]
         lib.vlasov_xshift_density_noalloc.argtypes = [vp, vp, vp, ip, ip, ctypes.c_double, ctypes.c_double, ip,
                                                       vp, vp]
@@ -390,6 +394,15 @@ class Sim:
     @fused_x.setter
     def fused_x(self, on: bool):
         _check(self._lib.vlasov_set_fused_x(self._h, 1 if on else 0))
+
+    @property
+    def spline(self) -> str:
+        """"fd" (f'' by Eq. findif, the default) or "gs" (the global spline of Eq. tridiagsys)."""
+        return "gs" if self._lib.vlasov_spline(self._h) == SPLINES["gs"] else "fd"
+
+    @spline.setter
+    def spline(self, name: str):
+        _check(self._lib.vlasov_set_spline(self._h, SPLINES[name]))
 
     def step_timed(self, n: int) -> np.ndarray:
         """Mean milliseconds of each launch slot of a step over n eager steps (see vlasov.h)."""
