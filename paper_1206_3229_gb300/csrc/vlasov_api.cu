@@ -690,7 +690,8 @@ int capture(vlasov_sim* s, cudaGraphExec_t* out, F&& enqueue)
 }
 
 // Graphs of 2^L whole steps from buffer c (L = 0: one step, ending on c^1; L > 0 ends on c).  All
-// levels are captured at the first call from c, so that no capture falls between two launches.
+// levels are captured at the first call (for both starting buffers), so that no capture falls
+// between two launches of a later call.
 int build_graphs(vlasov_sim* s, int c)
 {
     int rc = VLASOV_OK;
@@ -1142,7 +1143,9 @@ int vlasov_step(vlasov_sim* s, int n)
     if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_step before vlasov_set_f");
     if (s->fuse && n >= 2) {
         const int c = s->cur;
+        // both starting buffers' graphs at the first call, so that no later call captures
         int rc = build_fused_graphs(s, c);
+        if (!rc) rc = build_fused_graphs(s, c ^ 1);
         if (rc) return rc;
         // one graph launch per run of 2^L middle pieces, largest runs first (a graph launch costs
         // the stream a few microseconds more than a kernel boundary inside a graph)
@@ -1158,6 +1161,7 @@ int vlasov_step(vlasov_sim* s, int n)
     for (int L = RUN_LEVELS - 1; L >= 0; --L)
         for (; m >= (1 << L); m -= 1 << L) {
             int rc = build_graphs(s, s->cur);
+            if (!rc) rc = build_graphs(s, s->cur ^ 1);
             if (rc) return rc;
             CU_TRY(cudaGraphLaunch(s->grun[s->cur][L], s->st));
             if (L == 0) s->cur ^= 1;
