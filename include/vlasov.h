@@ -103,7 +103,9 @@ int vlasov_get_f(vlasov_sim* sim, double* host_f);
 int vlasov_get_f_device(vlasov_sim* sim, double* dev_f);
 
 /* Enqueue n Strang steps (Sec. 3 steps 1-4).  Asynchronous: launches CUDA graphs on the handle's
-   stream.  The moments of f after each step are appended to a device ring of 4096 records.
+   stream, one per run of 2^L steps (L < 6, largest runs first); the first call captures them for
+   both ping-pong buffers (a few milliseconds of host time), later calls only launch.  The moments
+   of f after each step are appended to a device ring of 4096 records.
    With fused x-shifts (vlasov_fused_x) a call of n >= 2 steps runs the second x half-shift of step
    k and the first of step k+1 as one launch that keeps the row between them on chip: the same
    arithmetic as separate launches, with one HBM round trip of f fewer per step.
