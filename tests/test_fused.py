@@ -180,3 +180,22 @@ def test_fp32_class_fused_defaults_and_accounting(precision):
             assert not s.fused_x                   # rows longer than 4096 cells: separate x-shifts
             with pytest.raises(V.VlasovError):
                 s.fused_x = True
+
+
+def test_full_size_hmf_4096_fp32_fused_steps_match_oracle():
+    """The 4096^2 HMF workload with FP32 storage (fused x-shifts on by default), one call of 3 steps:
+    f within the FP32 sweep bar (2e-6 max f per sweep, 9 sweeps), mass and magnetisation to 1e-6."""
+    w = I.HMF_4096_UNSTABLE
+    f0 = I.initial_state(w)
+    O.set_threads(0)
+    steps = 3
+    fo, mo = O.run(grid_of(w), f0, steps)
+    with V.Sim.from_workload(w, precision="f32") as s:
+        assert s.fused_x
+        s.set_f(f0)
+        s.step(steps)
+        fg = s.get_f()
+        mg = s.moments()
+    assert np.max(np.abs(fg - fo)) <= 2e-6 * 3 * steps * fo.max()
+    assert np.max(np.abs(mg[:, 1] - mo[:, 1])) <= 1e-6
+    assert np.max(np.abs(np.hypot(mg[:, 2], mg[:, 3]) - np.hypot(mo[:, 2], mo[:, 3]))) <= 1e-6
