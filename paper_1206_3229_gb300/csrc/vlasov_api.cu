@@ -108,7 +108,9 @@ struct vlasov_sim {
     long long* cos50 = nullptr;   // round(cos x_i 2^50), round(sin x_i 2^50)
     long long* sin50 = nullptr;
     void* ctapart = nullptr;      // [xgrid][3] int128 per-CTA HMF partials
-    bool hmf_cta = false;         // HMF, FX64: reductions from per-CTA partials (no per-column pass)
+    bool hmf_cta = false;         // HMF: reductions from per-CTA partials (no per-column pass)
+    bool hmf_cta_fd = false;      //   its value with the spline of Eq. findif (the global-spline
+                                  //   sweeps hand over column partials)
     void* ringdV = nullptr;     // in the storage type
     void* ringV = nullptr;
     // fixed-point scales of the reductions (from a bound 2^Ef >= 4 max|f|)
@@ -957,10 +959,10 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         CTRY(cudaMalloc(&s->ctapart_m, 48 * (size_t)s->nctas));
         CTRY(cudaMalloc(&s->colpart_m, sizeof(long long) * (size_t)s->nctas * Nx));
     }
-    // HMF with FX64 or BF16 storage needs no per-column density: the x-shifts hand over three exact
-    // numbers per CTA (bounded in int128 while Nx * Np <= 2^24).  (With FP32 storage the int128
-    // weighting of a CTA's 16 columns per thread measured slower than the integer partial rows.)
-    s->hmf_cta = (s->fx || esz == 2) && model == VLASOV_HMF && (double)Nx * (double)Np <= 16777216.0;
+    // HMF needs no per-column density: the x-shifts hand over three exact numbers per CTA (bounded
+    // in int128 while Nx * Np <= 2^24).
+    s->hmf_cta = (s->fx || esz <= 4) && model == VLASOV_HMF && (double)Nx * (double)Np <= 16777216.0;
+    s->hmf_cta_fd = s->hmf_cta;
     CTRY(cudaMalloc(&s->colacc, sizeof(unsigned long long) * (size_t)Nx));
     CTRY(cudaMemsetAsync(s->colacc, 0, sizeof(unsigned long long) * (size_t)Nx, s->st));
     CTRY(cudaMalloc(&s->kinpart, sizeof(double) * (size_t)s->nctas));
@@ -1374,6 +1376,7 @@ int vlasov_set_spline(vlasov_sim* s, int spline)
     CU_TRY(cudaStreamSynchronize(s->st));
     drop_graphs(s);
     s->gs = gs;
+    s->hmf_cta = gs ? false : s->hmf_cta_fd;
     return VLASOV_OK;
 }
 

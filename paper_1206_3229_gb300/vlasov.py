@@ -413,7 +413,8 @@ class Sim:
 
     def slot_names(self) -> list[str]:
         """Names of the step_timed slots (for n >= 2 when fused_x)."""
-        hmf_cta = self.model == HMF and self.precision in (FX64, BF16) and self.nx * self.np <= 1 << 24
+        hmf_cta = self.model == HMF and self.precision in (FX64, BF16, F32) and self.nx * self.np <= 1 << 24 \
+            and self.spline == "fd"
         if self.fused_x:
             names = ["xshift_fused", "reduce_moments"]
             if self.model == RING:
