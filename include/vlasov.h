@@ -177,8 +177,8 @@ long long vlasov_launches(const vlasov_sim* sim, int n);
    density partials), density reduction, [ring force], p-shift filters (force), p-shift (step 3),
    x-shift (step 4, density+kinetic partials), moment reduction, [ring potential].  HMF with
    VLASOV_FX64, VLASOV_F32 or VLASOV_BF16 storage (Nx * Np <= 2^24, spline of Eq. findif) has no
-   density reduction launch: the x-shifts
-   hand the reductions three exact per-CTA numbers and the filters launch forms Mx, My.
+   density reduction launch: the x-shifts hand the reductions three exact per-CTA numbers and the
+   filters launch forms Mx, My.
    With fused x-shifts and n >= 2 the slots are those between two steps, averaged over the n-1 such
    places: fused x-shifts (step 4 and the next step 1), moment reduction, [ring potential],
    [density reduction, ring force], p-shift filters, p-shift. */
