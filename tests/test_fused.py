@@ -199,3 +199,16 @@ def test_full_size_hmf_4096_fp32_fused_steps_match_oracle():
     assert np.max(np.abs(fg - fo)) <= 2e-6 * 3 * steps * fo.max()
     assert np.max(np.abs(mg[:, 1] - mo[:, 1])) <= 1e-6
     assert np.max(np.abs(np.hypot(mg[:, 2], mg[:, 3]) - np.hypot(mo[:, 2], mo[:, 3]))) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fx64", "f64_native", "f32"])
+def test_graph_runs_give_the_bits_of_single_steps(precision):
+    """vlasov_step(70) launches graphs of 2^L steps (fused middles or whole steps: 32 + 32 + 4 + 2
+    ...); the same 70 steps as 70 calls of one step give the same bits, f and every moment record."""
+    w = I.HMF_256.resized(128, 128)
+    f0 = I.initial_state(w)
+    fused = precision == "fx64"   # FX64: fused middles (= separate launches bitwise); else whole steps
+    fa, ma = run(w, f0, 70, fused=fused, precision=precision)
+    fb, mb = run(w, f0, 70, fused=fused, calls=[1] * 70, precision=precision)
+    assert np.array_equal(fa, fb) and np.array_equal(ma, mb)
+    assert ma.shape == (70, 8)
