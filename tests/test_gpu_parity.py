@@ -315,3 +315,32 @@ def test_device_pointer_round_trip():
         s.get_f_device(dst.data_ptr())
         s.sync()
     assert np.max(np.abs(dst.cpu().numpy() - f0)) <= 1e-7 * f0.max()
+
+
+# ------------------------------------------------------------------------------------- maximum sizes
+MAX_NX = {"f64": 4096, "fx64": 4096, "f64_native": 4096, "f32": 8192}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("xper", [True, False])
+def test_longest_rows_match_oracle(prec, xper):
+    """The longest row each storage mode takes (a whole row per thread block): x and p sweeps at
+    that Nx against the oracle, and one cell more is refused at creation."""
+    nx, np_ = MAX_NX[prec], 72
+    w = I.Workload("longest", "free", nx, np_, -1.0, 1.0, -2.0, 2.0, xper, False, 0.1, 1)
+    rng = np.random.default_rng(nx + int(xper))
+    f = rng.uniform(0.0, 1.0, (np_, nx))
+    xdisp = rng.uniform(-40, 40, np_)
+    pdisp = 6.0 * np.sin(2 * np.pi * np.arange(nx) / nx) - 0.4
+    with make(w, prec) as s:
+        s.set_f(f)
+        s.substep(0, xdisp)
+        gx = s.get_f()
+        s.set_f(f)
+        s.substep(1, pdisp)
+        gp = s.get_f()
+    assert rel_err(gx, O.advect_x(grid_of(w), f, xdisp)) <= TOL_SWEEP[prec]
+    want = O.advect_p(grid_of(w), f, pdisp)
+    assert np.max(np.abs(gp - want)) <= TOL_SWEEP[prec] * max(np.abs(want).max(), np.abs(f).max())
+    with pytest.raises(V.VlasovError):
+        make(w.resized(nx + 8, np_), prec)
