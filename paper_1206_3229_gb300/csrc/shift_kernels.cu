@@ -867,9 +867,39 @@ __global__ void __launch_bounds__(256) gs_pshift_kernel(PShiftArgs a)
         const double be = colok ? a.beta[i] : 0.0;
         for (int t = warp; t < GS_TAPS; t += 8) W[t * 32 + lane] = (S)gs_tap(be, a.gs_h, t);
         __syncthreads();
+        constexpr int RQ = GS_PTH / 8;   // output rows per thread (consecutive feet)
+        bool done = false;
+        if constexpr (sizeof(S) == 4) {
+            if (staged && colok) {
+                // FP32: the column's taps in registers and each staged node read once for the
+                // thread's RQ outputs (input-stationary: RQ + GS_TAPS - 1 reads, not RQ * GS_TAPS)
+                S wr[GS_TAPS], acc[RQ];
+#pragma unroll
+                for (int t = 0; t < GS_TAPS; ++t) wr[t] = W[t * 32 + lane];
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) acc[q] = S(0);
+                const int jb = j0 + warp * RQ;
+                const S* e = stage + (jb + n0 - GS_R - 1 - r0) * 32 + lane;
+#pragma unroll
+                for (int u = 0; u < RQ + GS_TAPS - 1; ++u) {
+                    const S v = e[u * 32];
+#pragma unroll
+                    for (int q = 0; q < RQ; ++q) {
+                        const int t = u - q;
+                        if (t >= 0 && t < GS_TAPS) acc[q] = fma(wr[t], v, acc[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < RQ; ++q) {
+                    const int j = jb + q, k = j + n0;
+                    if (j < Np) fout[(size_t)j * Nx + i] = (PPER || (k >= -1 && k < Np)) ? acc[q] : S(0);
+                }
+                done = true;
+            }
+        }
 #pragma unroll 1
-        for (int q = 0; q < GS_PTH / 8; ++q) {
-            const int j = j0 + warp * (GS_PTH / 8) + q;
+        for (int q = 0; q < (done ? 0 : RQ); ++q) {
+            const int j = j0 + warp * RQ + q;
             if (!colok || j >= Np) continue;
             const int k = j + n0;
             S out = S(0);
