@@ -1180,9 +1180,13 @@ int vlasov_moments(vlasov_sim* s, vlasov_moments_t* out, int max, int* count)
     long long first = std::max(s->read_step, h - (long long)HIST_CAP);
     long long n = std::min<long long>(h - first, (long long)std::max(max, 0));
     std::vector<MomentRec> tmp((size_t)std::max<long long>(n, 0));
-    for (long long k = 0; k < n; ++k) {
+    // the records are contiguous in the ring except across its wrap: at most two copies
+    for (long long k = 0; k < n;) {
         const long long idx = (first + k) % HIST_CAP;
-        CU_TRY(cudaMemcpyAsync(&tmp[(size_t)k], s->hist + idx, sizeof(MomentRec), cudaMemcpyDeviceToHost, s->st));
+        const long long len = std::min<long long>(n - k, (long long)HIST_CAP - idx);
+        CU_TRY(cudaMemcpyAsync(&tmp[(size_t)k], s->hist + idx, sizeof(MomentRec) * (size_t)len,
+                               cudaMemcpyDeviceToHost, s->st));
+        k += len;
     }
     CU_TRY(cudaStreamSynchronize(s->st));
     for (long long k = 0; k < n; ++k) {
