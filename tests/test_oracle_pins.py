@@ -271,6 +271,73 @@ def test_ring_force_large_eps_tends_to_hmf():
     assert errs[1] < errs[0] and errs[1] < 3e-3, errs
 
 
+def _f_with_density(g: O.Grid, rho: np.ndarray) -> np.ndarray:
+    """A state whose density dp * sum_j f[j, i] is rho (every row the same)."""
+    return np.tile(rho / (g.np * g.dp), (g.np, 1))
+
+
+def _ring_V_integrals(eps: float):
+    """Closed forms of int_{-pi}^{pi} V(u) du and int_{-pi}^{pi} V(u) cos u du for Eq. (ringpot).
+
+    With 1 - cos u = 2 sin^2(u/2) and t = u/2 both reduce to complete elliptic integrals of the
+    parameter m = -2/eps:  int V = -(2 sqrt2 / sqrt eps) K(m),  and since cos u = 1 - 2 sin^2 t,
+    int V cos u = -(2 sqrt2 / sqrt eps) [K(m) - (2/n)(E(m) - K(m))] with n = 2/eps."""
+    sp = pytest.importorskip("scipy.special")
+    n = 2.0 / eps
+    K, E = sp.ellipk(-n), sp.ellipe(-n)
+    c = -2.0 * math.sqrt(2.0) / math.sqrt(eps)
+    return c * K, c * (K - (2.0 / n) * (E - K))
+
+
+@pytest.mark.parametrize("eps,n", [(0.01, 256), (0.1, 128), (1.0, 64)])
+def test_ring_potential_of_uniform_density_is_an_elliptic_integral(eps, n):
+    """U = 1/2 int int V(x - x') rho rho' for rho = m/(2 pi): U = m^2/(4 pi) int V.  V is analytic
+    on the circle for eps > 0, so the rectangle rule of the oracle converges geometrically (rate
+    exp(-N sqrt(2 eps))) and the closed form holds to rounding."""
+    g = _ring_grid(n, eps)
+    mass = 0.7
+    rho = np.full(n, mass / (2 * math.pi))
+    U = O.moments(g, _f_with_density(g, rho))["potential"]
+    intV, _ = _ring_V_integrals(eps)
+    exact = mass ** 2 / (4 * math.pi) * intV
+    assert U < 0
+    assert abs(U - exact) <= 1e-12 * abs(exact), (U, exact)
+
+
+@pytest.mark.parametrize("a", [0.3, 0.9])
+def test_ring_potential_of_a_cosine_mode(a):
+    """rho = c (1 + a cos theta): by the Fourier series of V, int int V rho rho' =
+    c^2 [2 pi int V + pi a^2 int V cos u]; this fixes the k = +-1 harmonic of V as well."""
+    eps, n = 0.05, 256
+    g = _ring_grid(n, eps)
+    c = 0.4
+    th = g.xmin + np.arange(n) * g.dx
+    rho = c * (1 + a * np.cos(th))
+    U = O.moments(g, _f_with_density(g, rho))["potential"]
+    intV, intVc = _ring_V_integrals(eps)
+    exact = 0.5 * c * c * (2 * math.pi * intV + math.pi * a * a * intVc)
+    assert abs(U - exact) <= 1e-12 * abs(exact), (U, exact)
+
+
+def test_ring_potential_large_eps_tends_to_hmf():
+    """For eps >> 1, V = -1/sqrt(2 eps) + (1 - cos u)/(2 sqrt2 eps^{3/2}) + O(eps^{-5/2}), so
+    (U_ring + mass^2/(2 sqrt(2 eps))) * 2 sqrt2 eps^{3/2} tends to the HMF potential (the oracle's
+    HMF potential is pinned separately)."""
+    n = 64
+    th = -math.pi + np.arange(n) * 2 * math.pi / n
+    rho = 1 + 0.3 * np.cos(th - 0.4) + 0.1 * np.sin(2 * th)
+    gh = O.Grid("hmf", n, 16, -math.pi, math.pi, -1, 1, True, False, 0.1)
+    mh = O.moments(gh, _f_with_density(gh, rho))
+    errs = []
+    for eps in (1e2, 1e3, 1e4):
+        g = _ring_grid(n, eps)
+        m = O.moments(g, _f_with_density(g, rho))
+        scaled = (m["potential"] + m["mass"] ** 2 / (2 * math.sqrt(2 * eps))) * 2 * math.sqrt(2) * eps ** 1.5
+        errs.append(abs(scaled - mh["potential"]) / abs(mh["potential"]))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3, errs
+    assert 5 < errs[0] / errs[1] < 20, errs      # error O(1/eps)
+
+
 # ----------------------------------------------------------------------------- sheet (Eq. sheetpot)
 def test_sheet_field_of_uniform_slab():
     """rho = 1/2 on |x| < 1: E = -2 pi G x inside, -/+ 2 pi G outside; U = 2 pi G / 3."""
