@@ -909,4 +909,86 @@ cudaError_t launch_maxabs(int elem_bytes, const void* f, size_t n, unsigned long
     return cudaGetLastError();
 }
 
+// ============================================================================ waterbag initial states
+// The initial states of Sec. 4 written on the device: f0_ij = rowv[j] * colv[i] * (1 + noise xi_ij)
+// with the profile tables computed on the host (box or homogeneous cos-mode waterbag), and xi_ij =
+// 2u - 1, u the top 53 bits of the (j*Nx + i + 1)-th SplitMix64 output of `seed` (Steele, Lea &
+// Flood 2014; a counter-based draw, so every cell is generated independently).  The products are
+// rounded one by one (no FMA contraction), as the FP64 host generator rounds them.  Pass 1 sums the
+// unnormalised f exactly in int128 fixed point (deterministic); pass 2 regenerates each cell,
+// divides it by the mass and stores it in the storage type, keeping the largest |f| for the
+// fixed-point scales.
+__device__ __forceinline__ unsigned long long wb_splitmix64(unsigned long long seed, unsigned long long k)
+{
+    unsigned long long z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double wb_value(const WaterbagArgs& a, size_t k)
+{
+    const int j = (int)(k / (size_t)a.Nx), i = (int)(k - (size_t)j * a.Nx);
+    double v = __dmul_rn(__ldg(a.rowv + j), __ldg(a.colv + i));
+    if (v != 0.0 && a.noise != 0.0) {
+        const unsigned long long z = wb_splitmix64(a.seed, (unsigned long long)k + 1ull);
+        const double u = __dmul_rn((double)(z >> 11), 1.1102230246251565e-16);   // top 53 bits / 2^53
+        const double xi = __dadd_rn(__dmul_rn(2.0, u), -1.0);
+        v = __dmul_rn(v, __dadd_rn(1.0, __dmul_rn(a.noise, xi)));
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(WB_THREADS) waterbag_mass_kernel(WaterbagArgs a)
+{
+    __shared__ i128 red[33];
+    __shared__ bool is_last;
+    const size_t n = (size_t)a.Nx * a.Np;
+    i128 acc = 0;
+    for (size_t k = blockIdx.x * (size_t)WB_THREADS + threadIdx.x; k < n; k += (size_t)gridDim.x * WB_THREADS)
+        acc += fx128_from_f64(wb_value(a, k), a.k_m);
+    acc = block_sum_i128(acc, red);
+    i128* part = static_cast<i128*>(a.part);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = acc;
+        __threadfence();
+        is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    i128 t = 0;
+    const volatile i128* vp = part;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += WB_THREADS) t += vp[b];
+    t = block_sum_i128(t, red);
+    if (threadIdx.x == 0) *a.mass = __dmul_rn(a.dxdp, fx128_to_f64(t, a.k_m));
+}
+
+template <typename D>
+__global__ void __launch_bounds__(WB_THREADS) waterbag_write_kernel(WaterbagArgs a, D* __restrict__ f)
+{
+    const size_t n = (size_t)a.Nx * a.Np;
+    const double mass = *a.mass;
+    double m = 0.0;
+    for (size_t k = blockIdx.x * (size_t)WB_THREADS + threadIdx.x; k < n; k += (size_t)gridDim.x * WB_THREADS) {
+        const double v = __ddiv_rn(wb_value(a, k), mass);
+        m = fmax(m, fabs(v));
+        f[k] = (D)v;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(a.maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_waterbag(const WaterbagArgs& a, int elem_bytes, void* f, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    waterbag_mass_kernel<<<WB_BLOCKS, WB_THREADS, 0, st>>>(a);
+    if (elem_bytes == 8) waterbag_write_kernel<double><<<WB_BLOCKS, WB_THREADS, 0, st>>>(a, static_cast<double*>(f));
+    else if (elem_bytes == 4) waterbag_write_kernel<float><<<WB_BLOCKS, WB_THREADS, 0, st>>>(a, static_cast<float*>(f));
+    else waterbag_write_kernel<__nv_bfloat16><<<WB_BLOCKS, WB_THREADS, 0, st>>>(a, static_cast<__nv_bfloat16*>(f));
+    return cudaGetLastError();
+}
+
 }  // namespace vl

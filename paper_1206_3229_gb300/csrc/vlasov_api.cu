@@ -1097,6 +1097,75 @@ int vlasov_set_f_device(vlasov_sim* s, const double* dev_f)
     return VLASOV_OK;
 }
 
+int vlasov_init_waterbag(vlasov_sim* s, double x0, double p0, double noise, unsigned long long seed, int mode,
+                         double mode_amp)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (!(x0 > 0) || !(p0 > 0) || !std::isfinite(x0) || !std::isfinite(p0))
+        return fail(VLASOV_EINVAL, "waterbag half-widths must be finite and > 0");
+    if (mode != 0 && mode != 1) return fail(VLASOV_EINVAL, "mode must be 0 (box) or 1 (homogeneous + cos mode)");
+    if (!(noise >= 0 && noise < 1) || !(std::fabs(mode_amp) < 1))
+        return fail(VLASOV_EINVAL, "noise must be in [0, 1) and |mode_amp| < 1");
+    const int Nx = s->Nx, Np = s->Np;
+    const size_t cells = (size_t)Nx * Np;
+    // profile tables of Sec. 4's waterbags on the nodes x_i = xmin + i dx, p_j = pmin + j dp
+    std::vector<double> tab((size_t)Nx + Np);
+    double* rowv = tab.data();
+    double* colv = rowv + Np;
+    double rows = 0, cmax = 0;
+    for (int j = 0; j < Np; ++j) {
+        const double p = s->pmin + (double)j * s->dp;
+        rowv[j] = std::fabs(p) < p0 ? 1.0 : 0.0;
+        rows += rowv[j];
+    }
+    const double L = s->xmax - s->xmin, half_x = 0.5 * L;
+    for (int i = 0; i < Nx; ++i) {
+        const double x = s->xmin + (double)i * s->dx;
+        if (mode == 0) colv[i] = (x0 >= half_x || std::fabs(x) < x0) ? 1.0 / (4.0 * x0 * p0) : 0.0;
+        else colv[i] = (1.0 / (2.0 * p0 * L)) * (1.0 + mode_amp * std::cos(x));
+        cmax = std::max(cmax, std::fabs(colv[i]));
+    }
+    if (!(rows > 0) || !(cmax > 0)) return fail(VLASOV_EINVAL, "initial state is empty on this grid");
+
+    // one temporary block: tables, int128 block partials, ticket, mass
+    const size_t off_part = ((tab.size() * 8 + 15) / 16) * 16;
+    const size_t off_tail = off_part + 16 * (size_t)WB_BLOCKS;
+    char* tmp = nullptr;
+    CU_TRY(cudaMalloc(&tmp, off_tail + 16));
+    WaterbagArgs a;
+    a.rowv = reinterpret_cast<const double*>(tmp);
+    a.colv = a.rowv + Np;
+    a.Nx = Nx;
+    a.Np = Np;
+    a.noise = mode == 0 ? noise : 0.0;
+    a.seed = seed;
+    a.k_m = 120 - ceil_log2((double)cells * cmax * (1.0 + a.noise) * 2.0 + 1.0);
+    a.dxdp = s->dx * s->dp;
+    a.part = tmp + off_part;
+    a.ticket = reinterpret_cast<unsigned int*>(tmp + off_tail);
+    a.mass = reinterpret_cast<double*>(tmp + off_tail + 8);
+    a.maxbits = s->maxbits;
+    // 8-byte storage: the FP64 state goes through vlasov_set_f_device (FX64 from the other buffer)
+    void* dst = s->f[(s->esz == 8 && s->fx) ? s->cur ^ 1 : s->cur];
+    cudaError_t e = cudaMemcpyAsync(tmp, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = launch_waterbag(a, s->esz, dst, s->st);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, s->maxbits, sizeof bits, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(VLASOV_ECUDA, "vlasov_init_waterbag: %s", cudaGetErrorString(e));
+    if (s->esz == 8) return vlasov_set_f_device(s, static_cast<const double*>(dst));
+    double mx;
+    std::memcpy(&mx, &bits, sizeof mx);
+    if (!std::isfinite(mx)) return fail(VLASOV_EINVAL, "initial state holds a non-finite value");
+    update_scales(s, mx);
+    CU_TRY(cudaMemsetAsync(s->dstep, 0, sizeof(long long), s->st));
+    CU_TRY(cudaStreamSynchronize(s->st));
+    s->read_step = 0;
+    s->has_f = true;
+    return VLASOV_OK;
+}
+
 int vlasov_get_f(vlasov_sim* s, double* host_f)
 {
     if (!s || !host_f) return fail(VLASOV_EINVAL, "NULL argument");

@@ -363,6 +363,24 @@ constexpr int CAS_BLOCKS = 8 * 152;
 cudaError_t launch_casimirs(int kind, const void* f, size_t n, double unit, double dxdp, double* part, double* out,
                             cudaStream_t st);
 cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st);
+// Waterbag initial states (Sec. 4) written on the device; see aux_kernels.cu.
+constexpr int WB_BLOCKS = 4 * 152;
+constexpr int WB_THREADS = 256;
+struct WaterbagArgs {
+    const double* rowv;          // [Np] momentum profile (device)
+    const double* colv;          // [Nx] position profile (device)
+    int Nx, Np;
+    double noise;                // 0: no noise
+    unsigned long long seed;
+    int k_m;                     // fixed-point shift of the exact mass sum
+    double dxdp;
+    void* part;                  // int128 [WB_BLOCKS]
+    unsigned int* ticket;
+    double* mass;                // out: dx dp sum of the unnormalised f
+    unsigned long long* maxbits; // out: bits of the largest |f| after normalisation
+};
+// f (elem_bytes 8: double, 4: float, 2: bf16) = the normalised state; two launches, no sync.
+cudaError_t launch_waterbag(const WaterbagArgs& a, int elem_bytes, void* f, cudaStream_t st);
 cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cudaStream_t st);
 cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double* colpart, cudaStream_t st);
 

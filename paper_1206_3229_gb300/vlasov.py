@@ -28,7 +28,8 @@ EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_
             "vlasov_batch_admit", "vlasov_batch_step", "vlasov_batch_slot_steps", "vlasov_batch_get",
             "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve", "vlasov_launches",
             "vlasov_set_fused_x", "vlasov_fused_x", "vlasov_batch_create_shaped", "vlasov_batch_shape_of",
-            "vlasov_batch_autotune", "vlasov_casimirs", "vlasov_set_spline", "vlasov_spline")
+            "vlasov_batch_autotune", "vlasov_casimirs", "vlasov_set_spline", "vlasov_spline",
+            "vlasov_init_waterbag")
 
 SPLINES = {"fd": 0, "gs": 1}   # Eq. (findif) (the paper's method) / global spline, Eq. (tridiagsys)
 
@@ -222,6 +223,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_create.argtypes = [ip, ip, ip, ctypes.POINTER(Domain), ctypes.c_double, ctypes.POINTER(vp)]
         lib.vlasov_set_f.argtypes = [vp, dp]
         lib.vlasov_set_f_device.argtypes = [vp, vp]
+        lib.vlasov_init_waterbag.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_ulonglong, ip, ctypes.c_double]
         lib.vlasov_get_f.argtypes = [vp, dp]
         lib.vlasov_get_f_device.argtypes = [vp, vp]
         lib.vlasov_step.argtypes = [vp, ip]
@@ -338,6 +341,22 @@ class Sim:
 
     def set_f_device(self, dev_ptr: int):
         _check(self._lib.vlasov_set_f_device(self._h, ctypes.c_void_p(dev_ptr)))
+
+    def init_waterbag(self, x0: float, p0: float, noise: float = 0.0, seed: int = 0, mode: int = 0,
+                      mode_amp: float = 0.0):
+        """vlasov_init_waterbag: a Sec. 4 waterbag written on the device (mode 0 box with seeded
+        noise, mode 1 homogeneous with a cos mode), normalised to unit mass."""
+        _check(self._lib.vlasov_init_waterbag(self._h, float(x0), float(p0), float(noise), int(seed) & (2**64 - 1),
+                                              int(mode), float(mode_amp)))
+
+    def init_workload(self, w: Workload):
+        """The initial state of a workload description, generated on the device."""
+        if w.init == "box":
+            self.init_waterbag(w.x0, w.p0, w.noise, w.seed, 0, 0.0)
+        elif w.init == "mode":
+            self.init_waterbag(w.x0, w.p0, 0.0, 0, 1, w.mode_amp)
+        else:
+            raise ValueError(f"unknown init {w.init!r}")
 
     def get_f(self, out: np.ndarray | None = None) -> np.ndarray:
         if out is None:
