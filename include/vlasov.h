@@ -95,6 +95,22 @@ int vlasov_set_f(vlasov_sim* sim, const double* host_f);
    sums assume |f| stays below 4x the largest |f| uploaded. */
 int vlasov_set_f_device(vlasov_sim* sim, const double* dev_f);
 
+/* Write one of the waterbag initial states of Sec. 4 on the device (no host array), normalised to
+   unit mass dx dp sum f = 1, on the nodes x_i = xmin + i dx, p_j = pmin + j dp:
+     mode 0 (box, Secs. 4.1-4.3): f = 1/(4 x0 p0) where |x_i| < x0 and |p_j| < p0 (x0 >= half the x
+       extent: every column, the homogeneous waterbag), times (1 + noise xi_ij), xi_ij = 2u - 1 with
+       u the top 53 bits of the (j*Nx + i + 1)-th output of SplitMix64 started at `seed`;
+     mode 1 (homogeneous waterbag with a cos mode, Sec. 4.2): f = [|p_j| < p0] / (2 p0 L)
+       (1 + mode_amp cos x_i), L = xmax - xmin; `noise` and `seed` are not used.
+   Arithmetic: the profile in FP64, each product rounded on its own (no fused multiply-add), the
+   mass as an exact fixed-point sum rounded once, f = value / mass in FP64, then converted to the
+   handle's storage as vlasov_set_f_device converts.  Same reset of step counter and history as
+   vlasov_set_f.  Needs x0, p0 > 0, 0 <= noise < 1, |mode_amp| < 1 and a non-empty state on the
+   grid (else VLASOV_EINVAL).  Allocates a temporary (Nx + Np) * 8 + 10 KB block while it runs.
+   Syncs. */
+int vlasov_init_waterbag(vlasov_sim* sim, double x0, double p0, double noise, unsigned long long seed, int mode,
+                         double mode_amp);
+
 /* Download the current f as doubles (host, Np*Nx).  Syncs.  VLASOV_ETIMEOUT if a device wait
    expired since the last check. */
 int vlasov_get_f(vlasov_sim* sim, double* host_f);
@@ -282,8 +298,8 @@ typedef struct {
 int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* opt, vlasov_result* results,
                  double* makespan_s);
 
-/* One x-shift sweep (Eq. step1 form: row j moves by dev_disp[j] cells) with its density, for
-   callers that cannot allocate device memory.  The paper has no counterpart: this exists because
+/* One x-shift sweep (node i of row j takes the spline value at i - dev_disp[j]) with its density,
+   for callers that cannot allocate device memory.  The paper has no counterpart: this exists because
    some callers may not call cudaMalloc at all (a host callback or allocator hook, a framework that
    owns every device allocation, a plug-in that must keep its device footprint fixed after load).
    It allocates nothing: its scratch (row filters and column partial sums, about 5.1 MiB) is a
@@ -291,7 +307,8 @@ int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* 
    dev_fin, dev_fout: Np*Nx doubles (f[j*Nx+i], device, caller-owned, must not overlap);
    dev_rho: Nx doubles out, rho_i = dp * sum_j fout[j,i] with dp = (pmax-pmin)/Np;
    dev_disp: Np doubles (device).  Limits: 16 <= Nx, Np <= 4096, multiples of 8; with
-   x_periodic = 0 every |disp| must stay below 55 cells.  A displacement out of range (or NaN), or a
+   x_periodic = 0 every displacement s must satisfy -57 < s <= 56 (the foot cell floor(-s) at most
+   56 cells away; the fixed zero halo is 64 cells).  A displacement out of range (or NaN), or a
    bounded device wait that gives up, makes dev_rho all NaN.  FP64 only.
    Enqueued on `stream` (NULL = legacy default stream); returns VLASOV_EINVAL/ECUDA on bad input.
    The first call on a device looks up the scratch address and sets kernel attributes for that
