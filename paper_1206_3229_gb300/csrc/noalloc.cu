@@ -137,6 +137,12 @@ extern "C" int vlasov_xshift_density_noalloc(const double* dev_fin, double* dev_
     // periodic rows wrap, so any displacement is in range; zero-extended rows need |n0| + 8 <= pad
     const int max_n0 = x_periodic ? 0x3fffffff : pad - 8;
 
+    // staged rows in flight: as many as fit the opted-in shared memory, at most 4, at least 1
+    const long long row_bytes = (long long)(Nx + 2 * pad) * (long long)sizeof(double) + XREC_BYTES;
+    const long long room = (long long)optin - 2048 - 256;
+    const int stages = room > 0 ? (int)std::min<long long>(4, room / row_bytes) : 0;
+    if (stages < 1) return na_fail(VLASOV_EINVAL, "a staged row does not fit in this device's shared memory");
+
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return na_fail(VLASOV_ECUDA, "clear flag", e);
     na_row_filters<<<(Np + 127) / 128, 128, 0, st>>>(dev_disp, Np, max_n0, n0, w, gd, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(VLASOV_ECUDA, "row filters launch", e);
@@ -147,8 +153,7 @@ extern "C" int vlasov_xshift_density_noalloc(const double* dev_fin, double* dev_
     a.Nx = Nx;
     a.Np = Np;
     a.pad = pad;
-    const size_t row_bytes = (size_t)(Nx + 2 * a.pad) * sizeof(double) + XREC_BYTES;
-    a.stages = (int)std::min<size_t>(4, ((size_t)optin - 2048 - 256) / row_bytes);
+    a.stages = stages;
     a.n0 = n0;
     a.w = w;
     a.gd = gd;

@@ -53,6 +53,24 @@ def test_noalloc_matches_regular_path_on_two_calls_in_a_row():
         assert np.max(np.abs(got_rho - want_rho)) <= TOL * np.max(np.abs(want_rho)), w.name
 
 
+def test_noalloc_at_its_size_limits_and_halo_edge():
+    """Rows of the largest length (4096) on periodic and zero-outside rows, and zero-outside shifts
+    at both ends of the accepted range -57 < s <= 56 (the regular handle gets the same halo from a
+    time step whose row displacements reach 61 cells)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(23)
+    per = I.HMF_256.resized(4096, 64)
+    zero = I.SHEET_4096.resized(4096, 64, dt=0.12)
+    edge = rng.uniform(-56.9, 55.9, 64)
+    edge[:6] = [56.0, -56.99, 55.999, -56.5, 0.0, 55.9]
+    for w, disp in [(per, rng.uniform(-300.0, 300.0, 64)), (zero, edge)]:
+        f = I.initial_state(w) * (1.0 + 0.1 * rng.uniform(-1, 1, (w.np, w.nx)))
+        want_f, want_rho = regular_path(w, f, disp)
+        got_f, got_rho = noalloc_path(torch, w, f, disp)
+        assert np.max(np.abs(got_f - want_f)) <= TOL * np.max(np.abs(want_f)), w.name
+        assert np.max(np.abs(got_rho - want_rho)) <= TOL * np.max(np.abs(want_rho)), w.name
+
+
 def test_noalloc_flags_out_of_range_displacement():
     torch = pytest.importorskip("torch")
     w = I.SHEET_4096.resized(64, 64)
@@ -61,5 +79,10 @@ def test_noalloc_flags_out_of_range_displacement():
     disp[3] = 500.0                     # beyond the fixed zero halo of a non-periodic row
     _, rho = noalloc_path(torch, w, f, disp)
     assert np.all(np.isnan(rho))
+    for s_bad in (56.01, -57.0):        # just outside -57 < s <= 56
+        disp = np.zeros(w.np)
+        disp[5] = s_bad
+        _, rho = noalloc_path(torch, w, f, disp)
+        assert np.all(np.isnan(rho)), s_bad
     _, rho2 = noalloc_path(torch, w, f, np.zeros(w.np))   # the next call starts clean
     assert np.all(np.isfinite(rho2))
