@@ -151,6 +151,30 @@ int vlasov_spline(const vlasov_sim* sim);
 int vlasov_set_fused_x(vlasov_sim* sim, int on);
 int vlasov_fused_x(const vlasov_sim* sim);
 
+/* Method of the ring model's circulant convolutions, Eq. (ringpot) into Eq. (meanforce) (Sec. 2):
+   F_i = -dx sum_k V'((i-k) dx) rho_k each step, and Phi_i = dx sum_k V((i-k) dx) rho_k for the
+   potential energy U = 1/2 dx sum_i rho_i Phi_i of each moment record.
+     VLASOV_RING_DIRECT:  N^2 fused multiply-adds in the storage's arithmetic type (FP64 for the
+                          8-byte modes, FP32 for F32/BF16 storage).
+     VLASOV_RING_FIXED:   the same sums exactly in integer arithmetic: rho as the exact fixed-point
+                          column sums the x-shift produces, V' and V rounded to fixed point (relative
+                          2^-52), int128 products and sums; FP64-accurate in every storage mode,
+                          deterministic, and the same bits whatever the launch shape.  Default.
+     VLASOV_RING_FFT:     FP64 FFT convolution in shared memory (Nx a power of two, <= 4096); the
+                          potential by Parseval.  VLASOV_RING_FFT_F32: the same in FP32.
+   vlasov_set_ring_method returns VLASOV_EINVAL for another model, an unknown method, or an Nx the
+   method cannot take; it syncs and drops the captured step graphs.  vlasov_ring_method reports it
+   (0 for another model).  vlasov_ring_timings computes the density of the current f and times
+   `reps` force launches of each method that can run, with CUDA events on the handle's stream:
+   us[m] = microseconds per launch of method m (us[0] and methods that cannot run: 0); us holds
+   VLASOV_RING_METHODS doubles.  It leaves the method unchanged and overwrites only the force
+   buffer.  Syncs. */
+enum { VLASOV_RING_DIRECT = 1, VLASOV_RING_FIXED = 2, VLASOV_RING_FFT = 3, VLASOV_RING_FFT_F32 = 4,
+       VLASOV_RING_TENSOR = 5, VLASOV_RING_METHODS = 6 };
+int vlasov_set_ring_method(vlasov_sim* sim, int method);
+int vlasov_ring_method(const vlasov_sim* sim);
+int vlasov_ring_timings(vlasov_sim* sim, int reps, double* us);
+
 /* Copy out up to max moment records produced since the previous call (oldest first) into out,
    set *count.  Records older than the ring's 4096 are dropped (count tells what is returned).
    Syncs; VLASOV_ETIMEOUT if a device wait expired. */
@@ -171,6 +195,16 @@ int vlasov_density_force(vlasov_sim* sim, double* host_rho, double* host_F);
    either pointer may be NULL.  FP64 arithmetic on the stored values, fixed summation order
    (deterministic).  Syncs. */
 int vlasov_casimirs(vlasov_sim* sim, double* entropy, double* l2);
+
+/* Check of the failure path (the paper has no failure handling; this exercises the library's own).
+   Enqueues on the handle's stream one CTA that waits, with the bounded wait every staged sweep uses
+   (a %globaltimer limit, 2 s in the sweeps), on an mbarrier that nothing arrives on and no copy
+   completes, so the wait expires after limit_ns (1e3 <= limit_ns <= 2e9, else VLASOV_EINVAL); the
+   CTA then records the timeout code in the handle's device error flag and returns.  Nothing is in
+   flight while it waits, so the device context stays usable.  The next syncing call (vlasov_sync,
+   vlasov_get_f, vlasov_moments, ...) returns VLASOV_ETIMEOUT and clears the flag; the state f is
+   not touched.  Returns VLASOV_OK once enqueued. */
+int vlasov_test_expire_wait(vlasov_sim* sim, long long limit_ns);
 
 /* Wait for the handle's stream and report any device-side error flag. */
 int vlasov_sync(vlasov_sim* sim);

@@ -12,6 +12,7 @@
 // order-free, and without the long dependent FP64 chains that are slow on this GPU.
 #include "emul.cuh"
 #include "fixed_point.cuh"
+#include "ptx.cuh"
 #include <cuda_bf16.h>
 #include "vlasov_internal.cuh"
 
@@ -262,7 +263,7 @@ __device__ __forceinline__ void colreduce_acc_body(const ColReduceArgs& a)
             const int i = i0 + u * blockDim.x;
             if (i < a.Nx) {
                 a.colacc[i] = 0ull;
-                if (a.model == 2) a.colfx[i] = t[u];                                   // sheet: prefix scan input
+                if (a.model == 2 || a.model == 1) a.colfx[i] = t[u];                   // sheet scan / ring fixed-point input
                 if (a.model == 1) a.rho[i] = a.dp * fx128_to_f64((i128)t[u], a.k_col);   // ring: convolution input
             }
             m += (i128)t[u];
@@ -469,14 +470,6 @@ __global__ void __launch_bounds__(256) ring_kernel(RingArgs a)
     ring_body<T>(a);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) ring_batch_kernel(const RingArgs* __restrict__ args)
-{
-    const RingArgs a = args[blockIdx.y];
-    if (a.N <= 0) return;
-    ring_body<T>(a);
-}
-
 int ring_blocks(int N) { return (N + RING_OUT - 1) / RING_OUT; }
 
 // The ring kernels stage rho and the kernel table: 2 N elements of shared memory (64 KB at N = 4096
@@ -485,19 +478,7 @@ cudaError_t set_ring_attributes(int max_smem)
 {
     cudaError_t e = cudaFuncSetAttribute(ring_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ring_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ring_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ring_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
-}
-
-cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st)
-{
-    const dim3 grid(ring_blocks(max_n), slots);
-    if (elem_bytes == 8) ring_batch_kernel<double><<<grid, 256, (size_t)max_n * 16, st>>>(args);
-    else ring_batch_kernel<float><<<grid, 256, (size_t)max_n * 8, st>>>(args);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_ring(int elem_bytes, const RingArgs& a, cudaStream_t st)
@@ -988,6 +969,30 @@ cudaError_t launch_waterbag(const WaterbagArgs& a, int elem_bytes, void* f, cuda
     if (elem_bytes == 8) waterbag_write_kernel<double><<<WB_BLOCKS, WB_THREADS, 0, st>>>(a, static_cast<double*>(f));
     else if (elem_bytes == 4) waterbag_write_kernel<float><<<WB_BLOCKS, WB_THREADS, 0, st>>>(a, static_cast<float*>(f));
     else waterbag_write_kernel<__nv_bfloat16><<<WB_BLOCKS, WB_THREADS, 0, st>>>(a, static_cast<__nv_bfloat16*>(f));
+    return cudaGetLastError();
+}
+
+// ============================================================================ failure path
+// A wait that must expire: the barrier expects one arrival that no thread makes and no copy
+// completes, so mbar_wait_bounded gives up after limit_ns of %globaltimer time.  Every thread of
+// the CTA waits, as a sweep's threads wait for a staged row; on expiry the CTA records the error
+// code the sweeps record and returns.  Nothing is in flight, so the context stays usable.
+__global__ void __launch_bounds__(128) expire_wait_kernel(int* err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    __syncthreads();
+    if (!ok && threadIdx.x == 0) atomicCAS(err, DEV_ERR_NONE, DEV_ERR_TEST_WAIT);
+}
+
+cudaError_t launch_expire_wait(int* err, unsigned long long limit_ns, cudaStream_t st)
+{
+    expire_wait_kernel<<<1, 128, 0, st>>>(err, limit_ns);
     return cudaGetLastError();
 }
 

@@ -261,11 +261,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
 
 // ------------------------------------------------------------------------------------------- slot layout
 struct SlotLayout {
-    size_t f[2], xrec, pn0, pw, pgd, pWh, pwl, pwf, pWhe, pwle, pwfe, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart, ringpart,
-        tickets, sc, hist, dstep, err, costab, sintab, cosfx, sinfx, ringdV, ringV, rowv, colv, initpart, inv_mass, total;
+    size_t f[2], xrec, pn0, pw, pgd, pWh, pwl, pwf, pWhe, pwle, pwfe, colpart, colacc, kinpart, rho, F, Qd, colfx, blockpart,
+        tickets, sc, hist, dstep, err, costab, sintab, cosfx, sinfx, rowv, colv, initpart, inv_mass,
+        ringKq, ringVq, ringgpart, ringgticket, ringupart, total;
 };
 
 // esz: bytes per cell (4: FP32 storage, 8: FX64 storage)
+// Largest split of the ring's fixed-point sums for Nx nodes (the split itself follows the device).
+int ring_split_of(int Nx) { return std::max(1, Nx / 256); }
+
 SlotLayout layout(int Nx, int Np, int esz)
 {
     SlotLayout L;
@@ -295,7 +299,6 @@ SlotLayout layout(int Nx, int Np, int esz)
     L.Qd = take((size_t)Nx * 8);
     L.colfx = take((size_t)Nx * 8);
     L.blockpart = take((size_t)((Nx + 31) / 32) * 48);
-    L.ringpart = take((size_t)ring_blocks(Nx) * 16);
     L.tickets = take(16);
     L.sc = take(sizeof(Scalars));
     L.hist = take(sizeof(MomentRec) * HIST_CAP);
@@ -305,12 +308,16 @@ SlotLayout layout(int Nx, int Np, int esz)
     L.sintab = take((size_t)Nx * 8);
     L.cosfx = take((size_t)Nx * 8);
     L.sinfx = take((size_t)Nx * 8);
-    L.ringdV = take((size_t)Nx * esz);
-    L.ringV = take((size_t)Nx * esz);
     L.rowv = take((size_t)Np * esz);
     L.colv = take((size_t)Nx * esz);
     L.initpart = take((size_t)B_INIT_BLOCKS * 16);
     L.inv_mass = take(8);
+    // ring: exact fixed-point force and potential (ring.cu); a slot's split follows its own Nx
+    L.ringKq = take((size_t)Nx * 8);
+    L.ringVq = take((size_t)Nx * 8);
+    L.ringgpart = take((size_t)16 * ring_split_of(Nx) * Nx);
+    L.ringgticket = take((size_t)((Nx + 31) / 32) * 4);
+    L.ringupart = take((size_t)((Nx + 31) / 32) * 16);
     L.total = o;
     return L;
 }
@@ -323,6 +330,7 @@ struct Slot {
     SlotLayout L;
     int steps_done = 0;
     int Ef = 0, k_col = 0, k_kin = 0, k_pot = 0;
+    int ring_sK = 0, ring_sV = 0;   // shifts of the ring's fixed-point kernel tables
     double admit_s = 0;
     int done_event = -1;     // index into the step-event ring of the step that finished it
     long long result_index = -1;
@@ -336,6 +344,7 @@ struct vlasov_batch {
     int prec = VLASOV_F32;           // VLASOV_F32 or VLASOV_FX64, for every slot
     int esz = 4;
     int ctas_x = 16, ctas_p = 32;    // CTAs per slot of the batched sweeps (fixed at capture)
+    int nsm = 0;                     // SMs of the device (the ring sums' split follows it)
     vlasov_batch_shape shape = {B_ROWS_PER_CTA, B_TILES_PER_CTA};
     cudaStream_t st = nullptr;
     bool own_stream = false;
@@ -501,10 +510,7 @@ int fill_slot_args(vlasov_batch* b, int k)
             g.N = Nx;
             g.dx = dx;
             g.rho = c.rho;
-            g.dV = P(b, s, s.L.ringdV);
-            g.V = P(b, s, s.L.ringV);
             g.F = reinterpret_cast<double*>(P(b, s, s.L.F));
-            g.blockpart = P(b, s, s.L.ringpart);
             g.k_pot = s.k_pot;
             g.pot_scale = 0.5 * dx;
             g.ticket = reinterpret_cast<unsigned int*>(P(b, s, s.L.tickets)) + 1;
@@ -513,6 +519,17 @@ int fill_slot_args(vlasov_batch* b, int k)
             g.hist = c.hist;
             g.step = c.step;
             g.dt = r.dt;
+            g.colfx = c.colfx;
+            g.Kq = reinterpret_cast<const long long*>(P(b, s, s.L.ringKq));
+            g.Vq = reinterpret_cast<const long long*>(P(b, s, s.L.ringVq));
+            g.k_col = s.k_col;
+            g.sK = s.ring_sK;
+            g.sV = s.ring_sV;
+            g.dp = dp;
+            g.ksplit = ringfx_ksplit(Nx, b->nsm);
+            g.gpart = P(b, s, s.L.ringgpart);
+            g.gticket = reinterpret_cast<unsigned int*>(P(b, s, s.L.ringgticket));
+            g.upart = P(b, s, s.L.ringupart);
         }
     }
     PParamsArgs& p = b->pp[k];
@@ -745,7 +762,8 @@ int vlasov_batch_create_shaped(int slots, int max_n, long long mem_budget_bytes,
     BC(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     BC(set_kernel_attributes(optin - 1024));
     BC(set_kernel_attributes_fx(optin - 1024));
-    BC(set_ring_attributes(optin - 1024));
+    BC(set_ringfx_attributes(optin - 1024));
+    BC(cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev));
     BC(cudaMalloc(&b->arena.base, (size_t)mem_budget_bytes));
     b->arena.size = (size_t)mem_budget_bytes;
     b->arena.free_[0] = (size_t)mem_budget_bytes;
@@ -798,14 +816,14 @@ int vlasov_batch_create_shaped(int slots, int max_n, long long mem_budget_bytes,
     L(xs(true, false, b->d_xa + 0 * S * 2));
     L(xs(false, false, b->d_xa + 1 * S * 2));
     L(launch_colreduce_batch(slots, crb, b->d_cr, b->st));
-    L(launch_ring_batch(b->esz, slots, max_n, b->d_rg, b->st));
+    L(launch_ring_fixed_batch(false, slots, max_n, b->nsm, b->d_rg, b->st));
     L(launch_pparams_batch(b->esz, slots, max_n, b->d_pp, b->st));
     L(fx ? launch_pshift_fx_batch(slots, b->ctas_p, b->d_tm, b->d_pa, b->d_em, b->d_ver, b->st)
          : launch_pshift_batch(slots, b->ctas_p, b->d_tm, b->d_pa, b->d_ver, b->st));
     L(xs(true, true, b->d_xa + 2 * S * 2));
     L(xs(false, true, b->d_xa + 3 * S * 2));
     L(launch_colreduce_batch(slots, crb, b->d_cr + S, b->st));
-    L(launch_ring_batch(b->esz, slots, max_n, b->d_rg + S, b->st));
+    L(launch_ring_fixed_batch(true, slots, max_n, b->nsm, b->d_rg + S, b->st));
     flip_kernel<<<1, 256, 0, b->st>>>(b->d_ver, slots);
     L(cudaGetLastError());
     cudaError_t ec = cudaStreamEndCapture(b->st, &g);
@@ -909,19 +927,12 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
     }
     std::vector<double> c(Nx), sn(Nx);
     std::vector<long long> cfx(Nx), sfx(Nx);
-    std::vector<double> dV(Nx, 0.0), V(Nx, 0.0);
     for (int i = 0; i < Nx; ++i) {
         const double th = r->xmin + (double)i * dx;
         c[i] = std::cos(th);
         sn[i] = std::sin(th);
         cfx[i] = std::llround(std::ldexp(c[i], 62));
         sfx[i] = std::llround(std::ldexp(sn[i], 62));
-        if (r->model == VLASOV_RING) {
-            const double u = (double)i * dx;
-            const double q = 1.0 - std::cos(u) + r->eps;
-            dV[i] = std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q));
-            V[i] = -1.0 / (std::sqrt(2.0) * std::sqrt(q));
-        }
     }
     std::vector<unsigned char> recs((size_t)Np * XREC_BYTES, 0);
     const double cx = (0.5 * r->dt) / dx;
@@ -964,9 +975,12 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
     B_TRY(H2D(L.sintab, sn.data(), 8 * (size_t)Nx));
     B_TRY(H2D(L.cosfx, cfx.data(), 8 * (size_t)Nx));
     B_TRY(H2D(L.sinfx, sfx.data(), 8 * (size_t)Nx));
-    std::vector<float> dVf(dV.begin(), dV.end()), Vf(V.begin(), V.end());
-    B_TRY(H2D(L.ringdV, fx ? (const void*)dV.data() : (const void*)dVf.data(), (size_t)b->esz * Nx));
-    B_TRY(H2D(L.ringV, fx ? (const void*)V.data() : (const void*)Vf.data(), (size_t)b->esz * Nx));
+    std::vector<long long> Kq(Nx), Vq(Nx);
+    if (r->model == VLASOV_RING) {
+        ring_fixed_tables(Nx, dx, r->eps, Kq.data(), Vq.data(), &s.ring_sK, &s.ring_sV);
+        B_TRY(H2D(L.ringKq, Kq.data(), 8 * (size_t)Nx));
+        B_TRY(H2D(L.ringVq, Vq.data(), 8 * (size_t)Nx));
+    }
     B_TRY(H2D(L.xrec, recs.data(), recs.size()));
     if (host_f0 && fx) {
         std::vector<long long> tmp(cells);

@@ -1,0 +1,410 @@
+// ring.cu -- the ring model's mean force and potential energy, Eq. (ringpot) into Eq. (meanforce)
+// (Sec. 2), as a circulant convolution on the theta nodes:
+//
+//   F_i   = -dx sum_k V'((i-k) dx) rho_k        (after each first x half-shift)
+//   Phi_i =  dx sum_k V ((i-k) dx) rho_k,  U = 1/2 dx sum_i rho_i Phi_i   (after the step)
+//
+// Two methods besides the direct FMA loop of aux_kernels.cu (ring_kernel):
+//
+//  * FIXED: an exact fixed-point sum.  The density arrives as exact int64 column sums t_k
+//    (rho_k = dp t_k 2^-k_col, from the x-shift's partial sums), the kernel tables as round(V'(m dx)
+//    2^sK) and round(V(m dx) 2^sV) with |table| <= 2^(64 - log2 N); every product t_k * table is an
+//    exact int128 and so is every sum.  The only roundings are the table entries (relative 2^-52, the
+//    FP64 representation of V') and the final conversion, so the force is FP64-accurate in every
+//    storage mode, deterministic, and independent of the launch shape.  The multiply-adds run on
+//    the integer pipe (64-bit mad.lo/madc.hi pairs), which on this GPU is many times faster than the
+//    FP64 pipe.
+//  * FFT: a Stockham radix-2 FFT (Govindaraju et al., SC 2008) in shared memory, one CTA per
+//    grid, in FP64 or FP32: F = -dx/N Re IFFT(FFT(V') FFT(rho)); the potential by Parseval,
+//    sum_i rho_i Phi_i = dx/N sum_k |FFT(rho)_k|^2 FFT(V)_k (V even, so FFT(V) is real).  N a power
+//    of two.  The spectra of the kernel tables are computed once on the host.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fixed_point.cuh"
+#include "vlasov_internal.cuh"
+
+namespace vl {
+
+// ============================================================================ FIXED
+// acc (hi:lo, two's complement int128) += a * b, a and b signed int64.
+__device__ __forceinline__ void mac128(unsigned long long& lo, long long& hi, long long a, long long b)
+{
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.s64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+}
+
+__device__ __forceinline__ i128 ld_i128_cg(const void* p)
+{
+    const longlong2 v = __ldcg(static_cast<const longlong2*>(p));
+    return (i128)(((u128)(unsigned long long)v.y << 64) | (u128)(unsigned long long)v.x);
+}
+
+int ringfx_ksplit(int N, int nsm)
+{
+    const int ngrp = (N + 31) / 32;
+    const int ks = (int)std::lround(2.0 * (double)nsm / (double)ngrp);
+    return std::max(1, std::min(ks, std::max(1, N / 256)));
+}
+
+size_t ringfx_smem_bytes(int N, int ksplit)
+{
+    const int len = (N + ksplit - 1) / ksplit;
+    return (size_t)(2 * len + 32) * sizeof(long long);
+}
+
+// Block (g, q): outputs i = 32 g + lane, inputs k in the q-th of ksplit slices [kb, ke) of [0, N).
+// Warp w adds the w-th eighth of the slice.  Warp sums and slice sums are exact int128 additions,
+// so the result does not depend on the split; the last slice block of a group (ticket) finishes it.
+template <bool POT>
+__device__ __forceinline__ void ringfx_body(const RingArgs& a, int bx)
+{
+    constexpr int NW = RINGFX_THREADS / 32;
+    extern __shared__ __align__(16) long long rfx_smem[];
+    __shared__ i128 wsum[NW][32];
+    const int N = a.N, ngrp = (N + 31) >> 5;
+    const int g = bx % ngrp, q = bx / ngrp;
+    if (q >= a.ksplit) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int kb = (int)(((long long)N * q) / a.ksplit), ke = (int)(((long long)N * (q + 1)) / a.ksplit);
+    const int len = ke - kb;
+    const int i0 = g << 5;
+    long long* ts = rfx_smem;          // t_k, k = kb .. ke - 1
+    long long* kk = rfx_smem + len;    // table entries at m = (base + r) mod N, r = 0 .. len + 30
+    const long long* __restrict__ tab = POT ? a.Vq : a.Kq;
+    for (int r = threadIdx.x; r < len; r += RINGFX_THREADS) ts[r] = __ldcg(a.colfx + kb + r);
+    const int base = i0 - ke + 1;      // > -N
+    for (int r = threadIdx.x; r < len + 31; r += RINGFX_THREADS) {
+        int m = (base + r) % N;
+        if (m < 0) m += N;
+        kk[r] = __ldg(tab + m);
+    }
+    __syncthreads();
+    // output i = i0 + lane, input k = kb + j: the table entry at i - k is kk[len - 1 + lane - j].
+    // Four independent accumulators (j mod 4) keep four carry chains in flight per lane.
+    constexpr int NACC = 4;
+    unsigned long long lo[NACC];
+    long long hi[NACC];
+#pragma unroll
+    for (int u = 0; u < NACC; ++u) {
+        lo[u] = 0;
+        hi[u] = 0;
+    }
+    const int jb = (len * w) / NW, je = (len * (w + 1)) / NW;
+    const long long* kp = kk + (len - 1 + lane);
+    int j = jb;
+    for (; j + NACC <= je; j += NACC) {
+#pragma unroll
+        for (int u = 0; u < NACC; ++u) mac128(lo[u], hi[u], kp[-(j + u)], ts[j + u]);
+    }
+    for (; j < je; ++j) mac128(lo[0], hi[0], kp[-j], ts[j]);
+    i128 ws = 0;
+#pragma unroll
+    for (int u = 0; u < NACC; ++u) ws += (i128)(((u128)(unsigned long long)hi[u] << 64) | (u128)lo[u]);
+    wsum[w][lane] = ws;
+    __syncthreads();
+    if (w != 0) return;
+
+    i128 s = 0;
+#pragma unroll
+    for (int v = 0; v < NW; ++v) s += wsum[v][lane];
+    const int i = i0 + lane;
+    if (a.ksplit > 1) {
+        i128* gp = static_cast<i128*>(a.gpart);
+        if (i < N) gp[(size_t)q * N + i] = s;
+        __threadfence();
+        __syncwarp();
+        unsigned int tk = 0;
+        if (lane == 0) tk = atomicAdd(&a.gticket[g], 1u);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk != (unsigned int)a.ksplit - 1) return;
+        __threadfence();
+        s = 0;
+        if (i < N)
+            for (int r = 0; r < a.ksplit; ++r) s += ld_i128_cg(gp + (size_t)r * N + i);
+        if (lane == 0) a.gticket[g] = 0u;   // ready for the next launch
+    }
+    if constexpr (!POT) {
+        if (i < N) a.F[i] = fx128_to_f64(s, a.k_col + a.sK) * (-a.dx * a.dp);
+    } else {
+        // rho_i * Phi_i with Phi_i = dx dp 2^-(k_col+sV) S_i, summed exactly (scale 2^k_pot)
+        i128 u = 0;
+        if (i < N) u = fx128_from_f64(a.rho[i] * (a.dx * a.dp * fx128_to_f64(s, a.k_col + a.sV)), a.k_pot);
+        u = warp_sum_i128(u);
+        i128* up = static_cast<i128*>(a.upart);
+        unsigned int tk = 0;
+        if (lane == 0) {
+            up[g] = u;
+            __threadfence();
+            tk = atomicAdd(a.ticket, 1u);
+        }
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk != (unsigned int)ngrp - 1) return;
+        __threadfence();
+        i128 t = 0;
+        for (int r = lane; r < ngrp; r += 32) t += ld_i128_cg(up + r);
+        t = warp_sum_i128(t);
+        if (lane != 0) return;
+        *a.ticket = 0u;
+        const double U = a.pot_scale * fx128_to_f64(t, a.k_pot);
+        const Scalars sc = *a.sc;
+        const long long st = *a.step;
+        MomentRec rec;
+        rec.t = (double)(st + 1) * a.dt;
+        rec.mass = sc.mass;
+        rec.Mx = sc.Mx;
+        rec.My = sc.My;
+        rec.kinetic = sc.kinetic;
+        rec.potential = U;
+        rec.energy = sc.kinetic + U;
+        rec.step = st + 1;
+        a.hist[st % HIST_CAP] = rec;
+        *a.step = st + 1;
+        a.sc->potential = U;
+    }
+}
+
+template <bool POT>
+__global__ void __launch_bounds__(RINGFX_THREADS) ringfx_kernel(RingArgs a)
+{
+    ringfx_body<POT>(a, blockIdx.x);
+}
+
+// Batched form: blockIdx.y = slot (N = 0: not a ring slot); each slot keeps its own split.
+template <bool POT>
+__global__ void __launch_bounds__(RINGFX_THREADS) ringfx_batch_kernel(const RingArgs* __restrict__ args)
+{
+    const RingArgs a = args[blockIdx.y];
+    if (a.N <= 0) return;
+    ringfx_body<POT>(a, blockIdx.x);
+}
+
+// Blocks and shared memory a batched launch needs to cover every slot size N <= max_n (a smaller N
+// can take a few more blocks than max_n itself, as the split is rounded).
+static void ringfx_batch_shape(int max_n, int nsm, int* blocks, size_t* smem)
+{
+    *blocks = 1;
+    *smem = 0;
+    for (int N = 16; N <= max_n; N += 8) {
+        const int ks = ringfx_ksplit(N, nsm);
+        *blocks = std::max(*blocks, ((N + 31) / 32) * ks);
+        *smem = std::max(*smem, ringfx_smem_bytes(N, ks));
+    }
+}
+
+cudaError_t launch_ring_fixed_batch(bool pot, int slots, int max_n, int nsm, const RingArgs* args, cudaStream_t st)
+{
+    int blocks = 0;
+    size_t smem = 0;
+    ringfx_batch_shape(max_n, nsm, &blocks, &smem);
+    const dim3 grid(blocks, slots);
+    if (pot) ringfx_batch_kernel<true><<<grid, RINGFX_THREADS, smem, st>>>(args);
+    else ringfx_batch_kernel<false><<<grid, RINGFX_THREADS, smem, st>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring_fixed(const RingArgs& a, cudaStream_t st)
+{
+    const int ngrp = (a.N + 31) / 32;
+    const size_t smem = ringfx_smem_bytes(a.N, a.ksplit);
+    if (a.final_moments) ringfx_kernel<true><<<ngrp * a.ksplit, RINGFX_THREADS, smem, st>>>(a);
+    else ringfx_kernel<false><<<ngrp * a.ksplit, RINGFX_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static int ceil_log2_host(double v)
+{
+    int e = 0;
+    const double m = std::frexp(v, &e);   // v = m 2^e, m in [0.5, 1)
+    return m == 0.5 ? e - 1 : e;
+}
+
+void ring_fixed_tables(int N, double dx, double eps, long long* Kq, long long* Vq, int* sK, int* sV)
+{
+    // |entry| <= 2^(64 - ceil log2 N): N products with |t_k| < 2^62 stay inside int128
+    const int bits = 64 - ceil_log2_host((double)N);
+    std::vector<double> dV(N), V(N);
+    double mK = 0, mV = 0;
+    for (int i = 0; i < N; ++i) {
+        const double u = (double)i * dx;
+        const double q = 1.0 - std::cos(u) + eps;
+        dV[i] = std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q));   // V'(u), Eq. (ringpot)
+        V[i] = -1.0 / (std::sqrt(2.0) * std::sqrt(q));                      // V(u)
+        mK = std::max(mK, std::fabs(dV[i]));
+        mV = std::max(mV, std::fabs(V[i]));
+    }
+    *sK = bits - ceil_log2_host(mK);
+    *sV = bits - ceil_log2_host(mV);
+    for (int i = 0; i < N; ++i) {
+        Kq[i] = std::llround(std::ldexp(dV[i], *sK));
+        Vq[i] = std::llround(std::ldexp(V[i], *sV));
+    }
+}
+
+// ============================================================================ FFT
+bool ring_fft_ok(int N) { return N >= 16 && N <= 4096 && (N & (N - 1)) == 0; }
+
+size_t ring_fft_smem_bytes(int N, bool f64) { return (size_t)2 * N * (f64 ? 16 : 8); }
+
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b)
+{
+    T2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Stockham radix-2 transform of the N points in `a` (N a power of two), using `b` as the other
+// buffer; returns the buffer that holds the result (natural order).  Unnormalised; inverse = the
+// conjugate twiddles.  tw[m] = exp(-2 pi i m / N), m < N/2.
+template <typename T2>
+__device__ T2* stockham(T2* a, T2* b, int N, const T2* __restrict__ tw, bool inverse)
+{
+    const int half = N >> 1;
+    for (int Ns = 1; Ns < N; Ns <<= 1) {
+        const int stride = half / Ns;
+        for (int j = threadIdx.x; j < half; j += blockDim.x) {
+            const int k = j & (Ns - 1);
+            T2 w = tw[k * stride];
+            if (inverse) w.y = -w.y;
+            const T2 u = a[j];
+            const T2 v = cmul(a[j + half], w);
+            const int o = ((j - k) << 1) + k;   // (j / Ns) * 2 Ns + k
+            T2 p, m;
+            p.x = u.x + v.x;
+            p.y = u.y + v.y;
+            m.x = u.x - v.x;
+            m.y = u.y - v.y;
+            b[o] = p;
+            b[o + Ns] = m;
+        }
+        __syncthreads();
+        T2* t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// One CTA: FFT of rho; the force by the inverse transform of FFT(V') FFT(rho), or the potential by
+// Parseval with FFT(V) (then the moment record, as the other methods write it).
+template <typename T, typename T2>
+__global__ void __launch_bounds__(RING_FFT_THREADS) ring_fft_kernel(RingArgs a)
+{
+    extern __shared__ __align__(16) unsigned char rfft_smem[];
+    __shared__ i128 red[33];
+    T2* A = reinterpret_cast<T2*>(rfft_smem);
+    T2* B = A + a.N;
+    const int N = a.N;
+    const T2* __restrict__ tw = static_cast<const T2*>(a.twid);
+    for (int i = threadIdx.x; i < N; i += RING_FFT_THREADS) {
+        T2 z;
+        z.x = (T)a.rho[i];
+        z.y = T(0);
+        A[i] = z;
+    }
+    __syncthreads();
+    T2* R = stockham(A, B, N, tw, false);
+    T2* S = (R == A) ? B : A;
+    if (!a.final_moments) {
+        const T2* __restrict__ kh = static_cast<const T2*>(a.khat);
+        for (int k = threadIdx.x; k < N; k += RING_FFT_THREADS) R[k] = cmul(R[k], kh[k]);
+        __syncthreads();
+        const T2* out = stockham(R, S, N, tw, true);
+        const double scale = -a.dx / (double)N;
+        for (int i = threadIdx.x; i < N; i += RING_FFT_THREADS) a.F[i] = scale * (double)out[i].x;
+        return;
+    }
+    // the terms rho_i (dx sum_k V_{i-k} rho_k) the other methods add, by Parseval:
+    // sum_i rho_i dx (V * rho)_i = dx / N sum_k |R_k|^2 Vhat_k; summed exactly at scale 2^k_pot
+    const T2* __restrict__ vh = static_cast<const T2*>(a.vhat);
+    const double c = a.dx / (double)N;
+    i128 u = 0;
+    for (int k = threadIdx.x; k < N; k += RING_FFT_THREADS) {
+        const double re = (double)R[k].x, im = (double)R[k].y;
+        u += fx128_from_f64((re * re + im * im) * (double)vh[k].x * c, a.k_pot);
+    }
+    u = block_sum_i128(u, red);
+    if (threadIdx.x != 0) return;
+    const double U = a.pot_scale * fx128_to_f64(u, a.k_pot);
+    const Scalars sc = *a.sc;
+    const long long st = *a.step;
+    MomentRec rec;
+    rec.t = (double)(st + 1) * a.dt;
+    rec.mass = sc.mass;
+    rec.Mx = sc.Mx;
+    rec.My = sc.My;
+    rec.kinetic = sc.kinetic;
+    rec.potential = U;
+    rec.energy = sc.kinetic + U;
+    rec.step = st + 1;
+    a.hist[st % HIST_CAP] = rec;
+    *a.step = st + 1;
+    a.sc->potential = U;
+}
+
+cudaError_t launch_ring_fft(bool f64, const RingArgs& a, cudaStream_t st)
+{
+    const size_t smem = ring_fft_smem_bytes(a.N, f64);
+    if (f64) ring_fft_kernel<double, double2><<<1, RING_FFT_THREADS, smem, st>>>(a);
+    else ring_fft_kernel<float, float2><<<1, RING_FFT_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Opt every kernel of this file into the dynamic shared memory it may use: the per-block limit
+// max_smem less its own static shared memory.
+template <typename K>
+static cudaError_t allow_dynamic_smem(K kernel, int max_smem)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+}
+
+cudaError_t set_ringfx_attributes(int max_smem)
+{
+    cudaError_t e = allow_dynamic_smem(ringfx_kernel<false>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_kernel<true>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_batch_kernel<false>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_batch_kernel<true>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ring_fft_kernel<double, double2>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ring_fft_kernel<float, float2>, max_smem);
+    return e;
+}
+
+// Host DFT of a real table: out[2k] + i out[2k+1] = sum_m v_m exp(-2 pi i m k / N), with an FP64
+// twiddle table and Neumaier-compensated sums (used once per handle for the FFT method's spectra).
+void ring_dft_host(const double* v, int N, double* out)
+{
+    std::vector<double> c(N), s(N);
+    for (int r = 0; r < N; ++r) {
+        const double ang = 2.0 * 3.14159265358979323846 * (double)r / (double)N;
+        c[r] = std::cos(ang);
+        s[r] = -std::sin(ang);
+    }
+    auto add = [](double& sum, double& comp, double x) {
+        const double t = sum + x;
+        if (std::fabs(sum) >= std::fabs(x)) comp += (sum - t) + x;
+        else comp += (x - t) + sum;
+        sum = t;
+    };
+    for (int k = 0; k < N; ++k) {
+        double re = 0, rc = 0, im = 0, ic = 0;
+        long long r = 0;
+        for (int m = 0; m < N; ++m) {
+            add(re, rc, v[m] * c[r]);
+            add(im, ic, v[m] * s[r]);
+            r += k;
+            if (r >= N) r -= N;
+        }
+        out[2 * k] = re + rc;
+        out[2 * k + 1] = im + ic;
+    }
+}
+
+}  // namespace vl

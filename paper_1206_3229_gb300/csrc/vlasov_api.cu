@@ -71,7 +71,7 @@ struct vlasov_sim {
     double xmin = 0, xmax = 0, pmin = 0, pmax = 0, dx = 0, dp = 0, dt = 0, eps = 0, G = 1;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, max_smem = 0;   // max_smem: opt-in shared memory per block
 
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
@@ -113,6 +113,16 @@ struct vlasov_sim {
                                   //   sweeps hand over column partials)
     void* ringdV = nullptr;     // in the storage type
     void* ringV = nullptr;
+    // ring force methods (ring.cu): exact fixed-point tables and scratch, FFT spectra and twiddles
+    int ring_method = RING_M_FIXED;
+    long long* ringKq = nullptr;
+    long long* ringVq = nullptr;
+    int ring_sK = 0, ring_sV = 0, ring_ksplit = 1;
+    void* ring_gpart = nullptr;
+    unsigned int* ring_gticket = nullptr;
+    void* ring_upart = nullptr;
+    void* ring_fft64 = nullptr;   // [khat N | vhat N | twiddles N/2] double2
+    void* ring_fft32 = nullptr;   // same as float2
     // fixed-point scales of the reductions (from a bound 2^Ef >= 4 max|f|)
     int Ef = 0, k_col = 0, k_kin = 0, k_pot = 0;
     bool scales_set = false;
@@ -507,7 +517,37 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     a.hist = s->hist;
     a.step = s->dstep;
     a.dt = s->dt;
+    a.colfx = s->colfx;
+    a.Kq = s->ringKq;
+    a.Vq = s->ringVq;
+    a.k_col = s->k_col;
+    a.sK = s->ring_sK;
+    a.sV = s->ring_sV;
+    a.dp = s->dp;
+    a.ksplit = s->ring_ksplit;
+    a.gpart = s->ring_gpart;
+    a.gticket = s->ring_gticket;
+    a.upart = s->ring_upart;
+    const bool f64 = s->ring_method != RING_M_FFT32;
+    const size_t e2 = f64 ? 16 : 8;
+    unsigned char* t = static_cast<unsigned char*>(f64 ? s->ring_fft64 : s->ring_fft32);
+    a.khat = t;
+    a.vhat = t ? t + e2 * (size_t)s->Nx : nullptr;
+    a.twid = t ? t + 2 * e2 * (size_t)s->Nx : nullptr;
     return a;
+}
+
+// The ring force (final_moments = false) or potential and moment record (true) by the handle's
+// method; one launch either way.
+cudaError_t run_ring(vlasov_sim* s, bool final_moments)
+{
+    const RingArgs a = ringargs(s, final_moments);
+    switch (s->ring_method) {
+    case RING_M_FIXED: return launch_ring_fixed(a, s->st);
+    case RING_M_FFT64: return launch_ring_fft(true, a, s->st);
+    case RING_M_FFT32: return launch_ring_fft(false, a, s->st);
+    default: return launch_ring(s->msz, a, s->st);
+    }
 }
 
 int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int ctas = 0)
@@ -546,7 +586,7 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int 
 
 int launch_force_params(vlasov_sim* s, double* Fout)
 {
-    if (s->model == VLASOV_RING) CU_TRY(launch_ring(s->msz, ringargs(s, false), s->st));
+    if (s->model == VLASOV_RING) CU_TRY(run_ring(s, false));
     return launch_pparams_only(s, Fout);
 }
 
@@ -589,7 +629,7 @@ int enq_force_p(vlasov_sim* s, int c, int ctas, Marks* marks)
         CU_TRY(launch_colreduce(crargs(s, ctas, false, false), s->crgrid, s->st));
         MARK();
         if (s->model == VLASOV_RING) {
-            CU_TRY(launch_ring(s->msz, ringargs(s, false), s->st));
+            CU_TRY(run_ring(s, false));
             MARK();
         }
         int rc = launch_pparams_only(s, nullptr);
@@ -615,7 +655,7 @@ int enq_moments(vlasov_sim* s, int ctas, bool fused_m, Marks* marks)
     }
     MARK();
     if (s->model == VLASOV_RING) {
-        CU_TRY(launch_ring(s->msz, ringargs(s, true), s->st));
+        CU_TRY(run_ring(s, true));
         MARK();
     }
     return VLASOV_OK;
@@ -765,7 +805,8 @@ void vlasov_destroy(vlasov_sim* s)
     void* bufs[] = {s->colpart, s->colacc, s->kinpart, s->rho, s->colfx, s->Qd, s->F, s->Fout, s->blockpart, s->ringpart,
                     s->tickets, s->maxbits, s->sc, s->costab, s->sintab, s->cosfx, s->sinfx, s->ringdV, s->ringV,
                     s->hist, s->dstep, s->err, s->xrec, s->srec, s->cos50, s->sin50, s->ctapart,
-                    s->ctapart_m, s->colpart_m, s->kin128, s->gs_h};
+                    s->ctapart_m, s->colpart_m, s->kin128, s->gs_h, s->ringKq, s->ringVq, s->ring_gpart,
+                    s->ring_gticket, s->ring_upart, s->ring_fft64, s->ring_fft32};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -833,6 +874,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
     int max_optin = 0;
     CTRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
+    s->max_smem = max_optin;
     if (d->stream) {
         s->st = static_cast<cudaStream_t>(d->stream);
     } else {
@@ -843,6 +885,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(set_kernel_attributes_e(max_optin - 1024));
     CTRY(set_kernel_attributes_fx(max_optin - 1024));
     CTRY(set_ring_attributes(max_optin - 1024));
+    CTRY(set_ringfx_attributes(max_optin - 1024));
 
     const size_t cells = (size_t)Nx * (size_t)Np;
     for (int b = 0; b < 2; ++b) {
@@ -1034,6 +1077,23 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
             CTRY(cudaMemcpyAsync(s->ringdV, dVf.data(), sizeof(float) * Nx, cudaMemcpyHostToDevice, s->st));
             CTRY(cudaMemcpyAsync(s->ringV, Vf.data(), sizeof(float) * Nx, cudaMemcpyHostToDevice, s->st));
             CTRY(cudaStreamSynchronize(s->st));
+        }
+        if (model == VLASOV_RING) {
+            // tables and scratch of the exact fixed-point method
+            std::vector<long long> Kq(Nx), Vq(Nx);
+            ring_fixed_tables(Nx, s->dx, s->eps, Kq.data(), Vq.data(), &s->ring_sK, &s->ring_sV);
+            s->ring_ksplit = ringfx_ksplit(Nx, s->nsm);
+            const int ngrp = (Nx + 31) / 32;
+            CTRY(cudaMalloc(&s->ringKq, sizeof(long long) * Nx));
+            CTRY(cudaMalloc(&s->ringVq, sizeof(long long) * Nx));
+            CTRY(cudaMalloc(&s->ring_gpart, 16 * (size_t)s->ring_ksplit * Nx));
+            CTRY(cudaMalloc(&s->ring_gticket, sizeof(unsigned int) * ngrp));
+            CTRY(cudaMemsetAsync(s->ring_gticket, 0, sizeof(unsigned int) * ngrp, s->st));
+            CTRY(cudaMalloc(&s->ring_upart, 16 * (size_t)ngrp));
+            CTRY(cudaMemcpyAsync(s->ringKq, Kq.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
+            CTRY(cudaMemcpyAsync(s->ringVq, Vq.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
+            CTRY(cudaStreamSynchronize(s->st));
+            if (ringfx_smem_bytes(Nx, s->ring_ksplit) + 8192 > (size_t)max_optin) s->ring_method = RING_M_DIRECT;
         }
     }
     TRY(make_tmap(s, 0));
@@ -1338,6 +1398,116 @@ int vlasov_casimirs(vlasov_sim* s, double* entropy, double* l2)
     if (entropy) *entropy = h[0];
     if (l2) *l2 = h[1];
     return check_dev_err(s);
+}
+
+// Spectra and twiddles of the FFT ring method, computed once per handle and arithmetic type.
+static int ring_fft_tables(vlasov_sim* s, bool f64)
+{
+    void** slot = f64 ? &s->ring_fft64 : &s->ring_fft32;
+    if (*slot) return VLASOV_OK;
+    const int N = s->Nx;
+    std::vector<double> dV(N), V(N), kh(2 * (size_t)N), vh(2 * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        const double u = (double)i * s->dx;
+        const double q = 1.0 - std::cos(u) + s->eps;
+        dV[i] = std::sin(u) / (2.0 * std::sqrt(2.0) * q * std::sqrt(q));
+        V[i] = -1.0 / (std::sqrt(2.0) * std::sqrt(q));
+    }
+    ring_dft_host(dV.data(), N, kh.data());
+    ring_dft_host(V.data(), N, vh.data());
+    std::vector<double> all(2 * (size_t)N * 2 + (size_t)N);   // khat, vhat (N complex each), twiddles (N/2)
+    std::copy(kh.begin(), kh.end(), all.begin());
+    std::copy(vh.begin(), vh.end(), all.begin() + 2 * (size_t)N);
+    for (int m = 0; m < N / 2; ++m) {
+        const double ang = 2.0 * 3.14159265358979323846 * (double)m / (double)N;
+        all[4 * (size_t)N + 2 * m] = std::cos(ang);
+        all[4 * (size_t)N + 2 * m + 1] = -std::sin(ang);
+    }
+    const size_t n = all.size();
+    if (f64) {
+        CU_TRY(cudaMalloc(slot, n * sizeof(double)));
+        CU_TRY(cudaMemcpy(*slot, all.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> af(all.begin(), all.end());
+        CU_TRY(cudaMalloc(slot, n * sizeof(float)));
+        CU_TRY(cudaMemcpy(*slot, af.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return VLASOV_OK;
+}
+
+int vlasov_set_ring_method(vlasov_sim* s, int method)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (s->model != VLASOV_RING) return fail(VLASOV_EINVAL, "not a ring-model handle");
+    if (method == VLASOV_RING_FIXED) {
+        if (ringfx_smem_bytes(s->Nx, s->ring_ksplit) + 8192 > (size_t)s->max_smem)
+            return fail(VLASOV_EINVAL, "fixed-point ring method: Nx too large for shared memory");
+    } else if (method == VLASOV_RING_FFT || method == VLASOV_RING_FFT_F32) {
+        if (!ring_fft_ok(s->Nx)) return fail(VLASOV_EINVAL, "FFT ring method needs Nx a power of two <= 4096");
+        const bool f64 = method == VLASOV_RING_FFT;
+        if (ring_fft_smem_bytes(s->Nx, f64) + 8192 > (size_t)s->max_smem)
+            return fail(VLASOV_EINVAL, "FFT ring method: Nx too large for shared memory");
+        int rc = ring_fft_tables(s, f64);
+        if (rc) return rc;
+    } else if (method != VLASOV_RING_DIRECT) {
+        return fail(VLASOV_EINVAL, "unknown ring method %d", method);
+    }
+    CU_TRY(cudaStreamSynchronize(s->st));
+    if (s->ring_method != method) drop_graphs(s);
+    s->ring_method = method;
+    return VLASOV_OK;
+}
+
+int vlasov_ring_method(const vlasov_sim* s) { return (s && s->model == VLASOV_RING) ? s->ring_method : 0; }
+
+int vlasov_ring_timings(vlasov_sim* s, int reps, double* us)
+{
+    if (!s || !us) return fail(VLASOV_EINVAL, "NULL argument");
+    if (s->model != VLASOV_RING) return fail(VLASOV_EINVAL, "not a ring-model handle");
+    if (!s->has_f) return fail(VLASOV_ESTATE, "vlasov_ring_timings before vlasov_set_f");
+    if (reps < 1 || reps > 100000) return fail(VLASOV_EINVAL, "reps must be in [1, 1e5]");
+    for (int m = 0; m < VLASOV_RING_METHODS; ++m) us[m] = 0.0;
+    // density of the current f (as vlasov_density_force), then each method's force launch
+    if (s->fx) CU_TRY(launch_colsum_fx(static_cast<const long long*>(s->f[s->cur]), s->Nx, s->Np, s->Ef, s->colpart, s->st));
+    else CU_TRY(launch_colsum(s->esz, s->f[s->cur], s->Nx, s->Np, s->colpart, 1, s->st));
+    CU_TRY(launch_colreduce(crargs(s, 1, false, false, false), s->crgrid, s->st));
+    const int keep = s->ring_method;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU_TRY(cudaEventCreate(&e0));
+    CU_TRY(cudaEventCreate(&e1));
+    int rc = VLASOV_OK;
+    for (int m = VLASOV_RING_DIRECT; m < VLASOV_RING_METHODS && !rc; ++m) {
+        if (m == VLASOV_RING_TENSOR) continue;
+        const bool fft = m == VLASOV_RING_FFT || m == VLASOV_RING_FFT_F32;
+        if (fft && !ring_fft_ok(s->Nx)) continue;
+        if (fft && ring_fft_smem_bytes(s->Nx, m == VLASOV_RING_FFT) + 8192 > (size_t)s->max_smem) continue;
+        if (fft && (rc = ring_fft_tables(s, m == VLASOV_RING_FFT)) != VLASOV_OK) break;
+        if (m == VLASOV_RING_FIXED && ringfx_smem_bytes(s->Nx, s->ring_ksplit) + 8192 > (size_t)s->max_smem) continue;
+        s->ring_method = m;
+        cudaError_t e = run_ring(s, false);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s->st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run_ring(s, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = fail(VLASOV_ECUDA, "ring timing: %s", cudaGetErrorString(e));
+        else us[m] = 1e3 * (double)ms / reps;
+    }
+    s->ring_method = keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    return check_dev_err(s);
+}
+
+int vlasov_test_expire_wait(vlasov_sim* s, long long limit_ns)
+{
+    if (!s) return fail(VLASOV_EINVAL, "NULL handle");
+    if (limit_ns < 1000 || limit_ns > 2000000000ll)
+        return fail(VLASOV_EINVAL, "limit_ns must be in [1e3, 2e9]");
+    CU_TRY(launch_expire_wait(s->err, (unsigned long long)limit_ns, s->st));
+    return VLASOV_OK;
 }
 
 int vlasov_sync(vlasov_sim* s)

@@ -113,7 +113,8 @@ inline void gs_filter_h(double h[GS_HTAPS])
 }
 
 // Device-side error codes written to the handle's flag by a bounded wait that gave up.
-enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2, DEV_ERR_RANGE = 3 };
+enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2, DEV_ERR_RANGE = 3,
+             DEV_ERR_TEST_WAIT = 4 };
 
 // Scalars produced by the reductions of one sweep (device struct).
 struct Scalars {
@@ -290,7 +291,43 @@ struct RingArgs {
     MomentRec* hist;
     long long* step;
     double dt;
+    // exact fixed-point form (ring.cu): t_k = exact column sums (rho_k = dp t_k 2^-k_col), kernel
+    // tables round(V'(m dx) 2^sK) and round(V(m dx) 2^sV)
+    const long long* colfx;
+    const long long* Kq;
+    const long long* Vq;
+    int k_col, sK, sV;
+    double dp;
+    int ksplit;              // blocks per group of 32 outputs
+    void* gpart;             // int128 [ksplit][N] partial sums
+    unsigned int* gticket;   // [ceil(N/32)] per-group tickets
+    void* upart;             // int128 [ceil(N/32)] potential partials per group
+    // FFT form (ring.cu): spectra of the kernel tables and the twiddles exp(-2 pi i m / N), m < N/2,
+    // in the FFT's arithmetic type (double2 or float2)
+    const void* khat;
+    const void* vhat;
+    const void* twid;
 };
+
+// Ring force and potential by method (ring.cu): VLASOV_RING_DIRECT runs ring_kernel (FMA in the
+// arithmetic type); FIXED the exact fixed-point sum; FFT_F64 / FFT_F32 the shared-memory FFT.
+enum : int { RING_M_DIRECT = 1, RING_M_FIXED = 2, RING_M_FFT64 = 3, RING_M_FFT32 = 4, RING_M_TENSOR = 5 };
+constexpr int RINGFX_THREADS = 256;
+constexpr int RING_FFT_THREADS = 1024;
+int ringfx_ksplit(int N, int nsm);
+size_t ringfx_smem_bytes(int N, int ksplit);
+cudaError_t set_ringfx_attributes(int max_smem);
+cudaError_t launch_ring_fixed(const RingArgs& a, cudaStream_t st);
+// Batched fixed-point form: grid.y = slot; each slot's split follows its own N (as a single grid),
+// the launch covers the split of max_n.
+cudaError_t launch_ring_fixed_batch(bool pot, int slots, int max_n, int nsm, const RingArgs* args, cudaStream_t st);
+// Host: the fixed-point kernel tables of a ring grid of N nodes (Kq, Vq: N entries; shifts sK, sV).
+void ring_fixed_tables(int N, double dx, double eps, long long* Kq, long long* Vq, int* sK, int* sV);
+bool ring_fft_ok(int N);
+size_t ring_fft_smem_bytes(int N, bool f64);
+cudaError_t launch_ring_fft(bool f64, const RingArgs& a, cudaStream_t st);
+// Host: exact DFT of a real table (FP64 accumulation over an FP64 twiddle table), out[2k] = Re, out[2k+1] = Im.
+void ring_dft_host(const double* v, int N, double* out);
 
 // ---------------------------------------------------------------------------------------------
 // Launchers (return cudaError_t of the launch).
@@ -363,6 +400,9 @@ constexpr int CAS_BLOCKS = 8 * 152;
 cudaError_t launch_casimirs(int kind, const void* f, size_t n, double unit, double dxdp, double* part, double* out,
                             cudaStream_t st);
 cudaError_t launch_f64_to_fx(const double* s, long long* d, size_t n, int Ef, cudaStream_t st);
+// Failure-path check: one CTA waits on an mbarrier that nothing arrives on, with the bounded wait
+// of the sweep kernels and the given limit, then records DEV_ERR_TEST_WAIT in *err and returns.
+cudaError_t launch_expire_wait(int* err, unsigned long long limit_ns, cudaStream_t st);
 // Waterbag initial states (Sec. 4) written on the device; see aux_kernels.cu.
 constexpr int WB_BLOCKS = 4 * 152;
 constexpr int WB_THREADS = 256;
@@ -397,7 +437,6 @@ cudaError_t launch_xshift_fx_batch(bool periodic, bool kin, int slots, int ctas_
 cudaError_t launch_pshift_fx_batch(int slots, int ctas_per_slot, const CUtensorMap* tmaps, const PShiftArgs* args,
                                    const EmulArgs* ems, const int* ver, cudaStream_t st);
 cudaError_t launch_colreduce_batch(int slots, int blocks_per_slot, const ColReduceArgs* args, cudaStream_t st);
-cudaError_t launch_ring_batch(int elem_bytes, int slots, int max_n, const RingArgs* args, cudaStream_t st);
 cudaError_t launch_pparams_batch(int elem_bytes, int slots, int max_n, const PParamsArgs* args, cudaStream_t st);
 cudaError_t launch_pparams(int elem_bytes, const PParamsArgs& a, cudaStream_t st);
 // HMF, 8-byte storage, from the x-shift's per-CTA partials: force and p-shift parameters

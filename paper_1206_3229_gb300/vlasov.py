@@ -29,7 +29,11 @@ EXPORTED = ("vlasov_create", "vlasov_set_f", "vlasov_set_f_device", "vlasov_get_
             "vlasov_batch_release", "vlasov_batch_destroy", "vlasov_serve", "vlasov_launches",
             "vlasov_set_fused_x", "vlasov_fused_x", "vlasov_batch_create_shaped", "vlasov_batch_shape_of",
             "vlasov_batch_autotune", "vlasov_casimirs", "vlasov_set_spline", "vlasov_spline",
-            "vlasov_init_waterbag")
+            "vlasov_init_waterbag", "vlasov_test_expire_wait", "vlasov_set_ring_method", "vlasov_ring_method",
+            "vlasov_ring_timings")
+
+RING_METHODS = {"direct": 1, "fixed": 2, "fft": 3, "fft_f32": 4, "tensor": 5}
+N_RING_METHODS = 6
 
 SPLINES = {"fd": 0, "gs": 1}   # Eq. (findif) (the paper's method) / global spline, Eq. (tridiagsys)
 
@@ -223,6 +227,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.vlasov_create.argtypes = [ip, ip, ip, ctypes.POINTER(Domain), ctypes.c_double, ctypes.POINTER(vp)]
         lib.vlasov_set_f.argtypes = [vp, dp]
         lib.vlasov_set_f_device.argtypes = [vp, vp]
+        lib.vlasov_test_expire_wait.argtypes = [vp, ctypes.c_longlong]
+        lib.vlasov_set_ring_method.argtypes = [vp, ip]
+        lib.vlasov_ring_method.argtypes = [vp]
+        lib.vlasov_ring_timings.argtypes = [vp, ip, dp]
         lib.vlasov_init_waterbag.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_ulonglong, ip, ctypes.c_double]
         lib.vlasov_get_f.argtypes = [vp, dp]
@@ -391,6 +399,25 @@ class Sim:
 
     def sync(self):
         _check(self._lib.vlasov_sync(self._h))
+
+    @property
+    def ring_method(self) -> str:
+        m = int(self._lib.vlasov_ring_method(self._h))
+        return {v: k for k, v in RING_METHODS.items()}.get(m, "")
+
+    @ring_method.setter
+    def ring_method(self, name: str):
+        _check(self._lib.vlasov_set_ring_method(self._h, RING_METHODS[name]))
+
+    def ring_timings(self, reps: int = 50) -> dict:
+        """vlasov_ring_timings: microseconds per force launch of each ring method that can run."""
+        us = np.zeros(N_RING_METHODS)
+        _check(self._lib.vlasov_ring_timings(self._h, int(reps), _dptr(us)))
+        return {k: float(us[v]) for k, v in RING_METHODS.items() if us[v] > 0}
+
+    def test_expire_wait(self, limit_ns: int):
+        """vlasov_test_expire_wait: enqueue a bounded device wait that must expire (failure-path check)."""
+        _check(self._lib.vlasov_test_expire_wait(self._h, int(limit_ns)))
 
     def casimirs(self) -> tuple[float, float]:
         """(entropy, integral of f^2) of the current f (vlasov_casimirs)."""

@@ -56,6 +56,10 @@ def test_create_rejects_bad_arguments_without_gpu(lib, nx, np_, dt, model, eps, 
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.vlasov_step(None, 1) == V.EINVAL
     assert lib.vlasov_init_waterbag(None, 1.0, 1.0, 0.0, 0, 0, 0.0) == V.EINVAL
+    assert lib.vlasov_set_ring_method(None, V.RING_METHODS["fixed"]) == V.EINVAL
+    assert lib.vlasov_ring_method(None) == 0
+    assert lib.vlasov_ring_timings(None, 1, None) == V.EINVAL
+    assert lib.vlasov_test_expire_wait(None, 1000) == V.EINVAL
     assert lib.vlasov_sync(None) == V.EINVAL
     lib.vlasov_destroy(None)
     assert lib.vlasov_kernels_per_step(None) == 0

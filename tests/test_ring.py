@@ -1,0 +1,129 @@
+"""The ring model's circulant convolutions (Eq. ringpot into Eq. meanforce, Sec. 2) by each method,
+through the C ABI, against the FP64 oracle.
+
+The force is compared with the oracle's force of the very density the GPU computed (returned by
+vlasov_density_force), so the test isolates the convolution: FP64-accurate methods (the exact
+fixed-point sum, the FP64 FFT, the direct FP64 loop) to 1e-13 of max|F|; FP32 arithmetic (the direct
+loop under FP32 storage, the FP32 FFT) to 2e-6 of max|F|.  The potential energy of a moment record is
+compared with the oracle's potential of the state the GPU holds after that step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1206_3229_gb300 import inputs as I
+from paper_1206_3229_gb300 import vlasov as V
+
+pytestmark = pytest.mark.gpu
+
+FP32_ARITH = {("direct", "f32"), ("fft_f32", "f32"), ("fft_f32", "fx64"), ("fft_f32", "f64"),
+              ("fft_f32", "f64_native")}
+
+
+def ring(n, np_=64, **kw):
+    return I.RING_2048.resized(n, np_, **kw)
+
+
+def grid_of(w):
+    return O.Grid(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.x_periodic, w.p_periodic, w.dt,
+                  w.eps, w.G)
+
+
+def tol_of(method, prec):
+    return 2e-6 if (method, prec) in FP32_ARITH else 1e-13
+
+
+def state(w, seed=3):
+    f = I.initial_state(w)
+    rng = np.random.default_rng(seed)
+    # a lopsided density, so that the force has no symmetry to hide an index error
+    th = w.xmin + np.arange(w.nx) * w.dx
+    return f * (1.0 + 0.3 * np.sin(th - 0.7))[None, :] * (1.0 + 0.05 * rng.uniform(-1, 1, f.shape))
+
+
+@pytest.mark.parametrize("prec", ["fx64", "f64", "f64_native", "f32"])
+@pytest.mark.parametrize("method", ["direct", "fixed", "fft", "fft_f32"])
+@pytest.mark.parametrize("n", [256, 2048, 4096, 200])
+def test_force_matches_oracle(n, method, prec):
+    w = ring(n)
+    f = state(w)
+    with V.Sim.from_workload(w, precision=prec) as s:
+        s.set_f(f)
+        if method.startswith("fft") and n & (n - 1):
+            with pytest.raises(V.VlasovError) as e:
+                s.ring_method = method
+            assert e.value.code == V.EINVAL
+            return
+        s.ring_method = method
+        assert s.ring_method == method
+        rho, F = s.density_force()
+    Fo = O.force(grid_of(w), rho)
+    assert np.max(np.abs(F - Fo)) <= tol_of(method, prec) * np.max(np.abs(Fo))
+
+
+@pytest.mark.parametrize("prec", ["fx64", "f32"])
+@pytest.mark.parametrize("method", ["direct", "fixed", "fft", "fft_f32"])
+def test_potential_energy_matches_oracle(method, prec):
+    w = ring(256, 256)
+    with V.Sim.from_workload(w, precision=prec) as s:
+        s.set_f(state(w))
+        s.ring_method = method
+        s.step(3)
+        m = s.moments()
+        f3 = s.get_f()
+    mo = O.moments(grid_of(w), f3)
+    tol = 1e-12 if (method, prec) not in FP32_ARITH else 2e-6
+    assert abs(m[-1, 5] - mo["potential"]) <= tol * abs(mo["potential"])
+    assert abs(m[-1, 6] - (m[-1, 4] + m[-1, 5])) <= 1e-15 * abs(m[-1, 6]) + 1e-300
+
+
+def test_fp64_methods_agree_over_a_run_and_meet_the_oracle():
+    w = ring(256, 256, steps=60)
+    f0 = I.initial_state(w)
+    fo, mo = O.run(grid_of(w), f0, w.steps)
+    for method in ("fixed", "fft", "direct"):
+        with V.Sim.from_workload(w, precision="fx64") as s:
+            s.ring_method = method
+            s.set_f(f0)
+            s.step(w.steps)
+            f, m = s.get_f(), s.moments()
+        assert np.max(np.abs(f - fo)) <= 1e-12 * fo.max(), method
+        assert np.max(np.abs(m[:, 1:7] - mo[:, 1:7])) <= 1e-12, method
+
+
+def test_fixed_method_is_the_default_and_gives_the_same_bits_every_run():
+    w = ring(512, 128, steps=20)
+    out = []
+    for _ in range(2):
+        with V.Sim.from_workload(w, precision="f32") as s:
+            assert s.ring_method == "fixed"
+            s.set_f(I.initial_state(w))
+            s.step(w.steps)
+            out.append((s.get_f(), s.moments()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_ring_timings_report_every_method_and_keep_the_choice():
+    w = ring(2048, 64)
+    with V.Sim.from_workload(w, precision="fx64") as s:
+        s.set_f(state(w))
+        s.ring_method = "fft"
+        t = s.ring_timings(20)
+        assert s.ring_method == "fft"
+    assert set(t) == {"direct", "fixed", "fft", "fft_f32"}
+    assert all(v > 0 for v in t.values())
+
+
+def test_ring_method_errors():
+    with V.Sim.from_workload(I.HMF_256.resized(64), precision="fx64") as s:
+        assert s.ring_method == ""
+        with pytest.raises(V.VlasovError):
+            s.ring_method = "fixed"
+    with V.Sim.from_workload(ring(64), precision="fx64") as s:
+        assert s._lib.vlasov_set_ring_method(s._h, 99) == V.EINVAL
+        assert s.ring_method == "fixed"
+        with pytest.raises(V.VlasovError) as e:
+            s.ring_timings(10)                # no f yet
+        assert e.value.code == V.ESTATE
