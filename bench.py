@@ -144,78 +144,116 @@ def cpu_oracle_timing(w: I.Workload, f0: np.ndarray, budget_s: float, max_steps:
                               "sample": f"1 full Strang step of {w.name} on one core in {single:.2f} s"}}
 
 
-def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, fp64_mode: str = "fx64",
-                      precision: str = "f32") -> dict:
-    """The seeded 512-request serving stream (batched form with `precision` storage, continuous batching).
-
-    Offered load is set to 80% of a capacity measured in the same run on a short calibration burst.
-    Reports aggregate cell-updates/s over the makespan, p50/p99 time-to-result (completion of the
-    last step on the GPU minus arrival), and the same requests' estimated time one at a time on the
-    single-grid FP64-accurate path `fp64_mode` (per-step times measured here per model and grid size).
-    """
+def sequential_single_grid(V, stream_handle, stream, mode: str = "fx64") -> dict:
+    """The requests of a serving stream one at a time on the single-grid path `mode` (measured, not
+    estimated): each request is created, given its initial state on the device, run for its step
+    count and read back.  Device time: CUDA events around each request's steps (its first step,
+    which captures the step graphs, is timed too); wall time: everything, creation included.  The
+    last moment record of each request is the accuracy reference of the batched forms."""
     import torch
+    st_ = torch.cuda.ExternalStream(stream_handle)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev_ms = 0.0
+    last = []
+    t0 = time.perf_counter()
+    for (w, steps, _t) in stream:
+        with V.Sim.from_workload(w, precision=mode, stream=stream_handle) as s:
+            s.init_workload(w)
+            e0.record(st_)
+            s.step(steps)
+            e1.record(st_)
+            e1.synchronize()
+            dev_ms += e0.elapsed_time(e1)
+            last.append(s.moments()[-1])
+    return {"mode": mode, "device_s": dev_ms * 1e-3, "wall_s": time.perf_counter() - t0, "last": np.array(last)}
+
+
+def accuracy_vs(res, seq_last, stream) -> dict:
+    """|dM| = | |M| of the batched result - |M| of the one-at-a-time FP64-accurate run | for every
+    completed request (the magnetisation modulus; for the sheet the same cos/sin moments of x)."""
+    dM = []
+    for q, (r, (w, st, _t)) in enumerate(zip(res, stream)):
+        if r.status != 0:
+            continue
+        mb = math.hypot(r.last.Mx, r.last.My)
+        ms = math.hypot(seq_last[q, 2], seq_last[q, 3])
+        dM.append((abs(mb - ms), w.model, w.nx, st))
+    v = np.array([d[0] for d in dM]) if dM else np.zeros(0)
+    worst = sorted(dM, reverse=True)[:5]
+    by_model = {}
+    for m in ("hmf", "ring", "sheet"):
+        vm = np.array([d[0] for d in dM if d[1] == m])
+        if len(vm):
+            by_model[m] = {"n": int(len(vm)), "max": float(vm.max()), "frac_within_1e-5": float(np.mean(vm <= 1e-5))}
+    return {"dM_all_max": float(v.max()) if len(v) else None, "dM_by_model": by_model,
+            "dM_p99": float(np.percentile(v, 99)) if len(v) else None,
+            "dM_median": float(np.median(v)) if len(v) else None,
+            "frac_within_1e-5": float(np.mean(v <= 1e-5)) if len(v) else None,
+            "n_compared": int(len(v)),
+            "worst": [{"dM": d[0], "model": d[1], "n": d[2], "steps": d[3]} for d in worst]}
+
+
+def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, precision: str, stream, rate: float) -> dict:
+    """The seeded 512-request serving stream in the batched form with `precision` storage, by
+    continuous batching at the given arrival rate.  Reports aggregate cell-updates/s over the
+    makespan and p50/p99 time-to-result (completion of the last step on the GPU minus arrival)."""
     sizes = (256, 512, 1024, 2048)
     # launch shape of the batched sweeps: the project's autotuner, run once before anything is timed
     # (later batches of this max_n and precision use the shape it picked)
-    shape, shape_ms = V.batch_autotune(max(sizes), precision, stream_handle)
-    cal = I.serving_stream(48, seed=55, sizes=sizes, step_scale=0.1, rate_per_s=1e9)
-    reqs = [V.request_from_workload(w, st, 0.0) for (w, st, _t) in cal]
-    _, mk = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision=precision)
-    capacity = sum(w.cells * st for (w, st, _t) in cal) / mk
-    mean_work = float(np.mean([n * n for n in sizes])) * 1050.0
-    rate = 0.8 * capacity / mean_work
-    stream = I.serving_stream(512, seed=5, sizes=sizes, rate_per_s=rate)
+    if precision == "routed":   # two batches (FP32 and FX64 slots), each with the shape tuned for it
+        shapes = {p_: V.batch_autotune(max(sizes), p_, stream_handle)[0] for p_ in ("f32", "fx64")}
+        shape, shape_ms = shapes["f32"], {}
+    else:
+        shape, shape_ms = V.batch_autotune(max(sizes), precision, stream_handle)
     reqs = [V.request_from_workload(w, st, t) for (w, st, t) in stream]
     res, makespan = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision=precision)
     ok = [r.status == 0 for r in res]
     work = sum(w.cells * st for (w, st, _t), good in zip(stream, ok) if good)
     lat = np.array([r.done_s - r.arrival_s for r, good in zip(res, ok) if good])
-
-    # one-at-a-time FP64 single-grid estimate: measured step time per (model, N)
-    t_step = {}
-    for (w, st, _t) in stream:
-        key = (w.model, w.nx)
-        if key in t_step:
-            continue
-        sim = V.Sim.from_workload(w, precision=fp64_mode, stream=stream_handle)
-        sim.set_f(I.initial_state(w))
-        sim.step(3)
-        sim.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        st_ = torch.cuda.ExternalStream(stream_handle) if stream_handle else torch.cuda.current_stream()
-        e0.record(st_)
-        sim.step(10)
-        e1.record(st_)
-        e1.synchronize()
-        t_step[key] = e0.elapsed_time(e1) * 1e-3 / 10
-        sim.close()
-    seq_time = sum(st * t_step[(w.model, w.nx)] for (w, st, _t), good in zip(stream, ok) if good)
-
-    # accuracy: a few finished requests re-run on the FP64 single-grid path from the same f0
-    dM = []
-    for q in [i for i, (w, st, _t) in enumerate(stream) if w.nx <= 1024][:4]:
-        w, st, _t = stream[q]
-        sim = V.Sim.from_workload(w, precision=fp64_mode, stream=stream_handle)
-        sim.set_f(I.initial_state(w))
-        sim.step(st)
-        m = sim.moments()
-        sim.close()
-        dM.append({"model": w.model, "n": w.nx, "steps": st,
-                   "dM": abs(math.hypot(res[q].last.Mx, res[q].last.My) - math.hypot(m[-1, 2], m[-1, 3]))})
     return {"requests": len(reqs), "completed": int(sum(ok)), "slots": slots, "mem_budget_gb": budget_bytes / 2 ** 30,
             "precision": precision,
             "launch_shape": {"rows_per_cta": shape[0], "tiles_per_cta": shape[1],
                              "autotune_ms_per_batched_step": {f"{r}x{t}": round(v, 4) for (r, t), v in shape_ms.items()}},
-            "dtype": ("f32 storage, FP64-accurate displacements and moment sums" if precision == "f32"
-                      else "int64 fixed point + f32 (FP64-accurate), as the single-grid fx64 path"),
-            "aggregate_value": work / makespan, "unit": UNIT, "makespan_s": makespan,
+            "dtype": {"f32": "f32 storage, FP64-accurate displacements (exact fixed-point ring force) and moment sums",
+                      "fx64": "int64 fixed point + f32 (FP64-accurate), as the single-grid fx64 path",
+                      "routed": "ring requests in fx64 slots, HMF and sheet requests in f32 slots (two batches)"}[precision],
+            "aggregate_value": work / makespan, "unit": UNIT, "makespan_s": makespan, "arrival_rate_per_s": rate,
             "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
-            "offered_load_of_capacity": 0.8, "capacity_calibration": capacity, "arrival_rate_per_s": rate,
-            "fp64_single_grid_mode": fp64_mode,
-            "fp64_single_grid_sequential_value": work / seq_time if seq_time > 0 else None,
-            "speedup_vs_fp64_single_grid_sequential": seq_time / makespan if seq_time > 0 else None,
-            "max_abs_dM_vs_fp64_sampled": max(d["dM"] for d in dM) if dM else None, "dM_samples": dM}
+            "_results": res, "_work": work}
+
+
+def serving_section(V, stream_handle, slots: int, budget_bytes: int) -> dict:
+    """Both batched forms on the same stream, the same requests measured one at a time on the
+    single-grid FX64 path, and every request's |dM| against that run.  Offered load: 80% of the FP32
+    batched capacity measured on a calibration burst in the same run."""
+    sizes = (256, 512, 1024, 2048)
+    cal = I.serving_stream(48, seed=55, sizes=sizes, step_scale=0.1, rate_per_s=1e9)
+    creqs = [V.request_from_workload(w, st, 0.0) for (w, st, _t) in cal]
+    V.batch_autotune(max(sizes), "f32", stream_handle)
+    _, mk = V.serve(creqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision="f32")
+    capacity = sum(w.cells * st for (w, st, _t) in cal) / mk
+    rate = 0.8 * capacity / (float(np.mean([n * n for n in sizes])) * 1050.0)
+    stream = I.serving_stream(512, seed=5, sizes=sizes, rate_per_s=rate)
+    out = {"requests": len(stream), "capacity_calibration": capacity, "offered_load_of_capacity": 0.8}
+    seq = sequential_single_grid(V, stream_handle, stream, "fx64")
+    seq_work = sum(w.cells * st for (w, st, _t) in stream)
+    out["sequential_fx64"] = {"device_s": seq["device_s"], "wall_s": seq["wall_s"],
+                              "value_device": seq_work / seq["device_s"], "unit": UNIT,
+                              "note": "the 512 requests run one at a time on the single-grid FX64 path (measured)"}
+    for prec in ("f32", "fx64", "routed"):
+        r = serving_benchmark(V, stream_handle, slots, budget_bytes, prec, stream, rate)
+        res, work = r.pop("_results"), r.pop("_work")
+        r.update(accuracy_vs(res, seq["last"], stream))
+        r["speedup_vs_sequential_fx64_device"] = seq["device_s"] / r["makespan_s"] * (work / seq_work)
+        r["speedup_vs_sequential_fx64_wall"] = seq["wall_s"] / r["makespan_s"] * (work / seq_work)
+        out[prec] = r
+    ok = [p for p in ("f32", "fx64", "routed") if out[p]["dM_all_max"] is not None and out[p]["dM_all_max"] <= 1e-5
+          and out[p]["completed"] == out[p]["requests"]]
+    out["headline_form"] = max(ok, key=lambda p: out[p]["aggregate_value"]) if ok else None
+    out["headline_rule"] = ("the fastest batched form whose every result is within |dM| <= 1e-5 of the "
+                            "one-at-a-time FP64-accurate run")
+    return out
 
 
 DTYPE = {"fx64": "int64 fixed point + f32 (FP64-accurate)", "f64": "f64 storage, int64 + f32 arithmetic (FP64-accurate)",
@@ -265,6 +303,99 @@ def job_value(world: int, cells: int, steps: int, seconds_max: float) -> float:
     return world * cells * steps / seconds_max
 
 
+def bench_config(w: I.Workload, gpus: int, accuracy: str) -> dict:
+    """The `config` object of both arms' JSON lines (same keys and values for the same run)."""
+    cells = w.nx * w.np
+    return {"workload": w.name, "grid": f"{w.nx}x{w.np}", "dt": w.dt, "accuracy": accuracy,
+            "parallelism": "replicas" if gpus > 1 else "single",
+            "l2": f"inputs larger than L2: each sweep streams {16 * cells / 1e6:.0f} MB at FP64 (read + write) "
+                  "against a 129 MB L2"}
+
+
+ACCURACY = {"fx64": "fp64", "f64": "fp64", "f64_native": "fp64", "f32": "fp32", "bf16": "bf16"}
+
+
+def config_checks(V, stream_handle) -> dict:
+    """The three large workloads at their own sizes and step counts, in FX64 (FP64-accurate) and FP32
+    storage, each from its waterbag generated on the device: the growth rate of |M| of the unstable
+    HMF waterbag against the waterbag dispersion relation (gamma = sqrt(1/2 - p0^2), p0^2 = 3 <p^2> of
+    the discrete f0), |dM(t)| of FP32 against FX64, and mass and energy drift (mass leaves through the
+    zero-outside edges once the distribution reaches them)."""
+    out = {}
+    for w in (I.HMF_4096_UNSTABLE, I.RING_2048, I.SHEET_4096):
+        hist, secs = {}, {}
+        for prec in ("fx64", "f32"):
+            with V.Sim.from_workload(w, precision=prec, stream=stream_handle) as s:
+                s.init_workload(w)
+                t0 = time.perf_counter()
+                parts, left = [], w.steps
+                while left:
+                    k = min(left, 4000)
+                    s.step(k)
+                    parts.append(s.moments())
+                    left -= k
+                secs[prec] = time.perf_counter() - t0
+                hist[prec] = np.concatenate(parts)
+        a, b = hist["fx64"], hist["f32"]
+        Ma, Mb = np.hypot(a[:, 2], a[:, 3]), np.hypot(b[:, 2], b[:, 3])
+        d = np.abs(Ma - Mb)
+        over = np.nonzero(d > 1e-5)[0]
+        mass_def = np.abs(a[:, 1] - a[0, 1])
+        leak = np.nonzero(mass_def > 1e-12)[0]
+        e = {"steps": w.steps, "grid": f"{w.nx}x{w.np}", "wall_s": secs,
+             "dM_vs_fp64_max": float(d.max()),
+             "dM_vs_fp64_first_over_1e-5": ({"step": int(over[0]) + 1, "t": float(a[over[0], 0]),
+                                             "M_fp64": float(Ma[over[0]])} if len(over) else None),
+             "mass_drift_max": float(mass_def.max()),
+             "mass_conserved_until_t": float(a[leak[0], 0]) if len(leak) else float(a[-1, 0]),
+             "energy_rel_drift_end": float((a[-1, 6] - a[0, 6]) / abs(a[0, 6]))}
+        if len(leak):
+            k = max(int(leak[0]) - 1, 0)
+            e["energy_rel_drift_before_outflow"] = float((a[k, 6] - a[0, 6]) / abs(a[0, 6]))
+        if w.model == "hmf":
+            f0 = I.initial_state(w)
+            pj = w.pmin + np.arange(w.np) * w.dp
+            gth = math.sqrt(0.5 - 3 * float(np.sum(f0 * (pj ** 2)[:, None])) * w.dx * w.dp)
+            for prec, h in (("fx64", a), ("f32", b)):
+                M = np.hypot(h[:, 2], h[:, 3])
+                sel = (M > 1e-5) & (M < 1e-3)
+                g = float(np.polyfit(h[sel, 0], np.log(M[sel]), 1)[0])
+                e[f"growth_rate_{prec}"] = g
+                e[f"growth_rate_rel_err_{prec}"] = (g - gth) / gth
+            e["growth_rate_theory"] = gth
+        out[w.name] = e
+    return out
+
+
+def ring_section(V, stream_handle) -> dict:
+    """The ring workload (2048^2): microseconds per force launch of each circulant-convolution method
+    (vlasov_ring_timings) and ms per whole step with each method, in FX64 and FP32 storage."""
+    import torch
+    st_ = torch.cuda.ExternalStream(stream_handle)
+    w = I.RING_2048
+    out = {}
+    for prec in ("fx64", "f32"):
+        with V.Sim.from_workload(w, precision=prec, stream=stream_handle) as s:
+            s.init_workload(w)
+            s.step(5)
+            s.sync()
+            default = s.ring_method
+            r = {"default_method": default, "force_us": s.ring_timings(200), "ms_per_step": {}}
+            for m in ("fixed", "direct", "fft", "fft_f32"):
+                s.ring_method = m
+                s.step(8)
+                s.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st_)
+                s.step(64)
+                e1.record(st_)
+                e1.synchronize()
+                r["ms_per_step"][m] = e0.elapsed_time(e1) / 64
+            s.ring_method = default
+        out[prec] = r
+    return out
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -286,8 +417,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "grid": f"{w.nx}x{w.np}", "dt": w.dt, "precision": "f64",
-                       "parallelism": "replicas"},
+            "config": bench_config(w, args.gpus, "fp64"), "precision": "f64 (the FP64 oracle)",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{steps} full Strang steps of {w.name} on {cores} host threads"
                                        + ("" if steps == args.steps else f" (capped from {args.steps})")},
@@ -308,6 +438,8 @@ def main():
     ap.add_argument("--no-f32", action="store_true", help="skip the secondary measurements of the other storage modes")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the batched serving-stream measurement")
+    ap.add_argument("--no-checks", action="store_true",
+                    help="skip the full-length workload checks and the ring-method timings")
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     args = ap.parse_args()
@@ -364,21 +496,32 @@ def main():
     slot_ms = sim.step_timed(4)
     names = sim.slot_names()
     peak_gbs, peak_src = _peaks()
-    shift_bytes = 2.0 * cells * esz   # one read + one write of f per sweep (the algorithmic traffic)
+    shift_bytes = 2.0 * cells * esz   # one read + one write of f per sweep launch (the bytes it moves)
     dom = int(np.argmax(slot_ms))
     dom_name = names[dom]
-    achieved = shift_bytes / (slot_ms[dom] * 1e-3) / 1e9 if "shift" in dom_name else None
+    # the per-sweep traffic model (one read + one write of f per sweep and output) counts the fused
+    # launch, which does the arithmetic of two sweeps on one read and one write, as two sweeps
+    sweeps_in = 2 if dom_name == "xshift_fused" else 1
+    model_bytes = sweeps_in * shift_bytes
+    t_dom = slot_ms[dom] * 1e-3
+    achieved = model_bytes / t_dom / 1e9 if "shift" in dom_name else None
+    achieved_phys = shift_bytes / t_dom / 1e9 if "shift" in dom_name else None
     # HBM round trips of f per step: 3 sweeps, or 2 when the second x half-shift of a step and the
     # first of the next run as one launch (the row stays on chip between them)
     sweeps = 2 if sim.fused_x and args.steps >= 2 else 3
     step_gbs = sweeps * shift_bytes / (ms_max / args.steps * 1e-3) / 1e9
     traffic = stored_traffic(args.precision, dom_name)
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                "frac": (achieved / peak_gbs) if achieved else None, "traffic": traffic,
-                "algorithmic_bytes": shift_bytes, "peak_source": peak_src,
-                "note": ("the fused launch does the filter arithmetic of two sweeps on one read and one write of "
-                         "f; like the separate sweeps it is bound by instruction issue, not by HBM (ncu summary "
-                         "in profiles/)") if dom_name == "xshift_fused" else None,
+                "frac": (achieved / peak_gbs) if achieved else None,
+                "frac_model": (achieved / peak_gbs) if achieved else None,
+                "frac_physical": (achieved_phys / peak_gbs) if achieved_phys else None,
+                "achieved_physical": achieved_phys, "sweeps_in_launch": sweeps_in,
+                "traffic": traffic, "algorithmic_bytes": model_bytes, "physical_bytes": shift_bytes,
+                "launch_ms": float(slot_ms[dom]), "peak_source": peak_src,
+                "note": ("achieved/frac: the per-sweep model, 2 x sizeof(f) per output and sweep, for the two sweeps "
+                         "of arithmetic the fused launch does; frac_physical: the one read and one write of f it "
+                         "makes (traffic: its ncu DRAM bytes).  Bound by instruction issue, not HBM (profiles/)")
+                if dom_name == "xshift_fused" else None,
                 "per_kernel_ms": {n: round(float(v), 5) for n, v in zip(names, slot_ms)},
                 "per_kernel_gbs": {n: round(shift_bytes / (v * 1e-3) / 1e9, 1) for n, v in zip(names, slot_ms)
                                    if "shift" in n and not n.endswith("filters")}}
@@ -467,11 +610,12 @@ def main():
                                           "peak_source": "nominal unit count x max SM clock"}}
             s2.close()
 
+    checks = config_checks(V, stream.cuda_stream) if (rank == 0 and not args.no_checks) else None
+    rings = ring_section(V, stream.cuda_stream) if (rank == 0 and not args.no_checks) else None
+
     serving = None
     if not args.no_serve and rank == 0:
-        ref_mode = "fx64" if args.precision == "f32" else args.precision
-        serving = {prec: serving_benchmark(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30),
-                                           ref_mode, prec) for prec in ("f32", "fx64")}
+        serving = serving_section(V, stream.cuda_stream, args.serve_slots, int(args.serve_budget_gb * 2 ** 30))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,10 +626,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-                "config": {"workload": w.name, "grid": f"{w.nx}x{w.np}", "dt": w.dt, "precision": args.precision,
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "l2": f"inputs larger than L2: each sweep streams {2 * cells * esz / 1e6:.0f} MB "
-                                 "(read + write) against a 129 MB L2"},
+                "config": bench_config(w, world, ACCURACY[args.precision]), "precision": args.precision,
                 "hbm_roofline_frac_step": step_gbs / peak_gbs,
                 "hbm_sweeps_per_step": sweeps,
                 "hbm_frac_step_at_3_sweeps": 3 * shift_bytes / (ms_max / args.steps * 1e-3) / 1e9 / peak_gbs,
@@ -500,6 +641,8 @@ def main():
                 "other_precisions": others,
                 "global_spline": gspline,
                 "casimirs": casimirs,
+                "config_checks": checks,
+                "ring": rings,
                 "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:

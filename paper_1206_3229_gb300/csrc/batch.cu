@@ -1147,6 +1147,168 @@ int vlasov_batch_release(vlasov_batch* b, int slot)
 }
 
 // ------------------------------------------------------------------------------------------- serving loop
+}  // extern "C"
+
+namespace {
+
+// One batch of the serving loop with its queue of routed requests, the events that mark its launched
+// steps, and the slots whose last step is still in flight.
+struct ServeLane {
+    vlasov_batch* b = nullptr;
+    std::vector<int> queue;        // request indices routed here, in arrival order
+    size_t next = 0;               // first queue entry not yet admitted
+    std::vector<cudaEvent_t> ev;   // one per launched batched step (ring of NE)
+    std::vector<long long> ev_step;
+    cudaEvent_t ev0 = nullptr;     // recorded at the start of the run
+    struct Draining {
+        int slot, req;
+        long long step_index;
+    };
+    std::vector<Draining> draining;
+    std::vector<int> slot_req;
+    std::vector<MomentRec> hostrec;
+    long long launched = 0;
+};
+constexpr int SERVE_NE = 256;
+
+void lane_free(ServeLane& L)
+{
+    for (auto& e : L.ev)
+        if (e) cudaEventDestroy(e);
+    if (L.ev0) cudaEventDestroy(L.ev0);
+    vlasov_batch_destroy(L.b);
+    L = ServeLane{};
+}
+
+int lane_init(ServeLane& L, int slots, int max_n, long long budget, int prec, void* stream)
+{
+    int rc = vlasov_batch_create(std::max(1, slots), max_n, budget, prec, stream, &L.b);
+    if (rc) return rc;
+    L.ev.assign(SERVE_NE, nullptr);
+    L.ev_step.assign(SERVE_NE, -1);
+    for (auto& e : L.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bfail(VLASOV_ECUDA, "event create");
+    if (cudaEventCreate(&L.ev0) != cudaSuccess) return bfail(VLASOV_ECUDA, "event create");
+    L.slot_req.assign(L.b->S, -1);
+    L.hostrec.resize(2 * (size_t)L.b->S);
+    return VLASOV_OK;
+}
+
+// Admit this lane's arrived requests in arrival order while a slot and memory are free.
+template <typename Now>
+void lane_admit(ServeLane& L, const vlasov_request* reqs, vlasov_result* results, int* finished, Now now_s)
+{
+    vlasov_batch* b = L.b;
+    while (L.next < L.queue.size() && reqs[L.queue[L.next]].arrival_s <= now_s()) {
+        const int q = L.queue[L.next];
+        int slot = -1;
+        const int r2 = vlasov_batch_admit(b, &reqs[q], nullptr, &slot);
+        if (r2 == VLASOV_ESTATE || r2 == VLASOV_ENOMEM) {
+            // full now: admit later, unless nothing is running (then it can never fit)
+            bool busy = false;
+            for (auto& sl : b->slots) busy |= sl.used;
+            if (busy) break;
+            results[q].status = r2;
+            ++*finished;
+            ++L.next;
+            continue;
+        }
+        if (r2) {
+            results[q].status = r2;
+            ++*finished;
+            ++L.next;
+            continue;
+        }
+        results[q].admit_s = now_s();
+        L.slot_req[slot] = q;
+        ++L.next;
+        if (reqs[q].steps == 0) {
+            results[q].status = 0;
+            results[q].done_s = results[q].admit_s;
+            vlasov_batch_release(b, slot);
+            L.slot_req[slot] = -1;
+            ++*finished;
+        }
+    }
+}
+
+// Launch one batched step if any slot is active (at most `depth` steps in flight).  Returns 1 if a
+// step was launched, 0 if none was active, or a negative error.
+int lane_step(ServeLane& L, int depth)
+{
+    vlasov_batch* b = L.b;
+    bool any_active = false;
+    for (auto& sl : b->slots) any_active |= sl.active;
+    if (!any_active) return 0;
+    if (L.launched >= depth) cudaEventSynchronize(L.ev[(size_t)((L.launched - depth) % SERVE_NE)]);
+    std::vector<int> was_active(b->S, 0);
+    for (int k = 0; k < b->S; ++k) was_active[k] = b->slots[k].active;
+    const int rc = vlasov_batch_step(b, 1);
+    if (rc) return rc;
+    const int e = (int)(L.launched % SERVE_NE);
+    cudaEventRecord(L.ev[e], b->st);
+    L.ev_step[e] = L.launched;
+    for (int k = 0; k < b->S; ++k) {
+        if (was_active[k] && !b->slots[k].active) {
+            // copy its last and first moment records (stream-ordered after the step) and drain
+            Slot& sl = b->slots[k];
+            const int last = (sl.steps_done - 1) % HIST_CAP;
+            cudaMemcpyAsync(&L.hostrec[2 * k], P(b, sl, sl.L.hist) + sizeof(MomentRec) * last, sizeof(MomentRec),
+                            cudaMemcpyDeviceToHost, b->st);
+            cudaMemcpyAsync(&L.hostrec[2 * k + 1], P(b, sl, sl.L.hist), sizeof(MomentRec), cudaMemcpyDeviceToHost, b->st);
+            L.draining.push_back({k, L.slot_req[k], L.launched});
+        }
+    }
+    ++L.launched;
+    return 1;
+}
+
+// Retire drained slots whose last step has completed on the GPU.
+template <typename Now>
+void lane_retire(ServeLane& L, vlasov_result* results, int* finished, Now now_s)
+{
+    vlasov_batch* b = L.b;
+    for (size_t d = 0; d < L.draining.size();) {
+        const ServeLane::Draining dr = L.draining[d];
+        const int e = (int)(dr.step_index % SERVE_NE);
+        const bool recycled = L.ev_step[e] != dr.step_index;
+        if (!recycled && cudaEventQuery(L.ev[e]) != cudaSuccess) {
+            ++d;
+            continue;
+        }
+        if (recycled) cudaStreamSynchronize(b->st);
+        else cudaEventSynchronize(L.ev[e]);
+        cudaStreamSynchronize(b->st);   // the record copies were enqueued after the event
+        vlasov_result& out = results[dr.req];
+        float ms = 0.f;
+        if (!recycled) cudaEventElapsedTime(&ms, L.ev0, L.ev[e]);
+        else ms = (float)(now_s() * 1e3);
+        out.done_s = ms * 1e-3;
+        out.status = 0;
+        out.steps = b->slots[dr.slot].steps_done;
+        const MomentRec* m2[2] = {&L.hostrec[2 * dr.slot], &L.hostrec[2 * dr.slot + 1]};
+        vlasov_moments_t* dst[2] = {&out.last, &out.first};
+        for (int z = 0; z < 2; ++z) {
+            dst[z]->t = m2[z]->t;
+            dst[z]->mass = m2[z]->mass;
+            dst[z]->Mx = m2[z]->Mx;
+            dst[z]->My = m2[z]->My;
+            dst[z]->kinetic = m2[z]->kinetic;
+            dst[z]->potential = m2[z]->potential;
+            dst[z]->energy = m2[z]->energy;
+            dst[z]->step = m2[z]->step;
+        }
+        vlasov_batch_release(b, dr.slot);
+        L.slot_req[dr.slot] = -1;
+        ++*finished;
+        L.draining.erase(L.draining.begin() + (long)d);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
 int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* opt, vlasov_result* results,
                  double* makespan_s)
 {
@@ -1154,168 +1316,71 @@ int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* 
     int max_n = opt->max_n;
     if (max_n <= 0)
         for (int q = 0; q < n; ++q) max_n = std::max(max_n, std::max(reqs[q].Nx, reqs[q].Np));
-    vlasov_batch* b = nullptr;
-    const int prec = opt->precision ? opt->precision : VLASOV_F32;
     max_n = std::max(16, max_n);
-    if (opt->autotune) {
-        vlasov_batch_shape sh;
-        int rc0 = vlasov_batch_autotune(max_n, prec, opt->stream, &sh, nullptr);
-        if (rc0) return rc0;
+    const int prec = opt->precision ? opt->precision : VLASOV_F32;
+    const bool routed = prec == VLASOV_SERVE_ROUTED;
+    if (!routed && prec != VLASOV_F32 && prec != VLASOV_FX64)
+        return bfail(VLASOV_EINVAL, "serving precision must be VLASOV_F32, VLASOV_FX64 or VLASOV_SERVE_ROUTED");
+    // lane 0: FP32 slots (or the one precision asked for); lane 1 (routed): FX64 slots for the ring
+    const int nl = routed ? 2 : 1;
+    const int lane_prec[2] = {routed ? VLASOV_F32 : prec, VLASOV_FX64};
+    if (opt->autotune)
+        for (int l = 0; l < nl; ++l) {
+            vlasov_batch_shape sh;
+            const int rc0 = vlasov_batch_autotune(max_n, lane_prec[l], opt->stream, &sh, nullptr);
+            if (rc0) return rc0;
+        }
+    ServeLane lanes[2];
+    // a routed run puts its second batch on a stream of its own, so the two batches overlap
+    cudaStream_t st2 = nullptr;
+    if (routed && cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess)
+        return bfail(VLASOV_ECUDA, "stream create");
+    auto cleanup = [&]() {
+        for (int l = 0; l < nl; ++l) lane_free(lanes[l]);
+        if (st2) cudaStreamDestroy(st2);
+    };
+    const long long budget = routed ? opt->mem_budget_bytes / 2 : opt->mem_budget_bytes;
+    for (int l = 0; l < nl; ++l) {
+        const int rc0 = lane_init(lanes[l], opt->slots, max_n, budget, lane_prec[l], l == 0 ? opt->stream : (void*)st2);
+        if (rc0) {
+            cleanup();
+            return rc0;
+        }
     }
-    int rc = vlasov_batch_create(std::max(1, opt->slots), max_n, opt->mem_budget_bytes, prec, opt->stream, &b);
-    if (rc) return rc;
-    const int depth = std::max(1, opt->max_inflight);
     std::vector<int> order(n);
     for (int q = 0; q < n; ++q) order[q] = q;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return reqs[a].arrival_s < reqs[c].arrival_s; });
+    for (int q : order) lanes[(routed && reqs[q].model == VLASOV_RING) ? 1 : 0].queue.push_back(q);
     for (int q = 0; q < n; ++q) {
         std::memset(&results[q], 0, sizeof(vlasov_result));
         results[q].status = 1;   // pending
         results[q].arrival_s = reqs[q].arrival_s;
     }
-    // events: one at the start, one after each launched batched step (ring)
-    const int NE = 256;
-    std::vector<cudaEvent_t> ev(NE);
-    cudaEvent_t ev0;
-    auto cleanup = [&]() {
-        for (auto& e : ev)
-            if (e) cudaEventDestroy(e);
-        if (ev0) cudaEventDestroy(ev0);
-        vlasov_batch_destroy(b);
-    };
-    ev0 = nullptr;
-    for (auto& e : ev) e = nullptr;
-    for (auto& e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) {
-            cleanup();
-            return bfail(VLASOV_ECUDA, "event create");
-        }
-    if (cudaEventCreate(&ev0) != cudaSuccess) {
-        cleanup();
-        return bfail(VLASOV_ECUDA, "event create");
-    }
-    cudaStreamSynchronize(b->st);
+    for (int l = 0; l < nl; ++l) cudaStreamSynchronize(lanes[l].b->st);
     const auto t0 = std::chrono::steady_clock::now();
-    cudaEventRecord(ev0, b->st);
+    for (int l = 0; l < nl; ++l) cudaEventRecord(lanes[l].ev0, lanes[l].b->st);
     auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
-
-    struct Draining {
-        int slot;
-        int req;
-        long long step_index;   // global batched step after which it finished
-    };
-    std::vector<Draining> draining;
-    std::vector<int> slot_req(b->S, -1);
-    std::vector<MomentRec> hostrec(2 * b->S);
-    int next = 0, finished = 0;
-    long long launched = 0;
-    std::vector<long long> ev_step(NE, -1);   // which global step each ring event marks
-    rc = VLASOV_OK;
+    const int depth = std::max(1, opt->max_inflight);
+    int finished = 0, rc = VLASOV_OK;
     while (finished < n && rc == VLASOV_OK) {
-        // admit arrived requests in arrival order while a slot and memory are free
-        while (next < n && reqs[order[next]].arrival_s <= now_s()) {
-            const int q = order[next];
-            int slot = -1;
-            const int r2 = vlasov_batch_admit(b, &reqs[q], nullptr, &slot);
-            if (r2 == VLASOV_ESTATE || r2 == VLASOV_ENOMEM) {
-                // full now: admit later, unless nothing is running (then it can never fit)
-                bool busy = false;
-                for (auto& s : b->slots) busy |= s.used;
-                if (!busy) {
-                    results[q].status = r2;
-                    ++finished;
-                    ++next;
-                    continue;
-                }
-                break;
-            }
-            if (r2) {
-                results[q].status = r2;
-                ++finished;
-                ++next;
-                continue;
-            }
-            results[q].admit_s = now_s();
-            slot_req[slot] = q;
-            ++next;
-            if (reqs[q].steps == 0) {
-                results[q].status = 0;
-                results[q].done_s = results[q].admit_s;
-                vlasov_batch_release(b, slot);
-                slot_req[slot] = -1;
-                ++finished;
-            }
+        bool stepped = false;
+        for (int l = 0; l < nl && rc == VLASOV_OK; ++l) {
+            lane_admit(lanes[l], reqs, results, &finished, now_s);
+            const int r = lane_step(lanes[l], depth);
+            if (r < 0) rc = r;
+            stepped |= r > 0;
         }
-        bool any_active = false;
-        for (auto& s : b->slots) any_active |= s.active;
-        if (any_active) {
-            // keep at most `depth` steps in flight
-            if (launched >= depth) {
-                const int e = (int)((launched - depth) % NE);
-                cudaEventSynchronize(ev[e]);
-            }
-            std::vector<int> was_active(b->S, 0);
-            for (int k = 0; k < b->S; ++k) was_active[k] = b->slots[k].active;
-            rc = vlasov_batch_step(b, 1);
-            if (rc) break;
-            const int e = (int)(launched % NE);
-            cudaEventRecord(ev[e], b->st);
-            ev_step[e] = launched;
-            for (int k = 0; k < b->S; ++k) {
-                if (was_active[k] && !b->slots[k].active) {
-                    // copy its last moment record (stream-ordered after the step) and drain
-                    Slot& s = b->slots[k];
-                    const int last = (s.steps_done - 1) % HIST_CAP;
-                    cudaMemcpyAsync(&hostrec[2 * k], P(b, s, s.L.hist) + sizeof(MomentRec) * last, sizeof(MomentRec),
-                                    cudaMemcpyDeviceToHost, b->st);
-                    cudaMemcpyAsync(&hostrec[2 * k + 1], P(b, s, s.L.hist), sizeof(MomentRec), cudaMemcpyDeviceToHost,
-                                    b->st);
-                    draining.push_back({k, slot_req[k], launched});
-                }
-            }
-            ++launched;
-        } else if (next < n) {
-            const double wait = reqs[order[next]].arrival_s - now_s();
-            if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
+        if (!stepped && rc == VLASOV_OK) {
+            // nothing running: sleep until the next arrival of any lane
+            double wait = 1e30;
+            for (int l = 0; l < nl; ++l)
+                if (lanes[l].next < lanes[l].queue.size())
+                    wait = std::min(wait, reqs[lanes[l].queue[lanes[l].next]].arrival_s - now_s());
+            if (wait > 0 && wait < 1e30) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
         }
-        // retire drained slots whose last step has completed
-        for (size_t d = 0; d < draining.size();) {
-            const Draining& dr = draining[d];
-            const int e = (int)(dr.step_index % NE);
-            const bool recycled = ev_step[e] != dr.step_index;
-            if (recycled || cudaEventQuery(ev[e]) == cudaSuccess) {
-                if (recycled) cudaStreamSynchronize(b->st);
-                else cudaEventSynchronize(ev[e]);
-                cudaStreamSynchronize(b->st);   // the record copies were enqueued after the event
-                vlasov_result& out = results[dr.req];
-                float ms = 0.f;
-                if (!recycled) cudaEventElapsedTime(&ms, ev0, ev[e]);
-                else ms = (float)(now_s() * 1e3);
-                out.done_s = ms * 1e-3;
-                out.status = 0;
-                out.steps = b->slots[dr.slot].steps_done;
-                const MomentRec* m2[2] = {&hostrec[2 * dr.slot], &hostrec[2 * dr.slot + 1]};
-                vlasov_moments_t* dst[2] = {&out.last, &out.first};
-                for (int z = 0; z < 2; ++z) {
-                    dst[z]->t = m2[z]->t;
-                    dst[z]->mass = m2[z]->mass;
-                    dst[z]->Mx = m2[z]->Mx;
-                    dst[z]->My = m2[z]->My;
-                    dst[z]->kinetic = m2[z]->kinetic;
-                    dst[z]->potential = m2[z]->potential;
-                    dst[z]->energy = m2[z]->energy;
-                    dst[z]->step = m2[z]->step;
-                }
-                vlasov_batch_release(b, dr.slot);
-                slot_req[dr.slot] = -1;
-                ++finished;
-                draining.erase(draining.begin() + (long)d);
-            } else {
-                ++d;
-            }
-        }
+        for (int l = 0; l < nl; ++l) lane_retire(lanes[l], results, &finished, now_s);
     }
-    cudaStreamSynchronize(b->st);
+    for (int l = 0; l < nl; ++l) cudaStreamSynchronize(lanes[l].b->st);
     if (makespan_s) *makespan_s = now_s();
     cleanup();
     return rc;
