@@ -200,11 +200,7 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, precision
     sizes = (256, 512, 1024, 2048)
     # launch shape of the batched sweeps: the project's autotuner, run once before anything is timed
     # (later batches of this max_n and precision use the shape it picked)
-    if precision == "routed":   # two batches (FP32 and FX64 slots), each with the shape tuned for it
-        shapes = {p_: V.batch_autotune(max(sizes), p_, stream_handle)[0] for p_ in ("f32", "fx64")}
-        shape, shape_ms = shapes["f32"], {}
-    else:
-        shape, shape_ms = V.batch_autotune(max(sizes), precision, stream_handle)
+    shape, shape_ms = V.batch_autotune(max(sizes), precision, stream_handle)
     reqs = [V.request_from_workload(w, st, t) for (w, st, t) in stream]
     res, makespan = V.serve(reqs, slots, budget_bytes, max_n=max(sizes), stream=stream_handle, precision=precision)
     ok = [r.status == 0 for r in res]
@@ -215,8 +211,7 @@ def serving_benchmark(V, stream_handle, slots: int, budget_bytes: int, precision
             "launch_shape": {"rows_per_cta": shape[0], "tiles_per_cta": shape[1],
                              "autotune_ms_per_batched_step": {f"{r}x{t}": round(v, 4) for (r, t), v in shape_ms.items()}},
             "dtype": {"f32": "f32 storage, FP64-accurate displacements (exact fixed-point ring force) and moment sums",
-                      "fx64": "int64 fixed point + f32 (FP64-accurate), as the single-grid fx64 path",
-                      "routed": "ring requests in fx64 slots, HMF and sheet requests in f32 slots (two batches)"}[precision],
+                      "fx64": "int64 fixed point + f32 (FP64-accurate), as the single-grid fx64 path"}[precision],
             "aggregate_value": work / makespan, "unit": UNIT, "makespan_s": makespan, "arrival_rate_per_s": rate,
             "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
@@ -241,14 +236,14 @@ def serving_section(V, stream_handle, slots: int, budget_bytes: int) -> dict:
     out["sequential_fx64"] = {"device_s": seq["device_s"], "wall_s": seq["wall_s"],
                               "value_device": seq_work / seq["device_s"], "unit": UNIT,
                               "note": "the 512 requests run one at a time on the single-grid FX64 path (measured)"}
-    for prec in ("f32", "fx64", "routed"):
+    for prec in ("f32", "fx64"):
         r = serving_benchmark(V, stream_handle, slots, budget_bytes, prec, stream, rate)
         res, work = r.pop("_results"), r.pop("_work")
         r.update(accuracy_vs(res, seq["last"], stream))
         r["speedup_vs_sequential_fx64_device"] = seq["device_s"] / r["makespan_s"] * (work / seq_work)
         r["speedup_vs_sequential_fx64_wall"] = seq["wall_s"] / r["makespan_s"] * (work / seq_work)
         out[prec] = r
-    ok = [p for p in ("f32", "fx64", "routed") if out[p]["dM_all_max"] is not None and out[p]["dM_all_max"] <= 1e-5
+    ok = [p for p in ("f32", "fx64") if out[p]["dM_all_max"] is not None and out[p]["dM_all_max"] <= 1e-5
           and out[p]["completed"] == out[p]["requests"]]
     out["headline_form"] = max(ok, key=lambda p: out[p]["aggregate_value"]) if ok else None
     out["headline_rule"] = ("the fastest batched form whose every result is within |dM| <= 1e-5 of the "

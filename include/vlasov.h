@@ -321,7 +321,7 @@ typedef struct {
     int max_n;                   /* largest grid (0: from the requests) */
     long long mem_budget_bytes;  /* device memory for simulation state */
     int max_inflight;            /* batched steps queued ahead of the GPU */
-    int precision;               /* VLASOV_F32, VLASOV_FX64 or VLASOV_SERVE_ROUTED */
+    int precision;               /* VLASOV_F32 or VLASOV_FX64 */
     void* stream;
     int autotune;                /* 1: vlasov_batch_autotune for (max_n, precision) before the run */
 } vlasov_serve_options;
@@ -329,12 +329,7 @@ typedef struct {
 /* Continuous-batching run of a request stream: requests are admitted (in arrival order, at their
    arrival time on the wall clock) as slots and memory free up, advance together one batched step at
    a time, and retire independently.  results[i] belongs to reqs[i].  *makespan_s: wall time.
-   precision VLASOV_SERVE_ROUTED: two batches on two streams, advancing side by side: ring requests
-   go to FX64 slots (the FP64-accurate storage) and every other request to FP32 slots, each batch
-   with `slots` slots and half of mem_budget_bytes, each admitting its own requests in arrival order.
-   (The rule follows measurement: FP32 storage holds |dM| <= 1e-5 against the FP64-accurate path on
-   the HMF and sheet requests of the serving stream, not on long ring runs.) */
-enum { VLASOV_SERVE_ROUTED = 100 };
+   precision other than VLASOV_F32 or VLASOV_FX64: VLASOV_EINVAL. */
 int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* opt, vlasov_result* results,
                  double* makespan_s);
 

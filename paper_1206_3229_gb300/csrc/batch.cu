@@ -946,6 +946,7 @@ int vlasov_batch_admit(vlasov_batch* b, const vlasov_request* r, const double* h
         rc_.n0 = Ls.n0;
         rc_.m4 = (int)((((long long)Ls.n0 - 4) % Nx + Nx) % Nx);
         rc_.p2q = std::llround(std::ldexp(0.5 * p * p, KIN_Q));
+        rc_.p2h = (float)(0.5 * p * p);
         max_n0 = std::max(max_n0, std::abs(Ls.n0));
         rc_.g64 = Ls.g;
         rc_.d64 = Ls.d;
@@ -1151,11 +1152,11 @@ int vlasov_batch_release(vlasov_batch* b, int slot)
 
 namespace {
 
-// One batch of the serving loop with its queue of routed requests, the events that mark its launched
+// The batch of the serving loop with its queue of requests, the events that mark its launched
 // steps, and the slots whose last step is still in flight.
 struct ServeLane {
     vlasov_batch* b = nullptr;
-    std::vector<int> queue;        // request indices routed here, in arrival order
+    std::vector<int> queue;        // request indices, in arrival order
     size_t next = 0;               // first queue entry not yet admitted
     std::vector<cudaEvent_t> ev;   // one per launched batched step (ring of NE)
     std::vector<long long> ev_step;
@@ -1318,71 +1319,53 @@ int vlasov_serve(const vlasov_request* reqs, int n, const vlasov_serve_options* 
         for (int q = 0; q < n; ++q) max_n = std::max(max_n, std::max(reqs[q].Nx, reqs[q].Np));
     max_n = std::max(16, max_n);
     const int prec = opt->precision ? opt->precision : VLASOV_F32;
-    const bool routed = prec == VLASOV_SERVE_ROUTED;
-    if (!routed && prec != VLASOV_F32 && prec != VLASOV_FX64)
-        return bfail(VLASOV_EINVAL, "serving precision must be VLASOV_F32, VLASOV_FX64 or VLASOV_SERVE_ROUTED");
-    // lane 0: FP32 slots (or the one precision asked for); lane 1 (routed): FX64 slots for the ring
-    const int nl = routed ? 2 : 1;
-    const int lane_prec[2] = {routed ? VLASOV_F32 : prec, VLASOV_FX64};
-    if (opt->autotune)
-        for (int l = 0; l < nl; ++l) {
-            vlasov_batch_shape sh;
-            const int rc0 = vlasov_batch_autotune(max_n, lane_prec[l], opt->stream, &sh, nullptr);
-            if (rc0) return rc0;
-        }
-    ServeLane lanes[2];
-    // a routed run puts its second batch on a stream of its own, so the two batches overlap
-    cudaStream_t st2 = nullptr;
-    if (routed && cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess)
-        return bfail(VLASOV_ECUDA, "stream create");
-    auto cleanup = [&]() {
-        for (int l = 0; l < nl; ++l) lane_free(lanes[l]);
-        if (st2) cudaStreamDestroy(st2);
-    };
-    const long long budget = routed ? opt->mem_budget_bytes / 2 : opt->mem_budget_bytes;
-    for (int l = 0; l < nl; ++l) {
-        const int rc0 = lane_init(lanes[l], opt->slots, max_n, budget, lane_prec[l], l == 0 ? opt->stream : (void*)st2);
+    if (prec != VLASOV_F32 && prec != VLASOV_FX64)
+        return bfail(VLASOV_EINVAL, "serving precision must be VLASOV_F32 or VLASOV_FX64");
+    if (opt->autotune) {
+        vlasov_batch_shape sh;
+        const int rc0 = vlasov_batch_autotune(max_n, prec, opt->stream, &sh, nullptr);
+        if (rc0) return rc0;
+    }
+    ServeLane L;
+    {
+        const int rc0 = lane_init(L, opt->slots, max_n, opt->mem_budget_bytes, prec, opt->stream);
         if (rc0) {
-            cleanup();
+            lane_free(L);
             return rc0;
         }
     }
     std::vector<int> order(n);
     for (int q = 0; q < n; ++q) order[q] = q;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return reqs[a].arrival_s < reqs[c].arrival_s; });
-    for (int q : order) lanes[(routed && reqs[q].model == VLASOV_RING) ? 1 : 0].queue.push_back(q);
+    L.queue = order;
     for (int q = 0; q < n; ++q) {
         std::memset(&results[q], 0, sizeof(vlasov_result));
         results[q].status = 1;   // pending
         results[q].arrival_s = reqs[q].arrival_s;
     }
-    for (int l = 0; l < nl; ++l) cudaStreamSynchronize(lanes[l].b->st);
+    cudaStreamSynchronize(L.b->st);
     const auto t0 = std::chrono::steady_clock::now();
-    for (int l = 0; l < nl; ++l) cudaEventRecord(lanes[l].ev0, lanes[l].b->st);
+    cudaEventRecord(L.ev0, L.b->st);
     auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
     const int depth = std::max(1, opt->max_inflight);
     int finished = 0, rc = VLASOV_OK;
     while (finished < n && rc == VLASOV_OK) {
-        bool stepped = false;
-        for (int l = 0; l < nl && rc == VLASOV_OK; ++l) {
-            lane_admit(lanes[l], reqs, results, &finished, now_s);
-            const int r = lane_step(lanes[l], depth);
-            if (r < 0) rc = r;
-            stepped |= r > 0;
+        lane_admit(L, reqs, results, &finished, now_s);
+        const int r = lane_step(L, depth);
+        if (r < 0) {
+            rc = r;
+            break;
         }
-        if (!stepped && rc == VLASOV_OK) {
-            // nothing running: sleep until the next arrival of any lane
-            double wait = 1e30;
-            for (int l = 0; l < nl; ++l)
-                if (lanes[l].next < lanes[l].queue.size())
-                    wait = std::min(wait, reqs[lanes[l].queue[lanes[l].next]].arrival_s - now_s());
-            if (wait > 0 && wait < 1e30) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
+        if (r == 0 && L.next < L.queue.size()) {
+            // nothing running: sleep until the next arrival
+            const double wait = reqs[L.queue[L.next]].arrival_s - now_s();
+            if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
         }
-        for (int l = 0; l < nl; ++l) lane_retire(lanes[l], results, &finished, now_s);
+        lane_retire(L, results, &finished, now_s);
     }
-    for (int l = 0; l < nl; ++l) cudaStreamSynchronize(lanes[l].b->st);
+    cudaStreamSynchronize(L.b->st);
     if (makespan_s) *makespan_s = now_s();
-    cleanup();
+    lane_free(L);
     return rc;
 }
 

@@ -349,7 +349,11 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     for (int c = 0; c < maxch_of<S>(); ++c)
 #pragma unroll
         for (int v = 0; v < V; ++v) colacc[c][v] = acc_t(0);
+    // kinetic sum of this thread's rows: FP64 for FP64 storage; for FP32-class storage the row sums
+    // are FP32 already, and an FP32 fused multiply-add per row keeps the slow FP64 pipe out of the
+    // row loop (the sum becomes FP64 in the per-CTA epilogue)
     double kin = 0.0;
+    float kinf = 0.f;
 
     int it = 0;
     int r = blockIdx.x;
@@ -363,9 +367,11 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
             int n0;
             T w[NTAP];
             T g = T(0), d = T(0);
+            float p2h = 0.f;
             if (use_rec) {
                 const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
                 n0 = rc->n0;
+                p2h = rc->p2h;
 #pragma unroll
                 for (int t = 0; t < NTAP; ++t) w[t] = sizeof(T) == 8 ? (T)rc->w64[t] : (T)rc->w32[t];
                 if constexpr (!PERIODIC) {
@@ -409,8 +415,16 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
             }
 #undef VL_ROW
             if constexpr (KIN) {
-                const double pj = a.pmin + (double)r * a.dp;
-                kin += 0.5 * pj * pj * (double)rowsum;
+                if constexpr (sizeof(T) == 4) {
+                    if (!use_rec) {
+                        const double pj = a.pmin + (double)r * a.dp;
+                        p2h = (float)(0.5 * pj * pj);
+                    }
+                    kinf = fmaf(p2h, (float)rowsum, kinf);
+                } else {
+                    const double pj = a.pmin + (double)r * a.dp;
+                    kin += 0.5 * pj * pj * (double)rowsum;
+                }
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -442,7 +456,7 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
     }
 
     colsum_epilogue<S, maxch_of<S>()>(a, colacc, reinterpret_cast<i128*>(bufs));
-    if constexpr (KIN) kin_epilogue(a, kin, red);
+    if constexpr (KIN) kin_epilogue(a, sizeof(T) == 4 ? (double)kinf : kin, red);
 }
 
 template <typename S, bool PERIODIC, bool KIN>
@@ -539,7 +553,7 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
             acc1[c][v] = acc_t(0);
             acc2[c][v] = acc_t(0);
         }
-    double kin = 0.0;
+    float kinf = 0.f;   // FP32 kinetic sum of this thread's rows (FP64 in the epilogue)
 
     int it = 0;
     bool failed = false;
@@ -551,9 +565,11 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
         T w[NTAP];
         T g = T(0), d = T(0);
         acc_t rowsum = acc_t(0);
+        float p2h = 0.f;
         if (ok) {
             const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
             n0 = rc->n0;
+            p2h = rc->p2h;
 #pragma unroll
             for (int t = 0; t < NTAP; ++t) w[t] = sizeof(T) == 8 ? (T)rc->w64[t] : (T)rc->w32[t];
             if constexpr (!PERIODIC) {
@@ -596,10 +612,7 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
                 issue(s, rn);
             }
         }
-        {
-            const double pj = a.pmin + (double)r * a.dp;
-            kin += 0.5 * pj * pj * (double)rowsum;
-        }
+        kinf = fmaf(p2h, (float)rowsum, kinf);
         acc_t rowsum2 = acc_t(0);
         S* orow = fout + (size_t)r * Nx;
         const int A = (n0 - 4) & (V - 1);
@@ -638,7 +651,7 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
     }
     i128* scratch = reinterpret_cast<i128*>(bufs);
     colsum_epilogue<S, CH>(a, acc1, scratch);
-    kin_epilogue(a, kin, red);
+    kin_epilogue(a, (double)kinf, red);
     colsum_epilogue<S, CH>(b, acc2, scratch);
 }
 

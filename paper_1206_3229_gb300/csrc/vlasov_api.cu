@@ -222,6 +222,7 @@ int upload_params(vlasov_sim* s, LineParamsDev& p, const double* disp, int n, in
             if (rows_are_p) {
                 const double pj = s->pmin + (double)l * s->dp;   // as the kernels' p_j
                 r.p2q = std::llround(std::ldexp(0.5 * pj * pj, KIN_Q));
+                r.p2h = (float)(0.5 * pj * pj);
             }
             std::memcpy(&buf[(size_t)l * XREC_BYTES], &r, sizeof r);
         }

@@ -146,6 +146,8 @@ struct XRec {
     int Whe[2][NTAP];
     float wle[2][NTAP];
     float wfe[2][NTAP];
+    float p2h;            // p_j^2 / 2 of the row in FP32 (kinetic weight of the FP32-class sweeps)
+    float pad_;
 };
 constexpr int XREC_BYTES = 528;
 constexpr int KIN_Q = 40;   // |p| < 2896 keeps p^2/2 * 2^KIN_Q below 2^62

@@ -191,17 +191,14 @@ def batch_autotune(max_n: int, precision: str | int = "f32", stream: int | None 
     return best.as_tuple(), dict(zip(AUTOTUNE_CANDIDATES, [float(v) for v in ms]))
 
 
-SERVE_ROUTED = 100   # vlasov_serve: ring requests in FX64 slots, the others in FP32 slots
-
-
 def serve(reqs: list[Request], slots: int, mem_budget_bytes: int, max_n: int = 0, max_inflight: int = 4,
           stream: int | None = None, precision: str | int = "f32", autotune: bool = False):
-    """vlasov_serve: continuous batching of a request stream ("f32", "fx64", or "routed": two batches,
-    ring requests in FX64 slots and the rest in FP32 slots).  Returns (results, makespan_s)."""
+    """vlasov_serve: continuous batching of a request stream ("f32" or "fx64" slots).  Returns
+    (results, makespan_s)."""
     lib = load()
     arr = (Request * len(reqs))(*reqs)
     res = (Result * max(len(reqs), 1))()
-    prec = SERVE_ROUTED if precision in ("routed", SERVE_ROUTED) else _batch_precision(precision)
+    prec = _batch_precision(precision)
     opt = ServeOptions(int(slots), int(max_n), int(mem_budget_bytes), int(max_inflight), prec,
                        ctypes.c_void_p(stream) if stream else None, 1 if autotune else 0)
     mk = ctypes.c_double(0.0)

@@ -245,30 +245,6 @@ def test_fx64_serve_results_equal_single_grid_moments():
         assert V.moments_row(r.last) == list(m[-1])
 
 
-def test_routed_serve_puts_rings_in_fx64_slots_and_the_rest_in_fp32_slots():
-    """VLASOV_SERVE_ROUTED: ring requests reproduce an FX64 batch, the others an FP32 batch, bit for
-    bit (a slot's results do not depend on the rest of its batch), with requests arriving while
-    both batches run."""
-    pool = [I.HMF_256, I.RING_2048.resized(128, 128), I.SHEET_4096.resized(256, 256)]
-    reqs, ws = [], []
-    for q in range(9):
-        w = pool[q % len(pool)]
-        steps = 5 + 2 * q
-        reqs.append(V.request_from_workload(w, steps, arrival_s=0.003 * q))
-        ws.append((w, steps))
-    budget = 6 * max(V.batch_footprint(r, "fx64") for r in reqs)
-    results, mk = V.serve(reqs, slots=3, mem_budget_bytes=budget, max_n=256, precision="routed")
-    assert mk > 0
-    for (w, steps), r in zip(ws, results):
-        assert r.status == 0 and r.steps == steps
-        prec = "fx64" if w.model == "ring" else "f32"
-        with V.Batch(1, 256, GB, precision=prec) as b:
-            k = b.admit(V.request_from_workload(w, steps))
-            b.step(steps)
-            _, m = b.get(k, w.nx, w.np)
-        assert V.moments_row(r.last) == list(m[-1]), (w.name, prec)
-
-
 def test_serve_rejects_unknown_precision():
     req = V.request_from_workload(I.HMF_256.resized(64), 3)
     with pytest.raises(ValueError):
