@@ -143,7 +143,7 @@ int vlasov_spline(const vlasov_sim* sim);
 
 /* Turn the fused x-shifts on (1) or off (0).  Available with VLASOV_FX64 storage (Nx <= 4096 and
    a multiple of 64; on by default when x is periodic) and with VLASOV_F32 or VLASOV_BF16 storage
-   (Nx <= 4096; on by default for VLASOV_F32).  Elsewhere asking for them returns VLASOV_EINVAL.
+   (Nx <= 4096; on by default).  Elsewhere asking for them returns VLASOV_EINVAL.
    With FX64 the fused run gives the same bits as the separate launches; with FP32-class storage f
    is bitwise the same for a given force, but the per-CTA FP32 column and kinetic sums run over
    another row partition, so self-consistent runs agree to within the rounding of those sums.
@@ -162,6 +162,9 @@ int vlasov_fused_x(const vlasov_sim* sim);
                           deterministic, and the same bits whatever the launch shape.  Default.
      VLASOV_RING_FFT:     FP64 FFT convolution in shared memory (Nx a power of two, <= 4096); the
                           potential by Parseval.  VLASOV_RING_FFT_F32: the same in FP32.
+     VLASOV_RING_TENSOR:  the circulant product as a GEMM on the tensor cores (tcgen05, TF32 inputs
+                          split in high and low parts, three products accumulated in FP32: about
+                          FP32 accuracy); Nx = 128 k with 256 <= Nx <= 4096.
    vlasov_set_ring_method returns VLASOV_EINVAL for another model, an unknown method, or an Nx the
    method cannot take; it syncs and drops the captured step graphs.  vlasov_ring_method reports it
    (0 for another model).  vlasov_ring_timings computes the density of the current f and times

@@ -22,7 +22,10 @@
 #include <cmath>
 #include <vector>
 
+#include <cstring>
+
 #include "fixed_point.cuh"
+#include "ptx.cuh"
 #include "vlasov_internal.cuh"
 
 namespace vl {
@@ -244,6 +247,245 @@ void ring_fixed_tables(int N, double dx, double eps, long long* Kq, long long* V
     }
 }
 
+// ============================================================================ TENSOR
+// The circulant product as a GEMM on the tensor cores.  With N = N1 * 128, output i = a*128 + b and
+// input k = c*128 + d, and e = (a - c) mod N1:
+//   y[a*128 + b] = sum_e sum_d T_e[b, d] R_e[d, a],   T_e[b, d] = K((e*128 + b - d) mod N),
+//                                                      R_e[d, a] = rho[((a - e) mod N1)*128 + d],
+// i.e. Y (128 x N1) = [T_0 .. T_{N1-1}] (128 x N) [R_0; ..; R_{N1-1}] (N x N1).  CTA e forms
+// T_e R_e with tcgen05.mma (kind::tf32, M = 128, N = N1 padded to 16 or 32, K = 128 in 16 steps of
+// 8) on TF32 operands split in high and low parts (3xTF32: hi x hi + hi x lo + lo x hi, accumulated in
+// FP32 in tensor memory); the last CTA adds the N1 partial results in a fixed order.  T_e is constant for a
+// handle: its TF32 high and low parts are built once on the host as shared-memory images and
+// arrive by bulk copy; R_e is gathered from rho by the CTA.  Operands are K-major without swizzle:
+// 8-row x 16-byte core matrices, the cores of one 4-element K column contiguous.
+__host__ __device__ __forceinline__ uint32_t tc_off(int r, int k, int rows)
+{
+    return (uint32_t)((k >> 2) * (rows / 8) * 128 + (r >> 3) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+bool ring_tc_ok(int N) { return N % RING_TC_M == 0 && N >= 2 * RING_TC_M && N / RING_TC_M <= RING_TC_N; }
+
+// operand images (T_e high/low, R_e high/low), 1024 bytes of alignment slack, and 4 KB past the last
+// operand so that every read a descriptor could address stays inside the allocation
+size_t ring_tc_smem_bytes() { return 2 * RING_TC_IMG + 2 * (size_t)RING_TC_N * RING_TC_M * 4 + 1024 + 4096; }
+
+static float tf32_rna_host(float x)
+{
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0x7f800000u) != 0x7f800000u) b = (b + 0x1000u) & 0xffffe000u;   // nearest, ties away
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+void ring_tc_tables(const double* table, int N, float* images)
+{
+    const int N1 = N / RING_TC_M;
+    const size_t img = RING_TC_IMG / 4;
+    for (int e = 0; e < N1; ++e) {
+        float* hi = images + (size_t)(2 * e) * img;
+        float* lo = hi + img;
+        for (int m = 0; m < RING_TC_M; ++m)
+            for (int k = 0; k < RING_TC_M; ++k) {
+                int q = (e * RING_TC_M + m - k) % N;
+                if (q < 0) q += N;
+                const double v = table[q];
+                const float h = tf32_rna_host((float)v);
+                const uint32_t o = tc_off(m, k, RING_TC_M) / 4;
+                hi[o] = h;
+                // the low part rounded to TF32 here: the tensor cores would otherwise drop its low
+                // 13 bits by truncation, a bias that adds up step after step
+                lo[o] = tf32_rna_host((float)(v - (double)h));
+            }
+    }
+}
+
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: start, leading-dimension (K) and stride-dimension (M/N) byte
+// offsets between core matrices, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+template <bool POT>
+__global__ void __launch_bounds__(128, 1) ring_tc_kernel(RingArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem_dyn[];
+    __shared__ __align__(8) uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int tc_fail;
+    __shared__ bool is_last;
+    __shared__ i128 red[33];
+    const uint32_t raw = smem_u32(tc_smem_dyn);
+    unsigned char* sm = tc_smem_dyn + ((1024u - (raw & 1023u)) & 1023u);
+    const int N = a.N, N1 = N / RING_TC_M, e = blockIdx.x;
+    const int nmma = N1 <= 16 ? 16 : 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* Ahi = reinterpret_cast<float*>(sm);
+    float* Bhi = reinterpret_cast<float*>(sm + 2 * RING_TC_IMG);
+    float* Blo = Bhi + RING_TC_N * RING_TC_M;
+
+    if (tid == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma, 1);
+        tc_fail = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(32u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned char* src = static_cast<const unsigned char*>(POT ? a.tcV : a.tcK) + (size_t)e * 2 * RING_TC_IMG;
+        mbar_arrive_expect_tx(&bar_load, (uint32_t)(2 * RING_TC_IMG));
+        bulk_g2s(sm, src, (uint32_t)RING_TC_IMG, &bar_load);
+        bulk_g2s(sm + RING_TC_IMG, src + RING_TC_IMG, (uint32_t)RING_TC_IMG, &bar_load);
+    }
+    // R_e[d, n] for d = tid (this thread's K row), n < nmma (columns past N1 are zero)
+#pragma unroll 4
+    for (int n = 0; n < nmma; ++n) {
+        float h = 0.f, l = 0.f;
+        if (n < N1) {
+            int c = n - e;
+            c += (c < 0) ? N1 : 0;
+            const double r = a.rho[c * RING_TC_M + tid];
+            h = tf32_rna((float)r);
+            l = tf32_rna((float)(r - (double)h));
+        }
+        const uint32_t o = tc_off(n, tid, nmma) / 4;
+        Bhi[o] = h;
+        Blo[o] = l;
+    }
+    fence_proxy_async_smem();   // the generic-proxy writes of R_e, before the tensor cores read them
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (tid == 0) {
+        if (mbar_wait_bounded(&bar_load, 0u, WAIT_LIMIT_NS)) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                                   ((uint32_t)(RING_TC_M >> 4) << 24);
+            const uint32_t a_hi = smem_u32(Ahi), a_lo = a_hi + (uint32_t)RING_TC_IMG;
+            const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+            const uint32_t a_lbo = (RING_TC_M / 8) * 128, b_lbo = (uint32_t)(nmma / 8) * 128;
+            // three products of the split operands (lo x lo, 2^-22 of each term, measured to change
+            // nothing: the FP32 accumulation in the tensor cores sets the accuracy)
+            const uint32_t as[3] = {a_hi, a_hi, a_lo}, bs[3] = {b_hi, b_lo, b_hi};
+            for (int p = 0; p < 3; ++p)
+                for (int s = 0; s < RING_TC_M / 8; ++s)
+                    tc_mma(tmem, tc_desc(as[p] + 2u * s * a_lbo, a_lbo, 128u), tc_desc(bs[p] + 2u * s * b_lbo, b_lbo, 128u),
+                           idesc, (p | s) != 0 ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar_mma))
+                         : "memory");
+        } else {
+            tc_fail = 1;
+            atomicCAS(a.err, DEV_ERR_NONE, DEV_ERR_RING_WAIT);
+            mbar_wait_bounded(&bar_load, 0u, WAIT_LIMIT_NS);   // the copies must land before exit
+            mbar_arrive(&bar_mma);
+        }
+    }
+    const bool done = mbar_wait_bounded(&bar_mma, 0u, WAIT_LIMIT_NS);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done && !tc_fail) {
+        uint32_t y[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]),
+              "=r"(y[8]), "=r"(y[9]), "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15])
+            : "r"(taddr));
+        if (nmma > 16)
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(y[16]), "=r"(y[17]), "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]), "=r"(y[22]),
+                  "=r"(y[23]), "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]), "=r"(y[28]), "=r"(y[29]),
+                  "=r"(y[30]), "=r"(y[31])
+                : "r"(taddr + 16u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // this block's partial results into the exact fixed-point sums (order-free, so deterministic)
+        const int m = warp * 32 + lane;   // output row b of this block
+        const float sc = __int_as_float((127 + a.tcq) << 23);   // 2^tcq
+        for (int n = 0; n < N1; ++n)
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.tcacc) + n * RING_TC_M + m,
+                      (unsigned long long)__float2ll_rn(__uint_as_float(y[n]) * sc));
+    } else if (tid == 0 && !done) {
+        atomicCAS(a.err, DEV_ERR_NONE, DEV_ERR_RING_WAIT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u) : "memory");
+
+    // the last CTA adds the N1 partial results in block order
+    if (tid == 0) {
+        __threadfence();
+        is_last = atomicAdd(a.tcticket, 1u) == (unsigned int)N1 - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // every block has added its partial results: convert, and clear the sums for the next launch
+    i128 u = 0;
+    const double unit = ldexp(1.0, -a.tcq);
+    for (int i = tid; i < N; i += blockDim.x) {
+        const double sum = (double)__ldcg(a.tcacc + i) * unit;
+        a.tcacc[i] = 0;
+        if constexpr (!POT) a.F[i] = -a.dx * sum;
+        else u += fx128_from_f64(a.rho[i] * (a.dx * sum), a.k_pot);
+    }
+    if constexpr (POT) u = block_sum_i128(u, red);
+    if (tid != 0) return;
+    *a.tcticket = 0u;
+    if constexpr (POT) {
+        const double U = a.pot_scale * fx128_to_f64(u, a.k_pot);
+        const Scalars sc = *a.sc;
+        const long long st = *a.step;
+        MomentRec rec;
+        rec.t = (double)(st + 1) * a.dt;
+        rec.mass = sc.mass;
+        rec.Mx = sc.Mx;
+        rec.My = sc.My;
+        rec.kinetic = sc.kinetic;
+        rec.potential = U;
+        rec.energy = sc.kinetic + U;
+        rec.step = st + 1;
+        a.hist[st % HIST_CAP] = rec;
+        *a.step = st + 1;
+        a.sc->potential = U;
+    }
+}
+
+cudaError_t launch_ring_tc(const RingArgs& a, cudaStream_t st)
+{
+    const int grid = a.N / RING_TC_M;
+    if (a.final_moments) ring_tc_kernel<true><<<grid, 128, ring_tc_smem_bytes(), st>>>(a);
+    else ring_tc_kernel<false><<<grid, 128, ring_tc_smem_bytes(), st>>>(a);
+    return cudaGetLastError();
+}
+
 // ============================================================================ FFT
 bool ring_fft_ok(int N) { return N >= 16 && N <= 4096 && (N & (N - 1)) == 0; }
 
@@ -374,6 +616,8 @@ cudaError_t set_ringfx_attributes(int max_smem)
     if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_batch_kernel<true>, max_smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(ring_fft_kernel<double, double2>, max_smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(ring_fft_kernel<float, float2>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ring_tc_kernel<false>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ring_tc_kernel<true>, max_smem);
     return e;
 }
 

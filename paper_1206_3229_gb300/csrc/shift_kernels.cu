@@ -193,12 +193,12 @@ __device__ __forceinline__ void xshift_row(const S* __restrict__ rowbuf, S* __re
 // End of a sweep: hand over this CTA's column sums acc[c][v] (column V (tid + c blockDim) + v) in
 // the form the arguments ask for.  Every thread calls it; `scratch` (>= 2 KB of shared memory no
 // warp still reads) serves the block reduction.
-template <typename S, int CH>
-__device__ __forceinline__ void colsum_epilogue(const XShiftArgs& a, const typename VecOf<S>::acc (&colacc)[CH][VecOf<S>::V],
+template <typename S, int CH, int VW = VecOf<S>::V>
+__device__ __forceinline__ void colsum_epilogue(const XShiftArgs& a, const typename VecOf<S>::acc (&colacc)[CH][VW],
                                                 i128* scratch)
 {
     using acc_t = typename VecOf<S>::acc;
-    constexpr int V = VecOf<S>::V;
+    constexpr int V = VW;   // columns V (tid + c nthreads) + v, v < V
     const int Nx = a.Nx, tid = threadIdx.x, nthreads = blockDim.x;
     if (a.colacc) {
         // exact fixed-point column sums, added across CTAs (order-free)

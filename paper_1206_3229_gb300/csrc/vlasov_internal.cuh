@@ -114,7 +114,7 @@ inline void gs_filter_h(double h[GS_HTAPS])
 
 // Device-side error codes written to the handle's flag by a bounded wait that gave up.
 enum : int { DEV_ERR_NONE = 0, DEV_ERR_XSHIFT_WAIT = 1, DEV_ERR_PSHIFT_WAIT = 2, DEV_ERR_RANGE = 3,
-             DEV_ERR_TEST_WAIT = 4 };
+             DEV_ERR_TEST_WAIT = 4, DEV_ERR_RING_WAIT = 5 };
 
 // Scalars produced by the reductions of one sweep (device struct).
 struct Scalars {
@@ -309,6 +309,14 @@ struct RingArgs {
     const void* khat;
     const void* vhat;
     const void* twid;
+    // tensor-core form (ring.cu): per column block e of 128, the 128 x 128 Toeplitz block of V' (tcK)
+    // or V (tcV) as shared-memory images (TF32 high part, then low part)
+    const void* tcK;
+    const void* tcV;
+    long long* tcacc;        // [N] exact fixed-point sums of the blocks' partial results (scale 2^tcq)
+    int tcq;
+    unsigned int* tcticket;
+    int* err;                // device error flag of the handle (bounded waits that gave up)
 };
 
 // Ring force and potential by method (ring.cu): VLASOV_RING_DIRECT runs ring_kernel (FMA in the
@@ -325,6 +333,15 @@ cudaError_t launch_ring_fixed(const RingArgs& a, cudaStream_t st);
 cudaError_t launch_ring_fixed_batch(bool pot, int slots, int max_n, int nsm, const RingArgs* args, cudaStream_t st);
 // Host: the fixed-point kernel tables of a ring grid of N nodes (Kq, Vq: N entries; shifts sK, sV).
 void ring_fixed_tables(int N, double dx, double eps, long long* Kq, long long* Vq, int* sK, int* sV);
+// Tensor-core form: N = 128 N1 (256 <= N <= 4096), one CTA per column block, tcgen05 MMAs in
+// 3xTF32 split precision.  Table images: N1 blocks x (hi, lo) x RING_TC_IMG bytes.
+constexpr int RING_TC_M = 128;
+constexpr int RING_TC_N = 32;                            // MMA N: N1 padded to a multiple of 16 (<= 32)
+constexpr size_t RING_TC_IMG = (size_t)RING_TC_M * RING_TC_M * 4;   // one 128 x 128 TF32 block
+bool ring_tc_ok(int N);
+size_t ring_tc_smem_bytes();
+cudaError_t launch_ring_tc(const RingArgs& a, cudaStream_t st);
+void ring_tc_tables(const double* table, int N, float* images);   // images: N/128 x 2 x 128 x 128 floats
 bool ring_fft_ok(int N);
 size_t ring_fft_smem_bytes(int N, bool f64);
 cudaError_t launch_ring_fft(bool f64, const RingArgs& a, cudaStream_t st);

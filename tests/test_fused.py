@@ -163,7 +163,7 @@ def test_fp32_class_fused_defaults_and_accounting(precision):
     w = I.HMF_256.resized(128, 128)
     with V.Sim.from_workload(w, precision=precision) as s:
         s.set_f(I.initial_state(w))
-        assert s.fused_x == (precision == "f32")   # on by default for FP32 storage only
+        assert s.fused_x                            # on by default for FP32-class storage
         s.fused_x = True
         L = s.kernels_per_step()
         assert len(s.slot_names()) == L
@@ -172,7 +172,7 @@ def test_fp32_class_fused_defaults_and_accounting(precision):
         assert ms.shape == (L,) and np.all(ms > 0)
     w = I.SHEET_4096.resized(128, 256)
     with V.Sim.from_workload(w, precision=precision) as s:
-        assert s.fused_x == (precision == "f32")
+        assert s.fused_x
         s.fused_x = False
         assert not s.fused_x
     if precision == "f32":   # (BF16 grids are limited to Nx <= 4096 altogether)

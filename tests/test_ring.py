@@ -20,6 +20,9 @@ pytestmark = pytest.mark.gpu
 
 FP32_ARITH = {("direct", "f32"), ("fft_f32", "f32"), ("fft_f32", "fx64"), ("fft_f32", "f64"),
               ("fft_f32", "f64_native")}
+# the tensor-core method: 3xTF32 split products (TF32 high part times high and low parts; the
+# tensor cores read each low part as TF32 too, so about 21 significant bits), FP32 accumulation
+TENSOR_TOL = 5e-6
 
 
 def ring(n, np_=64, **kw):
@@ -32,6 +35,8 @@ def grid_of(w):
 
 
 def tol_of(method, prec):
+    if method == "tensor":
+        return TENSOR_TOL
     return 2e-6 if (method, prec) in FP32_ARITH else 1e-13
 
 
@@ -44,14 +49,14 @@ def state(w, seed=3):
 
 
 @pytest.mark.parametrize("prec", ["fx64", "f64", "f64_native", "f32"])
-@pytest.mark.parametrize("method", ["direct", "fixed", "fft", "fft_f32"])
+@pytest.mark.parametrize("method", ["direct", "fixed", "fft", "fft_f32", "tensor"])
 @pytest.mark.parametrize("n", [256, 2048, 4096, 200])
 def test_force_matches_oracle(n, method, prec):
     w = ring(n)
     f = state(w)
     with V.Sim.from_workload(w, precision=prec) as s:
         s.set_f(f)
-        if method.startswith("fft") and n & (n - 1):
+        if (method.startswith("fft") and n & (n - 1)) or (method == "tensor" and n % 128):
             with pytest.raises(V.VlasovError) as e:
                 s.ring_method = method
             assert e.value.code == V.EINVAL
@@ -64,7 +69,7 @@ def test_force_matches_oracle(n, method, prec):
 
 
 @pytest.mark.parametrize("prec", ["fx64", "f32"])
-@pytest.mark.parametrize("method", ["direct", "fixed", "fft", "fft_f32"])
+@pytest.mark.parametrize("method", ["direct", "fixed", "fft", "fft_f32", "tensor"])
 def test_potential_energy_matches_oracle(method, prec):
     w = ring(256, 256)
     with V.Sim.from_workload(w, precision=prec) as s:
@@ -74,7 +79,7 @@ def test_potential_energy_matches_oracle(method, prec):
         m = s.moments()
         f3 = s.get_f()
     mo = O.moments(grid_of(w), f3)
-    tol = 1e-12 if (method, prec) not in FP32_ARITH else 2e-6
+    tol = TENSOR_TOL if method == "tensor" else (1e-12 if (method, prec) not in FP32_ARITH else 2e-6)
     assert abs(m[-1, 5] - mo["potential"]) <= tol * abs(mo["potential"])
     assert abs(m[-1, 6] - (m[-1, 4] + m[-1, 5])) <= 1e-15 * abs(m[-1, 6]) + 1e-300
 
@@ -112,8 +117,36 @@ def test_ring_timings_report_every_method_and_keep_the_choice():
         s.ring_method = "fft"
         t = s.ring_timings(20)
         assert s.ring_method == "fft"
-    assert set(t) == {"direct", "fixed", "fft", "fft_f32"}
+    assert set(t) == {"direct", "fixed", "fft", "fft_f32", "tensor"}
     assert all(v > 0 for v in t.values())
+
+
+def test_tensor_method_repeats_bit_for_bit_and_its_bias_is_bounded():
+    """Its block sums are exact fixed-point additions, so runs repeat bit for bit.  The tensor cores'
+    FP32 accumulation is not round-to-nearest: on this sum, which cancels heavily (V' is odd), the
+    force comes out biased small (measured mean signed error -1.6e-6 relative; the direct FP32 loop:
+    +6e-9), so over 30 steps f moves 2.1e-4 max f from the run with the exact force (the direct FP32
+    loop: 2.1e-6).  Held to 3e-6 of bias per call and 1e-3 max f over the run."""
+    w = ring(1024, 256, steps=30)
+    g = O.Grid(w.model, w.nx, w.np, w.xmin, w.xmax, w.pmin, w.pmax, w.x_periodic, w.p_periodic, w.dt, w.eps, w.G)
+    out = {}
+    for method in ("tensor", "tensor2", "fixed"):
+        with V.Sim.from_workload(w, precision="f32") as s:
+            s.ring_method = method.rstrip("2")
+            s.set_f(I.initial_state(w))
+            if method == "tensor":
+                rho, F = s.density_force()
+                Fo = O.force(g, rho)
+                big = np.abs(Fo) > 0.1 * np.abs(Fo).max()
+                bias = float(np.mean((F - Fo)[big] * np.sign(Fo[big]) / np.abs(Fo[big])))
+                assert abs(bias) <= 3e-6, bias
+            s.step(w.steps)
+            out[method] = (s.get_f(), s.moments())
+    assert np.array_equal(out["tensor"][0], out["tensor2"][0])
+    assert np.array_equal(out["tensor"][1], out["tensor2"][1])
+    ref_f, ref_m = out["fixed"]
+    assert np.max(np.abs(out["tensor"][0] - ref_f)) <= 1e-3 * ref_f.max()
+    assert np.max(np.abs(out["tensor"][1][:, 1:7] - ref_m[:, 1:7])) <= 1e-4
 
 
 def test_ring_method_errors():
