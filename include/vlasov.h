@@ -234,7 +234,9 @@ long long vlasov_launches(const vlasov_sim* sim, int n);
    filters launch forms Mx, My.
    With fused x-shifts and n >= 2 the slots are those between two steps, averaged over the n-1 such
    places: fused x-shifts (step 4 and the next step 1), moment reduction, [ring potential],
-   [density reduction, ring force], p-shift filters, p-shift. */
+   [density reduction, ring force], p-shift filters, p-shift.  The ring with VLASOV_RING_FIXED
+   merges the two reductions into one launch and the two convolutions (the end state's potential,
+   the next force) into another: fused x-shifts, reductions, convolutions, filters, p-shift. */
 int vlasov_step_timed(vlasov_sim* sim, int n, double* ms_per_launch, int max_launches, int* nlaunch);
 
 /* ---------------------------------------------------------------------------------------------

@@ -295,15 +295,15 @@ __global__ void __launch_bounds__(CR_ACC_THREADS) colreduce_acc_kernel(ColReduce
 // thread adds only about B/32 partials; warp 0 forms the block's mass and cos/sin-weighted sums with
 // shuffles, and the last block to finish computes the totals (colreduce_final).
 constexpr int CRP_THREADS = 1024;
-__global__ void __launch_bounds__(CRP_THREADS) colreduce_p64_kernel(ColReduceArgs a)
+__device__ __forceinline__ void colreduce_p64_body(const ColReduceArgs& a, int bx)
 {
     __shared__ long long shc[32][33];
     __shared__ i128 red[33];
     __shared__ bool is_last;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
+    const int i = bx * 32 + lane;
     const int nblk = (a.Nx + 31) / 32;
-    if ((int)blockIdx.x >= nblk) return;
+    if (bx >= nblk) return;
     long long s = 0;
     if (i < a.Nx) {
         const long long* __restrict__ cp = a.colpart64 + i;
@@ -337,9 +337,9 @@ __global__ void __launch_bounds__(CRP_THREADS) colreduce_p64_kernel(ColReduceArg
         cx = warp_sum_i128(cx);
         cy = warp_sum_i128(cy);
         if (lane == 0) {
-            bp[blockIdx.x * 3 + 0] = cm;
-            bp[blockIdx.x * 3 + 1] = cx;
-            bp[blockIdx.x * 3 + 2] = cy;
+            bp[bx * 3 + 0] = cm;
+            bp[bx * 3 + 1] = cx;
+            bp[bx * 3 + 2] = cy;
             __threadfence();
             is_last = atomicAdd(a.ticket, 1u) == (unsigned int)nblk - 1;
         }
@@ -355,6 +355,27 @@ __global__ void __launch_bounds__(CRP_THREADS) colreduce_p64_kernel(ColReduceArg
         y += vb[b * 3 + 2];
     }
     colreduce_final(a, m, x, y, red);
+}
+
+__global__ void __launch_bounds__(CRP_THREADS) colreduce_p64_kernel(ColReduceArgs a)
+{
+    colreduce_p64_body(a, blockIdx.x);
+}
+
+// Two independent reductions of exact per-CTA partial rows in one launch (blocks [0, nblk) take a,
+// the rest b); each keeps its own outputs, scratch and ticket.
+__global__ void __launch_bounds__(CRP_THREADS) colreduce_p64_dual_kernel(ColReduceArgs a, ColReduceArgs b)
+{
+    const int nblk = (a.Nx + 31) / 32;
+    if ((int)blockIdx.x < nblk) colreduce_p64_body(a, blockIdx.x);
+    else colreduce_p64_body(b, (int)blockIdx.x - nblk);
+}
+
+cudaError_t launch_colreduce_p64_dual(const ColReduceArgs& a, const ColReduceArgs& b, cudaStream_t st)
+{
+    const int nblk = (a.Nx + 31) / 32;
+    colreduce_p64_dual_kernel<<<2 * nblk, CRP_THREADS, 0, st>>>(a, b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st)

@@ -176,6 +176,22 @@ __global__ void __launch_bounds__(RINGFX_THREADS) ringfx_kernel(RingArgs a)
     ringfx_body<POT>(a, blockIdx.x);
 }
 
+// The force of one state (f) and the potential of another (p) in one launch: blocks [0, nf) take
+// the force, the rest the potential; each keeps its own scratch and tickets.
+__global__ void __launch_bounds__(RINGFX_THREADS) ringfx_dual_kernel(RingArgs f, RingArgs p)
+{
+    const int nf = ((f.N + 31) / 32) * f.ksplit;
+    if ((int)blockIdx.x < nf) ringfx_body<false>(f, blockIdx.x);
+    else ringfx_body<true>(p, (int)blockIdx.x - nf);
+}
+
+cudaError_t launch_ring_fixed_dual(const RingArgs& f, const RingArgs& p, cudaStream_t st)
+{
+    const int nf = ((f.N + 31) / 32) * f.ksplit;
+    ringfx_dual_kernel<<<2 * nf, RINGFX_THREADS, ringfx_smem_bytes(f.N, f.ksplit), st>>>(f, p);
+    return cudaGetLastError();
+}
+
 // Batched form: blockIdx.y = slot (N = 0: not a ring slot); each slot keeps its own split.
 template <bool POT>
 __global__ void __launch_bounds__(RINGFX_THREADS) ringfx_batch_kernel(const RingArgs* __restrict__ args)
@@ -612,6 +628,7 @@ cudaError_t set_ringfx_attributes(int max_smem)
 {
     cudaError_t e = allow_dynamic_smem(ringfx_kernel<false>, max_smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_kernel<true>, max_smem);
+    if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_dual_kernel, max_smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_batch_kernel<false>, max_smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(ringfx_batch_kernel<true>, max_smem);
     if (e == cudaSuccess) e = allow_dynamic_smem(ring_fft_kernel<double, double2>, max_smem);

@@ -98,7 +98,7 @@ struct vlasov_sim {
     double* Fout = nullptr;
     void* blockpart = nullptr;  // int128 [crgrid][3]
     void* ringpart = nullptr;   // int128 [(Nx+7)/8]
-    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring
+    unsigned int* tickets = nullptr;  // [0] colreduce, [1] ring, [2] colreduce of the end state (fused ring)
     unsigned long long* maxbits = nullptr;
     Scalars* sc = nullptr;
     double* costab = nullptr;
@@ -125,6 +125,14 @@ struct vlasov_sim {
     void* ring_fft32 = nullptr;   // same as float2
     void* ring_tcK = nullptr;     // tensor-core method: Toeplitz block images of V' and V
     void* ring_tcV = nullptr;
+    // fused ring steps: the moments of the end of a step and the force of the next step's f^(I) are
+    // reduced and convolved side by side, so the end state has its own copies of these
+    double* rho_m = nullptr;
+    long long* colfx_m = nullptr;
+    Scalars* sc_m = nullptr;
+    void* blockpart_m = nullptr;
+    void* ring_gpart_m = nullptr;
+    unsigned int* ring_gticket_m = nullptr;
     long long* ring_tcacc = nullptr;   // [N] fixed-point sums of the blocks' partial results
     unsigned int* ring_tcticket = nullptr;
     double ring_tcmax[2] = {0, 0};     // max |V'|, max |V| (scale of those sums)
@@ -704,6 +712,54 @@ int enq_xx(vlasov_sim* s, int c, Marks* marks)
     return enq_moments(s, s->xxgrid, true, marks);
 }
 
+// Fused ring steps with the exact fixed-point convolutions: the two column reductions (end of this
+// step, f^(I) of the next) in one launch and the two convolutions (the end state's potential and
+// record, the next step's force) in one launch.
+bool ring_merged(const vlasov_sim* s)
+{
+    return s->model == VLASOV_RING && s->fuse && s->ring_method == RING_M_FIXED && s->ring_gpart_m != nullptr &&
+           s->colpart_m != nullptr;
+}
+
+int enq_mid_ring_merged(vlasov_sim* s, int c, Marks* marks)
+{
+    XShiftArgs a = xargs(s, s->f[c], nullptr, s->xp, true, true, s->xrec);
+    a.stages = s->xxstages;
+    a.box_h = s->xbox_h;
+    a.ctapart = nullptr;
+    a.colpart64 = s->colpart_m;
+    XShiftArgs b = xargs(s, nullptr, s->f[c ^ 1], s->xp, true, false, s->xrec);
+    if (s->fx) CU_TRY(launch_xxshift_fx(s->xper, s->xxgrid, &s->xtmap[c], a, b, emargs(s, s->xp, s->xe), s->st));
+    else CU_TRY(launch_xxshift(s->esz, s->xper, s->xxgrid, a, b, s->st));
+    MARK();
+    ColReduceArgs cm = crargs(s, s->xxgrid, true, true, true, true);   // end of this step: moments
+    cm.rho = s->rho_m;
+    cm.colfx = s->colfx_m;
+    cm.sc = s->sc_m;
+    cm.blockpart = s->blockpart_m;
+    cm.ticket = &s->tickets[2];
+    ColReduceArgs cd = crargs(s, s->xxgrid, false, false);             // f^(I) of the next step: density
+    if (!cm.colpart64 || !cd.colpart64 || cm.colacc || cd.colacc) return fail(VLASOV_ECUDA, "merged reduction needs partial rows");
+    CU_TRY(launch_colreduce_p64_dual(cm, cd, s->st));
+    MARK();
+    RingArgs rf = ringargs(s, false);
+    RingArgs rp = ringargs(s, true);
+    rp.colfx = s->colfx_m;
+    rp.rho = s->rho_m;
+    rp.sc = s->sc_m;
+    rp.gpart = s->ring_gpart_m;
+    rp.gticket = s->ring_gticket_m;
+    CU_TRY(launch_ring_fixed_dual(rf, rp, s->st));
+    MARK();
+    int rc = launch_pparams_only(s, nullptr);
+    if (rc) return rc;
+    MARK();
+    const int o = c ^ 1;
+    CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
+    MARK();
+    return VLASOV_OK;
+}
+
 // One whole Strang step from buffer c (result in c^1).
 int enqueue_step(vlasov_sim* s, int c, Marks* marks = nullptr)
 {
@@ -724,6 +780,7 @@ int enqueue_piece(vlasov_sim* s, int c, Piece k, Marks* marks = nullptr)
         return rc ? rc : enq_force_p(s, c, s->xgrid, marks);
     }
     if (k == P_MID) {
+        if (ring_merged(s)) return enq_mid_ring_merged(s, c, marks);
         int rc = enq_xx(s, c, marks);
         return rc ? rc : enq_force_p(s, c, s->xxgrid, marks);
     }
@@ -826,7 +883,8 @@ void vlasov_destroy(vlasov_sim* s)
                     s->hist, s->dstep, s->err, s->xrec, s->srec, s->cos50, s->sin50, s->ctapart,
                     s->ctapart_m, s->colpart_m, s->kin128, s->gs_h, s->ringKq, s->ringVq, s->ring_gpart,
                     s->ring_gticket, s->ring_upart, s->ring_fft64, s->ring_fft32, s->ring_tcK, s->ring_tcV,
-                    s->ring_tcacc, s->ring_tcticket};
+                    s->ring_tcacc, s->ring_tcticket, s->rho_m, s->colfx_m, s->sc_m, s->blockpart_m, s->ring_gpart_m,
+                    s->ring_gticket_m};
     for (void* p : bufs) cudaFree(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -1039,8 +1097,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     CTRY(cudaMalloc(&s->blockpart, 16 * 3 * (size_t)s->crgrid));
     CTRY(cudaMalloc(&s->ringpart, 16 * (size_t)ring_blocks(Nx)));
     CTRY(cudaMalloc(&s->maxbits, sizeof(unsigned long long)));
-    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 2));
-    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 2, s->st));
+    CTRY(cudaMalloc(&s->tickets, sizeof(unsigned int) * 4));
+    CTRY(cudaMemsetAsync(s->tickets, 0, sizeof(unsigned int) * 4, s->st));
     CTRY(cudaMalloc(&s->sc, sizeof(Scalars)));
     CTRY(cudaMemsetAsync(s->sc, 0, sizeof(Scalars), s->st));
     CTRY(cudaMalloc(&s->hist, sizeof(MomentRec) * HIST_CAP));
@@ -1109,6 +1167,14 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
             CTRY(cudaMalloc(&s->ring_gpart, 16 * (size_t)s->ring_ksplit * Nx));
             CTRY(cudaMalloc(&s->ring_gticket, sizeof(unsigned int) * ngrp));
             CTRY(cudaMemsetAsync(s->ring_gticket, 0, sizeof(unsigned int) * ngrp, s->st));
+            CTRY(cudaMalloc(&s->ring_gpart_m, 16 * (size_t)s->ring_ksplit * Nx));
+            CTRY(cudaMalloc(&s->ring_gticket_m, sizeof(unsigned int) * ngrp));
+            CTRY(cudaMemsetAsync(s->ring_gticket_m, 0, sizeof(unsigned int) * ngrp, s->st));
+            CTRY(cudaMalloc(&s->rho_m, sizeof(double) * Nx));
+            CTRY(cudaMalloc(&s->colfx_m, sizeof(long long) * Nx));
+            CTRY(cudaMalloc(&s->sc_m, sizeof(Scalars)));
+            CTRY(cudaMemsetAsync(s->sc_m, 0, sizeof(Scalars), s->st));
+            CTRY(cudaMalloc(&s->blockpart_m, 16 * 3 * (size_t)s->crgrid));
             CTRY(cudaMalloc(&s->ring_upart, 16 * (size_t)ngrp));
             CTRY(cudaMemcpyAsync(s->ringKq, Kq.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
             CTRY(cudaMemcpyAsync(s->ringVq, Vq.data(), sizeof(long long) * Nx, cudaMemcpyHostToDevice, s->st));
@@ -1632,6 +1698,7 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 int vlasov_kernels_per_step(const vlasov_sim* s)
 {
     if (!s) return 0;
+    if (ring_merged(s)) return 5;   // fused x-shifts, both reductions, both convolutions, filters, p-shift
     return (s->fuse ? 2 : 3) + force_launches(s) + moment_launches(s);
 }
 

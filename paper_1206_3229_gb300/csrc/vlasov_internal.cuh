@@ -328,6 +328,8 @@ int ringfx_ksplit(int N, int nsm);
 size_t ringfx_smem_bytes(int N, int ksplit);
 cudaError_t set_ringfx_attributes(int max_smem);
 cudaError_t launch_ring_fixed(const RingArgs& a, cudaStream_t st);
+// Fixed-point force of one state and potential (and moment record) of another in one launch.
+cudaError_t launch_ring_fixed_dual(const RingArgs& f, const RingArgs& p, cudaStream_t st);
 // Batched fixed-point form: grid.y = slot; each slot's split follows its own N (as a single grid),
 // the launch covers the split of max_n.
 cudaError_t launch_ring_fixed_batch(bool pot, int slots, int max_n, int nsm, const RingArgs* args, cudaStream_t st);
@@ -444,6 +446,8 @@ cudaError_t launch_fx_to_f64(const long long* s, double* d, size_t n, int Ef, cu
 cudaError_t launch_colsum_fx(const long long* f, int Nx, int Np, int Ef, double* colpart, cudaStream_t st);
 
 cudaError_t launch_colreduce(const ColReduceArgs& a, int grid, cudaStream_t st);
+// Two reductions of exact per-CTA partial rows (colpart64) in one launch.
+cudaError_t launch_colreduce_p64_dual(const ColReduceArgs& a, const ColReduceArgs& b, cudaStream_t st);
 
 // Batched forms (FP32 or FX64 storage): grid.y = slot; per-slot arguments (two buffer parities
 // for the sweeps) live in device arrays, so one captured graph serves any set of occupied slots.

@@ -463,6 +463,10 @@ class Sim:
         """Names of the step_timed slots (for n >= 2 when fused_x)."""
         hmf_cta = self.model == HMF and self.precision in (FX64, BF16, F32) and self.nx * self.np <= 1 << 24 \
             and self.spline == "fd"
+        if self.fused_x and self.model == RING and self.ring_method == "fixed":
+            # the end state's moments and the next force: reductions and convolutions merged
+            return ["xshift_fused", "reduce_moments_density", "ring_potential_force", "pshift_filters",
+                    "pshift_step3"]
         if self.fused_x:
             names = ["xshift_fused", "reduce_moments"]
             if self.model == RING:
