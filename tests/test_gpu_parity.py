@@ -102,7 +102,20 @@ def test_integer_free_streaming_is_exact_on_gpu(prec):
         s.step(3)
         got = s.get_f()
     expect = np.stack([np.roll(f0[j], 6 * (j - npp // 2)) for j in range(npp)])
-    assert np.max(np.abs(got - expect)) <= (1e-14 if prec == "f64_native" else 4e-14)
+    if prec == "f64_native":
+        # the foot fraction is exactly 0, so the filter is exactly (0, 0, 0, 0, 1, 0, ...)
+        assert np.array_equal(got, expect)
+        return
+    # the split arithmetic rounds the FP32 part of every output to a multiple of 2^12 grid units,
+    # 2^(Ef-49) (2^Ef >= 4 max f): the first sweep puts each value on that grid (at most half a step,
+    # 2^(Ef-50), off), after which an integer shift reproduces it exactly (its low bits are zero, so
+    # the FP32 conversion of its remainder is exact); plus the fixed-point upload (FX64, 2^(Ef-62)),
+    # or the split of an IEEE double, which keeps 24 bits below 2^(Ef-31) (F64, 2^(Ef-55))
+    Ef = math.frexp(float(np.abs(f0).max()))[1] + 2
+    bound = 2.0 ** (Ef - 50) + (2.0 ** (Ef - 62) if prec == "fx64" else 2.0 ** (Ef - 55))
+    err = float(np.max(np.abs(got - expect)))
+    print(f"{prec}: integer free streaming, max |df| = {err:.3e} (bound {bound:.3e})")
+    assert err <= bound
 
 
 # ------------------------------------------------------------------------------------- density and forces
