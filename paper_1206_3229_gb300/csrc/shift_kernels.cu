@@ -18,6 +18,7 @@
 #include "vlasov_internal.cuh"
 
 #include <cuda_bf16.h>
+#include <cstddef>
 #include <type_traits>
 
 namespace vl {
@@ -484,13 +485,53 @@ __global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_batch_kernel(const X
 // to HBM (its column sums: the next density).  Same arithmetic as two launches.  512 threads,
 // 8 / V chunks of V columns each (Nx <= 4096); two intermediate rows alternate (one barrier per row).
 //   a: input, records, shape, first-pass outputs; b: output buffer and second-pass column sums.
+// One pass over a fused row: chunks of V columns at V (tid + c XXS_THREADS), c < CH, from the row
+// staged at `src` whose window for output 0 starts at `base` (periodic rows: base in [0, Nx), the
+// wrap copy at src + Nx serves windows that cross the end), written to `dst`: the intermediate row
+// in shared memory (TO_SMEM; periodic rows also get the wrap copy of its first 16 columns) or the
+// output row in HBM.  The row constants come in from the caller, computed once for both passes.
+template <typename S, int A, bool PERIODIC, int CH, bool TO_SMEM, typename T = typename VecOf<S>::T>
+__device__ __forceinline__ void xx_pass(const S* __restrict__ src, S* __restrict__ dst, const T (&w)[NTAP],
+                                        int base, int n0, int Nx, T g, T d,
+                                        typename VecOf<S>::acc (&acc)[CH][VecOf<S>::V],
+                                        typename VecOf<S>::acc& rowsum)
+{
+    constexpr int V = VecOf<S>::V;
+    using vec = typename VecOf<S>::vec;
+    const int i0 = V * (int)threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int i = i0 + c * V * XXS_THREADS;
+        if (i < Nx) {
+            int e = i + base;
+            if constexpr (PERIODIC) e = e >= Nx ? e - Nx : e;
+            T out[V];
+            xshift_chunk<S, A, PERIODIC>(src, e, w, i, i + n0, Nx, g, d, out);
+            const vec o = pack<S>(out);
+            *reinterpret_cast<vec*>(dst + i) = o;
+            if constexpr (TO_SMEM && PERIODIC) {
+                if (i < 16) *reinterpret_cast<vec*>(dst + Nx + i) = o;
+            }
+            T stored[V];   // the column sums are those of the stored values
+            unpack<S>(o, stored);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc[c][v] += stored[v];
+                rowsum += stored[v];
+            }
+        }
+    }
+}
+
 template <typename S, bool PERIODIC>
 __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftArgs& b)
 {
     using T = typename VecOf<S>::T;
     using acc_t = typename VecOf<S>::acc;
     constexpr int V = VecOf<S>::V;
-    constexpr int CH = 8 / V;
+    constexpr int CH = XXS_MAX_NX / (V * XXS_THREADS);
+    static_assert(CH * V * XXS_THREADS == XXS_MAX_NX && sizeof(T) == 4, "FP32-class storage");
+    static_assert(offsetof(XRec, w32) % 16 == 0 && XREC_BYTES % 16 == 0, "16-byte weight loads");
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
@@ -502,7 +543,7 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
     S* __restrict__ fout = static_cast<S*>(b.fout);
     const int Nx = a.Nx, Np = a.Np, PAD = a.pad, NS = a.stages;
     const int stride = Nx + 2 * PAD;
-    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int tid = threadIdx.x;
     const int G = a.ctas > 0 ? a.ctas : (int)gridDim.x;
     S* ibufs = bufs + (size_t)NS * stride;   // two intermediate rows
     unsigned char* recs = reinterpret_cast<unsigned char*>(ibufs + 2 * (size_t)stride);
@@ -516,11 +557,11 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
         }
         fence_barrier_init();
     }
-    for (int e = tid; e < 2 * stride; e += nthreads) ibufs[e] = from_math<S>(T(0));
+    for (int e = tid; e < 2 * stride; e += XXS_THREADS) ibufs[e] = from_math<S>(T(0));
     if constexpr (!PERIODIC) {
         for (int s = 0; s < NS; ++s) {
             S* q = bufs + (size_t)s * stride;
-            for (int e = tid; e < PAD; e += nthreads) {
+            for (int e = tid; e < PAD; e += XXS_THREADS) {
                 q[e] = from_math<S>(T(0));
                 q[PAD + Nx + e] = from_math<S>(T(0));
             }
@@ -555,30 +596,48 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
         }
     float kinf = 0.f;   // FP32 kinetic sum of this thread's rows (FP64 in the epilogue)
 
+    int s = 0;          // stage of row r, and the parity of its barrier phase
+    uint32_t ph = 0;
     int it = 0;
     bool failed = false;
     for (int r = blockIdx.x; r < Np; r += G, ++it) {
-        const int s = it % NS;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((it / NS) & 1), WAIT_LIMIT_NS);
-        S* ib = ibufs + (size_t)(it & 1) * stride + PAD;
-        int n0 = 0;
+        const bool ok = mbar_wait_bounded(&bars[s], ph, WAIT_LIMIT_NS);
+        S* ib = ibufs + ((it & 1) ? stride : 0) + PAD;
+        // row constants, shared by both passes (the same displacement and weights)
+        int n0 = 0, A = 0, base = 0;
         T w[NTAP];
         T g = T(0), d = T(0);
-        acc_t rowsum = acc_t(0);
         float p2h = 0.f;
+        acc_t rowsum = acc_t(0);
         if (ok) {
             const XRec* rc = reinterpret_cast<const XRec*>(recs + (size_t)s * XREC_BYTES);
             n0 = rc->n0;
             p2h = rc->p2h;
-#pragma unroll
-            for (int t = 0; t < NTAP; ++t) w[t] = sizeof(T) == 8 ? (T)rc->w64[t] : (T)rc->w32[t];
-            if constexpr (!PERIODIC) {
-                g = sizeof(T) == 8 ? (T)rc->g64 : (T)rc->g32;
-                d = sizeof(T) == 8 ? (T)rc->d64 : (T)rc->d32;
+            const float4 w03 = *reinterpret_cast<const float4*>(rc->w32);
+            const float4 w47 = *reinterpret_cast<const float4*>(rc->w32 + 4);
+            const float2 w89 = *reinterpret_cast<const float2*>(rc->w32 + 8);
+            w[0] = w03.x;
+            w[1] = w03.y;
+            w[2] = w03.z;
+            w[3] = w03.w;
+            w[4] = w47.x;
+            w[5] = w47.y;
+            w[6] = w47.z;
+            w[7] = w47.w;
+            w[8] = w89.x;
+            w[9] = w89.y;
+            if constexpr (PERIODIC) {
+                const int m4 = rc->m4;   // (n0 - 4) mod Nx; Nx is a multiple of V
+                A = m4 & (V - 1);
+                base = m4 - A;
+            } else {
+                A = (n0 - 4) & (V - 1);
+                base = n0 - 4 - A;
+                g = rc->g32;
+                d = rc->d32;
             }
             const S* rowbuf = bufs + (size_t)s * stride + PAD;
-            const int A = (n0 - 4) & (V - 1);
-#define VL_PASS1(AA) xshift_row<S, AA, PERIODIC, CH, PERIODIC>(rowbuf, ib, w, n0, Nx, g, d, nthreads, acc1, rowsum)
+#define VL_PASS1(AA) xx_pass<S, AA, PERIODIC, CH, true>(rowbuf, ib, w, base, n0, Nx, g, d, acc1, rowsum)
             if constexpr (V == 4) {
                 switch (A) {
                     case 0: VL_PASS1(0); break;
@@ -615,8 +674,7 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
         kinf = fmaf(p2h, (float)rowsum, kinf);
         acc_t rowsum2 = acc_t(0);
         S* orow = fout + (size_t)r * Nx;
-        const int A = (n0 - 4) & (V - 1);
-#define VL_PASS2(AA) xshift_row<S, AA, PERIODIC, CH, false>(ib, orow, w, n0, Nx, g, d, nthreads, acc2, rowsum2)
+#define VL_PASS2(AA) xx_pass<S, AA, PERIODIC, CH, false>(ib, orow, w, base, n0, Nx, g, d, acc2, rowsum2)
         if constexpr (V == 4) {
             switch (A) {
                 case 0: VL_PASS2(0); break;
@@ -637,6 +695,10 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
             }
         }
 #undef VL_PASS2
+        if (++s == NS) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
     __syncthreads();   // every warp is done with the stages and intermediate rows
 
@@ -656,7 +718,7 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
 }
 
 template <typename S, bool PERIODIC>
-__global__ void __launch_bounds__(XXS_THREADS, 2) xxshift_kernel(XShiftArgs a, XShiftArgs b)
+__global__ void __launch_bounds__(XXS_THREADS, XXS_CTAS_PER_SM) xxshift_kernel(XShiftArgs a, XShiftArgs b)
 {
     xxshift_body<S, PERIODIC>(a, b);
 }
@@ -670,7 +732,7 @@ size_t xxshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
 cudaError_t launch_xxshift(int elem_bytes, bool periodic, int grid, const XShiftArgs& a, const XShiftArgs& b,
                            cudaStream_t st)
 {
-    if (a.rec == nullptr || a.Nx > 8 * XXS_THREADS || a.stages < 1 || a.stages > 8) return cudaErrorInvalidValue;
+    if (a.rec == nullptr || a.Nx > XXS_MAX_NX || a.stages < 1 || a.stages > 8) return cudaErrorInvalidValue;
     const size_t smem = xxshift_smem_bytes(a.Nx, a.pad, a.stages, elem_bytes);
     if (elem_bytes == 2) {
         if (periodic) xxshift_kernel<bf16, true><<<grid, XXS_THREADS, smem, st>>>(a, b);

@@ -1055,7 +1055,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
         auto stages_in = [&](size_t budget) {
             return budget > 256 + 2 * row ? (int)std::min<size_t>(3, (budget - 256 - 2 * row) / (row + XREC_BYTES)) : 0;
         };
-        int st = stages_in((size_t)max_optin / 2 - 2048);
+        int st = stages_in((size_t)max_optin / XXS_CTAS_PER_SM - 2048);
         if (st < 2) st = stages_in((size_t)max_optin - 2048);
         if (st >= 2) {
             int xocc = 0;

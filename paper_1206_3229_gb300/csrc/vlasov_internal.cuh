@@ -395,9 +395,11 @@ cudaError_t launch_gs_xshift(int elem_bytes, bool periodic, bool kin, int grid, 
 cudaError_t launch_gs_pshift(int elem_bytes, bool p_periodic, int grid, const PShiftArgs& a, cudaStream_t st);
 cudaError_t gs_occupancy(int elem_bytes, bool xdir, size_t smem, int* blocks);
 
-// Fused x-shifts with FP32-class storage (elem_bytes 4: FP32, 2: BF16): 512 threads of 8 columns.
+// Fused x-shifts with FP32-class storage (elem_bytes 4: FP32, 2: BF16): XXS_THREADS threads share
+// rows of up to XXS_MAX_NX columns; XXS_CTAS_PER_SM CTAs per SM.
 constexpr int XXS_THREADS = 512;
-constexpr int XXS_MAX_NX = 8 * XXS_THREADS;
+constexpr int XXS_CTAS_PER_SM = 2;
+constexpr int XXS_MAX_NX = 4096;
 size_t xxshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes);
 cudaError_t launch_xxshift(int elem_bytes, bool periodic, int grid, const XShiftArgs& a, const XShiftArgs& b,
                            cudaStream_t st);
