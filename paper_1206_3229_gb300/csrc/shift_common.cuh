@@ -35,6 +35,7 @@ __device__ __forceinline__ T edge_fix(T out, const T* x, int k, int n, T g, T d)
 
 struct TileWin {
     int i0, j0, r0, nb;
+    int kmin, kmax;   // least and greatest foot offset n0 over the tile's columns
     bool smem_ok;
 };
 
@@ -59,6 +60,8 @@ __device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __r
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
     if (!colvalid) n0_lane = kmin;   // columns past Nx read (and discard) the tile's own window
+    t.kmin = kmin;
+    t.kmax = kmax;
     t.r0 = t.j0 + kmin - 4;
     const long long R = (long long)PS_TH + 9 + ((long long)kmax - (long long)kmin);
     t.smem_ok = !PPER && R <= RB;

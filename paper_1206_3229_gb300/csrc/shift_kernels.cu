@@ -1143,17 +1143,33 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
                 for (int u = 0; u < PS_RPT + 9; ++u)
                     x[u] = colvalid ? to_math(gload_p<S, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np)) : T(0);
             }
+            // A tile whose columns and rows all lie inside the grid, with every foot cell inside
+            // too (the common case), takes the rows without per-row checks.
+            const bool interior = t.i0 + PS_TW <= Nx && t.j0 + PS_TH <= Np &&
+                                  (PPER || (t.j0 + t.kmin >= 0 && t.j0 + PS_TH - 1 + t.kmax < Np - 1));
+            if (interior) {
+                S* __restrict__ op = fout + (size_t)jb * Nx + i;
 #pragma unroll
-            for (int rr = 0; rr < PS_RPT; ++rr) {
-                const int j = jb + rr;
-                T acc = w[0] * x[rr];
+                for (int rr = 0; rr < PS_RPT; ++rr) {
+                    T acc = w[0] * x[rr];
 #pragma unroll
-                for (int k = 1; k < NTAP; ++k) acc = fma(w[k], x[rr + k], acc);
-                if constexpr (!PPER) {
-                    const int kk = j + n0_i;
-                    if (kk < 0 || kk >= Np - 1) acc = edge_fix(acc, &x[rr], kk, Np, g, d);
+                    for (int k = 1; k < NTAP; ++k) acc = fma(w[k], x[rr + k], acc);
+                    *op = from_math<S>(acc);
+                    op += Nx;
                 }
-                if (colvalid && j < Np) fout[(size_t)j * Nx + i] = from_math<S>(acc);
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < PS_RPT; ++rr) {
+                    const int j = jb + rr;
+                    T acc = w[0] * x[rr];
+#pragma unroll
+                    for (int k = 1; k < NTAP; ++k) acc = fma(w[k], x[rr + k], acc);
+                    if constexpr (!PPER) {
+                        const int kk = j + n0_i;
+                        if (kk < 0 || kk >= Np - 1) acc = edge_fix(acc, &x[rr], kk, Np, g, d);
+                    }
+                    if (colvalid && j < Np) fout[(size_t)j * Nx + i] = from_math<S>(acc);
+                }
             }
         }
         if (__syncthreads_or(!ok)) {
