@@ -442,72 +442,85 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_e_kernel(const __grid
                 feed(u, v.kx, v.r);
             }
         }
-        bool any_edge = false;
+        // a tile wholly inside the grid, every foot cell inside too (the common case): no per-row
+        // edge or bounds checks
+        const bool interior = t.i0 + PS_TW <= Nx && t.j0 + PS_TH <= Np &&
+                              (PPER || (t.j0 + t.kmin >= 0 && t.j0 + PS_TH - 1 + t.kmax < Np - 1));
+        if (interior) {
+            double* __restrict__ op = fout + (size_t)jb * Nx + i;
 #pragma unroll
-        for (int rw = 0; rw < PS_RPT; ++rw) {
-            const int j = jb + rw;
-            const double out = emul_to_f64(emul_finish(M[rw], Sacc[rw]), em.Ef);
-            bool edge = false;
-            if constexpr (!PPER) {
-                const int kk = j + n0_i;
-                edge = kk < 0 || kk >= Np - 1;
+            for (int rw = 0; rw < PS_RPT; ++rw) {
+                *op = emul_to_f64(emul_finish(M[rw], Sacc[rw]), em.Ef);
+                op += Nx;
             }
-            any_edge |= edge;
-            if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
-        }
-        if constexpr (!PPER) {
-            if (any_edge && colvalid && em.Whe) {
-                // rare boundary rows (f'' = 0 outside the grid): 0 where the foot cell is outside,
-                // the column's edge filters where it touches the end, in the interior arithmetic
-                for (int rw = 0; rw < PS_RPT; ++rw) {
-                    const int j = jb + rw, kk = j + n0_i;
-                    if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
-                    if (kk < -1 || kk >= Np) {
-                        fout[(size_t)j * Nx + i] = 0.0;
-                        continue;
-                    }
-                    const int q = kk < 0 ? 0 : 1;
-                    long long M = EMUL_M0;
-                    float sa = 0.f, sbb = 0.f;
-                    for (int u = 0; u < NTAP; ++u) {
-                        int kx;
-                        float rr;
-                        if (t.smem_ok) {
-                            const int2 v = sb[(base + rw + u) * PS_TW + lane];
-                            kx = v.x;
-                            rr = __int_as_float(v.y);
-                        } else {
-                            const double x = gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
-                            const EmulElem ev = emul_split(x, s_base, bad);
-                            kx = ev.kx;
-                            rr = ev.r;
-                        }
-                        const size_t idx = ((size_t)q * NTAP + u) * Nx + i;
-                        M = mad_wide(em.Whe[idx], kx, M);
-                        sa = fmaf(em.wle[idx], __int2float_rn(kx), sa);
-                        sbb = fmaf(em.wfe[idx], rr, sbb);
-                    }
-                    fout[(size_t)j * Nx + i] = emul_to_f64(emul_finish(M, sa + sbb), em.Ef);
+        } else {
+            bool any_edge = false;
+#pragma unroll
+            for (int rw = 0; rw < PS_RPT; ++rw) {
+                const int j = jb + rw;
+                const double out = emul_to_f64(emul_finish(M[rw], Sacc[rw]), em.Ef);
+                bool edge = false;
+                if constexpr (!PPER) {
+                    const int kk = j + n0_i;
+                    edge = kk < 0 || kk >= Np - 1;
                 }
-            } else if (any_edge && colvalid) {
-                // no edge filters (not given): recompute in FP64
-                for (int rw = 0; rw < PS_RPT; ++rw) {
-                    const int j = jb + rw, kk = j + n0_i;
-                    if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
-                    double xv[NTAP];
-                    double acc = 0.0;
-                    for (int u = 0; u < NTAP; ++u) {
-                        double x;
-                        if (t.smem_ok) {
-                            const int2 v = sb[(base + rw + u) * PS_TW + lane];
-                            x = ((double)v.x + (double)__int_as_float(v.y)) * grid;
-                        } else {
-                            x = gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                any_edge |= edge;
+                if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
+            }
+            if constexpr (!PPER) {
+                if (any_edge && colvalid && em.Whe) {
+                    // rare boundary rows (f'' = 0 outside the grid): 0 where the foot cell is outside,
+                    // the column's edge filters where it touches the end, in the interior arithmetic
+                    for (int rw = 0; rw < PS_RPT; ++rw) {
+                        const int j = jb + rw, kk = j + n0_i;
+                        if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
+                        if (kk < -1 || kk >= Np) {
+                            fout[(size_t)j * Nx + i] = 0.0;
+                            continue;
                         }
-                        xv[u] = x;
-                        acc = fma(em.w64[(size_t)u * Nx + i], x, acc);
+                        const int q = kk < 0 ? 0 : 1;
+                        long long M = EMUL_M0;
+                        float sa = 0.f, sbb = 0.f;
+                        for (int u = 0; u < NTAP; ++u) {
+                            int kx;
+                            float rr;
+                            if (t.smem_ok) {
+                                const int2 v = sb[(base + rw + u) * PS_TW + lane];
+                                kx = v.x;
+                                rr = __int_as_float(v.y);
+                            } else {
+                                const double x = gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                                const EmulElem ev = emul_split(x, s_base, bad);
+                                kx = ev.kx;
+                                rr = ev.r;
+                            }
+                            const size_t idx = ((size_t)q * NTAP + u) * Nx + i;
+                            M = mad_wide(em.Whe[idx], kx, M);
+                            sa = fmaf(em.wle[idx], __int2float_rn(kx), sa);
+                            sbb = fmaf(em.wfe[idx], rr, sbb);
+                        }
+                        fout[(size_t)j * Nx + i] = emul_to_f64(emul_finish(M, sa + sbb), em.Ef);
                     }
-                    fout[(size_t)j * Nx + i] = emul_edge(acc, xv, kk, Np, g, d);
+                } else if (any_edge && colvalid) {
+                    // no edge filters (not given): recompute in FP64
+                    for (int rw = 0; rw < PS_RPT; ++rw) {
+                        const int j = jb + rw, kk = j + n0_i;
+                        if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
+                        double xv[NTAP];
+                        double acc = 0.0;
+                        for (int u = 0; u < NTAP; ++u) {
+                            double x;
+                            if (t.smem_ok) {
+                                const int2 v = sb[(base + rw + u) * PS_TW + lane];
+                                x = ((double)v.x + (double)__int_as_float(v.y)) * grid;
+                            } else {
+                                x = gload_p<double, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                            }
+                            xv[u] = x;
+                            acc = fma(em.w64[(size_t)u * Nx + i], x, acc);
+                        }
+                        fout[(size_t)j * Nx + i] = emul_edge(acc, xv, kk, Np, g, d);
+                    }
                 }
             }
         }

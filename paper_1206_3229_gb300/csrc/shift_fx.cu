@@ -815,35 +815,48 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
                     feed2(u, X0, X1, u + 1 < NU);
                 }
             }
-            bool any_edge = false;
+            // a tile wholly inside the grid, every foot cell inside too (the common case): no
+            // per-row edge or bounds checks
+            const bool interior = t.i0 + PS_TW <= Nx && t.j0 + PS_TH <= Np &&
+                                  (PPER || (t.j0 + t.kmin >= 0 && t.j0 + PS_TH - 1 + t.kmax < Np - 1));
+            if (interior) {
+                long long* __restrict__ op = fout + (size_t)jb * Nx + i;
 #pragma unroll
-            for (int rw = 0; rw < PS_RPT; ++rw) {
-                const int j = jb + rw;
-                const long long out = fx_store(emul_finish(M[rw], Sacc[rw].x + Sacc[rw].y), rng);
-                bool edge = false;
-                if constexpr (!PPER) {
-                    const int kk = j + n0_i;
-                    edge = kk < 0 || kk >= Np - 1;
+                for (int rw = 0; rw < PS_RPT; ++rw) {
+                    *op = fx_store(emul_finish(M[rw], Sacc[rw].x + Sacc[rw].y), rng);
+                    op += Nx;
                 }
-                any_edge |= edge;
-                if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
-            }
-            if constexpr (!PPER) {
-                if (any_edge && colvalid) {
-                    const double g = em.gd[i], d = em.gd[Nx + i];
-                    for (int rw = 0; rw < PS_RPT; ++rw) {
-                        const int j = jb + rw, kk = j + n0_i;
-                        if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
-                        long long X[NTAP];
-                        for (int u = 0; u < NTAP; ++u)
-                            X[u] = t.smem_ok ? buf[(base + rw + u) * PS_TW + lane]
-                                             : gload_p<long long, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
-                        if (em.Whe) {   // fixed point, with the column's edge filters
-                            const FxOne o = fx_edge_one(X, em, i, Nx, kk, Np);
-                            rng |= o.rng;
-                            fout[(size_t)j * Nx + i] = o.v;
-                        } else {
-                            fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
+            } else {
+                bool any_edge = false;
+#pragma unroll
+                for (int rw = 0; rw < PS_RPT; ++rw) {
+                    const int j = jb + rw;
+                    const long long out = fx_store(emul_finish(M[rw], Sacc[rw].x + Sacc[rw].y), rng);
+                    bool edge = false;
+                    if constexpr (!PPER) {
+                        const int kk = j + n0_i;
+                        edge = kk < 0 || kk >= Np - 1;
+                    }
+                    any_edge |= edge;
+                    if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
+                }
+                if constexpr (!PPER) {
+                    if (any_edge && colvalid) {
+                        const double g = em.gd[i], d = em.gd[Nx + i];
+                        for (int rw = 0; rw < PS_RPT; ++rw) {
+                            const int j = jb + rw, kk = j + n0_i;
+                            if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
+                            long long X[NTAP];
+                            for (int u = 0; u < NTAP; ++u)
+                                X[u] = t.smem_ok ? buf[(base + rw + u) * PS_TW + lane]
+                                                 : gload_p<long long, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                            if (em.Whe) {   // fixed point, with the column's edge filters
+                                const FxOne o = fx_edge_one(X, em, i, Nx, kk, Np);
+                                rng |= o.rng;
+                                fout[(size_t)j * Nx + i] = o.v;
+                            } else {
+                                fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
+                            }
                         }
                     }
                 }
