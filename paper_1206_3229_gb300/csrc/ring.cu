@@ -613,17 +613,6 @@ cudaError_t launch_ring_fft(bool f64, const RingArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Opt every kernel of this file into the dynamic shared memory it may use: the per-block limit
-// max_smem less its own static shared memory.
-template <typename K>
-static cudaError_t allow_dynamic_smem(K kernel, int max_smem)
-{
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
-}
-
 cudaError_t set_ringfx_attributes(int max_smem)
 {
     cudaError_t e = allow_dynamic_smem(ringfx_kernel<false>, max_smem);

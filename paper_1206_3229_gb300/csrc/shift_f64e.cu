@@ -577,7 +577,7 @@ cudaError_t set_kernel_attributes_e(int max_smem)
 {
     cudaError_t e = cudaSuccess;
 #define VL_ATTR(fn) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)
+    if (e == cudaSuccess) e = allow_dynamic_smem(fn, max_smem)
     VL_ATTR((xshift_e_kernel<true, true>));
     VL_ATTR((xshift_e_kernel<true, false>));
     VL_ATTR((xshift_e_kernel<false, true>));

@@ -722,13 +722,37 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
         }
     };
 
-    int tile = blockIdx.x;
-    if (grp == 0 && tile < ntiles) {
+    // Warp 0 prepares each tile one iteration ahead: its window (and the copies into buffer b), and
+    // its columns' foot offsets and split filters into the slot info[b], so that no warp waits on
+    // those global loads when the tile starts.
+    struct TileInfo {
+        TileWin t;
+        int n0[PS_TW];
+        int Wh[NTAP][PS_TW];
+        float wl[NTAP][PS_TW], wr[NTAP][PS_TW];
+    };
+    __shared__ TileInfo info[2];
+    auto prepare = [&](int b, int tl) {   // warp 0
         int n0l;
         bool cv;
-        TileWin t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
-        if (lane == 0) issue(0, t);
-    }
+        const TileWin t = tile_window<PPER, PSF_RB>(tl, ntx, em.n0, Nx, lane, n0l, cv);
+        const size_t ic = (size_t)t.i0 + lane;
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) {
+            info[b].Wh[k][lane] = cv ? em.Wh[(size_t)k * Nx + ic] : 0;
+            info[b].wl[k][lane] = cv ? em.wl[(size_t)k * Nx + ic] : 0.f;
+            info[b].wr[k][lane] = cv ? em.wf[(size_t)k * Nx + ic] * 9.313225746154785e-10f : 0.f;
+        }
+        info[b].n0[lane] = n0l;
+        if (lane == 0) {
+            info[b].t = t;
+            issue(b, t);
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (grp == 0 && tile < ntiles) prepare(0, tile);
+    __syncthreads();
 
     int q = 0;
     bool failed = false;
@@ -736,33 +760,19 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
         const int b = q & 1;
         const int nt = tile + G;
         if (grp == 0 && nt < ntiles) {
-            int n0l;
-            bool cv;
-            TileWin tn = tile_window<PPER, PSF_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue(b ^ 1, tn);
-            }
-            if (cv) {   // the next tile's filters into L1 now, so that no warp waits for L2 on them then
-                const size_t in = (size_t)tn.i0 + lane;
-#pragma unroll
-                for (int k = 0; k < NTAP; ++k) {
-                    prefetch_l1(em.Wh + (size_t)k * Nx + in);
-                    prefetch_l1(em.wl + (size_t)k * Nx + in);
-                    prefetch_l1(em.wf + (size_t)k * Nx + in);
-                }
-            }
+            if (lane == 0) fence_proxy_async_smem();
+            __syncwarp();
+            prepare(b ^ 1, nt);
         }
-        int n0_i;
-        bool colvalid;
-        const TileWin t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
+        const TileWin t = info[b].t;
+        const int n0_i = info[b].n0[lane];
         const int i = t.i0 + lane;
+        const bool colvalid = i < Nx;
         FxW w;
 #pragma unroll
         for (int k = 0; k < NTAP; ++k) {
-            w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + i] : 0;
-            w.wlr[k] = colvalid ? make_float2(em.wl[(size_t)k * Nx + i], em.wf[(size_t)k * Nx + i] * 9.313225746154785e-10f)
-                                : make_float2(0.f, 0.f);
+            w.Wh[k] = info[b].Wh[k][lane];
+            w.wlr[k] = make_float2(info[b].wl[k][lane], info[b].wr[k][lane]);
         }
         const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
         if (ok) {
@@ -979,7 +989,7 @@ cudaError_t set_kernel_attributes_fx(int max_smem)
 {
     cudaError_t e = cudaSuccess;
 #define VL_ATTR(fn) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)
+    if (e == cudaSuccess) e = allow_dynamic_smem(fn, max_smem)
     VL_ATTR((xshift_fx_kernel<true, true>));
     VL_ATTR((xshift_fx_kernel<true, false>));
     VL_ATTR((xshift_fx_kernel<false, true>));

@@ -1093,13 +1093,37 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
         }
     };
 
-    int tile = blockIdx.x;
-    if (grp == 0 && tile < ntiles) {
+    // Warp 0 prepares each tile one iteration ahead: its window (and the copies into buffer b), and
+    // its columns' foot offsets and filters into the slot info[b], so that no warp waits on those
+    // global loads when the tile starts.
+    struct TileInfo {
+        TileWin t;
+        int n0[PS_TW];
+        T w[NTAP][PS_TW];
+        T gd[2][PS_TW];
+    };
+    __shared__ TileInfo info[2];
+    auto prepare = [&](int b, int tl) {   // warp 0
         int n0l;
         bool cv;
-        TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0l, cv);
-        if (lane == 0) issue(0, t);
-    }
+        const TileWin t = tile_window<PPER>(tl, ntx, a.n0, Nx, lane, n0l, cv);
+        const int ic = t.i0 + lane;
+#pragma unroll
+        for (int k = 0; k < NTAP; ++k) info[b].w[k][lane] = cv ? wcol[(size_t)k * Nx + ic] : T(0);
+        if constexpr (!PPER) {
+            info[b].gd[0][lane] = cv ? gdcol[ic] : T(0);
+            info[b].gd[1][lane] = cv ? gdcol[Nx + ic] : T(0);
+        }
+        info[b].n0[lane] = n0l;
+        if (lane == 0) {
+            info[b].t = t;
+            issue(b, t);
+        }
+    };
+
+    int tile = blockIdx.x;
+    if (grp == 0 && tile < ntiles) prepare(0, tile);
+    __syncthreads();
 
     int q = 0;
     bool failed = false;
@@ -1107,27 +1131,21 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
         const int b = q & 1;
         const int nt = tile + G;
         if (grp == 0 && nt < ntiles) {
-            int n0l;
-            bool cv;
-            TileWin tn = tile_window<PPER>(nt, ntx, a.n0, Nx, lane, n0l, cv);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue(b ^ 1, tn);
-            }
+            if (lane == 0) fence_proxy_async_smem();
+            __syncwarp();
+            prepare(b ^ 1, nt);
         }
-        int n0_i;
-        bool colvalid;
-        const TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0_i, colvalid);
+        const TileWin t = info[b].t;
+        const int n0_i = info[b].n0[lane];
         const int i = t.i0 + lane;
+        const bool colvalid = i < Nx;
         T w[NTAP];
 #pragma unroll
-        for (int k = 0; k < NTAP; ++k) w[k] = colvalid ? wcol[(size_t)k * Nx + i] : T(0);
+        for (int k = 0; k < NTAP; ++k) w[k] = info[b].w[k][lane];
         T g = T(0), d = T(0);
         if constexpr (!PPER) {
-            if (colvalid) {
-                g = gdcol[i];
-                d = gdcol[Nx + i];
-            }
+            g = info[b].gd[0][lane];
+            d = info[b].gd[1][lane];
         }
         const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
         if (ok) {
@@ -1253,7 +1271,7 @@ cudaError_t set_kernel_attributes(int max_smem)
 {
     cudaError_t e = cudaSuccess;
 #define VL_ATTR(fn) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)
+    if (e == cudaSuccess) e = allow_dynamic_smem(fn, max_smem)
     VL_ATTR((xshift_kernel<double, true, true>));
     VL_ATTR((xshift_kernel<double, true, false>));
     VL_ATTR((xshift_kernel<double, false, true>));

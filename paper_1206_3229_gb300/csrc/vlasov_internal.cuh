@@ -368,6 +368,16 @@ size_t pshift_smem_bytes(int elem_bytes);
 cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUtensorMap* tmap,
                           const PShiftArgs& a, cudaStream_t st);
 
+// Opt a kernel into the dynamic shared memory it may use: the per-block limit max_smem less its own
+// static shared memory.
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kernel, int max_smem)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+}
 cudaError_t set_kernel_attributes(int max_smem);
 cudaError_t set_kernel_attributes_e(int max_smem);
 int xshift_e_max_cols(int threads);
