@@ -1081,43 +1081,49 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
     }
     __syncthreads();
 
-    // lane 0 of warp 0: start the copies of a tile's window into buffer b (or complete the phase
-    // with no bytes when the tile takes the direct-load path).
-    auto issue = [&](int b, const TileWin& t) {
-        if (t.smem_ok) {
-            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(S)));
-            for (int q = 0; q < t.nb; ++q)
-                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap_ptr, t.i0, t.r0 + q * PS_BH, &bars[b]);
-        } else {
-            mbar_arrive_expect_tx(&bars[b], 0u);
-        }
-    };
-
-    // Warp 0 prepares each tile one iteration ahead: its window (and the copies into buffer b), and
-    // its columns' foot offsets and filters into the slot info[b], so that no warp waits on those
-    // global loads when the tile starts.
-    struct TileInfo {
-        TileWin t;
-        int n0[PS_TW];
+    // Warp 0 prepares each tile one iteration ahead: its window (copies into buffer b), its columns'
+    // foot offsets, and their filters into the slot info[b].  Filters of a tile with all 32 columns
+    // inside the grid arrive by bulk copies on the tile's barrier, so no warp issues a global load
+    // for them; the last, partial column tile loads them.
+    struct __align__(16) TileInfo {
         T w[NTAP][PS_TW];
         T gd[2][PS_TW];
+        int n0[PS_TW];
+        TileWin t;
     };
     __shared__ TileInfo info[2];
+    constexpr uint32_t ROWB = PS_TW * (uint32_t)sizeof(T);
+    constexpr uint32_t WBYTES = (NTAP + (PPER ? 0 : 2)) * ROWB;
     auto prepare = [&](int b, int tl) {   // warp 0
         int n0l;
         bool cv;
         const TileWin t = tile_window<PPER>(tl, ntx, a.n0, Nx, lane, n0l, cv);
+        // (BF16 storage loads them: measured faster there, its tiles being half the bytes)
+        const bool wbulk = sizeof(S) >= 4 && t.i0 + PS_TW <= Nx;
         const int ic = t.i0 + lane;
+        if (!wbulk) {
 #pragma unroll
-        for (int k = 0; k < NTAP; ++k) info[b].w[k][lane] = cv ? wcol[(size_t)k * Nx + ic] : T(0);
-        if constexpr (!PPER) {
-            info[b].gd[0][lane] = cv ? gdcol[ic] : T(0);
-            info[b].gd[1][lane] = cv ? gdcol[Nx + ic] : T(0);
+            for (int k = 0; k < NTAP; ++k) info[b].w[k][lane] = cv ? wcol[(size_t)k * Nx + ic] : T(0);
+            if constexpr (!PPER) {
+                info[b].gd[0][lane] = cv ? gdcol[ic] : T(0);
+                info[b].gd[1][lane] = cv ? gdcol[Nx + ic] : T(0);
+            }
         }
         info[b].n0[lane] = n0l;
         if (lane == 0) {
             info[b].t = t;
-            issue(b, t);
+            const uint32_t tile_bytes = t.smem_ok ? (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(S)) : 0u;
+            mbar_arrive_expect_tx(&bars[b], tile_bytes + (wbulk ? WBYTES : 0u));
+            if (t.smem_ok)
+                for (int q = 0; q < t.nb; ++q)
+                    tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap_ptr, t.i0, t.r0 + q * PS_BH, &bars[b]);
+            if (wbulk) {
+                for (int k = 0; k < NTAP; ++k) bulk_g2s(info[b].w[k], wcol + (size_t)k * Nx + t.i0, ROWB, &bars[b]);
+                if constexpr (!PPER) {
+                    bulk_g2s(info[b].gd[0], gdcol + t.i0, ROWB, &bars[b]);
+                    bulk_g2s(info[b].gd[1], gdcol + Nx + t.i0, ROWB, &bars[b]);
+                }
+            }
         }
     };
 
@@ -1139,16 +1145,16 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
         const int n0_i = info[b].n0[lane];
         const int i = t.i0 + lane;
         const bool colvalid = i < Nx;
-        T w[NTAP];
-#pragma unroll
-        for (int k = 0; k < NTAP; ++k) w[k] = info[b].w[k][lane];
-        T g = T(0), d = T(0);
-        if constexpr (!PPER) {
-            g = info[b].gd[0][lane];
-            d = info[b].gd[1][lane];
-        }
         const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
         if (ok) {
+            T w[NTAP];   // the tile's filters (landed with its rows)
+#pragma unroll
+            for (int k = 0; k < NTAP; ++k) w[k] = info[b].w[k][lane];
+            T g = T(0), d = T(0);
+            if constexpr (!PPER) {
+                g = info[b].gd[0][lane];
+                d = info[b].gd[1][lane];
+            }
             const int jb = t.j0 + grp * PS_RPT;     // first output row of this thread
             T x[PS_RPT + 9];
             if (t.smem_ok) {
