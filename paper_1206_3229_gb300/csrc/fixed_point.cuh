@@ -126,6 +126,23 @@ __device__ __forceinline__ i128 warp_sum_i128(i128 v)
     return v;
 }
 
+// Exact sum of products c_i t_i (|c| <= 2^51, |t| < 2^57) without 128-bit multiplies: each factor
+// splits at 2^26 into a high part and a low part in [0, 2^26), and the four partial products are
+// added in int64 (each below 2^57 in magnitude, so up to 64 terms fit) until fold() forms the int128
+// value.  Exact: the same integer as summing (int128) c_i * t_i.
+struct Mac26 {
+    long long hh = 0, mid = 0, ll = 0;
+    __device__ __forceinline__ void add(long long c, long long t)
+    {
+        const int ch = (int)(c >> 26), cl = (int)(c & 0x3FFFFFFll);
+        const int th = (int)(t >> 26), tl = (int)(t & 0x3FFFFFFll);
+        hh += (long long)ch * th;
+        mid += (long long)ch * tl + (long long)cl * th;
+        ll += (long long)cl * tl;
+    }
+    __device__ __forceinline__ i128 fold() const { return ((i128)hh << 52) + ((i128)mid << 26) + (i128)ll; }
+};
+
 // Exact block-wide sum (any order gives the same value); `sh` holds >= 32 entries.
 __device__ __forceinline__ i128 block_sum_i128(i128 v, i128* sh)
 {

@@ -286,6 +286,69 @@ __device__ __forceinline__ void kin_epilogue(const XShiftArgs& a, double kin, do
     }
 }
 
+// Shared memory the fused HMF epilogue needs: six int128 and one double per thread.
+constexpr size_t XX_HMF_EPI_BYTES = (size_t)XXS_THREADS * (6 * 16 + 8);
+static_assert(XXS_THREADS >= 7 * 32, "seven warps share the fused HMF epilogue");
+
+// End of the fused x-shifts, HMF: both passes' per-CTA sums (mass, cos- and sin-weighted column sums,
+// exact) and the first pass's kinetic sum in one pass over shared memory.  Every thread stores its
+// seven partials in slot-major order; then warp w (w < 6) adds slot w's partials with a lane-strided
+// loop and one warp reduction, and warp 6 the kinetic partials: seven short warp reductions instead
+// of a block-wide shuffle tree per value.  The weighted sums use split 32-bit products (Mac26).
+template <typename S, int CH>
+__device__ __forceinline__ void xx_hmf_epilogue(const XShiftArgs& a, const XShiftArgs& b,
+                                                const typename VecOf<S>::acc (&acc1)[CH][VecOf<S>::V],
+                                                const typename VecOf<S>::acc (&acc2)[CH][VecOf<S>::V], float kinf,
+                                                unsigned char* smem)
+{
+    constexpr int V = VecOf<S>::V;
+    const int Nx = a.Nx, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    i128* sm = reinterpret_cast<i128*>(smem);   // [6][XXS_THREADS]
+    double* kd = reinterpret_cast<double*>(sm + 6 * XXS_THREADS);
+    // one pass at a time (fewer live registers): slots 3q .. 3q + 2 for pass q
+    auto part = [&](const typename VecOf<S>::acc (&acc)[CH][V], int Ef, int q) {
+        long long m = 0;
+        Mac26 x, y;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = V * (tid + c * XXS_THREADS);
+            if (i < Nx) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const long long t = (long long)fx128_from_f32((float)acc[c][v], 51 - Ef);
+                    m += t;
+                    x.add(__ldg(a.cos50 + i + v), t);
+                    y.add(__ldg(a.sin50 + i + v), t);
+                }
+            }
+        }
+        sm[(3 * q + 0) * XXS_THREADS + tid] = (i128)m;
+        sm[(3 * q + 1) * XXS_THREADS + tid] = x.fold();
+        sm[(3 * q + 2) * XXS_THREADS + tid] = y.fold();
+    };
+    part(acc1, a.Ef, 0);
+    part(acc2, b.Ef, 1);
+    kd[tid] = (double)kinf;
+    __syncthreads();
+    if (wid < 6) {
+        i128 t = 0;
+#pragma unroll 4
+        for (int k = lane; k < XXS_THREADS; k += 32) t += sm[wid * XXS_THREADS + k];
+        t = warp_sum_i128(t);
+        if (lane == 0) {
+            const XShiftArgs& o = wid < 3 ? a : b;
+            static_cast<i128*>(o.ctapart)[(size_t)blockIdx.x * 3 + wid % 3] = t;
+        }
+    } else if (wid == 6) {
+        double t = 0.0;
+#pragma unroll 4
+        for (int k = lane; k < XXS_THREADS; k += 32) t += kd[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) a.kinpart[blockIdx.x] = t;
+    }
+}
+
 template <typename S, bool PERIODIC, bool KIN>
 __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
 {
@@ -711,6 +774,10 @@ __device__ __forceinline__ void xxshift_body(const XShiftArgs& a, const XShiftAr
         __syncthreads();
         return;
     }
+    if (a.ctapart && b.ctapart && a.kinpart) {
+        xx_hmf_epilogue<S, CH>(a, b, acc1, acc2, kinf, reinterpret_cast<unsigned char*>(bufs));
+        return;
+    }
     i128* scratch = reinterpret_cast<i128*>(bufs);
     colsum_epilogue<S, CH>(a, acc1, scratch);
     kin_epilogue(a, (double)kinf, red);
@@ -726,7 +793,8 @@ __global__ void __launch_bounds__(XXS_THREADS, XXS_CTAS_PER_SM) xxshift_kernel(X
 size_t xxshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes)
 {
     const size_t row = (size_t)(Nx + 2 * pad) * (size_t)elem_bytes;
-    return 256 + (size_t)stages * (row + XREC_BYTES) + 2 * row;
+    const size_t rows = (size_t)stages * (row + XREC_BYTES) + 2 * row;
+    return 256 + (rows > XX_HMF_EPI_BYTES ? rows : XX_HMF_EPI_BYTES);
 }
 
 cudaError_t launch_xxshift(int elem_bytes, bool periodic, int grid, const XShiftArgs& a, const XShiftArgs& b,
