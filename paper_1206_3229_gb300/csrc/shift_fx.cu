@@ -265,6 +265,55 @@ __device__ __forceinline__ void fx_kin_epilogue(const XShiftArgs& a, i128 kin, i
     }
 }
 
+// End of the fused x-shifts, HMF (blockDim >= 224): both passes' per-CTA sums (mass, cos- and
+// sin-weighted column sums) and the exact kinetic sum in one pass over shared memory `sm`
+// (7 blockDim int128): each thread stores its seven partials slot-major; warp w < 7 adds slot w with
+// a lane-strided loop and one warp reduction (seven short reductions instead of three block-wide
+// shuffle trees).  Weighted sums by exact split 32-bit products (Mac26).
+__device__ __forceinline__ void xxf_hmf_epilogue(const XShiftArgs& a, const XShiftArgs& b,
+                                                 const long long (&acc1)[1][XF_V], const long long (&acc2)[1][XF_V],
+                                                 i128 kin, int Ef, i128* sm)
+{
+    const int Nx = a.Nx, tid = threadIdx.x, n = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int i = XF_V * tid;
+    auto part = [&](const long long (&acc)[1][XF_V], int q) {
+        long long m = 0;
+        Mac26 x, y;
+        if (i < Nx) {
+#pragma unroll
+            for (int v = 0; v < XF_V; ++v) {
+                const long long t = acc[0][v];
+                m += t;
+                x.add(__ldg(a.cos50 + i + v), t);
+                y.add(__ldg(a.sin50 + i + v), t);
+            }
+        }
+        sm[(3 * q + 0) * n + tid] = (i128)m;
+        sm[(3 * q + 1) * n + tid] = x.fold();
+        sm[(3 * q + 2) * n + tid] = y.fold();
+    };
+    part(acc1, 0);
+    part(acc2, 1);
+    sm[6 * n + tid] = kin;
+    __syncthreads();
+    if (wid < 7) {
+        i128 t = 0;
+#pragma unroll 4
+        for (int k = lane; k < n; k += 32) t += sm[wid * n + k];
+        t = warp_sum_i128(t);
+        if (lane == 0) {
+            if (wid < 6) {
+                const XShiftArgs& o = wid < 3 ? a : b;
+                static_cast<i128*>(o.ctapart)[(size_t)blockIdx.x * 3 + wid % 3] = t;
+            } else if (a.kin128) {
+                static_cast<i128*>(a.kin128)[blockIdx.x] = t;
+            } else {
+                a.kinpart[blockIdx.x] = fx128_to_f64(t, 51 + KIN_Q - Ef);
+            }
+        }
+    }
+}
+
 // Padded rows (fused x-shifts): 8-element lines 80 bytes apart, so that pair p (elements 2p, 2p+1)
 // sits at 16-byte slot p + p / 4.  A warp's 16-byte window reads, 64 bytes apart per thread in a
 // plain row (four-way bank conflicts), then hit distinct banks.  A TMA box of 10 x H elements over
@@ -669,6 +718,10 @@ __device__ __forceinline__ void xxshift_fx_body(const CUtensorMap* tmap, const X
                 if (issued[k] > 0) mbar_wait_bounded(&bars[k], (uint32_t)((issued[k] - 1) & 1), WAIT_LIMIT_NS);
         }
         __syncthreads();
+        return;
+    }
+    if (a.ctapart && b.ctapart && blockDim.x >= 7 * 32) {
+        xxf_hmf_epilogue(a, b, acc1, acc2, kin, em.Ef, scratch);
         return;
     }
     fx_colsum_epilogue<1>(a, acc1, em.Ef, scratch);
