@@ -737,7 +737,11 @@ __global__ void __launch_bounds__(XXF_THREADS_MAX, 1) xxshift_fx_kernel(const __
 }
 
 // ============================================================================ p-shift (FX64)
-template <bool PPER>
+// STAGED: warp 0 prepares each tile in shared memory one iteration ahead (single grids, measured
+// faster there); otherwise every warp works out its tile's window and loads its filters, prefetched
+// into L1 one tile ahead (the batched form, whose slots are small grids of few tiles per CTA: the
+// staged form measured slower there).
+template <bool PPER, bool STAGED = true>
 __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -804,8 +808,17 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
     };
 
     int tile = blockIdx.x;
-    if (grp == 0 && tile < ntiles) prepare(0, tile);
-    __syncthreads();
+    if constexpr (STAGED) {
+        if (grp == 0 && tile < ntiles) prepare(0, tile);
+        __syncthreads();
+    } else {
+        if (grp == 0 && tile < ntiles) {
+            int n0l;
+            bool cv;
+            const TileWin t0 = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
+            if (lane == 0) issue(0, t0);
+        }
+    }
 
     int q = 0;
     bool failed = false;
@@ -813,20 +826,53 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
         const int b = q & 1;
         const int nt = tile + G;
         if (grp == 0 && nt < ntiles) {
-            if (lane == 0) fence_proxy_async_smem();
-            __syncwarp();
-            prepare(b ^ 1, nt);
-        }
-        const TileWin t = info[b].t;
-        const int n0_i = info[b].n0[lane];
-        const int i = t.i0 + lane;
-        const bool colvalid = i < Nx;
-        FxW w;
+            if constexpr (STAGED) {
+                if (lane == 0) fence_proxy_async_smem();
+                __syncwarp();
+                prepare(b ^ 1, nt);
+            } else {
+                int n0l;
+                bool cv;
+                const TileWin tn = tile_window<PPER, PSF_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    issue(b ^ 1, tn);
+                }
+                if (cv) {   // the next tile's filters into L1 now, so that no warp waits for L2 on them then
+                    const size_t in = (size_t)tn.i0 + lane;
 #pragma unroll
-        for (int k = 0; k < NTAP; ++k) {
-            w.Wh[k] = info[b].Wh[k][lane];
-            w.wlr[k] = make_float2(info[b].wl[k][lane], info[b].wr[k][lane]);
+                    for (int k = 0; k < NTAP; ++k) {
+                        prefetch_l1(em.Wh + (size_t)k * Nx + in);
+                        prefetch_l1(em.wl + (size_t)k * Nx + in);
+                        prefetch_l1(em.wf + (size_t)k * Nx + in);
+                    }
+                }
+            }
         }
+        TileWin t;
+        int n0_i;
+        bool colvalid;
+        FxW w;
+        if constexpr (STAGED) {
+            t = info[b].t;
+            n0_i = info[b].n0[lane];
+            colvalid = t.i0 + lane < Nx;
+#pragma unroll
+            for (int k = 0; k < NTAP; ++k) {
+                w.Wh[k] = info[b].Wh[k][lane];
+                w.wlr[k] = make_float2(info[b].wl[k][lane], info[b].wr[k][lane]);
+            }
+        } else {
+            t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
+            const size_t ic = (size_t)t.i0 + lane;
+#pragma unroll
+            for (int k = 0; k < NTAP; ++k) {
+                w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + ic] : 0;
+                w.wlr[k] = colvalid ? make_float2(em.wl[(size_t)k * Nx + ic], em.wf[(size_t)k * Nx + ic] * 9.313225746154785e-10f)
+                                    : make_float2(0.f, 0.f);
+            }
+        }
+        const int i = t.i0 + lane;
         const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
         if (ok) {
             const long long* buf = bufs + (size_t)b * BUF;
@@ -957,7 +1003,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_batch_kernel(const
     const PShiftArgs a = args[k];
     if (a.Nx <= 0) return;
     const EmulArgs em = ems[slot];
-    pshift_fx_body<PPER>(tmaps + k, a, em);
+    pshift_fx_body<PPER, false>(tmaps + k, a, em);
 }
 
 int xshift_fx_max_cols(int threads) { return XF_V * threads * XF_MAXCH; }
