@@ -1121,15 +1121,23 @@ cudaError_t gs_occupancy(int elem_bytes, bool xdir, size_t smem, int* blocks)
 }
 
 // ============================================================================ p-shift
+// Warp-specialised: PS_RG compute warps (16 output rows each) and one producer warp per CTA.  The
+// producer works out each tile's window, stages its columns' foot offsets (and, for partial column
+// tiles, filters) in the slot info[b] and issues the copies of its rows and filters into buffer b
+// (full[b]); the compute warps take the tiles in the same order and hand each buffer back through
+// empty[b].  No CTA-wide barrier per tile: a warp waits only for the data it reads.
 template <typename S, bool PPER>
 __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const PShiftArgs& a)
 {
     using T = typename VecOf<S>::T;
+    constexpr int NB = PS_NB;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + NB;
     S* bufs = reinterpret_cast<S*>(smem_raw + 128);
     constexpr int BUF = PS_RB * PS_TW;
+    static_assert(2 * NB * 8 <= 128, "barriers fit in front of the buffers");
 
     const S* __restrict__ fin = static_cast<const S*>(a.fin);
     S* __restrict__ fout = static_cast<S*>(a.fout);
@@ -1141,151 +1149,152 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
     const int ntiles = ntx * nty;
     const int G = gridDim.x;
 
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_barrier_init();
-        prefetch_tensormap(tmap_ptr);
-    }
-    __syncthreads();
-
-    // Warp 0 prepares each tile one iteration ahead: its window (copies into buffer b), its columns'
-    // foot offsets, and their filters into the slot info[b].  Filters of a tile with all 32 columns
-    // inside the grid arrive by bulk copies on the tile's barrier, so no warp issues a global load
-    // for them; the last, partial column tile loads them.
     struct __align__(16) TileInfo {
         T w[NTAP][PS_TW];
         T gd[2][PS_TW];
         int n0[PS_TW];
         TileWin t;
     };
-    __shared__ TileInfo info[2];
-    constexpr uint32_t ROWB = PS_TW * (uint32_t)sizeof(T);
-    constexpr uint32_t WBYTES = (NTAP + (PPER ? 0 : 2)) * ROWB;
-    auto prepare = [&](int b, int tl) {   // warp 0
-        int n0l;
-        bool cv;
-        const TileWin t = tile_window<PPER>(tl, ntx, a.n0, Nx, lane, n0l, cv);
-        // (BF16 storage loads them: measured faster there, its tiles being half the bytes)
-        const bool wbulk = sizeof(S) >= 4 && t.i0 + PS_TW <= Nx;
-        const int ic = t.i0 + lane;
-        if (!wbulk) {
-#pragma unroll
-            for (int k = 0; k < NTAP; ++k) info[b].w[k][lane] = cv ? wcol[(size_t)k * Nx + ic] : T(0);
-            if constexpr (!PPER) {
-                info[b].gd[0][lane] = cv ? gdcol[ic] : T(0);
-                info[b].gd[1][lane] = cv ? gdcol[Nx + ic] : T(0);
-            }
+    __shared__ TileInfo info[NB];
+
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], PS_RG);
         }
-        info[b].n0[lane] = n0l;
-        if (lane == 0) {
-            info[b].t = t;
-            const uint32_t tile_bytes = t.smem_ok ? (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(S)) : 0u;
-            mbar_arrive_expect_tx(&bars[b], tile_bytes + (wbulk ? WBYTES : 0u));
-            if (t.smem_ok)
-                for (int q = 0; q < t.nb; ++q)
-                    tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap_ptr, t.i0, t.r0 + q * PS_BH, &bars[b]);
-            if (wbulk) {
-                for (int k = 0; k < NTAP; ++k) bulk_g2s(info[b].w[k], wcol + (size_t)k * Nx + t.i0, ROWB, &bars[b]);
+        fence_barrier_init();
+        prefetch_tensormap(tmap_ptr);
+    }
+    __syncthreads();   // the last CTA-wide barrier: the roles part here
+
+    if (grp == PS_RG) {
+        // ---- producer.  Filters of a tile with all 32 columns inside the grid arrive by bulk copies
+        // on the tile's barrier; BF16 storage loads them (measured faster there, its tiles being half
+        // the bytes), as does the last, partial column tile.
+        constexpr uint32_t ROWB = PS_TW * (uint32_t)sizeof(T);
+        constexpr uint32_t WBYTES = (NTAP + (PPER ? 0 : 2)) * ROWB;
+        int k = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
+            const int b = k % NB;
+            if (k >= NB) ok = mbar_wait_bounded(&empty[b], (uint32_t)(((k / NB) - 1) & 1), WAIT_LIMIT_NS);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            int n0l;
+            bool cv;
+            const TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0l, cv);
+            const bool wbulk = sizeof(S) >= 4 && t.i0 + PS_TW <= Nx;
+            const int ic = t.i0 + lane;
+            if (!wbulk) {
+#pragma unroll
+                for (int q = 0; q < NTAP; ++q) info[b].w[q][lane] = cv ? wcol[(size_t)q * Nx + ic] : T(0);
                 if constexpr (!PPER) {
-                    bulk_g2s(info[b].gd[0], gdcol + t.i0, ROWB, &bars[b]);
-                    bulk_g2s(info[b].gd[1], gdcol + Nx + t.i0, ROWB, &bars[b]);
+                    info[b].gd[0][lane] = cv ? gdcol[ic] : T(0);
+                    info[b].gd[1][lane] = cv ? gdcol[Nx + ic] : T(0);
+                }
+            }
+            info[b].n0[lane] = n0l;
+            __syncwarp();
+            if (lane == 0) {
+                info[b].t = t;
+                fence_proxy_async_smem();   // the compute warps' reads of buffer b before its refill
+                const uint32_t tile_bytes = t.smem_ok ? (uint32_t)(t.nb * PS_BH * PS_TW * sizeof(S)) : 0u;
+                mbar_arrive_expect_tx(&full[b], tile_bytes + (wbulk ? WBYTES : 0u));   // releases info[b]
+                if (t.smem_ok)
+                    for (int q = 0; q < t.nb; ++q)
+                        tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap_ptr, t.i0, t.r0 + q * PS_BH, &full[b]);
+                if (wbulk) {
+                    for (int q = 0; q < NTAP; ++q) bulk_g2s(info[b].w[q], wcol + (size_t)q * Nx + t.i0, ROWB, &full[b]);
+                    if constexpr (!PPER) {
+                        bulk_g2s(info[b].gd[0], gdcol + t.i0, ROWB, &full[b]);
+                        bulk_g2s(info[b].gd[1], gdcol + Nx + t.i0, ROWB, &full[b]);
+                    }
                 }
             }
         }
-    };
+        if (lane == 0) {
+            if (!ok) atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+            // stay until every copy issued has landed (the CTA's shared memory must outlive them)
+            for (int j = k - 1; j >= 0 && j >= k - NB; --j)
+                mbar_wait_bounded(&full[j % NB], (uint32_t)((j / NB) & 1), WAIT_LIMIT_NS);
+        }
+        return;
+    }
 
-    int tile = blockIdx.x;
-    if (grp == 0 && tile < ntiles) prepare(0, tile);
-    __syncthreads();
-
-    int q = 0;
-    bool failed = false;
-    for (; tile < ntiles; tile += G, ++q) {
-        const int b = q & 1;
-        const int nt = tile + G;
-        if (grp == 0 && nt < ntiles) {
-            if (lane == 0) fence_proxy_async_smem();
-            __syncwarp();
-            prepare(b ^ 1, nt);
+    // ---- compute warps
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
+        const int b = k % NB;
+        if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NB) & 1), WAIT_LIMIT_NS)) {
+            if (lane == 0) atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+            break;
         }
         const TileWin t = info[b].t;
         const int n0_i = info[b].n0[lane];
         const int i = t.i0 + lane;
         const bool colvalid = i < Nx;
-        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
-        if (ok) {
-            T w[NTAP];   // the tile's filters (landed with its rows)
+        T w[NTAP];
 #pragma unroll
-            for (int k = 0; k < NTAP; ++k) w[k] = info[b].w[k][lane];
-            T g = T(0), d = T(0);
-            if constexpr (!PPER) {
-                g = info[b].gd[0][lane];
-                d = info[b].gd[1][lane];
+        for (int q = 0; q < NTAP; ++q) w[q] = info[b].w[q][lane];
+        T g = T(0), d = T(0);
+        if constexpr (!PPER) {
+            g = info[b].gd[0][lane];
+            d = info[b].gd[1][lane];
+        }
+        const int jb = t.j0 + grp * PS_RPT;     // first output row of this thread
+        T x[PS_RPT + 9];
+        if (t.smem_ok) {
+            const S* buf = bufs + (size_t)b * BUF;
+            const int base = jb + n0_i - 4 - t.r0;
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u) x[u] = to_math(buf[(base + u) * PS_TW + lane]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < PS_RPT + 9; ++u)
+                x[u] = colvalid ? to_math(gload_p<S, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np)) : T(0);
+        }
+        // the staged window and slot are read: hand buffer b back (stores below need neither)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+        // A tile whose columns and rows all lie inside the grid, with every foot cell inside
+        // too (the common case), takes the rows without per-row checks.
+        const bool interior = t.i0 + PS_TW <= Nx && t.j0 + PS_TH <= Np &&
+                              (PPER || (t.j0 + t.kmin >= 0 && t.j0 + PS_TH - 1 + t.kmax < Np - 1));
+        if (interior) {
+            S* __restrict__ op = fout + (size_t)jb * Nx + i;
+#pragma unroll
+            for (int rr = 0; rr < PS_RPT; ++rr) {
+                T acc = w[0] * x[rr];
+#pragma unroll
+                for (int q = 1; q < NTAP; ++q) acc = fma(w[q], x[rr + q], acc);
+                *op = from_math<S>(acc);
+                op += Nx;
             }
-            const int jb = t.j0 + grp * PS_RPT;     // first output row of this thread
-            T x[PS_RPT + 9];
-            if (t.smem_ok) {
-                const S* buf = bufs + (size_t)b * BUF;
-                const int base = jb + n0_i - 4 - t.r0;
+        } else {
 #pragma unroll
-                for (int u = 0; u < PS_RPT + 9; ++u) x[u] = to_math(buf[(base + u) * PS_TW + lane]);
-            } else {
+            for (int rr = 0; rr < PS_RPT; ++rr) {
+                const int j = jb + rr;
+                T acc = w[0] * x[rr];
 #pragma unroll
-                for (int u = 0; u < PS_RPT + 9; ++u)
-                    x[u] = colvalid ? to_math(gload_p<S, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np)) : T(0);
-            }
-            // A tile whose columns and rows all lie inside the grid, with every foot cell inside
-            // too (the common case), takes the rows without per-row checks.
-            const bool interior = t.i0 + PS_TW <= Nx && t.j0 + PS_TH <= Np &&
-                                  (PPER || (t.j0 + t.kmin >= 0 && t.j0 + PS_TH - 1 + t.kmax < Np - 1));
-            if (interior) {
-                S* __restrict__ op = fout + (size_t)jb * Nx + i;
-#pragma unroll
-                for (int rr = 0; rr < PS_RPT; ++rr) {
-                    T acc = w[0] * x[rr];
-#pragma unroll
-                    for (int k = 1; k < NTAP; ++k) acc = fma(w[k], x[rr + k], acc);
-                    *op = from_math<S>(acc);
-                    op += Nx;
+                for (int q = 1; q < NTAP; ++q) acc = fma(w[q], x[rr + q], acc);
+                if constexpr (!PPER) {
+                    const int kk = j + n0_i;
+                    if (kk < 0 || kk >= Np - 1) acc = edge_fix(acc, &x[rr], kk, Np, g, d);
                 }
-            } else {
-#pragma unroll
-                for (int rr = 0; rr < PS_RPT; ++rr) {
-                    const int j = jb + rr;
-                    T acc = w[0] * x[rr];
-#pragma unroll
-                    for (int k = 1; k < NTAP; ++k) acc = fma(w[k], x[rr + k], acc);
-                    if constexpr (!PPER) {
-                        const int kk = j + n0_i;
-                        if (kk < 0 || kk >= Np - 1) acc = edge_fix(acc, &x[rr], kk, Np, g, d);
-                    }
-                    if (colvalid && j < Np) fout[(size_t)j * Nx + i] = from_math<S>(acc);
-                }
+                if (colvalid && j < Np) fout[(size_t)j * Nx + i] = from_math<S>(acc);
             }
         }
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-    }
-    if (failed && tid == 0) {
-        atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
-        // the prefetch of the next tile may still be in flight
-        if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
-        mbar_wait_bounded(&bars[q & 1], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
     }
 }
 
 template <typename S, bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
+__global__ void __launch_bounds__(PS_THREADS, sizeof(S) == 8 ? 1 : PS_MINB) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
 {
     pshift_body<S, PPER>(&tmap, a);
 }
 
 // Batched form: tensor maps and arguments of each slot, per buffer parity, in global memory.
 template <typename T, bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_batch_kernel(const CUtensorMap* __restrict__ tmaps,
+__global__ void __launch_bounds__(PS_THREADS, PS_MINB) pshift_batch_kernel(const CUtensorMap* __restrict__ tmaps,
                                                                          const PShiftArgs* __restrict__ args,
                                                                          const int* __restrict__ ver)
 {
@@ -1298,14 +1307,14 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 1) pshift_batch_kernel(const CU
 
 size_t pshift_smem_bytes(int elem_bytes)
 {
-    return 256 + 2 * (size_t)PS_RB * PS_TW * (size_t)elem_bytes;
+    return 256 + (size_t)PS_NB * PS_RB * PS_TW * (size_t)elem_bytes;
 }
 
 template <typename S, bool PPER>
 static cudaError_t launch_p(int grid, const CUtensorMap* tmap, const PShiftArgs& a, cudaStream_t st)
 {
     const size_t smem = pshift_smem_bytes((int)sizeof(S));
-    pshift_kernel<S, PPER><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a);
+    pshift_kernel<S, PPER><<<grid, PS_THREADS, smem, st>>>(*tmap, a);
     return cudaGetLastError();
 }
 
@@ -1335,7 +1344,7 @@ cudaError_t launch_pshift_batch(int slots, int ctas_per_slot, const CUtensorMap*
                                 const int* ver, cudaStream_t st)
 {
     const dim3 grid(ctas_per_slot, slots);
-    pshift_batch_kernel<float, false><<<grid, PS_TW * PS_RG, pshift_smem_bytes(4), st>>>(tmaps, args, ver);
+    pshift_batch_kernel<float, false><<<grid, PS_THREADS, pshift_smem_bytes(4), st>>>(tmaps, args, ver);
     return cudaGetLastError();
 }
 
@@ -1405,10 +1414,10 @@ cudaError_t pshift_occupancy(int elem_bytes, int* blocks)
 {
     const size_t smem = pshift_smem_bytes(elem_bytes);
     if (elem_bytes == 8)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<double, false>, PS_TW * PS_RG, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<double, false>, PS_THREADS, smem);
     if (elem_bytes == 2)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<bf16, false>, PS_TW * PS_RG, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<float, false>, PS_TW * PS_RG, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<bf16, false>, PS_THREADS, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_kernel<float, false>, PS_THREADS, smem);
 }
 
 }  // namespace vl

@@ -364,6 +364,10 @@ constexpr int PS_RPT = 16;       // output rows per thread
 constexpr int PS_TH = PS_RG * PS_RPT;  // output rows per tile
 constexpr int PS_BH = 32;        // rows per TMA box
 constexpr int PS_RB = 256;       // staged rows per buffer
+// FP32-class p-shift: PS_RG compute warps and one producer warp per CTA, PS_NB staged tiles in flight
+constexpr int PS_THREADS = PS_TW * (PS_RG + 1);
+constexpr int PS_NB = 2;
+constexpr int PS_MINB = 3;       // CTAs per SM the register budget is set for, 4-byte storage (faster than 2)
 size_t pshift_smem_bytes(int elem_bytes);
 cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUtensorMap* tmap,
                           const PShiftArgs& a, cudaStream_t st);
