@@ -39,16 +39,16 @@ struct TileWin {
     bool smem_ok;
 };
 
-// Window of input rows a tile needs: [j0 + kmin - 4, j0 + TH - 1 + kmax + 5].  Called by whole
+// Window of input rows a tile of TH rows needs: [j0 + kmin - 4, j0 + TH - 1 + kmax + 5].  Called by whole
 // warps (all lanes hold one column); identical in every warp.
-template <bool PPER, int RB = PS_RB>
+template <bool PPER, int RB = PS_RB, int TH = PS_TH>
 __device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __restrict__ n0, int Nx, int lane,
                                                int& n0_lane, bool& colvalid)
 {
     TileWin t;
     const int tx = tile % ntx, ty = tile / ntx;
     t.i0 = tx * PS_TW;
-    t.j0 = ty * PS_TH;
+    t.j0 = ty * TH;
     const int i = t.i0 + lane;
     colvalid = i < Nx;
     n0_lane = colvalid ? n0[i] : 0;
@@ -63,7 +63,7 @@ __device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __r
     t.kmin = kmin;
     t.kmax = kmax;
     t.r0 = t.j0 + kmin - 4;
-    const long long R = (long long)PS_TH + 9 + ((long long)kmax - (long long)kmin);
+    const long long R = (long long)TH + 9 + ((long long)kmax - (long long)kmin);
     t.smem_ok = !PPER && R <= RB;
     t.nb = t.smem_ok ? (int)((R + PS_BH - 1) / PS_BH) : 0;
     return t;

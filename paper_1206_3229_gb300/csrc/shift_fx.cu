@@ -22,6 +22,12 @@ constexpr int XF_V = 8;       // consecutive outputs per thread and chunk
 constexpr int XF_W = 18;      // window elements: V + 9 + alignment slack (even)
 constexpr int XF_MAXCH = 2;   // chunks per row per thread (Nx <= 8 * 256 * 2 = 4096)
 constexpr int PSF_RB = 192;   // staged rows per p-shift buffer (two CTAs per SM)
+// Single-grid p-shift: PSF_RG compute warps and one producer warp (16 warps per SM at two CTAs, so
+// that the compute warps keep 128 registers), tiles of PS_TW columns x PSF_TH rows, PSF_NB in flight
+constexpr int PSF_RG = 7;
+constexpr int PSF_TH = PSF_RG * PS_RPT;
+constexpr int PSF_THREADS = PS_TW * (PSF_RG + 1);
+constexpr int PSF_NB = 2;
 
 struct FxW {
     int Wh[NTAP];
@@ -741,7 +747,254 @@ __global__ void __launch_bounds__(XXF_THREADS_MAX, 1) xxshift_fx_kernel(const __
 // faster there); otherwise every warp works out its tile's window and loads its filters, prefetched
 // into L1 one tile ahead (the batched form, whose slots are small grids of few tiles per CTA: the
 // staged form measured slower there).
-template <bool PPER, bool STAGED = true>
+// Input-stationary accumulation for the p-shift: elements u and u + 1 of a column's window (X0, X1;
+// X1 absent when !second) fed to the PS_RPT outputs they touch.  Their two products for an output
+// enter its int64 sum in one three-input add (two IMAD.WIDE + IADD3 + IADD3.X) instead of two 64-bit
+// multiply-adds (three instructions each on this GPU).  Shared by the single-grid and batched
+// p-shifts, which therefore give the same bits.
+__device__ __forceinline__ void psfx_feed2(int u, long long X0, long long X1, bool second, const FxW& w,
+                                           long long (&M)[PS_RPT], float2 (&S)[PS_RPT])
+{
+    int kx0, kx1;
+    float kf0, rf0, kf1, rf1;
+    fx_split(X0, kx0, kf0, rf0);
+    fx_split(X1, kx1, kf1, rf1);
+    const float2 xa = make_float2(kf0, rf0), xb = make_float2(kf1, rf1);
+#pragma unroll
+    for (int rw = 0; rw < PS_RPT; ++rw) {
+        const int t0 = u - rw, t1 = t0 + 1;
+        const bool v0 = t0 >= 0 && t0 < NTAP, v1 = second && t1 >= 0 && t1 < NTAP;
+        if (v0 && v1) M[rw] = M[rw] + mul_wide(w.Wh[t0], kx0) + mul_wide(w.Wh[t1], kx1);
+        else if (v0) M[rw] += mul_wide(w.Wh[t0], kx0);
+        else if (v1) M[rw] += mul_wide(w.Wh[t1], kx1);
+        if (v0) {
+            S[rw].x = fmaf(w.wlr[t0].x, xa.x, S[rw].x);
+            S[rw].y = fmaf(w.wlr[t0].y, xa.y, S[rw].y);
+        }
+        if (v1) {
+            S[rw].x = fmaf(w.wlr[t1].x, xb.x, S[rw].x);
+            S[rw].y = fmaf(w.wlr[t1].y, xb.y, S[rw].y);
+        }
+    }
+}
+
+// The PS_RPT outputs of one column (rows jb ..) from the window: staged (buf, window element u at
+// buf[(base + u) * PS_TW + lane]) or, for a tile whose window does not fit, loaded from f.
+template <bool PPER>
+__device__ __forceinline__ void psfx_accumulate(const TileWin& t, const long long* buf, int base, const long long* fin,
+                                                int jb, int n0_i, int i, bool colvalid, int Nx, int Np, const FxW& w,
+                                                long long (&M)[PS_RPT], float2 (&S)[PS_RPT])
+{
+#pragma unroll
+    for (int rw = 0; rw < PS_RPT; ++rw) {
+        M[rw] = EMUL_M0;
+        S[rw] = make_float2(0.f, 0.f);
+    }
+    constexpr int NU = PS_RPT + 9;
+    const int lane = threadIdx.x & 31;
+    if (t.smem_ok) {
+#pragma unroll
+        for (int u = 0; u < NU; u += 2)
+            psfx_feed2(u, buf[(base + u) * PS_TW + lane], u + 1 < NU ? buf[(base + u + 1) * PS_TW + lane] : 0ll,
+                       u + 1 < NU, w, M, S);
+    } else {
+#pragma unroll
+        for (int u = 0; u < NU; u += 2) {
+            const long long X0 = colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll;
+            const long long X1 = (colvalid && u + 1 < NU) ? gload_p<long long, PPER>(fin, jb + n0_i - 3 + u, i, Nx, Np) : 0ll;
+            psfx_feed2(u, X0, X1, u + 1 < NU, w, M, S);
+        }
+    }
+}
+
+// A tile wholly inside the grid, every foot cell inside too (the common case): its rows are stored
+// without per-row edge or bounds checks.
+template <bool PPER, int TH = PS_TH>
+__device__ __forceinline__ bool psfx_interior(const TileWin& t, int Nx, int Np)
+{
+    return t.i0 + PS_TW <= Nx && t.j0 + TH <= Np &&
+           (PPER || (t.j0 + t.kmin >= 0 && t.j0 + TH - 1 + t.kmax < Np - 1));
+}
+
+// Store the column's outputs.  Interior tiles: plain stores.  Otherwise rows past the grid are
+// skipped and outputs whose foot cell touches or leaves a zero-outside column end are recomputed
+// from the window (buf or f, as in psfx_accumulate) with the column's edge filters.
+template <bool PPER>
+__device__ __forceinline__ void psfx_store(bool interior, const TileWin& t, const long long* buf, int base,
+                                           const long long* fin, long long* fout, int jb, int n0_i, int i,
+                                           bool colvalid, int Nx, int Np, const EmulArgs& em,
+                                           const long long (&M)[PS_RPT], const float2 (&S)[PS_RPT], uint32_t& rng)
+{
+    if (interior) {
+        long long* __restrict__ op = fout + (size_t)jb * Nx + i;
+#pragma unroll
+        for (int rw = 0; rw < PS_RPT; ++rw) {
+            *op = fx_store(emul_finish(M[rw], S[rw].x + S[rw].y), rng);
+            op += Nx;
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    bool any_edge = false;
+#pragma unroll
+    for (int rw = 0; rw < PS_RPT; ++rw) {
+        const int j = jb + rw;
+        const long long out = fx_store(emul_finish(M[rw], S[rw].x + S[rw].y), rng);
+        bool edge = false;
+        if constexpr (!PPER) {
+            const int kk = j + n0_i;
+            edge = kk < 0 || kk >= Np - 1;
+        }
+        any_edge |= edge;
+        if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
+    }
+    if constexpr (!PPER) {
+        if (any_edge && colvalid) {
+            const double unit = ldexp(1.0, em.Ef - FX_FRAC);
+            const double g = em.gd[i], d = em.gd[Nx + i];
+            for (int rw = 0; rw < PS_RPT; ++rw) {
+                const int j = jb + rw, kk = j + n0_i;
+                if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
+                long long X[NTAP];
+                for (int u = 0; u < NTAP; ++u)
+                    X[u] = t.smem_ok ? buf[(base + rw + u) * PS_TW + lane]
+                                     : gload_p<long long, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
+                if (em.Whe) {   // fixed point, with the column's edge filters
+                    const FxOne o = fx_edge_one(X, em, i, Nx, kk, Np);
+                    rng |= o.rng;
+                    fout[(size_t)j * Nx + i] = o.v;
+                } else {
+                    fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
+                }
+            }
+        }
+    }
+}
+
+// Single-grid p-shift, warp-specialised: warp PSF_RG (the producer) prepares each tile of this CTA
+// into one of PSF_NB slots -- its window of input rows by 2-D TMA boxes (zero fill), its columns'
+// foot offsets and split filters -- and the PSF_RG compute warps take the slots in turn on full /
+// empty mbarriers, with no CTA-wide barrier per tile.  Thread (warp g, lane c) computes the PS_RPT
+// outputs of column c in rows j0 + g PS_RPT .., input-stationary over the PS_RPT + 9 staged rows.
+template <bool PPER>
+__device__ __forceinline__ void pshift_fx_ws_body(const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em)
+{
+    constexpr int NB = PSF_NB;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char* smem_raw = align128(smem_dyn);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + NB;
+    long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
+    constexpr int BUF = PSF_RB * PS_TW;
+    static_assert(2 * NB * 8 <= 128, "barriers fit in front of the buffers");
+
+    const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
+    long long* __restrict__ fout = static_cast<long long*>(a.fout);
+    const int Nx = a.Nx, Np = a.Np;
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+    const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PSF_TH - 1) / PSF_TH;
+    const int ntiles = ntx * nty;
+    const int G = gridDim.x;
+
+    struct TileInfo {
+        int n0[PS_TW];
+        int Wh[NTAP][PS_TW];
+        float wl[NTAP][PS_TW], wr[NTAP][PS_TW];
+        TileWin t;
+    };
+    __shared__ TileInfo info[NB];
+
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], PSF_RG);
+        }
+        fence_barrier_init();
+        prefetch_tensormap(tmap);
+    }
+    __syncthreads();   // the last CTA-wide barrier: the roles part here
+
+    if (grp == PSF_RG) {
+        // ---- producer
+        int k = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
+            const int b = k % NB;
+            if (k >= NB) ok = mbar_wait_bounded(&empty[b], (uint32_t)(((k / NB) - 1) & 1), WAIT_LIMIT_NS);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            int n0l;
+            bool cv;
+            const TileWin t = tile_window<PPER, PSF_RB, PSF_TH>(tile, ntx, em.n0, Nx, lane, n0l, cv);
+            const size_t ic = (size_t)t.i0 + lane;
+#pragma unroll
+            for (int q = 0; q < NTAP; ++q) {
+                info[b].Wh[q][lane] = cv ? em.Wh[(size_t)q * Nx + ic] : 0;
+                info[b].wl[q][lane] = cv ? em.wl[(size_t)q * Nx + ic] : 0.f;
+                info[b].wr[q][lane] = cv ? em.wf[(size_t)q * Nx + ic] * 9.313225746154785e-10f : 0.f;   // * 2^-30
+            }
+            info[b].n0[lane] = n0l;
+            __syncwarp();
+            if (lane == 0) {
+                info[b].t = t;
+                fence_proxy_async_smem();   // the compute warps' reads of buffer b before its refill
+                mbar_arrive_expect_tx(&full[b], t.smem_ok ? (uint32_t)(t.nb * PS_BH * PS_TW * 8) : 0u);   // releases info[b]
+                if (t.smem_ok)
+                    for (int q = 0; q < t.nb; ++q)
+                        tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap, t.i0, t.r0 + q * PS_BH, &full[b]);
+            }
+        }
+        if (lane == 0) {
+            if (!ok) atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+            // stay until every copy issued has landed (the CTA's shared memory must outlive them)
+            for (int j = k - 1; j >= 0 && j >= k - NB; --j)
+                mbar_wait_bounded(&full[j % NB], (uint32_t)((j / NB) & 1), WAIT_LIMIT_NS);
+        }
+        return;
+    }
+
+    // ---- compute warps
+    uint32_t rng = 0;   // OR of (high word + 2^29) of every stored result
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
+        const int b = k % NB;
+        if (!mbar_wait_bounded(&full[b], (uint32_t)((k / NB) & 1), WAIT_LIMIT_NS)) {
+            if (lane == 0) atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
+            break;
+        }
+        const TileWin t = info[b].t;
+        const int n0_i = info[b].n0[lane];
+        FxW w;
+#pragma unroll
+        for (int q = 0; q < NTAP; ++q) {
+            w.Wh[q] = info[b].Wh[q][lane];
+            w.wlr[q] = make_float2(info[b].wl[q][lane], info[b].wr[q][lane]);
+        }
+        const int i = t.i0 + lane;
+        const bool colvalid = i < Nx;
+        const int jb = t.j0 + grp * PS_RPT;   // first output row of this thread
+        const int base = jb + n0_i - 4 - t.r0;
+        const long long* buf = bufs + (size_t)b * BUF;
+        long long M[PS_RPT];
+        float2 S[PS_RPT];
+        psfx_accumulate<PPER>(t, buf, base, fin, jb, n0_i, i, colvalid, Nx, Np, w, M, S);
+        const bool interior = psfx_interior<PPER, PSF_TH>(t, Nx, Np);
+        if (interior) {   // the window and slot are read: hand buffer b back before the stores
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[b]);
+        }
+        psfx_store<PPER>(interior, t, buf, base, fin, fout, jb, n0_i, i, colvalid, Nx, Np, em, M, S, rng);
+        if (!interior) {   // edge outputs read the window again
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[b]);
+        }
+    }
+    if (rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+}
+
+// Batched p-shift: every warp works out each tile's window and its column's offset and filters
+// itself (the filters of the next tile prefetched into L1 by warp 0); one CTA-wide barrier per tile
+// releases the buffer.  On the batch's small grids this measured faster than the staged form.
+template <bool PPER>
 __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -757,8 +1010,6 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
     const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PS_TH - 1) / PS_TH;
     const int ntiles = ntx * nty;
     const int G = gridDim.x;
-    const double unit = ldexp(1.0, em.Ef - FX_FRAC);
-    bool bad = false;
     uint32_t rng = 0;   // OR of (high word + 2^29) of every stored result
 
     if (tid == 0) {
@@ -779,45 +1030,12 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
         }
     };
 
-    // Warp 0 prepares each tile one iteration ahead: its window (and the copies into buffer b), and
-    // its columns' foot offsets and split filters into the slot info[b], so that no warp waits on
-    // those global loads when the tile starts.
-    struct TileInfo {
-        TileWin t;
-        int n0[PS_TW];
-        int Wh[NTAP][PS_TW];
-        float wl[NTAP][PS_TW], wr[NTAP][PS_TW];
-    };
-    __shared__ TileInfo info[2];
-    auto prepare = [&](int b, int tl) {   // warp 0
+    int tile = blockIdx.x;
+    if (grp == 0 && tile < ntiles) {
         int n0l;
         bool cv;
-        const TileWin t = tile_window<PPER, PSF_RB>(tl, ntx, em.n0, Nx, lane, n0l, cv);
-        const size_t ic = (size_t)t.i0 + lane;
-#pragma unroll
-        for (int k = 0; k < NTAP; ++k) {
-            info[b].Wh[k][lane] = cv ? em.Wh[(size_t)k * Nx + ic] : 0;
-            info[b].wl[k][lane] = cv ? em.wl[(size_t)k * Nx + ic] : 0.f;
-            info[b].wr[k][lane] = cv ? em.wf[(size_t)k * Nx + ic] * 9.313225746154785e-10f : 0.f;
-        }
-        info[b].n0[lane] = n0l;
-        if (lane == 0) {
-            info[b].t = t;
-            issue(b, t);
-        }
-    };
-
-    int tile = blockIdx.x;
-    if constexpr (STAGED) {
-        if (grp == 0 && tile < ntiles) prepare(0, tile);
-        __syncthreads();
-    } else {
-        if (grp == 0 && tile < ntiles) {
-            int n0l;
-            bool cv;
-            const TileWin t0 = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
-            if (lane == 0) issue(0, t0);
-        }
+        const TileWin t0 = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
+        if (lane == 0) issue(0, t0);
     }
 
     int q = 0;
@@ -826,51 +1044,33 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
         const int b = q & 1;
         const int nt = tile + G;
         if (grp == 0 && nt < ntiles) {
-            if constexpr (STAGED) {
-                if (lane == 0) fence_proxy_async_smem();
-                __syncwarp();
-                prepare(b ^ 1, nt);
-            } else {
-                int n0l;
-                bool cv;
-                const TileWin tn = tile_window<PPER, PSF_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
-                if (lane == 0) {
-                    fence_proxy_async_smem();
-                    issue(b ^ 1, tn);
-                }
-                if (cv) {   // the next tile's filters into L1 now, so that no warp waits for L2 on them then
-                    const size_t in = (size_t)tn.i0 + lane;
+            int n0l;
+            bool cv;
+            const TileWin tn = tile_window<PPER, PSF_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(b ^ 1, tn);
+            }
+            if (cv) {   // the next tile's filters into L1 now, so that no warp waits for L2 on them then
+                const size_t in = (size_t)tn.i0 + lane;
 #pragma unroll
-                    for (int k = 0; k < NTAP; ++k) {
-                        prefetch_l1(em.Wh + (size_t)k * Nx + in);
-                        prefetch_l1(em.wl + (size_t)k * Nx + in);
-                        prefetch_l1(em.wf + (size_t)k * Nx + in);
-                    }
+                for (int k = 0; k < NTAP; ++k) {
+                    prefetch_l1(em.Wh + (size_t)k * Nx + in);
+                    prefetch_l1(em.wl + (size_t)k * Nx + in);
+                    prefetch_l1(em.wf + (size_t)k * Nx + in);
                 }
             }
         }
-        TileWin t;
         int n0_i;
         bool colvalid;
+        const TileWin t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
         FxW w;
-        if constexpr (STAGED) {
-            t = info[b].t;
-            n0_i = info[b].n0[lane];
-            colvalid = t.i0 + lane < Nx;
+        const size_t ic = (size_t)t.i0 + lane;
 #pragma unroll
-            for (int k = 0; k < NTAP; ++k) {
-                w.Wh[k] = info[b].Wh[k][lane];
-                w.wlr[k] = make_float2(info[b].wl[k][lane], info[b].wr[k][lane]);
-            }
-        } else {
-            t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
-            const size_t ic = (size_t)t.i0 + lane;
-#pragma unroll
-            for (int k = 0; k < NTAP; ++k) {
-                w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + ic] : 0;
-                w.wlr[k] = colvalid ? make_float2(em.wl[(size_t)k * Nx + ic], em.wf[(size_t)k * Nx + ic] * 9.313225746154785e-10f)
-                                    : make_float2(0.f, 0.f);
-            }
+        for (int k = 0; k < NTAP; ++k) {
+            w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + ic] : 0;
+            w.wlr[k] = colvalid ? make_float2(em.wl[(size_t)k * Nx + ic], em.wf[(size_t)k * Nx + ic] * 9.313225746154785e-10f)
+                                : make_float2(0.f, 0.f);
         }
         const int i = t.i0 + lane;
         const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
@@ -879,104 +1079,17 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
             const int jb = t.j0 + grp * PS_RPT;
             const int base = jb + n0_i - 4 - t.r0;
             long long M[PS_RPT];
-            float2 Sacc[PS_RPT];
-#pragma unroll
-            for (int rw = 0; rw < PS_RPT; ++rw) {
-                M[rw] = EMUL_M0;
-                Sacc[rw] = make_float2(0.f, 0.f);
-            }
-            // Elements u and u+1 together: their two products for an output enter its int64 sum in
-            // one three-input add (two IMAD.WIDE + IADD3 + IADD3.X) instead of two 64-bit
-            // multiply-adds (three instructions each on this GPU).
-            auto feed2 = [&](int u, long long X0, long long X1, bool second) {
-                int kx0, kx1;
-                float kf0, rf0, kf1, rf1;
-                fx_split(X0, kx0, kf0, rf0);
-                fx_split(X1, kx1, kf1, rf1);
-                const float2 xa = make_float2(kf0, rf0), xb = make_float2(kf1, rf1);
-#pragma unroll
-                for (int rw = 0; rw < PS_RPT; ++rw) {
-                    const int t0 = u - rw, t1 = t0 + 1;
-                    const bool v0 = t0 >= 0 && t0 < NTAP, v1 = second && t1 >= 0 && t1 < NTAP;
-                    if (v0 && v1) M[rw] = M[rw] + mul_wide(w.Wh[t0], kx0) + mul_wide(w.Wh[t1], kx1);
-                    else if (v0) M[rw] += mul_wide(w.Wh[t0], kx0);
-                    else if (v1) M[rw] += mul_wide(w.Wh[t1], kx1);
-                    if (v0) {
-                        Sacc[rw].x = fmaf(w.wlr[t0].x, xa.x, Sacc[rw].x);
-                        Sacc[rw].y = fmaf(w.wlr[t0].y, xa.y, Sacc[rw].y);
-                    }
-                    if (v1) {
-                        Sacc[rw].x = fmaf(w.wlr[t1].x, xb.x, Sacc[rw].x);
-                        Sacc[rw].y = fmaf(w.wlr[t1].y, xb.y, Sacc[rw].y);
-                    }
-                }
-            };
-            constexpr int NU = PS_RPT + 9;
-            if (t.smem_ok) {
-#pragma unroll
-                for (int u = 0; u < NU; u += 2)
-                    feed2(u, buf[(base + u) * PS_TW + lane], u + 1 < NU ? buf[(base + u + 1) * PS_TW + lane] : 0ll, u + 1 < NU);
-            } else {
-#pragma unroll
-                for (int u = 0; u < NU; u += 2) {
-                    const long long X0 = colvalid ? gload_p<long long, PPER>(fin, jb + n0_i - 4 + u, i, Nx, Np) : 0ll;
-                    const long long X1 = (colvalid && u + 1 < NU) ? gload_p<long long, PPER>(fin, jb + n0_i - 3 + u, i, Nx, Np) : 0ll;
-                    feed2(u, X0, X1, u + 1 < NU);
-                }
-            }
-            // a tile wholly inside the grid, every foot cell inside too (the common case): no
-            // per-row edge or bounds checks
-            const bool interior = t.i0 + PS_TW <= Nx && t.j0 + PS_TH <= Np &&
-                                  (PPER || (t.j0 + t.kmin >= 0 && t.j0 + PS_TH - 1 + t.kmax < Np - 1));
-            if (interior) {
-                long long* __restrict__ op = fout + (size_t)jb * Nx + i;
-#pragma unroll
-                for (int rw = 0; rw < PS_RPT; ++rw) {
-                    *op = fx_store(emul_finish(M[rw], Sacc[rw].x + Sacc[rw].y), rng);
-                    op += Nx;
-                }
-            } else {
-                bool any_edge = false;
-#pragma unroll
-                for (int rw = 0; rw < PS_RPT; ++rw) {
-                    const int j = jb + rw;
-                    const long long out = fx_store(emul_finish(M[rw], Sacc[rw].x + Sacc[rw].y), rng);
-                    bool edge = false;
-                    if constexpr (!PPER) {
-                        const int kk = j + n0_i;
-                        edge = kk < 0 || kk >= Np - 1;
-                    }
-                    any_edge |= edge;
-                    if (colvalid && j < Np && !edge) fout[(size_t)j * Nx + i] = out;
-                }
-                if constexpr (!PPER) {
-                    if (any_edge && colvalid) {
-                        const double g = em.gd[i], d = em.gd[Nx + i];
-                        for (int rw = 0; rw < PS_RPT; ++rw) {
-                            const int j = jb + rw, kk = j + n0_i;
-                            if (j >= Np || !(kk < 0 || kk >= Np - 1)) continue;
-                            long long X[NTAP];
-                            for (int u = 0; u < NTAP; ++u)
-                                X[u] = t.smem_ok ? buf[(base + rw + u) * PS_TW + lane]
-                                                 : gload_p<long long, PPER>(fin, j + n0_i - 4 + u, i, Nx, Np);
-                            if (em.Whe) {   // fixed point, with the column's edge filters
-                                const FxOne o = fx_edge_one(X, em, i, Nx, kk, Np);
-                                rng |= o.rng;
-                                fout[(size_t)j * Nx + i] = o.v;
-                            } else {
-                                fout[(size_t)j * Nx + i] = fx_edge(X, em.w64 + i, Nx, kk, Np, g, d, unit, em.Ef);
-                            }
-                        }
-                    }
-                }
-            }
+            float2 S[PS_RPT];
+            psfx_accumulate<PPER>(t, buf, base, fin, jb, n0_i, i, colvalid, Nx, Np, w, M, S);
+            psfx_store<PPER>(psfx_interior<PPER>(t, Nx, Np), t, buf, base, fin, fout, jb, n0_i, i, colvalid, Nx, Np, em,
+                             M, S, rng);
         }
         if (__syncthreads_or(!ok)) {   // also: every thread done with buffer b before it is refilled
             failed = true;
             break;
         }
     }
-    if (bad || rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
+    if (rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
     if (failed && tid == 0) {
         atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
         if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
@@ -985,10 +1098,10 @@ __device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PS
 }
 
 template <bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(PSF_THREADS, 2) pshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                      PShiftArgs a, EmulArgs em)
 {
-    pshift_fx_body<PPER>(&tmap, a, em);
+    pshift_fx_ws_body<PPER>(&tmap, a, em);
 }
 
 // Batched form: the slot's tensor map sits in global memory next to its arguments.
@@ -1003,10 +1116,12 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_batch_kernel(const
     const PShiftArgs a = args[k];
     if (a.Nx <= 0) return;
     const EmulArgs em = ems[slot];
-    pshift_fx_body<PPER, false>(tmaps + k, a, em);
+    pshift_fx_body<PPER>(tmaps + k, a, em);
 }
 
 int xshift_fx_max_cols(int threads) { return XF_V * threads * XF_MAXCH; }
+
+int pshift_fx_tile_rows() { return PSF_TH; }
 
 size_t pshift_fx_smem_bytes() { return 256 + 2 * (size_t)PSF_RB * PS_TW * 8; }
 
@@ -1057,8 +1172,8 @@ cudaError_t launch_pshift_fx(bool p_periodic, int grid, const CUtensorMap* tmap,
                              const EmulArgs& em, cudaStream_t st)
 {
     const size_t smem = pshift_fx_smem_bytes();
-    if (p_periodic) pshift_fx_kernel<true><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
-    else pshift_fx_kernel<false><<<grid, PS_TW * PS_RG, smem, st>>>(*tmap, a, em);
+    if (p_periodic) pshift_fx_kernel<true><<<grid, PSF_THREADS, smem, st>>>(*tmap, a, em);
+    else pshift_fx_kernel<false><<<grid, PSF_THREADS, smem, st>>>(*tmap, a, em);
     return cudaGetLastError();
 }
 
@@ -1114,7 +1229,7 @@ cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks)
 
 cudaError_t pshift_fx_occupancy(int* blocks)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_fx_kernel<false>, PS_TW * PS_RG,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pshift_fx_kernel<false>, PSF_THREADS,
                                                          pshift_fx_smem_bytes());
 }
 

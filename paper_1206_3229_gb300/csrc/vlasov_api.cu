@@ -1020,7 +1020,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     else if (s->emul) CTRY(pshift_e_occupancy(&pocc));
     else CTRY(pshift_occupancy(esz, &pocc));
     pocc = std::max(pocc, 1);
-    const int ptiles = ((Nx + PS_TW - 1) / PS_TW) * ((Np + PS_TH - 1) / PS_TH);
+    const int pth = s->fx ? pshift_fx_tile_rows() : PS_TH;
+    const int ptiles = ((Nx + PS_TW - 1) / PS_TW) * ((Np + pth - 1) / pth);
     s->pgrid = std::min(ptiles, s->nsm * pocc);
     s->crgrid = (Nx + 31) / 32;
 

@@ -400,6 +400,7 @@ cudaError_t set_kernel_attributes_fx(int max_smem);
 size_t pshift_fx_smem_bytes();
 cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks);
 cudaError_t pshift_fx_occupancy(int* blocks);
+int pshift_fx_tile_rows();   // output rows per tile of the single-grid FX64 p-shift
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                              cudaStream_t st);
 // Global-spline sweeps (IEEE FP64 or FP32 storage and arithmetic).
