@@ -77,8 +77,9 @@ typedef struct {
 } vlasov_moments_t;
 
 /* Create a simulation on the current CUDA device.
-   Nx, Np: multiples of 8, 16 <= N; Nx <= 4096 for F64 and <= 8192 for F32 (x rows are staged
-   whole in shared memory).
+   Nx, Np: multiples of 8, 16 <= N; Nx <= 8192 (x rows are staged whole in shared memory; 8-byte
+   rows longer than 4096 cells take x-shift thread blocks of 512 threads, and the fused x-shifts
+   then stay off).
    dt > 0.  domain: xmin < xmax, pmin < pmax; eps > 0 for the ring model.
    On success *out owns ~2*Nx*Np*sizeof(f) + O(Nx*#SM) bytes of device memory.
    Errors: VLASOV_EINVAL, VLASOV_ENOMEM, VLASOV_ECUDA. */

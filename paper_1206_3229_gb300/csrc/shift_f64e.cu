@@ -32,6 +32,7 @@ struct EmulW {
 
 constexpr int XE_V = 4;      // consecutive outputs per thread and chunk
 constexpr int PSE_RB = 192;  // staged rows per buffer of the emulated p-shift (two CTAs per SM)
+static_assert(PSE_RB % PS_BH == 0, "a staged window is whole TMA boxes: the slot must hold nb * PS_BH rows");
 constexpr int XE_W = 14;     // window elements: V + 9 + alignment slack (even)
 constexpr int XE_MAXCH = 4;  // chunks per row per thread (Nx <= 4 * 4 * 256 = 4096)
 
@@ -82,7 +83,7 @@ __device__ __forceinline__ double emul_edge(double out, const double* x, int k, 
 
 // ============================================================================ x-shift (emulated FP64)
 template <bool PERIODIC, bool KIN>
-__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_e_kernel(XShiftArgs a, EmulArgs em)
+__global__ void __launch_bounds__(XS_THREADS_MAX, 1) xshift_e_kernel(XShiftArgs a, EmulArgs em)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char* smem_raw = align128(smem_dyn);
@@ -538,10 +539,10 @@ int xshift_e_max_cols(int threads) { return XE_V * threads * XE_MAXCH; }
 
 size_t pshift_e_smem_bytes() { return 256 + 2 * (size_t)PSE_RB * PS_TW * 8; }
 
-cudaError_t xshift_e_occupancy(bool periodic, size_t smem, int* blocks)
+cudaError_t xshift_e_occupancy(bool periodic, int threads, size_t smem, int* blocks)
 {
-    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_e_kernel<true, true>, XS_THREADS_MIN, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_e_kernel<false, true>, XS_THREADS_MIN, smem);
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_e_kernel<true, true>, threads, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_e_kernel<false, true>, threads, smem);
 }
 
 cudaError_t pshift_e_occupancy(int* blocks)

@@ -22,6 +22,7 @@ constexpr int XF_V = 8;       // consecutive outputs per thread and chunk
 constexpr int XF_W = 18;      // window elements: V + 9 + alignment slack (even)
 constexpr int XF_MAXCH = 2;   // chunks per row per thread (Nx <= 8 * 256 * 2 = 4096)
 constexpr int PSF_RB = 192;   // staged rows per p-shift buffer (two CTAs per SM)
+static_assert(PSF_RB % PS_BH == 0, "a staged window is whole TMA boxes: the slot must hold nb * PS_BH rows");
 // Single-grid p-shift: PSF_RG compute warps and one producer warp (16 warps per SM at two CTAs, so
 // that the compute warps keep 128 registers), tiles of PS_TW columns x PSF_TH rows, PSF_NB in flight
 constexpr int PSF_RG = 7;
@@ -507,7 +508,7 @@ __device__ __forceinline__ void xshift_fx_body(const XShiftArgs& a, const EmulAr
 }
 
 template <bool PERIODIC, bool KIN>
-__global__ void __launch_bounds__(XS_THREADS_MIN, 2) xshift_fx_kernel(XShiftArgs a, EmulArgs em)
+__global__ void __launch_bounds__(XS_THREADS_MAX, 1) xshift_fx_kernel(XShiftArgs a, EmulArgs em)
 {
     xshift_fx_body<PERIODIC, KIN>(a, em);
 }
@@ -920,17 +921,27 @@ __device__ __forceinline__ void pshift_fx_ws_body(const CUtensorMap* tmap, const
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
             const int b = k % NB;
-            if (k >= NB) ok = mbar_wait_bounded(&empty[b], (uint32_t)(((k / NB) - 1) & 1), WAIT_LIMIT_NS);
-            if (!__all_sync(0xffffffffu, ok)) break;
+            // the tile's window, offsets and filters first: their global loads overlap the wait for
+            // the slot
             int n0l;
             bool cv;
             const TileWin t = tile_window<PPER, PSF_RB, PSF_TH>(tile, ntx, em.n0, Nx, lane, n0l, cv);
             const size_t ic = (size_t)t.i0 + lane;
+            int Whr[NTAP];
+            float wlr[NTAP], wrr[NTAP];
 #pragma unroll
             for (int q = 0; q < NTAP; ++q) {
-                info[b].Wh[q][lane] = cv ? em.Wh[(size_t)q * Nx + ic] : 0;
-                info[b].wl[q][lane] = cv ? em.wl[(size_t)q * Nx + ic] : 0.f;
-                info[b].wr[q][lane] = cv ? em.wf[(size_t)q * Nx + ic] * 9.313225746154785e-10f : 0.f;   // * 2^-30
+                Whr[q] = cv ? em.Wh[(size_t)q * Nx + ic] : 0;
+                wlr[q] = cv ? em.wl[(size_t)q * Nx + ic] : 0.f;
+                wrr[q] = cv ? em.wf[(size_t)q * Nx + ic] * 9.313225746154785e-10f : 0.f;   // * 2^-30
+            }
+            if (k >= NB) ok = mbar_wait_bounded(&empty[b], (uint32_t)(((k / NB) - 1) & 1), WAIT_LIMIT_NS);
+            if (!__all_sync(0xffffffffu, ok)) break;
+#pragma unroll
+            for (int q = 0; q < NTAP; ++q) {
+                info[b].Wh[q][lane] = Whr[q];
+                info[b].wl[q][lane] = wlr[q];
+                info[b].wr[q][lane] = wrr[q];
             }
             info[b].n0[lane] = n0l;
             __syncwarp();
@@ -1221,10 +1232,10 @@ cudaError_t set_kernel_attributes_fx(int max_smem)
     return e;
 }
 
-cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks)
+cudaError_t xshift_fx_occupancy(bool periodic, int threads, size_t smem, int* blocks)
 {
-    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_fx_kernel<true, true>, XS_THREADS_MIN, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_fx_kernel<false, true>, XS_THREADS_MIN, smem);
+    return periodic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_fx_kernel<true, true>, threads, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, xshift_fx_kernel<false, true>, threads, smem);
 }
 
 cudaError_t pshift_fx_occupancy(int* blocks)

@@ -524,7 +524,7 @@ __device__ __forceinline__ void xshift_body(const XShiftArgs& a)
 }
 
 template <typename S, bool PERIODIC, bool KIN>
-__global__ void __launch_bounds__(XS_THREADS_MIN, 1) xshift_kernel(XShiftArgs a)
+__global__ void __launch_bounds__(XS_THREADS_MAX, 1) xshift_kernel(XShiftArgs a)
 {
     xshift_body<S, PERIODIC, KIN>(a);
 }
@@ -1177,19 +1177,30 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
             const int b = k % NB;
-            if (k >= NB) ok = mbar_wait_bounded(&empty[b], (uint32_t)(((k / NB) - 1) & 1), WAIT_LIMIT_NS);
-            if (!__all_sync(0xffffffffu, ok)) break;
+            // the tile's window, offsets and (loaded) filters first: their global loads overlap the
+            // wait for the slot
             int n0l;
             bool cv;
             const TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0l, cv);
             const bool wbulk = sizeof(S) >= 4 && t.i0 + PS_TW <= Nx;
             const int ic = t.i0 + lane;
+            T wr[NTAP], gr[2];
             if (!wbulk) {
 #pragma unroll
-                for (int q = 0; q < NTAP; ++q) info[b].w[q][lane] = cv ? wcol[(size_t)q * Nx + ic] : T(0);
+                for (int q = 0; q < NTAP; ++q) wr[q] = cv ? wcol[(size_t)q * Nx + ic] : T(0);
                 if constexpr (!PPER) {
-                    info[b].gd[0][lane] = cv ? gdcol[ic] : T(0);
-                    info[b].gd[1][lane] = cv ? gdcol[Nx + ic] : T(0);
+                    gr[0] = cv ? gdcol[ic] : T(0);
+                    gr[1] = cv ? gdcol[Nx + ic] : T(0);
+                }
+            }
+            if (k >= NB) ok = mbar_wait_bounded(&empty[b], (uint32_t)(((k / NB) - 1) & 1), WAIT_LIMIT_NS);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            if (!wbulk) {
+#pragma unroll
+                for (int q = 0; q < NTAP; ++q) info[b].w[q][lane] = wr[q];
+                if constexpr (!PPER) {
+                    info[b].gd[0][lane] = gr[0];
+                    info[b].gd[1][lane] = gr[1];
                 }
             }
             info[b].n0[lane] = n0l;

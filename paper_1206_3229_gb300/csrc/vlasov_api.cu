@@ -902,8 +902,11 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     const int esz = d->precision == VLASOV_F32 ? 4 : d->precision == VLASOV_BF16 ? 2 : 8;
     if (Nx < 16 || Np < 16 || Nx % ALIGN_N || Np % ALIGN_N)
         return fail(VLASOV_EINVAL, "Nx=%d, Np=%d: both must be multiples of %d and >= 16", Nx, Np, ALIGN_N);
-    if (Nx > xshift_max_cols(esz, XS_THREADS_MIN))
-        return fail(VLASOV_EINVAL, "Nx=%d exceeds %d for this precision", Nx, xshift_max_cols(esz, XS_THREADS_MIN));
+    // x rows are staged whole: 256-thread CTAs cover 8192 FP32 or BF16 cells and 4096 8-byte cells;
+    // longer 8-byte rows (up to 8192) run on 512-thread CTAs
+    const int xs_threads = (esz == 8 && Nx > xshift_max_cols(esz, XS_THREADS_MIN)) ? XS_THREADS_MAX : XS_THREADS_MIN;
+    if (Nx > xshift_max_cols(esz, xs_threads))
+        return fail(VLASOV_EINVAL, "Nx=%d exceeds %d for this precision", Nx, xshift_max_cols(esz, xs_threads));
     if (!(dt > 0) || !std::isfinite(dt)) return fail(VLASOV_EINVAL, "dt must be > 0");
     if (!(d->xmax > d->xmin) || !(d->pmax > d->pmin)) return fail(VLASOV_EINVAL, "empty domain");
     if (model == VLASOV_RING && !(d->eps > 0)) return fail(VLASOV_EINVAL, "ring model needs eps > 0");
@@ -994,7 +997,7 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     TRY(upload_params(s, s->xp, srow.data(), Np, &max_n0, &s->xe, s->xrec, true));
 
     // x-shift launch shape: whole rows staged per CTA.
-    s->xthreads = XS_THREADS_MIN;
+    s->xthreads = xs_threads;
     // zero halo of non-periodic rows: the window of a chunk reaches |n0| + 4 + (V - 1) cells past the
     // row, V = 16 bytes / cell (8 for BF16 storage)
     s->xpad = s->xper ? 16 : ((max_n0 + xhalo_extra(esz) + 15) / 16) * 16;
@@ -1009,8 +1012,8 @@ int vlasov_create(int model, int Nx, int Np, const vlasov_domain* d, double dt, 
     }
     if (s->xstages < 1) return bail(fail(VLASOV_EINVAL, "a row of Nx=%d (+%d halo) does not fit shared memory", Nx, s->xpad));
     int occ = 0;
-    if (s->fx) CTRY(xshift_fx_occupancy(s->xper, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
-    else if (s->emul) CTRY(xshift_e_occupancy(s->xper, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    if (s->fx) CTRY(xshift_fx_occupancy(s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
+    else if (s->emul) CTRY(xshift_e_occupancy(s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
     else CTRY(xshift_occupancy(esz, s->xper, s->xthreads, xshift_smem_bytes(Nx, s->xpad, s->xstages, esz), &occ));
     occ = std::max(occ, 1);
     s->xgrid = std::min(Np, s->nsm * occ);

@@ -353,6 +353,7 @@ void ring_dft_host(const double* v, int N, double* out);
 // ---------------------------------------------------------------------------------------------
 // Launchers (return cudaError_t of the launch).
 constexpr int XS_THREADS_MIN = 256;
+constexpr int XS_THREADS_MAX = 512;   // 8-byte rows longer than 256 threads cover (Nx <= 8192)
 int xshift_max_cols(int elem_bytes, int threads);
 size_t xshift_smem_bytes(int Nx, int pad, int stages, int elem_bytes);
 cudaError_t launch_xshift(int elem_bytes, bool periodic, bool kin, int grid, int threads,
@@ -364,6 +365,7 @@ constexpr int PS_RPT = 16;       // output rows per thread
 constexpr int PS_TH = PS_RG * PS_RPT;  // output rows per tile
 constexpr int PS_BH = 32;        // rows per TMA box
 constexpr int PS_RB = 256;       // staged rows per buffer
+static_assert(PS_RB % PS_BH == 0, "a staged window is whole TMA boxes: the slot must hold nb * PS_BH rows");
 // FP32-class p-shift: PS_RG compute warps and one producer warp per CTA, PS_NB staged tiles in flight
 constexpr int PS_THREADS = PS_TW * (PS_RG + 1);
 constexpr int PS_NB = 2;
@@ -387,7 +389,7 @@ cudaError_t set_kernel_attributes_e(int max_smem);
 int xshift_e_max_cols(int threads);
 int xshift_fx_max_cols(int threads);
 size_t pshift_e_smem_bytes();
-cudaError_t xshift_e_occupancy(bool periodic, size_t smem, int* blocks);
+cudaError_t xshift_e_occupancy(bool periodic, int threads, size_t smem, int* blocks);
 cudaError_t pshift_e_occupancy(int* blocks);
 cudaError_t launch_xshift_e(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,
                             cudaStream_t st);
@@ -398,7 +400,7 @@ cudaError_t pshift_occupancy(int elem_bytes, int* blocks);
 
 cudaError_t set_kernel_attributes_fx(int max_smem);
 size_t pshift_fx_smem_bytes();
-cudaError_t xshift_fx_occupancy(bool periodic, size_t smem, int* blocks);
+cudaError_t xshift_fx_occupancy(bool periodic, int threads, size_t smem, int* blocks);
 cudaError_t pshift_fx_occupancy(int* blocks);
 int pshift_fx_tile_rows();   // output rows per tile of the single-grid FX64 p-shift
 cudaError_t launch_xshift_fx(bool periodic, bool kin, int grid, int threads, const XShiftArgs& a, const EmulArgs& em,

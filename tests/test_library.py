@@ -43,7 +43,8 @@ def test_library_exports_every_declared_symbol(lib):
     (64, 64, 0.1, V.RING, 0.0, V.F64),      # ring without softening
     (64, 64, 0.1, 7, 0.0, V.F64),           # unknown model
     (64, 64, 0.1, V.HMF, 0.0, 5),           # unknown precision
-    (8192, 64, 0.1, V.HMF, 0.0, V.F64),     # FP64 rows longer than the staged maximum
+    (8200, 64, 0.1, V.HMF, 0.0, V.F64),     # FP64 rows longer than the staged maximum
+    (8200, 64, 0.1, V.HMF, 0.0, V.F32),     # FP32 rows longer than the staged maximum
 ])
 def test_create_rejects_bad_arguments_without_gpu(lib, nx, np_, dt, model, eps, prec):
     dom = V.Domain(-3.14, 3.14, -4.0, 4.0, 1, 0, eps, 1.0, prec, None)
