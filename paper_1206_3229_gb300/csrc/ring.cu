@@ -25,6 +25,7 @@
 #include <cstring>
 
 #include "fixed_point.cuh"
+#include "pparams.cuh"
 #include "ptx.cuh"
 #include "vlasov_internal.cuh"
 
@@ -62,7 +63,7 @@ size_t ringfx_smem_bytes(int N, int ksplit)
 // Block (g, q): outputs i = 32 g + lane, inputs k in the q-th of ksplit slices [kb, ke) of [0, N).
 // Warp w adds the w-th eighth of the slice.  Warp sums and slice sums are exact int128 additions,
 // so the result does not depend on the split; the last slice block of a group (ticket) finishes it.
-template <bool POT>
+template <bool POT, bool FILT = false>
 __device__ __forceinline__ void ringfx_body(const RingArgs& a, int bx)
 {
     constexpr int NW = RINGFX_THREADS / 32;
@@ -131,7 +132,14 @@ __device__ __forceinline__ void ringfx_body(const RingArgs& a, int bx)
         if (lane == 0) a.gticket[g] = 0u;   // ready for the next launch
     }
     if constexpr (!POT) {
-        if (i < N) a.F[i] = fx128_to_f64(s, a.k_col + a.sK) * (-a.dx * a.dp);
+        if (i < N) {
+            const double F = fx128_to_f64(s, a.k_col + a.sK) * (-a.dx * a.dp);
+            a.F[i] = F;
+            if (FILT && a.pp_on) {   // this column's p-shift filters, as the filter launch would write them
+                if (a.pp_fixed) pparams_fixed(a.pp, i, F * a.pp.cp);
+                else pparams_f32(a.pp, i, F * a.pp.cp);
+            }
+        }
     } else {
         // rho_i * Phi_i with Phi_i = dx dp 2^-(k_col+sV) S_i, summed exactly (scale 2^k_pot)
         i128 u = 0;
@@ -173,7 +181,7 @@ __device__ __forceinline__ void ringfx_body(const RingArgs& a, int bx)
 template <bool POT>
 __global__ void __launch_bounds__(RINGFX_THREADS) ringfx_kernel(RingArgs a)
 {
-    ringfx_body<POT>(a, blockIdx.x);
+    ringfx_body<POT, true>(a, blockIdx.x);
 }
 
 // The force of one state (f) and the potential of another (p) in one launch: blocks [0, nf) take
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(RINGFX_THREADS) ringfx_kernel(RingArgs a)
 __global__ void __launch_bounds__(RINGFX_THREADS) ringfx_dual_kernel(RingArgs f, RingArgs p)
 {
     const int nf = ((f.N + 31) / 32) * f.ksplit;
-    if ((int)blockIdx.x < nf) ringfx_body<false>(f, blockIdx.x);
+    if ((int)blockIdx.x < nf) ringfx_body<false, true>(f, blockIdx.x);
     else ringfx_body<true>(p, (int)blockIdx.x - nf);
 }
 

@@ -565,9 +565,20 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
 
 // The ring force (final_moments = false) or potential and moment record (true) by the handle's
 // method; one launch either way.
-cudaError_t run_ring(vlasov_sim* s, bool final_moments)
+PParamsArgs pparams_args(const vlasov_sim* s, double* Fout);
+
+// Ring force with the fixed-point sums: its launch also writes the p-shift filters of the columns
+// (one launch fewer per step).
+bool ring_filters_in_force(const vlasov_sim* s) { return s->model == VLASOV_RING && s->ring_method == RING_M_FIXED; }
+
+cudaError_t run_ring(vlasov_sim* s, bool final_moments, bool with_filters = false)
 {
-    const RingArgs a = ringargs(s, final_moments);
+    RingArgs a = ringargs(s, final_moments);
+    if (with_filters && !final_moments && ring_filters_in_force(s)) {
+        a.pp = pparams_args(s, nullptr);
+        a.pp_on = 1;
+        a.pp_fixed = s->msz == 8 ? 1 : 0;
+    }
     switch (s->ring_method) {
     case RING_M_FIXED: return launch_ring_fixed(a, s->st);
     case RING_M_FFT64: return launch_ring_fft(true, a, s->st);
@@ -577,7 +588,7 @@ cudaError_t run_ring(vlasov_sim* s, bool final_moments)
     }
 }
 
-int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int ctas = 0)
+PParamsArgs pparams_args(const vlasov_sim* s, double* Fout)
 {
     PParamsArgs a;
     a.Nx = s->Nx;
@@ -599,6 +610,12 @@ int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int 
     a.wle = (s->emul || s->fx) ? s->pe.wle : nullptr;
     a.wfe = (s->emul || s->fx) ? s->pe.wfe : nullptr;
     a.beta = s->gs ? s->pp.beta : nullptr;
+    return a;
+}
+
+int launch_pparams_only(vlasov_sim* s, double* Fout, bool from_cta = false, int ctas = 0)
+{
+    PParamsArgs a = pparams_args(s, Fout);
     if (from_cta) {
         a.ctapart = s->ctapart;
         a.ctas = ctas > 0 ? ctas : s->xgrid;
@@ -652,17 +669,20 @@ int enq_force_p(vlasov_sim* s, int c, int ctas, Marks* marks)
     if (s->hmf_cta) {
         int rc = launch_pparams_only(s, nullptr, true, ctas);   // Mx, My from the per-CTA partials
         if (rc) return rc;
+        MARK();
     } else {
         CU_TRY(launch_colreduce(crargs(s, ctas, false, false), s->crgrid, s->st));
         MARK();
         if (s->model == VLASOV_RING) {
-            CU_TRY(run_ring(s, false));
+            CU_TRY(run_ring(s, false, true));
             MARK();
         }
-        int rc = launch_pparams_only(s, nullptr);
-        if (rc) return rc;
+        if (!ring_filters_in_force(s)) {
+            int rc = launch_pparams_only(s, nullptr);
+            if (rc) return rc;
+            MARK();
+        }
     }
-    MARK();
     CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
     MARK();
     return VLASOV_OK;
@@ -742,7 +762,10 @@ int enq_mid_ring_merged(vlasov_sim* s, int c, Marks* marks)
     if (!cm.colpart64 || !cd.colpart64 || cm.colacc || cd.colacc) return fail(VLASOV_ECUDA, "merged reduction needs partial rows");
     CU_TRY(launch_colreduce_p64_dual(cm, cd, s->st));
     MARK();
-    RingArgs rf = ringargs(s, false);
+    RingArgs rf = ringargs(s, false);   // with the p-shift filters of its columns
+    rf.pp = pparams_args(s, nullptr);
+    rf.pp_on = 1;
+    rf.pp_fixed = s->msz == 8 ? 1 : 0;
     RingArgs rp = ringargs(s, true);
     rp.colfx = s->colfx_m;
     rp.rho = s->rho_m;
@@ -750,9 +773,6 @@ int enq_mid_ring_merged(vlasov_sim* s, int c, Marks* marks)
     rp.gpart = s->ring_gpart_m;
     rp.gticket = s->ring_gticket_m;
     CU_TRY(launch_ring_fixed_dual(rf, rp, s->st));
-    MARK();
-    int rc = launch_pparams_only(s, nullptr);
-    if (rc) return rc;
     MARK();
     const int o = c ^ 1;
     CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
@@ -838,7 +858,12 @@ int build_fused_graphs(vlasov_sim* s, int c)
 
 // Launches per piece: x-shift 1; force (reductions, filters); p-shift; x-shift 4 or the fused
 // x-shifts; moments.
-int force_launches(const vlasov_sim* s) { return s->hmf_cta ? 1 : (s->model == VLASOV_RING ? 3 : 2); }
+int force_launches(const vlasov_sim* s)
+{
+    if (s->hmf_cta) return 1;
+    if (s->model == VLASOV_RING) return ring_filters_in_force(s) ? 2 : 3;
+    return 2;
+}
 int moment_launches(const vlasov_sim* s) { return s->model == VLASOV_RING ? 2 : 1; }
 
 int check_dev_err(vlasov_sim* s)
@@ -1702,7 +1727,7 @@ int vlasov_step_timed(vlasov_sim* s, int n, double* ms_per_launch, int max_launc
 int vlasov_kernels_per_step(const vlasov_sim* s)
 {
     if (!s) return 0;
-    if (ring_merged(s)) return 5;   // fused x-shifts, both reductions, both convolutions, filters, p-shift
+    if (ring_merged(s)) return 4;   // fused x-shifts, both reductions, both convolutions (+ filters), p-shift
     return (s->fuse ? 2 : 3) + force_launches(s) + moment_launches(s);
 }
 

@@ -301,6 +301,10 @@ struct RingArgs {
     int k_col, sK, sV;
     double dp;
     int ksplit;              // blocks per group of 32 outputs
+    // the force launch of the fixed-point form can also write the p-shift filters of its columns
+    // (the filter launch's work, same values): pp_on, with pp_fixed for 8-byte storage
+    PParamsArgs pp{};
+    int pp_on = 0, pp_fixed = 0;
     void* gpart;             // int128 [ksplit][N] partial sums
     unsigned int* gticket;   // [ceil(N/32)] per-group tickets
     void* upart;             // int128 [ceil(N/32)] potential partials per group

@@ -464,9 +464,9 @@ class Sim:
         hmf_cta = self.model == HMF and self.precision in (FX64, BF16, F32) and self.nx * self.np <= 1 << 24 \
             and self.spline == "fd"
         if self.fused_x and self.model == RING and self.ring_method == "fixed":
-            # the end state's moments and the next force: reductions and convolutions merged
-            return ["xshift_fused", "reduce_moments_density", "ring_potential_force", "pshift_filters",
-                    "pshift_step3"]
+            # the end state's moments and the next force: reductions and convolutions merged, the
+            # force launch also writing the p-shift filters
+            return ["xshift_fused", "reduce_moments_density", "ring_potential_force_filters", "pshift_step3"]
         if self.fused_x:
             names = ["xshift_fused", "reduce_moments"]
             if self.model == RING:
@@ -480,9 +480,13 @@ class Sim:
         if hmf_cta:
             return ["xshift_step1", "force_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
         names = ["xshift_step1", "reduce_density"]
-        if self.model == RING:
-            names.append("ring_force")
-        names += ["pshift_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
+        if self.model == RING and self.ring_method == "fixed":
+            names.append("ring_force_filters")
+        else:
+            if self.model == RING:
+                names.append("ring_force")
+            names.append("pshift_filters")
+        names += ["pshift_step3", "xshift_step4", "reduce_moments"]
         if self.model == RING:
             names.append("ring_potential")
         return names
