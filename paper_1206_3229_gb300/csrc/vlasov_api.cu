@@ -563,14 +563,15 @@ RingArgs ringargs(vlasov_sim* s, bool final_moments)
     return a;
 }
 
-// The ring force (final_moments = false) or potential and moment record (true) by the handle's
-// method; one launch either way.
 PParamsArgs pparams_args(const vlasov_sim* s, double* Fout);
 
 // Ring force with the fixed-point sums: its launch also writes the p-shift filters of the columns
 // (one launch fewer per step).
 bool ring_filters_in_force(const vlasov_sim* s) { return s->model == VLASOV_RING && s->ring_method == RING_M_FIXED; }
 
+// The ring force (final_moments = false) or potential and moment record (true) by the handle's
+// method; one launch either way (with_filters: the force launch of the fixed-point method also
+// writes the p-shift filters).
 cudaError_t run_ring(vlasov_sim* s, bool final_moments, bool with_filters = false)
 {
     RingArgs a = ringargs(s, final_moments);
