@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(PPC_THREADS) pparams_hmf_cta_kernel(PParamsArg
     if (i >= a.Nx) return;
     const double Mx = a.dxdp * fx128_to_f64(x, 101 - a.Ef);
     const double My = a.dxdp * fx128_to_f64(y, 101 - a.Ef);
-    const double F = -Mx * a.sintab[i] + My * a.costab[i];
+    const double F = hmf_force(Mx, My, a.sintab[i], a.costab[i]);
     if (a.Fout) a.Fout[i] = F;
     if constexpr (sizeof(T) == 8) pparams_fixed(a, i, F * a.cp);
     else pparams_f32(a, i, F * a.cp);

@@ -94,34 +94,77 @@ __device__ __forceinline__ void pparams_fixed(const PParamsArgs& a, int i, doubl
 }
 
 // FP32-class storage: the foot split in FP64, the ten weights in FP32.
-__device__ __forceinline__ void pparams_f32(const PParamsArgs& a, int i, double sigma)
+// The FP32 filter of a column moving by sigma cells: foot offset n0 = floor(-sigma) and fraction beta
+// in FP64, the ten weights of Eqs. (splinegen, splinecoeffs, findif) and g, d (the f'' factors of the
+// two spline nodes) in FP32.  One routine for the filter launch and the p-shift that forms its
+// tiles' filters itself, so both give the same values.
+struct FiltF32 {
+    int n0;
+    double beta;
+    float w[NTAP];
+    float g, d;
+};
+__device__ __forceinline__ FiltF32 filt_f32(double sigma)
 {
     using T = float;
+    FiltF32 o;
     const double ms = -sigma;
     const double fl = floor(ms);
-    const double beta = ms - fl;
-    if (a.beta) a.beta[i] = beta;
-    T* w = static_cast<T*>(a.w);
-    T* gd = static_cast<T*>(a.gd);
-    a.n0[i] = (int)fl;
-    const T b = (T)beta;
-    const T al = (T)(1.0 - beta);
+    o.beta = ms - fl;
+    o.n0 = (int)fl;
+    const T b = (T)o.beta;
+    const T al = (T)(1.0 - o.beta);
     const T g = (al * al * al - al) * (T)(1.0 / 6.0);
     const T d = (b * b * b - b) * (T)(1.0 / 6.0);
     const T c0 = T(VL_FD_C0), c1 = T(VL_FD_C1), c2 = T(VL_FD_C2), c3 = T(VL_FD_C3), c4 = T(VL_FD_C4);
+    o.w[0] = g * c4;
+    o.w[1] = g * c3 + d * c4;
+    o.w[2] = g * c2 + d * c3;
+    o.w[3] = g * c1 + d * c2;
+    o.w[4] = al + g * c0 + d * c1;
+    o.w[5] = b + g * c1 + d * c0;
+    o.w[6] = g * c2 + d * c1;
+    o.w[7] = g * c3 + d * c2;
+    o.w[8] = g * c4 + d * c3;
+    o.w[9] = d * c4;
+    o.g = g;
+    o.d = d;
+    return o;
+}
+
+__device__ __forceinline__ void pparams_f32(const PParamsArgs& a, int i, double sigma)
+{
+    const FiltF32 o = filt_f32(sigma);
+    if (a.beta) a.beta[i] = o.beta;
+    float* w = static_cast<float*>(a.w);
+    float* gd = static_cast<float*>(a.gd);
+    a.n0[i] = o.n0;
     const size_t n = (size_t)a.Nx;
-    w[0 * n + i] = g * c4;
-    w[1 * n + i] = g * c3 + d * c4;
-    w[2 * n + i] = g * c2 + d * c3;
-    w[3 * n + i] = g * c1 + d * c2;
-    w[4 * n + i] = al + g * c0 + d * c1;
-    w[5 * n + i] = b + g * c1 + d * c0;
-    w[6 * n + i] = g * c2 + d * c1;
-    w[7 * n + i] = g * c3 + d * c2;
-    w[8 * n + i] = g * c4 + d * c3;
-    w[9 * n + i] = d * c4;
-    gd[i] = g;
-    gd[n + i] = d;
+#pragma unroll
+    for (int t = 0; t < NTAP; ++t) w[t * n + i] = o.w[t];
+    gd[i] = o.g;
+    gd[n + i] = o.d;
+}
+
+// The HMF force of Eq. (hmfmeanforce) at a node with sin x_i = s, cos x_i = c.
+__device__ __forceinline__ double hmf_force(double Mx, double My, double s, double c) { return -Mx * s + My * c; }
+
+// HMF mean field from the x-shift's per-CTA numbers ([ctas][3] int128: mass, cos- and sin-weighted
+// column sums, units 2^(Ef-51) and 2^(Ef-101)), summed exactly by one warp: Mx, My of Eq. (mxmydef),
+// the same values as the filter launch's block sums give.
+__device__ __forceinline__ void hmf_mxmy_warp(const HmfFiltArgs& h, double& Mx, double& My)
+{
+    const int lane = threadIdx.x & 31;
+    const i128* p = static_cast<const i128*>(h.ctapart);
+    i128 x = 0, y = 0;
+    for (int b = lane; b < h.ctas; b += 32) {
+        x += p[(size_t)b * 3 + 1];
+        y += p[(size_t)b * 3 + 2];
+    }
+    x = warp_sum_i128(x);
+    y = warp_sum_i128(y);
+    Mx = h.dxdp * fx128_to_f64(x, 101 - h.Ef);
+    My = h.dxdp * fx128_to_f64(y, 101 - h.Ef);
 }
 
 }  // namespace vl

@@ -40,18 +40,16 @@ struct TileWin {
 };
 
 // Window of input rows a tile of TH rows needs: [j0 + kmin - 4, j0 + TH - 1 + kmax + 5].  Called by whole
-// warps (all lanes hold one column); identical in every warp.
+// warps (all lanes hold one column); identical in every warp.  tile_window_of takes this lane's foot
+// offset n0_lane (any value where !colvalid, replaced there by the tile's least offset); tile_window
+// loads it from n0.
 template <bool PPER, int RB = PS_RB, int TH = PS_TH>
-__device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __restrict__ n0, int Nx, int lane,
-                                               int& n0_lane, bool& colvalid)
+__device__ __forceinline__ TileWin tile_window_of(int tile, int ntx, bool colvalid, int& n0_lane)
 {
     TileWin t;
     const int tx = tile % ntx, ty = tile / ntx;
     t.i0 = tx * PS_TW;
     t.j0 = ty * TH;
-    const int i = t.i0 + lane;
-    colvalid = i < Nx;
-    n0_lane = colvalid ? n0[i] : 0;
     int kmin = colvalid ? n0_lane : 0x7fffffff;
     int kmax = colvalid ? n0_lane : (int)0x80000000;
 #pragma unroll
@@ -67,6 +65,16 @@ __device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __r
     t.smem_ok = !PPER && R <= RB;
     t.nb = t.smem_ok ? (int)((R + PS_BH - 1) / PS_BH) : 0;
     return t;
+}
+
+template <bool PPER, int RB = PS_RB, int TH = PS_TH>
+__device__ __forceinline__ TileWin tile_window(int tile, int ntx, const int* __restrict__ n0, int Nx, int lane,
+                                               int& n0_lane, bool& colvalid)
+{
+    const int i = (tile % ntx) * PS_TW + lane;
+    colvalid = i < Nx;
+    n0_lane = colvalid ? n0[i] : 0;
+    return tile_window_of<PPER, RB, TH>(tile, ntx, colvalid, n0_lane);
 }
 
 template <typename T, bool PPER>

@@ -13,6 +13,7 @@
 //  f = 0 outside reading of the p axis), each thread walks 16 rows of one column with a sliding
 //  register window.
 #include "fixed_point.cuh"
+#include "pparams.cuh"
 #include "ptx.cuh"
 #include "shift_common.cuh"
 #include "vlasov_internal.cuh"
@@ -1127,7 +1128,8 @@ cudaError_t gs_occupancy(int elem_bytes, bool xdir, size_t smem, int* blocks)
 // (full[b]); the compute warps take the tiles in the same order and hand each buffer back through
 // empty[b].  No CTA-wide barrier per tile: a warp waits only for the data it reads.
 template <typename S, bool PPER>
-__device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const PShiftArgs& a)
+__device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const PShiftArgs& a,
+                                            const HmfFiltArgs* hf = nullptr)
 {
     using T = typename VecOf<S>::T;
     constexpr int NB = PS_NB;
@@ -1171,21 +1173,42 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
         // ---- producer.  Filters of a tile with all 32 columns inside the grid arrive by bulk copies
         // on the tile's barrier; BF16 storage loads them (measured faster there, its tiles being half
         // the bytes), as does the last, partial column tile.
+        // HMF with hf->on: the filters of the tile's columns are formed here from Mx, My (Eq.
+        // hmfmeanforce) instead of being loaded, and no filter launch precedes this one.
         constexpr uint32_t ROWB = PS_TW * (uint32_t)sizeof(T);
         constexpr uint32_t WBYTES = (NTAP + (PPER ? 0 : 2)) * ROWB;
+        const bool hfilt = hf != nullptr && hf->on != 0;
+        double hMx = 0.0, hMy = 0.0;
+        if (hfilt) hmf_mxmy_warp(*hf, hMx, hMy);
         int k = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
             const int b = k % NB;
-            // the tile's window, offsets and (loaded) filters first: their global loads overlap the
-            // wait for the slot
+            // the tile's window, offsets and (loaded or formed) filters first: their global loads
+            // overlap the wait for the slot
             int n0l;
             bool cv;
-            const TileWin t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0l, cv);
-            const bool wbulk = sizeof(S) >= 4 && t.i0 + PS_TW <= Nx;
-            const int ic = t.i0 + lane;
+            TileWin t;
             T wr[NTAP], gr[2];
-            if (!wbulk) {
+            bool wbulk;
+            if (hfilt) {
+                const int icol = (tile % ntx) * PS_TW + lane;
+                cv = icol < Nx;
+                FiltF32 o{};
+                if (cv) o = filt_f32(hmf_force(hMx, hMy, hf->sintab[icol], hf->costab[icol]) * hf->cp);
+                n0l = o.n0;
+                t = tile_window_of<PPER>(tile, ntx, cv, n0l);
+#pragma unroll
+                for (int q = 0; q < NTAP; ++q) wr[q] = cv ? T(o.w[q]) : T(0);
+                gr[0] = cv ? T(o.g) : T(0);
+                gr[1] = cv ? T(o.d) : T(0);
+                wbulk = false;
+            } else {
+                t = tile_window<PPER>(tile, ntx, a.n0, Nx, lane, n0l, cv);
+                wbulk = sizeof(S) >= 4 && t.i0 + PS_TW <= Nx;
+            }
+            const int ic = t.i0 + lane;
+            if (!wbulk && !hfilt) {
 #pragma unroll
                 for (int q = 0; q < NTAP; ++q) wr[q] = cv ? wcol[(size_t)q * Nx + ic] : T(0);
                 if constexpr (!PPER) {
@@ -1298,9 +1321,10 @@ __device__ __forceinline__ void pshift_body(const CUtensorMap* tmap_ptr, const P
 }
 
 template <typename S, bool PPER>
-__global__ void __launch_bounds__(PS_THREADS, sizeof(S) == 8 ? 1 : PS_MINB) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a)
+__global__ void __launch_bounds__(PS_THREADS, sizeof(S) == 8 ? 1 : PS_MINB) pshift_kernel(const __grid_constant__ CUtensorMap tmap, PShiftArgs a,
+                                                                                          const __grid_constant__ HmfFiltArgs hf)
 {
-    pshift_body<S, PPER>(&tmap, a);
+    pshift_body<S, PPER>(&tmap, a, &hf);
 }
 
 // Batched form: tensor maps and arguments of each slot, per buffer parity, in global memory.
@@ -1322,19 +1346,21 @@ size_t pshift_smem_bytes(int elem_bytes)
 }
 
 template <typename S, bool PPER>
-static cudaError_t launch_p(int grid, const CUtensorMap* tmap, const PShiftArgs& a, cudaStream_t st)
+static cudaError_t launch_p(int grid, const CUtensorMap* tmap, const PShiftArgs& a, const HmfFiltArgs& hf, cudaStream_t st)
 {
     const size_t smem = pshift_smem_bytes((int)sizeof(S));
-    pshift_kernel<S, PPER><<<grid, PS_THREADS, smem, st>>>(*tmap, a);
+    pshift_kernel<S, PPER><<<grid, PS_THREADS, smem, st>>>(*tmap, a, hf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUtensorMap* tmap, const PShiftArgs& a,
-                          cudaStream_t st)
+                          const HmfFiltArgs* hfp, cudaStream_t st)
 {
-    if (elem_bytes == 8) return p_periodic ? launch_p<double, true>(grid, tmap, a, st) : launch_p<double, false>(grid, tmap, a, st);
-    if (elem_bytes == 2) return p_periodic ? launch_p<bf16, true>(grid, tmap, a, st) : launch_p<bf16, false>(grid, tmap, a, st);
-    return p_periodic ? launch_p<float, true>(grid, tmap, a, st) : launch_p<float, false>(grid, tmap, a, st);
+    HmfFiltArgs hf{};
+    if (hfp && elem_bytes <= 4) hf = *hfp;
+    if (elem_bytes == 8) return p_periodic ? launch_p<double, true>(grid, tmap, a, hf, st) : launch_p<double, false>(grid, tmap, a, hf, st);
+    if (elem_bytes == 2) return p_periodic ? launch_p<bf16, true>(grid, tmap, a, hf, st) : launch_p<bf16, false>(grid, tmap, a, hf, st);
+    return p_periodic ? launch_p<float, true>(grid, tmap, a, hf, st) : launch_p<float, false>(grid, tmap, a, hf, st);
 }
 
 cudaError_t launch_xshift_batch(bool periodic, bool kin, int slots, int ctas_per_slot, size_t smem,

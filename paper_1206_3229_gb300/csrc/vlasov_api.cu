@@ -470,13 +470,17 @@ cudaError_t run_xshift(vlasov_sim* s, const XShiftArgs& a, const LineParamsDev& 
     return launch_xshift(s->esz, s->xper, kin, s->xgrid, s->xthreads, a, s->st);
 }
 
+// HMF with FP32-class storage: the p-shift forms its filters itself from the x-shift's per-CTA
+// numbers (no filter launch).
+bool hmf_filters_in_pshift(const vlasov_sim* s) { return s->hmf_cta && !s->fx && s->esz <= 4; }
+
 cudaError_t run_pshift(vlasov_sim* s, const CUtensorMap* tmap, const PShiftArgs& a, const LineParamsDev& p,
-                       const EmulParamsDev& e)
+                       const EmulParamsDev& e, const HmfFiltArgs* hf = nullptr)
 {
     if (s->gs) return launch_gs_pshift(s->esz, s->pper, s->gspgrid, a, s->st);
     if (s->fx) return launch_pshift_fx(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
     if (s->emul) return launch_pshift_e(s->pper, s->pgrid, tmap, a, emargs(s, p, e), s->st);
-    return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, s->st);
+    return launch_pshift(s->esz, s->pper, s->pgrid, tmap, a, hf, s->st);
 }
 
 ColReduceArgs crargs(vlasov_sim* s, int B, bool kin, bool final_moments, bool from_acc = true, bool fused_m = false)
@@ -667,7 +671,17 @@ int enq_x1(vlasov_sim* s, int c, Marks* marks)
 int enq_force_p(vlasov_sim* s, int c, int ctas, Marks* marks)
 {
     const int o = c ^ 1;
-    if (s->hmf_cta) {
+    HmfFiltArgs hf{};
+    if (hmf_filters_in_pshift(s)) {   // Mx, My from the per-CTA partials, inside the p-shift
+        hf.ctapart = s->ctapart;
+        hf.ctas = ctas > 0 ? ctas : s->xgrid;
+        hf.Ef = s->Ef;
+        hf.on = 1;
+        hf.dxdp = s->dx * s->dp;
+        hf.cp = s->dt / s->dp;
+        hf.costab = s->costab;
+        hf.sintab = s->sintab;
+    } else if (s->hmf_cta) {
         int rc = launch_pparams_only(s, nullptr, true, ctas);   // Mx, My from the per-CTA partials
         if (rc) return rc;
         MARK();
@@ -684,7 +698,7 @@ int enq_force_p(vlasov_sim* s, int c, int ctas, Marks* marks)
             MARK();
         }
     }
-    CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe));
+    CU_TRY(run_pshift(s, &s->tmap[o], pargs(s, s->f[o], s->f[c], s->pp), s->pp, s->pe, hf.on ? &hf : nullptr));
     MARK();
     return VLASOV_OK;
 }
@@ -861,6 +875,7 @@ int build_fused_graphs(vlasov_sim* s, int c)
 // x-shifts; moments.
 int force_launches(const vlasov_sim* s)
 {
+    if (hmf_filters_in_pshift(s)) return 0;
     if (s->hmf_cta) return 1;
     if (s->model == VLASOV_RING) return ring_filters_in_force(s) ? 2 : 3;
     return 2;

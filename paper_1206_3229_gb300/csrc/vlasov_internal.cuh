@@ -251,6 +251,16 @@ struct ColReduceArgs {
     double dt;
 };
 
+// HMF p-shift filters formed inside the p-shift (FP32-class storage): the x-shift's per-CTA numbers
+// give Mx, My (one warp per CTA sums them exactly), and the producer warp forms each tile's filters.
+struct HmfFiltArgs {
+    const void* ctapart = nullptr;   // [ctas][3] int128
+    int ctas = 0, Ef = 0, on = 0;
+    double dxdp = 0, cp = 0;         // dx dp; dt / dp
+    const double* costab = nullptr;
+    const double* sintab = nullptr;
+};
+
 struct PParamsArgs {
     // HMF from the x-shift's per-CTA partials: every block adds the same [ctas][3] int128 partials
     // (exactly) to get Mx, My.
@@ -375,8 +385,9 @@ constexpr int PS_THREADS = PS_TW * (PS_RG + 1);
 constexpr int PS_NB = 2;
 constexpr int PS_MINB = 3;       // CTAs per SM the register budget is set for, 4-byte storage (faster than 2)
 size_t pshift_smem_bytes(int elem_bytes);
+// hf (may be NULL): form the HMF filters inside the launch (4-byte and 2-byte storage)
 cudaError_t launch_pshift(int elem_bytes, bool p_periodic, int grid, const CUtensorMap* tmap,
-                          const PShiftArgs& a, cudaStream_t st);
+                          const PShiftArgs& a, const HmfFiltArgs* hf, cudaStream_t st);
 
 // Opt a kernel into the dynamic shared memory it may use: the per-block limit max_smem less its own
 // static shared memory.

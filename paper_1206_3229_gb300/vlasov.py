@@ -467,18 +467,20 @@ class Sim:
             # the end state's moments and the next force: reductions and convolutions merged, the
             # force launch also writing the p-shift filters
             return ["xshift_fused", "reduce_moments_density", "ring_potential_force_filters", "pshift_step3"]
+        # HMF with FP32-class storage: the p-shift forms its filters itself (no filter launch)
+        filt = [] if (hmf_cta and self.precision in (BF16, F32)) else ["force_filters"]
         if self.fused_x:
             names = ["xshift_fused", "reduce_moments"]
             if self.model == RING:
                 names.append("ring_potential")
             if hmf_cta:
-                return names + ["force_filters", "pshift_step3"]
+                return names + filt + ["pshift_step3"]
             names.append("reduce_density")
             if self.model == RING:
                 names.append("ring_force")
             return names + ["pshift_filters", "pshift_step3"]
         if hmf_cta:
-            return ["xshift_step1", "force_filters", "pshift_step3", "xshift_step4", "reduce_moments"]
+            return ["xshift_step1"] + filt + ["pshift_step3", "xshift_step4", "reduce_moments"]
         names = ["xshift_step1", "reduce_density"]
         if self.model == RING and self.ring_method == "fixed":
             names.append("ring_force_filters")
