@@ -283,7 +283,7 @@ int vlasov_batch_create(int slots, int max_n, long long mem_budget_bytes, int pr
 
 /* Launch shape of the batched sweeps.  rows_per_cta: x-shift rows per CTA (a slot with Np rows runs
    on clamp(ceil(Np / rows_per_cta), 16, 512) CTAs, whatever else is in the batch); tiles_per_cta:
-   p-shift tiles (32 columns x 128 rows) per CTA of the batch's largest grid (each slot's p-shift
+   p-shift tiles (32 columns x 128 rows; 112 rows with VLASOV_FX64) per CTA of the batch's largest grid (each slot's p-shift
    launch has clamp(tiles / tiles_per_cta, 32, 1024) CTAs). */
 typedef struct {
     int rows_per_cta;

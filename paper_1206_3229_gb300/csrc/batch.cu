@@ -736,7 +736,8 @@ int vlasov_batch_create_shaped(int slots, int max_n, long long mem_budget_bytes,
     // surplus CTAs exit at once.
     b->ctas_x = slot_ctas_x(max_n, b->shape.rows_per_cta);
     {
-        const int tiles = ((max_n + PS_TW - 1) / PS_TW) * ((max_n + PS_TH - 1) / PS_TH);
+        const int th = precision == VLASOV_FX64 ? pshift_fx_tile_rows() : PS_TH;
+        const int tiles = ((max_n + PS_TW - 1) / PS_TW) * ((max_n + th - 1) / th);
         b->ctas_p = std::min(1024, std::max(32, tiles / b->shape.tiles_per_cta));
     }
     auto bail = [&](int rc) {

@@ -23,7 +23,7 @@ constexpr int XF_W = 18;      // window elements: V + 9 + alignment slack (even)
 constexpr int XF_MAXCH = 2;   // chunks per row per thread (Nx <= 8 * 256 * 2 = 4096)
 constexpr int PSF_RB = 192;   // staged rows per p-shift buffer (two CTAs per SM)
 static_assert(PSF_RB % PS_BH == 0, "a staged window is whole TMA boxes: the slot must hold nb * PS_BH rows");
-// Single-grid p-shift: PSF_RG compute warps and one producer warp (16 warps per SM at two CTAs, so
+// p-shift: PSF_RG compute warps and one producer warp (16 warps per SM at two CTAs, so
 // that the compute warps keep 128 registers), tiles of PS_TW columns x PSF_TH rows, PSF_NB in flight
 constexpr int PSF_RG = 7;
 constexpr int PSF_TH = PSF_RG * PS_RPT;
@@ -751,8 +751,7 @@ __global__ void __launch_bounds__(XXF_THREADS_MAX, 1) xxshift_fx_kernel(const __
 // Input-stationary accumulation for the p-shift: elements u and u + 1 of a column's window (X0, X1;
 // X1 absent when !second) fed to the PS_RPT outputs they touch.  Their two products for an output
 // enter its int64 sum in one three-input add (two IMAD.WIDE + IADD3 + IADD3.X) instead of two 64-bit
-// multiply-adds (three instructions each on this GPU).  Shared by the single-grid and batched
-// p-shifts, which therefore give the same bits.
+// multiply-adds (three instructions each on this GPU).
 __device__ __forceinline__ void psfx_feed2(int u, long long X0, long long X1, bool second, const FxW& w,
                                            long long (&M)[PS_RPT], float2 (&S)[PS_RPT])
 {
@@ -872,7 +871,7 @@ __device__ __forceinline__ void psfx_store(bool interior, const TileWin& t, cons
     }
 }
 
-// Single-grid p-shift, warp-specialised: warp PSF_RG (the producer) prepares each tile of this CTA
+// p-shift, warp-specialised (single grids and the batched form): warp PSF_RG (the producer) prepares each tile of this CTA
 // into one of PSF_NB slots -- its window of input rows by 2-D TMA boxes (zero fill), its columns'
 // foot offsets and split filters -- and the PSF_RG compute warps take the slots in turn on full /
 // empty mbarriers, with no CTA-wide barrier per tile.  Thread (warp g, lane c) computes the PS_RPT
@@ -1002,112 +1001,6 @@ __device__ __forceinline__ void pshift_fx_ws_body(const CUtensorMap* tmap, const
     if (rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
 }
 
-// Batched p-shift: every warp works out each tile's window and its column's offset and filters
-// itself (the filters of the next tile prefetched into L1 by warp 0); one CTA-wide barrier per tile
-// releases the buffer.  On the batch's small grids this measured faster than the staged form.
-template <bool PPER>
-__device__ __forceinline__ void pshift_fx_body(const CUtensorMap* tmap, const PShiftArgs& a, const EmulArgs& em)
-{
-    extern __shared__ __align__(128) unsigned char smem_dyn[];
-    unsigned char* smem_raw = align128(smem_dyn);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    long long* bufs = reinterpret_cast<long long*>(smem_raw + 128);
-    constexpr int BUF = PSF_RB * PS_TW;
-
-    const long long* __restrict__ fin = static_cast<const long long*>(a.fin);
-    long long* __restrict__ fout = static_cast<long long*>(a.fout);
-    const int Nx = a.Nx, Np = a.Np;
-    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
-    const int ntx = (Nx + PS_TW - 1) / PS_TW, nty = (Np + PS_TH - 1) / PS_TH;
-    const int ntiles = ntx * nty;
-    const int G = gridDim.x;
-    uint32_t rng = 0;   // OR of (high word + 2^29) of every stored result
-
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_barrier_init();
-        prefetch_tensormap(tmap);
-    }
-    __syncthreads();
-
-    auto issue = [&](int b, const TileWin& t) {
-        if (t.smem_ok) {
-            mbar_arrive_expect_tx(&bars[b], (uint32_t)(t.nb * PS_BH * PS_TW * 8));
-            for (int q = 0; q < t.nb; ++q)
-                tma_load_2d(bufs + (size_t)b * BUF + (size_t)q * PS_BH * PS_TW, tmap, t.i0, t.r0 + q * PS_BH, &bars[b]);
-        } else {
-            mbar_arrive_expect_tx(&bars[b], 0u);
-        }
-    };
-
-    int tile = blockIdx.x;
-    if (grp == 0 && tile < ntiles) {
-        int n0l;
-        bool cv;
-        const TileWin t0 = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0l, cv);
-        if (lane == 0) issue(0, t0);
-    }
-
-    int q = 0;
-    bool failed = false;
-    for (; tile < ntiles; tile += G, ++q) {
-        const int b = q & 1;
-        const int nt = tile + G;
-        if (grp == 0 && nt < ntiles) {
-            int n0l;
-            bool cv;
-            const TileWin tn = tile_window<PPER, PSF_RB>(nt, ntx, em.n0, Nx, lane, n0l, cv);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue(b ^ 1, tn);
-            }
-            if (cv) {   // the next tile's filters into L1 now, so that no warp waits for L2 on them then
-                const size_t in = (size_t)tn.i0 + lane;
-#pragma unroll
-                for (int k = 0; k < NTAP; ++k) {
-                    prefetch_l1(em.Wh + (size_t)k * Nx + in);
-                    prefetch_l1(em.wl + (size_t)k * Nx + in);
-                    prefetch_l1(em.wf + (size_t)k * Nx + in);
-                }
-            }
-        }
-        int n0_i;
-        bool colvalid;
-        const TileWin t = tile_window<PPER, PSF_RB>(tile, ntx, em.n0, Nx, lane, n0_i, colvalid);
-        FxW w;
-        const size_t ic = (size_t)t.i0 + lane;
-#pragma unroll
-        for (int k = 0; k < NTAP; ++k) {
-            w.Wh[k] = colvalid ? em.Wh[(size_t)k * Nx + ic] : 0;
-            w.wlr[k] = colvalid ? make_float2(em.wl[(size_t)k * Nx + ic], em.wf[(size_t)k * Nx + ic] * 9.313225746154785e-10f)
-                                : make_float2(0.f, 0.f);
-        }
-        const int i = t.i0 + lane;
-        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
-        if (ok) {
-            const long long* buf = bufs + (size_t)b * BUF;
-            const int jb = t.j0 + grp * PS_RPT;
-            const int base = jb + n0_i - 4 - t.r0;
-            long long M[PS_RPT];
-            float2 S[PS_RPT];
-            psfx_accumulate<PPER>(t, buf, base, fin, jb, n0_i, i, colvalid, Nx, Np, w, M, S);
-            psfx_store<PPER>(psfx_interior<PPER>(t, Nx, Np), t, buf, base, fin, fout, jb, n0_i, i, colvalid, Nx, Np, em,
-                             M, S, rng);
-        }
-        if (__syncthreads_or(!ok)) {   // also: every thread done with buffer b before it is refilled
-            failed = true;
-            break;
-        }
-    }
-    if (rng >= (1u << 30)) atomicCAS(a.err, 0, DEV_ERR_RANGE);
-    if (failed && tid == 0) {
-        atomicCAS(a.err, 0, DEV_ERR_PSHIFT_WAIT);
-        if (tile + G < ntiles) mbar_wait_bounded(&bars[(q + 1) & 1], (uint32_t)(((q + 1) >> 1) & 1), WAIT_LIMIT_NS);
-        mbar_wait_bounded(&bars[q & 1], (uint32_t)((q >> 1) & 1), WAIT_LIMIT_NS);
-    }
-}
-
 template <bool PPER>
 __global__ void __launch_bounds__(PSF_THREADS, 2) pshift_fx_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                      PShiftArgs a, EmulArgs em)
@@ -1115,9 +1008,10 @@ __global__ void __launch_bounds__(PSF_THREADS, 2) pshift_fx_kernel(const __grid_
     pshift_fx_ws_body<PPER>(&tmap, a, em);
 }
 
-// Batched form: the slot's tensor map sits in global memory next to its arguments.
+// Batched form (the same warp-specialised body): the slot's tensor map sits in global memory next to
+// its arguments.
 template <bool PPER>
-__global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_batch_kernel(const CUtensorMap* __restrict__ tmaps,
+__global__ void __launch_bounds__(PSF_THREADS, 2) pshift_fx_batch_kernel(const CUtensorMap* __restrict__ tmaps,
                                                                            const PShiftArgs* __restrict__ args,
                                                                            const EmulArgs* __restrict__ ems,
                                                                            const int* __restrict__ ver)
@@ -1127,7 +1021,7 @@ __global__ void __launch_bounds__(PS_TW * PS_RG, 2) pshift_fx_batch_kernel(const
     const PShiftArgs a = args[k];
     if (a.Nx <= 0) return;
     const EmulArgs em = ems[slot];
-    pshift_fx_body<PPER>(tmaps + k, a, em);
+    pshift_fx_ws_body<PPER>(tmaps + k, a, em);
 }
 
 int xshift_fx_max_cols(int threads) { return XF_V * threads * XF_MAXCH; }
@@ -1206,7 +1100,7 @@ cudaError_t launch_pshift_fx_batch(int slots, int ctas_per_slot, const CUtensorM
                                    const EmulArgs* ems, const int* ver, cudaStream_t st)
 {
     const dim3 grid(ctas_per_slot, slots);
-    pshift_fx_batch_kernel<false><<<grid, PS_TW * PS_RG, pshift_fx_smem_bytes(), st>>>(tmaps, args, ems, ver);
+    pshift_fx_batch_kernel<false><<<grid, PSF_THREADS, pshift_fx_smem_bytes(), st>>>(tmaps, args, ems, ver);
     return cudaGetLastError();
 }
 
