@@ -110,6 +110,33 @@ def test_launch_accounting_and_timed_slots():
             s.fused_x = True
 
 
+def test_launches_with_filters_formed_in_other_launches():
+    """FP32 HMF: the p-shift forms its filters itself (fused x-shifts, moment record, p-shift); the ring
+    with the fixed-point force: its force launch writes the filters (fused x-shifts, merged reductions,
+    convolutions, p-shift).  The timed slots match the launches."""
+    w = I.HMF_256.resized(128, 128)
+    for prec in ("f32", "bf16"):
+        with V.Sim.from_workload(w, precision=prec) as s:
+            s.set_f(I.initial_state(w))
+            L = s.kernels_per_step()
+            assert L == 3 and s.slot_names() == ["xshift_fused", "reduce_moments", "pshift_step3"]
+            # head: x-shift, p-shift; n-1 mids; tail: x-shift, moments
+            assert s.launches(1) == 4 and s.launches(10) == 2 + 9 * L + 2
+            assert s.step_timed(3).shape == (L,)
+            s.fused_x = False
+            assert s.kernels_per_step() == 4 and len(s.slot_names()) == 4 and s.launches(10) == 40
+    r = I.RING_2048.resized(128, 128)
+    for prec in ("fx64", "f32"):
+        with V.Sim.from_workload(r, precision=prec) as s:
+            s.set_f(I.initial_state(r))
+            assert s.ring_method == "fixed"
+            L = s.kernels_per_step()
+            assert L == 4 and len(s.slot_names()) == L
+            assert s.step_timed(3).shape == (L,)
+            s.ring_method = "direct"   # the filters get a launch of their own again
+            assert s.kernels_per_step() == L + 3 and len(s.slot_names()) == L + 3
+
+
 FREE_PERIODIC = I.Workload("free_periodic", "free", 512, 256, -np.pi, np.pi, -4.0, 4.0, True, False, 0.05, 4)
 FREE_ZERO = I.Workload("free_zero", "free", 256, 128, -8.0, 8.0, -4.0, 4.0, False, False, 2.0, 4)
 
